@@ -1,0 +1,183 @@
+/*
+ * sym.h — C ABI of the GB300 supernodal Cholesky library (numeric phase of decoupled sparse
+ * Cholesky, after Sympiler, arXiv 1705.06575).
+ *
+ * The library splits the work the way the paper does (Sec. 2.2, Sec. 3.2): a host-side symbolic
+ * inspector runs once per sparsity pattern (sym_analyze*), and CUDA kernels re-run the numeric
+ * factorization A = L L^T (sym_factor*) and the triangular solves (sym_solve*) for every new set
+ * of values on that pattern.
+ *
+ * Conventions for every call:
+ *   - A is symmetric positive definite; only its lower triangle is passed, in compressed sparse
+ *     column form, 0-based: Ap (int64, n+1 entries), Ai (int32, Ap[n] entries, strictly
+ *     increasing within a column, the diagonal present and first), Ax (float64, same order as Ai).
+ *     This is the input form of Sec. 2.1 / Sec. 4.2 of the paper.
+ *   - Return value 0 is success; negative values are the SYM_ERR_* codes below. No call aborts
+ *     or traps; a failed call leaves the handle usable unless it says otherwise.
+ *   - The caller keeps ownership of every pointer it passes. sym_analyze copies the pattern.
+ *     The handle owns the factor L (device memory) and its plan; sym_free releases both.
+ *   - Device pointers are plain CUDA device addresses of the current device (for example
+ *     torch.Tensor.data_ptr()). "_host" variants take host pointers and copy inside.
+ *   - Work is issued on the handle's stream (sym_set_stream; default: the legacy default
+ *     stream). Calls on one handle are not thread-safe; different handles are independent.
+ */
+#ifndef SYM_H_
+#define SYM_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Error codes. */
+#define SYM_OK 0
+#define SYM_ERR_INVALID -1 /* bad pattern, permutation, option or argument */
+#define SYM_ERR_NOT_SPD -2 /* non-positive or NaN pivot; see sym_last_error_column */
+#define SYM_ERR_CUDA -3    /* a CUDA runtime call failed (message: sym_last_error_string) */
+#define SYM_ERR_OOM -4     /* device or host allocation failed */
+#define SYM_ERR_STATE -5   /* call out of order (solve before factor, host-only handle) */
+#define SYM_ERR_TIMEOUT -6 /* a bounded device wait ran out */
+#define SYM_ERR_LIMIT -7   /* a size exceeds a documented limit */
+
+/* Orderings for sym_analyze_perm. */
+#define SYM_ORDER_NATURAL 0 /* identity (then etree postorder) */
+#define SYM_ORDER_GIVEN 1   /* the caller's perm (then etree postorder) */
+
+/* Option flags. */
+#define SYM_FLAG_HOST_ONLY 1u /* run the inspector only; no device memory, no factor/solve */
+
+typedef struct sym_handle_s *sym_handle;
+
+/* Inspector options. nrelax/zrelax_permille set the relaxed-amalgamation rule: supernode S is
+ * merged into the next supernode P when parent(last(S)) = last(S)+1 and, with m the merged column
+ * count and z the fraction of explicit zeros in the merged trapezoid,
+ *   m <= nrelax[0], or (m <= nrelax[1] and z <= zrelax[0]/1000),
+ *   or (m <= nrelax[2] and z <= zrelax[1]/1000), or z <= zrelax[2]/1000;
+ * passes repeat until nothing merges. The paper disables amalgamation (Sec. 4.1); set
+ * amalgamate = 0 for fundamental supernodes only (Sec. 3.2). */
+typedef struct {
+  int32_t ordering;            /* SYM_ORDER_* */
+  int32_t amalgamate;          /* 1 (default) or 0 */
+  int32_t nrelax[3];           /* default 4, 16, 48 */
+  int32_t zrelax_permille[3];  /* default 800, 100, 50 */
+  uint32_t flags;              /* SYM_FLAG_* */
+  int32_t reserved[8];
+} sym_options;
+
+/* Statistics of an analyzed pattern (sym_info). */
+typedef struct {
+  int64_t n;
+  int64_t nnz_a;            /* entries of the lower triangle of A */
+  int64_t nnz_l;            /* entries of L on its exact pattern (Eq. 1), diagonal included */
+  int64_t storage_l;        /* doubles held for L (supernodal panels, padding included) */
+  double flops;             /* sum_j c_j^2 over the exact pattern: the factor's useful flops */
+  double solve_flops;       /* per right-hand side: 2 * (2 nnz_l - n) */
+  int32_t nsuper_fund;      /* fundamental supernodes */
+  int32_t nsuper;           /* supernodes after amalgamation */
+  int32_t nlevels;          /* levels of the supernodal tree */
+  int32_t max_ncols;        /* widest supernode */
+  int64_t npairs;           /* (descendant, ancestor) update pairs */
+  int64_t nlaunch_factor;   /* kernel launches per sym_factor */
+  int64_t nlaunch_solve;    /* kernel launches per sym_solve */
+  double analyze_seconds;   /* host time of the inspector */
+  int64_t device_bytes;     /* device memory held by the handle */
+} sym_stats;
+
+/* Fill *opt with the defaults (SYM_ORDER_GIVEN with a NULL perm means natural order). */
+int sym_options_default(sym_options *opt);
+
+/* Inspector with default options and the natural order (plus etree postorder). Same as
+ * sym_analyze_perm(n, Ap, Ai, NULL, NULL, out). Host pointers. */
+int sym_analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, sym_handle *out);
+
+/* Inspector (Sec. 3.2 of the paper; amalgamation and the level schedule are this library's
+ * additions). perm (nullable, host, n entries) is a fill-reducing ordering: perm[k] is the
+ * original index placed at position k. The final ordering is perm composed with the postorder
+ * of the elimination tree. Steps: validate, permute, etree, postorder, column counts,
+ * fundamental supernodes, amalgamation, supernodal row structure, descendant lists (the block
+ * prune-set), relative row maps, level schedule, kernel task lists; then one upload of the
+ * plan to the current device (unless SYM_FLAG_HOST_ONLY). Errors: SYM_ERR_INVALID for a bad
+ * pattern or permutation, SYM_ERR_OOM, SYM_ERR_CUDA. On error *out is NULL. */
+int sym_analyze_perm(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm,
+                     const sym_options *opt, sym_handle *out);
+
+/* Use this CUDA stream (a cudaStream_t passed as void*) for all later work of the handle. */
+int sym_set_stream(sym_handle h, void *stream);
+
+/* Numeric factorization (Sec. 3.2: supernodal left-looking Cholesky; VS-Block turns each
+ * supernode into a dense POTRF of its diagonal block and TRSMs of the rows below, and VI-Prune
+ * restricts the update to the descendants in the prune-set). Ax: DEVICE pointer, Ap[n] float64
+ * values in the order of the Ai given to the inspector. Enqueues the scatter of A into the
+ * supernodal panels and the level-by-level update / POTRF / TRSM kernels on the handle's stream,
+ * then waits for them and reads the pivot status. Returns SYM_ERR_NOT_SPD when a pivot is not
+ * positive (or is NaN); sym_last_error_column then gives the first failing column in the
+ * caller's numbering and the factor is not usable. */
+int sym_factor(sym_handle h, const double *Ax);
+
+/* As sym_factor but returns right after enqueueing (no wait, no status check). Call
+ * sym_status afterwards to wait and read the pivot status. */
+int sym_factor_async(sym_handle h, const double *Ax);
+
+/* Wait for the handle's stream and return the status of the last factorization. */
+int sym_status(sym_handle h);
+
+/* As sym_factor with Ax in host memory (copied to the device inside). */
+int sym_factor_host(sym_handle h, const double *Ax);
+
+/* Solve A x = b with the current factor (Sec. 3.1 supernodal forward substitution, then the
+ * transposed backward sweep, which the paper does not spell out). b, x: DEVICE pointers of n
+ * float64; they may alias. SYM_ERR_STATE before a successful sym_factor. */
+int sym_solve(sym_handle h, const double *b, double *x);
+
+/* nrhs right-hand sides, column-major: B (ldb >= n) and X (ldx >= n), DEVICE pointers. */
+int sym_solve_multi(sym_handle h, int32_t nrhs, const double *B, int64_t ldb, double *X,
+                    int64_t ldx);
+
+/* As sym_solve_multi with host pointers (copied inside). */
+int sym_solve_host(sym_handle h, int32_t nrhs, const double *B, int64_t ldb, double *X,
+                   int64_t ldx);
+
+/* Statistics of the analyzed pattern. */
+int sym_info(sym_handle h, sym_stats *s);
+
+/* First failing column (caller's numbering) of the last SYM_ERR_NOT_SPD, else -1. */
+int sym_last_error_column(sym_handle h, int64_t *col);
+
+/* Copy the factor to host memory in its supernodal panel layout (storage_l doubles). */
+int sym_get_factor_host(sym_handle h, double *Lx_host);
+
+/* Export an integer array of the symbolic plan (host copy) for checks against an independent
+ * inspector. what = SYM_EXPORT_*; returns the element count (>= 0) or an error. When out is
+ * NULL only the count is returned. Element types are listed per item. */
+#define SYM_EXPORT_PERM 1        /* int32[n]: final ordering, perm[k] = original index */
+#define SYM_EXPORT_PARENT 2      /* int32[n]: etree of the permuted matrix, -1 for roots */
+#define SYM_EXPORT_COLCOUNT 3    /* int64[n]: |L_j| including the diagonal */
+#define SYM_EXPORT_FSUPER 4      /* int32[nfund+1]: first column of each fundamental supernode */
+#define SYM_EXPORT_SUPER 5       /* int32[nsuper+1]: first column of each supernode */
+#define SYM_EXPORT_ROWPTR 6      /* int64[nsuper+1]: offsets of each supernode's row list */
+#define SYM_EXPORT_ROWS 7        /* int32[]: sorted rows of each supernode (columns first) */
+#define SYM_EXPORT_SPARENT 8     /* int32[nsuper]: supernodal tree parent, -1 for roots */
+#define SYM_EXPORT_DESCPTR 9     /* int64[nsuper+1]: offsets of each descendant list */
+#define SYM_EXPORT_DESC 10       /* int32[]: descendants K of each J, increasing */
+#define SYM_EXPORT_DESCR0 11     /* int64[]: first position in rows(K) at or after first(J) */
+#define SYM_EXPORT_DESCNIN 12    /* int32[]: rows of K that fall in cols(J) */
+#define SYM_EXPORT_RELPTR 13     /* int64[npairs+1]: offsets of the relative maps */
+#define SYM_EXPORT_REL 14        /* int32[]: position of rows(K)[r0+t] within rows(J) */
+#define SYM_EXPORT_LEVEL 15      /* int32[nsuper]: level of each supernode */
+#define SYM_EXPORT_LEVELPTR 16   /* int32[nlevels+1] */
+#define SYM_EXPORT_LEVELLIST 17  /* int32[nsuper]: supernodes by level, increasing within one */
+#define SYM_EXPORT_LXPTR 18      /* int64[nsuper+1]: offset of each panel in the factor storage */
+int64_t sym_export(sym_handle h, int32_t what, void *out);
+
+/* Text for an error code, and the message of the last failure on this thread. */
+const char *sym_error_string(int code);
+const char *sym_last_error_string(void);
+
+/* Release the handle and everything it owns. NULL is allowed. */
+void sym_free(sym_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SYM_H_ */

@@ -1,0 +1,295 @@
+"""GB300 supernodal Cholesky (numeric phase of decoupled sparse Cholesky, after Sympiler).
+
+Thin Python binding of the C ABI in ``include/sym.h``: the functions below have the same names
+and arguments as the C entry points and only marshal arguments (numpy arrays for host data,
+``torch.Tensor`` or raw integers for device pointers). Every step of the factorization and the
+solve runs in the CUDA kernels of ``_build/libsym.so``; there is no Python or CPU fallback. If
+the library cannot be built or loaded the import of the binding fails with an error.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = [
+    "SymError", "sym_options", "sym_stats", "sym_options_default", "sym_analyze",
+    "sym_analyze_perm", "sym_set_stream", "sym_factor", "sym_factor_async", "sym_status",
+    "sym_factor_host", "sym_solve", "sym_solve_multi", "sym_solve_host", "sym_info",
+    "sym_last_error_column", "sym_get_factor_host", "sym_export", "sym_free", "load", "Solver",
+    "EXPORTS",
+]
+
+SYM_OK = 0
+SYM_ERR_INVALID = -1
+SYM_ERR_NOT_SPD = -2
+SYM_ERR_CUDA = -3
+SYM_ERR_OOM = -4
+SYM_ERR_STATE = -5
+SYM_ERR_TIMEOUT = -6
+SYM_ERR_LIMIT = -7
+SYM_ORDER_NATURAL = 0
+SYM_ORDER_GIVEN = 1
+SYM_FLAG_HOST_ONLY = 1
+
+# name -> (code, numpy dtype)
+EXPORTS = {
+    "perm": (1, np.int32), "parent": (2, np.int32), "colcount": (3, np.int64),
+    "fsuper": (4, np.int32), "super": (5, np.int32), "rowptr": (6, np.int64),
+    "rows": (7, np.int32), "sparent": (8, np.int32), "descptr": (9, np.int64),
+    "desc": (10, np.int32), "descr0": (11, np.int64), "descnin": (12, np.int32),
+    "relptr": (13, np.int64), "rel": (14, np.int32), "level": (15, np.int32),
+    "levelptr": (16, np.int32), "levellist": (17, np.int32), "lxptr": (18, np.int64),
+}
+
+
+class SymError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{msg} (code {code})")
+        self.code = code
+
+
+class sym_options(ct.Structure):
+    _fields_ = [("ordering", ct.c_int32), ("amalgamate", ct.c_int32), ("nrelax", ct.c_int32 * 3),
+                ("zrelax_permille", ct.c_int32 * 3), ("flags", ct.c_uint32),
+                ("reserved", ct.c_int32 * 8)]
+
+
+class sym_stats(ct.Structure):
+    _fields_ = [("n", ct.c_int64), ("nnz_a", ct.c_int64), ("nnz_l", ct.c_int64),
+                ("storage_l", ct.c_int64), ("flops", ct.c_double), ("solve_flops", ct.c_double),
+                ("nsuper_fund", ct.c_int32), ("nsuper", ct.c_int32), ("nlevels", ct.c_int32),
+                ("max_ncols", ct.c_int32), ("npairs", ct.c_int64), ("nlaunch_factor", ct.c_int64),
+                ("nlaunch_solve", ct.c_int64), ("analyze_seconds", ct.c_double),
+                ("device_bytes", ct.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load():
+    """Build (if stale) and load the CUDA library; raise if that is impossible."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ct.CDLL(_build.build())
+        P, i64, i32, I = ct.c_void_p, ct.c_int64, ct.c_int32, ct.c_int
+        sigs = {
+            "sym_options_default": ([ct.POINTER(sym_options)], I),
+            "sym_analyze": ([i64, P, P, ct.POINTER(P)], I),
+            "sym_analyze_perm": ([i64, P, P, P, ct.POINTER(sym_options), ct.POINTER(P)], I),
+            "sym_set_stream": ([P, P], I),
+            "sym_factor": ([P, P], I),
+            "sym_factor_async": ([P, P], I),
+            "sym_status": ([P], I),
+            "sym_factor_host": ([P, P], I),
+            "sym_solve": ([P, P, P], I),
+            "sym_solve_multi": ([P, i32, P, i64, P, i64], I),
+            "sym_solve_host": ([P, i32, P, i64, P, i64], I),
+            "sym_info": ([P, ct.POINTER(sym_stats)], I),
+            "sym_last_error_column": ([P, ct.POINTER(i64)], I),
+            "sym_get_factor_host": ([P, P], I),
+            "sym_export": ([P, i32, P], i64),
+            "sym_error_string": ([I], ct.c_char_p),
+            "sym_last_error_string": ([], ct.c_char_p),
+            "sym_free": ([P], None),
+        }
+        for name, (args, res) in sigs.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = lib
+        return lib
+
+
+def _check(rc):
+    if rc < 0:
+        lib = load()
+        raise SymError(rc, lib.sym_last_error_string().decode() or lib.sym_error_string(rc).decode())
+    return rc
+
+
+def _host(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _dptr(x):
+    """Device address of a torch tensor (or an int address)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def sym_options_default():
+    o = sym_options()
+    _check(load().sym_options_default(ct.byref(o)))
+    return o
+
+
+def sym_analyze(n, Ap, Ai):
+    Ap, Ai = _host(Ap, np.int64), _host(Ai, np.int32)
+    h = ct.c_void_p()
+    _check(load().sym_analyze(int(n), Ap.ctypes.data, Ai.ctypes.data, ct.byref(h)))
+    return h
+
+
+def sym_analyze_perm(n, Ap, Ai, perm=None, opt=None):
+    Ap, Ai = _host(Ap, np.int64), _host(Ai, np.int32)
+    pp = None if perm is None else _host(perm, np.int32)
+    h = ct.c_void_p()
+    _check(load().sym_analyze_perm(int(n), Ap.ctypes.data, Ai.ctypes.data,
+                                   None if pp is None else pp.ctypes.data,
+                                   None if opt is None else ct.byref(opt), ct.byref(h)))
+    return h
+
+
+def sym_set_stream(h, stream):
+    """stream: a torch.cuda.Stream, a raw cudaStream_t integer, or None (legacy default)."""
+    s = getattr(stream, "cuda_stream", stream)
+    return _check(load().sym_set_stream(h, s))
+
+
+def sym_factor(h, Ax):
+    return _check(load().sym_factor(h, _dptr(Ax)))
+
+
+def sym_factor_async(h, Ax):
+    return _check(load().sym_factor_async(h, _dptr(Ax)))
+
+
+def sym_status(h):
+    return _check(load().sym_status(h))
+
+
+def sym_factor_host(h, Ax):
+    Ax = _host(Ax, np.float64)
+    return _check(load().sym_factor_host(h, Ax.ctypes.data))
+
+
+def sym_solve(h, b, x):
+    return _check(load().sym_solve(h, _dptr(b), _dptr(x)))
+
+
+def sym_solve_multi(h, nrhs, B, ldb, X, ldx):
+    return _check(load().sym_solve_multi(h, int(nrhs), _dptr(B), int(ldb), _dptr(X), int(ldx)))
+
+
+def sym_solve_host(h, B):
+    """Host right-hand sides (n or n x nrhs); returns X with the same shape."""
+    B = np.asarray(B, dtype=np.float64)
+    one = B.ndim == 1
+    Bf = np.asfortranarray(B[:, None] if one else B)
+    X = np.zeros_like(Bf, order="F")
+    n = Bf.shape[0]
+    _check(load().sym_solve_host(h, Bf.shape[1], Bf.ctypes.data, n, X.ctypes.data, n))
+    return X[:, 0] if one else X
+
+
+def sym_info(h):
+    s = sym_stats()
+    _check(load().sym_info(h, ct.byref(s)))
+    return s
+
+
+def sym_last_error_column(h):
+    c = ct.c_int64()
+    _check(load().sym_last_error_column(h, ct.byref(c)))
+    return c.value
+
+
+def sym_get_factor_host(h):
+    st = sym_info(h)
+    out = np.zeros(st.storage_l, dtype=np.float64)
+    _check(load().sym_get_factor_host(h, out.ctypes.data))
+    return out
+
+
+def sym_export(h, what):
+    code, dt = EXPORTS[what]
+    lib = load()
+    cnt = _check(lib.sym_export(h, code, None))
+    out = np.zeros(cnt, dtype=dt)
+    if cnt:
+        _check(lib.sym_export(h, code, out.ctypes.data))
+    return out
+
+
+def sym_free(h):
+    if h:
+        load().sym_free(h)
+
+
+class Solver:
+    """Owning wrapper of one handle: analyze on construction, free on close."""
+
+    def __init__(self, n, Ap, Ai, perm=None, opt=None, host_only=False):
+        if opt is None:
+            opt = sym_options_default()
+        if perm is not None:
+            opt.ordering = SYM_ORDER_GIVEN
+        if host_only:
+            opt.flags |= SYM_FLAG_HOST_ONLY
+        self.n = int(n)
+        self.h = sym_analyze_perm(n, Ap, Ai, perm, opt)
+
+    def info(self):
+        return sym_info(self.h)
+
+    def export(self, what):
+        return sym_export(self.h, what)
+
+    def set_stream(self, stream):
+        sym_set_stream(self.h, stream)
+
+    def factor(self, Ax):
+        return sym_factor(self.h, Ax)
+
+    def factor_async(self, Ax):
+        return sym_factor_async(self.h, Ax)
+
+    def status(self):
+        return sym_status(self.h)
+
+    def factor_host(self, Ax):
+        return sym_factor_host(self.h, Ax)
+
+    def solve(self, B, X=None):
+        """Device solve. B, X: torch float64 tensors of shape (n,) or (nrhs, n) rows = columns
+        of the column-major block (each row of the tensor is one right-hand side)."""
+        if X is None:
+            X = B.new_empty(B.shape)
+        if B.dim() == 1:
+            sym_solve(self.h, B, X)
+        else:
+            sym_solve_multi(self.h, B.shape[0], B, B.stride(0), X, X.stride(0))
+        return X
+
+    def solve_host(self, B):
+        return sym_solve_host(self.h, B)
+
+    def factor_panels(self):
+        return sym_get_factor_host(self.h)
+
+    def error_column(self):
+        return sym_last_error_column(self.h)
+
+    def close(self):
+        if self.h:
+            sym_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,398 @@
+// capi.cu — the C ABI of include/sym.h: handle life cycle, plan upload, executor calls.
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "kernels.h"
+#include "plan.h"
+#include "sym.h"
+
+struct sym_handle_s {
+  sym::Plan plan;
+  bool host_only = true;
+  int device = -1;
+  cudaStream_t stream = nullptr;
+  sym::DevPlan dp;
+  // device allocations owned by the handle
+  void *d_sn = nullptr, *d_rows = nullptr, *d_rel = nullptr, *d_amap = nullptr, *d_updt = nullptr,
+       *d_upde = nullptr, *d_tasks = nullptr, *d_perm = nullptr;
+  double *d_Lx = nullptr;
+  long long *d_status = nullptr;
+  long long *h_status = nullptr;  // pinned: [0] holds the reset value, [1] receives the status
+  double *d_y = nullptr;          // solve work array
+  int64_t y_cap = 0;
+  double *d_stage = nullptr;      // staging for the host-pointer variants
+  int64_t stage_cap = 0;
+  int64_t device_bytes = 0;
+  bool factored = false;
+  int64_t err_col = -1;
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string &msg) {
+  g_last_error = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? SYM_ERR_OOM : SYM_ERR_CUDA;
+}
+
+#define CUDA_TRY(expr, what)                       \
+  do {                                             \
+    cudaError_t e_ = (expr);                       \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+template <typename V>
+int upload(const std::vector<V> &v, void **dst, int64_t &bytes) {
+  size_t sz = v.size() * sizeof(V);
+  if (sz == 0) sz = sizeof(V);
+  CUDA_TRY(cudaMalloc(dst, sz), "cudaMalloc(plan)");
+  bytes += (int64_t)sz;
+  if (!v.empty()) CUDA_TRY(cudaMemcpy(*dst, v.data(), v.size() * sizeof(V), cudaMemcpyHostToDevice), "cudaMemcpy(plan)");
+  return SYM_OK;
+}
+
+void release_device(sym_handle_s *h) {
+  void *ptrs[] = {h->d_sn, h->d_rows, h->d_rel, h->d_amap, h->d_updt, h->d_upde, h->d_tasks,
+                  h->d_perm, h->d_Lx, h->d_status, h->d_y, h->d_stage};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  if (h->h_status) cudaFreeHost(h->h_status);
+}
+
+int ensure_y(sym_handle_s *h, int64_t count) {
+  if (count <= h->y_cap) return SYM_OK;
+  if (h->d_y) cudaFree(h->d_y);
+  h->d_y = nullptr;
+  h->y_cap = 0;
+  CUDA_TRY(cudaMalloc(&h->d_y, sizeof(double) * (count > 0 ? count : 1)), "cudaMalloc(solve work)");
+  h->y_cap = count;
+  return SYM_OK;
+}
+
+int ensure_stage(sym_handle_s *h, int64_t count) {
+  if (count <= h->stage_cap) return SYM_OK;
+  if (h->d_stage) cudaFree(h->d_stage);
+  h->d_stage = nullptr;
+  h->stage_cap = 0;
+  CUDA_TRY(cudaMalloc(&h->d_stage, sizeof(double) * (count > 0 ? count : 1)), "cudaMalloc(staging)");
+  h->stage_cap = count;
+  return SYM_OK;
+}
+
+int check_device(sym_handle_s *h) {
+  if (!h) return fail(SYM_ERR_INVALID, "null handle");
+  if (h->host_only) return fail(SYM_ERR_STATE, "handle was analyzed with SYM_FLAG_HOST_ONLY");
+  int dev = -1;
+  CUDA_TRY(cudaGetDevice(&dev), "cudaGetDevice");
+  if (dev != h->device) return fail(SYM_ERR_STATE, "the current device is not the handle's device");
+  return SYM_OK;
+}
+
+int finish_status(sym_handle_s *h) {
+  CUDA_TRY(cudaStreamSynchronize(h->stream), "factor");
+  long long s = h->h_status[1];
+  if (s != LLONG_MAX) {
+    h->factored = false;
+    h->err_col = (s >= 0 && s < h->plan.n) ? h->plan.perm[s] : -1;
+    return fail(SYM_ERR_NOT_SPD, "matrix is not positive definite (pivot at column " +
+                                     std::to_string(h->err_col) + ")");
+  }
+  h->factored = true;
+  h->err_col = -1;
+  return SYM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sym_options_default(sym_options *opt) {
+  if (!opt) return SYM_ERR_INVALID;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->ordering = SYM_ORDER_GIVEN;
+  opt->amalgamate = 1;
+  opt->nrelax[0] = 4;
+  opt->nrelax[1] = 16;
+  opt->nrelax[2] = 48;
+  opt->zrelax_permille[0] = 800;
+  opt->zrelax_permille[1] = 100;
+  opt->zrelax_permille[2] = 50;
+  opt->flags = 0;
+  return SYM_OK;
+}
+
+int sym_analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, sym_handle *out) {
+  return sym_analyze_perm(n, Ap, Ai, nullptr, nullptr, out);
+}
+
+int sym_analyze_perm(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm,
+                     const sym_options *opt_in, sym_handle *out) {
+  if (!out) return fail(SYM_ERR_INVALID, "null output handle");
+  *out = nullptr;
+  sym_options opt;
+  if (opt_in) opt = *opt_in;
+  else sym_options_default(&opt);
+  if (opt.ordering != SYM_ORDER_NATURAL && opt.ordering != SYM_ORDER_GIVEN)
+    return fail(SYM_ERR_INVALID, "unknown ordering");
+  for (int i = 0; i < 3; ++i)
+    if (opt.nrelax[i] < 0 || opt.zrelax_permille[i] < 0 || opt.zrelax_permille[i] > 1000)
+      return fail(SYM_ERR_INVALID, "bad amalgamation parameters");
+  sym_handle_s *h = new (std::nothrow) sym_handle_s();
+  if (!h) return fail(SYM_ERR_OOM, "host allocation");
+  try {
+    std::string err;
+    int rc = sym::analyze(n, Ap, Ai, perm, opt, h->plan, err);
+    if (rc != SYM_OK) {
+      delete h;
+      return fail(rc, err);
+    }
+  } catch (const std::bad_alloc &) {
+    delete h;
+    return fail(SYM_ERR_OOM, "host allocation during analysis");
+  } catch (const std::exception &e) {
+    delete h;
+    return fail(SYM_ERR_INVALID, e.what());
+  }
+  h->host_only = (opt.flags & SYM_FLAG_HOST_ONLY) != 0;
+  if (!h->host_only) {
+    int rc = SYM_OK;
+    auto &P = h->plan;
+    int64_t bytes = 0;
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) rc = cuda_fail(e, "cudaGetDevice");
+    if (!rc) rc = upload(P.snodes, &h->d_sn, bytes);
+    if (!rc) rc = upload(P.rows, &h->d_rows, bytes);
+    if (!rc) rc = upload(P.rel, &h->d_rel, bytes);
+    if (!rc) rc = upload(P.amap, &h->d_amap, bytes);
+    if (!rc) rc = upload(P.upd_tasks, &h->d_updt, bytes);
+    if (!rc) rc = upload(P.upd_entries, &h->d_upde, bytes);
+    if (!rc) rc = upload(P.tasks, &h->d_tasks, bytes);
+    if (!rc) rc = upload(P.perm, &h->d_perm, bytes);
+    if (!rc) {
+      e = cudaMalloc(&h->d_Lx, sizeof(double) * (P.storage() > 0 ? P.storage() : 1));
+      if (e != cudaSuccess) rc = cuda_fail(e, "cudaMalloc(L)");
+      else bytes += sizeof(double) * P.storage();
+    }
+    if (!rc) {
+      e = cudaMalloc(&h->d_status, sizeof(long long));
+      if (e != cudaSuccess) rc = cuda_fail(e, "cudaMalloc(status)");
+    }
+    if (!rc) {
+      e = cudaMallocHost(&h->h_status, 2 * sizeof(long long));
+      if (e != cudaSuccess) rc = cuda_fail(e, "cudaMallocHost(status)");
+    }
+    if (rc) {
+      release_device(h);
+      delete h;
+      return rc;
+    }
+    h->device_bytes = bytes;
+    h->dp.sn = (const sym::SNode *)h->d_sn;
+    h->dp.rows = (const int32_t *)h->d_rows;
+    h->dp.rel = (const int32_t *)h->d_rel;
+    h->dp.amap = (const int64_t *)h->d_amap;
+    h->dp.upd_tasks = (const sym::UpdTask *)h->d_updt;
+    h->dp.upd_entries = (const sym::UpdEntry *)h->d_upde;
+    h->dp.tasks = (const sym::Int4 *)h->d_tasks;
+    h->dp.perm = (const int32_t *)h->d_perm;
+    h->dp.n = P.n;
+    h->dp.nnz_a = P.nnz_a;
+    h->dp.storage = P.storage();
+  }
+  *out = h;
+  return SYM_OK;
+}
+
+int sym_set_stream(sym_handle h, void *stream) {
+  if (!h) return fail(SYM_ERR_INVALID, "null handle");
+  h->stream = (cudaStream_t)stream;
+  return SYM_OK;
+}
+
+int sym_factor_async(sym_handle h, const double *Ax) {
+  int rc = check_device(h);
+  if (rc) return rc;
+  if (!Ax && h->plan.nnz_a > 0) return fail(SYM_ERR_INVALID, "null Ax");
+  h->factored = false;
+  h->h_status[0] = LLONG_MAX;
+  CUDA_TRY(cudaMemcpyAsync(h->d_status, &h->h_status[0], sizeof(long long), cudaMemcpyHostToDevice, h->stream),
+           "status reset");
+  CUDA_TRY(sym::run_factor<double>(h->dp, h->plan.factor_launches, Ax, h->d_Lx, h->d_status, h->stream),
+           "factor kernels");
+  CUDA_TRY(cudaMemcpyAsync(&h->h_status[1], h->d_status, sizeof(long long), cudaMemcpyDeviceToHost, h->stream),
+           "status read");
+  return SYM_OK;
+}
+
+int sym_status(sym_handle h) {
+  int rc = check_device(h);
+  if (rc) return rc;
+  return finish_status(h);
+}
+
+int sym_factor(sym_handle h, const double *Ax) {
+  int rc = sym_factor_async(h, Ax);
+  if (rc) return rc;
+  return finish_status(h);
+}
+
+int sym_factor_host(sym_handle h, const double *Ax) {
+  int rc = check_device(h);
+  if (rc) return rc;
+  if (!Ax && h->plan.nnz_a > 0) return fail(SYM_ERR_INVALID, "null Ax");
+  rc = ensure_stage(h, h->plan.nnz_a);
+  if (rc) return rc;
+  CUDA_TRY(cudaMemcpyAsync(h->d_stage, Ax, sizeof(double) * h->plan.nnz_a, cudaMemcpyHostToDevice, h->stream),
+           "copy Ax");
+  return sym_factor(h, h->d_stage);
+}
+
+int sym_solve_multi(sym_handle h, int32_t nrhs, const double *B, int64_t ldb, double *X, int64_t ldx) {
+  int rc = check_device(h);
+  if (rc) return rc;
+  if (!h->factored) return fail(SYM_ERR_STATE, "no successful factorization to solve with");
+  const int64_t n = h->plan.n;
+  if (nrhs < 0 || ldb < n || ldx < n || (nrhs > 0 && n > 0 && (!B || !X)))
+    return fail(SYM_ERR_INVALID, "bad solve arguments");
+  rc = ensure_y(h, n * (int64_t)nrhs);
+  if (rc) return rc;
+  CUDA_TRY(sym::run_solve<double>(h->dp, h->plan.fwd_launches, h->plan.bwd_launches, h->d_Lx, nrhs, B, ldb,
+                                  X, ldx, h->d_y, h->stream),
+           "solve kernels");
+  return SYM_OK;
+}
+
+int sym_solve(sym_handle h, const double *b, double *x) {
+  return sym_solve_multi(h, 1, b, h ? h->plan.n : 0, x, h ? h->plan.n : 0);
+}
+
+int sym_solve_host(sym_handle h, int32_t nrhs, const double *B, int64_t ldb, double *X, int64_t ldx) {
+  int rc = check_device(h);
+  if (rc) return rc;
+  const int64_t n = h->plan.n;
+  if (nrhs < 0 || ldb < n || ldx < n) return fail(SYM_ERR_INVALID, "bad solve arguments");
+  rc = ensure_stage(h, 2 * n * (int64_t)nrhs);
+  if (rc) return rc;
+  double *dB = h->d_stage, *dX = h->d_stage + n * (int64_t)nrhs;
+  CUDA_TRY(cudaMemcpy2DAsync(dB, sizeof(double) * n, B, sizeof(double) * ldb, sizeof(double) * n, nrhs,
+                             cudaMemcpyHostToDevice, h->stream),
+           "copy B");
+  rc = sym_solve_multi(h, nrhs, dB, n, dX, n);
+  if (rc) return rc;
+  CUDA_TRY(cudaMemcpy2DAsync(X, sizeof(double) * ldx, dX, sizeof(double) * n, sizeof(double) * n, nrhs,
+                             cudaMemcpyDeviceToHost, h->stream),
+           "copy X");
+  CUDA_TRY(cudaStreamSynchronize(h->stream), "solve");
+  return SYM_OK;
+}
+
+int sym_info(sym_handle h, sym_stats *s) {
+  if (!h || !s) return fail(SYM_ERR_INVALID, "null argument");
+  const auto &P = h->plan;
+  std::memset(s, 0, sizeof(*s));
+  s->n = P.n;
+  s->nnz_a = P.nnz_a;
+  s->nnz_l = P.nnz_l;
+  s->storage_l = P.storage();
+  s->flops = P.flops;
+  s->solve_flops = 2.0 * (2.0 * (double)P.nnz_l - (double)P.n);
+  s->nsuper_fund = (int32_t)P.fsuper.size() - 1;
+  s->nsuper = P.nsuper();
+  s->nlevels = (int32_t)P.levelptr.size() - 1;
+  s->max_ncols = P.max_ncols;
+  s->npairs = (int64_t)P.desc.size();
+  s->nlaunch_factor = (int64_t)P.factor_launches.size() + 2;
+  s->nlaunch_solve = (int64_t)P.fwd_launches.size() + (int64_t)P.bwd_launches.size() + 2;
+  s->analyze_seconds = P.analyze_seconds;
+  s->device_bytes = h->device_bytes;
+  return SYM_OK;
+}
+
+int sym_last_error_column(sym_handle h, int64_t *col) {
+  if (!h || !col) return fail(SYM_ERR_INVALID, "null argument");
+  *col = h->err_col;
+  return SYM_OK;
+}
+
+int sym_get_factor_host(sym_handle h, double *Lx_host) {
+  int rc = check_device(h);
+  if (rc) return rc;
+  if (!Lx_host) return fail(SYM_ERR_INVALID, "null output");
+  CUDA_TRY(cudaStreamSynchronize(h->stream), "sync");
+  CUDA_TRY(cudaMemcpy(Lx_host, h->d_Lx, sizeof(double) * h->plan.storage(), cudaMemcpyDeviceToHost), "copy L");
+  return SYM_OK;
+}
+
+int64_t sym_export(sym_handle h, int32_t what, void *out) {
+  if (!h) return fail(SYM_ERR_INVALID, "null handle");
+  const auto &P = h->plan;
+  const void *src = nullptr;
+  int64_t count = 0;
+  size_t esz = 0;
+  switch (what) {
+#define EXP(id, vec)          \
+  case id:                    \
+    src = P.vec.data();       \
+    count = (int64_t)P.vec.size(); \
+    esz = sizeof(P.vec[0]);   \
+    break;
+    EXP(SYM_EXPORT_PERM, perm)
+    EXP(SYM_EXPORT_PARENT, parent)
+    EXP(SYM_EXPORT_COLCOUNT, colcount)
+    EXP(SYM_EXPORT_FSUPER, fsuper)
+    EXP(SYM_EXPORT_SUPER, super)
+    EXP(SYM_EXPORT_ROWPTR, rowptr)
+    EXP(SYM_EXPORT_ROWS, rows)
+    EXP(SYM_EXPORT_SPARENT, sparent)
+    EXP(SYM_EXPORT_DESCPTR, descptr)
+    EXP(SYM_EXPORT_DESC, desc)
+    EXP(SYM_EXPORT_DESCR0, descr0)
+    EXP(SYM_EXPORT_DESCNIN, descnin)
+    EXP(SYM_EXPORT_RELPTR, relptr)
+    EXP(SYM_EXPORT_REL, rel)
+    EXP(SYM_EXPORT_LEVEL, level)
+    EXP(SYM_EXPORT_LEVELPTR, levelptr)
+    EXP(SYM_EXPORT_LEVELLIST, levellist)
+    EXP(SYM_EXPORT_LXPTR, lxptr)
+#undef EXP
+    default:
+      return fail(SYM_ERR_INVALID, "unknown export item");
+  }
+  if (out && count > 0) std::memcpy(out, src, (size_t)count * esz);
+  return count;
+}
+
+const char *sym_error_string(int code) {
+  switch (code) {
+    case SYM_OK: return "ok";
+    case SYM_ERR_INVALID: return "invalid argument or pattern";
+    case SYM_ERR_NOT_SPD: return "matrix is not positive definite";
+    case SYM_ERR_CUDA: return "CUDA error";
+    case SYM_ERR_OOM: return "out of memory";
+    case SYM_ERR_STATE: return "call out of order";
+    case SYM_ERR_TIMEOUT: return "device wait timed out";
+    case SYM_ERR_LIMIT: return "size limit exceeded";
+    default: return "unknown error";
+  }
+}
+
+const char *sym_last_error_string(void) { return g_last_error.c_str(); }
+
+void sym_free(sym_handle h) {
+  if (!h) return;
+  if (!h->host_only) release_device(h);
+  delete h;
+}
+
+}  // extern "C"

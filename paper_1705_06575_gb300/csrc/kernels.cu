@@ -1,0 +1,616 @@
+// kernels.cu — CUDA kernels (sm_103a) of the supernodal left-looking Cholesky numeric phase and
+// the supernodal triangular solves, plus the host loops that walk the precomputed schedule.
+//
+// Paper mapping (Sec. 3.2, VS-Block + VI-Prune on left-looking Cholesky): for each supernode J,
+//   (a) update: L_J -= sum over descendants K (the block prune-set) of L_K[R1,:] L_K[R0,:]^T,
+//       scattered through the relative row maps — k_update, one CTA per NB x NB tile of J;
+//   (b) dense Cholesky of the diagonal block — k_potrf (per diagonal tile) and
+//   (c) dense triangular solves on the rows below it — k_trsm, with k_gemm applying the
+//       trailing updates inside J when J is wider than one tile.
+// Supernodes of one level of the supernodal tree are independent and run in the same launches.
+// The solve follows Sec. 3.1: diagonal block first, then the off-diagonal part; the forward
+// sweep gathers each supernode's input from its descendants, the backward sweep (L^T) gathers
+// from the rows below the diagonal block.
+//
+// The FP64 path is bound by the FP64 FMA pipe (about 2 DFMA per clock per SM on GB300), so the
+// kernels keep that pipe busy: register tiles of 2 x 8 outputs per thread, operand chunks staged
+// in shared memory, warp-uniform guards that skip whole warps outside ragged tiles, and no
+// atomics in the factorization (every tile is owned by one CTA, descendants are applied in a
+// fixed order, so results are deterministic).
+#include <cstdint>
+
+#include "kernels.h"
+
+namespace sym {
+namespace {
+
+constexpr int THREADS = 256;
+constexpr int KC = 16;  // inner-dimension chunk staged in shared memory (k_gemm)
+constexpr int KCU = 8;  // the same for k_update, whose accumulator tile also lives in shared memory
+
+__device__ __forceinline__ int64_t d_row_tile_base(int32_t i, int32_t ncols, int32_t ncb) {
+  return i < ncb ? (int64_t)i * NB : (int64_t)ncols + (int64_t)(i - ncb) * NB;
+}
+__device__ __forceinline__ int d_row_tile_rows(int32_t i, int32_t ncols, int32_t nrows, int32_t ncb) {
+  int64_t base = d_row_tile_base(i, ncols, ncb);
+  int64_t end = i < ncb ? ncols : nrows;
+  int64_t r = end - base;
+  return (int)(r < NB ? r : NB);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Scatter of A into the zeroed panels (the temporary block storage of Sec. 2.3.2).
+template <typename T>
+__global__ void k_zero(T *__restrict__ x, int64_t count) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (; i < count; i += stride) x[i] = T(0);
+}
+
+template <typename T>
+__global__ void k_scatter(const double *__restrict__ Ax, const int64_t *__restrict__ amap,
+                          T *__restrict__ Lx, int64_t nnz) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (; i < nnz; i += stride) Lx[amap[i]] = (T)Ax[i];
+}
+
+// ---------------------------------------------------------------------------------------------
+// (a) External update of one tile (bi, bj) of supernode J by all its descendant entries.
+// Thread layout: warp w owns tile columns w + 8j (j < 8), lane owns rows lane and lane + 32.
+template <typename T>
+__global__ void __launch_bounds__(THREADS) k_update(const SNode *__restrict__ sn,
+                                                    const UpdTask *__restrict__ tasks,
+                                                    const UpdEntry *__restrict__ ents,
+                                                    const int32_t *__restrict__ rel,
+                                                    T *__restrict__ Lx, int64_t toff) {
+  __shared__ T acc[NB][NB + 1];  // [col][row]
+  __shared__ T As[KCU][NB];
+  __shared__ T Bs[KCU][NB];
+  __shared__ int prow[NB], pcol[NB];
+  const UpdTask t = tasks[toff + blockIdx.x];
+  const SNode sj = sn[t.J];
+  const int64_t rb = d_row_tile_base(t.bi, sj.ncols, sj.ncb);
+  const int tm = d_row_tile_rows(t.bi, sj.ncols, sj.nrows, sj.ncb);
+  const int cb = t.bj * NB;
+  const int tn = min(NB, sj.ncols - cb);
+  T *C = Lx + sj.lx + (int64_t)cb * sj.nrows + rb;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  for (int idx = tid; idx < NB * NB; idx += THREADS) {
+    int r = idx % NB, c = idx / NB;
+    acc[c][r] = (r < tm && c < tn) ? C[(int64_t)c * sj.nrows + r] : T(0);
+  }
+  for (int64_t e = t.e0; e < t.e1; ++e) {
+    const UpdEntry E = ents[e];
+    const SNode sk = sn[E.K];
+    if (tid < E.m) prow[tid] = rel[E.relr + tid] - (int)rb;
+    if (tid >= NB && tid - NB < E.n) pcol[tid - NB] = rel[E.relc + tid - NB] - cb;
+    __syncthreads();
+    const int ni = E.m > 32 ? 2 : 1;
+    const int nj = E.n > w ? (E.n - w + 7) / 8 : 0;
+    T r[2][8];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        int a = lane + 32 * i, b = w + 8 * j;
+        r[i][j] = (a < E.m && b < E.n) ? acc[pcol[b]][prow[a]] : T(0);
+      }
+    const T *Kp = Lx + sk.lx;
+    for (int k0 = 0; k0 < sk.ncols; k0 += KCU) {
+      const int kc = min(KCU, sk.ncols - k0);
+      for (int idx = tid; idx < KCU * NB; idx += THREADS) {
+        int a = idx % NB, kk = idx / NB;
+        const T *col = Kp + (int64_t)(k0 + kk) * sk.nrows;
+        As[kk][a] = (a < E.m && kk < kc) ? col[E.r_lo + a] : T(0);
+        Bs[kk][a] = (a < E.n && kk < kc) ? col[E.c_lo + a] : T(0);
+      }
+      __syncthreads();
+      if (nj > 0) {
+        for (int kk = 0; kk < kc; ++kk) {
+          const T a0 = As[kk][lane];
+          const T a1 = As[kk][lane + 32];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            if (j < nj) {
+              const T bv = Bs[kk][w + 8 * j];
+              r[0][j] = fma(-a0, bv, r[0][j]);
+              if (ni > 1) r[1][j] = fma(-a1, bv, r[1][j]);
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        int a = lane + 32 * i, b = w + 8 * j;
+        if (a < E.m && b < E.n) acc[pcol[b]][prow[a]] = r[i][j];
+      }
+    __syncthreads();
+  }
+  __syncthreads();
+  for (int idx = tid; idx < NB * NB; idx += THREADS) {
+    int r = idx % NB, c = idx / NB;
+    if (r < tm && c < tn) C[(int64_t)c * sj.nrows + r] = acc[c][r];
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// (b) Dense Cholesky of diagonal tile s of supernode J, in shared memory, column by column.
+// A pivot that is not positive (or NaN) records its permuted column in *status (atomic min)
+// and is replaced by 1 so the kernel finishes with finite values.
+template <typename T>
+__global__ void __launch_bounds__(THREADS) k_potrf(const SNode *__restrict__ sn,
+                                                   const Int4 *__restrict__ tasks,
+                                                   T *__restrict__ Lx, long long *status,
+                                                   int64_t toff) {
+  __shared__ T a[NB][NB + 1];  // [col][row]
+  __shared__ T pinv;
+  const Int4 t = tasks[toff + blockIdx.x];
+  const SNode sj = sn[t.a];
+  const int s = t.b;
+  const int ts = min(NB, sj.ncols - s * NB);
+  T *D = Lx + sj.lx + (int64_t)(s * NB) * sj.nrows + s * NB;
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < NB * NB; idx += THREADS) {
+    int r = idx % NB, c = idx / NB;
+    a[c][r] = (r < ts && c < ts && r >= c) ? D[(int64_t)c * sj.nrows + r] : T(0);
+  }
+  __syncthreads();
+  for (int c = 0; c < ts; ++c) {
+    if (tid == 0) {
+      T d = a[c][c];
+      if (!(d > T(0))) {
+        atomicMin(status, (long long)(sj.first + s * NB + c));
+        d = T(1);
+      }
+      const T l = sqrt(d);
+      a[c][c] = l;
+      pinv = T(1) / l;
+    }
+    __syncthreads();
+    const T inv = pinv;
+    for (int r = c + 1 + tid; r < ts; r += THREADS) a[c][r] *= inv;
+    __syncthreads();
+    const int rem = ts - c - 1;
+    for (int idx = tid; idx < rem * rem; idx += THREADS) {
+      int rr = c + 1 + idx % rem, cc = c + 1 + idx / rem;
+      if (rr >= cc) a[cc][rr] = fma(-a[c][rr], a[c][cc], a[cc][rr]);
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < NB * NB; idx += THREADS) {
+    int r = idx % NB, c = idx / NB;
+    if (r < ts && c < ts) D[(int64_t)c * sj.nrows + r] = r >= c ? a[c][r] : T(0);
+  }
+}
+
+// (c) Tile (i, s) <- tile * L_ss^{-T}: forward substitution over the tile's columns.
+template <typename T>
+__global__ void __launch_bounds__(THREADS) k_trsm(const SNode *__restrict__ sn,
+                                                  const Int4 *__restrict__ tasks,
+                                                  T *__restrict__ Lx, int64_t toff) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T(*Ls)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem_raw);           // [col][row], lower
+  T(*X)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem_raw) + NB;       // [col][row]
+  T *dinv = reinterpret_cast<T *>(smem_raw) + 2 * NB * (NB + 1);
+  const Int4 t = tasks[toff + blockIdx.x];
+  const SNode sj = sn[t.a];
+  const int i = t.b, s = t.c;
+  const int ts = min(NB, sj.ncols - s * NB);
+  const int64_t rb = d_row_tile_base(i, sj.ncols, sj.ncb);
+  const int tm = d_row_tile_rows(i, sj.ncols, sj.nrows, sj.ncb);
+  const T *D = Lx + sj.lx + (int64_t)(s * NB) * sj.nrows + s * NB;
+  T *B = Lx + sj.lx + (int64_t)(s * NB) * sj.nrows + rb;
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < NB * NB; idx += THREADS) {
+    int r = idx % NB, c = idx / NB;
+    Ls[c][r] = (r < ts && c < ts && r >= c) ? D[(int64_t)c * sj.nrows + r] : T(0);
+    X[c][r] = (r < tm && c < ts) ? B[(int64_t)c * sj.nrows + r] : T(0);
+  }
+  __syncthreads();
+  if (tid < ts) dinv[tid] = T(1) / Ls[tid][tid];
+  __syncthreads();
+  for (int c = 0; c < ts; ++c) {
+    if (tid < tm) X[c][tid] *= dinv[c];
+    __syncthreads();
+    const int rem = ts - c - 1;
+    for (int idx = tid; idx < tm * rem; idx += THREADS) {
+      int r = idx % tm, cc = c + 1 + idx / tm;
+      X[cc][r] = fma(-X[c][r], Ls[c][cc], X[cc][r]);
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < NB * NB; idx += THREADS) {
+    int r = idx % NB, c = idx / NB;
+    if (r < tm && c < ts) B[(int64_t)c * sj.nrows + r] = X[c][r];
+  }
+}
+
+// (c') Trailing update inside J: tile (i, j) -= tile (i, s) * tile (j, s)^T.
+template <typename T>
+__global__ void __launch_bounds__(THREADS) k_gemm(const SNode *__restrict__ sn,
+                                                  const Int4 *__restrict__ tasks,
+                                                  T *__restrict__ Lx, int64_t toff) {
+  __shared__ T As[KC][NB];
+  __shared__ T Bs[KC][NB];
+  const Int4 t = tasks[toff + blockIdx.x];
+  const SNode sj = sn[t.a];
+  const int i = t.b, j = t.c, s = t.d;
+  const int64_t rb = d_row_tile_base(i, sj.ncols, sj.ncb);
+  const int tm = d_row_tile_rows(i, sj.ncols, sj.nrows, sj.ncb);
+  const int tn = min(NB, sj.ncols - j * NB);
+  const int ks = min(NB, sj.ncols - s * NB);
+  const T *P = Lx + sj.lx + (int64_t)(s * NB) * sj.nrows;  // column block s
+  T *C = Lx + sj.lx + (int64_t)(j * NB) * sj.nrows + rb;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int ni = tm > 32 ? 2 : 1;
+  const int nj = tn > w ? (tn - w + 7) / 8 : 0;
+  T r[2][8];
+#pragma unroll
+  for (int ii = 0; ii < 2; ++ii)
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) {
+      int a = lane + 32 * ii, b = w + 8 * jj;
+      r[ii][jj] = (a < tm && b < tn) ? C[(int64_t)b * sj.nrows + a] : T(0);
+    }
+  for (int k0 = 0; k0 < ks; k0 += KC) {
+    const int kc = min(KC, ks - k0);
+    for (int idx = tid; idx < KC * NB; idx += THREADS) {
+      int a = idx % NB, kk = idx / NB;
+      const T *col = P + (int64_t)(k0 + kk) * sj.nrows;
+      As[kk][a] = (a < tm && kk < kc) ? col[rb + a] : T(0);
+      Bs[kk][a] = (a < tn && kk < kc) ? col[(int64_t)j * NB + a] : T(0);
+    }
+    __syncthreads();
+    if (nj > 0) {
+      for (int kk = 0; kk < kc; ++kk) {
+        const T a0 = As[kk][lane];
+        const T a1 = As[kk][lane + 32];
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) {
+          if (jj < nj) {
+            const T bv = Bs[kk][w + 8 * jj];
+            r[0][jj] = fma(-a0, bv, r[0][jj]);
+            if (ni > 1) r[1][jj] = fma(-a1, bv, r[1][jj]);
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int ii = 0; ii < 2; ++ii)
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) {
+      int a = lane + 32 * ii, b = w + 8 * jj;
+      if (a < tm && b < tn) C[(int64_t)b * sj.nrows + a] = r[ii][jj];
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Solve kernels. y is the permuted right-hand side block, n x nrhs, leading dimension n.
+__global__ void k_perm_in(const int32_t *__restrict__ perm, const double *__restrict__ B, int64_t ldb,
+                          double *__restrict__ y, int64_t n, int nrhs) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (; i < n * nrhs; i += stride) {
+    int64_t k = i % n, c = i / n;
+    y[i] = B[c * ldb + perm[k]];
+  }
+}
+__global__ void k_perm_out(const int32_t *__restrict__ perm, const double *__restrict__ y,
+                           double *__restrict__ X, int64_t ldx, int64_t n, int nrhs) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (; i < n * nrhs; i += stride) {
+    int64_t k = i % n, c = i / n;
+    X[c * ldx + perm[k]] = y[i];
+  }
+}
+
+constexpr int MAXRHS = 8;  // right-hand sides handled per pass of the solve kernels
+
+// Forward gather: y(cols of tile bj of J) -= sum over descendant entries of L_K(rows) y_K.
+// Warps take the entry's rows in turn; lanes split the inner dimension.
+template <typename T>
+__global__ void __launch_bounds__(THREADS) k_fgather(const SNode *__restrict__ sn,
+                                                     const Int4 *__restrict__ tasks,
+                                                     const UpdTask *__restrict__ utasks,
+                                                     const UpdEntry *__restrict__ ents,
+                                                     const int32_t *__restrict__ rel,
+                                                     const T *__restrict__ Lx, double *__restrict__ y,
+                                                     int64_t n, int r0, int nr, int64_t toff) {
+  __shared__ double acc[MAXRHS][NB];
+  const Int4 t = tasks[toff + blockIdx.x];
+  const SNode sj = sn[t.a];
+  const int bj = t.b;
+  const UpdTask u = utasks[t.c];
+  const int cb = bj * NB;
+  const int tn = min(NB, sj.ncols - cb);
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  for (int idx = tid; idx < MAXRHS * NB; idx += THREADS) {
+    int r = idx % NB, c = idx / NB;
+    acc[c][r] = (r < tn && c < nr) ? y[(int64_t)(r0 + c) * n + sj.first + cb + r] : 0.0;
+  }
+  __syncthreads();
+  for (int64_t e = u.e0; e < u.e1; ++e) {
+    const UpdEntry E = ents[e];
+    const SNode sk = sn[E.K];
+    for (int b = w; b < E.n; b += THREADS / 32) {
+      double s[MAXRHS];
+#pragma unroll
+      for (int c = 0; c < MAXRHS; ++c) s[c] = 0.0;
+      const T *rowp = Lx + sk.lx + E.c_lo + b;
+      for (int k = lane; k < sk.ncols; k += 32) {
+        const double l = (double)rowp[(int64_t)k * sk.nrows];
+#pragma unroll
+        for (int c = 0; c < MAXRHS; ++c)
+          if (c < nr) s[c] = fma(l, y[(int64_t)(r0 + c) * n + sk.first + k], s[c]);
+      }
+#pragma unroll
+      for (int c = 0; c < MAXRHS; ++c) {
+        if (c < nr) {
+          double v = s[c];
+          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+          s[c] = v;
+        }
+      }
+      if (lane == 0) {
+        const int pos = rel[E.relc + b] - cb;
+        for (int c = 0; c < nr; ++c) acc[c][pos] -= s[c];
+      }
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < MAXRHS * NB; idx += THREADS) {
+    int r = idx % NB, c = idx / NB;
+    if (r < tn && c < nr) y[(int64_t)(r0 + c) * n + sj.first + cb + r] = acc[c][r];
+  }
+}
+
+// Diagonal tile solve, forward (L_ss y = y) or backward (L_ss^T z = z), one CTA per tile.
+template <typename T, bool TRANS>
+__global__ void __launch_bounds__(THREADS) k_diag_solve(const SNode *__restrict__ sn,
+                                                        const Int4 *__restrict__ tasks,
+                                                        const T *__restrict__ Lx, double *__restrict__ y,
+                                                        int64_t n, int r0, int nr, int64_t toff) {
+  __shared__ double Ls[NB][NB + 1];  // [col][row]
+  __shared__ double v[MAXRHS][NB];
+  const Int4 t = tasks[toff + blockIdx.x];
+  const SNode sj = sn[t.a];
+  const int s = t.b;
+  const int ts = min(NB, sj.ncols - s * NB);
+  const T *D = Lx + sj.lx + (int64_t)(s * NB) * sj.nrows + s * NB;
+  const int64_t g0 = sj.first + s * NB;
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < NB * NB; idx += THREADS) {
+    int r = idx % NB, c = idx / NB;
+    Ls[c][r] = (r < ts && c < ts && r >= c) ? (double)D[(int64_t)c * sj.nrows + r] : 0.0;
+  }
+  for (int idx = tid; idx < MAXRHS * NB; idx += THREADS) {
+    int r = idx % NB, c = idx / NB;
+    v[c][r] = (r < ts && c < nr) ? y[(int64_t)(r0 + c) * n + g0 + r] : 0.0;
+  }
+  __syncthreads();
+  if (!TRANS) {
+    for (int c = 0; c < ts; ++c) {
+      if (tid < nr) v[tid][c] /= Ls[c][c];
+      __syncthreads();
+      const int rem = ts - c - 1;
+      for (int idx = tid; idx < rem * nr; idx += THREADS) {
+        int r = c + 1 + idx % rem, q = idx / rem;
+        v[q][r] = fma(-Ls[c][r], v[q][c], v[q][r]);
+      }
+      __syncthreads();
+    }
+  } else {
+    for (int c = ts - 1; c >= 0; --c) {
+      if (tid < nr) v[tid][c] /= Ls[c][c];
+      __syncthreads();
+      for (int idx = tid; idx < c * nr; idx += THREADS) {
+        int r = idx % c, q = idx / c;
+        v[q][r] = fma(-Ls[r][c], v[q][c], v[q][r]);  // L(c, r) at column r, row c
+      }
+      __syncthreads();
+    }
+  }
+  for (int idx = tid; idx < MAXRHS * NB; idx += THREADS) {
+    int r = idx % NB, c = idx / NB;
+    if (r < ts && c < nr) y[(int64_t)(r0 + c) * n + g0 + r] = v[c][r];
+  }
+}
+
+// Forward GEMV inside J: y(tile i) -= L(i, s) y(tile s), i > s within the diagonal block.
+template <typename T>
+__global__ void __launch_bounds__(THREADS) k_fgemv(const SNode *__restrict__ sn,
+                                                   const Int4 *__restrict__ tasks,
+                                                   const T *__restrict__ Lx, double *__restrict__ y,
+                                                   int64_t n, int r0, int nr, int64_t toff) {
+  __shared__ double vs[MAXRHS][NB];
+  const Int4 t = tasks[toff + blockIdx.x];
+  const SNode sj = sn[t.a];
+  const int i = t.b, s = t.c;
+  const int ts = min(NB, sj.ncols - s * NB);
+  const int tm = min(NB, sj.ncols - i * NB);
+  const T *Lt = Lx + sj.lx + (int64_t)(s * NB) * sj.nrows + i * NB;
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < MAXRHS * NB; idx += THREADS) {
+    int r = idx % NB, c = idx / NB;
+    vs[c][r] = (r < ts && c < nr) ? y[(int64_t)(r0 + c) * n + sj.first + s * NB + r] : 0.0;
+  }
+  __syncthreads();
+  for (int idx = tid; idx < tm * nr; idx += THREADS) {
+    int r = idx % tm, q = idx / tm;
+    double acc = 0.0;
+    for (int k = 0; k < ts; ++k) acc = fma((double)Lt[(int64_t)k * sj.nrows + r], vs[q][k], acc);
+    y[(int64_t)(r0 + q) * n + sj.first + i * NB + r] -= acc;
+  }
+}
+
+// Backward gather: z(cols of tile bj) -= L_J(rows below the diagonal block, tile)^T z(those rows).
+template <typename T>
+__global__ void __launch_bounds__(THREADS) k_bgather(const SNode *__restrict__ sn,
+                                                     const int32_t *__restrict__ rows,
+                                                     const Int4 *__restrict__ tasks,
+                                                     const T *__restrict__ Lx, double *__restrict__ y,
+                                                     int64_t n, int r0, int nr, int64_t toff) {
+  const Int4 t = tasks[toff + blockIdx.x];
+  const SNode sj = sn[t.a];
+  const int bj = t.b;
+  const int cb = bj * NB;
+  const int tn = min(NB, sj.ncols - cb);
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int32_t *R = rows + sj.rowp;
+  for (int c = w; c < tn; c += THREADS / 32) {
+    const T *col = Lx + sj.lx + (int64_t)(cb + c) * sj.nrows;
+    double s[MAXRHS];
+#pragma unroll
+    for (int q = 0; q < MAXRHS; ++q) s[q] = 0.0;
+    for (int r = sj.ncols + lane; r < sj.nrows; r += 32) {
+      const double l = (double)col[r];
+      const int64_t g = R[r];
+#pragma unroll
+      for (int q = 0; q < MAXRHS; ++q)
+        if (q < nr) s[q] = fma(l, y[(int64_t)(r0 + q) * n + g], s[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < MAXRHS; ++q) {
+      if (q < nr) {
+        double v = s[q];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) y[(int64_t)(r0 + q) * n + sj.first + cb + c] -= v;
+      }
+    }
+  }
+}
+
+// Backward GEMV inside J: z(tile i) -= L(s, i)^T z(tile s), i < s within the diagonal block.
+template <typename T>
+__global__ void __launch_bounds__(THREADS) k_bgemv(const SNode *__restrict__ sn,
+                                                   const Int4 *__restrict__ tasks,
+                                                   const T *__restrict__ Lx, double *__restrict__ y,
+                                                   int64_t n, int r0, int nr, int64_t toff) {
+  __shared__ double vs[MAXRHS][NB];
+  const Int4 t = tasks[toff + blockIdx.x];
+  const SNode sj = sn[t.a];
+  const int s = t.b, i = t.c;
+  const int ts = min(NB, sj.ncols - s * NB);
+  const int ti = min(NB, sj.ncols - i * NB);
+  const T *Lt = Lx + sj.lx + (int64_t)(i * NB) * sj.nrows + s * NB;  // rows of tile s, cols of tile i
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < MAXRHS * NB; idx += THREADS) {
+    int r = idx % NB, c = idx / NB;
+    vs[c][r] = (r < ts && c < nr) ? y[(int64_t)(r0 + c) * n + sj.first + s * NB + r] : 0.0;
+  }
+  __syncthreads();
+  for (int idx = tid; idx < ti * nr; idx += THREADS) {
+    int c = idx % ti, q = idx / ti;
+    const T *col = Lt + (int64_t)c * sj.nrows;
+    double acc = 0.0;
+    for (int k = 0; k < ts; ++k) acc = fma((double)col[k], vs[q][k], acc);
+    y[(int64_t)(r0 + q) * n + sj.first + i * NB + c] -= acc;
+  }
+}
+
+template <typename T>
+constexpr size_t trsm_smem() { return sizeof(T) * (2 * NB * (NB + 1) + NB); }
+
+inline int grid_for(int64_t count, int per) {
+  int64_t g = (count + per - 1) / per;
+  if (g > 152 * 16) g = 152 * 16;
+  return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, const double *Ax,
+                       T *Lx, long long *status, cudaStream_t st) {
+  static thread_local bool attr_set = false;  // per host thread: the attribute is per device
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_trsm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem<T>());
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  k_zero<T><<<grid_for(d.storage, THREADS * 4), THREADS, 0, st>>>(Lx, d.storage);
+  if (d.nnz_a > 0) k_scatter<T><<<grid_for(d.nnz_a, THREADS * 4), THREADS, 0, st>>>(Ax, d.amap, Lx, d.nnz_a);
+  for (const Launch &L : launches) {
+    const unsigned g = (unsigned)L.count;
+    switch (L.kind) {
+      case K_UPDATE:
+        k_update<T><<<g, THREADS, 0, st>>>(d.sn, d.upd_tasks, d.upd_entries, d.rel, Lx, L.off);
+        break;
+      case K_POTRF:
+        k_potrf<T><<<g, THREADS, 0, st>>>(d.sn, d.tasks, Lx, status, L.off);
+        break;
+      case K_TRSM:
+        k_trsm<T><<<g, THREADS, trsm_smem<T>(), st>>>(d.sn, d.tasks, Lx, L.off);
+        break;
+      case K_GEMM:
+        k_gemm<T><<<g, THREADS, 0, st>>>(d.sn, d.tasks, Lx, L.off);
+        break;
+      default:
+        return cudaErrorInvalidValue;
+    }
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t run_solve(const DevPlan &d, const std::vector<Launch> &fwd, const std::vector<Launch> &bwd,
+                      const T *Lx, int nrhs, const double *B, int64_t ldb, double *X, int64_t ldx,
+                      double *y, cudaStream_t st) {
+  const int64_t n = d.n;
+  if (n == 0 || nrhs == 0) return cudaSuccess;
+  k_perm_in<<<grid_for(n * nrhs, THREADS), THREADS, 0, st>>>(d.perm, B, ldb, y, n, nrhs);
+  for (int r0 = 0; r0 < nrhs; r0 += MAXRHS) {
+    const int nr = nrhs - r0 < MAXRHS ? nrhs - r0 : MAXRHS;
+    for (const Launch &L : fwd) {
+      const unsigned g = (unsigned)L.count;
+      switch (L.kind) {
+        case S_FGATHER:
+          k_fgather<T><<<g, THREADS, 0, st>>>(d.sn, d.tasks, d.upd_tasks, d.upd_entries, d.rel, Lx, y, n, r0, nr, L.off);
+          break;
+        case S_FDIAG:
+          k_diag_solve<T, false><<<g, THREADS, 0, st>>>(d.sn, d.tasks, Lx, y, n, r0, nr, L.off);
+          break;
+        case S_FGEMV:
+          k_fgemv<T><<<g, THREADS, 0, st>>>(d.sn, d.tasks, Lx, y, n, r0, nr, L.off);
+          break;
+        default:
+          return cudaErrorInvalidValue;
+      }
+    }
+    for (const Launch &L : bwd) {
+      const unsigned g = (unsigned)L.count;
+      switch (L.kind) {
+        case S_BGATHER:
+          k_bgather<T><<<g, THREADS, 0, st>>>(d.sn, d.rows, d.tasks, Lx, y, n, r0, nr, L.off);
+          break;
+        case S_BDIAG:
+          k_diag_solve<T, true><<<g, THREADS, 0, st>>>(d.sn, d.tasks, Lx, y, n, r0, nr, L.off);
+          break;
+        case S_BGEMV:
+          k_bgemv<T><<<g, THREADS, 0, st>>>(d.sn, d.tasks, Lx, y, n, r0, nr, L.off);
+          break;
+        default:
+          return cudaErrorInvalidValue;
+      }
+    }
+  }
+  k_perm_out<<<grid_for(n * nrhs, THREADS), THREADS, 0, st>>>(d.perm, y, X, ldx, n, nrhs);
+  return cudaGetLastError();
+}
+
+template cudaError_t run_factor<double>(const DevPlan &, const std::vector<Launch> &, const double *,
+                                        double *, long long *, cudaStream_t);
+template cudaError_t run_solve<double>(const DevPlan &, const std::vector<Launch> &,
+                                       const std::vector<Launch> &, const double *, int,
+                                       const double *, int64_t, double *, int64_t, double *,
+                                       cudaStream_t);
+
+}  // namespace sym

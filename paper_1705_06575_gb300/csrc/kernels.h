@@ -1,0 +1,38 @@
+// kernels.h — host entry points of the CUDA kernels (internal to the library).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "plan.h"
+
+namespace sym {
+
+// Device copy of the plan arrays the kernels read.
+struct DevPlan {
+  const SNode *sn = nullptr;
+  const int32_t *rows = nullptr;
+  const int32_t *rel = nullptr;
+  const int64_t *amap = nullptr;
+  const UpdTask *upd_tasks = nullptr;
+  const UpdEntry *upd_entries = nullptr;
+  const Int4 *tasks = nullptr;
+  const int32_t *perm = nullptr;
+  int64_t n = 0;
+  int64_t nnz_a = 0;
+  int64_t storage = 0;
+};
+
+// Numeric factorization: scatter A into the zeroed panels, then run the launch schedule.
+// status: device int64, receives the smallest failing (permuted) column, or stays INT64_MAX.
+template <typename T>
+cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, const double *Ax,
+                       T *Lx, long long *status, cudaStream_t st);
+
+// Solve with nrhs right-hand sides: y = P b, forward sweep, backward sweep, x = P^T y.
+// y: device work array of n * nrhs (ld n).
+template <typename T>
+cudaError_t run_solve(const DevPlan &d, const std::vector<Launch> &fwd, const std::vector<Launch> &bwd,
+                      const T *Lx, int nrhs, const double *B, int64_t ldb, double *X, int64_t ldx,
+                      double *y, cudaStream_t st);
+
+}  // namespace sym

@@ -1,0 +1,132 @@
+// plan.h — the symbolic plan that the host inspector builds once per sparsity pattern and the
+// CUDA kernels consume. Internal to the library (the public interface is include/sym.h).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "sym.h"
+
+namespace sym {
+
+// Edge of the square tiles that the numeric kernels work on (rows and columns of a supernode's
+// panel are cut into tiles of NB; see row_tile_base below).
+constexpr int NB = 64;
+
+// One supernode as the kernels see it. Its panel is column-major, nrows x ncols, leading
+// dimension nrows, at Lx + lx. Row r of the panel is global row rows[rowp + r]; the first ncols
+// rows are the supernode's own columns (the dense diagonal block).
+struct SNode {
+  int32_t first;  // first column
+  int32_t ncols;
+  int32_t nrows;
+  int32_t ncb;    // column tiles = ceil(ncols / NB)
+  int64_t rowp;   // offset into rows[]
+  int64_t lx;     // offset into Lx
+};
+
+// Row tiling of a panel: the diagonal block is cut at multiples of NB, and the rows below it
+// (the off-diagonal block) again from row ncols, so that tile (s, s) is exactly the square
+// diagonal tile of column tile s.
+inline int64_t row_tile_base(int32_t i, int32_t ncols, int32_t ncb) {
+  return i < ncb ? (int64_t)i * NB : (int64_t)ncols + (int64_t)(i - ncb) * NB;
+}
+inline int32_t row_tile_of(int64_t pos, int32_t ncols, int32_t ncb) {
+  return pos < ncols ? (int32_t)(pos / NB) : ncb + (int32_t)((pos - ncols) / NB);
+}
+inline int32_t num_row_tiles(int32_t nrows, int32_t ncols, int32_t ncb) {
+  return ncb + (int32_t)((nrows - ncols + NB - 1) / NB);
+}
+
+// One descendant contribution to one tile of an ancestor J (the left-looking update of
+// Sec. 3.2 restricted to a tile): rows r_lo..r_lo+m-1 of K's panel land in the tile's rows at
+// positions rel[relr + a] (positions within rows(J)), and rows c_lo..c_lo+n-1 of K's panel give
+// the tile's columns at positions rel[relc + b]. Inner dimension: ncols(K).
+struct UpdEntry {
+  int32_t K;
+  int32_t r_lo;
+  int32_t c_lo;
+  int32_t m;
+  int32_t n;
+  int32_t pad;
+  int64_t relr;
+  int64_t relc;
+};
+
+// A tile (bi, bj) of supernode J and the range of its UpdEntry list.
+struct UpdTask {
+  int32_t J;
+  int32_t bi;
+  int32_t bj;
+  int32_t pad;
+  int64_t e0;
+  int64_t e1;
+};
+
+// Kernel kinds of the launch schedule.
+enum Kind : int32_t {
+  K_UPDATE = 1,   // external updates of tiles (UpdTask list)
+  K_POTRF = 2,    // dense Cholesky of diagonal tile s (int4 {J, s, s, s})
+  K_TRSM = 3,     // tile (i, s) <- tile * L_ss^-T (int4 {J, i, s, s})
+  K_GEMM = 4,     // tile (i, j) -= L_is L_js^T (int4 {J, i, j, s})
+  S_FGATHER = 11, // y_J(tile bj) -= sum_K L_K(rows in tile) y_K (int4 {J, bj, task, 0})
+  S_FDIAG = 12,   // y_s <- L_ss^-1 y_s (int4 {J, s, s, s})
+  S_FGEMV = 13,   // y_i -= L_is y_s (int4 {J, i, s, s})
+  S_BGATHER = 14, // z_J(tile bj) -= L_J(off rows, tile)^T z(off rows) (int4 {J, bj, 0, 0})
+  S_BDIAG = 15,   // z_s <- L_ss^-T z_s (int4 {J, s, s, s})
+  S_BGEMV = 16,   // z_i -= L_si^T z_s (int4 {J, s, i, s})
+};
+
+struct Launch {
+  int32_t kind;
+  int32_t level;
+  int64_t off;    // offset into the task array of this kind
+  int64_t count;  // number of tasks (CTAs)
+};
+
+struct Int4 {
+  int32_t a, b, c, d;
+};
+
+struct Plan {
+  int64_t n = 0;
+  int64_t nnz_a = 0;
+  int64_t nnz_l = 0;
+  double flops = 0.0;
+  double analyze_seconds = 0.0;
+  std::vector<int32_t> perm, iperm;   // final ordering
+  std::vector<int32_t> parent;        // etree of P A P^T
+  std::vector<int64_t> colcount;      // |L_j|
+  std::vector<int32_t> fsuper;        // fundamental supernodes (first columns, +n)
+  std::vector<int32_t> super;         // supernodes after amalgamation (first columns, +n)
+  std::vector<int64_t> rowptr;        // nsuper+1
+  std::vector<int32_t> rows;          // rows(J)
+  std::vector<int32_t> sparent;       // supernodal tree
+  std::vector<int64_t> descptr;       // nsuper+1
+  std::vector<int32_t> desc;          // K of each pair
+  std::vector<int64_t> descr0;        // first position of rows(K) >= first(J)
+  std::vector<int32_t> descnin;       // rows of K inside cols(J)
+  std::vector<int64_t> relptr;        // npairs+1
+  std::vector<int32_t> rel;           // relative row maps
+  std::vector<int32_t> level, levelptr, levellist;
+  std::vector<int64_t> lxptr;         // nsuper+1; lxptr[nsuper] = storage
+  std::vector<int64_t> amap;          // nnz_a: panel position of each entry of A
+  std::vector<SNode> snodes;
+  std::vector<UpdEntry> upd_entries;
+  std::vector<UpdTask> upd_tasks;
+  std::vector<Int4> tasks;            // every other kind of task
+  std::vector<Launch> factor_launches;
+  std::vector<Launch> fwd_launches;
+  std::vector<Launch> bwd_launches;
+  int32_t max_ncols = 0;
+
+  int32_t nsuper() const { return (int32_t)super.size() - 1; }
+  int64_t storage() const { return lxptr.empty() ? 0 : lxptr.back(); }
+};
+
+// Run the inspector. Returns SYM_OK or an error code with a message in err.
+int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm,
+            const sym_options &opt, Plan &P, std::string &err);
+
+}  // namespace sym

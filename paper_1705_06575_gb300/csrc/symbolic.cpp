@@ -1,0 +1,547 @@
+// symbolic.cpp — host symbolic inspector (runs once per sparsity pattern).
+//
+// The paper's inspector for Cholesky (Sec. 3.2) computes the elimination tree, the row patterns
+// of L (the prune-set of VI-Prune) and the supernodes (the block-set of VS-Block). This file
+// computes the same objects with near-linear algorithms and adds what the GPU needs on top:
+// relaxed amalgamation, the supernodal row structure, descendant lists, relative row maps, a
+// level schedule of the supernodal tree, the scatter map of A into the panels and the kernel
+// task lists. No numeric work happens here (Sec. 4.2: the numeric code does no symbolic work).
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <numeric>
+
+#include "plan.h"
+
+namespace sym {
+namespace {
+
+// Validation of the input format (lower CSC, rows strictly increasing, diagonal first).
+bool valid_pattern(int64_t n, const int64_t *Ap, const int32_t *Ai, std::string &err) {
+  if (n < 0 || n > INT32_MAX - 1) { err = "n out of range"; return false; }
+  if (!Ap || (n > 0 && !Ai)) { err = "null pattern pointer"; return false; }
+  if (Ap[0] != 0) { err = "Ap[0] != 0"; return false; }
+  for (int64_t j = 0; j < n; ++j) {
+    if (Ap[j + 1] <= Ap[j]) { err = "column " + std::to_string(j) + " has no diagonal"; return false; }
+    if (Ai[Ap[j]] != j) { err = "column " + std::to_string(j) + " does not start with its diagonal"; return false; }
+    for (int64_t p = Ap[j] + 1; p < Ap[j + 1]; ++p)
+      if (Ai[p] <= Ai[p - 1] || Ai[p] >= n) {
+        err = "column " + std::to_string(j) + " has unsorted or out-of-range rows";
+        return false;
+      }
+  }
+  return true;
+}
+
+// Strictly-lower entries of P A P^T grouped by row: for row i, the columns j < i.
+void rows_of_permuted(int64_t n, const int64_t *Ap, const int32_t *Ai,
+                      const std::vector<int32_t> &iperm, std::vector<int64_t> &rp,
+                      std::vector<int32_t> &rj) {
+  rp.assign(n + 1, 0);
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t p = Ap[j] + 1; p < Ap[j + 1]; ++p) {
+      int32_t a = iperm[Ai[p]], b = iperm[j];
+      rp[std::max(a, b) + 1]++;
+    }
+  for (int64_t i = 0; i < n; ++i) rp[i + 1] += rp[i];
+  rj.resize(rp[n]);
+  std::vector<int64_t> fill(rp.begin(), rp.end() - 1);
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t p = Ap[j] + 1; p < Ap[j + 1]; ++p) {
+      int32_t a = iperm[Ai[p]], b = iperm[j];
+      rj[fill[std::max(a, b)]++] = std::min(a, b);
+    }
+}
+
+// Elimination tree by Liu's algorithm with path compression: row i of the strictly-lower part
+// links every tree root reachable from its columns to i.
+void etree_liu(int64_t n, const std::vector<int64_t> &rp, const std::vector<int32_t> &rj,
+               std::vector<int32_t> &parent) {
+  parent.assign(n, -1);
+  std::vector<int32_t> anc(n, -1);
+  for (int64_t i = 0; i < n; ++i) {
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+      int32_t j = rj[p];
+      while (j != -1 && j < i) {
+        int32_t next = anc[j];
+        anc[j] = (int32_t)i;
+        if (next == -1) { parent[j] = (int32_t)i; break; }
+        j = next;
+      }
+    }
+  }
+}
+
+// Postorder with children (and roots) taken in increasing order. post[k] = node at position k.
+void postorder(int64_t n, const std::vector<int32_t> &parent, std::vector<int32_t> &post) {
+  std::vector<int32_t> first_child(n, -1), sibling(n, -1);
+  for (int64_t j = n - 1; j >= 0; --j) {
+    int32_t p = parent[j];
+    if (p >= 0) { sibling[j] = first_child[p]; first_child[p] = (int32_t)j; }
+  }
+  post.clear();
+  post.reserve(n);
+  std::vector<int32_t> stack;
+  for (int64_t r = 0; r < n; ++r) {
+    if (parent[r] != -1) continue;
+    stack.push_back((int32_t)r);
+    while (!stack.empty()) {
+      int32_t v = stack.back();
+      int32_t c = first_child[v];
+      if (c != -1) {
+        first_child[v] = sibling[c];
+        stack.push_back(c);
+      } else {
+        stack.pop_back();
+        post.push_back(v);
+      }
+    }
+  }
+}
+
+struct Timer {
+  std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+  double seconds() const {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+};
+
+}  // namespace
+
+int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm_in,
+            const sym_options &opt, Plan &P, std::string &err) {
+  Timer timer;
+  if (!valid_pattern(n, Ap, Ai, err)) return SYM_ERR_INVALID;
+  P = Plan();
+  P.n = n;
+  P.nnz_a = Ap[n];
+
+  // 1. Given ordering.
+  std::vector<int32_t> p0(n), ip0(n, -1);
+  for (int64_t k = 0; k < n; ++k) {
+    int32_t v = (opt.ordering == SYM_ORDER_GIVEN && perm_in) ? perm_in[k] : (int32_t)k;
+    if (v < 0 || v >= n || ip0[v] != -1) { err = "perm is not a permutation"; return SYM_ERR_INVALID; }
+    p0[k] = v;
+    ip0[v] = (int32_t)k;
+  }
+  // 2. Etree of the given ordering, its postorder, and the final ordering perm0 o post.
+  std::vector<int64_t> rp;
+  std::vector<int32_t> rj, parent0, post;
+  rows_of_permuted(n, Ap, Ai, ip0, rp, rj);
+  etree_liu(n, rp, rj, parent0);
+  postorder(n, parent0, post);
+  std::vector<int32_t> ipost(n);
+  for (int64_t k = 0; k < n; ++k) ipost[post[k]] = (int32_t)k;
+  P.perm.resize(n);
+  P.iperm.resize(n);
+  for (int64_t k = 0; k < n; ++k) P.perm[k] = p0[post[k]];
+  for (int64_t k = 0; k < n; ++k) P.iperm[P.perm[k]] = (int32_t)k;
+  // The etree relabels with the postorder.
+  P.parent.resize(n);
+  for (int64_t k = 0; k < n; ++k) {
+    int32_t q = parent0[post[k]];
+    P.parent[k] = q < 0 ? -1 : ipost[q];
+  }
+  // 3. Column counts by row subtrees: row i of L is the union of the etree paths from each
+  //    column j of row i of C up to i; every node on them gains one entry.
+  rows_of_permuted(n, Ap, Ai, P.iperm, rp, rj);
+  P.colcount.assign(n, 1);
+  {
+    std::vector<int32_t> mark(n, -1);
+    for (int64_t i = 0; i < n; ++i) {
+      mark[i] = (int32_t)i;
+      for (int64_t p = rp[i]; p < rp[i + 1]; ++p)
+        for (int32_t j = rj[p]; mark[j] != i; j = P.parent[j]) {
+          mark[j] = (int32_t)i;
+          P.colcount[j]++;
+        }
+    }
+  }
+  P.nnz_l = 0;
+  P.flops = 0.0;
+  for (int64_t j = 0; j < n; ++j) {
+    P.nnz_l += P.colcount[j];
+    P.flops += (double)P.colcount[j] * (double)P.colcount[j];
+  }
+  // 4. Fundamental supernodes: j-1 joins j when j-1 is j's only child and |L_{j-1}| = |L_j|+1.
+  {
+    std::vector<int32_t> nchild(n, 0);
+    for (int64_t j = 0; j < n; ++j)
+      if (P.parent[j] >= 0) nchild[P.parent[j]]++;
+    for (int64_t j = 0; j < n; ++j) {
+      bool joins = j > 0 && P.parent[j - 1] == j && nchild[j] == 1 &&
+                   P.colcount[j - 1] == P.colcount[j] + 1;
+      if (!joins) P.fsuper.push_back((int32_t)j);
+    }
+    P.fsuper.push_back((int32_t)n);
+  }
+  const int32_t nf = (int32_t)P.fsuper.size() - 1;
+  // 5. Row structure of each fundamental supernode: its columns, the entries of C below it,
+  //    and the rows of its child supernodes below it (Eq. (1) applied per supernode).
+  //    Columns of C: the transpose of the row lists.
+  std::vector<int64_t> cp(n + 1, 0);
+  std::vector<int32_t> ci;
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) cp[rj[p] + 1]++;
+  for (int64_t j = 0; j < n; ++j) cp[j + 1] += cp[j];
+  ci.resize(cp[n]);
+  {
+    std::vector<int64_t> fill(cp.begin(), cp.end() - 1);
+    for (int64_t i = 0; i < n; ++i)
+      for (int64_t p = rp[i]; p < rp[i + 1]; ++p) ci[fill[rj[p]]++] = (int32_t)i;
+  }
+  std::vector<int32_t> col2f(n);
+  for (int32_t s = 0; s < nf; ++s)
+    for (int32_t j = P.fsuper[s]; j < P.fsuper[s + 1]; ++j) col2f[j] = s;
+  std::vector<std::vector<int32_t>> srows(nf);
+  std::vector<std::vector<int32_t>> fchildren(nf);
+  for (int32_t s = 0; s < nf; ++s) {
+    int32_t pl = P.parent[P.fsuper[s + 1] - 1];
+    if (pl >= 0) fchildren[col2f[pl]].push_back(s);
+  }
+  {
+    std::vector<int32_t> mark(n, -1);
+    for (int32_t s = 0; s < nf; ++s) {
+      int32_t f = P.fsuper[s], l = P.fsuper[s + 1] - 1;
+      std::vector<int32_t> &R = srows[s];
+      for (int32_t j = f; j <= l; ++j) { R.push_back(j); mark[j] = s; }
+      for (int32_t j = f; j <= l; ++j)
+        for (int64_t p = cp[j]; p < cp[j + 1]; ++p)
+          if (ci[p] > l && mark[ci[p]] != s) { mark[ci[p]] = s; R.push_back(ci[p]); }
+      for (int32_t c : fchildren[s])
+        for (int32_t r : srows[c])
+          if (r > l && mark[r] != s) { mark[r] = s; R.push_back(r); }
+      std::sort(R.begin() + (l - f + 1), R.end());
+    }
+  }
+  // 6. Relaxed amalgamation (this library's rule; the paper runs without it, Sec. 4.1).
+  std::vector<int64_t> ccum(n + 1, 0);
+  for (int64_t j = 0; j < n; ++j) ccum[j + 1] = ccum[j] + P.colcount[j];
+  std::vector<int32_t> sf(P.fsuper.begin(), P.fsuper.end() - 1);  // first column of each slot
+  std::vector<int32_t> sl(nf);                                    // last column of each slot
+  std::vector<int32_t> nxt(nf);
+  for (int32_t s = 0; s < nf; ++s) { sl[s] = P.fsuper[s + 1] - 1; nxt[s] = s + 1; }
+  int32_t head = nf > 0 ? 0 : nf;
+  if (opt.amalgamate) {
+    std::vector<int32_t> merged;
+    for (bool changed = true; changed;) {
+      changed = false;
+      int32_t prev = -1;
+      for (int32_t s = head; s < nf && nxt[s] < nf;) {
+        int32_t t = nxt[s];
+        if (P.parent[sl[s]] == sl[s] + 1) {
+          merged.clear();
+          std::set_union(srows[s].begin(), srows[s].end(), srows[t].begin(), srows[t].end(),
+                         std::back_inserter(merged));
+          const int64_t m = (int64_t)merged.size();
+          const int64_t nc = (int64_t)sl[t] - sf[s] + 1;
+          const int64_t total = nc * m - nc * (nc - 1) / 2;
+          const int64_t z = total - (ccum[sl[t] + 1] - ccum[sf[s]]);
+          const bool ok = nc <= opt.nrelax[0] ||
+                          (nc <= opt.nrelax[1] && z * 1000 <= (int64_t)opt.zrelax_permille[0] * total) ||
+                          (nc <= opt.nrelax[2] && z * 1000 <= (int64_t)opt.zrelax_permille[1] * total) ||
+                          z * 1000 <= (int64_t)opt.zrelax_permille[2] * total;
+          if (ok) {
+            srows[t].swap(merged);
+            std::vector<int32_t>().swap(srows[s]);
+            sf[t] = sf[s];
+            if (prev < 0) head = t; else nxt[prev] = t;
+            s = t;  // the merged supernode is next in order of last column
+            changed = true;
+            continue;
+          }
+        }
+        prev = s;
+        s = t;
+      }
+    }
+  }
+  // Final supernodes.
+  std::vector<int32_t> slots;
+  for (int32_t s = head; s < nf; s = nxt[s]) slots.push_back(s);
+  const int32_t ns = (int32_t)slots.size();
+  P.super.resize(ns + 1);
+  P.rowptr.assign(ns + 1, 0);
+  for (int32_t J = 0; J < ns; ++J) {
+    P.super[J] = sf[slots[J]];
+    P.rowptr[J + 1] = P.rowptr[J] + (int64_t)srows[slots[J]].size();
+  }
+  P.super[ns] = (int32_t)n;
+  P.rows.resize(P.rowptr[ns]);
+  for (int32_t J = 0; J < ns; ++J) {
+    std::copy(srows[slots[J]].begin(), srows[slots[J]].end(), P.rows.begin() + P.rowptr[J]);
+    std::vector<int32_t>().swap(srows[slots[J]]);
+  }
+  std::vector<int32_t> col2s(n);
+  for (int32_t J = 0; J < ns; ++J)
+    for (int32_t j = P.super[J]; j < P.super[J + 1]; ++j) col2s[j] = J;
+  P.sparent.resize(ns);
+  for (int32_t J = 0; J < ns; ++J) {
+    int32_t pl = P.parent[P.super[J + 1] - 1];
+    P.sparent[J] = pl < 0 ? -1 : col2s[pl];
+  }
+  // 7. Descendant lists: every K whose rows reach into the columns of J (the block-level
+  //    prune-set), with the first row position r0 at or after first(J) and the count nin of
+  //    K's rows inside cols(J). Scanning K in increasing order keeps each list sorted.
+  {
+    std::vector<int64_t> cnt(ns + 1, 0);
+    for (int32_t K = 0; K < ns; ++K) {
+      int32_t lastJ = -1;
+      for (int64_t p = P.rowptr[K] + (P.super[K + 1] - P.super[K]); p < P.rowptr[K + 1]; ++p) {
+        int32_t J = col2s[P.rows[p]];
+        if (J != lastJ) { cnt[J + 1]++; lastJ = J; }
+      }
+    }
+    P.descptr.assign(ns + 1, 0);
+    for (int32_t J = 0; J < ns; ++J) P.descptr[J + 1] = P.descptr[J] + cnt[J + 1];
+    const int64_t np = P.descptr[ns];
+    P.desc.resize(np);
+    P.descr0.resize(np);
+    P.descnin.resize(np);
+    std::vector<int64_t> fill(P.descptr.begin(), P.descptr.end() - 1);
+    for (int32_t K = 0; K < ns; ++K) {
+      int32_t lastJ = -1;
+      int64_t q = -1;
+      for (int64_t p = P.rowptr[K] + (P.super[K + 1] - P.super[K]); p < P.rowptr[K + 1]; ++p) {
+        int32_t J = col2s[P.rows[p]];
+        if (J != lastJ) {
+          q = fill[J]++;
+          P.desc[q] = K;
+          P.descr0[q] = p - P.rowptr[K];
+          P.descnin[q] = 0;
+          lastJ = J;
+        }
+        P.descnin[q]++;
+      }
+    }
+  }
+  // 8. Relative row maps through a position table of rows(J).
+  {
+    const int64_t np = P.descptr[ns];
+    P.relptr.assign(np + 1, 0);
+    for (int32_t J = 0; J < ns; ++J)
+      for (int64_t q = P.descptr[J]; q < P.descptr[J + 1]; ++q) {
+        int32_t K = P.desc[q];
+        P.relptr[q + 1] = P.relptr[q] + (P.rowptr[K + 1] - P.rowptr[K] - P.descr0[q]);
+      }
+    P.rel.resize(P.relptr[np]);
+    std::vector<int32_t> pos(n, -1);
+    for (int32_t J = 0; J < ns; ++J) {
+      for (int64_t p = P.rowptr[J]; p < P.rowptr[J + 1]; ++p) pos[P.rows[p]] = (int32_t)(p - P.rowptr[J]);
+      for (int64_t q = P.descptr[J]; q < P.descptr[J + 1]; ++q) {
+        int32_t K = P.desc[q];
+        int64_t t = P.relptr[q];
+        for (int64_t p = P.rowptr[K] + P.descr0[q]; p < P.rowptr[K + 1]; ++p) P.rel[t++] = pos[P.rows[p]];
+      }
+      for (int64_t p = P.rowptr[J]; p < P.rowptr[J + 1]; ++p) pos[P.rows[p]] = -1;
+    }
+  }
+  // 9. Level schedule: leaves at 0, a parent one above its highest child.
+  P.level.assign(ns, 0);
+  for (int32_t J = 0; J < ns; ++J)
+    if (P.sparent[J] >= 0) P.level[P.sparent[J]] = std::max(P.level[P.sparent[J]], P.level[J] + 1);
+  int32_t nlev = 0;
+  for (int32_t J = 0; J < ns; ++J) nlev = std::max(nlev, P.level[J] + 1);
+  P.levelptr.assign(nlev + 1, 0);
+  for (int32_t J = 0; J < ns; ++J) P.levelptr[P.level[J] + 1]++;
+  for (int32_t l = 0; l < nlev; ++l) P.levelptr[l + 1] += P.levelptr[l];
+  P.levellist.resize(ns);
+  {
+    std::vector<int32_t> fill(P.levelptr.begin(), P.levelptr.end() - 1);
+    for (int32_t J = 0; J < ns; ++J) P.levellist[fill[P.level[J]]++] = J;
+  }
+  // 10. Panel layout and the scatter map of A's entries (caller's order) into the panels.
+  P.lxptr.assign(ns + 1, 0);
+  P.snodes.resize(ns);
+  for (int32_t J = 0; J < ns; ++J) {
+    SNode &s = P.snodes[J];
+    s.first = P.super[J];
+    s.ncols = P.super[J + 1] - P.super[J];
+    s.nrows = (int32_t)(P.rowptr[J + 1] - P.rowptr[J]);
+    s.ncb = (s.ncols + NB - 1) / NB;
+    s.rowp = P.rowptr[J];
+    s.lx = P.lxptr[J];
+    P.lxptr[J + 1] = P.lxptr[J] + (int64_t)s.nrows * s.ncols;
+    P.max_ncols = std::max(P.max_ncols, s.ncols);
+  }
+  P.amap.resize(P.nnz_a);
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t p = Ap[j]; p < Ap[j + 1]; ++p) {
+      int32_t a = P.iperm[Ai[p]], b = P.iperm[j];
+      int32_t row = std::max(a, b), col = std::min(a, b);
+      const SNode &s = P.snodes[col2s[col]];
+      const int32_t *R = P.rows.data() + s.rowp;
+      int64_t r = std::lower_bound(R, R + s.nrows, row) - R;
+      P.amap[p] = s.lx + (int64_t)(col - s.first) * s.nrows + r;
+    }
+
+  // 11. Task lists and the launch schedule.
+  //   Factor, per level: K_UPDATE over all tiles that receive descendant updates, then for each
+  //   column tile s of the level's widest supernode: K_POTRF (diagonal tile s), K_TRSM (row
+  //   tiles below it) and K_GEMM (trailing tiles of the same supernode).
+  //   Forward solve, per level ascending: S_FGATHER, then S_FDIAG / S_FGEMV per column tile.
+  //   Backward solve, per level descending: S_BGATHER, then S_BDIAG / S_BGEMV per column tile,
+  //   last tile first.
+  std::vector<int64_t> diag_task(0);  // per (J, s): UpdTask index of tile (s, s) or -1
+  std::vector<int64_t> diag_task_base(ns + 1, 0);
+  for (int32_t J = 0; J < ns; ++J) diag_task_base[J + 1] = diag_task_base[J] + P.snodes[J].ncb;
+  diag_task.assign(diag_task_base[ns], -1);
+  {
+    struct Pending {
+      int32_t bi, bj;
+      double work;
+      std::vector<UpdEntry> ents;
+    };
+    std::vector<int32_t> tile_slot;
+    for (int32_t l = 0; l < nlev; ++l) {
+      // Gather the level's tasks, then order them by decreasing work (longest first) so that
+      // the longest tiles start early; ties keep (J, bi, bj) order.
+      struct LTask { int32_t J, bi, bj; double work; std::vector<UpdEntry> ents; };
+      std::vector<LTask> lt;
+      for (int32_t t = P.levelptr[l]; t < P.levelptr[l + 1]; ++t) {
+        const int32_t J = P.levellist[t];
+        const SNode &sj = P.snodes[J];
+        const int32_t nrb = num_row_tiles(sj.nrows, sj.ncols, sj.ncb);
+        std::vector<Pending> pend;
+        tile_slot.assign((size_t)nrb * sj.ncb, -1);
+        for (int64_t q = P.descptr[J]; q < P.descptr[J + 1]; ++q) {
+          const int32_t K = P.desc[q];
+          const SNode &sk = P.snodes[K];
+          const int32_t *rel = P.rel.data() + P.relptr[q];
+          const int32_t cnt = sk.nrows - (int32_t)P.descr0[q];
+          const int32_t nin = P.descnin[q];
+          // runs of rows with the same row tile (rel is increasing)
+          struct Run { int32_t tile, start, len; };
+          std::vector<Run> rr, cr;
+          for (int32_t a = 0; a < cnt;) {
+            int32_t ti = row_tile_of(rel[a], sj.ncols, sj.ncb);
+            int32_t b = a + 1;
+            while (b < cnt && row_tile_of(rel[b], sj.ncols, sj.ncb) == ti) ++b;
+            rr.push_back({ti, a, b - a});
+            if (a < nin) cr.push_back({ti, a, std::min(b, nin) - a});  // tiles of cols(J)
+            a = b;
+          }
+          for (const Run &c : cr)
+            for (const Run &r : rr) {
+              if (r.tile < c.tile) continue;
+              size_t key = (size_t)r.tile * sj.ncb + c.tile;
+              if (tile_slot[key] < 0) {
+                tile_slot[key] = (int32_t)pend.size();
+                pend.push_back({r.tile, c.tile, 0.0, {}});
+              }
+              Pending &pd = pend[tile_slot[key]];
+              UpdEntry e;
+              e.K = K;
+              e.r_lo = (int32_t)P.descr0[q] + r.start;
+              e.c_lo = (int32_t)P.descr0[q] + c.start;
+              e.m = r.len;
+              e.n = c.len;
+              e.pad = 0;
+              e.relr = P.relptr[q] + r.start;
+              e.relc = P.relptr[q] + c.start;
+              pd.ents.push_back(e);
+              pd.work += (double)r.len * c.len * sk.ncols;
+            }
+        }
+        for (Pending &pd : pend) lt.push_back({J, pd.bi, pd.bj, pd.work, std::move(pd.ents)});
+      }
+      std::stable_sort(lt.begin(), lt.end(), [](const LTask &x, const LTask &y) { return x.work > y.work; });
+      if (!lt.empty()) {
+        P.factor_launches.push_back({K_UPDATE, l, (int64_t)P.upd_tasks.size(), (int64_t)lt.size()});
+        for (LTask &x : lt) {
+          UpdTask u;
+          u.J = x.J;
+          u.bi = x.bi;
+          u.bj = x.bj;
+          u.pad = 0;
+          u.e0 = (int64_t)P.upd_entries.size();
+          P.upd_entries.insert(P.upd_entries.end(), x.ents.begin(), x.ents.end());
+          u.e1 = (int64_t)P.upd_entries.size();
+          if (x.bi == x.bj) diag_task[diag_task_base[x.J] + x.bj] = (int64_t)P.upd_tasks.size();
+          P.upd_tasks.push_back(u);
+        }
+      }
+      // Dense part of each supernode of this level.
+      int32_t maxcb = 0;
+      for (int32_t t = P.levelptr[l]; t < P.levelptr[l + 1]; ++t)
+        maxcb = std::max(maxcb, P.snodes[P.levellist[t]].ncb);
+      for (int32_t s = 0; s < maxcb; ++s) {
+        for (int kind : {K_POTRF, K_TRSM, K_GEMM}) {
+          int64_t off = (int64_t)P.tasks.size();
+          for (int32_t t = P.levelptr[l]; t < P.levelptr[l + 1]; ++t) {
+            const int32_t J = P.levellist[t];
+            const SNode &sj = P.snodes[J];
+            if (s >= sj.ncb) continue;
+            const int32_t nrb = num_row_tiles(sj.nrows, sj.ncols, sj.ncb);
+            if (kind == K_POTRF) P.tasks.push_back({J, s, s, s});
+            if (kind == K_TRSM)
+              for (int32_t i = s + 1; i < nrb; ++i) P.tasks.push_back({J, i, s, s});
+            if (kind == K_GEMM)
+              for (int32_t j = s + 1; j < sj.ncb; ++j)
+                for (int32_t i = j; i < nrb; ++i) P.tasks.push_back({J, i, j, s});
+          }
+          int64_t cnt = (int64_t)P.tasks.size() - off;
+          if (cnt > 0) P.factor_launches.push_back({kind, l, off, cnt});
+        }
+      }
+    }
+  }
+  // Solve schedules.
+  for (int32_t l = 0; l < nlev; ++l) {
+    int64_t off = (int64_t)P.tasks.size();
+    int32_t maxcb = 0;
+    for (int32_t t = P.levelptr[l]; t < P.levelptr[l + 1]; ++t) {
+      const int32_t J = P.levellist[t];
+      maxcb = std::max(maxcb, P.snodes[J].ncb);
+      for (int32_t bj = 0; bj < P.snodes[J].ncb; ++bj) {
+        int64_t task = diag_task[diag_task_base[J] + bj];
+        if (task >= 0) P.tasks.push_back({J, bj, (int32_t)task, 0});
+      }
+    }
+    if ((int64_t)P.tasks.size() > off) P.fwd_launches.push_back({S_FGATHER, l, off, (int64_t)P.tasks.size() - off});
+    for (int32_t s = 0; s < maxcb; ++s) {
+      for (int kind : {S_FDIAG, S_FGEMV}) {
+        off = (int64_t)P.tasks.size();
+        for (int32_t t = P.levelptr[l]; t < P.levelptr[l + 1]; ++t) {
+          const int32_t J = P.levellist[t];
+          const int32_t ncb = P.snodes[J].ncb;
+          if (s >= ncb) continue;
+          if (kind == S_FDIAG) P.tasks.push_back({J, s, s, s});
+          else
+            for (int32_t i = s + 1; i < ncb; ++i) P.tasks.push_back({J, i, s, s});
+        }
+        if ((int64_t)P.tasks.size() > off) P.fwd_launches.push_back({kind, l, off, (int64_t)P.tasks.size() - off});
+      }
+    }
+  }
+  for (int32_t l = nlev - 1; l >= 0; --l) {
+    int64_t off = (int64_t)P.tasks.size();
+    int32_t maxcb = 0;
+    for (int32_t t = P.levelptr[l]; t < P.levelptr[l + 1]; ++t) {
+      const int32_t J = P.levellist[t];
+      const SNode &sj = P.snodes[J];
+      maxcb = std::max(maxcb, sj.ncb);
+      if (sj.nrows > sj.ncols)
+        for (int32_t bj = 0; bj < sj.ncb; ++bj) P.tasks.push_back({J, bj, 0, 0});
+    }
+    if ((int64_t)P.tasks.size() > off) P.bwd_launches.push_back({S_BGATHER, l, off, (int64_t)P.tasks.size() - off});
+    for (int32_t s = maxcb - 1; s >= 0; --s) {
+      for (int kind : {S_BDIAG, S_BGEMV}) {
+        off = (int64_t)P.tasks.size();
+        for (int32_t t = P.levelptr[l]; t < P.levelptr[l + 1]; ++t) {
+          const int32_t J = P.levellist[t];
+          const int32_t ncb = P.snodes[J].ncb;
+          if (s >= ncb) continue;
+          if (kind == S_BDIAG) P.tasks.push_back({J, s, s, s});
+          else
+            for (int32_t i = 0; i < s; ++i) P.tasks.push_back({J, s, i, s});
+        }
+        if ((int64_t)P.tasks.size() > off) P.bwd_launches.push_back({kind, l, off, (int64_t)P.tasks.size() - off});
+      }
+    }
+  }
+  P.analyze_seconds = timer.seconds();
+  return SYM_OK;
+}
+
+}  // namespace sym

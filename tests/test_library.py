@@ -1,0 +1,145 @@
+"""CPU tests of the C-ABI library: it builds, loads, exports every declared entry point, and its
+host symbolic inspector is bit-exact against the independent oracle. No GPU compute here: the
+handles are analyzed with SYM_FLAG_HOST_ONLY."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1705_06575_gb300 as S
+import workloads as w
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+PAIRS = [("perm", "perm"), ("parent", "parent"), ("colcount", "colcount"), ("fsuper", "fsn"),
+         ("super", "sn"), ("rowptr", "srp"), ("rows", "sri"), ("sparent", "sparent"),
+         ("descptr", "dp"), ("desc", "dk"), ("descr0", "dr0"), ("descnin", "dnin"),
+         ("relptr", "relp"), ("rel", "rel"), ("level", "level"), ("levelptr", "lvp"),
+         ("levellist", "lvl")]
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(sym_[a-z_0-9]+)\s*\(", text))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = S.load()
+    names = declared_functions()
+    assert {"sym_analyze", "sym_factor", "sym_solve"} <= names
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def compare(M, perm=None, relax=oracle.DEFAULT_RELAX):
+    opt = S.sym_options_default()
+    if relax is None:
+        opt.amalgamate = 0
+    else:
+        opt.nrelax[:] = relax[:3]
+        opt.zrelax_permille[:] = relax[3:]
+    s = S.Solver(M.n, M.Ap, M.Ai, perm, opt=opt, host_only=True)
+    o = oracle.Oracle(M.n, M.Ap, M.Ai, perm, relax=relax, want_rel=True)
+    for a, b in PAIRS:
+        got = s.export(a)
+        ref = getattr(o, b)
+        if ref is None:  # no descendant pairs: the oracle keeps no map
+            assert got.size <= 1 and not got[1:].any()
+            continue
+        assert np.array_equal(got, ref), a
+    info = s.info()
+    assert info.nnz_l == o.nnzL
+    assert info.flops == float(o.flops_exact)
+    s.close()
+
+
+@pytest.mark.parametrize("n,density,seed", [(1, 1.0, 0), (2, 1.0, 1), (50, 0.1, 2), (300, 0.02, 3),
+                                            (800, 0.005, 4), (200, 1.0, 5), (400, 0.003, 6)])
+def test_symbolic_bit_exact_random(n, density, seed):
+    rng = np.random.default_rng(seed)
+    M = w.random_spd_pattern(n, density, rng)
+    compare(M)
+    compare(M, perm=rng.permutation(n).astype(np.int32))
+    compare(M, relax=None)
+    compare(M, relax=(2, 8, 24, 500, 50, 10))
+
+
+@pytest.mark.parametrize("maker", [
+    lambda: w.cfg("laplace2d5_64"),
+    lambda: w.dd2d9(40, np.random.default_rng(1)),
+    lambda: w.conduct3d(14, np.random.default_rng(2), "star"),
+    lambda: w.conduct3d(10, np.random.default_rng(3), "box"),
+    lambda: w.vector3d27(6, np.random.default_rng(4), sub=3),
+    lambda: w.erdos_renyi(600, 4, np.random.default_rng(5)),
+])
+def test_symbolic_bit_exact_workloads(maker):
+    M = maker()
+    compare(M, perm=M.perm)
+
+
+def test_special_structures():
+    n = 40
+    Ap = np.arange(n + 1, dtype=np.int64)
+    Ai = np.arange(n, dtype=np.int32)
+    compare(w.Matrix(n, Ap, Ai, np.ones(n)))  # diagonal
+    u = np.arange(n - 1)
+    Ap, Ai, Ax = w.lower_csc(n, u, u + 1, -np.ones(n - 1), np.full(n, 3.0))
+    compare(w.Matrix(n, Ap, Ai, Ax))  # tridiagonal
+    Ap, Ai, Ax = w.lower_csc(n, u, np.full(n - 1, n - 1), -np.ones(n - 1), np.full(n, float(n)))
+    compare(w.Matrix(n, Ap, Ai, Ax))  # arrowhead
+    Ap, Ai, Ax = w.lower_csc(n, np.zeros(n - 1, int), u + 1, -np.ones(n - 1), np.full(n, float(n)))
+    compare(w.Matrix(n, Ap, Ai, Ax))  # arrow pointing the other way: dense fill
+    # two disconnected blocks
+    Ap, Ai, Ax = w.lower_csc(n, np.r_[u[:10], u[20:30]], np.r_[u[:10] + 1, u[20:30] + 1],
+                             -np.ones(20), np.full(n, 3.0))
+    compare(w.Matrix(n, Ap, Ai, Ax))
+
+
+def test_empty_matrix_host_only():
+    s = S.Solver(0, np.zeros(1, np.int64), np.zeros(0, np.int32), host_only=True)
+    assert s.info().nsuper == 0 and s.info().nnz_l == 0
+
+
+def test_invalid_inputs_are_rejected():
+    n = 3
+    Ap = np.array([0, 2, 3, 4])
+    with pytest.raises(S.SymError) as e:
+        S.Solver(n, Ap, np.array([2, 0, 1, 2]), host_only=True)  # diagonal not first
+    assert e.value.code == S.SYM_ERR_INVALID
+    with pytest.raises(S.SymError):
+        S.Solver(n, np.array([0, 2, 2, 3]), np.array([0, 2, 2]), host_only=True)  # missing diagonal
+    with pytest.raises(S.SymError):
+        S.Solver(n, Ap, np.array([0, 5, 1, 2]), host_only=True)  # row out of range
+    with pytest.raises(S.SymError):
+        S.Solver(n, Ap, np.array([0, 2, 1, 2]), perm=np.array([0, 0, 2]), host_only=True)
+    opt = S.sym_options_default()
+    opt.zrelax_permille[0] = 2000
+    with pytest.raises(S.SymError):
+        S.Solver(n, Ap, np.array([0, 2, 1, 2]), opt=opt, host_only=True)
+
+
+def test_host_only_handle_refuses_numeric_calls():
+    M = w.laplace2d5(8, np.random.default_rng(0))
+    s = S.Solver(M.n, M.Ap, M.Ai, M.perm, host_only=True)
+    with pytest.raises(S.SymError) as e:
+        s.factor_host(M.Ax)
+    assert e.value.code == S.SYM_ERR_STATE
+    with pytest.raises(S.SymError):
+        s.solve_host(np.zeros(M.n))
+
+
+def test_plan_sizes_cfg2_scale():
+    """The 64^3 7-point workload: sizes of the plan (sizing check, not a parity target)."""
+    M = w.cfg("conduct3d7_64")
+    s = S.Solver(M.n, M.Ap, M.Ai, M.perm, host_only=True)
+    i = s.info()
+    assert i.nnz_l == 156727345
+    assert abs(i.flops - 4.15e11) / 4.15e11 < 0.01
+    assert i.max_ncols == 6080 and i.nlevels == 20
