@@ -170,6 +170,43 @@ int sym_get_factor_host(sym_handle h, double *Lx_host);
 #define SYM_EXPORT_LXPTR 18      /* int64[nsuper+1]: offset of each panel in the factor storage */
 int64_t sym_export(sym_handle h, int32_t what, void *out);
 
+/* Per-kernel timing for measurement (no counterpart in the paper). With SYM_PROFILE_ON the
+ * executor records a CUDA event on the handle's stream before the first launch and after every
+ * launch of sym_factor* / sym_solve*; each sym_factor* and sym_solve* call then waits for its
+ * work and adds the elapsed time of every launch to the totals of its kernel kind. OFF stops
+ * recording (totals kept); RESET clears the totals. */
+#define SYM_PROFILE_OFF 0
+#define SYM_PROFILE_ON 1
+#define SYM_PROFILE_RESET 2
+int sym_profile(sym_handle h, int32_t mode);
+
+/* Kernel kinds for sym_profile_read. */
+#define SYM_KIND_SCATTER 0   /* zero the panels and scatter A (two launches counted as one) */
+#define SYM_KIND_UPDATE 1    /* descendant updates of tiles */
+#define SYM_KIND_POTRF 2     /* dense Cholesky of diagonal tiles */
+#define SYM_KIND_TRSM 3      /* triangular solves of the tiles below a diagonal tile */
+#define SYM_KIND_GEMM 4      /* trailing updates inside a supernode */
+#define SYM_KIND_FGATHER 11  /* forward solve: gather from descendants */
+#define SYM_KIND_FDIAG 12    /* forward solve: diagonal tiles */
+#define SYM_KIND_FGEMV 13    /* forward solve: updates inside a supernode */
+#define SYM_KIND_BGATHER 14  /* backward solve: gather from the rows below */
+#define SYM_KIND_BDIAG 15    /* backward solve: diagonal tiles */
+#define SYM_KIND_BGEMV 16    /* backward solve: updates inside a supernode */
+#define SYM_KIND_PERM 17     /* solve: permutations in and out */
+#define SYM_NUM_KINDS 18
+
+/* Totals for one kernel kind since the last RESET: milliseconds, launches, and the algorithmic
+ * flops those launches performed (useful multiply-adds x2 plus divisions and square roots; the
+ * strict upper part of diagonal tiles excluded, explicit zeros of amalgamated panels included).
+ * Any output pointer may be NULL. */
+int sym_profile_read(sym_handle h, int32_t kind, double *ms, int64_t *launches, double *flops);
+
+/* Measured FMA throughput of the current device in GFLOP/s (2 flops per FMA) for precision 64
+ * (FP64 pipe) or 32 (FP32 pipe): register-resident FMA chains on every SM, best of three
+ * launches of about 50 ms. The denominator of the roofline fraction of the ALU-bound kernels
+ * (no counterpart in the paper). */
+int sym_fma_peak(int32_t precision, double *gflops);
+
 /* Text for an error code, and the message of the last failure on this thread. */
 const char *sym_error_string(int code);
 const char *sym_last_error_string(void);

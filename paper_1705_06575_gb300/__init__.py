@@ -20,7 +20,7 @@ __all__ = [
     "sym_analyze_perm", "sym_set_stream", "sym_factor", "sym_factor_async", "sym_status",
     "sym_factor_host", "sym_solve", "sym_solve_multi", "sym_solve_host", "sym_info",
     "sym_last_error_column", "sym_get_factor_host", "sym_export", "sym_free", "load", "Solver",
-    "EXPORTS",
+    "EXPORTS", "sym_profile", "sym_profile_read", "sym_fma_peak", "sym_solve_host_ptr", "KINDS",
 ]
 
 SYM_OK = 0
@@ -101,6 +101,10 @@ def load():
             "sym_error_string": ([I], ct.c_char_p),
             "sym_last_error_string": ([], ct.c_char_p),
             "sym_free": ([P], None),
+            "sym_profile": ([P, i32], I),
+            "sym_profile_read": ([P, i32, ct.POINTER(ct.c_double), ct.POINTER(i64),
+                                  ct.POINTER(ct.c_double)], I),
+            "sym_fma_peak": ([i32, ct.POINTER(ct.c_double)], I),
         }
         for name, (args, res) in sigs.items():
             f = getattr(lib, name)
@@ -172,6 +176,9 @@ def sym_status(h):
 
 
 def sym_factor_host(h, Ax):
+    """Ax: a numpy array, or the integer address of host memory (pinned or pageable)."""
+    if isinstance(Ax, int):
+        return _check(load().sym_factor_host(h, Ax))
     Ax = _host(Ax, np.float64)
     return _check(load().sym_factor_host(h, Ax.ctypes.data))
 
@@ -193,6 +200,33 @@ def sym_solve_host(h, B):
     n = Bf.shape[0]
     _check(load().sym_solve_host(h, Bf.shape[1], Bf.ctypes.data, n, X.ctypes.data, n))
     return X[:, 0] if one else X
+
+
+def sym_solve_host_ptr(h, nrhs, B, ldb, X, ldx):
+    """Host-pointer solve with raw integer addresses (for pinned buffers)."""
+    return _check(load().sym_solve_host(h, int(nrhs), B, int(ldb), X, int(ldx)))
+
+
+SYM_PROFILE_OFF, SYM_PROFILE_ON, SYM_PROFILE_RESET = 0, 1, 2
+KINDS = {"scatter": 0, "update": 1, "potrf": 2, "trsm": 3, "gemm": 4, "fgather": 11, "fdiag": 12,
+         "fgemv": 13, "bgather": 14, "bdiag": 15, "bgemv": 16, "perm": 17}
+
+
+def sym_profile(h, mode):
+    return _check(load().sym_profile(h, int(mode)))
+
+
+def sym_profile_read(h, kind):
+    """(milliseconds, launches, algorithmic flops) accumulated for one kernel kind."""
+    ms, nl, fl = ct.c_double(), ct.c_int64(), ct.c_double()
+    _check(load().sym_profile_read(h, int(kind), ct.byref(ms), ct.byref(nl), ct.byref(fl)))
+    return ms.value, nl.value, fl.value
+
+
+def sym_fma_peak(precision=64):
+    g = ct.c_double()
+    _check(load().sym_fma_peak(int(precision), ct.byref(g)))
+    return g.value
 
 
 def sym_info(h):
@@ -279,6 +313,12 @@ class Solver:
 
     def factor_panels(self):
         return sym_get_factor_host(self.h)
+
+    def profile(self, mode):
+        sym_profile(self.h, mode)
+
+    def profile_read(self, kind):
+        return sym_profile_read(self.h, KINDS[kind] if isinstance(kind, str) else kind)
 
     def error_column(self):
         return sym_last_error_column(self.h)

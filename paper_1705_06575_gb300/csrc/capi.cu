@@ -30,6 +30,12 @@ struct sym_handle_s {
   int64_t device_bytes = 0;
   bool factored = false;
   int64_t err_col = -1;
+  // per-kernel profiling
+  bool profiling = false;
+  std::vector<cudaEvent_t> events;
+  double prof_ms[sym::NUM_KINDS] = {};
+  int64_t prof_launches[sym::NUM_KINDS] = {};
+  double prof_flops[sym::NUM_KINDS] = {};
 };
 
 namespace {
@@ -62,7 +68,33 @@ int upload(const std::vector<V> &v, void **dst, int64_t &bytes) {
   return SYM_OK;
 }
 
+int ensure_events(sym_handle_s *h, size_t count) {
+  while (h->events.size() < count) {
+    cudaEvent_t e;
+    CUDA_TRY(cudaEventCreate(&e), "cudaEventCreate");
+    h->events.push_back(e);
+  }
+  return SYM_OK;
+}
+
+// After the traced work has finished: add each launch's elapsed time to its kind.
+int collect_trace(sym_handle_s *h, const sym::LaunchTrace &tr, double flop_scale, bool solve) {
+  CUDA_TRY(cudaStreamSynchronize(h->stream), "profile sync");
+  for (size_t i = 0; i < tr.kinds.size(); ++i) {
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, h->events[i], h->events[i + 1]), "cudaEventElapsedTime");
+    h->prof_ms[tr.kinds[i]] += ms;
+    h->prof_launches[tr.kinds[i]] += 1;
+  }
+  for (int k = 0; k < sym::NUM_KINDS; ++k) {
+    const bool is_solve = k >= sym::S_FGATHER;
+    if (is_solve == solve) h->prof_flops[k] += h->plan.kind_flops[k] * flop_scale;
+  }
+  return SYM_OK;
+}
+
 void release_device(sym_handle_s *h) {
+  for (cudaEvent_t e : h->events) cudaEventDestroy(e);
   void *ptrs[] = {h->d_sn, h->d_rows, h->d_rel, h->d_amap, h->d_updt, h->d_upde, h->d_tasks,
                   h->d_perm, h->d_Lx, h->d_status, h->d_y, h->d_stage};
   for (void *p : ptrs)
@@ -228,8 +260,19 @@ int sym_factor_async(sym_handle h, const double *Ax) {
   h->h_status[0] = LLONG_MAX;
   CUDA_TRY(cudaMemcpyAsync(h->d_status, &h->h_status[0], sizeof(long long), cudaMemcpyHostToDevice, h->stream),
            "status reset");
-  CUDA_TRY(sym::run_factor<double>(h->dp, h->plan.factor_launches, Ax, h->d_Lx, h->d_status, h->stream),
+  sym::LaunchTrace tr, *trp = nullptr;
+  if (h->profiling) {
+    rc = ensure_events(h, h->plan.factor_launches.size() + 3);
+    if (rc) return rc;
+    tr.events = &h->events;
+    trp = &tr;
+  }
+  CUDA_TRY(sym::run_factor<double>(h->dp, h->plan.factor_launches, Ax, h->d_Lx, h->d_status, h->stream, trp),
            "factor kernels");
+  if (trp) {
+    rc = collect_trace(h, tr, 1.0, false);
+    if (rc) return rc;
+  }
   CUDA_TRY(cudaMemcpyAsync(&h->h_status[1], h->d_status, sizeof(long long), cudaMemcpyDeviceToHost, h->stream),
            "status read");
   return SYM_OK;
@@ -267,9 +310,18 @@ int sym_solve_multi(sym_handle h, int32_t nrhs, const double *B, int64_t ldb, do
     return fail(SYM_ERR_INVALID, "bad solve arguments");
   rc = ensure_y(h, n * (int64_t)nrhs);
   if (rc) return rc;
+  sym::LaunchTrace tr, *trp = nullptr;
+  if (h->profiling) {
+    const size_t passes = (size_t)(nrhs + 7) / 8;
+    rc = ensure_events(h, passes * (h->plan.fwd_launches.size() + h->plan.bwd_launches.size()) + 4);
+    if (rc) return rc;
+    tr.events = &h->events;
+    trp = &tr;
+  }
   CUDA_TRY(sym::run_solve<double>(h->dp, h->plan.fwd_launches, h->plan.bwd_launches, h->d_Lx, nrhs, B, ldb,
-                                  X, ldx, h->d_y, h->stream),
+                                  X, ldx, h->d_y, h->stream, trp),
            "solve kernels");
+  if (trp) return collect_trace(h, tr, (double)nrhs, true);
   return SYM_OK;
 }
 
@@ -371,6 +423,31 @@ int64_t sym_export(sym_handle h, int32_t what, void *out) {
   }
   if (out && count > 0) std::memcpy(out, src, (size_t)count * esz);
   return count;
+}
+
+int sym_profile(sym_handle h, int32_t mode) {
+  if (!h) return fail(SYM_ERR_INVALID, "null handle");
+  if (mode == SYM_PROFILE_ON) h->profiling = true;
+  else if (mode == SYM_PROFILE_OFF) h->profiling = false;
+  else if (mode == SYM_PROFILE_RESET) {
+    for (int k = 0; k < sym::NUM_KINDS; ++k) {
+      h->prof_ms[k] = 0.0;
+      h->prof_launches[k] = 0;
+      h->prof_flops[k] = 0.0;
+    }
+  } else {
+    return fail(SYM_ERR_INVALID, "unknown profile mode");
+  }
+  return SYM_OK;
+}
+
+int sym_profile_read(sym_handle h, int32_t kind, double *ms, int64_t *launches, double *flops) {
+  if (!h) return fail(SYM_ERR_INVALID, "null handle");
+  if (kind < 0 || kind >= sym::NUM_KINDS) return fail(SYM_ERR_INVALID, "unknown kernel kind");
+  if (ms) *ms = h->prof_ms[kind];
+  if (launches) *launches = h->prof_launches[kind];
+  if (flops) *flops = h->prof_flops[kind];
+  return SYM_OK;
 }
 
 const char *sym_error_string(int code) {

@@ -38,6 +38,66 @@ __device__ __forceinline__ int d_row_tile_rows(int32_t i, int32_t ncols, int32_t
   return (int)(r < NB ? r : NB);
 }
 
+// r[i][j] -= A[kk][lane + 32 i] * B[kk][w + 8 j] for kk < kc, for the first NI row halves and the
+// first NJ column slots of this warp. The shapes are template parameters so that no FMA of an
+// inactive slot is ever issued (a run-time guard would be if-converted into predicated FMAs,
+// which still occupy the FP64 pipe).
+template <int NI, int NJ, int KMAX, typename T>
+__device__ __forceinline__ void fma_chunk(T (&r)[2][8], const T (*As)[NB], const T (*Bs)[NB], int kc,
+                                          int lane, int w) {
+#pragma unroll 2
+  for (int kk = 0; kk < kc; ++kk) {
+    const T a0 = As[kk][lane];
+    const T a1 = NI > 1 ? As[kk][lane + 32] : T(0);
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+      const T bv = Bs[kk][w + 8 * j];
+      r[0][j] = fma(-a0, bv, r[0][j]);
+      if (NI > 1) r[1][j] = fma(-a1, bv, r[1][j]);
+    }
+  }
+}
+
+// Warp-uniform dispatch on (ni, nj); every case is its own straight-line loop.
+template <int KMAX, typename T>
+__device__ __forceinline__ void fma_chunk_dispatch(T (&r)[2][8], const T (*As)[NB], const T (*Bs)[NB],
+                                                   int kc, int lane, int w, int ni, int nj) {
+#define SYM_CASE(J)                                                  \
+  case J:                                                            \
+    if (ni > 1) fma_chunk<2, J, KMAX>(r, As, Bs, kc, lane, w);       \
+    else fma_chunk<1, J, KMAX>(r, As, Bs, kc, lane, w);              \
+    break;
+  switch (nj) {
+    SYM_CASE(1)
+    SYM_CASE(2)
+    SYM_CASE(3)
+    SYM_CASE(4)
+    SYM_CASE(5)
+    SYM_CASE(6)
+    SYM_CASE(7)
+    SYM_CASE(8)
+    default:
+      break;
+  }
+#undef SYM_CASE
+}
+
+// Reciprocal square root of d > 0 in FP64 by Newton-Raphson on f(x) = 1/x^2 - d:
+// x <- x + (x/2)(1 - d x^2). A single-precision seed has 23 correct bits; each step doubles them
+// (46, then beyond 53), so two steps reach double precision up to a few ulps. The chain is six
+// dependent FP64 operations, which keeps the serial pivot path of a Cholesky short on a GPU
+// whose FP64 pipe is narrow. Outside the single-precision normal range it falls back to 1/sqrt.
+__device__ __forceinline__ double rsqrt_newton(double d) {
+  if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
+  double x = (double)rsqrtf((float)d);
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const double e = fma(-d * x, x, 1.0);
+    x = fma(0.5 * x, e, x);
+  }
+  return x;
+}
+
 // ---------------------------------------------------------------------------------------------
 // Scatter of A into the zeroed panels (the temporary block storage of Sec. 2.3.2).
 template <typename T>
@@ -86,8 +146,8 @@ __global__ void __launch_bounds__(THREADS) k_update(const SNode *__restrict__ sn
     if (tid < E.m) prow[tid] = rel[E.relr + tid] - (int)rb;
     if (tid >= NB && tid - NB < E.n) pcol[tid - NB] = rel[E.relc + tid - NB] - cb;
     __syncthreads();
-    const int ni = E.m > 32 ? 2 : 1;
-    const int nj = E.n > w ? (E.n - w + 7) / 8 : 0;
+    const int ni = E.m > 32 ? 2 : 1;           // row halves with at least one valid row
+    const int nj = E.n > w ? (E.n - w + 7) / 8 : 0;  // this warp's columns w + 8j < n
     T r[2][8];
 #pragma unroll
     for (int i = 0; i < 2; ++i)
@@ -106,20 +166,7 @@ __global__ void __launch_bounds__(THREADS) k_update(const SNode *__restrict__ sn
         Bs[kk][a] = (a < E.n && kk < kc) ? col[E.c_lo + a] : T(0);
       }
       __syncthreads();
-      if (nj > 0) {
-        for (int kk = 0; kk < kc; ++kk) {
-          const T a0 = As[kk][lane];
-          const T a1 = As[kk][lane + 32];
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            if (j < nj) {
-              const T bv = Bs[kk][w + 8 * j];
-              r[0][j] = fma(-a0, bv, r[0][j]);
-              if (ni > 1) r[1][j] = fma(-a1, bv, r[1][j]);
-            }
-          }
-        }
-      }
+      fma_chunk_dispatch<KCU>(r, As, Bs, kc, lane, w, ni, nj);
       __syncthreads();
     }
 #pragma unroll
@@ -155,9 +202,10 @@ __global__ void __launch_bounds__(THREADS) k_potrf(const SNode *__restrict__ sn,
   const int ts = min(NB, sj.ncols - s * NB);
   T *D = Lx + sj.lx + (int64_t)(s * NB) * sj.nrows + s * NB;
   const int tid = threadIdx.x;
+  const int r = tid & (NB - 1), g = tid >> 6;  // thread owns row r, columns g, g+4, ...
   for (int idx = tid; idx < NB * NB; idx += THREADS) {
-    int r = idx % NB, c = idx / NB;
-    a[c][r] = (r < ts && c < ts && r >= c) ? D[(int64_t)c * sj.nrows + r] : T(0);
+    int rr = idx % NB, c = idx / NB;
+    a[c][rr] = (rr < ts && c < ts && rr >= c) ? D[(int64_t)c * sj.nrows + rr] : T(0);
   }
   __syncthreads();
   for (int c = 0; c < ts; ++c) {
@@ -167,24 +215,23 @@ __global__ void __launch_bounds__(THREADS) k_potrf(const SNode *__restrict__ sn,
         atomicMin(status, (long long)(sj.first + s * NB + c));
         d = T(1);
       }
-      const T l = sqrt(d);
-      a[c][c] = l;
-      pinv = T(1) / l;
+      const T x = rsqrt_newton(d);
+      a[c][c] = d * x;  // sqrt(d)
+      pinv = x;
     }
     __syncthreads();
     const T inv = pinv;
-    for (int r = c + 1 + tid; r < ts; r += THREADS) a[c][r] *= inv;
-    __syncthreads();
-    const int rem = ts - c - 1;
-    for (int idx = tid; idx < rem * rem; idx += THREADS) {
-      int rr = c + 1 + idx % rem, cc = c + 1 + idx / rem;
-      if (rr >= cc) a[cc][rr] = fma(-a[c][rr], a[c][cc], a[cc][rr]);
+    if (r > c && r < ts) {
+      const T lrc = a[c][r] * inv;  // L(r, c); column c is rescaled after the barrier
+      for (int cc = c + 1 + g; cc <= r; cc += 4) a[cc][r] = fma(-lrc, a[c][cc] * inv, a[cc][r]);
     }
     __syncthreads();
+    if (g == 0 && r > c && r < ts) a[c][r] *= inv;
   }
+  __syncthreads();
   for (int idx = tid; idx < NB * NB; idx += THREADS) {
-    int r = idx % NB, c = idx / NB;
-    if (r < ts && c < ts) D[(int64_t)c * sj.nrows + r] = r >= c ? a[c][r] : T(0);
+    int rr = idx % NB, c = idx / NB;
+    if (rr < ts && c < ts) D[(int64_t)c * sj.nrows + rr] = rr >= c ? a[c][rr] : T(0);
   }
 }
 
@@ -214,16 +261,16 @@ __global__ void __launch_bounds__(THREADS) k_trsm(const SNode *__restrict__ sn,
   __syncthreads();
   if (tid < ts) dinv[tid] = T(1) / Ls[tid][tid];
   __syncthreads();
+  const int r = tid & (NB - 1), g = tid >> 6;  // thread owns row r, columns c+1+g, c+5+g, ...
   for (int c = 0; c < ts; ++c) {
-    if (tid < tm) X[c][tid] *= dinv[c];
-    __syncthreads();
-    const int rem = ts - c - 1;
-    for (int idx = tid; idx < tm * rem; idx += THREADS) {
-      int r = idx % tm, cc = c + 1 + idx / tm;
-      X[cc][r] = fma(-X[c][r], Ls[c][cc], X[cc][r]);
+    if (r < tm) {
+      const T xc = X[c][r] * dinv[c];  // X(r, c) is final once columns < c are applied
+      for (int cc = c + 1 + g; cc < ts; cc += 4) X[cc][r] = fma(-xc, Ls[c][cc], X[cc][r]);
     }
     __syncthreads();
+    if (g == 0 && r < tm) X[c][r] *= dinv[c];
   }
+  __syncthreads();
   for (int idx = tid; idx < NB * NB; idx += THREADS) {
     int r = idx % NB, c = idx / NB;
     if (r < tm && c < ts) B[(int64_t)c * sj.nrows + r] = X[c][r];
@@ -266,20 +313,7 @@ __global__ void __launch_bounds__(THREADS) k_gemm(const SNode *__restrict__ sn,
       Bs[kk][a] = (a < tn && kk < kc) ? col[(int64_t)j * NB + a] : T(0);
     }
     __syncthreads();
-    if (nj > 0) {
-      for (int kk = 0; kk < kc; ++kk) {
-        const T a0 = As[kk][lane];
-        const T a1 = As[kk][lane + 32];
-#pragma unroll
-        for (int jj = 0; jj < 8; ++jj) {
-          if (jj < nj) {
-            const T bv = Bs[kk][w + 8 * jj];
-            r[0][jj] = fma(-a0, bv, r[0][jj]);
-            if (ni > 1) r[1][jj] = fma(-a1, bv, r[1][jj]);
-          }
-        }
-      }
-    }
+    fma_chunk_dispatch<KC>(r, As, Bs, kc, lane, w, ni, nj);
     __syncthreads();
   }
 #pragma unroll
@@ -380,6 +414,7 @@ __global__ void __launch_bounds__(THREADS) k_diag_solve(const SNode *__restrict_
                                                         int64_t n, int r0, int nr, int64_t toff) {
   __shared__ double Ls[NB][NB + 1];  // [col][row]
   __shared__ double v[MAXRHS][NB];
+  __shared__ double dinv[NB];
   const Int4 t = tasks[toff + blockIdx.x];
   const SNode sj = sn[t.a];
   const int s = t.b;
@@ -396,28 +431,31 @@ __global__ void __launch_bounds__(THREADS) k_diag_solve(const SNode *__restrict_
     v[c][r] = (r < ts && c < nr) ? y[(int64_t)(r0 + c) * n + g0 + r] : 0.0;
   }
   __syncthreads();
+  if (tid < ts) dinv[tid] = 1.0 / Ls[tid][tid];
+  __syncthreads();
+  const int r = tid & (NB - 1), qg = tid >> 6;  // row r, right-hand sides qg, qg + 4
   if (!TRANS) {
     for (int c = 0; c < ts; ++c) {
-      if (tid < nr) v[tid][c] /= Ls[c][c];
-      __syncthreads();
-      const int rem = ts - c - 1;
-      for (int idx = tid; idx < rem * nr; idx += THREADS) {
-        int r = c + 1 + idx % rem, q = idx / rem;
-        v[q][r] = fma(-Ls[c][r], v[q][c], v[q][r]);
+      if (r > c && r < ts) {
+        const double l = Ls[c][r];
+        for (int q = qg; q < nr; q += 4) v[q][r] = fma(-l, v[q][c] * dinv[c], v[q][r]);
       }
       __syncthreads();
+      if (r == c)
+        for (int q = qg; q < nr; q += 4) v[q][c] *= dinv[c];
     }
   } else {
     for (int c = ts - 1; c >= 0; --c) {
-      if (tid < nr) v[tid][c] /= Ls[c][c];
-      __syncthreads();
-      for (int idx = tid; idx < c * nr; idx += THREADS) {
-        int r = idx % c, q = idx / c;
-        v[q][r] = fma(-Ls[r][c], v[q][c], v[q][r]);  // L(c, r) at column r, row c
+      if (r < c) {
+        const double l = Ls[r][c];  // L(c, r)
+        for (int q = qg; q < nr; q += 4) v[q][r] = fma(-l, v[q][c] * dinv[c], v[q][r]);
       }
       __syncthreads();
+      if (r == c)
+        for (int q = qg; q < nr; q += 4) v[q][c] *= dinv[c];
     }
   }
+  __syncthreads();
   for (int idx = tid; idx < MAXRHS * NB; idx += THREADS) {
     int r = idx % NB, c = idx / NB;
     if (r < ts && c < nr) y[(int64_t)(r0 + c) * n + g0 + r] = v[c][r];
@@ -527,17 +565,25 @@ inline int grid_for(int64_t count, int per) {
 
 }  // namespace
 
+inline void trace_mark(LaunchTrace *tr, int32_t kind, cudaStream_t st) {
+  if (!tr) return;
+  cudaEventRecord((*tr->events)[tr->used++], st);
+  if (kind >= 0) tr->kinds.push_back(kind);
+}
+
 template <typename T>
 cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, const double *Ax,
-                       T *Lx, long long *status, cudaStream_t st) {
+                       T *Lx, long long *status, cudaStream_t st, LaunchTrace *trace) {
   static thread_local bool attr_set = false;  // per host thread: the attribute is per device
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(k_trsm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem<T>());
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
+  trace_mark(trace, -1, st);
   k_zero<T><<<grid_for(d.storage, THREADS * 4), THREADS, 0, st>>>(Lx, d.storage);
   if (d.nnz_a > 0) k_scatter<T><<<grid_for(d.nnz_a, THREADS * 4), THREADS, 0, st>>>(Ax, d.amap, Lx, d.nnz_a);
+  trace_mark(trace, K_SCATTER, st);
   for (const Launch &L : launches) {
     const unsigned g = (unsigned)L.count;
     switch (L.kind) {
@@ -556,6 +602,7 @@ cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, co
       default:
         return cudaErrorInvalidValue;
     }
+    trace_mark(trace, L.kind, st);
   }
   return cudaGetLastError();
 }
@@ -563,10 +610,12 @@ cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, co
 template <typename T>
 cudaError_t run_solve(const DevPlan &d, const std::vector<Launch> &fwd, const std::vector<Launch> &bwd,
                       const T *Lx, int nrhs, const double *B, int64_t ldb, double *X, int64_t ldx,
-                      double *y, cudaStream_t st) {
+                      double *y, cudaStream_t st, LaunchTrace *trace) {
   const int64_t n = d.n;
   if (n == 0 || nrhs == 0) return cudaSuccess;
+  trace_mark(trace, -1, st);
   k_perm_in<<<grid_for(n * nrhs, THREADS), THREADS, 0, st>>>(d.perm, B, ldb, y, n, nrhs);
+  trace_mark(trace, S_PERM, st);
   for (int r0 = 0; r0 < nrhs; r0 += MAXRHS) {
     const int nr = nrhs - r0 < MAXRHS ? nrhs - r0 : MAXRHS;
     for (const Launch &L : fwd) {
@@ -584,6 +633,7 @@ cudaError_t run_solve(const DevPlan &d, const std::vector<Launch> &fwd, const st
         default:
           return cudaErrorInvalidValue;
       }
+      trace_mark(trace, L.kind, st);
     }
     for (const Launch &L : bwd) {
       const unsigned g = (unsigned)L.count;
@@ -600,17 +650,19 @@ cudaError_t run_solve(const DevPlan &d, const std::vector<Launch> &fwd, const st
         default:
           return cudaErrorInvalidValue;
       }
+      trace_mark(trace, L.kind, st);
     }
   }
   k_perm_out<<<grid_for(n * nrhs, THREADS), THREADS, 0, st>>>(d.perm, y, X, ldx, n, nrhs);
+  trace_mark(trace, S_PERM, st);
   return cudaGetLastError();
 }
 
 template cudaError_t run_factor<double>(const DevPlan &, const std::vector<Launch> &, const double *,
-                                        double *, long long *, cudaStream_t);
+                                        double *, long long *, cudaStream_t, LaunchTrace *);
 template cudaError_t run_solve<double>(const DevPlan &, const std::vector<Launch> &,
                                        const std::vector<Launch> &, const double *, int,
                                        const double *, int64_t, double *, int64_t, double *,
-                                       cudaStream_t);
+                                       cudaStream_t, LaunchTrace *);
 
 }  // namespace sym

@@ -22,17 +22,26 @@ struct DevPlan {
   int64_t storage = 0;
 };
 
+// Optional per-launch timing: when non-null, an event is recorded before the first launch and
+// after every launch on the same stream; kinds[i] is the Kind of launch i (K_SCATTER for the
+// zero + scatter pair, S_PERM for the permutations of the solve).
+struct LaunchTrace {
+  std::vector<cudaEvent_t> *events = nullptr;  // at least launches + 3 events
+  std::vector<int32_t> kinds;
+  int used = 0;
+};
+
 // Numeric factorization: scatter A into the zeroed panels, then run the launch schedule.
 // status: device int64, receives the smallest failing (permuted) column, or stays INT64_MAX.
 template <typename T>
 cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, const double *Ax,
-                       T *Lx, long long *status, cudaStream_t st);
+                       T *Lx, long long *status, cudaStream_t st, LaunchTrace *trace = nullptr);
 
 // Solve with nrhs right-hand sides: y = P b, forward sweep, backward sweep, x = P^T y.
 // y: device work array of n * nrhs (ld n).
 template <typename T>
 cudaError_t run_solve(const DevPlan &d, const std::vector<Launch> &fwd, const std::vector<Launch> &bwd,
                       const T *Lx, int nrhs, const double *B, int64_t ldb, double *X, int64_t ldx,
-                      double *y, cudaStream_t st);
+                      double *y, cudaStream_t st, LaunchTrace *trace = nullptr);
 
 }  // namespace sym

@@ -66,6 +66,7 @@ struct UpdTask {
 
 // Kernel kinds of the launch schedule.
 enum Kind : int32_t {
+  K_SCATTER = 0,  // zero the panels and scatter A into them (two launches)
   K_UPDATE = 1,   // external updates of tiles (UpdTask list)
   K_POTRF = 2,    // dense Cholesky of diagonal tile s (int4 {J, s, s, s})
   K_TRSM = 3,     // tile (i, s) <- tile * L_ss^-T (int4 {J, i, s, s})
@@ -76,6 +77,8 @@ enum Kind : int32_t {
   S_BGATHER = 14, // z_J(tile bj) -= L_J(off rows, tile)^T z(off rows) (int4 {J, bj, 0, 0})
   S_BDIAG = 15,   // z_s <- L_ss^-T z_s (int4 {J, s, s, s})
   S_BGEMV = 16,   // z_i -= L_si^T z_s (int4 {J, s, i, s})
+  S_PERM = 17,    // y = P b and x = P^T y
+  NUM_KINDS = 18,
 };
 
 struct Launch {
@@ -120,6 +123,10 @@ struct Plan {
   std::vector<Launch> fwd_launches;
   std::vector<Launch> bwd_launches;
   int32_t max_ncols = 0;
+  // Algorithmic flops per kind for one factorization (solve kinds: per right-hand side): the
+  // useful multiply-adds (x2), square roots and divisions, excluding the strict upper part of
+  // diagonal tiles; explicit zeros of amalgamated panels are included.
+  double kind_flops[NUM_KINDS] = {};
 
   int32_t nsuper() const { return (int32_t)super.size() - 1; }
   int64_t storage() const { return lxptr.empty() ? 0 : lxptr.back(); }

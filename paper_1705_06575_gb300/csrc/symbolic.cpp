@@ -540,6 +540,59 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
       }
     }
   }
+  // 12. Algorithmic flops of each kernel kind (see Plan::kind_flops).
+  {
+    auto sq = [](double x) { return x * x; };
+    for (const UpdTask &u : P.upd_tasks) {
+      for (int64_t e = u.e0; e < u.e1; ++e) {
+        const UpdEntry &E = P.upd_entries[e];
+        const double k = P.snodes[E.K].ncols;
+        if (u.bi != u.bj) {
+          P.kind_flops[K_UPDATE] += 2.0 * E.m * E.n * k;
+        } else {
+          const int32_t *rr = P.rel.data() + E.relr;
+          const int32_t *rc = P.rel.data() + E.relc;
+          double pairs = 0;
+          for (int32_t b = 0; b < E.n; ++b)
+            pairs += (double)(E.m - (std::lower_bound(rr, rr + E.m, rc[b]) - rr));
+          P.kind_flops[K_UPDATE] += 2.0 * k * pairs;
+        }
+        if (u.bi == u.bj) P.kind_flops[S_FGATHER] += 2.0 * E.n * k;
+      }
+    }
+    auto cols_of_tile = [](const SNode &s, int32_t t) { return std::min<int32_t>(NB, s.ncols - t * NB); };
+    for (const Launch &L : P.factor_launches) {
+      if (L.kind == K_UPDATE) continue;
+      for (int64_t t = L.off; t < L.off + L.count; ++t) {
+        const Int4 &q = P.tasks[t];
+        const SNode &s = P.snodes[q.a];
+        if (L.kind == K_POTRF) {
+          const double ts = cols_of_tile(s, q.b);
+          P.kind_flops[K_POTRF] += ts * (ts + 1) * (2 * ts + 1) / 6.0;
+        } else if (L.kind == K_TRSM) {
+          const double ts = cols_of_tile(s, q.c);
+          const int64_t rb = row_tile_base(q.b, s.ncols, s.ncb);
+          const double tm = std::min<int64_t>(NB, (q.b < s.ncb ? s.ncols : s.nrows) - rb);
+          P.kind_flops[K_TRSM] += tm * sq(ts);
+        } else if (L.kind == K_GEMM) {
+          const double ks = cols_of_tile(s, q.d), tn = cols_of_tile(s, q.c);
+          const int64_t rb = row_tile_base(q.b, s.ncols, s.ncb);
+          const double tm = std::min<int64_t>(NB, (q.b < s.ncb ? s.ncols : s.nrows) - rb);
+          P.kind_flops[K_GEMM] += q.b == q.c ? ks * tn * (tn + 1) : 2.0 * tm * tn * ks;
+        }
+      }
+    }
+    for (const std::vector<Launch> *list : {&P.fwd_launches, &P.bwd_launches})
+      for (const Launch &L : *list)
+        for (int64_t t = L.off; t < L.off + L.count; ++t) {
+          const Int4 &q = P.tasks[t];
+          const SNode &s = P.snodes[q.a];
+          if (L.kind == S_FDIAG || L.kind == S_BDIAG) P.kind_flops[L.kind] += sq(cols_of_tile(s, q.b));
+          if (L.kind == S_FGEMV) P.kind_flops[L.kind] += 2.0 * cols_of_tile(s, q.b) * cols_of_tile(s, q.c);
+          if (L.kind == S_BGEMV) P.kind_flops[L.kind] += 2.0 * cols_of_tile(s, q.b) * cols_of_tile(s, q.c);
+          if (L.kind == S_BGATHER) P.kind_flops[L.kind] += 2.0 * (s.nrows - s.ncols) * cols_of_tile(s, q.b);
+        }
+  }
   P.analyze_seconds = timer.seconds();
   return SYM_OK;
 }

@@ -118,6 +118,29 @@ def test_diagonal_and_tridiagonal(torch_cuda):
     check_matrix(torch_cuda, w.Matrix(n, Ap, Ai, Ax))
 
 
+def test_pivot_square_roots_within_two_ulp(torch_cuda):
+    """Diagonal matrices: every L_jj is a pivot square root computed by the POTRF kernel's
+    Newton-Raphson reciprocal square root; it must match IEEE sqrt within 2 ulp over a wide
+    range of magnitudes (including values outside the single-precision range)."""
+    torch = torch_cuda
+    S = _lib()
+    rng = np.random.default_rng(17)
+    d = np.concatenate([10.0 ** rng.uniform(-300, 300, 2000), rng.uniform(0.5, 2.0, 2000),
+                        10.0 ** rng.uniform(-29, 29, 2000)])
+    n = d.size
+    Ap = np.arange(n + 1, dtype=np.int64)
+    Ai = np.arange(n, dtype=np.int32)
+    s = S.Solver(n, Ap, Ai)
+    s.factor(torch.from_numpy(d).cuda())
+    Lx = s.factor_panels()
+    perm = s.export("perm")
+    lx = s.export("lxptr")
+    got = Lx[lx[:-1]]  # one 1 x 1 panel per column, in the final order
+    ref = np.sqrt(d[perm])
+    ulp = np.abs(got - ref) / np.spacing(ref)
+    assert ulp.max() <= 2.0, ulp.max()
+
+
 def test_grids_nested_dissection(torch_cuda):
     rng = np.random.default_rng(7)
     check_matrix(torch_cuda, w.dd2d9(48, rng), nrhs=2)
