@@ -134,6 +134,25 @@ int sym_solve(sym_handle h, const double *b, double *x);
 int sym_solve_multi(sym_handle h, int32_t nrhs, const double *B, int64_t ldb, double *X,
                     int64_t ldx);
 
+/* As sym_solve_multi, but allocates nothing: for callers that may not call cudaMalloc (device
+ * memory owned by their own pool or caching allocator, or loops that cannot take the device
+ * synchronization cudaMalloc/cudaFree imply). The paper has no counterpart; it is a property of
+ * this library's interface. The permuted work block (n * nrhs doubles) lives in a fixed array of
+ * SYM_NOALLOC_MAX_WORK doubles (8 MiB) in the library's device memory, which every device that
+ * loads the library holds until the process exits. Limits and behaviour:
+ *   - n * nrhs > SYM_NOALLOC_MAX_WORK returns SYM_ERR_LIMIT before any work is issued;
+ *   - the first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ *     that device current; make that first call before any stream capture;
+ *   - every call, on any handle and stream of a device, shares the one array: calls whose work
+ *     overlaps on the GPU race and give wrong results, so serialize them (one stream, or events);
+ *   - the array keeps the previous call's contents; the solve overwrites every element it reads,
+ *     so no clearing is needed;
+ *   - sym_profile does not time this entry point.
+ * Other arguments, errors and results as sym_solve_multi (DEVICE pointers). */
+#define SYM_NOALLOC_MAX_WORK 1048576
+int sym_solve_multi_noalloc(sym_handle h, int32_t nrhs, const double *B, int64_t ldb, double *X,
+                            int64_t ldx);
+
 /* As sym_solve_multi with host pointers (copied inside). */
 int sym_solve_host(sym_handle h, int32_t nrhs, const double *B, int64_t ldb, double *X,
                    int64_t ldx);

@@ -21,6 +21,7 @@ __all__ = [
     "sym_factor_host", "sym_solve", "sym_solve_multi", "sym_solve_host", "sym_info",
     "sym_last_error_column", "sym_get_factor_host", "sym_export", "sym_free", "load", "Solver",
     "EXPORTS", "sym_profile", "sym_profile_read", "sym_fma_peak", "sym_solve_host_ptr", "KINDS",
+    "sym_solve_multi_noalloc",
 ]
 
 SYM_OK = 0
@@ -105,6 +106,7 @@ def load():
             "sym_profile_read": ([P, i32, ct.POINTER(ct.c_double), ct.POINTER(i64),
                                   ct.POINTER(ct.c_double)], I),
             "sym_fma_peak": ([i32, ct.POINTER(ct.c_double)], I),
+            "sym_solve_multi_noalloc": ([P, i32, P, i64, P, i64], I),
         }
         for name, (args, res) in sigs.items():
             f = getattr(lib, name)
@@ -189,6 +191,14 @@ def sym_solve(h, b, x):
 
 def sym_solve_multi(h, nrhs, B, ldb, X, ldx):
     return _check(load().sym_solve_multi(h, int(nrhs), _dptr(B), int(ldb), _dptr(X), int(ldx)))
+
+
+SYM_NOALLOC_MAX_WORK = 1048576
+
+
+def sym_solve_multi_noalloc(h, nrhs, B, ldb, X, ldx):
+    """sym_solve_multi without any allocation (work block in the library's fixed device array)."""
+    return _check(load().sym_solve_multi_noalloc(h, int(nrhs), _dptr(B), int(ldb), _dptr(X), int(ldx)))
 
 
 def sym_solve_host(h, B):

@@ -325,6 +325,30 @@ int sym_solve_multi(sym_handle h, int32_t nrhs, const double *B, int64_t ldb, do
   return SYM_OK;
 }
 
+}  // extern "C"
+
+namespace sym {
+// Solve with a work array supplied by the caller (at least n * nrhs doubles); performs no
+// allocation and records no profile events.
+int solve_with_work(sym_handle h, int32_t nrhs, const double *B, int64_t ldb, double *X, int64_t ldx,
+                    double *work) {
+  int rc = check_device(h);
+  if (rc) return rc;
+  if (!h->factored) return fail(SYM_ERR_STATE, "no successful factorization to solve with");
+  const int64_t n = h->plan.n;
+  if (nrhs < 0 || ldb < n || ldx < n || (nrhs > 0 && n > 0 && (!B || !X)))
+    return fail(SYM_ERR_INVALID, "bad solve arguments");
+  CUDA_TRY(sym::run_solve<double>(h->dp, h->plan.fwd_launches, h->plan.bwd_launches, h->d_Lx, nrhs, B, ldb,
+                                  X, ldx, work, h->stream),
+           "solve kernels");
+  return SYM_OK;
+}
+int set_error(int code, const char *msg) { return fail(code, msg); }
+int64_t plan_n(sym_handle h) { return h ? h->plan.n : 0; }
+}  // namespace sym
+
+extern "C" {
+
 int sym_solve(sym_handle h, const double *b, double *x) {
   return sym_solve_multi(h, 1, b, h ? h->plan.n : 0, x, h ? h->plan.n : 0);
 }
