@@ -39,13 +39,21 @@ extern "C" {
 #define SYM_ERR_STATE -5   /* call out of order (solve before factor, host-only handle) */
 #define SYM_ERR_TIMEOUT -6 /* a bounded device wait ran out */
 #define SYM_ERR_LIMIT -7   /* a size exceeds a documented limit */
+#define SYM_ERR_NO_CONVERGENCE -8 /* refinement stopped at its iteration limit above tolerance */
 
 /* Orderings for sym_analyze_perm. */
 #define SYM_ORDER_NATURAL 0 /* identity (then etree postorder) */
 #define SYM_ORDER_GIVEN 1   /* the caller's perm (then etree postorder) */
 
+/* Precision of the factor (sym_options.precision). */
+#define SYM_PREC_FP64 0  /* FP64 factor and FP64 solves (the plain path) */
+#define SYM_PREC_MIXED 1 /* FP32 factor (FP64 diagonal-tile pivots); solves refined in FP64 by
+                            conjugate gradients preconditioned with the FP32 factor, to a normwise
+                            backward error <= the refinement tolerance (default 1e-12) */
+
 /* Option flags. */
 #define SYM_FLAG_HOST_ONLY 1u /* run the inspector only; no device memory, no factor/solve */
+#define SYM_FLAG_NO_GRAPHS 2u /* launch kernel by kernel instead of replaying CUDA graphs */
 
 typedef struct sym_handle_s *sym_handle;
 
@@ -62,7 +70,8 @@ typedef struct {
   int32_t nrelax[3];           /* default 4, 16, 48 */
   int32_t zrelax_permille[3];  /* default 800, 100, 50 */
   uint32_t flags;              /* SYM_FLAG_* */
-  int32_t reserved[8];
+  int32_t precision;           /* SYM_PREC_* (default SYM_PREC_FP64) */
+  int32_t reserved[7];
 } sym_options;
 
 /* Statistics of an analyzed pattern (sym_info). */
@@ -104,6 +113,11 @@ int sym_analyze_perm(int64_t n, const int64_t *Ap, const int32_t *Ai, const int3
 
 /* Use this CUDA stream (a cudaStream_t passed as void*) for all later work of the handle. */
 int sym_set_stream(sym_handle h, void *stream);
+
+/* Launching. sym_factor* and sym_solve_multi capture their launch sequence in a CUDA graph on
+ * first use (on a private stream) and replay it on the handle's stream while the device
+ * pointers and sizes stay the same (a change re-captures). SYM_FLAG_NO_GRAPHS, or profiling,
+ * launches kernel by kernel. */
 
 /* Numeric factorization (Sec. 3.2: supernodal left-looking Cholesky; VS-Block turns each
  * supernode into a dense POTRF of its diagonal block and TRSMs of the rows below, and VI-Prune
@@ -157,13 +171,25 @@ int sym_solve_multi_noalloc(sym_handle h, int32_t nrhs, const double *B, int64_t
 int sym_solve_host(sym_handle h, int32_t nrhs, const double *B, int64_t ldb, double *X,
                    int64_t ldx);
 
+/* Mixed precision only: stopping rule of the FP64 refinement of sym_solve* (normwise backward
+ * error <= tol for every right-hand side, at most max_iter conjugate-gradient iterations; each
+ * iteration is one FP64 product with A and one FP32 solve with the factor). Not an operation of
+ * the paper: its refinement counterpart is this library's mixed-precision addition. */
+int sym_set_refinement(sym_handle h, double tol, int32_t max_iter);
+
+/* Mixed precision only: iterations and final backward error of the last sym_solve* call.
+ * sym_solve* returns SYM_ERR_NO_CONVERGENCE (with X holding the last iterate) when the limit is
+ * reached above tolerance. */
+int sym_refinement_info(sym_handle h, int32_t *iterations, double *backward_error);
+
 /* Statistics of the analyzed pattern. */
 int sym_info(sym_handle h, sym_stats *s);
 
 /* First failing column (caller's numbering) of the last SYM_ERR_NOT_SPD, else -1. */
 int sym_last_error_column(sym_handle h, int64_t *col);
 
-/* Copy the factor to host memory in its supernodal panel layout (storage_l doubles). */
+/* Copy the factor to host memory in its supernodal panel layout (storage_l doubles; an FP32
+ * factor is widened to double). */
 int sym_get_factor_host(sym_handle h, double *Lx_host);
 
 /* Export an integer array of the symbolic plan (host copy) for checks against an independent

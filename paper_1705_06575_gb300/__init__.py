@@ -21,7 +21,7 @@ __all__ = [
     "sym_factor_host", "sym_solve", "sym_solve_multi", "sym_solve_host", "sym_info",
     "sym_last_error_column", "sym_get_factor_host", "sym_export", "sym_free", "load", "Solver",
     "EXPORTS", "sym_profile", "sym_profile_read", "sym_fma_peak", "sym_solve_host_ptr", "KINDS",
-    "sym_solve_multi_noalloc",
+    "sym_solve_multi_noalloc", "sym_set_refinement", "sym_refinement_info",
 ]
 
 SYM_OK = 0
@@ -32,9 +32,13 @@ SYM_ERR_OOM = -4
 SYM_ERR_STATE = -5
 SYM_ERR_TIMEOUT = -6
 SYM_ERR_LIMIT = -7
+SYM_ERR_NO_CONVERGENCE = -8
+SYM_PREC_FP64 = 0
+SYM_PREC_MIXED = 1
 SYM_ORDER_NATURAL = 0
 SYM_ORDER_GIVEN = 1
 SYM_FLAG_HOST_ONLY = 1
+SYM_FLAG_NO_GRAPHS = 2
 
 # name -> (code, numpy dtype)
 EXPORTS = {
@@ -56,7 +60,7 @@ class SymError(RuntimeError):
 class sym_options(ct.Structure):
     _fields_ = [("ordering", ct.c_int32), ("amalgamate", ct.c_int32), ("nrelax", ct.c_int32 * 3),
                 ("zrelax_permille", ct.c_int32 * 3), ("flags", ct.c_uint32),
-                ("reserved", ct.c_int32 * 8)]
+                ("precision", ct.c_int32), ("reserved", ct.c_int32 * 7)]
 
 
 class sym_stats(ct.Structure):
@@ -107,6 +111,8 @@ def load():
                                   ct.POINTER(ct.c_double)], I),
             "sym_fma_peak": ([i32, ct.POINTER(ct.c_double)], I),
             "sym_solve_multi_noalloc": ([P, i32, P, i64, P, i64], I),
+            "sym_set_refinement": ([P, ct.c_double, i32], I),
+            "sym_refinement_info": ([P, ct.POINTER(i32), ct.POINTER(ct.c_double)], I),
         }
         for name, (args, res) in sigs.items():
             f = getattr(lib, name)
@@ -239,6 +245,17 @@ def sym_fma_peak(precision=64):
     return g.value
 
 
+def sym_set_refinement(h, tol, max_iter):
+    return _check(load().sym_set_refinement(h, float(tol), int(max_iter)))
+
+
+def sym_refinement_info(h):
+    """(iterations, backward error) of the last mixed-precision solve."""
+    it, be = ct.c_int32(), ct.c_double()
+    _check(load().sym_refinement_info(h, ct.byref(it), ct.byref(be)))
+    return it.value, be.value
+
+
 def sym_info(h):
     s = sym_stats()
     _check(load().sym_info(h, ct.byref(s)))
@@ -276,9 +293,11 @@ def sym_free(h):
 class Solver:
     """Owning wrapper of one handle: analyze on construction, free on close."""
 
-    def __init__(self, n, Ap, Ai, perm=None, opt=None, host_only=False):
+    def __init__(self, n, Ap, Ai, perm=None, opt=None, host_only=False, precision=None):
         if opt is None:
             opt = sym_options_default()
+        if precision is not None:
+            opt.precision = SYM_PREC_MIXED if precision in ("mixed", SYM_PREC_MIXED) else SYM_PREC_FP64
         if perm is not None:
             opt.ordering = SYM_ORDER_GIVEN
         if host_only:
@@ -329,6 +348,12 @@ class Solver:
 
     def profile_read(self, kind):
         return sym_profile_read(self.h, KINDS[kind] if isinstance(kind, str) else kind)
+
+    def set_refinement(self, tol, max_iter):
+        sym_set_refinement(self.h, tol, max_iter)
+
+    def refinement_info(self):
+        return sym_refinement_info(self.h)
 
     def error_column(self):
         return sym_last_error_column(self.h)

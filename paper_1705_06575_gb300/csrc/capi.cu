@@ -9,10 +9,12 @@
 
 #include "kernels.h"
 #include "plan.h"
+#include "refine.h"
 #include "sym.h"
 
 struct sym_handle_s {
   sym::Plan plan;
+  int precision = SYM_PREC_FP64;
   bool host_only = true;
   int device = -1;
   cudaStream_t stream = nullptr;
@@ -30,6 +32,28 @@ struct sym_handle_s {
   int64_t device_bytes = 0;
   bool factored = false;
   int64_t err_col = -1;
+  // CUDA graphs of the launch sequences (replayed while their arguments stay the same)
+  bool use_graphs = true;
+  bool prepared = false;
+  cudaStream_t capture_stream = nullptr;
+  cudaGraphExec_t fgraph = nullptr;
+  const double *fgraph_ax = nullptr;
+  cudaGraphExec_t sgraph = nullptr;
+  const void *sgraph_key[3] = {nullptr, nullptr, nullptr};
+  int64_t sgraph_ikey[3] = {0, 0, 0};
+  // mixed precision: FP32 panels, a copy of A's values, CSR of P A P^T, refinement work
+  float *d_Lf = nullptr;
+  double *d_Axc = nullptr;
+  double *d_anorm = nullptr;
+  double *d_anorm_work = nullptr;
+  void *d_csr_p = nullptr, *d_csr_i = nullptr, *d_csr_map = nullptr;
+  double *d_rwork = nullptr;
+  int64_t rwork_cap = 0;
+  double *h_eta = nullptr;  // pinned, 256 doubles
+  double refine_tol = 1e-12;
+  int32_t refine_max_iter = 100;
+  int32_t last_iterations = 0;
+  double last_berr = 0.0;
   // per-kernel profiling
   bool profiling = false;
   std::vector<cudaEvent_t> events;
@@ -94,12 +118,68 @@ int collect_trace(sym_handle_s *h, const sym::LaunchTrace &tr, double flop_scale
 }
 
 void release_device(sym_handle_s *h) {
+  {
+    void *mp[] = {h->d_Lf, h->d_Axc, h->d_anorm, h->d_anorm_work, h->d_csr_p, h->d_csr_i, h->d_csr_map, h->d_rwork};
+    for (void *p : mp)
+      if (p) cudaFree(p);
+    if (h->h_eta) cudaFreeHost(h->h_eta);
+  }
   for (cudaEvent_t e : h->events) cudaEventDestroy(e);
+  if (h->fgraph) cudaGraphExecDestroy(h->fgraph);
+  if (h->sgraph) cudaGraphExecDestroy(h->sgraph);
+  if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
   void *ptrs[] = {h->d_sn, h->d_rows, h->d_rel, h->d_amap, h->d_updt, h->d_upde, h->d_tasks,
                   h->d_perm, h->d_Lx, h->d_status, h->d_y, h->d_stage};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (h->h_status) cudaFreeHost(h->h_status);
+}
+
+int ensure_rwork(sym_handle_s *h, int64_t count) {
+  if (count <= h->rwork_cap) return SYM_OK;
+  if (h->d_rwork) cudaFree(h->d_rwork);
+  h->d_rwork = nullptr;
+  h->rwork_cap = 0;
+  CUDA_TRY(cudaMalloc(&h->d_rwork, sizeof(double) * (count > 0 ? count : 1)), "cudaMalloc(refinement work)");
+  h->rwork_cap = count;
+  return SYM_OK;
+}
+
+sym::RefineCtx refine_ctx(sym_handle_s *h) {
+  sym::RefineCtx r;
+  r.dp = &h->dp;
+  r.fwd = &h->plan.fwd_launches;
+  r.bwd = &h->plan.bwd_launches;
+  r.Lf = h->d_Lf;
+  r.cp = (const int64_t *)h->d_csr_p;
+  r.ci = (const int32_t *)h->d_csr_i;
+  r.cmap = (const int64_t *)h->d_csr_map;
+  r.Ax = h->d_Axc;
+  r.anorm = h->d_anorm;
+  r.anorm_work = h->d_anorm_work;
+  r.work = h->d_rwork;
+  r.n = h->plan.n;
+  return r;
+}
+
+// Everything one factorization enqueues after the status reset (the part a graph captures).
+cudaError_t enqueue_factor(sym_handle_s *h, const double *Ax, cudaStream_t st, sym::LaunchTrace *tr) {
+  if (h->precision == SYM_PREC_MIXED) {
+    if (h->plan.nnz_a > 0) {
+      cudaError_t e = cudaMemcpyAsync(h->d_Axc, Ax, sizeof(double) * h->plan.nnz_a, cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = sym::run_factor<float>(h->dp, h->plan.factor_launches, Ax, h->d_Lf, h->d_status, st, tr);
+    if (e != cudaSuccess) return e;
+    return sym::refine_anorm(refine_ctx(h), st);
+  }
+  return sym::run_factor<double>(h->dp, h->plan.factor_launches, Ax, h->d_Lx, h->d_status, st, tr);
+}
+
+int ensure_capture_stream(sym_handle_s *h) {
+  if (h->capture_stream) return SYM_OK;
+  CUDA_TRY(cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+  return SYM_OK;
 }
 
 int ensure_y(sym_handle_s *h, int64_t count) {
@@ -177,6 +257,8 @@ int sym_analyze_perm(int64_t n, const int64_t *Ap, const int32_t *Ai, const int3
   else sym_options_default(&opt);
   if (opt.ordering != SYM_ORDER_NATURAL && opt.ordering != SYM_ORDER_GIVEN)
     return fail(SYM_ERR_INVALID, "unknown ordering");
+  if (opt.precision != SYM_PREC_FP64 && opt.precision != SYM_PREC_MIXED)
+    return fail(SYM_ERR_INVALID, "unknown precision");
   for (int i = 0; i < 3; ++i)
     if (opt.nrelax[i] < 0 || opt.zrelax_permille[i] < 0 || opt.zrelax_permille[i] > 1000)
       return fail(SYM_ERR_INVALID, "bad amalgamation parameters");
@@ -189,6 +271,8 @@ int sym_analyze_perm(int64_t n, const int64_t *Ap, const int32_t *Ai, const int3
       delete h;
       return fail(rc, err);
     }
+    h->precision = opt.precision;
+    if (h->precision == SYM_PREC_MIXED) sym::build_permuted_csr(Ap, Ai, h->plan);
   } catch (const std::bad_alloc &) {
     delete h;
     return fail(SYM_ERR_OOM, "host allocation during analysis");
@@ -197,6 +281,7 @@ int sym_analyze_perm(int64_t n, const int64_t *Ap, const int32_t *Ai, const int3
     return fail(SYM_ERR_INVALID, e.what());
   }
   h->host_only = (opt.flags & SYM_FLAG_HOST_ONLY) != 0;
+  h->use_graphs = (opt.flags & SYM_FLAG_NO_GRAPHS) == 0;
   if (!h->host_only) {
     int rc = SYM_OK;
     auto &P = h->plan;
@@ -211,10 +296,36 @@ int sym_analyze_perm(int64_t n, const int64_t *Ap, const int32_t *Ai, const int3
     if (!rc) rc = upload(P.upd_entries, &h->d_upde, bytes);
     if (!rc) rc = upload(P.tasks, &h->d_tasks, bytes);
     if (!rc) rc = upload(P.perm, &h->d_perm, bytes);
-    if (!rc) {
+    if (!rc && h->precision == SYM_PREC_FP64) {
       e = cudaMalloc(&h->d_Lx, sizeof(double) * (P.storage() > 0 ? P.storage() : 1));
       if (e != cudaSuccess) rc = cuda_fail(e, "cudaMalloc(L)");
       else bytes += sizeof(double) * P.storage();
+    }
+    if (!rc && h->precision == SYM_PREC_MIXED) {
+      e = cudaMalloc(&h->d_Lf, sizeof(float) * (P.storage() > 0 ? P.storage() : 1));
+      if (e != cudaSuccess) rc = cuda_fail(e, "cudaMalloc(L)");
+      else bytes += sizeof(float) * P.storage();
+      if (!rc) rc = upload(P.csr_p, &h->d_csr_p, bytes);
+      if (!rc) rc = upload(P.csr_i, &h->d_csr_i, bytes);
+      if (!rc) rc = upload(P.csr_map, &h->d_csr_map, bytes);
+      if (!rc) {
+        e = cudaMalloc(&h->d_Axc, sizeof(double) * (P.nnz_a > 0 ? P.nnz_a : 1));
+        if (e != cudaSuccess) rc = cuda_fail(e, "cudaMalloc(A copy)");
+        else bytes += sizeof(double) * P.nnz_a;
+      }
+      if (!rc) {
+        e = cudaMalloc(&h->d_anorm, sizeof(double));
+        if (e != cudaSuccess) rc = cuda_fail(e, "cudaMalloc(norm)");
+      }
+      if (!rc) {
+        e = cudaMalloc(&h->d_anorm_work, sizeof(double) * (P.n + 512));
+        if (e != cudaSuccess) rc = cuda_fail(e, "cudaMalloc(norm work)");
+      }
+      if (!rc) {
+        e = cudaMallocHost(&h->h_eta, 256 * sizeof(double));
+        if (e != cudaSuccess) rc = cuda_fail(e, "cudaMallocHost(refinement)");
+      }
+      if (!rc) rc = ensure_rwork(h, sym::refine_work_doubles(P.n, 1));
     }
     if (!rc) {
       e = cudaMalloc(&h->d_status, sizeof(long long));
@@ -260,6 +371,11 @@ int sym_factor_async(sym_handle h, const double *Ax) {
   h->h_status[0] = LLONG_MAX;
   CUDA_TRY(cudaMemcpyAsync(h->d_status, &h->h_status[0], sizeof(long long), cudaMemcpyHostToDevice, h->stream),
            "status reset");
+  if (!h->prepared) {
+    CUDA_TRY(h->precision == SYM_PREC_MIXED ? sym::prepare_factor<float>() : sym::prepare_factor<double>(),
+             "factor set-up");
+    h->prepared = true;
+  }
   sym::LaunchTrace tr, *trp = nullptr;
   if (h->profiling) {
     rc = ensure_events(h, h->plan.factor_launches.size() + 3);
@@ -267,8 +383,31 @@ int sym_factor_async(sym_handle h, const double *Ax) {
     tr.events = &h->events;
     trp = &tr;
   }
-  CUDA_TRY(sym::run_factor<double>(h->dp, h->plan.factor_launches, Ax, h->d_Lx, h->d_status, h->stream, trp),
-           "factor kernels");
+  if (!trp && h->use_graphs) {
+    // Replay the captured launch sequence; capture it again when Ax moved.
+    if (!h->fgraph || h->fgraph_ax != Ax) {
+      rc = ensure_capture_stream(h);
+      if (rc) return rc;
+      if (h->fgraph) cudaGraphExecDestroy(h->fgraph);
+      h->fgraph = nullptr;
+      cudaGraph_t g = nullptr;
+      CUDA_TRY(cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal), "capture factor");
+      cudaError_t e = enqueue_factor(h, Ax, h->capture_stream, nullptr);
+      cudaError_t e2 = cudaStreamEndCapture(h->capture_stream, &g);
+      if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return cuda_fail(e != cudaSuccess ? e : e2, "capture factor");
+      }
+      e = cudaGraphInstantiate(&h->fgraph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return cuda_fail(e, "instantiate factor graph");
+      h->fgraph_ax = Ax;
+    }
+    CUDA_TRY(cudaGraphLaunch(h->fgraph, h->stream), "factor graph");
+  } else {
+    CUDA_TRY(enqueue_factor(h, Ax, h->stream, trp), "factor kernels");
+  }
   if (trp) {
     rc = collect_trace(h, tr, 1.0, false);
     if (rc) return rc;
@@ -308,6 +447,28 @@ int sym_solve_multi(sym_handle h, int32_t nrhs, const double *B, int64_t ldb, do
   const int64_t n = h->plan.n;
   if (nrhs < 0 || ldb < n || ldx < n || (nrhs > 0 && n > 0 && (!B || !X)))
     return fail(SYM_ERR_INVALID, "bad solve arguments");
+  if (h->precision == SYM_PREC_MIXED) {
+    // FP64 conjugate gradients preconditioned with the FP32 factor, up to 64 columns at a time.
+    int32_t iters = 0;
+    double berr = 0.0;
+    bool conv = true;
+    for (int32_t c0 = 0; c0 < nrhs; c0 += 64) {
+      const int32_t nc = nrhs - c0 < 64 ? nrhs - c0 : 64;
+      rc = ensure_rwork(h, sym::refine_work_doubles(n, nc));
+      if (rc) return rc;
+      sym::RefineResult res;
+      if (sym::refine_solve(refine_ctx(h), nc, B + (int64_t)c0 * ldb, ldb, X + (int64_t)c0 * ldx, ldx,
+                            h->refine_tol, h->refine_max_iter, h->h_eta, &res, h->stream) != 0)
+        return cuda_fail(cudaGetLastError(), "refinement");
+      iters = res.iterations > iters ? res.iterations : iters;
+      berr = res.backward_error > berr ? res.backward_error : berr;
+      conv = conv && res.converged;
+    }
+    h->last_iterations = iters;
+    h->last_berr = berr;
+    if (!conv) return fail(SYM_ERR_NO_CONVERGENCE, "refinement reached its iteration limit above tolerance");
+    return SYM_OK;
+  }
   rc = ensure_y(h, n * (int64_t)nrhs);
   if (rc) return rc;
   sym::LaunchTrace tr, *trp = nullptr;
@@ -317,6 +478,38 @@ int sym_solve_multi(sym_handle h, int32_t nrhs, const double *B, int64_t ldb, do
     if (rc) return rc;
     tr.events = &h->events;
     trp = &tr;
+  }
+  if (!trp && h->use_graphs && n > 0 && nrhs > 0) {
+    const bool same = h->sgraph && h->sgraph_key[0] == B && h->sgraph_key[1] == X &&
+                      h->sgraph_key[2] == h->d_y && h->sgraph_ikey[0] == nrhs && h->sgraph_ikey[1] == ldb &&
+                      h->sgraph_ikey[2] == ldx;
+    if (!same) {
+      rc = ensure_capture_stream(h);
+      if (rc) return rc;
+      if (h->sgraph) cudaGraphExecDestroy(h->sgraph);
+      h->sgraph = nullptr;
+      cudaGraph_t g = nullptr;
+      CUDA_TRY(cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal), "capture solve");
+      cudaError_t e = sym::run_solve<double>(h->dp, h->plan.fwd_launches, h->plan.bwd_launches, h->d_Lx, nrhs, B,
+                                             ldb, X, ldx, h->d_y, h->capture_stream, nullptr);
+      cudaError_t e2 = cudaStreamEndCapture(h->capture_stream, &g);
+      if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return cuda_fail(e != cudaSuccess ? e : e2, "capture solve");
+      }
+      e = cudaGraphInstantiate(&h->sgraph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return cuda_fail(e, "instantiate solve graph");
+      h->sgraph_key[0] = B;
+      h->sgraph_key[1] = X;
+      h->sgraph_key[2] = h->d_y;
+      h->sgraph_ikey[0] = nrhs;
+      h->sgraph_ikey[1] = ldb;
+      h->sgraph_ikey[2] = ldx;
+    }
+    CUDA_TRY(cudaGraphLaunch(h->sgraph, h->stream), "solve graph");
+    return SYM_OK;
   }
   CUDA_TRY(sym::run_solve<double>(h->dp, h->plan.fwd_launches, h->plan.bwd_launches, h->d_Lx, nrhs, B, ldb,
                                   X, ldx, h->d_y, h->stream, trp),
@@ -335,6 +528,7 @@ int solve_with_work(sym_handle h, int32_t nrhs, const double *B, int64_t ldb, do
   int rc = check_device(h);
   if (rc) return rc;
   if (!h->factored) return fail(SYM_ERR_STATE, "no successful factorization to solve with");
+  if (h->precision != SYM_PREC_FP64) return fail(SYM_ERR_STATE, "this entry point needs an FP64 factor");
   const int64_t n = h->plan.n;
   if (nrhs < 0 || ldb < n || ldx < n || (nrhs > 0 && n > 0 && (!B || !X)))
     return fail(SYM_ERR_INVALID, "bad solve arguments");
@@ -406,6 +600,12 @@ int sym_get_factor_host(sym_handle h, double *Lx_host) {
   if (rc) return rc;
   if (!Lx_host) return fail(SYM_ERR_INVALID, "null output");
   CUDA_TRY(cudaStreamSynchronize(h->stream), "sync");
+  if (h->precision == SYM_PREC_MIXED) {
+    std::vector<float> tmp(h->plan.storage());
+    CUDA_TRY(cudaMemcpy(tmp.data(), h->d_Lf, sizeof(float) * tmp.size(), cudaMemcpyDeviceToHost), "copy L");
+    for (size_t i = 0; i < tmp.size(); ++i) Lx_host[i] = tmp[i];
+    return SYM_OK;
+  }
   CUDA_TRY(cudaMemcpy(Lx_host, h->d_Lx, sizeof(double) * h->plan.storage(), cudaMemcpyDeviceToHost), "copy L");
   return SYM_OK;
 }
@@ -449,6 +649,21 @@ int64_t sym_export(sym_handle h, int32_t what, void *out) {
   return count;
 }
 
+int sym_set_refinement(sym_handle h, double tol, int32_t max_iter) {
+  if (!h) return fail(SYM_ERR_INVALID, "null handle");
+  if (!(tol > 0.0) || max_iter < 1) return fail(SYM_ERR_INVALID, "bad refinement parameters");
+  h->refine_tol = tol;
+  h->refine_max_iter = max_iter;
+  return SYM_OK;
+}
+
+int sym_refinement_info(sym_handle h, int32_t *iterations, double *backward_error) {
+  if (!h) return fail(SYM_ERR_INVALID, "null handle");
+  if (iterations) *iterations = h->last_iterations;
+  if (backward_error) *backward_error = h->last_berr;
+  return SYM_OK;
+}
+
 int sym_profile(sym_handle h, int32_t mode) {
   if (!h) return fail(SYM_ERR_INVALID, "null handle");
   if (mode == SYM_PROFILE_ON) h->profiling = true;
@@ -484,6 +699,7 @@ const char *sym_error_string(int code) {
     case SYM_ERR_STATE: return "call out of order";
     case SYM_ERR_TIMEOUT: return "device wait timed out";
     case SYM_ERR_LIMIT: return "size limit exceeded";
+    case SYM_ERR_NO_CONVERGENCE: return "refinement did not converge";
     default: return "unknown error";
   }
 }

@@ -194,44 +194,56 @@ __global__ void __launch_bounds__(THREADS) k_potrf(const SNode *__restrict__ sn,
                                                    const Int4 *__restrict__ tasks,
                                                    T *__restrict__ Lx, long long *status,
                                                    int64_t toff) {
-  __shared__ T a[NB][NB + 1];  // [col][row]
-  __shared__ T pinv;
+  // The diagonal tile is factored in FP64 whatever the storage type T (for an FP32 factor the
+  // pivots and this tile stay accurate; the result is rounded to T once).
+  __shared__ double a[NB][NB + 1];                 // [col][row]
+  __shared__ unsigned short tri[NB * (NB - 1) / 2];  // packed lower triangle: (i << 8) | j, i >= j
+  __shared__ double pinv;
   const Int4 t = tasks[toff + blockIdx.x];
   const SNode sj = sn[t.a];
   const int s = t.b;
   const int ts = min(NB, sj.ncols - s * NB);
   T *D = Lx + sj.lx + (int64_t)(s * NB) * sj.nrows + s * NB;
   const int tid = threadIdx.x;
-  const int r = tid & (NB - 1), g = tid >> 6;  // thread owns row r, columns g, g+4, ...
   for (int idx = tid; idx < NB * NB; idx += THREADS) {
     int rr = idx % NB, c = idx / NB;
-    a[c][rr] = (rr < ts && c < ts && rr >= c) ? D[(int64_t)c * sj.nrows + rr] : T(0);
+    a[c][rr] = (rr < ts && c < ts && rr >= c) ? (double)D[(int64_t)c * sj.nrows + rr] : 0.0;
+  }
+  // Row-major packed index of the lower triangle: idx = i (i + 1) / 2 + j. The first
+  // m (m + 1) / 2 entries are the triangle of order m, whatever m is.
+  for (int idx = tid; idx < NB * (NB - 1) / 2; idx += THREADS) {
+    int i = (int)((sqrtf(8.0f * idx + 1.0f) - 1.0f) * 0.5f);
+    while ((i + 1) * (i + 2) / 2 <= idx) ++i;
+    while (i * (i + 1) / 2 > idx) --i;
+    tri[idx] = (unsigned short)((i << 8) | (idx - i * (i + 1) / 2));
   }
   __syncthreads();
   for (int c = 0; c < ts; ++c) {
     if (tid == 0) {
-      T d = a[c][c];
-      if (!(d > T(0))) {
+      double d = a[c][c];
+      if (!(d > 0.0)) {
         atomicMin(status, (long long)(sj.first + s * NB + c));
-        d = T(1);
+        d = 1.0;
       }
-      const T x = rsqrt_newton(d);
+      const double x = rsqrt_newton(d);
       a[c][c] = d * x;  // sqrt(d)
       pinv = x;
     }
     __syncthreads();
-    const T inv = pinv;
-    if (r > c && r < ts) {
-      const T lrc = a[c][r] * inv;  // L(r, c); column c is rescaled after the barrier
-      for (int cc = c + 1 + g; cc <= r; cc += 4) a[cc][r] = fma(-lrc, a[c][cc] * inv, a[cc][r]);
+    if (tid > c && tid < ts) a[c][tid] *= pinv;  // column c of L
+    __syncthreads();
+    const int m = ts - c - 1;  // trailing lower triangle of order m, rows/cols c+1..ts-1
+    const int tot = m * (m + 1) / 2;
+    for (int idx = tid; idx < tot; idx += THREADS) {
+      const int ij = tri[idx];
+      const int rr = c + 1 + (ij >> 8), cc = c + 1 + (ij & 0xff);
+      a[cc][rr] = fma(-a[c][rr], a[c][cc], a[cc][rr]);
     }
     __syncthreads();
-    if (g == 0 && r > c && r < ts) a[c][r] *= inv;
   }
-  __syncthreads();
   for (int idx = tid; idx < NB * NB; idx += THREADS) {
     int rr = idx % NB, c = idx / NB;
-    if (rr < ts && c < ts) D[(int64_t)c * sj.nrows + rr] = rr >= c ? a[c][rr] : T(0);
+    if (rr < ts && c < ts) D[(int64_t)c * sj.nrows + rr] = rr >= c ? (T)a[c][rr] : T(0);
   }
 }
 
@@ -326,77 +338,97 @@ __global__ void __launch_bounds__(THREADS) k_gemm(const SNode *__restrict__ sn,
 }
 
 // ---------------------------------------------------------------------------------------------
-// Solve kernels. y is the permuted right-hand side block, n x nrhs, leading dimension n.
+// Solve kernels. y is the permuted right-hand side block, n x nrhs, leading dimension n, of the
+// vector type V (double for the FP64 path; float for the preconditioner of the mixed path). The
+// factor is read in its storage type T and the arithmetic is done in V.
+template <typename V>
 __global__ void k_perm_in(const int32_t *__restrict__ perm, const double *__restrict__ B, int64_t ldb,
-                          double *__restrict__ y, int64_t n, int nrhs) {
+                          V *__restrict__ y, int64_t n, int nrhs) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (; i < n * nrhs; i += stride) {
     int64_t k = i % n, c = i / n;
-    y[i] = B[c * ldb + perm[k]];
+    y[i] = (V)B[c * ldb + perm[k]];
   }
 }
-__global__ void k_perm_out(const int32_t *__restrict__ perm, const double *__restrict__ y,
+template <typename V>
+__global__ void k_perm_out(const int32_t *__restrict__ perm, const V *__restrict__ y,
                            double *__restrict__ X, int64_t ldx, int64_t n, int nrhs) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (; i < n * nrhs; i += stride) {
     int64_t k = i % n, c = i / n;
-    X[c * ldx + perm[k]] = y[i];
+    X[c * ldx + perm[k]] = (double)y[i];
   }
 }
 
 constexpr int MAXRHS = 8;  // right-hand sides handled per pass of the solve kernels
+constexpr int BG = SOLVE_BG;  // columns per backward-gather CTA
 
 // Forward gather: y(cols of tile bj of J) -= sum over descendant entries of L_K(rows) y_K.
-// Warps take the entry's rows in turn; lanes split the inner dimension.
-template <typename T>
+// Per entry the n rows of K's panel are read column by column (coalesced): thread t takes row
+// t % nb and every groups-th column of K, partial sums are combined in shared memory.
+template <typename T, typename V>
 __global__ void __launch_bounds__(THREADS) k_fgather(const SNode *__restrict__ sn,
                                                      const Int4 *__restrict__ tasks,
                                                      const UpdTask *__restrict__ utasks,
                                                      const UpdEntry *__restrict__ ents,
                                                      const int32_t *__restrict__ rel,
-                                                     const T *__restrict__ Lx, double *__restrict__ y,
+                                                     const T *__restrict__ Lx, V *__restrict__ y,
                                                      int64_t n, int r0, int nr, int64_t toff) {
-  __shared__ double acc[MAXRHS][NB];
+  __shared__ V acc[MAXRHS][NB];
+  __shared__ V part[THREADS][MAXRHS + 1];
   const Int4 t = tasks[toff + blockIdx.x];
   const SNode sj = sn[t.a];
   const int bj = t.b;
   const UpdTask u = utasks[t.c];
   const int cb = bj * NB;
   const int tn = min(NB, sj.ncols - cb);
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int tid = threadIdx.x;
   for (int idx = tid; idx < MAXRHS * NB; idx += THREADS) {
     int r = idx % NB, c = idx / NB;
-    acc[c][r] = (r < tn && c < nr) ? y[(int64_t)(r0 + c) * n + sj.first + cb + r] : 0.0;
+    acc[c][r] = (r < tn && c < nr) ? y[(int64_t)(r0 + c) * n + sj.first + cb + r] : V(0);
   }
-  __syncthreads();
   for (int64_t e = u.e0; e < u.e1; ++e) {
     const UpdEntry E = ents[e];
     const SNode sk = sn[E.K];
-    for (int b = w; b < E.n; b += THREADS / 32) {
-      double s[MAXRHS];
+    int nb = 1;
+    while (nb < E.n) nb <<= 1;  // rows per group (power of two, <= NB)
+    const int groups = THREADS / nb;
+    const int b = tid & (nb - 1), kg = tid / nb;
+    V s[MAXRHS];
 #pragma unroll
-      for (int c = 0; c < MAXRHS; ++c) s[c] = 0.0;
+    for (int q = 0; q < MAXRHS; ++q) s[q] = V(0);
+    if (b < E.n) {
       const T *rowp = Lx + sk.lx + E.c_lo + b;
-      for (int k = lane; k < sk.ncols; k += 32) {
-        const double l = (double)rowp[(int64_t)k * sk.nrows];
+      const V *yk = y + (int64_t)r0 * n + sk.first;
+      constexpr int U = 8;  // loads in flight per thread
+      int k = kg;
+      for (; k + (U - 1) * groups < sk.ncols; k += U * groups) {
+        V l[U];
 #pragma unroll
-        for (int c = 0; c < MAXRHS; ++c)
-          if (c < nr) s[c] = fma(l, y[(int64_t)(r0 + c) * n + sk.first + k], s[c]);
-      }
+        for (int u = 0; u < U; ++u) l[u] = (V)rowp[(int64_t)(k + u * groups) * sk.nrows];
 #pragma unroll
-      for (int c = 0; c < MAXRHS; ++c) {
-        if (c < nr) {
-          double v = s[c];
-          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-          s[c] = v;
-        }
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+          for (int q = 0; q < MAXRHS; ++q)
+            if (q < nr) s[q] = fma(l[u], yk[(int64_t)q * n + k + u * groups], s[q]);
       }
-      if (lane == 0) {
-        const int pos = rel[E.relc + b] - cb;
-        for (int c = 0; c < nr; ++c) acc[c][pos] -= s[c];
+      for (; k < sk.ncols; k += groups) {
+        const V l = (V)rowp[(int64_t)k * sk.nrows];
+#pragma unroll
+        for (int q = 0; q < MAXRHS; ++q)
+          if (q < nr) s[q] = fma(l, yk[(int64_t)q * n + k], s[q]);
       }
+    }
+#pragma unroll
+    for (int q = 0; q < MAXRHS; ++q) part[tid][q] = s[q];
+    __syncthreads();
+    for (int idx = tid; idx < E.n * nr; idx += THREADS) {
+      const int bb = idx % E.n, q = idx / E.n;
+      V v = V(0);
+      for (int g = 0; g < groups; ++g) v += part[g * nb + bb][q];
+      acc[q][rel[E.relc + bb] - cb] -= v;
     }
     __syncthreads();
   }
@@ -407,14 +439,14 @@ __global__ void __launch_bounds__(THREADS) k_fgather(const SNode *__restrict__ s
 }
 
 // Diagonal tile solve, forward (L_ss y = y) or backward (L_ss^T z = z), one CTA per tile.
-template <typename T, bool TRANS>
+template <typename T, typename V, bool TRANS>
 __global__ void __launch_bounds__(THREADS) k_diag_solve(const SNode *__restrict__ sn,
                                                         const Int4 *__restrict__ tasks,
-                                                        const T *__restrict__ Lx, double *__restrict__ y,
+                                                        const T *__restrict__ Lx, V *__restrict__ y,
                                                         int64_t n, int r0, int nr, int64_t toff) {
-  __shared__ double Ls[NB][NB + 1];  // [col][row]
-  __shared__ double v[MAXRHS][NB];
-  __shared__ double dinv[NB];
+  __shared__ V Ls[NB][NB + 1];  // [col][row]
+  __shared__ V v[MAXRHS][NB];
+  __shared__ V dinv[NB];
   const Int4 t = tasks[toff + blockIdx.x];
   const SNode sj = sn[t.a];
   const int s = t.b;
@@ -424,20 +456,20 @@ __global__ void __launch_bounds__(THREADS) k_diag_solve(const SNode *__restrict_
   const int tid = threadIdx.x;
   for (int idx = tid; idx < NB * NB; idx += THREADS) {
     int r = idx % NB, c = idx / NB;
-    Ls[c][r] = (r < ts && c < ts && r >= c) ? (double)D[(int64_t)c * sj.nrows + r] : 0.0;
+    Ls[c][r] = (r < ts && c < ts && r >= c) ? (V)D[(int64_t)c * sj.nrows + r] : V(0);
   }
   for (int idx = tid; idx < MAXRHS * NB; idx += THREADS) {
     int r = idx % NB, c = idx / NB;
-    v[c][r] = (r < ts && c < nr) ? y[(int64_t)(r0 + c) * n + g0 + r] : 0.0;
+    v[c][r] = (r < ts && c < nr) ? y[(int64_t)(r0 + c) * n + g0 + r] : V(0);
   }
   __syncthreads();
-  if (tid < ts) dinv[tid] = 1.0 / Ls[tid][tid];
+  if (tid < ts) dinv[tid] = V(1) / Ls[tid][tid];
   __syncthreads();
   const int r = tid & (NB - 1), qg = tid >> 6;  // row r, right-hand sides qg, qg + 4
   if (!TRANS) {
     for (int c = 0; c < ts; ++c) {
       if (r > c && r < ts) {
-        const double l = Ls[c][r];
+        const V l = Ls[c][r];
         for (int q = qg; q < nr; q += 4) v[q][r] = fma(-l, v[q][c] * dinv[c], v[q][r]);
       }
       __syncthreads();
@@ -447,7 +479,7 @@ __global__ void __launch_bounds__(THREADS) k_diag_solve(const SNode *__restrict_
   } else {
     for (int c = ts - 1; c >= 0; --c) {
       if (r < c) {
-        const double l = Ls[r][c];  // L(c, r)
+        const V l = Ls[r][c];  // L(c, r)
         for (int q = qg; q < nr; q += 4) v[q][r] = fma(-l, v[q][c] * dinv[c], v[q][r]);
       }
       __syncthreads();
@@ -463,12 +495,12 @@ __global__ void __launch_bounds__(THREADS) k_diag_solve(const SNode *__restrict_
 }
 
 // Forward GEMV inside J: y(tile i) -= L(i, s) y(tile s), i > s within the diagonal block.
-template <typename T>
+template <typename T, typename V>
 __global__ void __launch_bounds__(THREADS) k_fgemv(const SNode *__restrict__ sn,
                                                    const Int4 *__restrict__ tasks,
-                                                   const T *__restrict__ Lx, double *__restrict__ y,
+                                                   const T *__restrict__ Lx, V *__restrict__ y,
                                                    int64_t n, int r0, int nr, int64_t toff) {
-  __shared__ double vs[MAXRHS][NB];
+  __shared__ V vs[MAXRHS][NB];
   const Int4 t = tasks[toff + blockIdx.x];
   const SNode sj = sn[t.a];
   const int i = t.b, s = t.c;
@@ -478,38 +510,55 @@ __global__ void __launch_bounds__(THREADS) k_fgemv(const SNode *__restrict__ sn,
   const int tid = threadIdx.x;
   for (int idx = tid; idx < MAXRHS * NB; idx += THREADS) {
     int r = idx % NB, c = idx / NB;
-    vs[c][r] = (r < ts && c < nr) ? y[(int64_t)(r0 + c) * n + sj.first + s * NB + r] : 0.0;
+    vs[c][r] = (r < ts && c < nr) ? y[(int64_t)(r0 + c) * n + sj.first + s * NB + r] : V(0);
   }
   __syncthreads();
   for (int idx = tid; idx < tm * nr; idx += THREADS) {
     int r = idx % tm, q = idx / tm;
-    double acc = 0.0;
-    for (int k = 0; k < ts; ++k) acc = fma((double)Lt[(int64_t)k * sj.nrows + r], vs[q][k], acc);
+    V acc = V(0);
+    for (int k = 0; k < ts; ++k) acc = fma((V)Lt[(int64_t)k * sj.nrows + r], vs[q][k], acc);
     y[(int64_t)(r0 + q) * n + sj.first + i * NB + r] -= acc;
   }
 }
 
-// Backward gather: z(cols of tile bj) -= L_J(rows below the diagonal block, tile)^T z(those rows).
-template <typename T>
+// Backward gather: z(cols c0..c0+BG) -= L_J(rows below the diagonal block, cols)^T z(those rows).
+// One CTA per BG-column slice; each warp takes BG / 8 columns, lanes stride over the rows
+// (coalesced), and a warp shuffle reduces each column.
+template <typename T, typename V>
 __global__ void __launch_bounds__(THREADS) k_bgather(const SNode *__restrict__ sn,
                                                      const int32_t *__restrict__ rows,
                                                      const Int4 *__restrict__ tasks,
-                                                     const T *__restrict__ Lx, double *__restrict__ y,
+                                                     const T *__restrict__ Lx, V *__restrict__ y,
                                                      int64_t n, int r0, int nr, int64_t toff) {
   const Int4 t = tasks[toff + blockIdx.x];
   const SNode sj = sn[t.a];
-  const int bj = t.b;
-  const int cb = bj * NB;
-  const int tn = min(NB, sj.ncols - cb);
+  const int c0 = t.b * BG;
+  const int tn = min(BG, sj.ncols - c0);
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int32_t *R = rows + sj.rowp;
   for (int c = w; c < tn; c += THREADS / 32) {
-    const T *col = Lx + sj.lx + (int64_t)(cb + c) * sj.nrows;
-    double s[MAXRHS];
+    const T *col = Lx + sj.lx + (int64_t)(c0 + c) * sj.nrows;
+    V s[MAXRHS];
 #pragma unroll
-    for (int q = 0; q < MAXRHS; ++q) s[q] = 0.0;
-    for (int r = sj.ncols + lane; r < sj.nrows; r += 32) {
-      const double l = (double)col[r];
+    for (int q = 0; q < MAXRHS; ++q) s[q] = V(0);
+    constexpr int U = 4;  // rows in flight per lane
+    int r = sj.ncols + lane;
+    for (; r + (U - 1) * 32 < sj.nrows; r += U * 32) {
+      V l[U];
+      int64_t g[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        l[u] = (V)col[r + u * 32];
+        g[u] = R[r + u * 32];
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int q = 0; q < MAXRHS; ++q)
+          if (q < nr) s[q] = fma(l[u], y[(int64_t)(r0 + q) * n + g[u]], s[q]);
+    }
+    for (; r < sj.nrows; r += 32) {
+      const V l = (V)col[r];
       const int64_t g = R[r];
 #pragma unroll
       for (int q = 0; q < MAXRHS; ++q)
@@ -518,21 +567,21 @@ __global__ void __launch_bounds__(THREADS) k_bgather(const SNode *__restrict__ s
 #pragma unroll
     for (int q = 0; q < MAXRHS; ++q) {
       if (q < nr) {
-        double v = s[q];
+        V v = s[q];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) y[(int64_t)(r0 + q) * n + sj.first + cb + c] -= v;
+        if (lane == 0) y[(int64_t)(r0 + q) * n + sj.first + c0 + c] -= v;
       }
     }
   }
 }
 
 // Backward GEMV inside J: z(tile i) -= L(s, i)^T z(tile s), i < s within the diagonal block.
-template <typename T>
+template <typename T, typename V>
 __global__ void __launch_bounds__(THREADS) k_bgemv(const SNode *__restrict__ sn,
                                                    const Int4 *__restrict__ tasks,
-                                                   const T *__restrict__ Lx, double *__restrict__ y,
+                                                   const T *__restrict__ Lx, V *__restrict__ y,
                                                    int64_t n, int r0, int nr, int64_t toff) {
-  __shared__ double vs[MAXRHS][NB];
+  __shared__ V vs[MAXRHS][NB];
   const Int4 t = tasks[toff + blockIdx.x];
   const SNode sj = sn[t.a];
   const int s = t.b, i = t.c;
@@ -542,14 +591,14 @@ __global__ void __launch_bounds__(THREADS) k_bgemv(const SNode *__restrict__ sn,
   const int tid = threadIdx.x;
   for (int idx = tid; idx < MAXRHS * NB; idx += THREADS) {
     int r = idx % NB, c = idx / NB;
-    vs[c][r] = (r < ts && c < nr) ? y[(int64_t)(r0 + c) * n + sj.first + s * NB + r] : 0.0;
+    vs[c][r] = (r < ts && c < nr) ? y[(int64_t)(r0 + c) * n + sj.first + s * NB + r] : V(0);
   }
   __syncthreads();
   for (int idx = tid; idx < ti * nr; idx += THREADS) {
     int c = idx % ti, q = idx / ti;
     const T *col = Lt + (int64_t)c * sj.nrows;
-    double acc = 0.0;
-    for (int k = 0; k < ts; ++k) acc = fma((double)col[k], vs[q][k], acc);
+    V acc = V(0);
+    for (int k = 0; k < ts; ++k) acc = fma((V)col[k], vs[q][k], acc);
     y[(int64_t)(r0 + q) * n + sj.first + i * NB + c] -= acc;
   }
 }
@@ -572,14 +621,13 @@ inline void trace_mark(LaunchTrace *tr, int32_t kind, cudaStream_t st) {
 }
 
 template <typename T>
+cudaError_t prepare_factor() {
+  return cudaFuncSetAttribute(k_trsm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem<T>());
+}
+
+template <typename T>
 cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, const double *Ax,
                        T *Lx, long long *status, cudaStream_t st, LaunchTrace *trace) {
-  static thread_local bool attr_set = false;  // per host thread: the attribute is per device
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_trsm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem<T>());
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
   trace_mark(trace, -1, st);
   k_zero<T><<<grid_for(d.storage, THREADS * 4), THREADS, 0, st>>>(Lx, d.storage);
   if (d.nnz_a > 0) k_scatter<T><<<grid_for(d.nnz_a, THREADS * 4), THREADS, 0, st>>>(Ax, d.amap, Lx, d.nnz_a);
@@ -607,28 +655,23 @@ cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, co
   return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t run_solve(const DevPlan &d, const std::vector<Launch> &fwd, const std::vector<Launch> &bwd,
-                      const T *Lx, int nrhs, const double *B, int64_t ldb, double *X, int64_t ldx,
-                      double *y, cudaStream_t st, LaunchTrace *trace) {
+template <typename T, typename V>
+cudaError_t run_sweeps(const DevPlan &d, const std::vector<Launch> &fwd, const std::vector<Launch> &bwd,
+                       const T *Lx, int nrhs, V *y, cudaStream_t st, LaunchTrace *trace) {
   const int64_t n = d.n;
-  if (n == 0 || nrhs == 0) return cudaSuccess;
-  trace_mark(trace, -1, st);
-  k_perm_in<<<grid_for(n * nrhs, THREADS), THREADS, 0, st>>>(d.perm, B, ldb, y, n, nrhs);
-  trace_mark(trace, S_PERM, st);
   for (int r0 = 0; r0 < nrhs; r0 += MAXRHS) {
     const int nr = nrhs - r0 < MAXRHS ? nrhs - r0 : MAXRHS;
     for (const Launch &L : fwd) {
       const unsigned g = (unsigned)L.count;
       switch (L.kind) {
         case S_FGATHER:
-          k_fgather<T><<<g, THREADS, 0, st>>>(d.sn, d.tasks, d.upd_tasks, d.upd_entries, d.rel, Lx, y, n, r0, nr, L.off);
+          k_fgather<T, V><<<g, THREADS, 0, st>>>(d.sn, d.tasks, d.upd_tasks, d.upd_entries, d.rel, Lx, y, n, r0, nr, L.off);
           break;
         case S_FDIAG:
-          k_diag_solve<T, false><<<g, THREADS, 0, st>>>(d.sn, d.tasks, Lx, y, n, r0, nr, L.off);
+          k_diag_solve<T, V, false><<<g, THREADS, 0, st>>>(d.sn, d.tasks, Lx, y, n, r0, nr, L.off);
           break;
         case S_FGEMV:
-          k_fgemv<T><<<g, THREADS, 0, st>>>(d.sn, d.tasks, Lx, y, n, r0, nr, L.off);
+          k_fgemv<T, V><<<g, THREADS, 0, st>>>(d.sn, d.tasks, Lx, y, n, r0, nr, L.off);
           break;
         default:
           return cudaErrorInvalidValue;
@@ -639,13 +682,13 @@ cudaError_t run_solve(const DevPlan &d, const std::vector<Launch> &fwd, const st
       const unsigned g = (unsigned)L.count;
       switch (L.kind) {
         case S_BGATHER:
-          k_bgather<T><<<g, THREADS, 0, st>>>(d.sn, d.rows, d.tasks, Lx, y, n, r0, nr, L.off);
+          k_bgather<T, V><<<g, THREADS, 0, st>>>(d.sn, d.rows, d.tasks, Lx, y, n, r0, nr, L.off);
           break;
         case S_BDIAG:
-          k_diag_solve<T, true><<<g, THREADS, 0, st>>>(d.sn, d.tasks, Lx, y, n, r0, nr, L.off);
+          k_diag_solve<T, V, true><<<g, THREADS, 0, st>>>(d.sn, d.tasks, Lx, y, n, r0, nr, L.off);
           break;
         case S_BGEMV:
-          k_bgemv<T><<<g, THREADS, 0, st>>>(d.sn, d.tasks, Lx, y, n, r0, nr, L.off);
+          k_bgemv<T, V><<<g, THREADS, 0, st>>>(d.sn, d.tasks, Lx, y, n, r0, nr, L.off);
           break;
         default:
           return cudaErrorInvalidValue;
@@ -653,16 +696,53 @@ cudaError_t run_solve(const DevPlan &d, const std::vector<Launch> &fwd, const st
       trace_mark(trace, L.kind, st);
     }
   }
-  k_perm_out<<<grid_for(n * nrhs, THREADS), THREADS, 0, st>>>(d.perm, y, X, ldx, n, nrhs);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t run_solve(const DevPlan &d, const std::vector<Launch> &fwd, const std::vector<Launch> &bwd,
+                      const T *Lx, int nrhs, const double *B, int64_t ldb, double *X, int64_t ldx,
+                      double *y, cudaStream_t st, LaunchTrace *trace) {
+  const int64_t n = d.n;
+  if (n == 0 || nrhs == 0) return cudaSuccess;
+  trace_mark(trace, -1, st);
+  k_perm_in<double><<<grid_for(n * nrhs, THREADS), THREADS, 0, st>>>(d.perm, B, ldb, y, n, nrhs);
+  trace_mark(trace, S_PERM, st);
+  cudaError_t e = run_sweeps<T, double>(d, fwd, bwd, Lx, nrhs, y, st, trace);
+  if (e != cudaSuccess) return e;
+  k_perm_out<double><<<grid_for(n * nrhs, THREADS), THREADS, 0, st>>>(d.perm, y, X, ldx, n, nrhs);
   trace_mark(trace, S_PERM, st);
   return cudaGetLastError();
 }
 
+template <typename V>
+cudaError_t permute_in(const DevPlan &d, int nrhs, const double *B, int64_t ldb, V *y, cudaStream_t st) {
+  if (d.n == 0 || nrhs == 0) return cudaSuccess;
+  k_perm_in<V><<<grid_for(d.n * nrhs, THREADS), THREADS, 0, st>>>(d.perm, B, ldb, y, d.n, nrhs);
+  return cudaGetLastError();
+}
+
+template <typename V>
+cudaError_t permute_out(const DevPlan &d, int nrhs, const V *y, double *X, int64_t ldx, cudaStream_t st) {
+  if (d.n == 0 || nrhs == 0) return cudaSuccess;
+  k_perm_out<V><<<grid_for(d.n * nrhs, THREADS), THREADS, 0, st>>>(d.perm, y, X, ldx, d.n, nrhs);
+  return cudaGetLastError();
+}
+
+template cudaError_t prepare_factor<double>();
+template cudaError_t prepare_factor<float>();
 template cudaError_t run_factor<double>(const DevPlan &, const std::vector<Launch> &, const double *,
                                         double *, long long *, cudaStream_t, LaunchTrace *);
+template cudaError_t run_factor<float>(const DevPlan &, const std::vector<Launch> &, const double *,
+                                       float *, long long *, cudaStream_t, LaunchTrace *);
 template cudaError_t run_solve<double>(const DevPlan &, const std::vector<Launch> &,
                                        const std::vector<Launch> &, const double *, int,
                                        const double *, int64_t, double *, int64_t, double *,
                                        cudaStream_t, LaunchTrace *);
+template cudaError_t run_sweeps<float, float>(const DevPlan &, const std::vector<Launch> &,
+                                              const std::vector<Launch> &, const float *, int, float *,
+                                              cudaStream_t, LaunchTrace *);
+template cudaError_t permute_in<double>(const DevPlan &, int, const double *, int64_t, double *, cudaStream_t);
+template cudaError_t permute_out<double>(const DevPlan &, int, const double *, double *, int64_t, cudaStream_t);
 
 }  // namespace sym

@@ -31,6 +31,11 @@ struct LaunchTrace {
   int used = 0;
 };
 
+// Per-device function attributes the factor kernels need (call with the device current, before
+// the first run_factor and outside stream capture).
+template <typename T>
+cudaError_t prepare_factor();
+
 // Numeric factorization: scatter A into the zeroed panels, then run the launch schedule.
 // status: device int64, receives the smallest failing (permuted) column, or stays INT64_MAX.
 template <typename T>
@@ -43,5 +48,16 @@ template <typename T>
 cudaError_t run_solve(const DevPlan &d, const std::vector<Launch> &fwd, const std::vector<Launch> &bwd,
                       const T *Lx, int nrhs, const double *B, int64_t ldb, double *X, int64_t ldx,
                       double *y, cudaStream_t st, LaunchTrace *trace = nullptr);
+
+// The forward and backward sweeps alone on a permuted block y (n x nrhs, ld n) of type V.
+template <typename T, typename V>
+cudaError_t run_sweeps(const DevPlan &d, const std::vector<Launch> &fwd, const std::vector<Launch> &bwd,
+                       const T *Lx, int nrhs, V *y, cudaStream_t st, LaunchTrace *trace = nullptr);
+
+// y = P B and X = P^T y for nrhs columns.
+template <typename V>
+cudaError_t permute_in(const DevPlan &d, int nrhs, const double *B, int64_t ldb, V *y, cudaStream_t st);
+template <typename V>
+cudaError_t permute_out(const DevPlan &d, int nrhs, const V *y, double *X, int64_t ldx, cudaStream_t st);
 
 }  // namespace sym

@@ -13,6 +13,8 @@ namespace sym {
 // Edge of the square tiles that the numeric kernels work on (rows and columns of a supernode's
 // panel are cut into tiles of NB; see row_tile_base below).
 constexpr int NB = 64;
+// Columns per CTA of the backward solve's gather from the rows below a diagonal block.
+constexpr int SOLVE_BG = 16;
 
 // One supernode as the kernels see it. Its panel is column-major, nrows x ncols, leading
 // dimension nrows, at Lx + lx. Row r of the panel is global row rows[rowp + r]; the first ncols
@@ -74,7 +76,8 @@ enum Kind : int32_t {
   S_FGATHER = 11, // y_J(tile bj) -= sum_K L_K(rows in tile) y_K (int4 {J, bj, task, 0})
   S_FDIAG = 12,   // y_s <- L_ss^-1 y_s (int4 {J, s, s, s})
   S_FGEMV = 13,   // y_i -= L_is y_s (int4 {J, i, s, s})
-  S_BGATHER = 14, // z_J(tile bj) -= L_J(off rows, tile)^T z(off rows) (int4 {J, bj, 0, 0})
+  S_BGATHER = 14, // z_J(slice) -= L_J(off rows, slice)^T z(off rows) (int4 {J, slice, 0, 0}),
+                  // slices of SOLVE_BG columns
   S_BDIAG = 15,   // z_s <- L_ss^-T z_s (int4 {J, s, s, s})
   S_BGEMV = 16,   // z_i -= L_si^T z_s (int4 {J, s, i, s})
   S_PERM = 17,    // y = P b and x = P^T y
@@ -115,6 +118,10 @@ struct Plan {
   std::vector<int32_t> level, levelptr, levellist;
   std::vector<int64_t> lxptr;         // nsuper+1; lxptr[nsuper] = storage
   std::vector<int64_t> amap;          // nnz_a: panel position of each entry of A
+  // Full CSR of C = P A P^T (both triangles) for FP64 residuals of the mixed-precision path;
+  // built only when requested. cmap[p] is the index of the entry of A that gives C's entry p.
+  std::vector<int64_t> csr_p, csr_map;
+  std::vector<int32_t> csr_i;
   std::vector<SNode> snodes;
   std::vector<UpdEntry> upd_entries;
   std::vector<UpdTask> upd_tasks;
@@ -131,6 +138,9 @@ struct Plan {
   int32_t nsuper() const { return (int32_t)super.size() - 1; }
   int64_t storage() const { return lxptr.empty() ? 0 : lxptr.back(); }
 };
+
+// Build P.csr_* from the pattern (after analyze).
+void build_permuted_csr(const int64_t *Ap, const int32_t *Ai, Plan &P);
 
 // Run the inspector. Returns SYM_OK or an error code with a message in err.
 int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm,

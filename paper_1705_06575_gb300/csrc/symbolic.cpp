@@ -108,6 +108,33 @@ struct Timer {
 
 }  // namespace
 
+void build_permuted_csr(const int64_t *Ap, const int32_t *Ai, Plan &P) {
+  const int64_t n = P.n;
+  P.csr_p.assign(n + 1, 0);
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t p = Ap[j]; p < Ap[j + 1]; ++p) {
+      const int32_t a = P.iperm[Ai[p]], b = P.iperm[j];
+      P.csr_p[a + 1]++;
+      if (a != b) P.csr_p[b + 1]++;
+    }
+  for (int64_t i = 0; i < n; ++i) P.csr_p[i + 1] += P.csr_p[i];
+  P.csr_i.resize(P.csr_p[n]);
+  P.csr_map.resize(P.csr_p[n]);
+  std::vector<int64_t> fill(P.csr_p.begin(), P.csr_p.end() - 1);
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t p = Ap[j]; p < Ap[j + 1]; ++p) {
+      const int32_t a = P.iperm[Ai[p]], b = P.iperm[j];
+      int64_t q = fill[a]++;
+      P.csr_i[q] = b;
+      P.csr_map[q] = p;
+      if (a != b) {
+        q = fill[b]++;
+        P.csr_i[q] = a;
+        P.csr_map[q] = p;
+      }
+    }
+}
+
 int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm_in,
             const sym_options &opt, Plan &P, std::string &err) {
   Timer timer;
@@ -522,7 +549,7 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
       const SNode &sj = P.snodes[J];
       maxcb = std::max(maxcb, sj.ncb);
       if (sj.nrows > sj.ncols)
-        for (int32_t bj = 0; bj < sj.ncb; ++bj) P.tasks.push_back({J, bj, 0, 0});
+        for (int32_t sl = 0; sl * SOLVE_BG < sj.ncols; ++sl) P.tasks.push_back({J, sl, 0, 0});
     }
     if ((int64_t)P.tasks.size() > off) P.bwd_launches.push_back({S_BGATHER, l, off, (int64_t)P.tasks.size() - off});
     for (int32_t s = maxcb - 1; s >= 0; --s) {
@@ -590,7 +617,8 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
           if (L.kind == S_FDIAG || L.kind == S_BDIAG) P.kind_flops[L.kind] += sq(cols_of_tile(s, q.b));
           if (L.kind == S_FGEMV) P.kind_flops[L.kind] += 2.0 * cols_of_tile(s, q.b) * cols_of_tile(s, q.c);
           if (L.kind == S_BGEMV) P.kind_flops[L.kind] += 2.0 * cols_of_tile(s, q.b) * cols_of_tile(s, q.c);
-          if (L.kind == S_BGATHER) P.kind_flops[L.kind] += 2.0 * (s.nrows - s.ncols) * cols_of_tile(s, q.b);
+          if (L.kind == S_BGATHER)
+            P.kind_flops[L.kind] += 2.0 * (s.nrows - s.ncols) * std::min<int32_t>(SOLVE_BG, s.ncols - q.b * SOLVE_BG);
         }
   }
   P.analyze_seconds = timer.seconds();
