@@ -307,7 +307,7 @@ def run_ours(args):
         if nl:
             kinds[name] = {"ms_per_step": ms / args.steps, "launches_per_step": nl / args.steps,
                            "gflops_alg": fl / ms / 1e6 if ms > 0 else None}
-    factor_kinds = ("scatter", "update", "potrf", "trsm", "gemm")
+    factor_kinds = ("scatter", "update", "potrf", "trsm", "gemm", "trtri")
     ms_factor = sum(kinds[k]["ms_per_step"] for k in factor_kinds if k in kinds)
     ms_solve = sum(v["ms_per_step"] for k, v in kinds.items() if k not in factor_kinds)
     dom = max(kinds, key=lambda k: kinds[k]["ms_per_step"])

@@ -231,12 +231,11 @@ int sym_profile(sym_handle h, int32_t mode);
 #define SYM_KIND_POTRF 2     /* dense Cholesky of diagonal tiles */
 #define SYM_KIND_TRSM 3      /* triangular solves of the tiles below a diagonal tile */
 #define SYM_KIND_GEMM 4      /* trailing updates inside a supernode */
+#define SYM_KIND_TRTRI 5     /* inverses of the diagonal tiles (for the solve) */
 #define SYM_KIND_FGATHER 11  /* forward solve: gather from descendants */
-#define SYM_KIND_FDIAG 12    /* forward solve: diagonal tiles */
-#define SYM_KIND_FGEMV 13    /* forward solve: updates inside a supernode */
+#define SYM_KIND_FSTEP 12    /* forward solve: diagonal tile and updates inside a supernode */
 #define SYM_KIND_BGATHER 14  /* backward solve: gather from the rows below */
-#define SYM_KIND_BDIAG 15    /* backward solve: diagonal tiles */
-#define SYM_KIND_BGEMV 16    /* backward solve: updates inside a supernode */
+#define SYM_KIND_BSTEP 15    /* backward solve: diagonal tile and updates inside a supernode */
 #define SYM_KIND_PERM 17     /* solve: permutations in and out */
 #define SYM_NUM_KINDS 18
 

@@ -224,8 +224,8 @@ def sym_solve_host_ptr(h, nrhs, B, ldb, X, ldx):
 
 
 SYM_PROFILE_OFF, SYM_PROFILE_ON, SYM_PROFILE_RESET = 0, 1, 2
-KINDS = {"scatter": 0, "update": 1, "potrf": 2, "trsm": 3, "gemm": 4, "fgather": 11, "fdiag": 12,
-         "fgemv": 13, "bgather": 14, "bdiag": 15, "bgemv": 16, "perm": 17}
+KINDS = {"scatter": 0, "update": 1, "potrf": 2, "trsm": 3, "gemm": 4, "trtri": 5, "fgather": 11,
+         "fstep": 12, "bgather": 14, "bstep": 15, "perm": 17}
 
 
 def sym_profile(h, mode):

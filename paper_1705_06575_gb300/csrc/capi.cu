@@ -23,6 +23,8 @@ struct sym_handle_s {
   void *d_sn = nullptr, *d_rows = nullptr, *d_rel = nullptr, *d_amap = nullptr, *d_updt = nullptr,
        *d_upde = nullptr, *d_tasks = nullptr, *d_perm = nullptr;
   double *d_Lx = nullptr;
+  double *d_Linv = nullptr;  // inverses of the diagonal tiles (FP64 factor)
+  float *d_Lfinv = nullptr;  // the same for an FP32 factor
   long long *d_status = nullptr;
   long long *h_status = nullptr;  // pinned: [0] holds the reset value, [1] receives the status
   double *d_y = nullptr;          // solve work array
@@ -35,6 +37,7 @@ struct sym_handle_s {
   // CUDA graphs of the launch sequences (replayed while their arguments stay the same)
   bool use_graphs = true;
   bool prepared = false;
+  bool solve_prepared = false;
   cudaStream_t capture_stream = nullptr;
   cudaGraphExec_t fgraph = nullptr;
   const double *fgraph_ax = nullptr;
@@ -119,7 +122,7 @@ int collect_trace(sym_handle_s *h, const sym::LaunchTrace &tr, double flop_scale
 
 void release_device(sym_handle_s *h) {
   {
-    void *mp[] = {h->d_Lf, h->d_Axc, h->d_anorm, h->d_anorm_work, h->d_csr_p, h->d_csr_i, h->d_csr_map, h->d_rwork};
+    void *mp[] = {h->d_Linv, h->d_Lfinv, h->d_Lf, h->d_Axc, h->d_anorm, h->d_anorm_work, h->d_csr_p, h->d_csr_i, h->d_csr_map, h->d_rwork};
     for (void *p : mp)
       if (p) cudaFree(p);
     if (h->h_eta) cudaFreeHost(h->h_eta);
@@ -151,6 +154,7 @@ sym::RefineCtx refine_ctx(sym_handle_s *h) {
   r.fwd = &h->plan.fwd_launches;
   r.bwd = &h->plan.bwd_launches;
   r.Lf = h->d_Lf;
+  r.Lfinv = h->d_Lfinv;
   r.cp = (const int64_t *)h->d_csr_p;
   r.ci = (const int32_t *)h->d_csr_i;
   r.cmap = (const int64_t *)h->d_csr_map;
@@ -169,11 +173,12 @@ cudaError_t enqueue_factor(sym_handle_s *h, const double *Ax, cudaStream_t st, s
       cudaError_t e = cudaMemcpyAsync(h->d_Axc, Ax, sizeof(double) * h->plan.nnz_a, cudaMemcpyDeviceToDevice, st);
       if (e != cudaSuccess) return e;
     }
-    cudaError_t e = sym::run_factor<float>(h->dp, h->plan.factor_launches, Ax, h->d_Lf, h->d_status, st, tr);
+    cudaError_t e = sym::run_factor<float>(h->dp, h->plan.factor_launches, Ax, h->d_Lf, h->d_Lfinv, h->d_status,
+                                           st, tr);
     if (e != cudaSuccess) return e;
     return sym::refine_anorm(refine_ctx(h), st);
   }
-  return sym::run_factor<double>(h->dp, h->plan.factor_launches, Ax, h->d_Lx, h->d_status, st, tr);
+  return sym::run_factor<double>(h->dp, h->plan.factor_launches, Ax, h->d_Lx, h->d_Linv, h->d_status, st, tr);
 }
 
 int ensure_capture_stream(sym_handle_s *h) {
@@ -300,6 +305,16 @@ int sym_analyze_perm(int64_t n, const int64_t *Ap, const int32_t *Ai, const int3
       e = cudaMalloc(&h->d_Lx, sizeof(double) * (P.storage() > 0 ? P.storage() : 1));
       if (e != cudaSuccess) rc = cuda_fail(e, "cudaMalloc(L)");
       else bytes += sizeof(double) * P.storage();
+    }
+    if (!rc && h->precision == SYM_PREC_FP64) {
+      e = cudaMalloc(&h->d_Linv, sizeof(double) * (P.dinv_storage > 0 ? P.dinv_storage : 1));
+      if (e != cudaSuccess) rc = cuda_fail(e, "cudaMalloc(diagonal inverses)");
+      else bytes += sizeof(double) * P.dinv_storage;
+    }
+    if (!rc && h->precision == SYM_PREC_MIXED) {
+      e = cudaMalloc(&h->d_Lfinv, sizeof(float) * (P.dinv_storage > 0 ? P.dinv_storage : 1));
+      if (e != cudaSuccess) rc = cuda_fail(e, "cudaMalloc(diagonal inverses)");
+      else bytes += sizeof(float) * P.dinv_storage;
     }
     if (!rc && h->precision == SYM_PREC_MIXED) {
       e = cudaMalloc(&h->d_Lf, sizeof(float) * (P.storage() > 0 ? P.storage() : 1));
@@ -447,6 +462,12 @@ int sym_solve_multi(sym_handle h, int32_t nrhs, const double *B, int64_t ldb, do
   const int64_t n = h->plan.n;
   if (nrhs < 0 || ldb < n || ldx < n || (nrhs > 0 && n > 0 && (!B || !X)))
     return fail(SYM_ERR_INVALID, "bad solve arguments");
+  if (!h->solve_prepared) {
+    CUDA_TRY((h->precision == SYM_PREC_MIXED ? sym::prepare_solve<float, float>()
+                                             : sym::prepare_solve<double, double>()),
+             "solve set-up");
+    h->solve_prepared = true;
+  }
   if (h->precision == SYM_PREC_MIXED) {
     // FP64 conjugate gradients preconditioned with the FP32 factor, up to 64 columns at a time.
     int32_t iters = 0;
@@ -490,7 +511,7 @@ int sym_solve_multi(sym_handle h, int32_t nrhs, const double *B, int64_t ldb, do
       h->sgraph = nullptr;
       cudaGraph_t g = nullptr;
       CUDA_TRY(cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal), "capture solve");
-      cudaError_t e = sym::run_solve<double>(h->dp, h->plan.fwd_launches, h->plan.bwd_launches, h->d_Lx, nrhs, B,
+      cudaError_t e = sym::run_solve<double>(h->dp, h->plan.fwd_launches, h->plan.bwd_launches, h->d_Lx, h->d_Linv, nrhs, B,
                                              ldb, X, ldx, h->d_y, h->capture_stream, nullptr);
       cudaError_t e2 = cudaStreamEndCapture(h->capture_stream, &g);
       if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -511,7 +532,7 @@ int sym_solve_multi(sym_handle h, int32_t nrhs, const double *B, int64_t ldb, do
     CUDA_TRY(cudaGraphLaunch(h->sgraph, h->stream), "solve graph");
     return SYM_OK;
   }
-  CUDA_TRY(sym::run_solve<double>(h->dp, h->plan.fwd_launches, h->plan.bwd_launches, h->d_Lx, nrhs, B, ldb,
+  CUDA_TRY(sym::run_solve<double>(h->dp, h->plan.fwd_launches, h->plan.bwd_launches, h->d_Lx, h->d_Linv, nrhs, B, ldb,
                                   X, ldx, h->d_y, h->stream, trp),
            "solve kernels");
   if (trp) return collect_trace(h, tr, (double)nrhs, true);
@@ -529,10 +550,14 @@ int solve_with_work(sym_handle h, int32_t nrhs, const double *B, int64_t ldb, do
   if (rc) return rc;
   if (!h->factored) return fail(SYM_ERR_STATE, "no successful factorization to solve with");
   if (h->precision != SYM_PREC_FP64) return fail(SYM_ERR_STATE, "this entry point needs an FP64 factor");
+  if (!h->solve_prepared) {
+    CUDA_TRY((sym::prepare_solve<double, double>()), "solve set-up");
+    h->solve_prepared = true;
+  }
   const int64_t n = h->plan.n;
   if (nrhs < 0 || ldb < n || ldx < n || (nrhs > 0 && n > 0 && (!B || !X)))
     return fail(SYM_ERR_INVALID, "bad solve arguments");
-  CUDA_TRY(sym::run_solve<double>(h->dp, h->plan.fwd_launches, h->plan.bwd_launches, h->d_Lx, nrhs, B, ldb,
+  CUDA_TRY(sym::run_solve<double>(h->dp, h->plan.fwd_launches, h->plan.bwd_launches, h->d_Lx, h->d_Linv, nrhs, B, ldb,
                                   X, ldx, work, h->stream),
            "solve kernels");
   return SYM_OK;

@@ -17,9 +17,13 @@
 // in shared memory, warp-uniform guards that skip whole warps outside ragged tiles, and no
 // atomics in the factorization (every tile is owned by one CTA, descendants are applied in a
 // fixed order, so results are deterministic).
+#include <cooperative_groups.h>
+
 #include <cstdint>
 
 #include "kernels.h"
+
+namespace cg = cooperative_groups;
 
 namespace sym {
 namespace {
@@ -366,8 +370,10 @@ constexpr int MAXRHS = 8;  // right-hand sides handled per pass of the solve ker
 constexpr int BG = SOLVE_BG;  // columns per backward-gather CTA
 
 // Forward gather: y(cols of tile bj of J) -= sum over descendant entries of L_K(rows) y_K.
-// Per entry the n rows of K's panel are read column by column (coalesced): thread t takes row
-// t % nb and every groups-th column of K, partial sums are combined in shared memory.
+// A thread-block cluster of cs CTAs shares one tile: CTA r takes entries r, r + cs, ...; rank 0
+// adds the partial sums of all ranks in rank order through distributed shared memory, so the
+// result does not depend on scheduling. Per entry the n rows of K's panel are read column by
+// column (coalesced): thread t takes row t % nb and every groups-th column of K.
 template <typename T, typename V>
 __global__ void __launch_bounds__(THREADS) k_fgather(const SNode *__restrict__ sn,
                                                      const Int4 *__restrict__ tasks,
@@ -378,18 +384,19 @@ __global__ void __launch_bounds__(THREADS) k_fgather(const SNode *__restrict__ s
                                                      int64_t n, int r0, int nr, int64_t toff) {
   __shared__ V acc[MAXRHS][NB];
   __shared__ V part[THREADS][MAXRHS + 1];
-  const Int4 t = tasks[toff + blockIdx.x];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int cs = (int)cluster.num_blocks();
+  const int rank = (int)cluster.block_rank();
+  const Int4 t = tasks[toff + blockIdx.x / cs];
   const SNode sj = sn[t.a];
   const int bj = t.b;
   const UpdTask u = utasks[t.c];
   const int cb = bj * NB;
   const int tn = min(NB, sj.ncols - cb);
   const int tid = threadIdx.x;
-  for (int idx = tid; idx < MAXRHS * NB; idx += THREADS) {
-    int r = idx % NB, c = idx / NB;
-    acc[c][r] = (r < tn && c < nr) ? y[(int64_t)(r0 + c) * n + sj.first + cb + r] : V(0);
-  }
-  for (int64_t e = u.e0; e < u.e1; ++e) {
+  for (int idx = tid; idx < MAXRHS * NB; idx += THREADS) acc[idx / NB][idx % NB] = V(0);
+  __syncthreads();
+  for (int64_t e = u.e0 + rank; e < u.e1; e += cs) {
     const UpdEntry E = ents[e];
     const SNode sk = sn[E.K];
     int nb = 1;
@@ -428,97 +435,22 @@ __global__ void __launch_bounds__(THREADS) k_fgather(const SNode *__restrict__ s
       const int bb = idx % E.n, q = idx / E.n;
       V v = V(0);
       for (int g = 0; g < groups; ++g) v += part[g * nb + bb][q];
-      acc[q][rel[E.relc + bb] - cb] -= v;
+      acc[q][rel[E.relc + bb] - cb] += v;
     }
     __syncthreads();
   }
-  for (int idx = tid; idx < MAXRHS * NB; idx += THREADS) {
-    int r = idx % NB, c = idx / NB;
-    if (r < tn && c < nr) y[(int64_t)(r0 + c) * n + sj.first + cb + r] = acc[c][r];
-  }
-}
-
-// Diagonal tile solve, forward (L_ss y = y) or backward (L_ss^T z = z), one CTA per tile.
-template <typename T, typename V, bool TRANS>
-__global__ void __launch_bounds__(THREADS) k_diag_solve(const SNode *__restrict__ sn,
-                                                        const Int4 *__restrict__ tasks,
-                                                        const T *__restrict__ Lx, V *__restrict__ y,
-                                                        int64_t n, int r0, int nr, int64_t toff) {
-  __shared__ V Ls[NB][NB + 1];  // [col][row]
-  __shared__ V v[MAXRHS][NB];
-  __shared__ V dinv[NB];
-  const Int4 t = tasks[toff + blockIdx.x];
-  const SNode sj = sn[t.a];
-  const int s = t.b;
-  const int ts = min(NB, sj.ncols - s * NB);
-  const T *D = Lx + sj.lx + (int64_t)(s * NB) * sj.nrows + s * NB;
-  const int64_t g0 = sj.first + s * NB;
-  const int tid = threadIdx.x;
-  for (int idx = tid; idx < NB * NB; idx += THREADS) {
-    int r = idx % NB, c = idx / NB;
-    Ls[c][r] = (r < ts && c < ts && r >= c) ? (V)D[(int64_t)c * sj.nrows + r] : V(0);
-  }
-  for (int idx = tid; idx < MAXRHS * NB; idx += THREADS) {
-    int r = idx % NB, c = idx / NB;
-    v[c][r] = (r < ts && c < nr) ? y[(int64_t)(r0 + c) * n + g0 + r] : V(0);
-  }
-  __syncthreads();
-  if (tid < ts) dinv[tid] = V(1) / Ls[tid][tid];
-  __syncthreads();
-  const int r = tid & (NB - 1), qg = tid >> 6;  // row r, right-hand sides qg, qg + 4
-  if (!TRANS) {
-    for (int c = 0; c < ts; ++c) {
-      if (r > c && r < ts) {
-        const V l = Ls[c][r];
-        for (int q = qg; q < nr; q += 4) v[q][r] = fma(-l, v[q][c] * dinv[c], v[q][r]);
+  cluster.sync();  // every rank's partial sums are complete
+  if (rank == 0) {
+    for (int idx = tid; idx < MAXRHS * NB; idx += THREADS) {
+      const int r = idx % NB, c = idx / NB;
+      if (r < tn && c < nr) {
+        V v = acc[c][r];
+        for (int o = 1; o < cs; ++o) v += cluster.map_shared_rank(&acc[0][0], o)[c * NB + r];
+        y[(int64_t)(r0 + c) * n + sj.first + cb + r] -= v;
       }
-      __syncthreads();
-      if (r == c)
-        for (int q = qg; q < nr; q += 4) v[q][c] *= dinv[c];
-    }
-  } else {
-    for (int c = ts - 1; c >= 0; --c) {
-      if (r < c) {
-        const V l = Ls[r][c];  // L(c, r)
-        for (int q = qg; q < nr; q += 4) v[q][r] = fma(-l, v[q][c] * dinv[c], v[q][r]);
-      }
-      __syncthreads();
-      if (r == c)
-        for (int q = qg; q < nr; q += 4) v[q][c] *= dinv[c];
     }
   }
-  __syncthreads();
-  for (int idx = tid; idx < MAXRHS * NB; idx += THREADS) {
-    int r = idx % NB, c = idx / NB;
-    if (r < ts && c < nr) y[(int64_t)(r0 + c) * n + g0 + r] = v[c][r];
-  }
-}
-
-// Forward GEMV inside J: y(tile i) -= L(i, s) y(tile s), i > s within the diagonal block.
-template <typename T, typename V>
-__global__ void __launch_bounds__(THREADS) k_fgemv(const SNode *__restrict__ sn,
-                                                   const Int4 *__restrict__ tasks,
-                                                   const T *__restrict__ Lx, V *__restrict__ y,
-                                                   int64_t n, int r0, int nr, int64_t toff) {
-  __shared__ V vs[MAXRHS][NB];
-  const Int4 t = tasks[toff + blockIdx.x];
-  const SNode sj = sn[t.a];
-  const int i = t.b, s = t.c;
-  const int ts = min(NB, sj.ncols - s * NB);
-  const int tm = min(NB, sj.ncols - i * NB);
-  const T *Lt = Lx + sj.lx + (int64_t)(s * NB) * sj.nrows + i * NB;
-  const int tid = threadIdx.x;
-  for (int idx = tid; idx < MAXRHS * NB; idx += THREADS) {
-    int r = idx % NB, c = idx / NB;
-    vs[c][r] = (r < ts && c < nr) ? y[(int64_t)(r0 + c) * n + sj.first + s * NB + r] : V(0);
-  }
-  __syncthreads();
-  for (int idx = tid; idx < tm * nr; idx += THREADS) {
-    int r = idx % tm, q = idx / tm;
-    V acc = V(0);
-    for (int k = 0; k < ts; ++k) acc = fma((V)Lt[(int64_t)k * sj.nrows + r], vs[q][k], acc);
-    y[(int64_t)(r0 + q) * n + sj.first + i * NB + r] -= acc;
-  }
+  cluster.sync();  // keep the other ranks' shared memory alive until rank 0 has read it
 }
 
 // Backward gather: z(cols c0..c0+BG) -= L_J(rows below the diagonal block, cols)^T z(those rows).
@@ -575,36 +507,224 @@ __global__ void __launch_bounds__(THREADS) k_bgather(const SNode *__restrict__ s
   }
 }
 
-// Backward GEMV inside J: z(tile i) -= L(s, i)^T z(tile s), i < s within the diagonal block.
-template <typename T, typename V>
-__global__ void __launch_bounds__(THREADS) k_bgemv(const SNode *__restrict__ sn,
-                                                   const Int4 *__restrict__ tasks,
-                                                   const T *__restrict__ Lx, V *__restrict__ y,
-                                                   int64_t n, int r0, int nr, int64_t toff) {
-  __shared__ V vs[MAXRHS][NB];
-  const Int4 t = tasks[toff + blockIdx.x];
-  const SNode sj = sn[t.a];
-  const int s = t.b, i = t.c;
-  const int ts = min(NB, sj.ncols - s * NB);
-  const int ti = min(NB, sj.ncols - i * NB);
-  const T *Lt = Lx + sj.lx + (int64_t)(i * NB) * sj.nrows + s * NB;  // rows of tile s, cols of tile i
+// Shared-memory layout of the solve steps: the inverse of the diagonal tile and one panel tile,
+// each [col][row] with padding, plus the right-hand-side tile before and after the diagonal solve.
+template <typename V>
+struct StepSmem {
+  V Li[NB][NB + 1];
+  V Lt[NB][NB + 1];
+  V vs[MAXRHS][NB];
+  V ys[MAXRHS][NB];
+};
+template <typename V>
+constexpr size_t step_smem() { return sizeof(StepSmem<V>); }
+
+// Solves one diagonal tile u of J in place in global memory: y_u <- L_uu^{-1} y_u (forward) or
+// z_u <- L_uu^{-T} z_u (backward), with the precomputed inverse staged in shared memory.
+template <typename T, typename V, bool TRANS>
+__device__ void write_solved_tile(StepSmem<V> &S, const SNode &sj, const T *__restrict__ Linv, int u,
+                                  V *__restrict__ y, int64_t n, int r0, int nr) {
+  const int tu = min(NB, sj.ncols - u * NB);
+  const int64_t g0 = sj.first + u * NB;
   const int tid = threadIdx.x;
+  __syncthreads();  // S may still be in use by the caller
+  const T *Li = Linv + sj.dx + (int64_t)u * NB * NB;
+  for (int idx = tid; idx < tu * tu; idx += THREADS) S.Li[idx / tu][idx % tu] = (V)Li[idx];
   for (int idx = tid; idx < MAXRHS * NB; idx += THREADS) {
     int r = idx % NB, c = idx / NB;
-    vs[c][r] = (r < ts && c < nr) ? y[(int64_t)(r0 + c) * n + sj.first + s * NB + r] : V(0);
+    S.vs[c][r] = (r < tu && c < nr) ? y[(int64_t)(r0 + c) * n + g0 + r] : V(0);
+  }
+  __syncthreads();
+  for (int idx = tid; idx < tu * nr; idx += THREADS) {
+    const int r = idx % tu, q = idx / tu;
+    V a0 = V(0), a1 = V(0);
+    if (!TRANS) {
+      int k = 0;
+      for (; k + 1 <= r; k += 2) {
+        a0 = fma(S.Li[k][r], S.vs[q][k], a0);
+        a1 = fma(S.Li[k + 1][r], S.vs[q][k + 1], a1);
+      }
+      if (k <= r) a0 = fma(S.Li[k][r], S.vs[q][k], a0);
+    } else {
+      int k = r;
+      for (; k + 1 < tu; k += 2) {
+        a0 = fma(S.Li[r][k], S.vs[q][k], a0);
+        a1 = fma(S.Li[r][k + 1], S.vs[q][k + 1], a1);
+      }
+      if (k < tu) a0 = fma(S.Li[r][k], S.vs[q][k], a0);
+    }
+    y[(int64_t)(r0 + q) * n + g0 + r] = a0 + a1;
+  }
+}
+
+// Forward step of column tile s inside J (tasks {J, i, s}). CTAs i > s read the not yet solved
+// y_s, form ys = L_ss^{-1} y_s themselves from the precomputed inverse and apply
+// y_i -= L_is ys. No CTA of this launch may overwrite y_s, so the solved values are written one
+// step late: the CTA i = s writes the solved y_{s-1} (read by nobody now) and, for the last
+// tile of J (no readers of y_s), the solved y_s as well. Tiles are staged in shared memory with
+// all their loads in flight at once.
+template <typename T, typename V>
+__global__ void __launch_bounds__(THREADS) k_fstep(const SNode *__restrict__ sn,
+                                                   const Int4 *__restrict__ tasks,
+                                                   const T *__restrict__ Lx, const T *__restrict__ Linv,
+                                                   V *__restrict__ y, int64_t n, int r0, int nr, int64_t toff) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  StepSmem<V> &S = *reinterpret_cast<StepSmem<V> *>(smem_raw);
+  const Int4 t = tasks[toff + blockIdx.x];
+  const SNode sj = sn[t.a];
+  const int i = t.b, s = t.c;
+  if (i == s) {
+    if (s >= 1) write_solved_tile<T, V, false>(S, sj, Linv, s - 1, y, n, r0, nr);
+    if (s == sj.ncb - 1) write_solved_tile<T, V, false>(S, sj, Linv, s, y, n, r0, nr);
+    return;
+  }
+  const int ts = min(NB, sj.ncols - s * NB);
+  const int tm = min(NB, sj.ncols - i * NB);
+  const int64_t g0 = sj.first + s * NB;
+  const int tid = threadIdx.x;
+  const T *Li = Linv + sj.dx + (int64_t)s * NB * NB;                  // ts x ts, column-major, lower
+  const T *Lt = Lx + sj.lx + (int64_t)(s * NB) * sj.nrows + i * NB;  // rows of tile i, cols of tile s
+  for (int idx = tid; idx < ts * ts; idx += THREADS) S.Li[idx / ts][idx % ts] = (V)Li[idx];
+  for (int idx = tid; idx < NB * ts; idx += THREADS) {
+    const int r = idx % NB, c = idx / NB;
+    if (r < tm) S.Lt[c][r] = (V)Lt[(int64_t)c * sj.nrows + r];
+  }
+  for (int idx = tid; idx < MAXRHS * NB; idx += THREADS) {
+    int r = idx % NB, c = idx / NB;
+    S.vs[c][r] = (r < ts && c < nr) ? y[(int64_t)(r0 + c) * n + g0 + r] : V(0);
+  }
+  __syncthreads();
+  for (int idx = tid; idx < ts * nr; idx += THREADS) {
+    const int r = idx % ts, q = idx / ts;
+    V a0 = V(0), a1 = V(0);
+    int k = 0;
+    for (; k + 1 <= r; k += 2) {
+      a0 = fma(S.Li[k][r], S.vs[q][k], a0);
+      a1 = fma(S.Li[k + 1][r], S.vs[q][k + 1], a1);
+    }
+    if (k <= r) a0 = fma(S.Li[k][r], S.vs[q][k], a0);
+    S.ys[q][r] = a0 + a1;
+  }
+  __syncthreads();
+  for (int idx = tid; idx < tm * nr; idx += THREADS) {
+    const int r = idx % tm, q = idx / tm;
+    V a0 = V(0), a1 = V(0);
+    int k = 0;
+    for (; k + 1 < ts; k += 2) {
+      a0 = fma(S.Lt[k][r], S.ys[q][k], a0);
+      a1 = fma(S.Lt[k + 1][r], S.ys[q][k + 1], a1);
+    }
+    if (k < ts) a0 = fma(S.Lt[k][r], S.ys[q][k], a0);
+    y[(int64_t)(r0 + q) * n + sj.first + i * NB + r] -= a0 + a1;
+  }
+}
+
+// Backward step of column tile s inside J (tasks {J, i, s}, s descending): CTAs i < s form
+// zs = L_ss^{-T} z_s and apply z_i -= L_si^T zs; the CTA i = s writes the solved z_{s+1} and,
+// for tile 0, the solved z_0 (the mirror image of the forward step).
+template <typename T, typename V>
+__global__ void __launch_bounds__(THREADS) k_bstep(const SNode *__restrict__ sn,
+                                                   const Int4 *__restrict__ tasks,
+                                                   const T *__restrict__ Lx, const T *__restrict__ Linv,
+                                                   V *__restrict__ y, int64_t n, int r0, int nr, int64_t toff) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  StepSmem<V> &S = *reinterpret_cast<StepSmem<V> *>(smem_raw);
+  const Int4 t = tasks[toff + blockIdx.x];
+  const SNode sj = sn[t.a];
+  const int i = t.b, s = t.c;
+  if (i == s) {
+    if (s + 1 < sj.ncb) write_solved_tile<T, V, true>(S, sj, Linv, s + 1, y, n, r0, nr);
+    if (s == 0) write_solved_tile<T, V, true>(S, sj, Linv, 0, y, n, r0, nr);
+    return;
+  }
+  const int ts = min(NB, sj.ncols - s * NB);
+  const int ti = min(NB, sj.ncols - i * NB);
+  const int64_t g0 = sj.first + s * NB;
+  const int tid = threadIdx.x;
+  const T *Li = Linv + sj.dx + (int64_t)s * NB * NB;                  // ts x ts, column-major, lower
+  const T *Lt = Lx + sj.lx + (int64_t)(i * NB) * sj.nrows + s * NB;  // rows of tile s, cols of tile i
+  for (int idx = tid; idx < ts * ts; idx += THREADS) S.Li[idx / ts][idx % ts] = (V)Li[idx];
+  for (int idx = tid; idx < NB * ti; idx += THREADS) {
+    const int k = idx % NB, c = idx / NB;
+    if (k < ts) S.Lt[c][k] = (V)Lt[(int64_t)c * sj.nrows + k];
+  }
+  for (int idx = tid; idx < MAXRHS * NB; idx += THREADS) {
+    int r = idx % NB, c = idx / NB;
+    S.vs[c][r] = (r < ts && c < nr) ? y[(int64_t)(r0 + c) * n + g0 + r] : V(0);
+  }
+  __syncthreads();
+  for (int idx = tid; idx < ts * nr; idx += THREADS) {
+    const int r = idx % ts, q = idx / ts;
+    V a0 = V(0), a1 = V(0);
+    int k = r;
+    for (; k + 1 < ts; k += 2) {  // (L^-1)(k, r) for k >= r
+      a0 = fma(S.Li[r][k], S.vs[q][k], a0);
+      a1 = fma(S.Li[r][k + 1], S.vs[q][k + 1], a1);
+    }
+    if (k < ts) a0 = fma(S.Li[r][k], S.vs[q][k], a0);
+    S.ys[q][r] = a0 + a1;
   }
   __syncthreads();
   for (int idx = tid; idx < ti * nr; idx += THREADS) {
-    int c = idx % ti, q = idx / ti;
-    const T *col = Lt + (int64_t)c * sj.nrows;
-    V acc = V(0);
-    for (int k = 0; k < ts; ++k) acc = fma((V)col[k], vs[q][k], acc);
-    y[(int64_t)(r0 + q) * n + sj.first + i * NB + c] -= acc;
+    const int c = idx % ti, q = idx / ti;
+    V a0 = V(0), a1 = V(0);
+    int k = 0;
+    for (; k + 1 < ts; k += 2) {
+      a0 = fma(S.Lt[c][k], S.ys[q][k], a0);
+      a1 = fma(S.Lt[c][k + 1], S.ys[q][k + 1], a1);
+    }
+    if (k < ts) a0 = fma(S.Lt[c][k], S.ys[q][k], a0);
+    y[(int64_t)(r0 + q) * n + sj.first + i * NB + c] -= a0 + a1;
+  }
+}
+
+// Inverse of diagonal tile s of J (in FP64 from the factored tile), stored column-major ts x ts
+// at Linv + dx + s NB^2. Solves L X = I row by row of X: row c is final once scaled by
+// 1 / L(c, c); it is then eliminated from the rows below.
+template <typename T>
+__global__ void __launch_bounds__(THREADS) k_trtri(const SNode *__restrict__ sn,
+                                                   const Int4 *__restrict__ tasks,
+                                                   const T *__restrict__ Lx, T *__restrict__ Linv,
+                                                   int64_t toff) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double(*a)[NB + 1] = reinterpret_cast<double(*)[NB + 1]>(smem_raw);  // L, [col][row]
+  double(*x)[NB + 1] = a + NB;                                          // X, [col][row]
+  double *dinv = reinterpret_cast<double *>(smem_raw) + 2 * NB * (NB + 1);
+  const Int4 t = tasks[toff + blockIdx.x];
+  const SNode sj = sn[t.a];
+  const int s = t.b;
+  const int ts = min(NB, sj.ncols - s * NB);
+  const T *D = Lx + sj.lx + (int64_t)(s * NB) * sj.nrows + s * NB;
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < NB * NB; idx += THREADS) {
+    int r = idx % NB, c = idx / NB;
+    a[c][r] = (r < ts && c < ts && r >= c) ? (double)D[(int64_t)c * sj.nrows + r] : 0.0;
+    x[c][r] = r == c ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  if (tid < ts) dinv[tid] = 1.0 / a[tid][tid];
+  __syncthreads();
+  const int r = tid & (NB - 1), jg = tid >> 6;
+  for (int c = 0; c < ts; ++c) {
+    if (r > c && r < ts) {
+      const double l = a[c][r];
+      for (int j = jg; j <= c; j += 4) x[j][r] = fma(-l, x[j][c] * dinv[c], x[j][r]);
+    }
+    __syncthreads();
+    if (r == c)
+      for (int j = jg; j <= c; j += 4) x[j][c] *= dinv[c];
+  }
+  __syncthreads();
+  T *out = Linv + sj.dx + (int64_t)s * NB * NB;
+  for (int idx = tid; idx < ts * ts; idx += THREADS) {
+    const int rr = idx % ts, c = idx / ts;
+    out[(int64_t)c * ts + rr] = rr >= c ? (T)x[c][rr] : T(0);
   }
 }
 
 template <typename T>
 constexpr size_t trsm_smem() { return sizeof(T) * (2 * NB * (NB + 1) + NB); }
+constexpr size_t trtri_smem() { return sizeof(double) * (2 * NB * (NB + 1) + NB); }
 
 inline int grid_for(int64_t count, int per) {
   int64_t g = (count + per - 1) / per;
@@ -622,12 +742,23 @@ inline void trace_mark(LaunchTrace *tr, int32_t kind, cudaStream_t st) {
 
 template <typename T>
 cudaError_t prepare_factor() {
-  return cudaFuncSetAttribute(k_trsm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem<T>());
+  cudaError_t e = cudaFuncSetAttribute(k_trsm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem<T>());
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_trtri<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trtri_smem());
+}
+
+template <typename T, typename V>
+cudaError_t prepare_solve() {
+  cudaError_t e = cudaFuncSetAttribute(k_fstep<T, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)step_smem<V>());
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_bstep<T, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)step_smem<V>());
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_fgather<T, V>, cudaFuncAttributeNonPortableClusterSizeAllowed, 0);
 }
 
 template <typename T>
 cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, const double *Ax,
-                       T *Lx, long long *status, cudaStream_t st, LaunchTrace *trace) {
+                       T *Lx, T *Linv, long long *status, cudaStream_t st, LaunchTrace *trace) {
   trace_mark(trace, -1, st);
   k_zero<T><<<grid_for(d.storage, THREADS * 4), THREADS, 0, st>>>(Lx, d.storage);
   if (d.nnz_a > 0) k_scatter<T><<<grid_for(d.nnz_a, THREADS * 4), THREADS, 0, st>>>(Ax, d.amap, Lx, d.nnz_a);
@@ -647,6 +778,9 @@ cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, co
       case K_GEMM:
         k_gemm<T><<<g, THREADS, 0, st>>>(d.sn, d.tasks, Lx, L.off);
         break;
+      case K_TRTRI:
+        k_trtri<T><<<g, THREADS, trtri_smem(), st>>>(d.sn, d.tasks, Lx, Linv, L.off);
+        break;
       default:
         return cudaErrorInvalidValue;
     }
@@ -657,21 +791,33 @@ cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, co
 
 template <typename T, typename V>
 cudaError_t run_sweeps(const DevPlan &d, const std::vector<Launch> &fwd, const std::vector<Launch> &bwd,
-                       const T *Lx, int nrhs, V *y, cudaStream_t st, LaunchTrace *trace) {
+                       const T *Lx, const T *Linv, int nrhs, V *y, cudaStream_t st, LaunchTrace *trace) {
   const int64_t n = d.n;
   for (int r0 = 0; r0 < nrhs; r0 += MAXRHS) {
     const int nr = nrhs - r0 < MAXRHS ? nrhs - r0 : MAXRHS;
     for (const Launch &L : fwd) {
       const unsigned g = (unsigned)L.count;
       switch (L.kind) {
-        case S_FGATHER:
-          k_fgather<T, V><<<g, THREADS, 0, st>>>(d.sn, d.tasks, d.upd_tasks, d.upd_entries, d.rel, Lx, y, n, r0, nr, L.off);
+        case S_FGATHER: {
+          cudaLaunchConfig_t cfg = {};
+          cudaLaunchAttribute attr[1];
+          cfg.gridDim = dim3(g * (unsigned)L.cluster, 1, 1);
+          cfg.blockDim = dim3(THREADS, 1, 1);
+          cfg.dynamicSmemBytes = 0;
+          cfg.stream = st;
+          attr[0].id = cudaLaunchAttributeClusterDimension;
+          attr[0].val.clusterDim.x = (unsigned)L.cluster;
+          attr[0].val.clusterDim.y = 1;
+          attr[0].val.clusterDim.z = 1;
+          cfg.attrs = attr;
+          cfg.numAttrs = 1;
+          cudaError_t e = cudaLaunchKernelEx(&cfg, k_fgather<T, V>, d.sn, d.tasks, d.upd_tasks, d.upd_entries,
+                                             d.rel, Lx, y, n, r0, nr, L.off);
+          if (e != cudaSuccess) return e;
           break;
-        case S_FDIAG:
-          k_diag_solve<T, V, false><<<g, THREADS, 0, st>>>(d.sn, d.tasks, Lx, y, n, r0, nr, L.off);
-          break;
-        case S_FGEMV:
-          k_fgemv<T, V><<<g, THREADS, 0, st>>>(d.sn, d.tasks, Lx, y, n, r0, nr, L.off);
+        }
+        case S_FSTEP:
+          k_fstep<T, V><<<g, THREADS, step_smem<V>(), st>>>(d.sn, d.tasks, Lx, Linv, y, n, r0, nr, L.off);
           break;
         default:
           return cudaErrorInvalidValue;
@@ -684,11 +830,8 @@ cudaError_t run_sweeps(const DevPlan &d, const std::vector<Launch> &fwd, const s
         case S_BGATHER:
           k_bgather<T, V><<<g, THREADS, 0, st>>>(d.sn, d.rows, d.tasks, Lx, y, n, r0, nr, L.off);
           break;
-        case S_BDIAG:
-          k_diag_solve<T, V, true><<<g, THREADS, 0, st>>>(d.sn, d.tasks, Lx, y, n, r0, nr, L.off);
-          break;
-        case S_BGEMV:
-          k_bgemv<T, V><<<g, THREADS, 0, st>>>(d.sn, d.tasks, Lx, y, n, r0, nr, L.off);
+        case S_BSTEP:
+          k_bstep<T, V><<<g, THREADS, step_smem<V>(), st>>>(d.sn, d.tasks, Lx, Linv, y, n, r0, nr, L.off);
           break;
         default:
           return cudaErrorInvalidValue;
@@ -701,14 +844,14 @@ cudaError_t run_sweeps(const DevPlan &d, const std::vector<Launch> &fwd, const s
 
 template <typename T>
 cudaError_t run_solve(const DevPlan &d, const std::vector<Launch> &fwd, const std::vector<Launch> &bwd,
-                      const T *Lx, int nrhs, const double *B, int64_t ldb, double *X, int64_t ldx,
-                      double *y, cudaStream_t st, LaunchTrace *trace) {
+                      const T *Lx, const T *Linv, int nrhs, const double *B, int64_t ldb, double *X,
+                      int64_t ldx, double *y, cudaStream_t st, LaunchTrace *trace) {
   const int64_t n = d.n;
   if (n == 0 || nrhs == 0) return cudaSuccess;
   trace_mark(trace, -1, st);
   k_perm_in<double><<<grid_for(n * nrhs, THREADS), THREADS, 0, st>>>(d.perm, B, ldb, y, n, nrhs);
   trace_mark(trace, S_PERM, st);
-  cudaError_t e = run_sweeps<T, double>(d, fwd, bwd, Lx, nrhs, y, st, trace);
+  cudaError_t e = run_sweeps<T, double>(d, fwd, bwd, Lx, Linv, nrhs, y, st, trace);
   if (e != cudaSuccess) return e;
   k_perm_out<double><<<grid_for(n * nrhs, THREADS), THREADS, 0, st>>>(d.perm, y, X, ldx, n, nrhs);
   trace_mark(trace, S_PERM, st);
@@ -729,19 +872,21 @@ cudaError_t permute_out(const DevPlan &d, int nrhs, const V *y, double *X, int64
   return cudaGetLastError();
 }
 
+template cudaError_t prepare_solve<double, double>();
+template cudaError_t prepare_solve<float, float>();
 template cudaError_t prepare_factor<double>();
 template cudaError_t prepare_factor<float>();
 template cudaError_t run_factor<double>(const DevPlan &, const std::vector<Launch> &, const double *,
-                                        double *, long long *, cudaStream_t, LaunchTrace *);
+                                        double *, double *, long long *, cudaStream_t, LaunchTrace *);
 template cudaError_t run_factor<float>(const DevPlan &, const std::vector<Launch> &, const double *,
-                                       float *, long long *, cudaStream_t, LaunchTrace *);
+                                       float *, float *, long long *, cudaStream_t, LaunchTrace *);
 template cudaError_t run_solve<double>(const DevPlan &, const std::vector<Launch> &,
-                                       const std::vector<Launch> &, const double *, int,
+                                       const std::vector<Launch> &, const double *, const double *, int,
                                        const double *, int64_t, double *, int64_t, double *,
                                        cudaStream_t, LaunchTrace *);
 template cudaError_t run_sweeps<float, float>(const DevPlan &, const std::vector<Launch> &,
-                                              const std::vector<Launch> &, const float *, int, float *,
-                                              cudaStream_t, LaunchTrace *);
+                                              const std::vector<Launch> &, const float *, const float *, int,
+                                              float *, cudaStream_t, LaunchTrace *);
 template cudaError_t permute_in<double>(const DevPlan &, int, const double *, int64_t, double *, cudaStream_t);
 template cudaError_t permute_out<double>(const DevPlan &, int, const double *, double *, int64_t, cudaStream_t);
 

@@ -36,23 +36,27 @@ struct LaunchTrace {
 template <typename T>
 cudaError_t prepare_factor();
 
+// Per-device function attributes of the solve kernels (with the device current, outside capture).
+template <typename T, typename V>
+cudaError_t prepare_solve();
+
 // Numeric factorization: scatter A into the zeroed panels, then run the launch schedule.
 // status: device int64, receives the smallest failing (permuted) column, or stays INT64_MAX.
 template <typename T>
 cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, const double *Ax,
-                       T *Lx, long long *status, cudaStream_t st, LaunchTrace *trace = nullptr);
+                       T *Lx, T *Linv, long long *status, cudaStream_t st, LaunchTrace *trace = nullptr);
 
 // Solve with nrhs right-hand sides: y = P b, forward sweep, backward sweep, x = P^T y.
-// y: device work array of n * nrhs (ld n).
+// y: device work array of n * nrhs (ld n); Linv: the diagonal-tile inverses run_factor wrote.
 template <typename T>
 cudaError_t run_solve(const DevPlan &d, const std::vector<Launch> &fwd, const std::vector<Launch> &bwd,
-                      const T *Lx, int nrhs, const double *B, int64_t ldb, double *X, int64_t ldx,
-                      double *y, cudaStream_t st, LaunchTrace *trace = nullptr);
+                      const T *Lx, const T *Linv, int nrhs, const double *B, int64_t ldb, double *X,
+                      int64_t ldx, double *y, cudaStream_t st, LaunchTrace *trace = nullptr);
 
 // The forward and backward sweeps alone on a permuted block y (n x nrhs, ld n) of type V.
 template <typename T, typename V>
 cudaError_t run_sweeps(const DevPlan &d, const std::vector<Launch> &fwd, const std::vector<Launch> &bwd,
-                       const T *Lx, int nrhs, V *y, cudaStream_t st, LaunchTrace *trace = nullptr);
+                       const T *Lx, const T *Linv, int nrhs, V *y, cudaStream_t st, LaunchTrace *trace = nullptr);
 
 // y = P B and X = P^T y for nrhs columns.
 template <typename V>

@@ -26,6 +26,8 @@ struct SNode {
   int32_t ncb;    // column tiles = ceil(ncols / NB)
   int64_t rowp;   // offset into rows[]
   int64_t lx;     // offset into Lx
+  int64_t dx;     // offset of the inverses of its diagonal tiles: tile s (order ts) is a
+                  // column-major ts x ts block at dx + s * NB * NB
 };
 
 // Row tiling of a panel: the diagonal block is cut at multiples of NB, and the rows below it
@@ -73,13 +75,14 @@ enum Kind : int32_t {
   K_POTRF = 2,    // dense Cholesky of diagonal tile s (int4 {J, s, s, s})
   K_TRSM = 3,     // tile (i, s) <- tile * L_ss^-T (int4 {J, i, s, s})
   K_GEMM = 4,     // tile (i, j) -= L_is L_js^T (int4 {J, i, j, s})
+  K_TRTRI = 5,    // inverse of every diagonal tile, for the solve (int4 {J, s, s, s})
   S_FGATHER = 11, // y_J(tile bj) -= sum_K L_K(rows in tile) y_K (int4 {J, bj, task, 0})
-  S_FDIAG = 12,   // y_s <- L_ss^-1 y_s (int4 {J, s, s, s})
-  S_FGEMV = 13,   // y_i -= L_is y_s (int4 {J, i, s, s})
+  S_FSTEP = 12,   // column tile s of J: y_i -= L_is L_ss^-1 y_s (CTAs i > s); CTA i = s writes
+                  // the solved tiles s-1 (and s if last) (int4 {J, i, s, s})
   S_BGATHER = 14, // z_J(slice) -= L_J(off rows, slice)^T z(off rows) (int4 {J, slice, 0, 0}),
                   // slices of SOLVE_BG columns
-  S_BDIAG = 15,   // z_s <- L_ss^-T z_s (int4 {J, s, s, s})
-  S_BGEMV = 16,   // z_i -= L_si^T z_s (int4 {J, s, i, s})
+  S_BSTEP = 15,   // column tile s of J: z_i -= L_si^T L_ss^-T z_s (CTAs i < s); CTA i = s writes
+                  // the solved tiles s+1 (and 0 if s = 0) (int4 {J, i, s, s})
   S_PERM = 17,    // y = P b and x = P^T y
   NUM_KINDS = 18,
 };
@@ -87,8 +90,10 @@ enum Kind : int32_t {
 struct Launch {
   int32_t kind;
   int32_t level;
-  int64_t off;    // offset into the task array of this kind
-  int64_t count;  // number of tasks (CTAs)
+  int64_t off;          // offset into the task array of this kind
+  int64_t count;        // number of tasks
+  int32_t cluster = 1;  // CTAs per task (a thread-block cluster) where the kernel supports it
+  int32_t pad = 0;
 };
 
 struct Int4 {
@@ -117,6 +122,7 @@ struct Plan {
   std::vector<int32_t> rel;           // relative row maps
   std::vector<int32_t> level, levelptr, levellist;
   std::vector<int64_t> lxptr;         // nsuper+1; lxptr[nsuper] = storage
+  int64_t dinv_storage = 0;           // entries of all diagonal-tile inverses
   std::vector<int64_t> amap;          // nnz_a: panel position of each entry of A
   // Full CSR of C = P A P^T (both triangles) for FP64 residuals of the mixed-precision path;
   // built only when requested. cmap[p] is the index of the entry of A that gives C's entry p.

@@ -172,7 +172,7 @@ int refine_solve(const RefineCtx &c, int nrhs, const double *B, int64_t ldb, dou
   };
   auto precond = [&](const double *in, double *out) -> cudaError_t {
     k_to_float<<<blocks(nn), RT, 0, st>>>(in, yf, nn);
-    cudaError_t e = run_sweeps<float, float>(*c.dp, *c.fwd, *c.bwd, c.Lf, nrhs, yf, st, nullptr);
+    cudaError_t e = run_sweeps<float, float>(*c.dp, *c.fwd, *c.bwd, c.Lf, c.Lfinv, nrhs, yf, st, nullptr);
     if (e != cudaSuccess) return e;
     k_to_double<<<blocks(nn), RT, 0, st>>>(yf, out, nn);
     return cudaGetLastError();

@@ -15,6 +15,7 @@ struct RefineCtx {
   const std::vector<Launch> *fwd = nullptr;
   const std::vector<Launch> *bwd = nullptr;
   const float *Lf = nullptr;      // FP32 factor panels
+  const float *Lfinv = nullptr;   // inverses of its diagonal tiles
   const int64_t *cp = nullptr;    // CSR of P A P^T (both triangles)
   const int32_t *ci = nullptr;
   const int64_t *cmap = nullptr;  // value of entry p is Ax[cmap[p]]

@@ -389,6 +389,11 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
     s.rowp = P.rowptr[J];
     s.lx = P.lxptr[J];
     P.lxptr[J + 1] = P.lxptr[J] + (int64_t)s.nrows * s.ncols;
+    s.dx = P.dinv_storage;
+    if (s.ncb > 0) {
+      const int64_t last = s.ncols - (int64_t)(s.ncb - 1) * NB;
+      P.dinv_storage += (int64_t)(s.ncb - 1) * NB * NB + last * last;
+    }
     P.max_ncols = std::max(P.max_ncols, s.ncols);
   }
   P.amap.resize(P.nnz_a);
@@ -513,6 +518,13 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
       }
     }
   }
+  // Inverses of all diagonal tiles, in one launch after the factorization (the solve uses them).
+  {
+    const int64_t off = (int64_t)P.tasks.size();
+    for (int32_t J = 0; J < ns; ++J)
+      for (int32_t t = 0; t < P.snodes[J].ncb; ++t) P.tasks.push_back({J, t, t, t});
+    if ((int64_t)P.tasks.size() > off) P.factor_launches.push_back({K_TRTRI, nlev, off, (int64_t)P.tasks.size() - off});
+  }
   // Solve schedules.
   for (int32_t l = 0; l < nlev; ++l) {
     int64_t off = (int64_t)P.tasks.size();
@@ -525,20 +537,21 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
         if (task >= 0) P.tasks.push_back({J, bj, (int32_t)task, 0});
       }
     }
-    if ((int64_t)P.tasks.size() > off) P.fwd_launches.push_back({S_FGATHER, l, off, (int64_t)P.tasks.size() - off});
+    if ((int64_t)P.tasks.size() > off) {
+      // Few tiles: spread each tile's descendants over a cluster of CTAs.
+      const int64_t cnt = (int64_t)P.tasks.size() - off;
+      Launch L{S_FGATHER, l, off, cnt};
+      L.cluster = cnt < 304 ? 8 : (cnt < 1216 ? 2 : 1);
+      P.fwd_launches.push_back(L);
+    }
     for (int32_t s = 0; s < maxcb; ++s) {
-      for (int kind : {S_FDIAG, S_FGEMV}) {
-        off = (int64_t)P.tasks.size();
-        for (int32_t t = P.levelptr[l]; t < P.levelptr[l + 1]; ++t) {
-          const int32_t J = P.levellist[t];
-          const int32_t ncb = P.snodes[J].ncb;
-          if (s >= ncb) continue;
-          if (kind == S_FDIAG) P.tasks.push_back({J, s, s, s});
-          else
-            for (int32_t i = s + 1; i < ncb; ++i) P.tasks.push_back({J, i, s, s});
-        }
-        if ((int64_t)P.tasks.size() > off) P.fwd_launches.push_back({kind, l, off, (int64_t)P.tasks.size() - off});
+      off = (int64_t)P.tasks.size();
+      for (int32_t t = P.levelptr[l]; t < P.levelptr[l + 1]; ++t) {
+        const int32_t J = P.levellist[t];
+        const int32_t ncb = P.snodes[J].ncb;
+        for (int32_t i = s; i < ncb; ++i) P.tasks.push_back({J, i, s, s});
       }
+      if ((int64_t)P.tasks.size() > off) P.fwd_launches.push_back({S_FSTEP, l, off, (int64_t)P.tasks.size() - off});
     }
   }
   for (int32_t l = nlev - 1; l >= 0; --l) {
@@ -553,18 +566,14 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
     }
     if ((int64_t)P.tasks.size() > off) P.bwd_launches.push_back({S_BGATHER, l, off, (int64_t)P.tasks.size() - off});
     for (int32_t s = maxcb - 1; s >= 0; --s) {
-      for (int kind : {S_BDIAG, S_BGEMV}) {
-        off = (int64_t)P.tasks.size();
-        for (int32_t t = P.levelptr[l]; t < P.levelptr[l + 1]; ++t) {
-          const int32_t J = P.levellist[t];
-          const int32_t ncb = P.snodes[J].ncb;
-          if (s >= ncb) continue;
-          if (kind == S_BDIAG) P.tasks.push_back({J, s, s, s});
-          else
-            for (int32_t i = 0; i < s; ++i) P.tasks.push_back({J, s, i, s});
-        }
-        if ((int64_t)P.tasks.size() > off) P.bwd_launches.push_back({kind, l, off, (int64_t)P.tasks.size() - off});
+      off = (int64_t)P.tasks.size();
+      for (int32_t t = P.levelptr[l]; t < P.levelptr[l + 1]; ++t) {
+        const int32_t J = P.levellist[t];
+        const int32_t ncb = P.snodes[J].ncb;
+        if (s >= ncb) continue;
+        for (int32_t i = s; i >= 0; --i) P.tasks.push_back({J, i, s, s});
       }
+      if ((int64_t)P.tasks.size() > off) P.bwd_launches.push_back({S_BSTEP, l, off, (int64_t)P.tasks.size() - off});
     }
   }
   // 12. Algorithmic flops of each kernel kind (see Plan::kind_flops).
@@ -601,6 +610,9 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
           const int64_t rb = row_tile_base(q.b, s.ncols, s.ncb);
           const double tm = std::min<int64_t>(NB, (q.b < s.ncb ? s.ncols : s.nrows) - rb);
           P.kind_flops[K_TRSM] += tm * sq(ts);
+        } else if (L.kind == K_TRTRI) {
+          const double ts = cols_of_tile(s, q.b);
+          P.kind_flops[K_TRTRI] += ts * ts * ts / 3.0;
         } else if (L.kind == K_GEMM) {
           const double ks = cols_of_tile(s, q.d), tn = cols_of_tile(s, q.c);
           const int64_t rb = row_tile_base(q.b, s.ncols, s.ncb);
@@ -614,9 +626,10 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
         for (int64_t t = L.off; t < L.off + L.count; ++t) {
           const Int4 &q = P.tasks[t];
           const SNode &s = P.snodes[q.a];
-          if (L.kind == S_FDIAG || L.kind == S_BDIAG) P.kind_flops[L.kind] += sq(cols_of_tile(s, q.b));
-          if (L.kind == S_FGEMV) P.kind_flops[L.kind] += 2.0 * cols_of_tile(s, q.b) * cols_of_tile(s, q.c);
-          if (L.kind == S_BGEMV) P.kind_flops[L.kind] += 2.0 * cols_of_tile(s, q.b) * cols_of_tile(s, q.c);
+          // diagonal tile: ts^2 (solve with L_ss); off-diagonal tile: 2 tm ts
+          if (L.kind == S_FSTEP || L.kind == S_BSTEP)
+            P.kind_flops[L.kind] += q.b == q.c ? sq(cols_of_tile(s, q.c))
+                                                : 2.0 * cols_of_tile(s, q.b) * cols_of_tile(s, q.c);
           if (L.kind == S_BGATHER)
             P.kind_flops[L.kind] += 2.0 * (s.nrows - s.ncols) * std::min<int32_t>(SOLVE_BG, s.ncols - q.b * SOLVE_BG);
         }
