@@ -229,6 +229,64 @@ def bench_mixed(S, torch, M, B, flops, args, stream, barrier, world):
             "definition": "same step as the main line; value = factor flops / step time"}
 
 
+def bench_batched(S, torch, args, stream, barrier, world):
+    """Batched refactorization: 512 value sets on one 128 x 128 9-point pattern (w ~ U(0.5, 2),
+    diagonal 1.05 sum |w|), one right-hand side each, factor + solve of the whole batch per step,
+    against the same work done by one-matrix calls in sequence (timed on 16 and scaled to 512)."""
+    import workloads as w
+    nb = args.batch
+    M, vals = w.same_pattern_batch(lambda r: w.dd2d9(128, r), nb, 2000)
+    s = S.Solver(M.n, M.Ap, M.Ai, M.perm)
+    s.set_stream(stream)
+    info = s.info()
+    V = torch.from_numpy(vals).cuda()
+    B = torch.from_numpy(np.random.default_rng(5).standard_normal((nb, M.n))).cuda()
+    X = torch.empty_like(B)
+
+    def step():
+        S.sym_factor_batch(s.h, nb, V, M.nnz)
+        S.sym_solve_batch(s.h, nb, 1, B, M.n, M.n, X, M.n, M.n)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    Xh = X.cpu().numpy()
+    worst = 0.0
+    for b in (0, nb // 2, nb - 1):
+        Mb = w.Matrix(M.n, M.Ap, M.Ai, vals[b])
+        worst = max(worst, backward_error(Mb, B[b].cpu().numpy()[:, None], Xh[b][:, None]))
+    # the same work, one matrix per call
+    one = S.Solver(M.n, M.Ap, M.Ai, M.perm)
+    one.set_stream(stream)
+    xs = torch.empty(M.n, dtype=torch.float64, device="cuda")
+    nseq = min(16, nb)
+    for b in range(2):
+        one.factor(V[b])
+        S.sym_solve(one.h, B[b], xs)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for b in range(nseq):
+        one.factor(V[b])
+        S.sym_solve(one.h, B[b], xs)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_seq = e0.elapsed_time(e1) / nseq * nb
+    s.close()
+    one.close()
+    return {"value": info.flops * nb * world / (ms * 1e-3) / 1e9, "unit": "GFLOP/s", "ms_per_step": ms,
+            "matrices": nb, "n": M.n, "nnz_l_per_matrix": info.nnz_l, "backward_error": worst,
+            "ms_sequential_calls": ms_seq, "speedup_vs_sequential": ms_seq / ms, "dtype": "f64",
+            "definition": "512 x (factor + 1-RHS solve) of the 128^2 9-point pattern per step"}
+
+
 def run_ours(args):
     import torch
 
@@ -349,6 +407,8 @@ def run_ours(args):
     variants = {}
     if not args.no_variants:
         variants["mixed_fp32_pcg"] = bench_mixed(S, torch, M, B, info.flops, args, stream, barrier, world)
+        if args.batch > 0:
+            variants["batched_512x_dd2d9_128"] = bench_batched(S, torch, args, stream, barrier, world)
     clocks = read_clocks(clock_path, local) if rank == 0 else None
     flops = info.flops
     value = flops * world / (ms_step * 1e-3) / 1e9
@@ -397,7 +457,8 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=WORKLOAD,
                     help="the benchmark workload is the default; the others are smaller cases")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-variants", action="store_true", help="skip the mixed-precision variant")
+    ap.add_argument("--no-variants", action="store_true", help="skip the mixed-precision and batched variants")
+    ap.add_argument("--batch", type=int, default=512, help="matrices of the batched variant (0: skip)")
     ap.add_argument("--cpu-flops", type=float, default=1.0e10,
                     help="flops of the leading block the oracle baseline factors")
     ap.add_argument("--ref-flops", type=float, default=2.0e9,

@@ -133,6 +133,25 @@ int sym_factor(sym_handle h, const double *Ax);
  * sym_status afterwards to wait and read the pivot status. */
 int sym_factor_async(sym_handle h, const double *Ax);
 
+/* Batched refactorization (this library's addition: many matrices with the pattern of the handle
+ * factored together, every kernel launch covering all of them, the launch sequence replayed as
+ * one CUDA graph). Ax: DEVICE pointer to nbatch value arrays, matrix b at Ax + b * stride
+ * (stride >= nnz(A)); 1 <= nbatch <= 65535. The handle grows its factor storage to nbatch
+ * matrices on demand (one allocation, kept). Waits like sym_factor; SYM_ERR_NOT_SPD when any
+ * matrix fails (sym_batch_error_columns gives every matrix's first failing column, or -1). */
+int sym_factor_batch(sym_handle h, int32_t nbatch, const double *Ax, int64_t stride);
+
+/* Per-matrix first failing columns (caller's numbering; -1 when fine) of the last factorization,
+ * nbatch entries (1 after sym_factor). */
+int sym_batch_error_columns(sym_handle h, int64_t *cols);
+
+/* Solve for the first nbatch matrices of the last batch: matrix b's nrhs right-hand sides are
+ * column-major at B + b * bstride (ld ldb), its solutions at X + b * xstride (ld ldx). DEVICE
+ * pointers; bstride >= ldb * nrhs and xstride >= ldx * nrhs when nbatch > 1. FP64 factors solve
+ * all matrices in the same launches; a mixed-precision handle refines each matrix in turn. */
+int sym_solve_batch(sym_handle h, int32_t nbatch, int32_t nrhs, const double *B, int64_t ldb,
+                    int64_t bstride, double *X, int64_t ldx, int64_t xstride);
+
 /* Wait for the handle's stream and return the status of the last factorization. */
 int sym_status(sym_handle h);
 
@@ -188,8 +207,12 @@ int sym_info(sym_handle h, sym_stats *s);
 /* First failing column (caller's numbering) of the last SYM_ERR_NOT_SPD, else -1. */
 int sym_last_error_column(sym_handle h, int64_t *col);
 
+/* Copy matrix index of the factored batch to host memory (storage_l doubles, widened from FP32
+ * for a mixed-precision handle). */
+int sym_get_batch_factor_host(sym_handle h, int32_t index, double *Lx_host);
+
 /* Copy the factor to host memory in its supernodal panel layout (storage_l doubles; an FP32
- * factor is widened to double). */
+ * factor is widened to double). For a batch: matrix 0. */
 int sym_get_factor_host(sym_handle h, double *Lx_host);
 
 /* Export an integer array of the symbolic plan (host copy) for checks against an independent

@@ -21,7 +21,8 @@ __all__ = [
     "sym_factor_host", "sym_solve", "sym_solve_multi", "sym_solve_host", "sym_info",
     "sym_last_error_column", "sym_get_factor_host", "sym_export", "sym_free", "load", "Solver",
     "EXPORTS", "sym_profile", "sym_profile_read", "sym_fma_peak", "sym_solve_host_ptr", "KINDS",
-    "sym_solve_multi_noalloc", "sym_set_refinement", "sym_refinement_info",
+    "sym_solve_multi_noalloc", "sym_set_refinement", "sym_refinement_info", "sym_factor_batch",
+    "sym_batch_error_columns", "sym_solve_batch", "sym_get_batch_factor_host",
 ]
 
 SYM_OK = 0
@@ -112,6 +113,10 @@ def load():
             "sym_fma_peak": ([i32, ct.POINTER(ct.c_double)], I),
             "sym_solve_multi_noalloc": ([P, i32, P, i64, P, i64], I),
             "sym_set_refinement": ([P, ct.c_double, i32], I),
+            "sym_factor_batch": ([P, i32, P, i64], I),
+            "sym_batch_error_columns": ([P, P], I),
+            "sym_solve_batch": ([P, i32, i32, P, i64, i64, P, i64, i64], I),
+            "sym_get_batch_factor_host": ([P, i32, P], I),
             "sym_refinement_info": ([P, ct.POINTER(i32), ct.POINTER(ct.c_double)], I),
         }
         for name, (args, res) in sigs.items():
@@ -254,6 +259,29 @@ def sym_refinement_info(h):
     it, be = ct.c_int32(), ct.c_double()
     _check(load().sym_refinement_info(h, ct.byref(it), ct.byref(be)))
     return it.value, be.value
+
+
+def sym_factor_batch(h, nbatch, Ax, stride):
+    """Ax: device tensor (nbatch, stride) or address; matrix b's values at Ax + b * stride."""
+    return _check(load().sym_factor_batch(h, int(nbatch), _dptr(Ax), int(stride)))
+
+
+def sym_batch_error_columns(h, nbatch):
+    out = np.zeros(nbatch, dtype=np.int64)
+    _check(load().sym_batch_error_columns(h, out.ctypes.data))
+    return out
+
+
+def sym_solve_batch(h, nbatch, nrhs, B, ldb, bstride, X, ldx, xstride):
+    return _check(load().sym_solve_batch(h, int(nbatch), int(nrhs), _dptr(B), int(ldb), int(bstride), _dptr(X),
+                                         int(ldx), int(xstride)))
+
+
+def sym_get_batch_factor_host(h, index):
+    st = sym_info(h)
+    out = np.zeros(st.storage_l, dtype=np.float64)
+    _check(load().sym_get_batch_factor_host(h, int(index), out.ctypes.data))
+    return out
 
 
 def sym_info(h):

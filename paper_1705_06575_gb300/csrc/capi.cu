@@ -34,6 +34,15 @@ struct sym_handle_s {
   int64_t device_bytes = 0;
   bool factored = false;
   int64_t err_col = -1;
+  // batches of matrices with this pattern: capacity (matrices whose factor fits), the size of
+  // the last factored batch and its per-matrix failing columns
+  int32_t bcap = 1;
+  int32_t nbatch = 1;
+  std::vector<int64_t> batch_err;
+  int32_t fgraph_nb = 0;
+  int64_t fgraph_stride = 0;
+  int32_t sgraph_nb = 0;
+  int64_t sgraph_bx[2] = {0, 0};
   // CUDA graphs of the launch sequences (replayed while their arguments stay the same)
   bool use_graphs = true;
   bool prepared = false;
@@ -148,18 +157,18 @@ int ensure_rwork(sym_handle_s *h, int64_t count) {
   return SYM_OK;
 }
 
-sym::RefineCtx refine_ctx(sym_handle_s *h) {
+sym::RefineCtx refine_ctx(sym_handle_s *h, int32_t b = 0) {
   sym::RefineCtx r;
   r.dp = &h->dp;
   r.fwd = &h->plan.fwd_launches;
   r.bwd = &h->plan.bwd_launches;
-  r.Lf = h->d_Lf;
-  r.Lfinv = h->d_Lfinv;
+  r.Lf = h->d_Lf + (int64_t)b * h->plan.storage();
+  r.Lfinv = h->d_Lfinv + (int64_t)b * h->plan.dinv_storage;
   r.cp = (const int64_t *)h->d_csr_p;
   r.ci = (const int32_t *)h->d_csr_i;
   r.cmap = (const int64_t *)h->d_csr_map;
-  r.Ax = h->d_Axc;
-  r.anorm = h->d_anorm;
+  r.Ax = h->d_Axc + (int64_t)b * h->plan.nnz_a;
+  r.anorm = h->d_anorm + b;
   r.anorm_work = h->d_anorm_work;
   r.work = h->d_rwork;
   r.n = h->plan.n;
@@ -167,18 +176,82 @@ sym::RefineCtx refine_ctx(sym_handle_s *h) {
 }
 
 // Everything one factorization enqueues after the status reset (the part a graph captures).
-cudaError_t enqueue_factor(sym_handle_s *h, const double *Ax, cudaStream_t st, sym::LaunchTrace *tr) {
+sym::Batch factor_batch(const sym_handle_s *h, int32_t nbatch, int64_t stride) {
+  sym::Batch bt;
+  bt.count = nbatch;
+  bt.lx = h->plan.storage();
+  bt.ax = stride;
+  bt.dinv = h->plan.dinv_storage;
+  return bt;
+}
+
+cudaError_t enqueue_factor(sym_handle_s *h, const double *Ax, int32_t nbatch, int64_t stride, cudaStream_t st,
+                           sym::LaunchTrace *tr) {
+  const sym::Batch bt = factor_batch(h, nbatch, stride);
   if (h->precision == SYM_PREC_MIXED) {
-    if (h->plan.nnz_a > 0) {
-      cudaError_t e = cudaMemcpyAsync(h->d_Axc, Ax, sizeof(double) * h->plan.nnz_a, cudaMemcpyDeviceToDevice, st);
+    const int64_t nnz = h->plan.nnz_a;
+    if (nnz > 0) {
+      cudaError_t e = cudaMemcpy2DAsync(h->d_Axc, sizeof(double) * nnz, Ax, sizeof(double) * (nbatch > 1 ? stride : nnz),
+                                        sizeof(double) * nnz, nbatch, cudaMemcpyDeviceToDevice, st);
       if (e != cudaSuccess) return e;
     }
     cudaError_t e = sym::run_factor<float>(h->dp, h->plan.factor_launches, Ax, h->d_Lf, h->d_Lfinv, h->d_status,
-                                           st, tr);
+                                           st, tr, bt);
     if (e != cudaSuccess) return e;
-    return sym::refine_anorm(refine_ctx(h), st);
+    for (int32_t b = 0; b < nbatch; ++b) {
+      e = sym::refine_anorm(refine_ctx(h, b), st);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
   }
-  return sym::run_factor<double>(h->dp, h->plan.factor_launches, Ax, h->d_Lx, h->d_Linv, h->d_status, st, tr);
+  return sym::run_factor<double>(h->dp, h->plan.factor_launches, Ax, h->d_Lx, h->d_Linv, h->d_status, st, tr, bt);
+}
+
+void drop_graphs(sym_handle_s *h) {
+  if (h->fgraph) cudaGraphExecDestroy(h->fgraph);
+  if (h->sgraph) cudaGraphExecDestroy(h->sgraph);
+  h->fgraph = nullptr;
+  h->sgraph = nullptr;
+}
+
+// Room for the factors of nbatch matrices (panels, diagonal inverses, pivot status and, for the
+// mixed precision, the copies of A's values and their norms). Growing drops the captured graphs
+// (they hold the old addresses) and the current factor.
+int ensure_batch(sym_handle_s *h, int32_t nbatch) {
+  if (nbatch <= h->bcap) return SYM_OK;
+  drop_graphs(h);
+  h->factored = false;
+  const auto &P = h->plan;
+  auto regrow = [&](void **p, size_t bytes, const char *what) -> int {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    CUDA_TRY(cudaMalloc(p, bytes > 0 ? bytes : 8), what);
+    return SYM_OK;
+  };
+  const size_t nb = (size_t)nbatch;
+  int rc = SYM_OK;
+  if (h->precision == SYM_PREC_FP64) {
+    rc = regrow((void **)&h->d_Lx, sizeof(double) * P.storage() * nb, "cudaMalloc(L batch)");
+    if (!rc) rc = regrow((void **)&h->d_Linv, sizeof(double) * P.dinv_storage * nb, "cudaMalloc(inverses batch)");
+  } else {
+    rc = regrow((void **)&h->d_Lf, sizeof(float) * P.storage() * nb, "cudaMalloc(L batch)");
+    if (!rc) rc = regrow((void **)&h->d_Lfinv, sizeof(float) * P.dinv_storage * nb, "cudaMalloc(inverses batch)");
+    if (!rc) rc = regrow((void **)&h->d_Axc, sizeof(double) * P.nnz_a * nb, "cudaMalloc(A copies)");
+    if (!rc) rc = regrow((void **)&h->d_anorm, sizeof(double) * nb, "cudaMalloc(norms)");
+  }
+  if (!rc) rc = regrow((void **)&h->d_status, sizeof(long long) * nb, "cudaMalloc(status batch)");
+  if (!rc) {
+    if (h->h_status) cudaFreeHost(h->h_status);
+    h->h_status = nullptr;
+    cudaError_t e = cudaMallocHost(&h->h_status, 2 * sizeof(long long) * nb);
+    if (e != cudaSuccess) rc = cuda_fail(e, "cudaMallocHost(status batch)");
+  }
+  if (rc) {
+    h->bcap = 0;  // partially reallocated: unusable until a successful ensure_batch
+    return rc;
+  }
+  h->bcap = nbatch;
+  return SYM_OK;
 }
 
 int ensure_capture_stream(sym_handle_s *h) {
@@ -218,15 +291,23 @@ int check_device(sym_handle_s *h) {
 
 int finish_status(sym_handle_s *h) {
   CUDA_TRY(cudaStreamSynchronize(h->stream), "factor");
-  long long s = h->h_status[1];
-  if (s != LLONG_MAX) {
+  const int32_t nb = h->nbatch;
+  h->batch_err.assign(nb, -1);
+  h->err_col = -1;
+  int32_t bad = 0;
+  for (int32_t b = 0; b < nb; ++b) {
+    const long long s = h->h_status[h->bcap + b];
+    if (s != LLONG_MAX) {
+      h->batch_err[b] = (s >= 0 && s < h->plan.n) ? h->plan.perm[s] : -1;
+      if (bad++ == 0) h->err_col = h->batch_err[b];
+    }
+  }
+  if (bad) {
     h->factored = false;
-    h->err_col = (s >= 0 && s < h->plan.n) ? h->plan.perm[s] : -1;
     return fail(SYM_ERR_NOT_SPD, "matrix is not positive definite (pivot at column " +
-                                     std::to_string(h->err_col) + ")");
+                                     std::to_string(h->err_col) + (nb > 1 ? " of the first failing matrix)" : ")"));
   }
   h->factored = true;
-  h->err_col = -1;
   return SYM_OK;
 }
 
@@ -347,7 +428,7 @@ int sym_analyze_perm(int64_t n, const int64_t *Ap, const int32_t *Ai, const int3
       if (e != cudaSuccess) rc = cuda_fail(e, "cudaMalloc(status)");
     }
     if (!rc) {
-      e = cudaMallocHost(&h->h_status, 2 * sizeof(long long));
+      e = cudaMallocHost(&h->h_status, 2 * sizeof(long long));  // [reset value, result] for one matrix
       if (e != cudaSuccess) rc = cuda_fail(e, "cudaMallocHost(status)");
     }
     if (rc) {
@@ -378,13 +459,22 @@ int sym_set_stream(sym_handle h, void *stream) {
   return SYM_OK;
 }
 
-int sym_factor_async(sym_handle h, const double *Ax) {
+}  // extern "C"
+
+namespace {
+
+int factor_impl(sym_handle h, int32_t nbatch, const double *Ax, int64_t stride) {
   int rc = check_device(h);
   if (rc) return rc;
   if (!Ax && h->plan.nnz_a > 0) return fail(SYM_ERR_INVALID, "null Ax");
+  if (nbatch < 1 || (nbatch > 1 && stride < h->plan.nnz_a)) return fail(SYM_ERR_INVALID, "bad batch arguments");
+  if (nbatch > 65535) return fail(SYM_ERR_LIMIT, "more than 65535 matrices in one batch");
+  rc = ensure_batch(h, nbatch);
+  if (rc) return rc;
   h->factored = false;
-  h->h_status[0] = LLONG_MAX;
-  CUDA_TRY(cudaMemcpyAsync(h->d_status, &h->h_status[0], sizeof(long long), cudaMemcpyHostToDevice, h->stream),
+  h->nbatch = nbatch;
+  for (int32_t b = 0; b < nbatch; ++b) h->h_status[b] = LLONG_MAX;
+  CUDA_TRY(cudaMemcpyAsync(h->d_status, h->h_status, sizeof(long long) * nbatch, cudaMemcpyHostToDevice, h->stream),
            "status reset");
   if (!h->prepared) {
     CUDA_TRY(h->precision == SYM_PREC_MIXED ? sym::prepare_factor<float>() : sym::prepare_factor<double>(),
@@ -399,15 +489,15 @@ int sym_factor_async(sym_handle h, const double *Ax) {
     trp = &tr;
   }
   if (!trp && h->use_graphs) {
-    // Replay the captured launch sequence; capture it again when Ax moved.
-    if (!h->fgraph || h->fgraph_ax != Ax) {
+    // Replay the captured launch sequence; capture it again when Ax or the batch moved.
+    if (!h->fgraph || h->fgraph_ax != Ax || h->fgraph_nb != nbatch || h->fgraph_stride != stride) {
       rc = ensure_capture_stream(h);
       if (rc) return rc;
       if (h->fgraph) cudaGraphExecDestroy(h->fgraph);
       h->fgraph = nullptr;
       cudaGraph_t g = nullptr;
       CUDA_TRY(cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal), "capture factor");
-      cudaError_t e = enqueue_factor(h, Ax, h->capture_stream, nullptr);
+      cudaError_t e = enqueue_factor(h, Ax, nbatch, stride, h->capture_stream, nullptr);
       cudaError_t e2 = cudaStreamEndCapture(h->capture_stream, &g);
       if (e != cudaSuccess || e2 != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -418,18 +508,146 @@ int sym_factor_async(sym_handle h, const double *Ax) {
       cudaGraphDestroy(g);
       if (e != cudaSuccess) return cuda_fail(e, "instantiate factor graph");
       h->fgraph_ax = Ax;
+      h->fgraph_nb = nbatch;
+      h->fgraph_stride = stride;
     }
     CUDA_TRY(cudaGraphLaunch(h->fgraph, h->stream), "factor graph");
   } else {
-    CUDA_TRY(enqueue_factor(h, Ax, h->stream, trp), "factor kernels");
+    CUDA_TRY(enqueue_factor(h, Ax, nbatch, stride, h->stream, trp), "factor kernels");
   }
   if (trp) {
-    rc = collect_trace(h, tr, 1.0, false);
+    rc = collect_trace(h, tr, (double)nbatch, false);
     if (rc) return rc;
   }
-  CUDA_TRY(cudaMemcpyAsync(&h->h_status[1], h->d_status, sizeof(long long), cudaMemcpyDeviceToHost, h->stream),
+  CUDA_TRY(cudaMemcpyAsync(h->h_status + h->bcap, h->d_status, sizeof(long long) * nbatch, cudaMemcpyDeviceToHost,
+                           h->stream),
            "status read");
   return SYM_OK;
+}
+
+int solve_impl(sym_handle h, int32_t nbatch, int32_t nrhs, const double *B, int64_t ldb, int64_t bstride,
+               double *X, int64_t ldx, int64_t xstride) {
+  int rc = check_device(h);
+  if (rc) return rc;
+  if (!h->factored) return fail(SYM_ERR_STATE, "no successful factorization to solve with");
+  const int64_t n = h->plan.n;
+  if (nrhs < 0 || ldb < n || ldx < n || (nrhs > 0 && n > 0 && (!B || !X)))
+    return fail(SYM_ERR_INVALID, "bad solve arguments");
+  if (nbatch < 1 || nbatch > h->nbatch) return fail(SYM_ERR_INVALID, "batch larger than the factored batch");
+  if (nbatch > 1 && (bstride < ldb * (int64_t)nrhs || xstride < ldx * (int64_t)nrhs))
+    return fail(SYM_ERR_INVALID, "bad batch strides");
+  if (!h->solve_prepared) {
+    CUDA_TRY((h->precision == SYM_PREC_MIXED ? sym::prepare_solve<float, float>()
+                                             : sym::prepare_solve<double, double>()),
+             "solve set-up");
+    h->solve_prepared = true;
+  }
+  if (h->precision == SYM_PREC_MIXED) {
+    // FP64 conjugate gradients preconditioned with the FP32 factor, per matrix, up to 64
+    // right-hand sides at a time.
+    int32_t iters = 0;
+    double berr = 0.0;
+    bool conv = true;
+    for (int32_t b = 0; b < nbatch; ++b)
+      for (int32_t c0 = 0; c0 < nrhs; c0 += 64) {
+        const int32_t nc = nrhs - c0 < 64 ? nrhs - c0 : 64;
+        rc = ensure_rwork(h, sym::refine_work_doubles(n, nc));
+        if (rc) return rc;
+        sym::RefineResult res;
+        if (sym::refine_solve(refine_ctx(h, b), nc, B + b * bstride + (int64_t)c0 * ldb, ldb,
+                              X + b * xstride + (int64_t)c0 * ldx, ldx, h->refine_tol, h->refine_max_iter, h->h_eta,
+                              &res, h->stream) != 0)
+          return cuda_fail(cudaGetLastError(), "refinement");
+        iters = res.iterations > iters ? res.iterations : iters;
+        berr = res.backward_error > berr ? res.backward_error : berr;
+        conv = conv && res.converged;
+      }
+    h->last_iterations = iters;
+    h->last_berr = berr;
+    if (!conv) return fail(SYM_ERR_NO_CONVERGENCE, "refinement reached its iteration limit above tolerance");
+    return SYM_OK;
+  }
+  rc = ensure_y(h, n * (int64_t)nrhs * nbatch);
+  if (rc) return rc;
+  sym::Batch bt;
+  bt.count = nbatch;
+  bt.lx = h->plan.storage();
+  bt.dinv = h->plan.dinv_storage;
+  bt.y = n * (int64_t)nrhs;
+  bt.b = bstride;
+  bt.x = xstride;
+  sym::LaunchTrace tr, *trp = nullptr;
+  if (h->profiling) {
+    const size_t passes = (size_t)(nrhs + 7) / 8;
+    rc = ensure_events(h, passes * (h->plan.fwd_launches.size() + h->plan.bwd_launches.size()) + 4);
+    if (rc) return rc;
+    tr.events = &h->events;
+    trp = &tr;
+  }
+  if (!trp && h->use_graphs && n > 0 && nrhs > 0) {
+    const bool same = h->sgraph && h->sgraph_key[0] == B && h->sgraph_key[1] == X &&
+                      h->sgraph_key[2] == h->d_y && h->sgraph_ikey[0] == nrhs && h->sgraph_ikey[1] == ldb &&
+                      h->sgraph_ikey[2] == ldx && h->sgraph_nb == nbatch && h->sgraph_bx[0] == bstride &&
+                      h->sgraph_bx[1] == xstride;
+    if (!same) {
+      rc = ensure_capture_stream(h);
+      if (rc) return rc;
+      if (h->sgraph) cudaGraphExecDestroy(h->sgraph);
+      h->sgraph = nullptr;
+      cudaGraph_t g = nullptr;
+      CUDA_TRY(cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal), "capture solve");
+      cudaError_t e = sym::run_solve<double>(h->dp, h->plan.fwd_launches, h->plan.bwd_launches, h->d_Lx, h->d_Linv,
+                                             nrhs, B, ldb, X, ldx, h->d_y, h->capture_stream, nullptr, bt);
+      cudaError_t e2 = cudaStreamEndCapture(h->capture_stream, &g);
+      if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return cuda_fail(e != cudaSuccess ? e : e2, "capture solve");
+      }
+      e = cudaGraphInstantiate(&h->sgraph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return cuda_fail(e, "instantiate solve graph");
+      h->sgraph_key[0] = B;
+      h->sgraph_key[1] = X;
+      h->sgraph_key[2] = h->d_y;
+      h->sgraph_ikey[0] = nrhs;
+      h->sgraph_ikey[1] = ldb;
+      h->sgraph_ikey[2] = ldx;
+      h->sgraph_nb = nbatch;
+      h->sgraph_bx[0] = bstride;
+      h->sgraph_bx[1] = xstride;
+    }
+    CUDA_TRY(cudaGraphLaunch(h->sgraph, h->stream), "solve graph");
+    return SYM_OK;
+  }
+  CUDA_TRY(sym::run_solve<double>(h->dp, h->plan.fwd_launches, h->plan.bwd_launches, h->d_Lx, h->d_Linv, nrhs, B,
+                                  ldb, X, ldx, h->d_y, h->stream, trp, bt),
+           "solve kernels");
+  if (trp) return collect_trace(h, tr, (double)nrhs * nbatch, true);
+  return SYM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sym_factor_async(sym_handle h, const double *Ax) { return factor_impl(h, 1, Ax, 0); }
+
+int sym_factor_batch(sym_handle h, int32_t nbatch, const double *Ax, int64_t stride) {
+  int rc = factor_impl(h, nbatch, Ax, stride);
+  if (rc) return rc;
+  return finish_status(h);
+}
+
+int sym_batch_error_columns(sym_handle h, int64_t *cols) {
+  if (!h || !cols) return fail(SYM_ERR_INVALID, "null argument");
+  for (size_t b = 0; b < h->batch_err.size(); ++b) cols[b] = h->batch_err[b];
+  return SYM_OK;
+}
+
+int sym_solve_batch(sym_handle h, int32_t nbatch, int32_t nrhs, const double *B, int64_t ldb, int64_t bstride,
+                    double *X, int64_t ldx, int64_t xstride) {
+  return solve_impl(h, nbatch, nrhs, B, ldb, bstride, X, ldx, xstride);
 }
 
 int sym_status(sym_handle h) {
@@ -456,87 +674,7 @@ int sym_factor_host(sym_handle h, const double *Ax) {
 }
 
 int sym_solve_multi(sym_handle h, int32_t nrhs, const double *B, int64_t ldb, double *X, int64_t ldx) {
-  int rc = check_device(h);
-  if (rc) return rc;
-  if (!h->factored) return fail(SYM_ERR_STATE, "no successful factorization to solve with");
-  const int64_t n = h->plan.n;
-  if (nrhs < 0 || ldb < n || ldx < n || (nrhs > 0 && n > 0 && (!B || !X)))
-    return fail(SYM_ERR_INVALID, "bad solve arguments");
-  if (!h->solve_prepared) {
-    CUDA_TRY((h->precision == SYM_PREC_MIXED ? sym::prepare_solve<float, float>()
-                                             : sym::prepare_solve<double, double>()),
-             "solve set-up");
-    h->solve_prepared = true;
-  }
-  if (h->precision == SYM_PREC_MIXED) {
-    // FP64 conjugate gradients preconditioned with the FP32 factor, up to 64 columns at a time.
-    int32_t iters = 0;
-    double berr = 0.0;
-    bool conv = true;
-    for (int32_t c0 = 0; c0 < nrhs; c0 += 64) {
-      const int32_t nc = nrhs - c0 < 64 ? nrhs - c0 : 64;
-      rc = ensure_rwork(h, sym::refine_work_doubles(n, nc));
-      if (rc) return rc;
-      sym::RefineResult res;
-      if (sym::refine_solve(refine_ctx(h), nc, B + (int64_t)c0 * ldb, ldb, X + (int64_t)c0 * ldx, ldx,
-                            h->refine_tol, h->refine_max_iter, h->h_eta, &res, h->stream) != 0)
-        return cuda_fail(cudaGetLastError(), "refinement");
-      iters = res.iterations > iters ? res.iterations : iters;
-      berr = res.backward_error > berr ? res.backward_error : berr;
-      conv = conv && res.converged;
-    }
-    h->last_iterations = iters;
-    h->last_berr = berr;
-    if (!conv) return fail(SYM_ERR_NO_CONVERGENCE, "refinement reached its iteration limit above tolerance");
-    return SYM_OK;
-  }
-  rc = ensure_y(h, n * (int64_t)nrhs);
-  if (rc) return rc;
-  sym::LaunchTrace tr, *trp = nullptr;
-  if (h->profiling) {
-    const size_t passes = (size_t)(nrhs + 7) / 8;
-    rc = ensure_events(h, passes * (h->plan.fwd_launches.size() + h->plan.bwd_launches.size()) + 4);
-    if (rc) return rc;
-    tr.events = &h->events;
-    trp = &tr;
-  }
-  if (!trp && h->use_graphs && n > 0 && nrhs > 0) {
-    const bool same = h->sgraph && h->sgraph_key[0] == B && h->sgraph_key[1] == X &&
-                      h->sgraph_key[2] == h->d_y && h->sgraph_ikey[0] == nrhs && h->sgraph_ikey[1] == ldb &&
-                      h->sgraph_ikey[2] == ldx;
-    if (!same) {
-      rc = ensure_capture_stream(h);
-      if (rc) return rc;
-      if (h->sgraph) cudaGraphExecDestroy(h->sgraph);
-      h->sgraph = nullptr;
-      cudaGraph_t g = nullptr;
-      CUDA_TRY(cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal), "capture solve");
-      cudaError_t e = sym::run_solve<double>(h->dp, h->plan.fwd_launches, h->plan.bwd_launches, h->d_Lx, h->d_Linv, nrhs, B,
-                                             ldb, X, ldx, h->d_y, h->capture_stream, nullptr);
-      cudaError_t e2 = cudaStreamEndCapture(h->capture_stream, &g);
-      if (e != cudaSuccess || e2 != cudaSuccess) {
-        if (g) cudaGraphDestroy(g);
-        cudaGetLastError();
-        return cuda_fail(e != cudaSuccess ? e : e2, "capture solve");
-      }
-      e = cudaGraphInstantiate(&h->sgraph, g, 0);
-      cudaGraphDestroy(g);
-      if (e != cudaSuccess) return cuda_fail(e, "instantiate solve graph");
-      h->sgraph_key[0] = B;
-      h->sgraph_key[1] = X;
-      h->sgraph_key[2] = h->d_y;
-      h->sgraph_ikey[0] = nrhs;
-      h->sgraph_ikey[1] = ldb;
-      h->sgraph_ikey[2] = ldx;
-    }
-    CUDA_TRY(cudaGraphLaunch(h->sgraph, h->stream), "solve graph");
-    return SYM_OK;
-  }
-  CUDA_TRY(sym::run_solve<double>(h->dp, h->plan.fwd_launches, h->plan.bwd_launches, h->d_Lx, h->d_Linv, nrhs, B, ldb,
-                                  X, ldx, h->d_y, h->stream, trp),
-           "solve kernels");
-  if (trp) return collect_trace(h, tr, (double)nrhs, true);
-  return SYM_OK;
+  return solve_impl(h, 1, nrhs, B, ldb, 0, X, ldx, 0);
 }
 
 }  // extern "C"
@@ -617,6 +755,22 @@ int sym_info(sym_handle h, sym_stats *s) {
 int sym_last_error_column(sym_handle h, int64_t *col) {
   if (!h || !col) return fail(SYM_ERR_INVALID, "null argument");
   *col = h->err_col;
+  return SYM_OK;
+}
+
+int sym_get_batch_factor_host(sym_handle h, int32_t index, double *Lx_host) {
+  int rc = check_device(h);
+  if (rc) return rc;
+  if (!Lx_host || index < 0 || index >= h->bcap) return fail(SYM_ERR_INVALID, "bad argument");
+  CUDA_TRY(cudaStreamSynchronize(h->stream), "sync");
+  const int64_t st = h->plan.storage();
+  if (h->precision == SYM_PREC_MIXED) {
+    std::vector<float> tmp(st);
+    CUDA_TRY(cudaMemcpy(tmp.data(), h->d_Lf + index * st, sizeof(float) * st, cudaMemcpyDeviceToHost), "copy L");
+    for (int64_t i = 0; i < st; ++i) Lx_host[i] = tmp[i];
+    return SYM_OK;
+  }
+  CUDA_TRY(cudaMemcpy(Lx_host, h->d_Lx + index * st, sizeof(double) * st, cudaMemcpyDeviceToHost), "copy L");
   return SYM_OK;
 }
 

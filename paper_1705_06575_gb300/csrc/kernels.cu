@@ -105,7 +105,8 @@ __device__ __forceinline__ double rsqrt_newton(double d) {
 // ---------------------------------------------------------------------------------------------
 // Scatter of A into the zeroed panels (the temporary block storage of Sec. 2.3.2).
 template <typename T>
-__global__ void k_zero(T *__restrict__ x, int64_t count) {
+__global__ void k_zero(T *__restrict__ x, int64_t count, const Batch bt) {
+  x += blockIdx.y * bt.lx;
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (; i < count; i += stride) x[i] = T(0);
@@ -113,7 +114,9 @@ __global__ void k_zero(T *__restrict__ x, int64_t count) {
 
 template <typename T>
 __global__ void k_scatter(const double *__restrict__ Ax, const int64_t *__restrict__ amap,
-                          T *__restrict__ Lx, int64_t nnz) {
+                          T *__restrict__ Lx, int64_t nnz, const Batch bt) {
+  Ax += blockIdx.y * bt.ax;
+  Lx += blockIdx.y * bt.lx;
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (; i < nnz; i += stride) Lx[amap[i]] = (T)Ax[i];
@@ -127,7 +130,8 @@ __global__ void __launch_bounds__(THREADS) k_update(const SNode *__restrict__ sn
                                                     const UpdTask *__restrict__ tasks,
                                                     const UpdEntry *__restrict__ ents,
                                                     const int32_t *__restrict__ rel,
-                                                    T *__restrict__ Lx, int64_t toff) {
+                                                    T *__restrict__ Lx, int64_t toff, const Batch bt) {
+  Lx += blockIdx.y * bt.lx;
   __shared__ T acc[NB][NB + 1];  // [col][row]
   __shared__ T As[KCU][NB];
   __shared__ T Bs[KCU][NB];
@@ -197,7 +201,9 @@ template <typename T>
 __global__ void __launch_bounds__(THREADS) k_potrf(const SNode *__restrict__ sn,
                                                    const Int4 *__restrict__ tasks,
                                                    T *__restrict__ Lx, long long *status,
-                                                   int64_t toff) {
+                                                   int64_t toff, const Batch bt) {
+  Lx += blockIdx.y * bt.lx;
+  status += blockIdx.y;
   // The diagonal tile is factored in FP64 whatever the storage type T (for an FP32 factor the
   // pivots and this tile stay accurate; the result is rounded to T once).
   __shared__ double a[NB][NB + 1];                 // [col][row]
@@ -255,7 +261,8 @@ __global__ void __launch_bounds__(THREADS) k_potrf(const SNode *__restrict__ sn,
 template <typename T>
 __global__ void __launch_bounds__(THREADS) k_trsm(const SNode *__restrict__ sn,
                                                   const Int4 *__restrict__ tasks,
-                                                  T *__restrict__ Lx, int64_t toff) {
+                                                  T *__restrict__ Lx, int64_t toff, const Batch bt) {
+  Lx += blockIdx.y * bt.lx;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T(*Ls)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem_raw);           // [col][row], lower
   T(*X)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem_raw) + NB;       // [col][row]
@@ -297,7 +304,8 @@ __global__ void __launch_bounds__(THREADS) k_trsm(const SNode *__restrict__ sn,
 template <typename T>
 __global__ void __launch_bounds__(THREADS) k_gemm(const SNode *__restrict__ sn,
                                                   const Int4 *__restrict__ tasks,
-                                                  T *__restrict__ Lx, int64_t toff) {
+                                                  T *__restrict__ Lx, int64_t toff, const Batch bt) {
+  Lx += blockIdx.y * bt.lx;
   __shared__ T As[KC][NB];
   __shared__ T Bs[KC][NB];
   const Int4 t = tasks[toff + blockIdx.x];
@@ -347,7 +355,9 @@ __global__ void __launch_bounds__(THREADS) k_gemm(const SNode *__restrict__ sn,
 // factor is read in its storage type T and the arithmetic is done in V.
 template <typename V>
 __global__ void k_perm_in(const int32_t *__restrict__ perm, const double *__restrict__ B, int64_t ldb,
-                          V *__restrict__ y, int64_t n, int nrhs) {
+                          V *__restrict__ y, int64_t n, int nrhs, const Batch bt) {
+  B += blockIdx.y * bt.b;
+  y += blockIdx.y * bt.y;
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (; i < n * nrhs; i += stride) {
@@ -357,7 +367,9 @@ __global__ void k_perm_in(const int32_t *__restrict__ perm, const double *__rest
 }
 template <typename V>
 __global__ void k_perm_out(const int32_t *__restrict__ perm, const V *__restrict__ y,
-                           double *__restrict__ X, int64_t ldx, int64_t n, int nrhs) {
+                           double *__restrict__ X, int64_t ldx, int64_t n, int nrhs, const Batch bt) {
+  y += blockIdx.y * bt.y;
+  X += blockIdx.y * bt.x;
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (; i < n * nrhs; i += stride) {
@@ -381,7 +393,9 @@ __global__ void __launch_bounds__(THREADS) k_fgather(const SNode *__restrict__ s
                                                      const UpdEntry *__restrict__ ents,
                                                      const int32_t *__restrict__ rel,
                                                      const T *__restrict__ Lx, V *__restrict__ y,
-                                                     int64_t n, int r0, int nr, int64_t toff) {
+                                                     int64_t n, int r0, int nr, int64_t toff, const Batch bt) {
+  Lx += blockIdx.y * bt.lx;
+  y += blockIdx.y * bt.y;
   __shared__ V acc[MAXRHS][NB];
   __shared__ V part[THREADS][MAXRHS + 1];
   cg::cluster_group cluster = cg::this_cluster();
@@ -461,7 +475,9 @@ __global__ void __launch_bounds__(THREADS) k_bgather(const SNode *__restrict__ s
                                                      const int32_t *__restrict__ rows,
                                                      const Int4 *__restrict__ tasks,
                                                      const T *__restrict__ Lx, V *__restrict__ y,
-                                                     int64_t n, int r0, int nr, int64_t toff) {
+                                                     int64_t n, int r0, int nr, int64_t toff, const Batch bt) {
+  Lx += blockIdx.y * bt.lx;
+  y += blockIdx.y * bt.y;
   const Int4 t = tasks[toff + blockIdx.x];
   const SNode sj = sn[t.a];
   const int c0 = t.b * BG;
@@ -567,7 +583,11 @@ template <typename T, typename V>
 __global__ void __launch_bounds__(THREADS) k_fstep(const SNode *__restrict__ sn,
                                                    const Int4 *__restrict__ tasks,
                                                    const T *__restrict__ Lx, const T *__restrict__ Linv,
-                                                   V *__restrict__ y, int64_t n, int r0, int nr, int64_t toff) {
+                                                   V *__restrict__ y, int64_t n, int r0, int nr, int64_t toff,
+                                                   const Batch bt) {
+  Lx += blockIdx.y * bt.lx;
+  Linv += blockIdx.y * bt.dinv;
+  y += blockIdx.y * bt.y;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   StepSmem<V> &S = *reinterpret_cast<StepSmem<V> *>(smem_raw);
   const Int4 t = tasks[toff + blockIdx.x];
@@ -626,7 +646,11 @@ template <typename T, typename V>
 __global__ void __launch_bounds__(THREADS) k_bstep(const SNode *__restrict__ sn,
                                                    const Int4 *__restrict__ tasks,
                                                    const T *__restrict__ Lx, const T *__restrict__ Linv,
-                                                   V *__restrict__ y, int64_t n, int r0, int nr, int64_t toff) {
+                                                   V *__restrict__ y, int64_t n, int r0, int nr, int64_t toff,
+                                                   const Batch bt) {
+  Lx += blockIdx.y * bt.lx;
+  Linv += blockIdx.y * bt.dinv;
+  y += blockIdx.y * bt.y;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   StepSmem<V> &S = *reinterpret_cast<StepSmem<V> *>(smem_raw);
   const Int4 t = tasks[toff + blockIdx.x];
@@ -685,7 +709,9 @@ template <typename T>
 __global__ void __launch_bounds__(THREADS) k_trtri(const SNode *__restrict__ sn,
                                                    const Int4 *__restrict__ tasks,
                                                    const T *__restrict__ Lx, T *__restrict__ Linv,
-                                                   int64_t toff) {
+                                                   int64_t toff, const Batch bt) {
+  Lx += blockIdx.y * bt.lx;
+  Linv += blockIdx.y * bt.dinv;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double(*a)[NB + 1] = reinterpret_cast<double(*)[NB + 1]>(smem_raw);  // L, [col][row]
   double(*x)[NB + 1] = a + NB;                                          // X, [col][row]
@@ -758,28 +784,30 @@ cudaError_t prepare_solve() {
 
 template <typename T>
 cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, const double *Ax,
-                       T *Lx, T *Linv, long long *status, cudaStream_t st, LaunchTrace *trace) {
+                       T *Lx, T *Linv, long long *status, cudaStream_t st, LaunchTrace *trace, const Batch &bt) {
+  const unsigned nb = (unsigned)bt.count;
   trace_mark(trace, -1, st);
-  k_zero<T><<<grid_for(d.storage, THREADS * 4), THREADS, 0, st>>>(Lx, d.storage);
-  if (d.nnz_a > 0) k_scatter<T><<<grid_for(d.nnz_a, THREADS * 4), THREADS, 0, st>>>(Ax, d.amap, Lx, d.nnz_a);
+  k_zero<T><<<dim3(grid_for(d.storage, THREADS * 4), nb), THREADS, 0, st>>>(Lx, d.storage, bt);
+  if (d.nnz_a > 0)
+    k_scatter<T><<<dim3(grid_for(d.nnz_a, THREADS * 4), nb), THREADS, 0, st>>>(Ax, d.amap, Lx, d.nnz_a, bt);
   trace_mark(trace, K_SCATTER, st);
   for (const Launch &L : launches) {
     const unsigned g = (unsigned)L.count;
     switch (L.kind) {
       case K_UPDATE:
-        k_update<T><<<g, THREADS, 0, st>>>(d.sn, d.upd_tasks, d.upd_entries, d.rel, Lx, L.off);
+        k_update<T><<<dim3(g, nb), THREADS, 0, st>>>(d.sn, d.upd_tasks, d.upd_entries, d.rel, Lx, L.off, bt);
         break;
       case K_POTRF:
-        k_potrf<T><<<g, THREADS, 0, st>>>(d.sn, d.tasks, Lx, status, L.off);
+        k_potrf<T><<<dim3(g, nb), THREADS, 0, st>>>(d.sn, d.tasks, Lx, status, L.off, bt);
         break;
       case K_TRSM:
-        k_trsm<T><<<g, THREADS, trsm_smem<T>(), st>>>(d.sn, d.tasks, Lx, L.off);
+        k_trsm<T><<<dim3(g, nb), THREADS, trsm_smem<T>(), st>>>(d.sn, d.tasks, Lx, L.off, bt);
         break;
       case K_GEMM:
-        k_gemm<T><<<g, THREADS, 0, st>>>(d.sn, d.tasks, Lx, L.off);
+        k_gemm<T><<<dim3(g, nb), THREADS, 0, st>>>(d.sn, d.tasks, Lx, L.off, bt);
         break;
       case K_TRTRI:
-        k_trtri<T><<<g, THREADS, trtri_smem(), st>>>(d.sn, d.tasks, Lx, Linv, L.off);
+        k_trtri<T><<<dim3(g, nb), THREADS, trtri_smem(), st>>>(d.sn, d.tasks, Lx, Linv, L.off, bt);
         break;
       default:
         return cudaErrorInvalidValue;
@@ -791,8 +819,10 @@ cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, co
 
 template <typename T, typename V>
 cudaError_t run_sweeps(const DevPlan &d, const std::vector<Launch> &fwd, const std::vector<Launch> &bwd,
-                       const T *Lx, const T *Linv, int nrhs, V *y, cudaStream_t st, LaunchTrace *trace) {
+                       const T *Lx, const T *Linv, int nrhs, V *y, cudaStream_t st, LaunchTrace *trace,
+                       const Batch &bt) {
   const int64_t n = d.n;
+  const unsigned nb = (unsigned)bt.count;
   for (int r0 = 0; r0 < nrhs; r0 += MAXRHS) {
     const int nr = nrhs - r0 < MAXRHS ? nrhs - r0 : MAXRHS;
     for (const Launch &L : fwd) {
@@ -801,7 +831,7 @@ cudaError_t run_sweeps(const DevPlan &d, const std::vector<Launch> &fwd, const s
         case S_FGATHER: {
           cudaLaunchConfig_t cfg = {};
           cudaLaunchAttribute attr[1];
-          cfg.gridDim = dim3(g * (unsigned)L.cluster, 1, 1);
+          cfg.gridDim = dim3(g * (unsigned)L.cluster, nb, 1);
           cfg.blockDim = dim3(THREADS, 1, 1);
           cfg.dynamicSmemBytes = 0;
           cfg.stream = st;
@@ -812,12 +842,12 @@ cudaError_t run_sweeps(const DevPlan &d, const std::vector<Launch> &fwd, const s
           cfg.attrs = attr;
           cfg.numAttrs = 1;
           cudaError_t e = cudaLaunchKernelEx(&cfg, k_fgather<T, V>, d.sn, d.tasks, d.upd_tasks, d.upd_entries,
-                                             d.rel, Lx, y, n, r0, nr, L.off);
+                                             d.rel, Lx, y, n, r0, nr, L.off, bt);
           if (e != cudaSuccess) return e;
           break;
         }
         case S_FSTEP:
-          k_fstep<T, V><<<g, THREADS, step_smem<V>(), st>>>(d.sn, d.tasks, Lx, Linv, y, n, r0, nr, L.off);
+          k_fstep<T, V><<<dim3(g, nb), THREADS, step_smem<V>(), st>>>(d.sn, d.tasks, Lx, Linv, y, n, r0, nr, L.off, bt);
           break;
         default:
           return cudaErrorInvalidValue;
@@ -828,10 +858,10 @@ cudaError_t run_sweeps(const DevPlan &d, const std::vector<Launch> &fwd, const s
       const unsigned g = (unsigned)L.count;
       switch (L.kind) {
         case S_BGATHER:
-          k_bgather<T, V><<<g, THREADS, 0, st>>>(d.sn, d.rows, d.tasks, Lx, y, n, r0, nr, L.off);
+          k_bgather<T, V><<<dim3(g, nb), THREADS, 0, st>>>(d.sn, d.rows, d.tasks, Lx, y, n, r0, nr, L.off, bt);
           break;
         case S_BSTEP:
-          k_bstep<T, V><<<g, THREADS, step_smem<V>(), st>>>(d.sn, d.tasks, Lx, Linv, y, n, r0, nr, L.off);
+          k_bstep<T, V><<<dim3(g, nb), THREADS, step_smem<V>(), st>>>(d.sn, d.tasks, Lx, Linv, y, n, r0, nr, L.off, bt);
           break;
         default:
           return cudaErrorInvalidValue;
@@ -845,15 +875,16 @@ cudaError_t run_sweeps(const DevPlan &d, const std::vector<Launch> &fwd, const s
 template <typename T>
 cudaError_t run_solve(const DevPlan &d, const std::vector<Launch> &fwd, const std::vector<Launch> &bwd,
                       const T *Lx, const T *Linv, int nrhs, const double *B, int64_t ldb, double *X,
-                      int64_t ldx, double *y, cudaStream_t st, LaunchTrace *trace) {
+                      int64_t ldx, double *y, cudaStream_t st, LaunchTrace *trace, const Batch &bt) {
   const int64_t n = d.n;
+  const unsigned nb = (unsigned)bt.count;
   if (n == 0 || nrhs == 0) return cudaSuccess;
   trace_mark(trace, -1, st);
-  k_perm_in<double><<<grid_for(n * nrhs, THREADS), THREADS, 0, st>>>(d.perm, B, ldb, y, n, nrhs);
+  k_perm_in<double><<<dim3(grid_for(n * nrhs, THREADS), nb), THREADS, 0, st>>>(d.perm, B, ldb, y, n, nrhs, bt);
   trace_mark(trace, S_PERM, st);
-  cudaError_t e = run_sweeps<T, double>(d, fwd, bwd, Lx, Linv, nrhs, y, st, trace);
+  cudaError_t e = run_sweeps<T, double>(d, fwd, bwd, Lx, Linv, nrhs, y, st, trace, bt);
   if (e != cudaSuccess) return e;
-  k_perm_out<double><<<grid_for(n * nrhs, THREADS), THREADS, 0, st>>>(d.perm, y, X, ldx, n, nrhs);
+  k_perm_out<double><<<dim3(grid_for(n * nrhs, THREADS), nb), THREADS, 0, st>>>(d.perm, y, X, ldx, n, nrhs, bt);
   trace_mark(trace, S_PERM, st);
   return cudaGetLastError();
 }
@@ -861,14 +892,14 @@ cudaError_t run_solve(const DevPlan &d, const std::vector<Launch> &fwd, const st
 template <typename V>
 cudaError_t permute_in(const DevPlan &d, int nrhs, const double *B, int64_t ldb, V *y, cudaStream_t st) {
   if (d.n == 0 || nrhs == 0) return cudaSuccess;
-  k_perm_in<V><<<grid_for(d.n * nrhs, THREADS), THREADS, 0, st>>>(d.perm, B, ldb, y, d.n, nrhs);
+  k_perm_in<V><<<grid_for(d.n * nrhs, THREADS), THREADS, 0, st>>>(d.perm, B, ldb, y, d.n, nrhs, Batch());
   return cudaGetLastError();
 }
 
 template <typename V>
 cudaError_t permute_out(const DevPlan &d, int nrhs, const V *y, double *X, int64_t ldx, cudaStream_t st) {
   if (d.n == 0 || nrhs == 0) return cudaSuccess;
-  k_perm_out<V><<<grid_for(d.n * nrhs, THREADS), THREADS, 0, st>>>(d.perm, y, X, ldx, d.n, nrhs);
+  k_perm_out<V><<<grid_for(d.n * nrhs, THREADS), THREADS, 0, st>>>(d.perm, y, X, ldx, d.n, nrhs, Batch());
   return cudaGetLastError();
 }
 
@@ -877,16 +908,21 @@ template cudaError_t prepare_solve<float, float>();
 template cudaError_t prepare_factor<double>();
 template cudaError_t prepare_factor<float>();
 template cudaError_t run_factor<double>(const DevPlan &, const std::vector<Launch> &, const double *,
-                                        double *, double *, long long *, cudaStream_t, LaunchTrace *);
+                                        double *, double *, long long *, cudaStream_t, LaunchTrace *,
+                                        const Batch &);
 template cudaError_t run_factor<float>(const DevPlan &, const std::vector<Launch> &, const double *,
-                                       float *, float *, long long *, cudaStream_t, LaunchTrace *);
+                                       float *, float *, long long *, cudaStream_t, LaunchTrace *,
+                                       const Batch &);
 template cudaError_t run_solve<double>(const DevPlan &, const std::vector<Launch> &,
                                        const std::vector<Launch> &, const double *, const double *, int,
                                        const double *, int64_t, double *, int64_t, double *,
-                                       cudaStream_t, LaunchTrace *);
+                                       cudaStream_t, LaunchTrace *, const Batch &);
 template cudaError_t run_sweeps<float, float>(const DevPlan &, const std::vector<Launch> &,
                                               const std::vector<Launch> &, const float *, const float *, int,
-                                              float *, cudaStream_t, LaunchTrace *);
+                                              float *, cudaStream_t, LaunchTrace *, const Batch &);
+template cudaError_t run_sweeps<double, double>(const DevPlan &, const std::vector<Launch> &,
+                                                const std::vector<Launch> &, const double *, const double *,
+                                                int, double *, cudaStream_t, LaunchTrace *, const Batch &);
 template cudaError_t permute_in<double>(const DevPlan &, int, const double *, int64_t, double *, cudaStream_t);
 template cudaError_t permute_out<double>(const DevPlan &, int, const double *, double *, int64_t, cudaStream_t);
 

@@ -22,6 +22,15 @@ struct DevPlan {
   int64_t storage = 0;
 };
 
+// Several matrices with one pattern (blockIdx.y = matrix): offsets, in elements, from one matrix to
+// the next of the panels (lx), of A's values (ax), of the diagonal-tile inverses (dinv), of the
+// permuted solve block (y) and of the caller's right-hand sides (b) and solutions (x). The
+// default describes a single matrix.
+struct Batch {
+  int32_t count = 1;
+  int64_t lx = 0, ax = 0, dinv = 0, y = 0, b = 0, x = 0;
+};
+
 // Optional per-launch timing: when non-null, an event is recorded before the first launch and
 // after every launch on the same stream; kinds[i] is the Kind of launch i (K_SCATTER for the
 // zero + scatter pair, S_PERM for the permutations of the solve).
@@ -44,19 +53,22 @@ cudaError_t prepare_solve();
 // status: device int64, receives the smallest failing (permuted) column, or stays INT64_MAX.
 template <typename T>
 cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, const double *Ax,
-                       T *Lx, T *Linv, long long *status, cudaStream_t st, LaunchTrace *trace = nullptr);
+                       T *Lx, T *Linv, long long *status, cudaStream_t st, LaunchTrace *trace = nullptr,
+                       const Batch &bt = Batch());
 
 // Solve with nrhs right-hand sides: y = P b, forward sweep, backward sweep, x = P^T y.
 // y: device work array of n * nrhs (ld n); Linv: the diagonal-tile inverses run_factor wrote.
 template <typename T>
 cudaError_t run_solve(const DevPlan &d, const std::vector<Launch> &fwd, const std::vector<Launch> &bwd,
                       const T *Lx, const T *Linv, int nrhs, const double *B, int64_t ldb, double *X,
-                      int64_t ldx, double *y, cudaStream_t st, LaunchTrace *trace = nullptr);
+                      int64_t ldx, double *y, cudaStream_t st, LaunchTrace *trace = nullptr,
+                      const Batch &bt = Batch());
 
 // The forward and backward sweeps alone on a permuted block y (n x nrhs, ld n) of type V.
 template <typename T, typename V>
 cudaError_t run_sweeps(const DevPlan &d, const std::vector<Launch> &fwd, const std::vector<Launch> &bwd,
-                       const T *Lx, const T *Linv, int nrhs, V *y, cudaStream_t st, LaunchTrace *trace = nullptr);
+                       const T *Lx, const T *Linv, int nrhs, V *y, cudaStream_t st, LaunchTrace *trace = nullptr,
+                       const Batch &bt = Batch());
 
 // y = P B and X = P^T y for nrhs columns.
 template <typename V>

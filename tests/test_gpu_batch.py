@@ -1,0 +1,109 @@
+"""GPU parity of batched refactorization (many value sets on one pattern) and of uneven batches
+(a block-diagonal union of different grids analyzed once)."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as w
+from tests.helpers import exports, panels_on_pattern
+
+pytestmark = pytest.mark.gpu
+
+ENTRY_RTOL = 1e-10
+BERR_TOL = 1e-13
+REFINED_BERR = 1e-12
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def test_batch_matches_single_factorizations(torch_cuda):
+    torch = torch_cuda
+    import paper_1705_06575_gb300 as S
+    nb, nrhs = 6, 3
+    M, vals = w.same_pattern_batch(lambda r: w.dd2d9(24, r), nb, 40)
+    stride = M.nnz + 5  # padded rows
+    V = np.zeros((nb, stride))
+    V[:, :M.nnz] = vals
+    s = S.Solver(M.n, M.Ap, M.Ai, M.perm)
+    S.sym_factor_batch(s.h, nb, torch.from_numpy(V).cuda(), stride)
+    rng = np.random.default_rng(1)
+    B = np.stack([w.rhs(M.n, nrhs, rng).T for _ in range(nb)])  # (nb, nrhs, n): row = one RHS
+    Bt = torch.from_numpy(np.ascontiguousarray(B)).cuda()
+    Xt = torch.empty_like(Bt)
+    S.sym_solve_batch(s.h, nb, nrhs, Bt, M.n, nrhs * M.n, Xt, M.n, nrhs * M.n)
+    torch.cuda.synchronize()
+    X = Xt.cpu().numpy()
+    o = oracle.Oracle(M.n, M.Ap, M.Ai, M.perm)
+    sx = exports(s)
+    for b in range(nb):
+        assert oracle.backward_error(M.n, M.Ap, M.Ai, vals[b], B[b].T, X[b].T) <= BERR_TOL
+        o.factor(vals[b])
+        Lb, outside = panels_on_pattern(sx, S.sym_get_batch_factor_host(s.h, b), o.Lp, o.Li)
+        assert outside == 0.0
+        assert np.abs(Lb - o.Lx).max() <= ENTRY_RTOL * np.abs(o.Lx).max()
+    # a single factorization of matrix 4 gives the same panels as the batch
+    single = S.Solver(M.n, M.Ap, M.Ai, M.perm)
+    single.factor(torch.from_numpy(vals[4]).cuda())
+    assert np.array_equal(single.factor_panels(), S.sym_get_batch_factor_host(s.h, 4))
+
+
+def test_batch_reports_each_failing_matrix(torch_cuda):
+    torch = torch_cuda
+    import paper_1705_06575_gb300 as S
+    nb = 5
+    M, vals = w.same_pattern_batch(lambda r: w.laplace2d5(16, r), nb, 7)
+    vals = vals.copy()
+    vals[1, M.Ap[33]] = -1.0
+    vals[3, M.Ap[200]] = -2.0
+    s = S.Solver(M.n, M.Ap, M.Ai, M.perm)
+    with pytest.raises(S.SymError) as e:
+        S.sym_factor_batch(s.h, nb, torch.from_numpy(vals).cuda(), M.nnz)
+    assert e.value.code == S.SYM_ERR_NOT_SPD
+    cols = S.sym_batch_error_columns(s.h, nb)
+    o = oracle.Oracle(M.n, M.Ap, M.Ai, M.perm)
+    for b in range(nb):
+        rc = o.factor(vals[b])
+        assert cols[b] == (o.perm[o.err_col] if rc == oracle.ERR_NOT_SPD else -1)
+    assert cols[0] == -1 and cols[1] >= 0 and cols[3] >= 0
+
+
+def test_mixed_precision_batch(torch_cuda):
+    torch = torch_cuda
+    import paper_1705_06575_gb300 as S
+    nb = 4
+    M, vals = w.same_pattern_batch(lambda r: w.conduct3d(10, r, "star"), nb, 3)
+    s = S.Solver(M.n, M.Ap, M.Ai, M.perm, precision="mixed")
+    S.sym_factor_batch(s.h, nb, torch.from_numpy(vals).cuda(), M.nnz)
+    B = np.stack([w.rhs(M.n, 2, np.random.default_rng(b)).T for b in range(nb)])
+    Bt = torch.from_numpy(np.ascontiguousarray(B)).cuda()
+    Xt = torch.empty_like(Bt)
+    S.sym_solve_batch(s.h, nb, 2, Bt, M.n, 2 * M.n, Xt, M.n, 2 * M.n)
+    torch.cuda.synchronize()
+    X = Xt.cpu().numpy()
+    for b in range(nb):
+        assert oracle.backward_error(M.n, M.Ap, M.Ai, vals[b], B[b].T, X[b].T) <= REFINED_BERR
+
+
+def test_uneven_batch_as_block_diagonal(torch_cuda):
+    torch = torch_cuda
+    import paper_1705_06575_gb300 as S
+    rng = np.random.default_rng(11)
+    mats, sides = w.uneven_grid_batch(7, rng, lo=12, hi=70)
+    U = w.block_diagonal(mats)
+    s = S.Solver(U.n, U.Ap, U.Ai, U.perm)
+    s.factor(torch.from_numpy(U.Ax).cuda())
+    b = w.rhs(U.n, 1, np.random.default_rng(2))[:, 0]
+    x = s.solve(torch.from_numpy(b).cuda())
+    torch.cuda.synchronize()
+    x = x.cpu().numpy()
+    off = 0
+    for M in mats:
+        seg = slice(off, off + M.n)
+        assert oracle.backward_error(M.n, M.Ap, M.Ai, M.Ax, b[seg], x[seg]) <= BERR_TOL
+        off += M.n

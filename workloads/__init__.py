@@ -287,6 +287,44 @@ def csc_to_dense(M):
     return A
 
 
+def block_diagonal(mats):
+    """One matrix whose diagonal blocks are the given matrices (an uneven batch). Its ordering
+    places each block's own ordering in its own index range."""
+    n = sum(M.n for M in mats)
+    Ap = [np.zeros(1, dtype=np.int64)]
+    Ai, Ax, perm = [], [], []
+    off_n = 0
+    off_nz = 0
+    for M in mats:
+        Ap.append(M.Ap[1:] + off_nz)
+        Ai.append(M.Ai.astype(np.int64) + off_n)
+        Ax.append(M.Ax)
+        perm.append((M.perm if M.perm is not None else np.arange(M.n)).astype(np.int64) + off_n)
+        off_n += M.n
+        off_nz += M.nnz
+    return Matrix(n, np.concatenate(Ap), np.concatenate(Ai), np.concatenate(Ax), np.concatenate(perm),
+                  name=f"blockdiag_{len(mats)}")
+
+
+def uneven_grid_batch(count, rng, lo=32, hi=256):
+    """Uneven batch of 2D 5-point grids with sides uniform in lo..hi (values as laplace2d5)."""
+    sides = rng.integers(lo, hi + 1, size=count)
+    return [laplace2d5(int(s), rng) for s in sides], sides
+
+
+def same_pattern_batch(maker, count, seed):
+    """count value sets on one pattern: maker(rng) must build the same pattern for every rng.
+    Returns the first matrix and a (count, nnz) array of values."""
+    first = maker(np.random.default_rng(seed))
+    vals = np.empty((count, first.nnz))
+    vals[0] = first.Ax
+    for b in range(1, count):
+        M = maker(np.random.default_rng(seed + b))
+        assert M.nnz == first.nnz
+        vals[b] = M.Ax
+    return first, vals
+
+
 def cfg(name, matrix_index=0):
     """The named workloads with their seeds (1000 * config index + matrix index)."""
     if name == "laplace2d5_64":
