@@ -63,6 +63,10 @@ def _load():
         lib.orc_factor_residual_with.restype = ct.c_double
         lib.orc_backward_error.argtypes = [i64, P, P, P, i64, P, P]
         lib.orc_backward_error.restype = ct.c_double
+        lib.orc_reach.argtypes = [P, i64, P, P]
+        lib.orc_reach.restype = i64
+        lib.orc_sparse_lsolve.argtypes = [P, i64, P, i64, P, P, P]
+        lib.orc_sparse_lsolve.restype = None
         lib.orc_row_patterns_check.argtypes = [P]
         lib.orc_row_patterns_check.restype = ct.c_int
         for name, rt in [("n", i64), ("nnzL", i64), ("nfsn", i32), ("nsn", i32), ("nsrows", i64),
@@ -178,6 +182,23 @@ class Oracle:
     def factor_residual(self, Ax=None, kmax=0):
         Ax = self._Ax if Ax is None else np.ascontiguousarray(Ax, dtype=np.float64)
         return self._lib.orc_factor_residual(self._h, _ptr(Ax), int(kmax))
+
+    def reach(self, beta):
+        """Reach_L(beta) (permuted numbering) in a topological order (reverse DFS finishing)."""
+        beta = np.ascontiguousarray(beta, dtype=np.int32)
+        out = np.zeros(self.n, dtype=np.int32)
+        nr = self._lib.orc_reach(self._h, beta.size, _ptr(beta), _ptr(out))
+        return out[:nr].copy()
+
+    def sparse_lsolve(self, beta, bvals, reach=None):
+        """Solve L x = b for b with entries bvals at beta (permuted numbering); returns (reach,
+        dense x with zeros outside the reach)."""
+        beta = np.ascontiguousarray(beta, dtype=np.int32)
+        bvals = np.ascontiguousarray(bvals, dtype=np.float64)
+        r = self.reach(beta) if reach is None else np.ascontiguousarray(reach, dtype=np.int32)
+        x = np.zeros(self.n)
+        self._lib.orc_sparse_lsolve(self._h, r.size, _ptr(r), beta.size, _ptr(beta), _ptr(bvals), _ptr(x))
+        return r, x
 
     def factor_residual_with(self, Ax, Lx, kmax=0):
         """||L L^T - C||_F / ||C||_F for values Lx given on this oracle's pattern."""

@@ -708,6 +708,59 @@ double orc_backward_error(int64_t n, const int64_t *Ap, const int32_t *Ai, const
   return worst;
 }
 
+/* Sparse right-hand side (Sec. 1.1, Sec. 3.1): the nonzero pattern of the solution of L x = b is
+ * Reach_L(beta), the nodes reachable in the dependence graph DG_L (edge j -> i for L_ij != 0)
+ * from beta = {i : b_i != 0}. Depth-first search from every node of beta; the reverse of the
+ * finishing order is a topological order. beta and the result are in the permuted numbering.
+ * Returns the reach size; reach must hold n entries. */
+int64_t orc_reach(const orc_t *o, int64_t nb, const int32_t *beta, int32_t *reach) {
+  int64_t n = o->n;
+  uint8_t *mark = xcalloc(n, 1);
+  int32_t *stack = xcalloc(n, sizeof(int32_t));
+  int64_t *next = xcalloc(n, sizeof(int64_t)); /* next pattern position to explore per node */
+  int32_t *finish = xcalloc(n, sizeof(int32_t));
+  int64_t nf = 0;
+  for (int64_t t = 0; t < nb; ++t) {
+    int32_t s = beta[t];
+    if (mark[s]) continue;
+    int64_t top = 0;
+    stack[top++] = s;
+    mark[s] = 1;
+    next[s] = o->Lp[s] + 1; /* skip the diagonal */
+    while (top > 0) {
+      int32_t j = stack[top - 1];
+      if (next[j] < o->Lp[j + 1]) {
+        int32_t i = o->Li[next[j]++];
+        if (!mark[i]) {
+          mark[i] = 1;
+          next[i] = o->Lp[i] + 1;
+          stack[top++] = i;
+        }
+      } else {
+        --top;
+        finish[nf++] = j;
+      }
+    }
+  }
+  for (int64_t t = 0; t < nf; ++t) reach[t] = finish[nf - 1 - t];
+  free(mark); free(stack); free(next); free(finish);
+  return nf;
+}
+
+/* Numeric sparse lower solve over a reach set in topological order (the decoupled code of
+ * Sec. 1.1): x = b on beta, zero elsewhere; for j in reach: x_j /= L_jj; x_i -= L_ij x_j for the
+ * rows i of column j. x is a dense work vector of n entries (permuted numbering). */
+void orc_sparse_lsolve(const orc_t *o, int64_t nr, const int32_t *reach, int64_t nb, const int32_t *beta,
+                       const double *bvals, double *x) {
+  for (int64_t t = 0; t < nr; ++t) x[reach[t]] = 0.0;
+  for (int64_t t = 0; t < nb; ++t) x[beta[t]] = bvals[t];
+  for (int64_t t = 0; t < nr; ++t) {
+    int32_t j = reach[t];
+    x[j] /= o->Lx[o->Lp[j]];
+    for (int64_t p = o->Lp[j] + 1; p < o->Lp[j + 1]; ++p) x[o->Li[p]] -= o->Lx[p] * x[j];
+  }
+}
+
 /* Sizes and read-only views for the Python wrapper. */
 int64_t orc_n(const orc_t *o) { return o->n; }
 int64_t orc_nnzL(const orc_t *o) { return o->Lp[o->n]; }

@@ -365,3 +365,42 @@ def test_planted_mistakes_are_caught():
     dropped[off[10]] = 0.0
     for bad in (wrong_sign, dropped):
         assert o.factor_residual_with(M.Ax, bad) > 1e-4
+
+
+def test_reach_set_brute_force_and_topological_order():
+    """Reach_L(beta) equals the closure of beta under the edges j -> i (L_ij != 0), computed by
+    boolean matrix powers, and the returned order is topological (every edge goes forward)."""
+    rng = np.random.default_rng(51)
+    for trial in range(6):
+        M = w.random_spd_pattern(60, 0.04 + 0.02 * trial, rng)
+        o = oracle.Oracle(M.n, M.Ap, M.Ai, rng.permutation(60).astype(np.int32))
+        G = oracle_pattern(o).astype(np.int64)
+        np.fill_diagonal(G, 0)
+        beta = rng.choice(60, size=3, replace=False).astype(np.int32)
+        v = np.zeros(60, dtype=np.int64)
+        v[beta] = 1
+        for _ in range(60):  # closure under x -> G x (column j reaches rows of column j)
+            v = np.minimum(1, v + G @ v)
+        r = o.reach(beta)
+        assert set(r.tolist()) == set(np.nonzero(v)[0].tolist())
+        pos = {int(j): t for t, j in enumerate(r)}
+        for j in r:
+            for i in np.nonzero(G[:, j])[0]:
+                assert pos[int(i)] > pos[int(j)]
+
+
+def test_sparse_lower_solve_matches_dense_triangular_solve():
+    rng = np.random.default_rng(52)
+    M = w.laplace2d5(20, rng)
+    o = oracle.Oracle(M.n, M.Ap, M.Ai, M.perm)
+    o.factor(M.Ax)
+    L = o.L_dense()
+    beta = rng.choice(M.n, size=4, replace=False).astype(np.int32)
+    bvals = rng.standard_normal(4)
+    r, x = o.sparse_lsolve(beta, bvals)
+    b = np.zeros(M.n)
+    b[beta] = bvals
+    ref = np.linalg.solve(L, b)
+    assert np.abs(x - ref).max() <= 1e-13 * np.abs(ref).max()
+    outside = np.setdiff1d(np.arange(M.n), r)
+    assert np.all(ref[outside] == 0.0)  # the solution vanishes outside the reach set
