@@ -287,6 +287,36 @@ def bench_batched(S, torch, args, stream, barrier, world):
             "definition": "512 x (factor + 1-RHS solve) of the 128^2 9-point pattern per step"}
 
 
+def bench_sparse_rhs(S, torch, s, M, args, stream):
+    """Forward solve L y = P b for sparse b over the reach set (VI-Prune + VS-Block) on the
+    benchmark matrix: b = one column of A (a local source) and b with 1% random nonzeros, each
+    against the same solve for a full b (every supernode visited, i.e. no pruning)."""
+    rng = np.random.default_rng(77)
+    j = M.n // 3
+    cases = {"column_of_A": M.Ai[M.Ap[j]:M.Ap[j + 1]].astype(np.int32),
+             "random_1pct": rng.choice(M.n, size=M.n // 100, replace=False).astype(np.int32),
+             "full": np.arange(M.n, dtype=np.int32)}
+    out = {}
+    for name, bidx in cases.items():
+        r = S.Reach(s.h, bidx)
+        bv = torch.from_numpy(rng.standard_normal(bidx.size)).cuda()
+        xv = torch.empty(r.size(), dtype=torch.float64, device="cuda")
+        for _ in range(args.warmup):
+            r.solve(bv, xv)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            r.solve(bv, xv)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[name] = {"nnz_b": int(bidx.size), "reach_columns": r.size(), "ms": e0.elapsed_time(e1) / args.steps}
+        r.close()
+    for name in ("column_of_A", "random_1pct"):
+        out[name]["speedup_vs_full"] = out["full"]["ms"] / out[name]["ms"]
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -406,6 +436,7 @@ def run_ours(args):
 
     variants = {}
     if not args.no_variants:
+        variants["sparse_rhs_forward"] = bench_sparse_rhs(S, torch, s, M, args, stream)
         variants["mixed_fp32_pcg"] = bench_mixed(S, torch, M, B, info.flops, args, stream, barrier, world)
         if args.batch > 0:
             variants["batched_512x_dd2d9_128"] = bench_batched(S, torch, args, stream, barrier, world)

@@ -201,6 +201,33 @@ int sym_set_refinement(sym_handle h, double tol, int32_t max_iter);
  * reached above tolerance. */
 int sym_refinement_info(sym_handle h, int32_t *iterations, double *backward_error);
 
+/* Sparse right-hand sides (Sec. 1.1 and Sec. 3.1 of the paper: decoupled sparse triangular
+ * solve over the reach-set, with VI-Prune and VS-Block). For L y = P b with b nonzero only at
+ * bidx (nnzb distinct indices, caller's numbering, host), sym_reach_analyze computes once per
+ * pattern of b the set Reach_L(beta) of columns where y can be nonzero (the etree paths from the
+ * nonzeros up) and a forward-solve schedule pruned to the supernodes holding them and to their
+ * reached descendants. The reach handle depends on the pattern only: it stays valid across
+ * refactorizations of its sym_handle, and must be freed before it. On a SYM_FLAG_HOST_ONLY handle
+ * the reach is computed but cannot be solved with. Errors: SYM_ERR_INVALID for an index out of
+ * range or repeated. */
+typedef struct sym_reach_s *sym_reach;
+int sym_reach_analyze(sym_handle h, int64_t nnzb, const int32_t *bidx, sym_reach *out);
+
+/* Number of reached columns, and the reached columns in solve order (caller's numbering). */
+int64_t sym_reach_size(sym_reach r);
+int sym_reach_indices(sym_reach r, int32_t *idx);
+
+/* Integer arrays of the reach set for checks: what = 0: reached columns (permuted numbering,
+ * increasing); what = 1: reached supernodes. Returns the count; out may be NULL. */
+int64_t sym_reach_export(sym_reach r, int32_t what, void *out);
+
+/* Forward solve L y = P b for the sparse b: bvals (DEVICE, nnzb values in the order of bidx),
+ * xvals (DEVICE, sym_reach_size values in the order of sym_reach_indices). Needs an FP64 factor
+ * of the handle; only the reached supernodes are visited. */
+int sym_solve_lower_sparse(sym_handle h, sym_reach r, const double *bvals, double *xvals);
+
+void sym_reach_free(sym_reach r);
+
 /* Statistics of the analyzed pattern. */
 int sym_info(sym_handle h, sym_stats *s);
 

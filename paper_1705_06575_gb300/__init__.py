@@ -22,7 +22,7 @@ __all__ = [
     "sym_last_error_column", "sym_get_factor_host", "sym_export", "sym_free", "load", "Solver",
     "EXPORTS", "sym_profile", "sym_profile_read", "sym_fma_peak", "sym_solve_host_ptr", "KINDS",
     "sym_solve_multi_noalloc", "sym_set_refinement", "sym_refinement_info", "sym_factor_batch",
-    "sym_batch_error_columns", "sym_solve_batch", "sym_get_batch_factor_host",
+    "sym_batch_error_columns", "sym_solve_batch", "sym_get_batch_factor_host", "Reach",
 ]
 
 SYM_OK = 0
@@ -114,6 +114,12 @@ def load():
             "sym_solve_multi_noalloc": ([P, i32, P, i64, P, i64], I),
             "sym_set_refinement": ([P, ct.c_double, i32], I),
             "sym_factor_batch": ([P, i32, P, i64], I),
+            "sym_reach_analyze": ([P, i64, P, ct.POINTER(P)], I),
+            "sym_reach_size": ([P], i64),
+            "sym_reach_indices": ([P, P], I),
+            "sym_reach_export": ([P, i32, P], i64),
+            "sym_solve_lower_sparse": ([P, P, P, P], I),
+            "sym_reach_free": ([P], None),
             "sym_batch_error_columns": ([P, P], I),
             "sym_solve_batch": ([P, i32, i32, P, i64, i64, P, i64, i64], I),
             "sym_get_batch_factor_host": ([P, i32, P], I),
@@ -282,6 +288,49 @@ def sym_get_batch_factor_host(h, index):
     out = np.zeros(st.storage_l, dtype=np.float64)
     _check(load().sym_get_batch_factor_host(h, int(index), out.ctypes.data))
     return out
+
+
+class Reach:
+    """Reach set of a sparse right-hand-side pattern (owning wrapper of sym_reach)."""
+
+    def __init__(self, h, bidx):
+        self.h = h
+        self.bidx = np.ascontiguousarray(bidx, dtype=np.int32)
+        r = ct.c_void_p()
+        _check(load().sym_reach_analyze(h, self.bidx.size, self.bidx.ctypes.data, ct.byref(r)))
+        self.r = r
+
+    def size(self):
+        return _check(load().sym_reach_size(self.r))
+
+    def indices(self):
+        out = np.zeros(self.size(), dtype=np.int32)
+        if out.size:
+            _check(load().sym_reach_indices(self.r, out.ctypes.data))
+        return out
+
+    def export(self, what):
+        lib = load()
+        cnt = _check(lib.sym_reach_export(self.r, int(what), None))
+        out = np.zeros(cnt, dtype=np.int32)
+        if cnt:
+            _check(lib.sym_reach_export(self.r, int(what), out.ctypes.data))
+        return out
+
+    def solve(self, bvals, xvals):
+        """Device tensors: bvals (len(bidx)), xvals (size())."""
+        return _check(load().sym_solve_lower_sparse(self.h, self.r, _dptr(bvals), _dptr(xvals)))
+
+    def close(self):
+        if self.r:
+            load().sym_reach_free(self.r)
+            self.r = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def sym_info(h):

@@ -9,6 +9,7 @@
 
 #include "kernels.h"
 #include "plan.h"
+#include "reach.h"
 #include "refine.h"
 #include "sym.h"
 
@@ -866,6 +867,115 @@ int sym_profile_read(sym_handle h, int32_t kind, double *ms, int64_t *launches, 
   if (launches) *launches = h->prof_launches[kind];
   if (flops) *flops = h->prof_flops[kind];
   return SYM_OK;
+}
+
+}  // extern "C"
+
+struct sym_reach_s {
+  sym_handle h = nullptr;
+  sym::Reach r;
+  sym::DevPlan dp;
+  void *d_pbeta = nullptr, *d_cols = nullptr, *d_snodes = nullptr, *d_ut = nullptr, *d_ue = nullptr,
+       *d_tasks = nullptr;
+};
+
+namespace {
+void reach_release(sym_reach_s *r) {
+  void *p[] = {r->d_pbeta, r->d_cols, r->d_snodes, r->d_ut, r->d_ue, r->d_tasks};
+  for (void *q : p)
+    if (q) cudaFree(q);
+}
+}  // namespace
+
+extern "C" {
+
+int sym_reach_analyze(sym_handle h, int64_t nnzb, const int32_t *bidx, sym_reach *out) {
+  if (!out) return fail(SYM_ERR_INVALID, "null output");
+  *out = nullptr;
+  if (!h) return fail(SYM_ERR_INVALID, "null handle");
+  int rc = h->host_only ? SYM_OK : check_device(h);
+  if (rc) return rc;
+  if (nnzb < 0 || (nnzb > 0 && !bidx)) return fail(SYM_ERR_INVALID, "bad right-hand side pattern");
+  sym_reach_s *r = new (std::nothrow) sym_reach_s();
+  if (!r) return fail(SYM_ERR_OOM, "host allocation");
+  r->h = h;
+  std::string err;
+  try {
+    rc = sym::build_reach(h->plan, nnzb, bidx, r->r, err);
+  } catch (const std::bad_alloc &) {
+    rc = SYM_ERR_OOM;
+    err = "host allocation";
+  }
+  if (rc) {
+    delete r;
+    return fail(rc, err);
+  }
+  if (h->host_only) {  // inspection only: the reach can be exported but not solved with
+    *out = r;
+    return SYM_OK;
+  }
+  int64_t bytes = 0;
+  rc = upload(r->r.pbeta, &r->d_pbeta, bytes);
+  if (!rc) rc = upload(r->r.cols, &r->d_cols, bytes);
+  if (!rc) rc = upload(r->r.snodes, &r->d_snodes, bytes);
+  if (!rc) rc = upload(r->r.upd_tasks, &r->d_ut, bytes);
+  if (!rc) rc = upload(r->r.upd_entries, &r->d_ue, bytes);
+  if (!rc) rc = upload(r->r.tasks, &r->d_tasks, bytes);
+  if (rc) {
+    reach_release(r);
+    delete r;
+    return rc;
+  }
+  r->dp = h->dp;
+  r->dp.upd_tasks = (const sym::UpdTask *)r->d_ut;
+  r->dp.upd_entries = (const sym::UpdEntry *)r->d_ue;
+  r->dp.tasks = (const sym::Int4 *)r->d_tasks;
+  *out = r;
+  return SYM_OK;
+}
+
+int64_t sym_reach_size(sym_reach r) { return r ? (int64_t)r->r.cols.size() : fail(SYM_ERR_INVALID, "null reach"); }
+
+int sym_reach_indices(sym_reach r, int32_t *idx) {
+  if (!r || !idx) return fail(SYM_ERR_INVALID, "null argument");
+  const auto &perm = r->h->plan.perm;
+  for (size_t t = 0; t < r->r.cols.size(); ++t) idx[t] = perm[r->r.cols[t]];
+  return SYM_OK;
+}
+
+int64_t sym_reach_export(sym_reach r, int32_t what, void *out) {
+  if (!r) return fail(SYM_ERR_INVALID, "null reach");
+  const std::vector<int32_t> *v = what == 0 ? &r->r.cols : what == 1 ? &r->r.snodes : nullptr;
+  if (!v) return fail(SYM_ERR_INVALID, "unknown item");
+  if (out && !v->empty()) std::memcpy(out, v->data(), v->size() * sizeof(int32_t));
+  return (int64_t)v->size();
+}
+
+int sym_solve_lower_sparse(sym_handle h, sym_reach r, const double *bvals, double *xvals) {
+  int rc = check_device(h);
+  if (rc) return rc;
+  if (!r || r->h != h) return fail(SYM_ERR_INVALID, "reach set of another handle");
+  if (!h->factored) return fail(SYM_ERR_STATE, "no successful factorization to solve with");
+  if (h->precision != SYM_PREC_FP64) return fail(SYM_ERR_STATE, "the sparse solve needs an FP64 factor");
+  if ((!bvals && !r->r.pbeta.empty()) || (!xvals && !r->r.cols.empty())) return fail(SYM_ERR_INVALID, "null vector");
+  if (!h->solve_prepared) {
+    CUDA_TRY((sym::prepare_solve<double, double>()), "solve set-up");
+    h->solve_prepared = true;
+  }
+  rc = ensure_y(h, h->plan.n);
+  if (rc) return rc;
+  CUDA_TRY(sym::run_sparse_lower(r->dp, r->r.fwd, h->d_Lx, h->d_Linv, (const int32_t *)r->d_snodes,
+                                 (int64_t)r->r.snodes.size(), (const int32_t *)r->d_pbeta, bvals,
+                                 (int64_t)r->r.pbeta.size(), (const int32_t *)r->d_cols, (int64_t)r->r.cols.size(),
+                                 h->d_y, xvals, h->stream),
+           "sparse solve");
+  return SYM_OK;
+}
+
+void sym_reach_free(sym_reach r) {
+  if (!r) return;
+  reach_release(r);
+  delete r;
 }
 
 const char *sym_error_string(int code) {

@@ -773,6 +773,23 @@ cudaError_t prepare_factor() {
   return cudaFuncSetAttribute(k_trtri<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trtri_smem());
 }
 
+// Sparse right-hand side: zero the columns of the reached supernodes, scatter b, gather x.
+__global__ void k_reach_zero(const SNode *__restrict__ sn, const int32_t *__restrict__ snodes,
+                             double *__restrict__ y) {
+  const SNode s = sn[snodes[blockIdx.x]];
+  for (int c = threadIdx.x; c < s.ncols; c += blockDim.x) y[s.first + c] = 0.0;
+}
+__global__ void k_reach_scatter(const int32_t *__restrict__ pbeta, const double *__restrict__ bvals, int64_t nb,
+                                double *__restrict__ y) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < nb) y[pbeta[t]] = bvals[t];
+}
+__global__ void k_reach_gather(const int32_t *__restrict__ cols, int64_t nr, const double *__restrict__ y,
+                               double *__restrict__ x) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < nr) x[t] = y[cols[t]];
+}
+
 template <typename T, typename V>
 cudaError_t prepare_solve() {
   cudaError_t e = cudaFuncSetAttribute(k_fstep<T, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)step_smem<V>());
@@ -886,6 +903,19 @@ cudaError_t run_solve(const DevPlan &d, const std::vector<Launch> &fwd, const st
   if (e != cudaSuccess) return e;
   k_perm_out<double><<<dim3(grid_for(n * nrhs, THREADS), nb), THREADS, 0, st>>>(d.perm, y, X, ldx, n, nrhs, bt);
   trace_mark(trace, S_PERM, st);
+  return cudaGetLastError();
+}
+
+cudaError_t run_sparse_lower(const DevPlan &d, const std::vector<Launch> &fwd, const double *Lx,
+                             const double *Linv, const int32_t *snodes, int64_t nsn, const int32_t *pbeta,
+                             const double *bvals, int64_t nb, const int32_t *cols, int64_t nr, double *y,
+                             double *x, cudaStream_t st) {
+  if (nsn > 0) k_reach_zero<<<(unsigned)nsn, 128, 0, st>>>(d.sn, snodes, y);
+  if (nb > 0) k_reach_scatter<<<(unsigned)((nb + THREADS - 1) / THREADS), THREADS, 0, st>>>(pbeta, bvals, nb, y);
+  static const std::vector<Launch> none;
+  cudaError_t e = run_sweeps<double, double>(d, fwd, none, Lx, Linv, 1, y, st, nullptr, Batch());
+  if (e != cudaSuccess) return e;
+  if (nr > 0) k_reach_gather<<<(unsigned)((nr + THREADS - 1) / THREADS), THREADS, 0, st>>>(cols, nr, y, x);
   return cudaGetLastError();
 }
 

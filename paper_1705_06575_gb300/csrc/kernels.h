@@ -70,6 +70,14 @@ cudaError_t run_sweeps(const DevPlan &d, const std::vector<Launch> &fwd, const s
                        const T *Lx, const T *Linv, int nrhs, V *y, cudaStream_t st, LaunchTrace *trace = nullptr,
                        const Batch &bt = Batch());
 
+// Forward solve L y = P b for a sparse b on a pruned schedule: zero the reached supernodes'
+// columns of y, scatter b (permuted positions pbeta), run the pruned forward sweep, gather the
+// nr reached columns into x.
+cudaError_t run_sparse_lower(const DevPlan &d, const std::vector<Launch> &fwd, const double *Lx,
+                             const double *Linv, const int32_t *snodes, int64_t nsn, const int32_t *pbeta,
+                             const double *bvals, int64_t nb, const int32_t *cols, int64_t nr, double *y,
+                             double *x, cudaStream_t st);
+
 // y = P B and X = P^T y for nrhs columns.
 template <typename V>
 cudaError_t permute_in(const DevPlan &d, int nrhs, const double *B, int64_t ldb, V *y, cudaStream_t st);

@@ -143,3 +143,38 @@ def test_plan_sizes_cfg2_scale():
     assert i.nnz_l == 156727345
     assert abs(i.flops - 4.15e11) / 4.15e11 < 0.01
     assert i.max_ncols == 6080 and i.nlevels == 20
+
+
+@pytest.mark.parametrize("maker,nb", [
+    (lambda: w.cfg("laplace2d5_64"), 5),
+    (lambda: w.conduct3d(12, np.random.default_rng(3), "star"), 20),
+    (lambda: w.random_spd_pattern(700, 0.005, np.random.default_rng(4)), 1),
+    (lambda: w.random_spd_pattern(300, 0.02, np.random.default_rng(5)), 40),
+])
+def test_reach_set_bit_exact(maker, nb):
+    """The library's reach of a sparse right-hand side (etree paths) equals the oracle's
+    depth-first search of the dependence graph of L, as sets of permuted columns."""
+    M = maker()
+    rng = np.random.default_rng(nb)
+    bidx = rng.choice(M.n, size=nb, replace=False).astype(np.int32)
+    s = S.Solver(M.n, M.Ap, M.Ai, M.perm, host_only=True)
+    r = S.Reach(s.h, bidx)
+    o = oracle.Oracle(M.n, M.Ap, M.Ai, M.perm)
+    iperm = np.empty(M.n, dtype=np.int64)
+    iperm[o.perm] = np.arange(M.n)
+    ref = np.sort(o.reach(iperm[bidx].astype(np.int32)))
+    cols = r.export(0)
+    assert np.array_equal(cols, ref)
+    assert np.array_equal(r.indices(), o.perm[ref])
+    sup = s.export("super")
+    held = np.unique(np.searchsorted(sup, cols, side="right") - 1)
+    assert np.array_equal(r.export(1), held)
+    r.close()
+
+
+def test_reach_rejects_bad_patterns():
+    M = w.laplace2d5(10, np.random.default_rng(0))
+    s = S.Solver(M.n, M.Ap, M.Ai, M.perm, host_only=True)
+    for bad in ([M.n], [-1], [3, 3]):
+        with pytest.raises(S.SymError):
+            S.Reach(s.h, np.array(bad))
