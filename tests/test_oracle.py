@@ -404,3 +404,29 @@ def test_sparse_lower_solve_matches_dense_triangular_solve():
     assert np.abs(x - ref).max() <= 1e-13 * np.abs(ref).max()
     outside = np.setdiff1d(np.arange(M.n), r)
     assert np.all(ref[outside] == 0.0)  # the solution vanishes outside the reach set
+
+
+def test_mlp_gradient_matches_finite_differences():
+    """The reference MLP's chain-rule gradient agrees with central differences of its loss."""
+    from oracle import mlp
+    rng = np.random.default_rng(61)
+    nin, h, N = 5, 7, 23
+    theta = rng.standard_normal(mlp.nparams(nin, h)) * 0.5
+    X = rng.standard_normal((N, nin))
+    t = rng.standard_normal(N)
+    g = mlp.gradient(theta, X, t, nin, h)
+    eps = 1e-6
+    fd = np.empty_like(theta)
+    for i in range(theta.size):
+        tp, tm = theta.copy(), theta.copy()
+        tp[i] += eps
+        tm[i] -= eps
+        fd[i] = (mlp.loss(tp, X, t, nin, h) - mlp.loss(tm, X, t, nin, h)) / (2 * eps)
+    assert np.abs(g - fd).max() <= 1e-6 * max(1.0, np.abs(fd).max())
+    # a planted mistake (dropping the ReLU mask of the first layer) is detected
+    W1, b1, W2, b2, w3, b3 = mlp.unpack(theta, nin, h)
+    y, (Xc, z1, h1, z2, h2) = mlp.forward(theta, X, nin, h)
+    dy = 2.0 * (y - t) / N
+    dz2 = np.outer(dy, w3) * (z2 > 0)
+    wrong_dW1 = (dz2 @ W2).T @ X  # no mask
+    assert np.abs(wrong_dW1.ravel() - g[:h * nin]).max() > 1e-6 or np.all(z1 > 0)
