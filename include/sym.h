@@ -91,6 +91,10 @@ typedef struct {
   int64_t nlaunch_solve;    /* kernel launches per sym_solve */
   double analyze_seconds;   /* host time of the inspector */
   int64_t device_bytes;     /* device memory held by the handle */
+  int64_t upd_tasks;        /* tiles receiving descendant updates */
+  int64_t upd_entries;      /* (tile, descendant) update entries */
+  int64_t dense_tasks;      /* POTRF + TRSM + GEMM + inverse tile tasks */
+  double exec_flops;        /* factor flops the kernels execute (explicit zeros included) */
 } sym_stats;
 
 /* Fill *opt with the defaults (SYM_ORDER_GIVEN with a NULL perm means natural order). */
@@ -227,6 +231,30 @@ int64_t sym_reach_export(sym_reach r, int32_t what, void *out);
 int sym_solve_lower_sparse(sym_handle h, sym_reach r, const double *bvals, double *xvals);
 
 void sym_reach_free(sym_reach r);
+
+/* Cost model network (this library's addition for the learned schedule; the paper tunes its
+ * thresholds by hand, Sec. 2.4 and Sec. 4.2). A multilayer perceptron
+ *   y = w3 . relu(W2 relu(W1 x + b1) + b2) + b3
+ * with nin inputs and two hidden layers of `hidden` units, FP32, trained on the GPU by its own
+ * forward, backward and Adam kernels on the mean squared error. Parameters are one flat vector:
+ * W1 (hidden x nin, row-major), b1, W2 (hidden x hidden), b2, w3, b3. Row-major inputs X
+ * (nrows x nin) and targets t (nrows) are DEVICE pointers; parameter and gradient copies are
+ * host arrays. Initial weights are uniform in +-1/sqrt(fan-in) from a splitmix64 counter
+ * stream of seed. Calls run on the legacy default stream and wait for their work. */
+typedef struct sym_mlp_s *sym_mlp;
+int sym_mlp_create(int32_t nin, int32_t hidden, uint64_t seed, sym_mlp *out);
+int64_t sym_mlp_nparams(sym_mlp m);
+int sym_mlp_set_params(sym_mlp m, const float *theta);
+int sym_mlp_get_params(sym_mlp m, float *theta);
+/* y (DEVICE, nrows) = network(X). */
+int sym_mlp_predict(sym_mlp m, int64_t nrows, const float *X, float *y);
+/* Gradient of the loss mean((y - t)^2) with respect to the parameters (host copy, may be
+ * NULL) and the loss (host, may be NULL), at the current parameters. */
+int sym_mlp_gradient(sym_mlp m, int64_t nrows, const float *X, const float *t, float *grad, float *loss);
+/* steps full-batch Adam steps (beta1 0.9, beta2 0.999, eps 1e-8) at learning rate lr; the
+ * final loss into *loss (host, may be NULL). */
+int sym_mlp_train(sym_mlp m, int64_t nrows, const float *X, const float *t, int32_t steps, float lr, float *loss);
+void sym_mlp_free(sym_mlp m);
 
 /* Statistics of the analyzed pattern. */
 int sym_info(sym_handle h, sym_stats *s);

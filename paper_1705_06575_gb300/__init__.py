@@ -22,7 +22,7 @@ __all__ = [
     "sym_last_error_column", "sym_get_factor_host", "sym_export", "sym_free", "load", "Solver",
     "EXPORTS", "sym_profile", "sym_profile_read", "sym_fma_peak", "sym_solve_host_ptr", "KINDS",
     "sym_solve_multi_noalloc", "sym_set_refinement", "sym_refinement_info", "sym_factor_batch",
-    "sym_batch_error_columns", "sym_solve_batch", "sym_get_batch_factor_host", "Reach",
+    "sym_batch_error_columns", "sym_solve_batch", "sym_get_batch_factor_host", "Reach", "MLP",
 ]
 
 SYM_OK = 0
@@ -70,7 +70,8 @@ class sym_stats(ct.Structure):
                 ("nsuper_fund", ct.c_int32), ("nsuper", ct.c_int32), ("nlevels", ct.c_int32),
                 ("max_ncols", ct.c_int32), ("npairs", ct.c_int64), ("nlaunch_factor", ct.c_int64),
                 ("nlaunch_solve", ct.c_int64), ("analyze_seconds", ct.c_double),
-                ("device_bytes", ct.c_int64)]
+                ("device_bytes", ct.c_int64), ("upd_tasks", ct.c_int64), ("upd_entries", ct.c_int64),
+                ("dense_tasks", ct.c_int64), ("exec_flops", ct.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -120,6 +121,14 @@ def load():
             "sym_reach_export": ([P, i32, P], i64),
             "sym_solve_lower_sparse": ([P, P, P, P], I),
             "sym_reach_free": ([P], None),
+            "sym_mlp_create": ([i32, i32, ct.c_uint64, ct.POINTER(P)], I),
+            "sym_mlp_nparams": ([P], i64),
+            "sym_mlp_set_params": ([P, P], I),
+            "sym_mlp_get_params": ([P, P], I),
+            "sym_mlp_predict": ([P, i64, P, P], I),
+            "sym_mlp_gradient": ([P, i64, P, P, P, P], I),
+            "sym_mlp_train": ([P, i64, P, P, i32, ct.c_float, P], I),
+            "sym_mlp_free": ([P], None),
             "sym_batch_error_columns": ([P, P], I),
             "sym_solve_batch": ([P, i32, i32, P, i64, i64, P, i64, i64], I),
             "sym_get_batch_factor_host": ([P, i32, P], I),
@@ -288,6 +297,54 @@ def sym_get_batch_factor_host(h, index):
     out = np.zeros(st.storage_l, dtype=np.float64)
     _check(load().sym_get_batch_factor_host(h, int(index), out.ctypes.data))
     return out
+
+
+class MLP:
+    """The cost model network (owning wrapper of sym_mlp); X and t are torch CUDA float32 tensors."""
+
+    def __init__(self, nin, hidden, seed=0):
+        self.nin, self.hidden = int(nin), int(hidden)
+        m = ct.c_void_p()
+        _check(load().sym_mlp_create(self.nin, self.hidden, ct.c_uint64(seed), ct.byref(m)))
+        self.m = m
+        self.nparams = int(load().sym_mlp_nparams(m))
+
+    def get_params(self):
+        out = np.zeros(self.nparams, dtype=np.float32)
+        _check(load().sym_mlp_get_params(self.m, out.ctypes.data))
+        return out
+
+    def set_params(self, theta):
+        theta = np.ascontiguousarray(theta, dtype=np.float32)
+        assert theta.size == self.nparams
+        _check(load().sym_mlp_set_params(self.m, theta.ctypes.data))
+
+    def predict(self, X):
+        y = X.new_empty(X.shape[0])
+        _check(load().sym_mlp_predict(self.m, X.shape[0], _dptr(X), _dptr(y)))
+        return y
+
+    def gradient(self, X, t):
+        g = np.zeros(self.nparams, dtype=np.float32)
+        loss = ct.c_float()
+        _check(load().sym_mlp_gradient(self.m, X.shape[0], _dptr(X), _dptr(t), g.ctypes.data, ct.byref(loss)))
+        return g, loss.value
+
+    def train(self, X, t, steps, lr):
+        loss = ct.c_float()
+        _check(load().sym_mlp_train(self.m, X.shape[0], _dptr(X), _dptr(t), int(steps), ct.c_float(lr), ct.byref(loss)))
+        return loss.value
+
+    def close(self):
+        if self.m:
+            load().sym_mlp_free(self.m)
+            self.m = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Reach:

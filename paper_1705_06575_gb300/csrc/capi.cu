@@ -750,6 +750,14 @@ int sym_info(sym_handle h, sym_stats *s) {
   s->nlaunch_solve = (int64_t)P.fwd_launches.size() + (int64_t)P.bwd_launches.size() + 2;
   s->analyze_seconds = P.analyze_seconds;
   s->device_bytes = h->device_bytes;
+  s->upd_tasks = (int64_t)P.upd_tasks.size();
+  s->upd_entries = (int64_t)P.upd_entries.size();
+  int64_t dense = 0;
+  for (const auto &L : P.factor_launches)
+    if (L.kind != sym::K_UPDATE) dense += L.count;
+  s->dense_tasks = dense;
+  s->exec_flops = 0.0;
+  for (int k = sym::K_SCATTER; k <= sym::K_TRTRI; ++k) s->exec_flops += P.kind_flops[k];
   return SYM_OK;
 }
 

@@ -325,6 +325,44 @@ def same_pattern_batch(maker, count, seed):
     return first, vals
 
 
+def rcm_perm(M):
+    """Reverse Cuthill-McKee ordering (scipy) for patterns without geometry."""
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import reverse_cuthill_mckee
+    L = sp.csc_matrix((np.ones(M.nnz), M.Ai, M.Ap), shape=(M.n, M.n))
+    G = (L + L.T).tocsr()
+    return np.ascontiguousarray(reverse_cuthill_mckee(G, symmetric_mode=True), dtype=np.int32)
+
+
+def pattern_suite(count, seed):
+    """A mix of generated SPD patterns for the cost model: 2D 5/9-point grids (sides 24..160),
+    3D 7/27-point grids (sides 8..32), 3-dof 27-point grids (sides 5..12) and Erdos-Renyi graphs
+    (n 800..4000, average degree 4..16, reverse Cuthill-McKee order). Pattern i uses the seed
+    seed + i, so disjoint seed ranges give disjoint sets."""
+    out = []
+    for i in range(count):
+        rng = np.random.default_rng(seed + i)
+        kind = i % 7
+        if kind == 0:
+            M = laplace2d5(int(rng.integers(24, 161)), rng)
+        elif kind == 1:
+            M = dd2d9(int(rng.integers(24, 161)), rng)
+        elif kind == 2:
+            M = conduct3d(int(rng.integers(8, 33)), rng, "star")
+        elif kind == 3:
+            M = conduct3d(int(rng.integers(8, 25)), rng, "box")
+        elif kind == 4:
+            M = vector3d27(int(rng.integers(5, 13)), rng, sub=4)
+        elif kind == 5:
+            M = conduct3d(int(rng.integers(10, 29)), rng, "star", shift=1e-2)
+        else:
+            M = erdos_renyi(int(rng.integers(800, 4001)), int(rng.integers(4, 17)), rng)
+            M.perm = rcm_perm(M)
+        M.name = f"suite{seed + i}_{M.name}"
+        out.append(M)
+    return out
+
+
 def cfg(name, matrix_index=0):
     """The named workloads with their seeds (1000 * config index + matrix index)."""
     if name == "laplace2d5_64":
