@@ -291,6 +291,17 @@ int sym_get_factor_host(sym_handle h, double *Lx_host);
 #define SYM_EXPORT_LEVELPTR 16   /* int32[nlevels+1] */
 #define SYM_EXPORT_LEVELLIST 17  /* int32[nsuper]: supernodes by level, increasing within one */
 #define SYM_EXPORT_LXPTR 18      /* int64[nsuper+1]: offset of each panel in the factor storage */
+/* The launch schedule and its task lists (raw records, for checks of the scheduler):
+ * launches: int64 words {kind | level << 32, off, count, cluster} per launch;
+ * tasks: int32 words {a, b, c, d} per task (meaning per kind, see the SYM_KIND_* list);
+ * update tasks: int64 words {J | bi << 32, bj, e0, e1}; update entries: int64 words
+ * {K | r_lo << 32, c_lo | m << 32, n, relr, relc}. The count is in words. */
+#define SYM_EXPORT_FACTOR_LAUNCHES 19
+#define SYM_EXPORT_FWD_LAUNCHES 20
+#define SYM_EXPORT_BWD_LAUNCHES 21
+#define SYM_EXPORT_TASKS 22
+#define SYM_EXPORT_UPD_TASKS 23
+#define SYM_EXPORT_UPD_ENTRIES 24
 int64_t sym_export(sym_handle h, int32_t what, void *out);
 
 /* Per-kernel timing for measurement (no counterpart in the paper). With SYM_PROFILE_ON the

@@ -49,6 +49,8 @@ EXPORTS = {
     "desc": (10, np.int32), "descr0": (11, np.int64), "descnin": (12, np.int32),
     "relptr": (13, np.int64), "rel": (14, np.int32), "level": (15, np.int32),
     "levelptr": (16, np.int32), "levellist": (17, np.int32), "lxptr": (18, np.int64),
+    "factor_launches": (19, np.int64), "fwd_launches": (20, np.int64), "bwd_launches": (21, np.int64),
+    "tasks": (22, np.int32), "upd_tasks": (23, np.int64), "upd_entries": (24, np.int64),
 }
 
 

@@ -830,6 +830,19 @@ int64_t sym_export(sym_handle h, int32_t what, void *out) {
     EXP(SYM_EXPORT_LEVELLIST, levellist)
     EXP(SYM_EXPORT_LXPTR, lxptr)
 #undef EXP
+#define EXPB(id, vec, words)                                                     \
+  case id:                                                                       \
+    src = P.vec.data();                                                          \
+    count = (int64_t)P.vec.size() * (int64_t)(sizeof(P.vec[0]) / (words));       \
+    esz = (words);                                                               \
+    break;
+    EXPB(SYM_EXPORT_FACTOR_LAUNCHES, factor_launches, 8)
+    EXPB(SYM_EXPORT_FWD_LAUNCHES, fwd_launches, 8)
+    EXPB(SYM_EXPORT_BWD_LAUNCHES, bwd_launches, 8)
+    EXPB(SYM_EXPORT_TASKS, tasks, 4)
+    EXPB(SYM_EXPORT_UPD_TASKS, upd_tasks, 8)
+    EXPB(SYM_EXPORT_UPD_ENTRIES, upd_entries, 8)
+#undef EXPB
     default:
       return fail(SYM_ERR_INVALID, "unknown export item");
   }

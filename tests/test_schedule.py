@@ -1,0 +1,324 @@
+"""CPU check of the host scheduler: the exported launch schedule is executed by a numpy emulator
+of the kernels with the semantics of one GPU launch (every task of a launch sees the state from
+before the launch; writes land afterwards) and with a conflict check (within one launch no two
+tasks write the same element and no task reads an element another task writes). The emulated
+factor and solve must reproduce the oracle. A schedule with a missing dependency or a race
+fails here without a GPU."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1705_06575_gb300 as S
+import workloads as w
+
+NB = 64
+BG = 16
+K_UPDATE, K_POTRF, K_TRSM, K_GEMM, K_TRTRI = 1, 2, 3, 4, 5
+S_FGATHER, S_FSTEP, S_BGATHER, S_BSTEP = 11, 12, 14, 15
+
+
+class Sched:
+    def __init__(self, s):
+        self.sup = s.export("super")
+        self.rowptr = s.export("rowptr")
+        self.rows = s.export("rows")
+        self.rel = s.export("rel")
+        self.tasks = s.export("tasks").reshape(-1, 4)
+        ut = s.export("upd_tasks").reshape(-1, 4)
+        self.ut = np.stack([ut[:, 0] & 0xffffffff, ut[:, 0] >> 32, ut[:, 1], ut[:, 2], ut[:, 3]], 1)
+        ue = s.export("upd_entries").reshape(-1, 5)
+        self.ue = np.stack([ue[:, 0] & 0xffffffff, ue[:, 0] >> 32, ue[:, 1] & 0xffffffff, ue[:, 1] >> 32,
+                            ue[:, 2], ue[:, 3], ue[:, 4]], 1)
+        self.launches = {k: s.export(k).reshape(-1, 4) for k in ("factor_launches", "fwd_launches", "bwd_launches")}
+
+    def J(self, j):
+        f, l = int(self.sup[j]), int(self.sup[j + 1])
+        nr = int(self.rowptr[j + 1] - self.rowptr[j])
+        return f, l - f, nr, (l - f + NB - 1) // NB
+
+    def row_base(self, j, i):
+        _, nc, nr, ncb = self.J(j)
+        return i * NB if i < ncb else nc + (i - ncb) * NB
+
+    def row_len(self, j, i):
+        _, nc, nr, ncb = self.J(j)
+        end = nc if i < ncb else nr
+        return min(NB, end - self.row_base(j, i))
+
+    def tile(self, j, i, c):
+        """(row slice, col slice) of tile (i, c) of supernode j's panel."""
+        rb = self.row_base(j, i)
+        _, nc, _, _ = self.J(j)
+        return slice(rb, rb + self.row_len(j, i)), slice(c * NB, min(nc, (c + 1) * NB))
+
+
+class Launch:
+    """Collects the effects of the tasks of one launch, then applies them; conflict checks."""
+
+    def __init__(self):
+        self.writes = {}  # key -> (task id, value)
+        self.reads = []   # (task id, key)
+
+    def read(self, t, key):
+        self.reads.append((t, key))
+
+    def write(self, t, key, value):
+        assert key not in self.writes or self.writes[key][0] == t, ("two tasks write", key)
+        self.writes[key] = (t, value)
+
+    def commit(self, store):
+        for t, key in self.reads:
+            if key in self.writes:
+                assert self.writes[key][0] == t, ("read of an element another task writes", key)
+        for key, (_, v) in self.writes.items():
+            store[key] = v
+
+
+def emulate_factor(sc, panels, store):
+    """store maps ('L', j, r, c) and ('I', j, s, r, c) to values."""
+    def get(j, r, c):
+        return store[("L", j, r, c)]
+
+    for word0, off, count, _ in sc.launches["factor_launches"]:
+        kind = int(word0 & 0xffffffff)
+        L = Launch()
+        for t in range(int(off), int(off + count)):
+            if kind == K_UPDATE:
+                j, bi, bj, e0, e1 = (int(v) for v in sc.ut[t])
+                rs, cs = sc.tile(j, bi, bj)
+                rb, cb = rs.start, cs.start
+                acc = {}
+                for r in range(rs.start, rs.stop):
+                    for c in range(cs.start, cs.stop):
+                        acc[(r, c)] = get(j, r, c)
+                        L.read(t, ("L", j, r, c))
+                for e in range(e0, e1):
+                    K, r_lo, c_lo, m, n, relr, relc = (int(v) for v in sc.ue[e])
+                    _, kc, _, _ = sc.J(K)
+                    A = np.array([[get(K, r_lo + a, k) for k in range(kc)] for a in range(m)])
+                    B = np.array([[get(K, c_lo + b, k) for k in range(kc)] for b in range(n)])
+                    for a in range(m):
+                        for k in range(kc):
+                            L.read(t, ("L", K, r_lo + a, k))
+                    for b in range(n):
+                        for k in range(kc):
+                            L.read(t, ("L", K, c_lo + b, k))
+                    P = A @ B.T
+                    for a in range(m):
+                        for b in range(n):
+                            key = (rb + int(sc.rel[relr + a]) - rb, cb + int(sc.rel[relc + b]) - cb)
+                            acc[key] -= P[a, b]
+                for (r, c), v in acc.items():
+                    L.write(t, ("L", j, r, c), v)
+            elif kind in (K_POTRF, K_TRSM, K_GEMM, K_TRTRI):
+                j, ti, tj, ts_ = (int(v) for v in sc.tasks[t])
+                f, nc, nr, ncb = sc.J(j)
+                if kind == K_POTRF:
+                    rs, cs = sc.tile(j, ti, ti)
+                    D = np.array([[get(j, r, c) if r - rs.start >= c - cs.start else 0.0 for c in range(cs.start, cs.stop)]
+                                  for r in range(rs.start, rs.stop)])
+                    for r in range(rs.start, rs.stop):
+                        for c in range(cs.start, cs.stop):
+                            L.read(t, ("L", j, r, c))
+                    Lc = np.linalg.cholesky(D)
+                    for a, r in enumerate(range(rs.start, rs.stop)):
+                        for b, c in enumerate(range(cs.start, cs.stop)):
+                            L.write(t, ("L", j, r, c), Lc[a, b] if a >= b else 0.0)
+                elif kind == K_TRSM:
+                    i, s = ti, tj
+                    drs, dcs = sc.tile(j, s, s)
+                    rs, cs = sc.tile(j, i, s)
+                    D = np.array([[get(j, r, c) for c in range(dcs.start, dcs.stop)] for r in range(drs.start, drs.stop)])
+                    X = np.array([[get(j, r, c) for c in range(cs.start, cs.stop)] for r in range(rs.start, rs.stop)])
+                    for r in range(drs.start, drs.stop):
+                        for c in range(dcs.start, dcs.stop):
+                            if r - drs.start >= c - dcs.start:
+                                L.read(t, ("L", j, r, c))
+                    X = np.linalg.solve(np.tril(D), X.T).T
+                    for a, r in enumerate(range(rs.start, rs.stop)):
+                        for b, c in enumerate(range(cs.start, cs.stop)):
+                            L.write(t, ("L", j, r, c), X[a, b])
+                elif kind == K_GEMM:
+                    i, jj, s = ti, tj, ts_
+                    rs, cs = sc.tile(j, i, jj)
+                    ars, acs = sc.tile(j, i, s)
+                    brs, _ = sc.tile(j, jj, s)
+                    A = np.array([[get(j, r, c) for c in range(acs.start, acs.stop)] for r in range(ars.start, ars.stop)])
+                    B = np.array([[get(j, r, c) for c in range(acs.start, acs.stop)] for r in range(brs.start, brs.stop)])
+                    for r in list(range(ars.start, ars.stop)) + list(range(brs.start, brs.stop)):
+                        for c in range(acs.start, acs.stop):
+                            L.read(t, ("L", j, r, c))
+                    P = A @ B.T
+                    for a, r in enumerate(range(rs.start, rs.stop)):
+                        for b, c in enumerate(range(cs.start, cs.stop)):
+                            L.write(t, ("L", j, r, c), get(j, r, c) - P[a, b])
+                else:  # K_TRTRI
+                    s = ti
+                    rs, cs = sc.tile(j, s, s)
+                    D = np.array([[get(j, r, c) for c in range(cs.start, cs.stop)] for r in range(rs.start, rs.stop)])
+                    Inv = np.linalg.inv(np.tril(D))
+                    for a in range(Inv.shape[0]):
+                        for b in range(Inv.shape[1]):
+                            L.write(t, ("I", j, s, a, b), Inv[a, b])
+            else:
+                raise AssertionError(f"unknown kind {kind}")
+        L.commit(store)
+
+
+def emulate_solve(sc, store, y):
+    """y: dict index -> value (permuted numbering), updated in place."""
+    def Lv(j, r, c):
+        return store[("L", j, r, c)]
+
+    def Iv(j, s, a, b):
+        return store[("I", j, s, a, b)]
+
+    for name in ("fwd_launches", "bwd_launches"):
+        for word0, off, count, _ in sc.launches[name]:
+            kind = int(word0 & 0xffffffff)
+            L = Launch()
+            for t in range(int(off), int(off + count)):
+                j, ti, tc, _ = (int(v) for v in sc.tasks[t])
+                f, nc, nr, ncb = sc.J(j)
+                R = sc.rows[sc.rowptr[j]:sc.rowptr[j + 1]]
+                tsz = lambda s: min(NB, nc - s * NB)
+                if kind == S_FGATHER:
+                    bj, ut = ti, tc
+                    cb = bj * NB
+                    acc = {f + cb + r: y[f + cb + r] for r in range(min(NB, nc - cb))}
+                    for key in acc:
+                        L.read(t, key)
+                    _, _, _, e0, e1 = (int(v) for v in sc.ut[ut])
+                    for e in range(e0, e1):
+                        K, r_lo, c_lo, m, n, relr, relc = (int(v) for v in sc.ue[e])
+                        fk, kc, _, _ = sc.J(K)
+                        for b in range(n):
+                            v = sum(Lv(K, c_lo + b, k) * y[fk + k] for k in range(kc))
+                            for k in range(kc):
+                                L.read(t, fk + k)
+                            acc[f + int(sc.rel[relc + b])] -= v
+                    for key, v in acc.items():
+                        L.write(t, key, v)
+                elif kind == S_BGATHER:
+                    c0 = ti * BG
+                    for c in range(c0, min(nc, c0 + BG)):
+                        v = sum(Lv(j, r, c) * y[int(R[r])] for r in range(nc, nr))
+                        for r in range(nc, nr):
+                            L.read(t, int(R[r]))
+                        L.read(t, f + c)
+                        L.write(t, f + c, y[f + c] - v)
+                elif kind in (S_FSTEP, S_BSTEP):
+                    i, s = ti, tc
+                    fwd = kind == S_FSTEP
+
+                    def solved(u):
+                        g = [f + u * NB + a for a in range(tsz(u))]
+                        v = np.array([y[k] for k in g])
+                        Inv = np.array([[Iv(j, u, a, b) for b in range(tsz(u))] for a in range(tsz(u))])
+                        return g, (Inv @ v if fwd else Inv.T @ v)
+
+                    if i == s:
+                        targets = ([s - 1] if s >= 1 else []) + ([s] if s == ncb - 1 else []) if fwd else \
+                                  ([s + 1] if s + 1 < ncb else []) + ([0] if s == 0 else [])
+                        for u in targets:
+                            g, v = solved(u)
+                            for k, val in zip(g, v):
+                                L.read(t, k)
+                                L.write(t, k, val)
+                    else:
+                        g, zs = solved(s)
+                        for k in g:
+                            L.read(t, k)
+                        for a in range(tsz(i)):
+                            k = f + i * NB + a
+                            if fwd:
+                                v = sum(Lv(j, i * NB + a, s * NB + b) * zs[b] for b in range(tsz(s)))
+                            else:
+                                v = sum(Lv(j, s * NB + b, i * NB + a) * zs[b] for b in range(tsz(s)))
+                            L.read(t, k)
+                            L.write(t, k, y[k] - v)
+                else:
+                    raise AssertionError(f"unknown kind {kind}")
+            L.commit(y)
+
+
+@pytest.mark.parametrize("maker", [
+    lambda: w.laplace2d5(14, np.random.default_rng(1)),
+    lambda: w.conduct3d(6, np.random.default_rng(2), "box"),
+    lambda: w.random_spd_pattern(150, 1.0, np.random.default_rng(3)),      # one wide supernode: 3 tiles
+    lambda: w.random_spd_pattern(220, 0.03, np.random.default_rng(4)),
+])
+def test_schedule_emulation_reproduces_oracle(maker):
+    M = maker()
+    s = S.Solver(M.n, M.Ap, M.Ai, M.perm, host_only=True)
+    sc = Sched(s)
+    o = oracle.Oracle(M.n, M.Ap, M.Ai, M.perm)
+    assert o.factor(M.Ax) == 0
+    # H1: the panels hold the lower part of C = P A P^T, zeros elsewhere
+    store = {}
+    Cval = {}
+    for jcol in range(M.n):
+        for p in range(o.Cp[jcol], o.Cp[jcol + 1]):
+            Cval[(int(o.Ci[p]), jcol)] = M.Ax[o.Cmap[p]]
+    for j in range(len(sc.sup) - 1):
+        f, nc, nr, _ = sc.J(j)
+        R = sc.rows[sc.rowptr[j]:sc.rowptr[j + 1]]
+        for r in range(nr):
+            for c in range(nc):
+                store[("L", j, r, c)] = Cval.get((int(R[r]), f + c), 0.0) if R[r] >= f + c else 0.0
+    emulate_factor(sc, None, store)
+    # compare with the oracle on its pattern
+    for j in range(len(sc.sup) - 1):
+        f, nc, nr, _ = sc.J(j)
+        R = list(sc.rows[sc.rowptr[j]:sc.rowptr[j + 1]])
+        for c in range(nc):
+            col = f + c
+            for p in range(o.Lp[col], o.Lp[col + 1]):
+                r = R.index(int(o.Li[p]))
+                assert abs(store[("L", j, r, c)] - o.Lx[p]) <= 1e-12 * np.abs(o.Lx).max()
+    # solve with one right-hand side in the permuted space
+    b = np.random.default_rng(9).standard_normal(M.n)
+    y = {k: b[o.perm[k]] for k in range(M.n)}
+    emulate_solve(sc, store, y)
+    x = np.zeros(M.n)
+    for k in range(M.n):
+        x[o.perm[k]] = y[k]
+    ref = o.solve(b)[:, 0]
+    assert np.abs(x - ref).max() <= 1e-10 * np.abs(ref).max()
+
+
+def test_emulator_detects_a_missing_launch():
+    """Planted mistake: dropping one trailing-update launch from the schedule is detected."""
+    M = w.random_spd_pattern(150, 1.0, np.random.default_rng(3))
+    s = S.Solver(M.n, M.Ap, M.Ai, M.perm, host_only=True)
+    sc = Sched(s)
+    kinds = [int(x & 0xffffffff) for x in sc.launches["factor_launches"][:, 0]]
+    sc.launches["factor_launches"] = np.delete(sc.launches["factor_launches"], kinds.index(K_GEMM), axis=0)
+    o = oracle.Oracle(M.n, M.Ap, M.Ai, M.perm)
+    o.factor(M.Ax)
+    store = {}
+    Cval = {(int(o.Ci[p]), jc): M.Ax[o.Cmap[p]] for jc in range(M.n) for p in range(o.Cp[jc], o.Cp[jc + 1])}
+    f, nc, nr, _ = sc.J(0)
+    R = sc.rows[sc.rowptr[0]:sc.rowptr[1]]
+    for r in range(nr):
+        for c in range(nc):
+            store[("L", 0, r, c)] = Cval.get((int(R[r]), f + c), 0.0) if R[r] >= f + c else 0.0
+    try:
+        emulate_factor(sc, None, store)
+        err = max(abs(store[("L", 0, int(np.nonzero(R == o.Li[p])[0][0]), c)] - o.Lx[p])
+                  for c in range(nc) for p in range(o.Lp[c], o.Lp[c + 1]))
+    except np.linalg.LinAlgError:
+        err = np.inf
+    assert err > 1e-3
+
+
+def test_conflict_checker():
+    L = Launch()
+    L.write(0, ("L", 0, 1, 1), 1.0)
+    with pytest.raises(AssertionError):
+        L.write(1, ("L", 0, 1, 1), 2.0)  # two tasks write one element
+    L2 = Launch()
+    L2.read(0, 5)
+    L2.write(1, 5, 3.0)
+    with pytest.raises(AssertionError):
+        L2.commit({})  # a task reads what another task of the launch writes
