@@ -150,6 +150,16 @@ class CostModel:
         return CostModel(d["theta"], d["mean"], d["std"], d["hidden"])
 
 
+WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "costmodel_weights.json")
+
+
+def pretrained():
+    """The network trained on 1600 generated patterns (400 more held out) of the pattern suite;
+    its training run is `python -m paper_1705_06575_gb300.costmodel --patterns 2000 --holdout 0.2
+    --seed 20000`."""
+    return CostModel.load(WEIGHTS)
+
+
 def choose_preset(M, torch, model=None):
     """The learned choice, or the fixed rule when no model is available."""
     return DEFAULT if model is None else model.choose(M, torch)

@@ -74,3 +74,22 @@ def test_learned_schedule_gain_over_fixed_rule(torch_cuda):
     assert ev["geomean_speedup_vs_fixed_rule"] >= 0.97
     assert ev["total_time_ratio"] >= 0.97
     assert ev["geomean_speedup_vs_fixed_rule"] >= ev["geomean_speedup_of_best_setting"] / 1.03
+
+
+def test_pretrained_model_on_fresh_patterns(torch_cuda):
+    """The packaged network (trained on 1600 patterns of another seed): its predictions through the
+    library's FP32 kernels match the FP64 reference MLP, and on 10 fresh generated patterns its
+    choices are not slower than the fixed rule by measured time (3% noise allowance)."""
+    torch = torch_cuda
+    import workloads as w
+    from paper_1705_06575_gb300 import costmodel as cm
+    m = cm.pretrained()
+    mats = w.pattern_suite(10, 31000)
+    X, Y, G, skipped = cm.collect(mats, torch, flop_budget=2e10)
+    got = m.predict(X, torch)
+    want, _ = ref.forward(m.theta.astype(np.float64), (X - m.mean) / m.std, cm.NFEAT, cm.HIDDEN)
+    assert np.abs(got - want).max() <= 1e-4 * max(1.0, np.abs(want).max())
+    ev = cm.evaluate(m, X, Y, G, torch)
+    print("packaged model on fresh patterns:", ev)
+    assert ev["geomean_speedup_vs_fixed_rule"] >= 0.97
+    assert ev["total_time_ratio"] >= 0.97
