@@ -58,6 +58,28 @@ def dist_env():
     return rank, world, local
 
 
+def dist_aggregate(ms, units, world):
+    """Whole-job figures of one timed region: the slowest rank's time and the units of work all
+    ranks processed (each rank runs its own replica or its own shard; no data exchange)."""
+    if world <= 1:
+        return ms, units
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    u = torch.tensor([units], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def shard(count, rank, world):
+    """Contiguous share [lo, hi) of count independent matrices for one rank."""
+    per, extra = divmod(count, world)
+    lo = rank * per + min(rank, extra)
+    return lo, lo + per + (1 if rank < extra else 0)
+
+
 def start_clock_sampler(path):
     try:
         return subprocess.Popen(["nvidia-smi", f"--query-gpu={CLOCK_QUERY}", "--format=csv", "-lms", "200"],
@@ -205,11 +227,7 @@ def bench_mixed(S, torch, M, B, flops, args, stream, barrier, world):
     torch.cuda.synchronize()
     barrier()
     ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms, _ = dist_aggregate(ms, 0.0, world)
     it, be_dev = s.refinement_info()
     X = Xt.cpu().numpy().T
     berr = backward_error(M, B, X)
@@ -222,9 +240,22 @@ def bench_mixed(S, torch, M, B, flops, args, stream, barrier, world):
     f1.record(stream)
     torch.cuda.synchronize()
     ms_f = f0.elapsed_time(f1) / args.steps
+    # per-kernel breakdown of the FP32 factor (profiled pass, kernel by kernel)
+    s.profile(S.SYM_PROFILE_RESET)
+    s.profile(S.SYM_PROFILE_ON)
+    for _ in range(args.steps):
+        s.factor(Ax)
+    torch.cuda.synchronize()
+    s.profile(S.SYM_PROFILE_OFF)
+    kinds = {}
+    for name in ("scatter", "update", "potrf", "trsm", "gemm", "trtri"):
+        kms, knl, kfl = s.profile_read(S.KINDS[name])
+        if knl:
+            kinds[name] = {"ms_per_step": kms / args.steps, "gflops_alg": kfl / kms / 1e6 if kms > 0 else None}
     s.close()
     return {"value": flops * world / (ms * 1e-3) / 1e9, "unit": "GFLOP/s", "ms_per_step": ms,
             "ms_factor": ms_f, "ms_refined_solve": ms - ms_f, "refinement_iterations": it,
+            "factor_kernels": kinds,
             "backward_error": berr, "dtype": "f32 factor + f64 refinement",
             "definition": "same step as the main line; value = factor flops / step time"}
 
@@ -381,11 +412,7 @@ def run_ours(args):
         step()
     torch.cuda.synchronize()
     s.profile(S.SYM_PROFILE_OFF)
-    if world > 1:
-        import torch.distributed as dist
-        tmax = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        ms_step = float(tmax.item())
+    ms_step, total_flops = dist_aggregate(ms_step, info.flops, world)
     X = Xt.cpu().numpy().T
     berr = backward_error(M, B, X)
 
@@ -427,11 +454,7 @@ def run_ours(args):
         e2e_step()
     torch.cuda.synchronize()
     t_e2e = (time.perf_counter() - t0) / e2e_steps
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t_e2e], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_e2e = float(tt.item())
+    t_e2e, _ = dist_aggregate(t_e2e, 0.0, world)
     berr_e2e = backward_error(M, B, X_h.numpy().T)
 
     variants = {}
@@ -442,7 +465,7 @@ def run_ours(args):
             variants["batched_512x_dd2d9_128"] = bench_batched(S, torch, args, stream, barrier, world)
     clocks = read_clocks(clock_path, local) if rank == 0 else None
     flops = info.flops
-    value = flops * world / (ms_step * 1e-3) / 1e9
+    value = total_flops / (ms_step * 1e-3) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -458,7 +481,7 @@ def run_ours(args):
         "analyze_s": analyze_s, "backward_error": berr, "backward_error_e2e": berr_e2e,
         "kernels": kinds,
         "roofline": roofline,
-        "e2e": {"value": flops * world / t_e2e / 1e9, "unit": "GFLOP/s", "ms_per_step": t_e2e * 1e3,
+        "e2e": {"value": total_flops / t_e2e / 1e9, "unit": "GFLOP/s", "ms_per_step": t_e2e * 1e3,
                 "h2d_bytes_per_step": 8 * (M.nnz + M.n * NRHS), "d2h_bytes_per_step": 8 * M.n * NRHS},
         "gpu_launches": int(args.steps * (info.nlaunch_factor + info.nlaunch_solve)),
         "clocks": clocks,

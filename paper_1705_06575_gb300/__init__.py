@@ -40,6 +40,7 @@ SYM_ORDER_NATURAL = 0
 SYM_ORDER_GIVEN = 1
 SYM_FLAG_HOST_ONLY = 1
 SYM_FLAG_NO_GRAPHS = 2
+SYM_FLAG_ONE_STREAM = 4
 
 # name -> (code, numpy dtype)
 EXPORTS = {
@@ -429,9 +430,10 @@ def sym_free(h):
 class Solver:
     """Owning wrapper of one handle: analyze on construction, free on close."""
 
-    def __init__(self, n, Ap, Ai, perm=None, opt=None, host_only=False, precision=None):
+    def __init__(self, n, Ap, Ai, perm=None, opt=None, host_only=False, precision=None, flags=0):
         if opt is None:
             opt = sym_options_default()
+        opt.flags |= int(flags)
         if precision is not None:
             opt.precision = SYM_PREC_MIXED if precision in ("mixed", SYM_PREC_MIXED) else SYM_PREC_FP64
         if perm is not None:

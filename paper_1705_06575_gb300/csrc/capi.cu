@@ -67,6 +67,12 @@ struct sym_handle_s {
   int32_t refine_max_iter = 100;
   int32_t last_iterations = 0;
   double last_berr = 0.0;
+  // lookahead streams of the factor
+  cudaStream_t aux_stream = nullptr;
+  std::vector<cudaEvent_t> la_events;
+  cudaEvent_t la_fork = nullptr, la_join = nullptr;
+  sym::TwoStreams two;
+  bool lookahead = true;  // run the factor schedule's auxiliary-stream launches concurrently
   // per-kernel profiling
   bool profiling = false;
   std::vector<cudaEvent_t> events;
@@ -131,6 +137,10 @@ int collect_trace(sym_handle_s *h, const sym::LaunchTrace &tr, double flop_scale
 }
 
 void release_device(sym_handle_s *h) {
+  for (cudaEvent_t e : h->la_events) cudaEventDestroy(e);
+  if (h->la_fork) cudaEventDestroy(h->la_fork);
+  if (h->la_join) cudaEventDestroy(h->la_join);
+  if (h->aux_stream) cudaStreamDestroy(h->aux_stream);
   {
     void *mp[] = {h->d_Linv, h->d_Lfinv, h->d_Lf, h->d_Axc, h->d_anorm, h->d_anorm_work, h->d_csr_p, h->d_csr_i, h->d_csr_map, h->d_rwork};
     for (void *p : mp)
@@ -197,7 +207,7 @@ cudaError_t enqueue_factor(sym_handle_s *h, const double *Ax, int32_t nbatch, in
       if (e != cudaSuccess) return e;
     }
     cudaError_t e = sym::run_factor<float>(h->dp, h->plan.factor_launches, Ax, h->d_Lf, h->d_Lfinv, h->d_status,
-                                           st, tr, bt);
+                                           st, tr, bt, h->aux_stream ? &h->two : nullptr);
     if (e != cudaSuccess) return e;
     for (int32_t b = 0; b < nbatch; ++b) {
       e = sym::refine_anorm(refine_ctx(h, b), st);
@@ -205,7 +215,8 @@ cudaError_t enqueue_factor(sym_handle_s *h, const double *Ax, int32_t nbatch, in
     }
     return cudaSuccess;
   }
-  return sym::run_factor<double>(h->dp, h->plan.factor_launches, Ax, h->d_Lx, h->d_Linv, h->d_status, st, tr, bt);
+  return sym::run_factor<double>(h->dp, h->plan.factor_launches, Ax, h->d_Lx, h->d_Linv, h->d_status, st, tr, bt,
+                                 h->aux_stream ? &h->two : nullptr);
 }
 
 void drop_graphs(sym_handle_s *h) {
@@ -257,7 +268,30 @@ int ensure_batch(sym_handle_s *h, int32_t nbatch) {
 
 int ensure_capture_stream(sym_handle_s *h) {
   if (h->capture_stream) return SYM_OK;
-  CUDA_TRY(cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+  int lo = 0, hi = 0;
+  CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi), "stream priorities");
+  CUDA_TRY(cudaStreamCreateWithPriority(&h->capture_stream, cudaStreamNonBlocking, hi), "cudaStreamCreate");
+  return SYM_OK;
+}
+
+// The lookahead's auxiliary stream and one event per factor launch (created once).
+int ensure_two_streams(sym_handle_s *h) {
+  if (h->aux_stream) return SYM_OK;
+  int lo = 0, hi = 0;
+  CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi), "stream priorities");
+  CUDA_TRY(cudaStreamCreateWithPriority(&h->aux_stream, cudaStreamNonBlocking, lo), "cudaStreamCreate");
+  const size_t nl = h->plan.factor_launches.size();
+  h->la_events.resize(nl, nullptr);
+  for (size_t i = 0; i < nl; ++i)
+    CUDA_TRY(cudaEventCreateWithFlags(&h->la_events[i], cudaEventDisableTiming), "cudaEventCreate");
+  CUDA_TRY(cudaEventCreateWithFlags(&h->la_fork, cudaEventDisableTiming), "cudaEventCreate");
+  CUDA_TRY(cudaEventCreateWithFlags(&h->la_join, cudaEventDisableTiming), "cudaEventCreate");
+  h->two.aux = h->aux_stream;
+  h->two.events = &h->la_events;
+  h->two.fork = h->la_fork;
+  h->two.join = h->la_join;
+  h->two.prio_high = hi;
+  h->two.prio_low = lo;
   return SYM_OK;
 }
 
@@ -369,6 +403,7 @@ int sym_analyze_perm(int64_t n, const int64_t *Ap, const int32_t *Ai, const int3
   }
   h->host_only = (opt.flags & SYM_FLAG_HOST_ONLY) != 0;
   h->use_graphs = (opt.flags & SYM_FLAG_NO_GRAPHS) == 0;
+  h->lookahead = (opt.flags & SYM_FLAG_ONE_STREAM) == 0;
   if (!h->host_only) {
     int rc = SYM_OK;
     auto &P = h->plan;
@@ -480,6 +515,10 @@ int factor_impl(sym_handle h, int32_t nbatch, const double *Ax, int64_t stride) 
   if (!h->prepared) {
     CUDA_TRY(h->precision == SYM_PREC_MIXED ? sym::prepare_factor<float>() : sym::prepare_factor<double>(),
              "factor set-up");
+    if (h->lookahead) {
+      rc = ensure_two_streams(h);
+      if (rc) return rc;
+    }
     h->prepared = true;
   }
   sym::LaunchTrace tr, *trp = nullptr;
@@ -505,7 +544,7 @@ int factor_impl(sym_handle h, int32_t nbatch, const double *Ax, int64_t stride) 
         cudaGetLastError();
         return cuda_fail(e != cudaSuccess ? e : e2, "capture factor");
       }
-      e = cudaGraphInstantiate(&h->fgraph, g, 0);
+      e = cudaGraphInstantiate(&h->fgraph, g, cudaGraphInstantiateFlagUseNodePriority);
       cudaGraphDestroy(g);
       if (e != cudaSuccess) return cuda_fail(e, "instantiate factor graph");
       h->fgraph_ax = Ax;
@@ -839,6 +878,7 @@ int64_t sym_export(sym_handle h, int32_t what, void *out) {
     EXPB(SYM_EXPORT_FACTOR_LAUNCHES, factor_launches, 8)
     EXPB(SYM_EXPORT_FWD_LAUNCHES, fwd_launches, 8)
     EXPB(SYM_EXPORT_BWD_LAUNCHES, bwd_launches, 8)
+    static_assert(sizeof(sym::Launch) == 40, "launch record layout");
     EXPB(SYM_EXPORT_TASKS, tasks, 4)
     EXPB(SYM_EXPORT_UPD_TASKS, upd_tasks, 8)
     EXPB(SYM_EXPORT_UPD_ENTRIES, upd_entries, 8)

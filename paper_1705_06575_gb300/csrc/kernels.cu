@@ -20,6 +20,7 @@
 #include <cooperative_groups.h>
 
 #include <cstdint>
+#include <utility>
 
 #include "kernels.h"
 
@@ -271,8 +272,13 @@ __global__ void __launch_bounds__(THREADS) k_trsm(const SNode *__restrict__ sn,
   const SNode sj = sn[t.a];
   const int i = t.b, s = t.c;
   const int ts = min(NB, sj.ncols - s * NB);
-  const int64_t rb = d_row_tile_base(i, sj.ncols, sj.ncb);
-  const int tm = d_row_tile_rows(i, sj.ncols, sj.nrows, sj.ncb);
+  int64_t rb = d_row_tile_base(i, sj.ncols, sj.ncb);
+  int tm = d_row_tile_rows(i, sj.ncols, sj.nrows, sj.ncb);
+  const int half = t.d >> 16;  // 0: whole tile; 1, 2: its first or second 32 rows
+  if (half) {
+    rb += (half - 1) * (NB / 2);
+    tm = max(0, min(NB / 2, tm - (half - 1) * (NB / 2)));
+  }
   const T *D = Lx + sj.lx + (int64_t)(s * NB) * sj.nrows + s * NB;
   T *B = Lx + sj.lx + (int64_t)(s * NB) * sj.nrows + rb;
   const int tid = threadIdx.x;
@@ -310,9 +316,14 @@ __global__ void __launch_bounds__(THREADS) k_gemm(const SNode *__restrict__ sn,
   __shared__ T Bs[KC][NB];
   const Int4 t = tasks[toff + blockIdx.x];
   const SNode sj = sn[t.a];
-  const int i = t.b, j = t.c, s = t.d;
-  const int64_t rb = d_row_tile_base(i, sj.ncols, sj.ncb);
-  const int tm = d_row_tile_rows(i, sj.ncols, sj.nrows, sj.ncb);
+  const int i = t.b, j = t.c, s = t.d & 0xffff;
+  int64_t rb = d_row_tile_base(i, sj.ncols, sj.ncb);
+  int tm = d_row_tile_rows(i, sj.ncols, sj.nrows, sj.ncb);
+  const int half = t.d >> 16;  // 0: whole tile; 1, 2: its first or second 32 rows
+  if (half) {
+    rb += (half - 1) * (NB / 2);
+    tm = max(0, min(NB / 2, tm - (half - 1) * (NB / 2)));
+  }
   const int tn = min(NB, sj.ncols - j * NB);
   const int ks = min(NB, sj.ncols - s * NB);
   const T *P = Lx + sj.lx + (int64_t)(s * NB) * sj.nrows;  // column block s
@@ -760,6 +771,22 @@ inline int grid_for(int64_t count, int per) {
 
 }  // namespace
 
+// Launch with a stream priority attribute (kept by CUDA-graph capture as a node priority).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_prio(void (*kernel)(KArgs...), dim3 grid, size_t smem, cudaStream_t st, int prio, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(THREADS, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  attr[0].id = cudaLaunchAttributePriority;
+  attr[0].val.priority = prio;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 inline void trace_mark(LaunchTrace *tr, int32_t kind, cudaStream_t st) {
   if (!tr) return;
   cudaEventRecord((*tr->events)[tr->used++], st);
@@ -801,35 +828,54 @@ cudaError_t prepare_solve() {
 
 template <typename T>
 cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, const double *Ax,
-                       T *Lx, T *Linv, long long *status, cudaStream_t st, LaunchTrace *trace, const Batch &bt) {
+                       T *Lx, T *Linv, long long *status, cudaStream_t st, LaunchTrace *trace, const Batch &bt,
+                       const TwoStreams *two) {
   const unsigned nb = (unsigned)bt.count;
+  // With two streams the schedule's stream/wait fields are honoured (lookahead); otherwise (and
+  // when tracing) every launch goes to st in list order, which satisfies every wait.
+  const bool dual = two && two->aux && two->events && !trace;
   trace_mark(trace, -1, st);
   k_zero<T><<<dim3(grid_for(d.storage, THREADS * 4), nb), THREADS, 0, st>>>(Lx, d.storage, bt);
   if (d.nnz_a > 0)
     k_scatter<T><<<dim3(grid_for(d.nnz_a, THREADS * 4), nb), THREADS, 0, st>>>(Ax, d.amap, Lx, d.nnz_a, bt);
   trace_mark(trace, K_SCATTER, st);
-  for (const Launch &L : launches) {
+  if (dual) {  // the auxiliary stream starts after the panels hold A
+    cudaEventRecord(two->fork, st);
+    cudaStreamWaitEvent(two->aux, two->fork, 0);
+  }
+  for (size_t li = 0; li < launches.size(); ++li) {
+    const Launch &L = launches[li];
     const unsigned g = (unsigned)L.count;
+    cudaStream_t s = (dual && L.stream == 1) ? two->aux : st;
+    const int prio = (dual && L.stream == 1) ? two->prio_low : two ? two->prio_high : 0;
+    if (dual && L.wait >= 0) cudaStreamWaitEvent(s, (*two->events)[L.wait], 0);
+    cudaError_t e = cudaSuccess;
     switch (L.kind) {
       case K_UPDATE:
-        k_update<T><<<dim3(g, nb), THREADS, 0, st>>>(d.sn, d.upd_tasks, d.upd_entries, d.rel, Lx, L.off, bt);
+        e = launch_prio(k_update<T>, dim3(g, nb), 0, s, prio, d.sn, d.upd_tasks, d.upd_entries, d.rel, Lx, L.off, bt);
         break;
       case K_POTRF:
-        k_potrf<T><<<dim3(g, nb), THREADS, 0, st>>>(d.sn, d.tasks, Lx, status, L.off, bt);
+        e = launch_prio(k_potrf<T>, dim3(g, nb), 0, s, prio, d.sn, d.tasks, Lx, status, L.off, bt);
         break;
       case K_TRSM:
-        k_trsm<T><<<dim3(g, nb), THREADS, trsm_smem<T>(), st>>>(d.sn, d.tasks, Lx, L.off, bt);
+        e = launch_prio(k_trsm<T>, dim3(g, nb), trsm_smem<T>(), s, prio, d.sn, d.tasks, Lx, L.off, bt);
         break;
       case K_GEMM:
-        k_gemm<T><<<dim3(g, nb), THREADS, 0, st>>>(d.sn, d.tasks, Lx, L.off, bt);
+        e = launch_prio(k_gemm<T>, dim3(g, nb), 0, s, prio, d.sn, d.tasks, Lx, L.off, bt);
         break;
       case K_TRTRI:
-        k_trtri<T><<<dim3(g, nb), THREADS, trtri_smem(), st>>>(d.sn, d.tasks, Lx, Linv, L.off, bt);
+        e = launch_prio(k_trtri<T>, dim3(g, nb), trtri_smem(), s, prio, d.sn, d.tasks, (const T *)Lx, Linv, L.off, bt);
         break;
       default:
         return cudaErrorInvalidValue;
     }
+    if (e != cudaSuccess) return e;
+    if (dual) cudaEventRecord((*two->events)[li], s);
     trace_mark(trace, L.kind, st);
+  }
+  if (dual) {
+    cudaEventRecord(two->join, two->aux);
+    cudaStreamWaitEvent(st, two->join, 0);
   }
   return cudaGetLastError();
 }
@@ -939,10 +985,10 @@ template cudaError_t prepare_factor<double>();
 template cudaError_t prepare_factor<float>();
 template cudaError_t run_factor<double>(const DevPlan &, const std::vector<Launch> &, const double *,
                                         double *, double *, long long *, cudaStream_t, LaunchTrace *,
-                                        const Batch &);
+                                        const Batch &, const TwoStreams *);
 template cudaError_t run_factor<float>(const DevPlan &, const std::vector<Launch> &, const double *,
                                        float *, float *, long long *, cudaStream_t, LaunchTrace *,
-                                       const Batch &);
+                                       const Batch &, const TwoStreams *);
 template cudaError_t run_solve<double>(const DevPlan &, const std::vector<Launch> &,
                                        const std::vector<Launch> &, const double *, const double *, int,
                                        const double *, int64_t, double *, int64_t, double *,

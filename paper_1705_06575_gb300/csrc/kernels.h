@@ -31,6 +31,16 @@ struct Batch {
   int64_t lx = 0, ax = 0, dinv = 0, y = 0, b = 0, x = 0;
 };
 
+// Second stream for the factor's lookahead: aux runs the launches with stream == 1 at low
+// priority; events[i] is recorded after launch i (at least one event per launch); fork/join
+// attach aux to the main stream (also inside a CUDA-graph capture).
+struct TwoStreams {
+  cudaStream_t aux = nullptr;
+  std::vector<cudaEvent_t> *events = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  int prio_high = 0, prio_low = 0;
+};
+
 // Optional per-launch timing: when non-null, an event is recorded before the first launch and
 // after every launch on the same stream; kinds[i] is the Kind of launch i (K_SCATTER for the
 // zero + scatter pair, S_PERM for the permutations of the solve).
@@ -54,7 +64,7 @@ cudaError_t prepare_solve();
 template <typename T>
 cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, const double *Ax,
                        T *Lx, T *Linv, long long *status, cudaStream_t st, LaunchTrace *trace = nullptr,
-                       const Batch &bt = Batch());
+                       const Batch &bt = Batch(), const TwoStreams *two = nullptr);
 
 // Solve with nrhs right-hand sides: y = P b, forward sweep, backward sweep, x = P^T y.
 // y: device work array of n * nrhs (ld n); Linv: the diagonal-tile inverses run_factor wrote.

@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cstring>
+#include <functional>
 #include <numeric>
 
 #include "plan.h"
@@ -425,6 +426,7 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
       std::vector<UpdEntry> ents;
     };
     std::vector<int32_t> tile_slot;
+    int32_t pending_join = -1;  // auxiliary launch the next main-stream launch must wait for
     for (int32_t l = 0; l < nlev; ++l) {
       // Gather the level's tasks, then order them by decreasing work (longest first) so that
       // the longest tiles start early; ties keep (J, bi, bj) order.
@@ -479,7 +481,10 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
       }
       std::stable_sort(lt.begin(), lt.end(), [](const LTask &x, const LTask &y) { return x.work > y.work; });
       if (!lt.empty()) {
-        P.factor_launches.push_back({K_UPDATE, l, (int64_t)P.upd_tasks.size(), (int64_t)lt.size()});
+        Launch U{K_UPDATE, l, (int64_t)P.upd_tasks.size(), (int64_t)lt.size()};
+        U.wait = pending_join;
+        pending_join = -1;
+        P.factor_launches.push_back(U);
         for (LTask &x : lt) {
           UpdTask u;
           u.J = x.J;
@@ -493,37 +498,103 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
           P.upd_tasks.push_back(u);
         }
       }
-      // Dense part of each supernode of this level.
+      // Dense part of each supernode of this level: right-looking over column tiles s with
+      // lookahead 1. After TRSM(s), the trailing update of column tile s+1 (NEXT) runs on the
+      // main stream, followed at once by POTRF(s+1) and TRSM(s+1), while the update of the
+      // tiles right of it (REST) runs on the auxiliary stream. NEXT(s) waits for REST(s-1),
+      // the last earlier update of column s+1; REST(s) waits for TRSM(s).
       int32_t maxcb = 0;
       for (int32_t t = P.levelptr[l]; t < P.levelptr[l + 1]; ++t)
         maxcb = std::max(maxcb, P.snodes[P.levellist[t]].ncb);
-      for (int32_t s = 0; s < maxcb; ++s) {
-        for (int kind : {K_POTRF, K_TRSM, K_GEMM}) {
-          int64_t off = (int64_t)P.tasks.size();
-          for (int32_t t = P.levelptr[l]; t < P.levelptr[l + 1]; ++t) {
-            const int32_t J = P.levellist[t];
-            const SNode &sj = P.snodes[J];
-            if (s >= sj.ncb) continue;
-            const int32_t nrb = num_row_tiles(sj.nrows, sj.ncols, sj.ncb);
-            if (kind == K_POTRF) P.tasks.push_back({J, s, s, s});
-            if (kind == K_TRSM)
-              for (int32_t i = s + 1; i < nrb; ++i) P.tasks.push_back({J, i, s, s});
-            if (kind == K_GEMM)
-              for (int32_t j = s + 1; j < sj.ncb; ++j)
-                for (int32_t i = j; i < nrb; ++i) P.tasks.push_back({J, i, j, s});
-          }
-          int64_t cnt = (int64_t)P.tasks.size() - off;
-          if (cnt > 0) P.factor_launches.push_back({kind, l, off, cnt});
+      auto emit = [&](int kind, int32_t s, int stream, int32_t wait,
+                      const std::function<void(int32_t J, const SNode &, int32_t nrb)> &gen) -> int32_t {
+        const int64_t off = (int64_t)P.tasks.size();
+        for (int32_t t = P.levelptr[l]; t < P.levelptr[l + 1]; ++t) {
+          const int32_t J = P.levellist[t];
+          const SNode &sj = P.snodes[J];
+          gen(J, sj, num_row_tiles(sj.nrows, sj.ncols, sj.ncb));
         }
+        int64_t cnt = (int64_t)P.tasks.size() - off;
+        if (cnt == 0) return -1;
+        // A short launch on the main stream (the lookahead chain) splits its tiles into row
+        // halves so that twice as many SMs share the work of this latency-critical step.
+        if (stream == 0 && (kind == K_TRSM || kind == K_GEMM) && 2 * cnt <= 152) {
+          std::vector<Int4> halves;
+          for (int64_t q = off; q < off + cnt; ++q) {
+            const Int4 a = P.tasks[q];
+            halves.push_back({a.a, a.b, a.c, a.d | (1 << 16)});
+            halves.push_back({a.a, a.b, a.c, a.d | (2 << 16)});
+          }
+          P.tasks.resize(off);
+          P.tasks.insert(P.tasks.end(), halves.begin(), halves.end());
+          cnt = (int64_t)halves.size();
+        }
+        Launch L{kind, l, off, cnt};
+        L.stream = stream;
+        L.wait = wait;
+        P.factor_launches.push_back(L);
+        (void)s;
+        return (int32_t)P.factor_launches.size() - 1;
+      };
+      auto potrf = [&](int32_t s) {
+        return emit(K_POTRF, s, 0, -1, [&](int32_t J, const SNode &sj, int32_t) {
+          if (s < sj.ncb) P.tasks.push_back({J, s, s, s});
+        });
+      };
+      auto trsm = [&](int32_t s) {
+        return emit(K_TRSM, s, 0, -1, [&](int32_t J, const SNode &sj, int32_t nrb) {
+          if (s < sj.ncb)
+            for (int32_t i = s + 1; i < nrb; ++i) P.tasks.push_back({J, i, s, s});
+        });
+      };
+      if (maxcb > 0) {
+        int32_t last_main = -1;  // latest main-stream launch (panel s is final after it)
+        auto note = [&](int32_t idx) {
+          if (idx >= 0) last_main = idx;
+        };
+        {
+          // the first dense launch of the level also joins any pending auxiliary work
+          const int32_t idx = potrf(0);
+          if (idx >= 0 && pending_join >= 0) {
+            P.factor_launches[idx].wait = pending_join;
+            pending_join = -1;
+          }
+          note(idx);
+        }
+        note(trsm(0));
+        int32_t rest_prev = -1;
+        for (int32_t s = 0; s + 1 < maxcb; ++s) {
+          const int32_t rest_idx = emit(K_GEMM, s, 1, last_main, [&](int32_t J, const SNode &sj, int32_t nrb) {
+            for (int32_t j = s + 2; j < sj.ncb; ++j)
+              for (int32_t i = j; i < nrb; ++i) P.tasks.push_back({J, i, j, s});
+          });
+          note(emit(K_GEMM, s, 0, rest_prev, [&](int32_t J, const SNode &sj, int32_t nrb) {
+            if (s + 1 < sj.ncb)
+              for (int32_t i = s + 1; i < nrb; ++i) P.tasks.push_back({J, i, s + 1, s});
+          }));
+          note(potrf(s + 1));
+          note(trsm(s + 1));
+          if (rest_idx >= 0) rest_prev = rest_idx;
+        }
+        // join: the next launch on the main stream waits for the last auxiliary launch
+        pending_join = rest_prev;
       }
     }
   }
   // Inverses of all diagonal tiles, in one launch after the factorization (the solve uses them).
+  // It joins the auxiliary stream's last launch.
   {
+    int32_t final_join = -1;
+    for (const Launch &L : P.factor_launches)
+      if (L.stream == 1) final_join = (int32_t)(&L - P.factor_launches.data());
     const int64_t off = (int64_t)P.tasks.size();
     for (int32_t J = 0; J < ns; ++J)
       for (int32_t t = 0; t < P.snodes[J].ncb; ++t) P.tasks.push_back({J, t, t, t});
-    if ((int64_t)P.tasks.size() > off) P.factor_launches.push_back({K_TRTRI, nlev, off, (int64_t)P.tasks.size() - off});
+    if ((int64_t)P.tasks.size() > off) {
+      Launch T{K_TRTRI, nlev, off, (int64_t)P.tasks.size() - off};
+      T.wait = final_join;
+      P.factor_launches.push_back(T);
+    }
   }
   // Solve schedules.
   for (int32_t l = 0; l < nlev; ++l) {
@@ -597,6 +668,14 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
       }
     }
     auto cols_of_tile = [](const SNode &s, int32_t t) { return std::min<int32_t>(NB, s.ncols - t * NB); };
+    // rows of the row tile q.b of a TRSM or GEMM task, or of its row half (bits 16+ of q.d)
+    auto task_rows = [](const SNode &s, const Int4 &q) {
+      const int64_t rb = row_tile_base(q.b, s.ncols, s.ncb);
+      int64_t tm = std::min<int64_t>(NB, (q.b < s.ncb ? s.ncols : s.nrows) - rb);
+      const int half = q.d >> 16;
+      if (half) tm = std::max<int64_t>(0, std::min<int64_t>(NB / 2, tm - (half - 1) * (NB / 2)));
+      return (double)tm;
+    };
     for (const Launch &L : P.factor_launches) {
       if (L.kind == K_UPDATE) continue;
       for (int64_t t = L.off; t < L.off + L.count; ++t) {
@@ -607,17 +686,16 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
           P.kind_flops[K_POTRF] += ts * (ts + 1) * (2 * ts + 1) / 6.0;
         } else if (L.kind == K_TRSM) {
           const double ts = cols_of_tile(s, q.c);
-          const int64_t rb = row_tile_base(q.b, s.ncols, s.ncb);
-          const double tm = std::min<int64_t>(NB, (q.b < s.ncb ? s.ncols : s.nrows) - rb);
-          P.kind_flops[K_TRSM] += tm * sq(ts);
+          P.kind_flops[K_TRSM] += task_rows(s, q) * sq(ts);
         } else if (L.kind == K_TRTRI) {
           const double ts = cols_of_tile(s, q.b);
           P.kind_flops[K_TRTRI] += ts * ts * ts / 3.0;
         } else if (L.kind == K_GEMM) {
-          const double ks = cols_of_tile(s, q.d), tn = cols_of_tile(s, q.c);
-          const int64_t rb = row_tile_base(q.b, s.ncols, s.ncb);
-          const double tm = std::min<int64_t>(NB, (q.b < s.ncb ? s.ncols : s.nrows) - rb);
-          P.kind_flops[K_GEMM] += q.b == q.c ? ks * tn * (tn + 1) : 2.0 * tm * tn * ks;
+          const double ks = cols_of_tile(s, q.d & 0xffff), tn = cols_of_tile(s, q.c);
+          const double tm = task_rows(s, q);
+          // diagonal tile: only its lower triangle is useful; a row half counts half of it
+          P.kind_flops[K_GEMM] += q.b == q.c ? ks * tn * (tn + 1) * ((q.d >> 16) ? 0.5 : 1.0)
+                                             : 2.0 * tm * tn * ks;
         }
       }
     }

@@ -29,7 +29,11 @@ class Sched:
         ue = s.export("upd_entries").reshape(-1, 5)
         self.ue = np.stack([ue[:, 0] & 0xffffffff, ue[:, 0] >> 32, ue[:, 1] & 0xffffffff, ue[:, 1] >> 32,
                             ue[:, 2], ue[:, 3], ue[:, 4]], 1)
-        self.launches = {k: s.export(k).reshape(-1, 4) for k in ("factor_launches", "fwd_launches", "bwd_launches")}
+        self.launches = {}
+        for k in ("factor_launches", "fwd_launches", "bwd_launches"):
+            raw = s.export(k).reshape(-1, 5)
+            self.launches[k] = np.stack([raw[:, 0] & 0xffffffff, raw[:, 1], raw[:, 2], raw[:, 3] >> 32,
+                                         (raw[:, 4] & 0xffffffff).astype(np.uint32).astype(np.int32)], 1)
 
     def J(self, j):
         f, l = int(self.sup[j]), int(self.sup[j + 1])
@@ -50,6 +54,34 @@ class Sched:
         rb = self.row_base(j, i)
         _, nc, _, _ = self.J(j)
         return slice(rb, rb + self.row_len(j, i)), slice(c * NB, min(nc, (c + 1) * NB))
+
+
+def concurrent_pairs(L):
+    """Pairs (i, j), i < j, of launches that may overlap: j is not ordered after i by stream
+    order (launches of one stream run in list order) or by a chain of waits."""
+    n = len(L)
+    after = [set() for _ in range(n)]  # launches that finish before launch j starts
+    last = {}
+    for j in range(n):
+        stream, wait = int(L[j][3]), int(L[j][4])
+        preds = []
+        if stream in last:
+            preds.append(last[stream])
+        if wait >= 0:
+            preds.append(wait)
+        for p in preds:
+            after[j] |= after[p] | {p}
+        last[stream] = j
+    return [(i, j) for j in range(n) for i in range(j) if i not in after[j]]
+
+
+def half_rows(tile, half):
+    """Rows of a tile restricted to its first (half 1) or second (half 2) 32 rows."""
+    rs, cs = tile
+    if half:
+        lo = rs.start + (half - 1) * (NB // 2)
+        rs = slice(lo, max(lo, min(rs.stop, lo + NB // 2)))
+    return rs, cs
 
 
 class Launch:
@@ -79,9 +111,11 @@ def emulate_factor(sc, panels, store):
     def get(j, r, c):
         return store[("L", j, r, c)]
 
-    for word0, off, count, _ in sc.launches["factor_launches"]:
-        kind = int(word0 & 0xffffffff)
+    record = []
+    for kind, off, count, _, _ in sc.launches["factor_launches"]:
+        kind = int(kind)
         L = Launch()
+        record.append(L)
         for t in range(int(off), int(off + count)):
             if kind == K_UPDATE:
                 j, bi, bj, e0, e1 = (int(v) for v in sc.ut[t])
@@ -103,7 +137,7 @@ def emulate_factor(sc, panels, store):
                     for b in range(n):
                         for k in range(kc):
                             L.read(t, ("L", K, c_lo + b, k))
-                    P = A @ B.T
+                    P = A @ B.T if A.size else np.zeros((0, B.shape[0]))
                     for a in range(m):
                         for b in range(n):
                             key = (rb + int(sc.rel[relr + a]) - rb, cb + int(sc.rel[relc + b]) - cb)
@@ -127,28 +161,29 @@ def emulate_factor(sc, panels, store):
                 elif kind == K_TRSM:
                     i, s = ti, tj
                     drs, dcs = sc.tile(j, s, s)
-                    rs, cs = sc.tile(j, i, s)
+                    rs, cs = half_rows(sc.tile(j, i, s), ts_ >> 16)
                     D = np.array([[get(j, r, c) for c in range(dcs.start, dcs.stop)] for r in range(drs.start, drs.stop)])
                     X = np.array([[get(j, r, c) for c in range(cs.start, cs.stop)] for r in range(rs.start, rs.stop)])
                     for r in range(drs.start, drs.stop):
                         for c in range(dcs.start, dcs.stop):
                             if r - drs.start >= c - dcs.start:
                                 L.read(t, ("L", j, r, c))
-                    X = np.linalg.solve(np.tril(D), X.T).T
+                    if X.size:
+                        X = np.linalg.solve(np.tril(D), X.T).T
                     for a, r in enumerate(range(rs.start, rs.stop)):
                         for b, c in enumerate(range(cs.start, cs.stop)):
                             L.write(t, ("L", j, r, c), X[a, b])
                 elif kind == K_GEMM:
-                    i, jj, s = ti, tj, ts_
-                    rs, cs = sc.tile(j, i, jj)
-                    ars, acs = sc.tile(j, i, s)
+                    i, jj, s = ti, tj, ts_ & 0xffff
+                    rs, cs = half_rows(sc.tile(j, i, jj), ts_ >> 16)
+                    ars, acs = half_rows(sc.tile(j, i, s), ts_ >> 16)
                     brs, _ = sc.tile(j, jj, s)
                     A = np.array([[get(j, r, c) for c in range(acs.start, acs.stop)] for r in range(ars.start, ars.stop)])
                     B = np.array([[get(j, r, c) for c in range(acs.start, acs.stop)] for r in range(brs.start, brs.stop)])
                     for r in list(range(ars.start, ars.stop)) + list(range(brs.start, brs.stop)):
                         for c in range(acs.start, acs.stop):
                             L.read(t, ("L", j, r, c))
-                    P = A @ B.T
+                    P = A @ B.T if A.size else np.zeros((0, B.shape[0]))
                     for a, r in enumerate(range(rs.start, rs.stop)):
                         for b, c in enumerate(range(cs.start, cs.stop)):
                             L.write(t, ("L", j, r, c), get(j, r, c) - P[a, b])
@@ -163,6 +198,12 @@ def emulate_factor(sc, panels, store):
             else:
                 raise AssertionError(f"unknown kind {kind}")
         L.commit(store)
+    # launches that may run at the same time (two streams) must not touch each other's elements
+    for i, j in concurrent_pairs(sc.launches["factor_launches"]):
+        wi, wj = set(record[i].writes), set(record[j].writes)
+        ri = {k for _, k in record[i].reads}
+        rj = {k for _, k in record[j].reads}
+        assert not (wi & (wj | rj)) and not (ri & wj), ("concurrent launches conflict", i, j)
 
 
 def emulate_solve(sc, store, y):
@@ -174,8 +215,8 @@ def emulate_solve(sc, store, y):
         return store[("I", j, s, a, b)]
 
     for name in ("fwd_launches", "bwd_launches"):
-        for word0, off, count, _ in sc.launches[name]:
-            kind = int(word0 & 0xffffffff)
+        for kind, off, count, _, _ in sc.launches[name]:
+            kind = int(kind)
             L = Launch()
             for t in range(int(off), int(off + count)):
                 j, ti, tc, _ = (int(v) for v in sc.tasks[t])
@@ -292,7 +333,7 @@ def test_emulator_detects_a_missing_launch():
     M = w.random_spd_pattern(150, 1.0, np.random.default_rng(3))
     s = S.Solver(M.n, M.Ap, M.Ai, M.perm, host_only=True)
     sc = Sched(s)
-    kinds = [int(x & 0xffffffff) for x in sc.launches["factor_launches"][:, 0]]
+    kinds = [int(x) for x in sc.launches["factor_launches"][:, 0]]
     sc.launches["factor_launches"] = np.delete(sc.launches["factor_launches"], kinds.index(K_GEMM), axis=0)
     o = oracle.Oracle(M.n, M.Ap, M.Ai, M.perm)
     o.factor(M.Ax)
@@ -322,3 +363,17 @@ def test_conflict_checker():
     L2.write(1, 5, 3.0)
     with pytest.raises(AssertionError):
         L2.commit({})  # a task reads what another task of the launch writes
+
+
+
+def test_lookahead_streams_are_used_and_ordered():
+    """Wide supernodes get a second stream: some trailing updates run concurrently with the
+    next panel's factorization, and every auxiliary launch waits for the panel it reads."""
+    M = w.random_spd_pattern(300, 1.0, np.random.default_rng(8))  # one supernode, 5 column tiles
+    s = S.Solver(M.n, M.Ap, M.Ai, M.perm, host_only=True)
+    L = Sched(s).launches["factor_launches"]
+    aux = [i for i in range(len(L)) if L[i][3] == 1]
+    assert aux, "no lookahead launch"
+    assert all(L[i][4] >= 0 for i in aux)
+    pairs = concurrent_pairs(L)
+    assert any(int(L[i][0]) == K_POTRF or int(L[j][0]) == K_POTRF for i, j in pairs)
