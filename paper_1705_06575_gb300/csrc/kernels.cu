@@ -195,9 +195,11 @@ __global__ void __launch_bounds__(THREADS) k_update(const SNode *__restrict__ sn
 }
 
 // ---------------------------------------------------------------------------------------------
-// (b) Dense Cholesky of diagonal tile s of supernode J, in shared memory, column by column.
-// A pivot that is not positive (or NaN) records its permuted column in *status (atomic min)
-// and is replaced by 1 so the kernel finishes with finite values.
+// (b) Dense Cholesky of diagonal tile s of supernode J, in shared memory, column by column
+// (right-looking). Column c+1 is on the critical path: warp 0 applies column c to it, takes its
+// pivot and scales it, while the other warps apply column c to columns c+2.. — one barrier per
+// column. A pivot that is not positive (or NaN) records its permuted column in *status (atomic
+// min) and is replaced by 1 so the kernel finishes with finite values.
 template <typename T>
 __global__ void __launch_bounds__(THREADS) k_potrf(const SNode *__restrict__ sn,
                                                    const Int4 *__restrict__ tasks,
@@ -209,13 +211,12 @@ __global__ void __launch_bounds__(THREADS) k_potrf(const SNode *__restrict__ sn,
   // pivots and this tile stay accurate; the result is rounded to T once).
   __shared__ double a[NB][NB + 1];                 // [col][row]
   __shared__ unsigned short tri[NB * (NB - 1) / 2];  // packed lower triangle: (i << 8) | j, i >= j
-  __shared__ double pinv;
   const Int4 t = tasks[toff + blockIdx.x];
   const SNode sj = sn[t.a];
   const int s = t.b;
   const int ts = min(NB, sj.ncols - s * NB);
   T *D = Lx + sj.lx + (int64_t)(s * NB) * sj.nrows + s * NB;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int idx = tid; idx < NB * NB; idx += THREADS) {
     int rr = idx % NB, c = idx / NB;
     a[c][rr] = (rr < ts && c < ts && rr >= c) ? (double)D[(int64_t)c * sj.nrows + rr] : 0.0;
@@ -229,26 +230,33 @@ __global__ void __launch_bounds__(THREADS) k_potrf(const SNode *__restrict__ sn,
     tri[idx] = (unsigned short)((i << 8) | (idx - i * (i + 1) / 2));
   }
   __syncthreads();
-  for (int c = 0; c < ts; ++c) {
-    if (tid == 0) {
-      double d = a[c][c];
-      if (!(d > 0.0)) {
-        atomicMin(status, (long long)(sj.first + s * NB + c));
-        d = 1.0;
-      }
-      const double x = rsqrt_newton(d);
-      a[c][c] = d * x;  // sqrt(d)
-      pinv = x;
+  // warp 0: pivot of column c (already updated by columns < c) and scaling of the column
+  auto finish_column = [&](int c) {
+    double d = a[c][c];
+    if (!(d > 0.0)) {
+      if (lane == 0) atomicMin(status, (long long)(sj.first + s * NB + c));
+      d = 1.0;
     }
-    __syncthreads();
-    if (tid > c && tid < ts) a[c][tid] *= pinv;  // column c of L
-    __syncthreads();
-    const int m = ts - c - 1;  // trailing lower triangle of order m, rows/cols c+1..ts-1
-    const int tot = m * (m + 1) / 2;
-    for (int idx = tid; idx < tot; idx += THREADS) {
-      const int ij = tri[idx];
-      const int rr = c + 1 + (ij >> 8), cc = c + 1 + (ij & 0xff);
-      a[cc][rr] = fma(-a[c][rr], a[c][cc], a[cc][rr]);
+    const double x = rsqrt_newton(d);
+    __syncwarp();
+    for (int r = c + lane; r < ts; r += 32) a[c][r] = r == c ? d * x : a[c][r] * x;  // d x = sqrt(d)
+  };
+  if (warp == 0 && ts > 0) finish_column(0);
+  __syncthreads();
+  for (int c = 0; c + 1 < ts; ++c) {
+    if (warp == 0) {
+      const double l = a[c][c + 1];
+      for (int r = c + 1 + lane; r < ts; r += 32) a[c + 1][r] = fma(-a[c][r], l, a[c + 1][r]);
+      __syncwarp();
+      finish_column(c + 1);
+    } else {
+      const int m = ts - c - 2;  // trailing lower triangle of order m, rows/cols c+2..ts-1
+      const int tot = m * (m + 1) / 2;
+      for (int idx = tid - 32; idx < tot; idx += THREADS - 32) {
+        const int ij = tri[idx];
+        const int rr = c + 2 + (ij >> 8), cc = c + 2 + (ij & 0xff);
+        a[cc][rr] = fma(-a[c][rr], a[c][cc], a[cc][rr]);
+      }
     }
     __syncthreads();
   }
