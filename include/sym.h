@@ -306,6 +306,13 @@ int sym_get_factor_host(sym_handle h, double *Lx_host);
 #define SYM_EXPORT_TASKS 22
 #define SYM_EXPORT_UPD_TASKS 23
 #define SYM_EXPORT_UPD_ENTRIES 24
+/* Forward solve by pushes: supernode J writes, per chunk ch of SOLVE_CW = 512 of its columns,
+ * the products L_J(r, chunk) y_J(chunk) of its rows r below the diagonal block to a buffer t at
+ * tx_J + ch (nrows_J - ncols_J) + (r - ncols_J), tx_J = sum over K < J of
+ * (nrows_K - ncols_K) ceil(ncols_K / 512); column g then subtracts the entries of t listed in
+ * contrib[contrib_ptr[g] .. contrib_ptr[g+1]) (ascending J, then ch). */
+#define SYM_EXPORT_CONTRIB_PTR 25 /* int64[n+1] */
+#define SYM_EXPORT_CONTRIB 26     /* int32[] */
 int64_t sym_export(sym_handle h, int32_t what, void *out);
 
 /* Per-kernel timing for measurement (no counterpart in the paper). With SYM_PROFILE_ON the
@@ -325,8 +332,10 @@ int sym_profile(sym_handle h, int32_t mode);
 #define SYM_KIND_TRSM 3      /* triangular solves of the tiles below a diagonal tile */
 #define SYM_KIND_GEMM 4      /* trailing updates inside a supernode */
 #define SYM_KIND_TRTRI 5     /* inverses of the diagonal tiles (for the solve) */
-#define SYM_KIND_FGATHER 11  /* forward solve: gather from descendants */
+#define SYM_KIND_FGATHER 11  /* forward solve restricted to a reach set: gather from descendants */
 #define SYM_KIND_FSTEP 12    /* forward solve: diagonal tile and updates inside a supernode */
+#define SYM_KIND_FPUSH 13    /* forward solve: products of solved supernodes for the rows below */
+#define SYM_KIND_FSUM 16     /* forward solve: columns subtract the pushed products */
 #define SYM_KIND_BGATHER 14  /* backward solve: gather from the rows below */
 #define SYM_KIND_BSTEP 15    /* backward solve: diagonal tile and updates inside a supernode */
 #define SYM_KIND_PERM 17     /* solve: permutations in and out */

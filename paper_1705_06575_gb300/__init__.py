@@ -52,6 +52,7 @@ EXPORTS = {
     "levelptr": (16, np.int32), "levellist": (17, np.int32), "lxptr": (18, np.int64),
     "factor_launches": (19, np.int64), "fwd_launches": (20, np.int64), "bwd_launches": (21, np.int64),
     "tasks": (22, np.int32), "upd_tasks": (23, np.int64), "upd_entries": (24, np.int64),
+    "contrib_ptr": (25, np.int64), "contrib": (26, np.int32),
 }
 
 
@@ -248,7 +249,7 @@ def sym_solve_host_ptr(h, nrhs, B, ldb, X, ldx):
 
 SYM_PROFILE_OFF, SYM_PROFILE_ON, SYM_PROFILE_RESET = 0, 1, 2
 KINDS = {"scatter": 0, "update": 1, "potrf": 2, "trsm": 3, "gemm": 4, "trtri": 5, "fgather": 11,
-         "fstep": 12, "bgather": 14, "bstep": 15, "perm": 17}
+         "fstep": 12, "fpush": 13, "bgather": 14, "bstep": 15, "fsum": 16, "perm": 17}
 
 
 def sym_profile(h, mode):

@@ -29,6 +29,8 @@ struct sym_handle_s {
   long long *d_status = nullptr;
   long long *h_status = nullptr;  // pinned: [0] holds the reset value, [1] receives the status
   double *d_y = nullptr;          // solve work array
+  void *d_cptr = nullptr, *d_contrib = nullptr;  // contribution lists of the forward solve
+  double *d_t = nullptr;          // forward-solve buffer (SOLVE_MAXRHS x tsize per matrix)
   int64_t y_cap = 0;
   double *d_stage = nullptr;      // staging for the host-pointer variants
   int64_t stage_cap = 0;
@@ -152,7 +154,7 @@ void release_device(sym_handle_s *h) {
   if (h->sgraph) cudaGraphExecDestroy(h->sgraph);
   if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
   void *ptrs[] = {h->d_sn, h->d_rows, h->d_rel, h->d_amap, h->d_updt, h->d_upde, h->d_tasks,
-                  h->d_perm, h->d_Lx, h->d_status, h->d_y, h->d_stage};
+                  h->d_perm, h->d_Lx, h->d_status, h->d_y, h->d_stage, h->d_cptr, h->d_contrib, h->d_t};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (h->h_status) cudaFreeHost(h->h_status);
@@ -252,6 +254,8 @@ int ensure_batch(sym_handle_s *h, int32_t nbatch) {
     if (!rc) rc = regrow((void **)&h->d_anorm, sizeof(double) * nb, "cudaMalloc(norms)");
   }
   if (!rc) rc = regrow((void **)&h->d_status, sizeof(long long) * nb, "cudaMalloc(status batch)");
+  if (!rc) rc = regrow((void **)&h->d_t, sizeof(double) * sym::SOLVE_MAXRHS * P.tsize * nb, "cudaMalloc(solve buffer batch)");
+  h->dp.t = h->d_t;
   if (!rc) {
     if (h->h_status) cudaFreeHost(h->h_status);
     h->h_status = nullptr;
@@ -418,6 +422,14 @@ int sym_analyze_perm(int64_t n, const int64_t *Ap, const int32_t *Ai, const int3
     if (!rc) rc = upload(P.upd_entries, &h->d_upde, bytes);
     if (!rc) rc = upload(P.tasks, &h->d_tasks, bytes);
     if (!rc) rc = upload(P.perm, &h->d_perm, bytes);
+    if (!rc) rc = upload(P.contrib_ptr, &h->d_cptr, bytes);
+    if (!rc) rc = upload(P.contrib, &h->d_contrib, bytes);
+    if (!rc) {
+      const int64_t tb = (int64_t)sizeof(double) * sym::SOLVE_MAXRHS * (P.tsize > 0 ? P.tsize : 1);
+      e = cudaMalloc(&h->d_t, tb);
+      if (e != cudaSuccess) rc = cuda_fail(e, "cudaMalloc(solve buffer)");
+      else bytes += tb;
+    }
     if (!rc && h->precision == SYM_PREC_FP64) {
       e = cudaMalloc(&h->d_Lx, sizeof(double) * (P.storage() > 0 ? P.storage() : 1));
       if (e != cudaSuccess) rc = cuda_fail(e, "cudaMalloc(L)");
@@ -481,6 +493,10 @@ int sym_analyze_perm(int64_t n, const int64_t *Ap, const int32_t *Ai, const int3
     h->dp.upd_entries = (const sym::UpdEntry *)h->d_upde;
     h->dp.tasks = (const sym::Int4 *)h->d_tasks;
     h->dp.perm = (const int32_t *)h->d_perm;
+    h->dp.cptr = (const int64_t *)h->d_cptr;
+    h->dp.contrib = (const int32_t *)h->d_contrib;
+    h->dp.t = h->d_t;
+    h->dp.tsize = P.tsize;
     h->dp.n = P.n;
     h->dp.nnz_a = P.nnz_a;
     h->dp.storage = P.storage();
@@ -616,6 +632,7 @@ int solve_impl(sym_handle h, int32_t nbatch, int32_t nrhs, const double *B, int6
   bt.y = n * (int64_t)nrhs;
   bt.b = bstride;
   bt.x = xstride;
+  bt.t = (int64_t)sym::SOLVE_MAXRHS * h->plan.tsize;
   sym::LaunchTrace tr, *trp = nullptr;
   if (h->profiling) {
     const size_t passes = (size_t)(nrhs + 7) / 8;
@@ -868,6 +885,8 @@ int64_t sym_export(sym_handle h, int32_t what, void *out) {
     EXP(SYM_EXPORT_LEVELPTR, levelptr)
     EXP(SYM_EXPORT_LEVELLIST, levellist)
     EXP(SYM_EXPORT_LXPTR, lxptr)
+    EXP(SYM_EXPORT_CONTRIB_PTR, contrib_ptr)
+    EXP(SYM_EXPORT_CONTRIB, contrib)
 #undef EXP
 #define EXPB(id, vec, words)                                                     \
   case id:                                                                       \

@@ -87,20 +87,19 @@ __device__ __forceinline__ void fma_chunk_dispatch(T (&r)[2][8], const T (*As)[N
 #undef SYM_CASE
 }
 
-// Reciprocal square root of d > 0 in FP64 by Newton-Raphson on f(x) = 1/x^2 - d:
-// x <- x + (x/2)(1 - d x^2). A single-precision seed has 23 correct bits; each step doubles them
-// (46, then beyond 53), so two steps reach double precision up to a few ulps. The chain is six
-// dependent FP64 operations, which keeps the serial pivot path of a Cholesky short on a GPU
-// whose FP64 pipe is narrow. Outside the single-precision normal range it falls back to 1/sqrt.
+// Reciprocal square root of d > 0 in FP64: with a single-precision seed x0 (relative error e0
+// of about 2^-22) and e = 1 - d x0^2, the exact value is x0 (1 - e)^(-1/2) =
+// x0 (1 + e/2 + 3e^2/8 + 5e^3/16 + ...). Keeping the terms through e^2 leaves a relative error of
+// about 5 e^3 / 16 < 2^-60, so one step reaches double precision up to rounding (a Householder
+// step of order 3). The chain is four dependent FP64 operations, which keeps the serial pivot
+// path of a Cholesky short on a GPU whose FP64 pipe is narrow. Outside the single-precision
+// normal range it falls back to 1/sqrt.
 __device__ __forceinline__ double rsqrt_newton(double d) {
   if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
-  double x = (double)rsqrtf((float)d);
-#pragma unroll
-  for (int it = 0; it < 2; ++it) {
-    const double e = fma(-d * x, x, 1.0);
-    x = fma(0.5 * x, e, x);
-  }
-  return x;
+  const double x0 = (double)rsqrtf((float)d);
+  const double e = fma(-d * x0, x0, 1.0);
+  const double p = fma(0.375, e, 0.5);
+  return fma(x0 * e, p, x0);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -398,6 +397,20 @@ __global__ void k_perm_out(const int32_t *__restrict__ perm, const V *__restrict
 }
 
 constexpr int MAXRHS = 8;  // right-hand sides handled per pass of the solve kernels
+static_assert(MAXRHS == SOLVE_MAXRHS, "solve pass width");
+
+// Runs STMT with the compile-time constant NR equal to the run-time count nr (1..MAXRHS).
+#define SYM_NR_DISPATCH(nr, STMT)           \
+  switch (nr) {                             \
+    case 1: { constexpr int NR = 1; STMT; } break; \
+    case 2: { constexpr int NR = 2; STMT; } break; \
+    case 3: { constexpr int NR = 3; STMT; } break; \
+    case 4: { constexpr int NR = 4; STMT; } break; \
+    case 5: { constexpr int NR = 5; STMT; } break; \
+    case 6: { constexpr int NR = 6; STMT; } break; \
+    case 7: { constexpr int NR = 7; STMT; } break; \
+    default: { constexpr int NR = 8; STMT; } break; \
+  }
 constexpr int BG = SOLVE_BG;  // columns per backward-gather CTA
 
 // Forward gather: y(cols of tile bj of J) -= sum over descendant entries of L_K(rows) y_K.
@@ -486,58 +499,157 @@ __global__ void __launch_bounds__(THREADS) k_fgather(const SNode *__restrict__ s
   cluster.sync();  // keep the other ranks' shared memory alive until rank 0 has read it
 }
 
+// Forward push (the right-looking half of the forward solve, Sec. 3.1's y_rows -= L_off y_J
+// written as a product per supernode): once the level's supernodes are solved, CTA {J, i, ch}
+// forms t = L_J(rows of row tile i, columns of chunk ch) y_J(chunk) for a row tile below J's
+// diagonal block and stores it at J's place in t. The panel is read once, column by column
+// (64 consecutive rows: coalesced); y_J's chunk is staged in shared memory. NR right-hand sides
+// are a template parameter so no multiply-add is issued for an absent one.
+template <typename T, typename V, int NR>
+__global__ void __launch_bounds__(THREADS) k_fpush(const SNode *__restrict__ sn, const Int4 *__restrict__ tasks,
+                                                   const T *__restrict__ Lx, const V *__restrict__ y,
+                                                   V *__restrict__ t, int64_t tsize, int64_t n, int r0,
+                                                   int64_t toff, const Batch bt) {
+  Lx += blockIdx.y * bt.lx;
+  y += blockIdx.y * bt.y;
+  t += blockIdx.y * bt.t;
+  __shared__ V ys[NR][SOLVE_CW];  // reused for the partial sums [4][NR][NB] after the products
+  const Int4 tk = tasks[toff + blockIdx.x];
+  const SNode sj = sn[tk.a];
+  const int64_t rb = d_row_tile_base(tk.b, sj.ncols, sj.ncb);
+  const int tm = d_row_tile_rows(tk.b, sj.ncols, sj.nrows, sj.ncb);
+  const int c0 = tk.c * SOLVE_CW, cw = min(SOLVE_CW, sj.ncols - c0);
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < NR * SOLVE_CW; idx += THREADS) {
+    const int c = idx % SOLVE_CW, q = idx / SOLVE_CW;
+    ys[q][c] = c < cw ? y[(int64_t)(r0 + q) * n + sj.first + c0 + c] : V(0);
+  }
+  __syncthreads();
+  const int r = tid & (NB - 1), g = tid >> 6;  // row r of the tile, columns g, g + 4, ...
+  V acc[NR];
+#pragma unroll
+  for (int q = 0; q < NR; ++q) acc[q] = V(0);
+  if (r < tm) {
+    const T *col = Lx + sj.lx + (int64_t)c0 * sj.nrows + rb + r;
+    constexpr int U = 8;  // loads in flight per thread
+    int c = g;
+    for (; c + 4 * (U - 1) < cw; c += 4 * U) {
+      V l[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) l[u] = (V)col[(int64_t)(c + 4 * u) * sj.nrows];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int q = 0; q < NR; ++q) acc[q] = fma(l[u], ys[q][c + 4 * u], acc[q]);
+    }
+    for (; c < cw; c += 4) {
+      const V l = (V)col[(int64_t)c * sj.nrows];
+#pragma unroll
+      for (int q = 0; q < NR; ++q) acc[q] = fma(l, ys[q][c], acc[q]);
+    }
+  }
+  __syncthreads();  // ys is reused below
+  V *part = &ys[0][0];  // [g][q][r]: 4 * NR * NB <= NR * SOLVE_CW
+#pragma unroll
+  for (int q = 0; q < NR; ++q) part[(g * NR + q) * NB + r] = acc[q];
+  __syncthreads();
+  const int64_t base = sj.tx + (int64_t)tk.c * (sj.nrows - sj.ncols) + (rb - sj.ncols);
+  for (int idx = tid; idx < NR * NB; idx += THREADS) {
+    const int rr = idx % NB, q = idx / NB;
+    if (rr < tm) {
+      const V v = (part[(0 * NR + q) * NB + rr] + part[(1 * NR + q) * NB + rr]) +
+                  (part[(2 * NR + q) * NB + rr] + part[(3 * NR + q) * NB + rr]);
+      t[(int64_t)q * tsize + base + rr] = v;
+    }
+  }
+}
+
+// Forward sum: column g of J subtracts what its descendants pushed to row g, the entries of t
+// named by its contribution list, added in list order (one thread per column).
+template <typename V, int NR>
+__global__ void __launch_bounds__(THREADS) k_fsum(const SNode *__restrict__ sn, const Int4 *__restrict__ tasks,
+                                                  const int64_t *__restrict__ cptr, const int32_t *__restrict__ contrib,
+                                                  const V *__restrict__ t, int64_t tsize, V *__restrict__ y,
+                                                  int64_t n, int r0, int64_t toff, const Batch bt) {
+  y += blockIdx.y * bt.y;
+  t += blockIdx.y * bt.t;
+  const Int4 tk = tasks[toff + blockIdx.x];
+  const SNode sj = sn[tk.a];
+  const int c = tk.b * 256 + threadIdx.x;
+  if (c >= sj.ncols) return;
+  const int64_t gcol = sj.first + c;
+  V acc[NR];
+#pragma unroll
+  for (int q = 0; q < NR; ++q) acc[q] = V(0);
+#pragma unroll 4
+  for (int64_t p = cptr[gcol]; p < cptr[gcol + 1]; ++p) {
+    const int64_t e = contrib[p];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) acc[q] += t[(int64_t)q * tsize + e];
+  }
+#pragma unroll
+  for (int q = 0; q < NR; ++q) y[(int64_t)(r0 + q) * n + gcol] -= acc[q];
+}
+
 // Backward gather: z(cols c0..c0+BG) -= L_J(rows below the diagonal block, cols)^T z(those rows).
-// One CTA per BG-column slice; each warp takes BG / 8 columns, lanes stride over the rows
-// (coalesced), and a warp shuffle reduces each column.
-template <typename T, typename V>
+// One CTA per BG-column slice. The rows are taken in chunks of 256: z at the chunk's rows is
+// gathered once into shared memory, then each warp takes two columns, its lanes striding over the
+// chunk's rows (coalesced panel reads), and a warp shuffle reduces each column at the end.
+template <typename T, typename V, int NR>
 __global__ void __launch_bounds__(THREADS) k_bgather(const SNode *__restrict__ sn,
                                                      const int32_t *__restrict__ rows,
                                                      const Int4 *__restrict__ tasks,
                                                      const T *__restrict__ Lx, V *__restrict__ y,
-                                                     int64_t n, int r0, int nr, int64_t toff, const Batch bt) {
+                                                     int64_t n, int r0, int64_t toff, const Batch bt) {
+  static_assert(BG == 2 * (THREADS / 32), "two columns per warp");
+  constexpr int RC = 256;
   Lx += blockIdx.y * bt.lx;
   y += blockIdx.y * bt.y;
+  __shared__ V zg[NR][RC];
   const Int4 t = tasks[toff + blockIdx.x];
   const SNode sj = sn[t.a];
   const int c0 = t.b * BG;
   const int tn = min(BG, sj.ncols - c0);
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int32_t *R = rows + sj.rowp;
-  for (int c = w; c < tn; c += THREADS / 32) {
-    const T *col = Lx + sj.lx + (int64_t)(c0 + c) * sj.nrows;
-    V s[MAXRHS];
+  // columns w and w + 8 of the slice; an absent column reads column c0 (valid) and is not stored
+  const int ca = w, cb = w + 8;
+  const T *cola = Lx + sj.lx + (int64_t)(c0 + (ca < tn ? ca : 0)) * sj.nrows;
+  const T *colb = Lx + sj.lx + (int64_t)(c0 + (cb < tn ? cb : 0)) * sj.nrows;
+  V sa[NR], sb[NR];
 #pragma unroll
-    for (int q = 0; q < MAXRHS; ++q) s[q] = V(0);
-    constexpr int U = 4;  // rows in flight per lane
-    int r = sj.ncols + lane;
-    for (; r + (U - 1) * 32 < sj.nrows; r += U * 32) {
-      V l[U];
-      int64_t g[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        l[u] = (V)col[r + u * 32];
-        g[u] = R[r + u * 32];
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-#pragma unroll
-        for (int q = 0; q < MAXRHS; ++q)
-          if (q < nr) s[q] = fma(l[u], y[(int64_t)(r0 + q) * n + g[u]], s[q]);
+  for (int q = 0; q < NR; ++q) sa[q] = sb[q] = V(0);
+  for (int rc0 = sj.ncols; rc0 < sj.nrows; rc0 += RC) {
+    const int rc = min(RC, sj.nrows - rc0);
+    for (int idx = tid; idx < NR * RC; idx += THREADS) {
+      const int rr = idx % RC, q = idx / RC;
+      if (rr < rc) zg[q][rr] = y[(int64_t)(r0 + q) * n + R[rc0 + rr]];
     }
-    for (; r < sj.nrows; r += 32) {
-      const V l = (V)col[r];
-      const int64_t g = R[r];
+    __syncthreads();
+    if (ca < tn) {
+#pragma unroll 4
+      for (int rr = lane; rr < rc; rr += 32) {
+        const V la = (V)cola[rc0 + rr], lb = (V)colb[rc0 + rr];
 #pragma unroll
-      for (int q = 0; q < MAXRHS; ++q)
-        if (q < nr) s[q] = fma(l, y[(int64_t)(r0 + q) * n + g], s[q]);
-    }
-#pragma unroll
-    for (int q = 0; q < MAXRHS; ++q) {
-      if (q < nr) {
-        V v = s[q];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) y[(int64_t)(r0 + q) * n + sj.first + c0 + c] -= v;
+        for (int q = 0; q < NR; ++q) {
+          const V z = zg[q][rr];
+          sa[q] = fma(la, z, sa[q]);
+          sb[q] = fma(lb, z, sb[q]);
+        }
       }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < NR; ++q) {
+    V va = sa[q], vb = sb[q];
+    for (int o = 16; o > 0; o >>= 1) {
+      va += __shfl_xor_sync(0xffffffffu, va, o);
+      vb += __shfl_xor_sync(0xffffffffu, vb, o);
+    }
+    if (lane == 0) {
+      if (ca < tn) y[(int64_t)(r0 + q) * n + sj.first + c0 + ca] -= va;
+      if (cb < tn) y[(int64_t)(r0 + q) * n + sj.first + c0 + cb] -= vb;
     }
   }
 }
@@ -894,6 +1006,7 @@ cudaError_t run_sweeps(const DevPlan &d, const std::vector<Launch> &fwd, const s
                        const Batch &bt) {
   const int64_t n = d.n;
   const unsigned nb = (unsigned)bt.count;
+  V *tbuf = reinterpret_cast<V *>(d.t);
   for (int r0 = 0; r0 < nrhs; r0 += MAXRHS) {
     const int nr = nrhs - r0 < MAXRHS ? nrhs - r0 : MAXRHS;
     for (const Launch &L : fwd) {
@@ -920,6 +1033,14 @@ cudaError_t run_sweeps(const DevPlan &d, const std::vector<Launch> &fwd, const s
         case S_FSTEP:
           k_fstep<T, V><<<dim3(g, nb), THREADS, step_smem<V>(), st>>>(d.sn, d.tasks, Lx, Linv, y, n, r0, nr, L.off, bt);
           break;
+        case S_FPUSH:
+          SYM_NR_DISPATCH(nr, (k_fpush<T, V, NR><<<dim3(g, nb), THREADS, 0, st>>>(
+                                  d.sn, d.tasks, Lx, y, tbuf, d.tsize, n, r0, L.off, bt)));
+          break;
+        case S_FSUM:
+          SYM_NR_DISPATCH(nr, (k_fsum<V, NR><<<dim3(g, nb), THREADS, 0, st>>>(
+                                  d.sn, d.tasks, d.cptr, d.contrib, tbuf, d.tsize, y, n, r0, L.off, bt)));
+          break;
         default:
           return cudaErrorInvalidValue;
       }
@@ -929,7 +1050,8 @@ cudaError_t run_sweeps(const DevPlan &d, const std::vector<Launch> &fwd, const s
       const unsigned g = (unsigned)L.count;
       switch (L.kind) {
         case S_BGATHER:
-          k_bgather<T, V><<<dim3(g, nb), THREADS, 0, st>>>(d.sn, d.rows, d.tasks, Lx, y, n, r0, nr, L.off, bt);
+          SYM_NR_DISPATCH(nr, (k_bgather<T, V, NR><<<dim3(g, nb), THREADS, 0, st>>>(
+                                  d.sn, d.rows, d.tasks, Lx, y, n, r0, L.off, bt)));
           break;
         case S_BSTEP:
           k_bstep<T, V><<<dim3(g, nb), THREADS, step_smem<V>(), st>>>(d.sn, d.tasks, Lx, Linv, y, n, r0, nr, L.off, bt);

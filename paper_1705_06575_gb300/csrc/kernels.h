@@ -17,6 +17,10 @@ struct DevPlan {
   const UpdEntry *upd_entries = nullptr;
   const Int4 *tasks = nullptr;
   const int32_t *perm = nullptr;
+  const int64_t *cptr = nullptr;     // contribution lists of the forward solve (n + 1)
+  const int32_t *contrib = nullptr;
+  void *t = nullptr;                 // forward-solve buffer: SOLVE_MAXRHS x tsize of the solve type
+  int64_t tsize = 0;
   int64_t n = 0;
   int64_t nnz_a = 0;
   int64_t storage = 0;
@@ -28,7 +32,7 @@ struct DevPlan {
 // default describes a single matrix.
 struct Batch {
   int32_t count = 1;
-  int64_t lx = 0, ax = 0, dinv = 0, y = 0, b = 0, x = 0;
+  int64_t lx = 0, ax = 0, dinv = 0, y = 0, b = 0, x = 0, t = 0;
 };
 
 // Second stream for the factor's lookahead: aux runs the launches with stream == 1 at low

@@ -15,6 +15,11 @@ namespace sym {
 constexpr int NB = 64;
 // Columns per CTA of the backward solve's gather from the rows below a diagonal block.
 constexpr int SOLVE_BG = 16;
+// Columns per CTA of the forward solve's push from a solved supernode to the rows below its
+// diagonal block (a supernode with more columns writes one partial result per chunk).
+constexpr int SOLVE_CW = 512;
+// Right-hand sides per pass of the solve kernels (the buffer t holds this many).
+constexpr int SOLVE_MAXRHS = 8;
 
 // One supernode as the kernels see it. Its panel is column-major, nrows x ncols, leading
 // dimension nrows, at Lx + lx. Row r of the panel is global row rows[rowp + r]; the first ncols
@@ -28,6 +33,9 @@ struct SNode {
   int64_t lx;     // offset into Lx
   int64_t dx;     // offset of the inverses of its diagonal tiles: tile s (order ts) is a
                   // column-major ts x ts block at dx + s * NB * NB
+  int64_t tx;     // offset of its pushed products in the forward solve's buffer t: chunk ch of
+                  // its columns gives t[tx + ch * (nrows - ncols) + (r - ncols)] for each row r
+                  // below the diagonal block
 };
 
 // Row tiling of a panel: the diagonal block is cut at multiples of NB, and the rows below it
@@ -79,10 +87,14 @@ enum Kind : int32_t {
   S_FGATHER = 11, // y_J(tile bj) -= sum_K L_K(rows in tile) y_K (int4 {J, bj, task, 0})
   S_FSTEP = 12,   // column tile s of J: y_i -= L_is L_ss^-1 y_s (CTAs i > s); CTA i = s writes
                   // the solved tiles s-1 (and s if last) (int4 {J, i, s, s})
+  S_FPUSH = 13,   // t_J(rows of row tile i, chunk ch) = L_J(tile rows, chunk cols) y_J(chunk cols)
+                  // for the row tiles below J's diagonal block (int4 {J, i, ch, 0})
   S_BGATHER = 14, // z_J(slice) -= L_J(off rows, slice)^T z(off rows) (int4 {J, slice, 0, 0}),
                   // slices of SOLVE_BG columns
   S_BSTEP = 15,   // column tile s of J: z_i -= L_si^T L_ss^-T z_s (CTAs i < s); CTA i = s writes
                   // the solved tiles s+1 (and 0 if s = 0) (int4 {J, i, s, s})
+  S_FSUM = 16,    // y_g -= sum of t over the contribution list of column g, for the columns
+                  // of J in block cb of 256 (int4 {J, cb, 0, 0})
   S_PERM = 17,    // y = P b and x = P^T y
   NUM_KINDS = 18,
 };
@@ -137,6 +149,13 @@ struct Plan {
   std::vector<Launch> factor_launches;
   std::vector<Launch> fwd_launches;
   std::vector<Launch> bwd_launches;
+  // Forward solve by pushes: t holds tsize entries per right-hand side; the contribution list of
+  // column g, contrib[contrib_ptr[g] .. contrib_ptr[g+1]), names the entries of t that column g
+  // subtracts (every row g below the diagonal block of a supernode, once per column chunk), in
+  // ascending supernode and chunk order.
+  int64_t tsize = 0;
+  std::vector<int64_t> contrib_ptr;
+  std::vector<int32_t> contrib;
   int32_t max_ncols = 0;
   // Algorithmic flops per kind for one factorization (solve kinds: per right-hand side): the
   // useful multiply-adds (x2), square roots and divisions, excluding the strict upper part of

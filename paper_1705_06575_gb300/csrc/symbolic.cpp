@@ -396,6 +396,32 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
       P.dinv_storage += (int64_t)(s.ncb - 1) * NB * NB + last * last;
     }
     P.max_ncols = std::max(P.max_ncols, s.ncols);
+    s.tx = P.tsize;
+    P.tsize += (int64_t)(s.nrows - s.ncols) * ((s.ncols + SOLVE_CW - 1) / SOLVE_CW);
+  }
+  // Contribution lists of the forward solve: row g below the diagonal block of J receives
+  // L_J(g, :) y_J, pushed as one partial product per column chunk of J.
+  if (P.tsize >= INT32_MAX) {
+    err = "forward-solve buffer exceeds 2^31 entries";
+    return SYM_ERR_LIMIT;
+  }
+  P.contrib_ptr.assign(n + 1, 0);
+  for (int32_t J = 0; J < ns; ++J) {
+    const SNode &sj = P.snodes[J];
+    const int32_t nch = (sj.ncols + SOLVE_CW - 1) / SOLVE_CW;
+    for (int32_t r = sj.ncols; r < sj.nrows; ++r) P.contrib_ptr[P.rows[sj.rowp + r] + 1] += nch;
+  }
+  for (int64_t g = 0; g < n; ++g) P.contrib_ptr[g + 1] += P.contrib_ptr[g];
+  P.contrib.resize(P.contrib_ptr[n]);
+  {
+    std::vector<int64_t> fill(P.contrib_ptr.begin(), P.contrib_ptr.end() - 1);
+    for (int32_t J = 0; J < ns; ++J) {
+      const SNode &sj = P.snodes[J];
+      const int32_t nch = (sj.ncols + SOLVE_CW - 1) / SOLVE_CW, off = sj.nrows - sj.ncols;
+      for (int32_t ch = 0; ch < nch; ++ch)
+        for (int32_t r = sj.ncols; r < sj.nrows; ++r)
+          P.contrib[fill[P.rows[sj.rowp + r]]++] = (int32_t)(sj.tx + (int64_t)ch * off + (r - sj.ncols));
+    }
   }
   P.amap.resize(P.nnz_a);
   for (int64_t j = 0; j < n; ++j)
@@ -412,13 +438,9 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
   //   Factor, per level: K_UPDATE over all tiles that receive descendant updates, then for each
   //   column tile s of the level's widest supernode: K_POTRF (diagonal tile s), K_TRSM (row
   //   tiles below it) and K_GEMM (trailing tiles of the same supernode).
-  //   Forward solve, per level ascending: S_FGATHER, then S_FDIAG / S_FGEMV per column tile.
-  //   Backward solve, per level descending: S_BGATHER, then S_BDIAG / S_BGEMV per column tile,
-  //   last tile first.
-  std::vector<int64_t> diag_task(0);  // per (J, s): UpdTask index of tile (s, s) or -1
-  std::vector<int64_t> diag_task_base(ns + 1, 0);
-  for (int32_t J = 0; J < ns; ++J) diag_task_base[J + 1] = diag_task_base[J] + P.snodes[J].ncb;
-  diag_task.assign(diag_task_base[ns], -1);
+  //   Forward solve, per level ascending: S_FSUM, S_FSTEP per column tile, S_FPUSH.
+  //   Backward solve, per level descending: S_BGATHER, then S_BSTEP per column tile, last tile
+  //   first.
   {
     struct Pending {
       int32_t bi, bj;
@@ -494,7 +516,6 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
           u.e0 = (int64_t)P.upd_entries.size();
           P.upd_entries.insert(P.upd_entries.end(), x.ents.begin(), x.ents.end());
           u.e1 = (int64_t)P.upd_entries.size();
-          if (x.bi == x.bj) diag_task[diag_task_base[x.J] + x.bj] = (int64_t)P.upd_tasks.size();
           P.upd_tasks.push_back(u);
         }
       }
@@ -596,25 +617,20 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
       P.factor_launches.push_back(T);
     }
   }
-  // Solve schedules.
+  // Solve schedules. Forward, per level: S_FSUM (columns subtract what their descendants
+  // pushed), S_FSTEP per column tile, S_FPUSH (the level's solved supernodes push their products
+  // to the rows below their diagonal blocks).
   for (int32_t l = 0; l < nlev; ++l) {
     int64_t off = (int64_t)P.tasks.size();
     int32_t maxcb = 0;
     for (int32_t t = P.levelptr[l]; t < P.levelptr[l + 1]; ++t) {
       const int32_t J = P.levellist[t];
-      maxcb = std::max(maxcb, P.snodes[J].ncb);
-      for (int32_t bj = 0; bj < P.snodes[J].ncb; ++bj) {
-        int64_t task = diag_task[diag_task_base[J] + bj];
-        if (task >= 0) P.tasks.push_back({J, bj, (int32_t)task, 0});
-      }
+      const SNode &sj = P.snodes[J];
+      maxcb = std::max(maxcb, sj.ncb);
+      if (P.contrib_ptr[sj.first + sj.ncols] > P.contrib_ptr[sj.first])
+        for (int32_t cb = 0; cb * 256 < sj.ncols; ++cb) P.tasks.push_back({J, cb, 0, 0});
     }
-    if ((int64_t)P.tasks.size() > off) {
-      // Few tiles: spread each tile's descendants over a cluster of CTAs.
-      const int64_t cnt = (int64_t)P.tasks.size() - off;
-      Launch L{S_FGATHER, l, off, cnt};
-      L.cluster = cnt < 304 ? 8 : (cnt < 1216 ? 2 : 1);
-      P.fwd_launches.push_back(L);
-    }
+    if ((int64_t)P.tasks.size() > off) P.fwd_launches.push_back({S_FSUM, l, off, (int64_t)P.tasks.size() - off});
     for (int32_t s = 0; s < maxcb; ++s) {
       off = (int64_t)P.tasks.size();
       for (int32_t t = P.levelptr[l]; t < P.levelptr[l + 1]; ++t) {
@@ -624,6 +640,15 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
       }
       if ((int64_t)P.tasks.size() > off) P.fwd_launches.push_back({S_FSTEP, l, off, (int64_t)P.tasks.size() - off});
     }
+    off = (int64_t)P.tasks.size();
+    for (int32_t t = P.levelptr[l]; t < P.levelptr[l + 1]; ++t) {
+      const int32_t J = P.levellist[t];
+      const SNode &sj = P.snodes[J];
+      const int32_t nrb = num_row_tiles(sj.nrows, sj.ncols, sj.ncb);
+      for (int32_t ch = 0; ch * SOLVE_CW < sj.ncols; ++ch)
+        for (int32_t i = sj.ncb; i < nrb; ++i) P.tasks.push_back({J, i, ch, 0});
+    }
+    if ((int64_t)P.tasks.size() > off) P.fwd_launches.push_back({S_FPUSH, l, off, (int64_t)P.tasks.size() - off});
   }
   for (int32_t l = nlev - 1; l >= 0; --l) {
     int64_t off = (int64_t)P.tasks.size();
@@ -664,7 +689,6 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
             pairs += (double)(E.m - (std::lower_bound(rr, rr + E.m, rc[b]) - rr));
           P.kind_flops[K_UPDATE] += 2.0 * k * pairs;
         }
-        if (u.bi == u.bj) P.kind_flops[S_FGATHER] += 2.0 * E.n * k;
       }
     }
     auto cols_of_tile = [](const SNode &s, int32_t t) { return std::min<int32_t>(NB, s.ncols - t * NB); };
@@ -710,6 +734,13 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
                                                 : 2.0 * cols_of_tile(s, q.b) * cols_of_tile(s, q.c);
           if (L.kind == S_BGATHER)
             P.kind_flops[L.kind] += 2.0 * (s.nrows - s.ncols) * std::min<int32_t>(SOLVE_BG, s.ncols - q.b * SOLVE_BG);
+          if (L.kind == S_FPUSH)
+            P.kind_flops[L.kind] += 2.0 * std::min<int64_t>(NB, s.nrows - row_tile_base(q.b, s.ncols, s.ncb)) *
+                                    std::min<int32_t>(SOLVE_CW, s.ncols - q.c * SOLVE_CW);
+          if (L.kind == S_FSUM) {
+            const int64_t g0 = s.first + (int64_t)q.b * 256, g1 = std::min<int64_t>(s.first + s.ncols, g0 + 256);
+            P.kind_flops[L.kind] += (double)(P.contrib_ptr[g1] - P.contrib_ptr[g0]);
+          }
         }
   }
   P.analyze_seconds = timer.seconds();

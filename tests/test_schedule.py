@@ -13,8 +13,9 @@ import workloads as w
 
 NB = 64
 BG = 16
+CW = 512  # columns per forward push chunk
 K_UPDATE, K_POTRF, K_TRSM, K_GEMM, K_TRTRI = 1, 2, 3, 4, 5
-S_FGATHER, S_FSTEP, S_BGATHER, S_BSTEP = 11, 12, 14, 15
+S_FGATHER, S_FSTEP, S_FPUSH, S_BGATHER, S_BSTEP, S_FSUM = 11, 12, 13, 14, 15, 16
 
 
 class Sched:
@@ -29,6 +30,13 @@ class Sched:
         ue = s.export("upd_entries").reshape(-1, 5)
         self.ue = np.stack([ue[:, 0] & 0xffffffff, ue[:, 0] >> 32, ue[:, 1] & 0xffffffff, ue[:, 1] >> 32,
                             ue[:, 2], ue[:, 3], ue[:, 4]], 1)
+        self.cptr = s.export("contrib_ptr")
+        self.contrib = s.export("contrib")
+        # offset of each supernode's pushed products: its rows below the diagonal block, once per
+        # column chunk, in supernode order
+        nc = np.diff(self.sup).astype(np.int64)
+        off = np.diff(self.rowptr).astype(np.int64) - nc
+        self.tx = np.concatenate([[0], np.cumsum(off * ((nc + CW - 1) // CW))])
         self.launches = {}
         for k in ("factor_launches", "fwd_launches", "bwd_launches"):
             raw = s.export(k).reshape(-1, 5)
@@ -240,6 +248,24 @@ def emulate_solve(sc, store, y):
                             acc[f + int(sc.rel[relc + b])] -= v
                     for key, v in acc.items():
                         L.write(t, key, v)
+                elif kind == S_FPUSH:
+                    i, ch = ti, tc
+                    rs, _ = sc.tile(j, i, 0)
+                    cols = range(ch * CW, min(nc, (ch + 1) * CW))
+                    for c in cols:
+                        L.read(t, f + c)
+                    for r in range(rs.start, rs.stop):
+                        v = sum(Lv(j, r, c) * y[f + c] for c in cols)
+                        L.write(t, ("t", int(sc.tx[j]) + ch * (nr - nc) + (r - nc)), v)
+                elif kind == S_FSUM:
+                    cb = ti
+                    for c in range(cb * 256, min(nc, (cb + 1) * 256)):
+                        g = f + c
+                        keys = [("t", int(e)) for e in sc.contrib[sc.cptr[g]:sc.cptr[g + 1]]]
+                        for k in keys:
+                            L.read(t, k)
+                        L.read(t, g)
+                        L.write(t, g, y[g] - sum(y[k] for k in keys))
                 elif kind == S_BGATHER:
                     c0 = ti * BG
                     for c in range(c0, min(nc, c0 + BG)):
@@ -288,6 +314,7 @@ def emulate_solve(sc, store, y):
     lambda: w.conduct3d(6, np.random.default_rng(2), "box"),
     lambda: w.random_spd_pattern(150, 1.0, np.random.default_rng(3)),      # one wide supernode: 3 tiles
     lambda: w.random_spd_pattern(220, 0.03, np.random.default_rng(4)),
+    lambda: w.wide_block(520, 40, np.random.default_rng(5)),                # two push chunks
 ])
 def test_schedule_emulation_reproduces_oracle(maker):
     M = maker()

@@ -271,6 +271,24 @@ def random_spd_pattern(n, density, rng, dominance=1.5):
     return Matrix(n, Ap, Ai, Ax, None, name=f"rand_{n}")
 
 
+def wide_block(nblock, ntail, rng):
+    """Natural-order pattern with one wide supernode: columns 0..nblock-1 are coupled densely and
+    every row of a first tail (ntail rows after the block) to column 0; a second tail of ntail rows
+    is coupled to the first tail's first column only. The factor's first supernode then has nblock
+    columns and the first tail as its rows below the diagonal block, and amalgamation with its
+    parent would add nblock * ntail explicit zeros. Diagonally dominant."""
+    n = nblock + 2 * ntail
+    r, c = np.tril_indices(nblock, -1)
+    r = np.concatenate([r, np.arange(nblock, nblock + ntail), np.arange(nblock + ntail, n)])
+    c = np.concatenate([c, np.zeros(ntail, dtype=r.dtype), np.full(ntail, nblock, dtype=r.dtype)])
+    wv = rng.uniform(0.5, 2.0, size=r.size)
+    s = np.zeros(n)
+    np.add.at(s, r, wv)
+    np.add.at(s, c, wv)
+    Ap, Ai, Ax = lower_csc(n, r, c, -wv, 1.5 * s + 1.0)
+    return Matrix(n, Ap, Ai, Ax, None, name=f"wide_{nblock}_{ntail}")
+
+
 def rhs(n, nrhs, rng):
     """Dense right-hand sides, column-major (n x nrhs), entries N(0,1)."""
     return np.asfortranarray(rng.standard_normal((n, nrhs)))
