@@ -18,6 +18,7 @@
 // atomics in the factorization (every tile is owned by one CTA, descendants are applied in a
 // fixed order, so results are deterministic).
 #include <cooperative_groups.h>
+#include <type_traits>
 
 #include <cstdint>
 #include <utility>
@@ -184,6 +185,122 @@ __global__ void __launch_bounds__(THREADS) k_update(const SNode *__restrict__ sn
         int a = lane + 32 * i, b = w + 8 * j;
         if (a < E.m && b < E.n) acc[pcol[b]][prow[a]] = r[i][j];
       }
+    __syncthreads();
+  }
+  __syncthreads();
+  for (int idx = tid; idx < NB * NB; idx += THREADS) {
+    int r = idx % NB, c = idx / NB;
+    if (r < tm && c < tn) C[(int64_t)c * sj.nrows + r] = acc[c][r];
+  }
+}
+
+// r[j] -= A[kk][a_j] * B[kk][b_j] for kk < kc and the first J element slots of this thread
+// (a_j = ab[j] & 0xff, b_j = ab[j] >> 8).
+template <int J, typename T>
+__device__ __forceinline__ void flat_chunk(T (&r)[16], const int (&ab)[16], const T (*As)[NB], const T (*Bs)[NB],
+                                           int kc) {
+#pragma unroll 2
+  for (int kk = 0; kk < kc; ++kk) {
+#pragma unroll
+    for (int j = 0; j < J; ++j) r[j] = fma(-As[kk][ab[j] & 0xff], Bs[kk][ab[j] >> 8], r[j]);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void flat_chunk_dispatch(T (&r)[16], const int (&ab)[16], const T (*As)[NB],
+                                                    const T (*Bs)[NB], int kc, int jw) {
+#define SYM_CASE(J) \
+  case J:           \
+    flat_chunk<J>(r, ab, As, Bs, kc); \
+    break;
+  switch (jw) {
+    SYM_CASE(1) SYM_CASE(2) SYM_CASE(3) SYM_CASE(4) SYM_CASE(5) SYM_CASE(6) SYM_CASE(7) SYM_CASE(8)
+    SYM_CASE(9) SYM_CASE(10) SYM_CASE(11) SYM_CASE(12) SYM_CASE(13) SYM_CASE(14) SYM_CASE(15) SYM_CASE(16)
+    default:
+      break;
+  }
+#undef SYM_CASE
+}
+
+// (a') The same external update for an FP64 factor, with a flat map of the entry's output
+// elements onto the threads: element e of an entry (e < m n, or e < m (m + 1) / 2 on a diagonal
+// tile, whose strictly upper part is never needed) goes to thread e % 256, slot e / 256. Every
+// multiply-add is then useful except in the last slot of a partial warp (the register-blocked
+// k_update computes whole 32-row halves and full squares on diagonal tiles: 92% useful on the
+// 64^3 workload). Each multiply-add takes its own two operands from shared memory, which the
+// narrow FP64 pipe leaves ample room for (one warp-wide DFMA per sub-partition every 64 cycles).
+// The accumulation order of every element is the one of k_update: the factor is bit-identical.
+template <typename T>
+__global__ void __launch_bounds__(THREADS, 2) k_update_flat(const SNode *__restrict__ sn,
+                                                            const UpdTask *__restrict__ tasks,
+                                                            const UpdEntry *__restrict__ ents,
+                                                            const int32_t *__restrict__ rel,
+                                                            T *__restrict__ Lx, int64_t toff, const Batch bt) {
+  Lx += blockIdx.y * bt.lx;
+  __shared__ T acc[NB][NB + 1];  // [col][row]
+  __shared__ T As[KCU][NB];
+  __shared__ T Bs[KCU][NB];
+  __shared__ int prow[NB], pcol[NB];
+  const UpdTask t = tasks[toff + blockIdx.x];
+  const SNode sj = sn[t.J];
+  const int64_t rb = d_row_tile_base(t.bi, sj.ncols, sj.ncb);
+  const int tm = d_row_tile_rows(t.bi, sj.ncols, sj.nrows, sj.ncb);
+  const int cb = t.bj * NB;
+  const int tn = min(NB, sj.ncols - cb);
+  const bool diag = t.bi == t.bj;  // rows and columns of the tile are the same positions
+  T *C = Lx + sj.lx + (int64_t)cb * sj.nrows + rb;
+  const int tid = threadIdx.x, w = tid >> 5;
+  for (int idx = tid; idx < NB * NB; idx += THREADS) {
+    int r = idx % NB, c = idx / NB;
+    acc[c][r] = (r < tm && c < tn) ? C[(int64_t)c * sj.nrows + r] : T(0);
+  }
+  for (int64_t e = t.e0; e < t.e1; ++e) {
+    const UpdEntry E = ents[e];
+    const SNode sk = sn[E.K];
+    if (tid < E.m) prow[tid] = rel[E.relr + tid] - (int)rb;
+    if (tid >= NB && tid - NB < E.n) pcol[tid - NB] = rel[E.relc + tid - NB] - cb;
+    __syncthreads();
+    const int cnt = diag ? E.m * (E.m + 1) / 2 : E.m * E.n;
+    const int nslot = (cnt + THREADS - 1) / THREADS;                          // <= 16
+    const int jw = THREADS * (nslot - 1) + 32 * w < cnt ? nslot : nslot - 1;  // warp-uniform
+    int ab[16];
+    T r[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int el = tid + THREADS * j;
+      int a = 0, b = 0;
+      if (el < cnt) {
+        if (diag) {  // row-major lower triangle: el = a (a + 1) / 2 + b, b <= a
+          a = (int)((sqrtf(8.0f * el + 1.0f) - 1.0f) * 0.5f);
+          while ((a + 1) * (a + 2) / 2 <= el) ++a;
+          while (a * (a + 1) / 2 > el) --a;
+          b = el - a * (a + 1) / 2;
+        } else {
+          a = el % E.m;
+          b = el / E.m;
+        }
+      }
+      ab[j] = a | (b << 8);
+      r[j] = el < cnt ? acc[pcol[b]][prow[a]] : T(0);
+    }
+    const T *Kp = Lx + sk.lx;
+    for (int k0 = 0; k0 < sk.ncols; k0 += KCU) {
+      const int kc = min(KCU, sk.ncols - k0);
+      for (int idx = tid; idx < KCU * NB; idx += THREADS) {
+        int a = idx % NB, kk = idx / NB;
+        const T *col = Kp + (int64_t)(k0 + kk) * sk.nrows;
+        As[kk][a] = (a < E.m && kk < kc) ? col[E.r_lo + a] : T(0);
+        Bs[kk][a] = (a < E.n && kk < kc) ? col[E.c_lo + a] : T(0);
+      }
+      __syncthreads();
+      flat_chunk_dispatch(r, ab, As, Bs, kc, jw);
+      __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int el = tid + THREADS * j;
+      if (el < cnt) acc[pcol[ab[j] >> 8]][prow[ab[j] & 0xff]] = r[j];
+    }
     __syncthreads();
   }
   __syncthreads();
@@ -972,7 +1089,10 @@ cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, co
     cudaError_t e = cudaSuccess;
     switch (L.kind) {
       case K_UPDATE:
-        e = launch_prio(k_update<T>, dim3(g, nb), 0, s, prio, d.sn, d.upd_tasks, d.upd_entries, d.rel, Lx, L.off, bt);
+        // the flat element map where the schedule asks for it (FP64 only); register-blocked tiles
+        e = std::is_same<T, double>::value && L.variant == 1
+                ? launch_prio(k_update_flat<T>, dim3(g, nb), 0, s, prio, d.sn, d.upd_tasks, d.upd_entries, d.rel, Lx, L.off, bt)
+                : launch_prio(k_update<T>, dim3(g, nb), 0, s, prio, d.sn, d.upd_tasks, d.upd_entries, d.rel, Lx, L.off, bt);
         break;
       case K_POTRF:
         e = launch_prio(k_potrf<T>, dim3(g, nb), 0, s, prio, d.sn, d.tasks, Lx, status, L.off, bt);

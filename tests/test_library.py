@@ -178,3 +178,37 @@ def test_reach_rejects_bad_patterns():
     for bad in ([M.n], [-1], [3, 3]):
         with pytest.raises(S.SymError):
             S.Reach(s.h, np.array(bad))
+
+
+@pytest.mark.parametrize("maker", [
+    lambda: w.cfg("laplace2d5_64"),
+    lambda: w.conduct3d(16, np.random.default_rng(3), "star"),
+    lambda: w.vector3d27(6, np.random.default_rng(4), sub=3),
+    lambda: w.random_spd_pattern(300, 0.05, np.random.default_rng(2)),
+])
+def test_update_entries_against_their_definition(maker):
+    """Every update entry of tile (bi, bj) of J lists a contiguous run of descendant K's rows whose
+    relative positions fall in the tile's rows (r_lo, m) and columns (c_lo, n), checked against
+    the rows and relative maps; on a diagonal tile the two runs coincide (m = n, r_lo = c_lo),
+    which the FP64 update kernel relies on to compute the lower triangle only."""
+    M = maker()
+    s = S.Solver(M.n, M.Ap, M.Ai, M.perm, host_only=True)
+    sup = s.export("super"); rp = s.export("rowptr"); rows = s.export("rows")
+    ut = s.export("upd_tasks").reshape(-1, 4)
+    ue = s.export("upd_entries").reshape(-1, 5)
+    NB = 64
+    for J, bi, bj, e0, e1 in zip(ut[:, 0] & 0xffffffff, ut[:, 0] >> 32, ut[:, 1], ut[:, 2], ut[:, 3]):
+        f, nc = int(sup[J]), int(sup[J + 1] - sup[J])
+        RJ = rows[rp[J]:rp[J + 1]]
+        ncb = (nc + NB - 1) // NB
+        rb = bi * NB if bi < ncb else nc + (bi - ncb) * NB
+        rend = min(rb + NB, nc if bi < ncb else len(RJ))
+        tile_rows = set(RJ[rb:rend].tolist())
+        tile_cols = set(range(f + bj * NB, f + min(nc, (bj + 1) * NB)))
+        for K, r_lo, c_lo, m, n in zip(ue[e0:e1, 0] & 0xffffffff, ue[e0:e1, 0] >> 32, ue[e0:e1, 1] & 0xffffffff,
+                                       ue[e0:e1, 1] >> 32, ue[e0:e1, 2]):
+            RK = rows[rp[K]:rp[K + 1]]
+            assert set(RK[r_lo:r_lo + m].tolist()) == tile_rows & set(RK.tolist())
+            assert set(RK[c_lo:c_lo + n].tolist()) == tile_cols & set(RK.tolist())
+            if bi == bj:
+                assert m == n and r_lo == c_lo
