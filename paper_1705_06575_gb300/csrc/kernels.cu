@@ -196,9 +196,10 @@ __global__ void __launch_bounds__(THREADS) k_update(const SNode *__restrict__ sn
 
 // r[j] -= A[kk][a_j] * B[kk][b_j] for kk < kc and the first J element slots of this thread
 // (a_j = ab[j] & 0xff, b_j = ab[j] >> 8).
+constexpr int FLAT_SLOTS = 8;  // output elements per thread and pass
 template <int J, typename T>
-__device__ __forceinline__ void flat_chunk(T (&r)[16], const int (&ab)[16], const T (*As)[NB], const T (*Bs)[NB],
-                                           int kc) {
+__device__ __forceinline__ void flat_chunk(T (&r)[FLAT_SLOTS], const int (&ab)[FLAT_SLOTS], const T (*As)[NB],
+                                           const T (*Bs)[NB], int kc) {
 #pragma unroll 2
   for (int kk = 0; kk < kc; ++kk) {
 #pragma unroll
@@ -207,15 +208,14 @@ __device__ __forceinline__ void flat_chunk(T (&r)[16], const int (&ab)[16], cons
 }
 
 template <typename T>
-__device__ __forceinline__ void flat_chunk_dispatch(T (&r)[16], const int (&ab)[16], const T (*As)[NB],
-                                                    const T (*Bs)[NB], int kc, int jw) {
+__device__ __forceinline__ void flat_chunk_dispatch(T (&r)[FLAT_SLOTS], const int (&ab)[FLAT_SLOTS],
+                                                    const T (*As)[NB], const T (*Bs)[NB], int kc, int jw) {
 #define SYM_CASE(J) \
   case J:           \
     flat_chunk<J>(r, ab, As, Bs, kc); \
     break;
   switch (jw) {
     SYM_CASE(1) SYM_CASE(2) SYM_CASE(3) SYM_CASE(4) SYM_CASE(5) SYM_CASE(6) SYM_CASE(7) SYM_CASE(8)
-    SYM_CASE(9) SYM_CASE(10) SYM_CASE(11) SYM_CASE(12) SYM_CASE(13) SYM_CASE(14) SYM_CASE(15) SYM_CASE(16)
     default:
       break;
   }
@@ -224,14 +224,16 @@ __device__ __forceinline__ void flat_chunk_dispatch(T (&r)[16], const int (&ab)[
 
 // (a') The same external update for an FP64 factor, with a flat map of the entry's output
 // elements onto the threads: element e of an entry (e < m n, or e < m (m + 1) / 2 on a diagonal
-// tile, whose strictly upper part is never needed) goes to thread e % 256, slot e / 256. Every
-// multiply-add is then useful except in the last slot of a partial warp (the register-blocked
-// k_update computes whole 32-row halves and full squares on diagonal tiles: 92% useful on the
-// 64^3 workload). Each multiply-add takes its own two operands from shared memory, which the
-// narrow FP64 pipe leaves ample room for (one warp-wide DFMA per sub-partition every 64 cycles).
-// The accumulation order of every element is the one of k_update: the factor is bit-identical.
+// tile, whose strictly upper part is never needed) goes to thread e % 256, slot e / 256; slots
+// are taken 8 at a time (one pass over ncols(K) per 2048 elements) to keep three CTAs per SM.
+// Every multiply-add is then useful except in the last slot of a partial warp (the
+// register-blocked k_update computes whole 32-row halves and full squares on diagonal tiles:
+// 92% useful on the 64^3 workload). Each multiply-add takes its own two operands from shared
+// memory, which the narrow FP64 pipe leaves ample room for (one warp-wide DFMA per
+// sub-partition every 64 cycles). The accumulation order of every element is the one of
+// k_update: the factor is bit-identical.
 template <typename T>
-__global__ void __launch_bounds__(THREADS, 2) k_update_flat(const SNode *__restrict__ sn,
+__global__ void __launch_bounds__(THREADS, 3) k_update_flat(const SNode *__restrict__ sn,
                                                             const UpdTask *__restrict__ tasks,
                                                             const UpdEntry *__restrict__ ents,
                                                             const int32_t *__restrict__ rel,
@@ -261,45 +263,48 @@ __global__ void __launch_bounds__(THREADS, 2) k_update_flat(const SNode *__restr
     if (tid >= NB && tid - NB < E.n) pcol[tid - NB] = rel[E.relc + tid - NB] - cb;
     __syncthreads();
     const int cnt = diag ? E.m * (E.m + 1) / 2 : E.m * E.n;
-    const int nslot = (cnt + THREADS - 1) / THREADS;                          // <= 16
-    const int jw = THREADS * (nslot - 1) + 32 * w < cnt ? nslot : nslot - 1;  // warp-uniform
-    int ab[16];
-    T r[16];
+    for (int e0 = 0; e0 < cnt; e0 += FLAT_SLOTS * THREADS) {  // block-uniform passes
+      const int rem = cnt - e0;
+      const int nslot = min(FLAT_SLOTS, (rem + THREADS - 1) / THREADS);
+      const int jw = THREADS * (nslot - 1) + 32 * w < rem ? nslot : nslot - 1;  // warp-uniform
+      int ab[FLAT_SLOTS];
+      T r[FLAT_SLOTS];
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      const int el = tid + THREADS * j;
-      int a = 0, b = 0;
-      if (el < cnt) {
-        if (diag) {  // row-major lower triangle: el = a (a + 1) / 2 + b, b <= a
-          a = (int)((sqrtf(8.0f * el + 1.0f) - 1.0f) * 0.5f);
-          while ((a + 1) * (a + 2) / 2 <= el) ++a;
-          while (a * (a + 1) / 2 > el) --a;
-          b = el - a * (a + 1) / 2;
-        } else {
-          a = el % E.m;
-          b = el / E.m;
+      for (int j = 0; j < FLAT_SLOTS; ++j) {
+        const int el = e0 + tid + THREADS * j;
+        int a = 0, b = 0;
+        if (el < cnt) {
+          if (diag) {  // row-major lower triangle: el = a (a + 1) / 2 + b, b <= a
+            a = (int)((sqrtf(8.0f * el + 1.0f) - 1.0f) * 0.5f);
+            while ((a + 1) * (a + 2) / 2 <= el) ++a;
+            while (a * (a + 1) / 2 > el) --a;
+            b = el - a * (a + 1) / 2;
+          } else {
+            a = el % E.m;
+            b = el / E.m;
+          }
         }
+        ab[j] = a | (b << 8);
+        r[j] = el < cnt ? acc[pcol[b]][prow[a]] : T(0);
       }
-      ab[j] = a | (b << 8);
-      r[j] = el < cnt ? acc[pcol[b]][prow[a]] : T(0);
-    }
-    const T *Kp = Lx + sk.lx;
-    for (int k0 = 0; k0 < sk.ncols; k0 += KCU) {
-      const int kc = min(KCU, sk.ncols - k0);
-      for (int idx = tid; idx < KCU * NB; idx += THREADS) {
-        int a = idx % NB, kk = idx / NB;
-        const T *col = Kp + (int64_t)(k0 + kk) * sk.nrows;
-        As[kk][a] = (a < E.m && kk < kc) ? col[E.r_lo + a] : T(0);
-        Bs[kk][a] = (a < E.n && kk < kc) ? col[E.c_lo + a] : T(0);
+      const T *Kp = Lx + sk.lx;
+      for (int k0 = 0; k0 < sk.ncols; k0 += KCU) {
+        const int kc = min(KCU, sk.ncols - k0);
+        for (int idx = tid; idx < KCU * NB; idx += THREADS) {
+          int a = idx % NB, kk = idx / NB;
+          const T *col = Kp + (int64_t)(k0 + kk) * sk.nrows;
+          As[kk][a] = (a < E.m && kk < kc) ? col[E.r_lo + a] : T(0);
+          Bs[kk][a] = (a < E.n && kk < kc) ? col[E.c_lo + a] : T(0);
+        }
+        __syncthreads();
+        flat_chunk_dispatch(r, ab, As, Bs, kc, jw);
+        __syncthreads();
       }
-      __syncthreads();
-      flat_chunk_dispatch(r, ab, As, Bs, kc, jw);
-      __syncthreads();
-    }
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      const int el = tid + THREADS * j;
-      if (el < cnt) acc[pcol[ab[j] >> 8]][prow[ab[j] & 0xff]] = r[j];
+      for (int j = 0; j < FLAT_SLOTS; ++j) {
+        const int el = e0 + tid + THREADS * j;
+        if (el < cnt) acc[pcol[ab[j] >> 8]][prow[ab[j] & 0xff]] = r[j];
+      }
     }
     __syncthreads();
   }
