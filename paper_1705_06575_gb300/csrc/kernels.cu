@@ -1094,8 +1094,9 @@ cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, co
     cudaError_t e = cudaSuccess;
     switch (L.kind) {
       case K_UPDATE:
-        // the flat element map where the schedule asks for it (FP64 only); register-blocked tiles
-        e = std::is_same<T, double>::value && L.variant == 1
+        // FP64: flat element map (the FP64 pipe is the bound and every issued DFMA should be
+        // useful); FP32: register-blocked tiles (operand reuse matters at the FP32 rate)
+        e = std::is_same<T, double>::value
                 ? launch_prio(k_update_flat<T>, dim3(g, nb), 0, s, prio, d.sn, d.upd_tasks, d.upd_entries, d.rel, Lx, L.off, bt)
                 : launch_prio(k_update<T>, dim3(g, nb), 0, s, prio, d.sn, d.upd_tasks, d.upd_entries, d.rel, Lx, L.off, bt);
         break;

@@ -107,7 +107,7 @@ struct Launch {
   int32_t cluster = 1;  // CTAs per task (a thread-block cluster) where the kernel supports it
   int32_t stream = 0;   // 0: the main (high-priority) stream, 1: the auxiliary (low-priority) one
   int32_t wait = -1;    // index of an earlier launch of this list to wait for (other stream), or -1
-  int32_t variant = 0;  // kernel variant (K_UPDATE: 1 = flat element map for an FP64 factor)
+  int32_t pad = 0;
 };
 
 struct Int4 {

@@ -504,21 +504,6 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
       std::stable_sort(lt.begin(), lt.end(), [](const LTask &x, const LTask &y) { return x.work > y.work; });
       if (!lt.empty()) {
         Launch U{K_UPDATE, l, (int64_t)P.upd_tasks.size(), (int64_t)lt.size()};
-        // Kernel variant: the flat element map when the level's updates are long inner products
-        // (work-weighted mean ncols(K) >= 64: the FP64 pipe is the bound and every issued DFMA
-        // should be useful), the register-blocked tiles otherwise (short updates are bound by
-        // latency, where the blocked kernel's higher occupancy pays).
-        {
-          double wsum = 0, wk = 0;
-          for (const LTask &x : lt)
-            for (const UpdEntry &e : x.ents) {
-              const double k = (double)P.snodes[e.K].ncols;
-              const double wgt = (double)e.m * e.n * k;
-              wsum += wgt;
-              wk += wgt * k;
-            }
-          U.variant = (wsum > 0 && wk >= 64.0 * wsum) ? 1 : 0;
-        }
         U.wait = pending_join;
         pending_join = -1;
         P.factor_launches.push_back(U);

@@ -404,27 +404,3 @@ def test_lookahead_streams_are_used_and_ordered():
     assert all(L[i][4] >= 0 for i in aux)
     pairs = concurrent_pairs(L)
     assert any(int(L[i][0]) == K_POTRF or int(L[j][0]) == K_POTRF for i, j in pairs)
-
-
-@pytest.mark.parametrize("maker", [lambda: w.cfg("conduct3d7_64"), lambda: w.cfg("dd2d9_128"),
-                                   lambda: w.conduct3d(20, np.random.default_rng(5), "star")])
-def test_update_kernel_variant_rule(maker):
-    """An update launch asks for the flat element map exactly when the work-weighted mean inner
-    dimension ncols(K) of its entries is at least 64 (recomputed here from the exported tasks)."""
-    M = maker()
-    s = S.Solver(M.n, M.Ap, M.Ai, M.perm, host_only=True)
-    sc = Sched(s)
-    raw = s.export("factor_launches").reshape(-1, 5)
-    nc = np.diff(sc.sup)
-    for (kind, off, count, _, _), variant in zip(sc.launches["factor_launches"], raw[:, 4] >> 32):
-        if kind != K_UPDATE:
-            assert variant == 0
-            continue
-        wsum = wk = 0.0
-        for t in range(off, off + count):
-            _, _, _, e0, e1 = sc.ut[t]
-            for K, _, _, m, n, _, _ in sc.ue[e0:e1]:
-                wgt = float(m) * n * nc[K]
-                wsum += wgt
-                wk += wgt * nc[K]
-        assert variant == (1 if wk >= 64.0 * wsum else 0)
