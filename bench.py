@@ -289,6 +289,18 @@ def bench_batched(S, torch, args, stream, barrier, world):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
+    # per-kernel breakdown of the batched step (profiled pass, kernel by kernel)
+    s.profile(S.SYM_PROFILE_RESET)
+    s.profile(S.SYM_PROFILE_ON)
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    s.profile(S.SYM_PROFILE_OFF)
+    kinds = {}
+    for name, kid in S.KINDS.items():
+        kms, knl, kfl = s.profile_read(kid)
+        if knl:
+            kinds[name] = {"ms_per_step": kms / args.steps, "launches_per_step": knl / args.steps}
     Xh = X.cpu().numpy()
     worst = 0.0
     for b in (0, nb // 2, nb - 1):
@@ -314,7 +326,7 @@ def bench_batched(S, torch, args, stream, barrier, world):
     one.close()
     return {"value": info.flops * nb * world / (ms * 1e-3) / 1e9, "unit": "GFLOP/s", "ms_per_step": ms,
             "matrices": nb, "n": M.n, "nnz_l_per_matrix": info.nnz_l, "backward_error": worst,
-            "ms_sequential_calls": ms_seq, "speedup_vs_sequential": ms_seq / ms, "dtype": "f64",
+            "ms_sequential_calls": ms_seq, "speedup_vs_sequential": ms_seq / ms, "kernels": kinds, "dtype": "f64",
             "definition": "512 x (factor + 1-RHS solve) of the 128^2 9-point pattern per step"}
 
 

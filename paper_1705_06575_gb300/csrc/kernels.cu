@@ -33,6 +33,17 @@ namespace {
 constexpr int THREADS = 256;
 constexpr int KC = 16;  // inner-dimension chunk staged in shared memory (k_gemm)
 constexpr int KCU = 8;  // the same for k_update, whose accumulator tile also lives in shared memory
+// Chunks of the register-blocked kernels per storage type: FP64 is bound by its pipe, so small
+// chunks suffice; at the FP32 rate a chunk must carry enough multiply-adds to cover the latency
+// of staging the next one.
+template <typename T>
+struct Chunk {
+  static constexpr int upd = KCU, gemm = KC;
+};
+template <>
+struct Chunk<float> {
+  static constexpr int upd = 32, gemm = 64;
+};
 
 __device__ __forceinline__ int64_t d_row_tile_base(int32_t i, int32_t ncols, int32_t ncb) {
   return i < ncb ? (int64_t)i * NB : (int64_t)ncols + (int64_t)(i - ncb) * NB;
@@ -134,8 +145,9 @@ __global__ void __launch_bounds__(THREADS) k_update(const SNode *__restrict__ sn
                                                     T *__restrict__ Lx, int64_t toff, const Batch bt) {
   Lx += blockIdx.y * bt.lx;
   __shared__ T acc[NB][NB + 1];  // [col][row]
-  __shared__ T As[KCU][NB];
-  __shared__ T Bs[KCU][NB];
+  constexpr int KU = Chunk<T>::upd;
+  __shared__ T As[KU][NB];
+  __shared__ T Bs[KU][NB];
   __shared__ int prow[NB], pcol[NB];
   const UpdTask t = tasks[toff + blockIdx.x];
   const SNode sj = sn[t.J];
@@ -145,9 +157,9 @@ __global__ void __launch_bounds__(THREADS) k_update(const SNode *__restrict__ sn
   const int tn = min(NB, sj.ncols - cb);
   T *C = Lx + sj.lx + (int64_t)cb * sj.nrows + rb;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  for (int idx = tid; idx < NB * NB; idx += THREADS) {
-    int r = idx % NB, c = idx / NB;
-    acc[c][r] = (r < tm && c < tn) ? C[(int64_t)c * sj.nrows + r] : T(0);
+  for (int idx = tid; idx < tm * tn; idx += THREADS) {  // only the tile's own part is read
+    int r = idx % tm, c = idx / tm;
+    acc[c][r] = C[(int64_t)c * sj.nrows + r];
   }
   for (int64_t e = t.e0; e < t.e1; ++e) {
     const UpdEntry E = ents[e];
@@ -166,16 +178,16 @@ __global__ void __launch_bounds__(THREADS) k_update(const SNode *__restrict__ sn
         r[i][j] = (a < E.m && b < E.n) ? acc[pcol[b]][prow[a]] : T(0);
       }
     const T *Kp = Lx + sk.lx;
-    for (int k0 = 0; k0 < sk.ncols; k0 += KCU) {
-      const int kc = min(KCU, sk.ncols - k0);
-      for (int idx = tid; idx < KCU * NB; idx += THREADS) {
+    for (int k0 = 0; k0 < sk.ncols; k0 += KU) {
+      const int kc = min(KU, sk.ncols - k0);
+      for (int idx = tid; idx < KU * NB; idx += THREADS) {
         int a = idx % NB, kk = idx / NB;
         const T *col = Kp + (int64_t)(k0 + kk) * sk.nrows;
         As[kk][a] = (a < E.m && kk < kc) ? col[E.r_lo + a] : T(0);
         Bs[kk][a] = (a < E.n && kk < kc) ? col[E.c_lo + a] : T(0);
       }
       __syncthreads();
-      fma_chunk_dispatch<KCU>(r, As, Bs, kc, lane, w, ni, nj);
+      fma_chunk_dispatch<KU>(r, As, Bs, kc, lane, w, ni, nj);
       __syncthreads();
     }
 #pragma unroll
@@ -188,9 +200,9 @@ __global__ void __launch_bounds__(THREADS) k_update(const SNode *__restrict__ sn
     __syncthreads();
   }
   __syncthreads();
-  for (int idx = tid; idx < NB * NB; idx += THREADS) {
-    int r = idx % NB, c = idx / NB;
-    if (r < tm && c < tn) C[(int64_t)c * sj.nrows + r] = acc[c][r];
+  for (int idx = tid; idx < tm * tn; idx += THREADS) {
+    int r = idx % tm, c = idx / tm;
+    C[(int64_t)c * sj.nrows + r] = acc[c][r];
   }
 }
 
@@ -252,9 +264,9 @@ __global__ void __launch_bounds__(THREADS, 3) k_update_flat(const SNode *__restr
   const bool diag = t.bi == t.bj;  // rows and columns of the tile are the same positions
   T *C = Lx + sj.lx + (int64_t)cb * sj.nrows + rb;
   const int tid = threadIdx.x, w = tid >> 5;
-  for (int idx = tid; idx < NB * NB; idx += THREADS) {
-    int r = idx % NB, c = idx / NB;
-    acc[c][r] = (r < tm && c < tn) ? C[(int64_t)c * sj.nrows + r] : T(0);
+  for (int idx = tid; idx < tm * tn; idx += THREADS) {  // only the tile's own part is read
+    int r = idx % tm, c = idx / tm;
+    acc[c][r] = C[(int64_t)c * sj.nrows + r];
   }
   for (int64_t e = t.e0; e < t.e1; ++e) {
     const UpdEntry E = ents[e];
@@ -309,9 +321,9 @@ __global__ void __launch_bounds__(THREADS, 3) k_update_flat(const SNode *__restr
     __syncthreads();
   }
   __syncthreads();
-  for (int idx = tid; idx < NB * NB; idx += THREADS) {
-    int r = idx % NB, c = idx / NB;
-    if (r < tm && c < tn) C[(int64_t)c * sj.nrows + r] = acc[c][r];
+  for (int idx = tid; idx < tm * tn; idx += THREADS) {
+    int r = idx % tm, c = idx / tm;
+    C[(int64_t)c * sj.nrows + r] = acc[c][r];
   }
 }
 
@@ -338,13 +350,14 @@ __global__ void __launch_bounds__(THREADS) k_potrf(const SNode *__restrict__ sn,
   const int ts = min(NB, sj.ncols - s * NB);
   T *D = Lx + sj.lx + (int64_t)(s * NB) * sj.nrows + s * NB;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int idx = tid; idx < NB * NB; idx += THREADS) {
-    int rr = idx % NB, c = idx / NB;
-    a[c][rr] = (rr < ts && c < ts && rr >= c) ? (double)D[(int64_t)c * sj.nrows + rr] : 0.0;
+  for (int idx = tid; idx < ts * ts; idx += THREADS) {  // only the lower triangle is read
+    int rr = idx % ts, c = idx / ts;
+    if (rr >= c) a[c][rr] = (double)D[(int64_t)c * sj.nrows + rr];
   }
   // Row-major packed index of the lower triangle: idx = i (i + 1) / 2 + j. The first
-  // m (m + 1) / 2 entries are the triangle of order m, whatever m is.
-  for (int idx = tid; idx < NB * (NB - 1) / 2; idx += THREADS) {
+  // m (m + 1) / 2 entries are the triangle of order m, whatever m is; the largest trailing
+  // triangle has order ts - 2.
+  for (int idx = tid; idx < ts * (ts - 1) / 2; idx += THREADS) {
     int i = (int)((sqrtf(8.0f * idx + 1.0f) - 1.0f) * 0.5f);
     while ((i + 1) * (i + 2) / 2 <= idx) ++i;
     while (i * (i + 1) / 2 > idx) --i;
@@ -381,9 +394,9 @@ __global__ void __launch_bounds__(THREADS) k_potrf(const SNode *__restrict__ sn,
     }
     __syncthreads();
   }
-  for (int idx = tid; idx < NB * NB; idx += THREADS) {
-    int rr = idx % NB, c = idx / NB;
-    if (rr < ts && c < ts) D[(int64_t)c * sj.nrows + rr] = rr >= c ? (T)a[c][rr] : T(0);
+  for (int idx = tid; idx < ts * ts; idx += THREADS) {
+    int rr = idx % ts, c = idx / ts;
+    D[(int64_t)c * sj.nrows + rr] = rr >= c ? (T)a[c][rr] : T(0);
   }
 }
 
@@ -411,10 +424,13 @@ __global__ void __launch_bounds__(THREADS) k_trsm(const SNode *__restrict__ sn,
   const T *D = Lx + sj.lx + (int64_t)(s * NB) * sj.nrows + s * NB;
   T *B = Lx + sj.lx + (int64_t)(s * NB) * sj.nrows + rb;
   const int tid = threadIdx.x;
-  for (int idx = tid; idx < NB * NB; idx += THREADS) {
-    int r = idx % NB, c = idx / NB;
-    Ls[c][r] = (r < ts && c < ts && r >= c) ? D[(int64_t)c * sj.nrows + r] : T(0);
-    X[c][r] = (r < tm && c < ts) ? B[(int64_t)c * sj.nrows + r] : T(0);
+  for (int idx = tid; idx < ts * ts; idx += THREADS) {  // lower triangle of L_ss
+    int r = idx % ts, c = idx / ts;
+    if (r >= c) Ls[c][r] = D[(int64_t)c * sj.nrows + r];
+  }
+  for (int idx = tid; idx < tm * ts; idx += THREADS) {
+    int r = idx % tm, c = idx / tm;
+    X[c][r] = B[(int64_t)c * sj.nrows + r];
   }
   __syncthreads();
   if (tid < ts) dinv[tid] = T(1) / Ls[tid][tid];
@@ -429,9 +445,9 @@ __global__ void __launch_bounds__(THREADS) k_trsm(const SNode *__restrict__ sn,
     if (g == 0 && r < tm) X[c][r] *= dinv[c];
   }
   __syncthreads();
-  for (int idx = tid; idx < NB * NB; idx += THREADS) {
-    int r = idx % NB, c = idx / NB;
-    if (r < tm && c < ts) B[(int64_t)c * sj.nrows + r] = X[c][r];
+  for (int idx = tid; idx < tm * ts; idx += THREADS) {
+    int r = idx % tm, c = idx / tm;
+    B[(int64_t)c * sj.nrows + r] = X[c][r];
   }
 }
 
@@ -441,8 +457,9 @@ __global__ void __launch_bounds__(THREADS) k_gemm(const SNode *__restrict__ sn,
                                                   const Int4 *__restrict__ tasks,
                                                   T *__restrict__ Lx, int64_t toff, const Batch bt) {
   Lx += blockIdx.y * bt.lx;
-  __shared__ T As[KC][NB];
-  __shared__ T Bs[KC][NB];
+  constexpr int KG = Chunk<T>::gemm;
+  __shared__ T As[KG][NB];
+  __shared__ T Bs[KG][NB];
   const Int4 t = tasks[toff + blockIdx.x];
   const SNode sj = sn[t.a];
   const int i = t.b, j = t.c, s = t.d & 0xffff;
@@ -468,16 +485,16 @@ __global__ void __launch_bounds__(THREADS) k_gemm(const SNode *__restrict__ sn,
       int a = lane + 32 * ii, b = w + 8 * jj;
       r[ii][jj] = (a < tm && b < tn) ? C[(int64_t)b * sj.nrows + a] : T(0);
     }
-  for (int k0 = 0; k0 < ks; k0 += KC) {
-    const int kc = min(KC, ks - k0);
-    for (int idx = tid; idx < KC * NB; idx += THREADS) {
+  for (int k0 = 0; k0 < ks; k0 += KG) {
+    const int kc = min(KG, ks - k0);
+    for (int idx = tid; idx < KG * NB; idx += THREADS) {
       int a = idx % NB, kk = idx / NB;
       const T *col = P + (int64_t)(k0 + kk) * sj.nrows;
       As[kk][a] = (a < tm && kk < kc) ? col[rb + a] : T(0);
       Bs[kk][a] = (a < tn && kk < kc) ? col[(int64_t)j * NB + a] : T(0);
     }
     __syncthreads();
-    fma_chunk_dispatch<KC>(r, As, Bs, kc, lane, w, ni, nj);
+    fma_chunk_dispatch<KG>(r, As, Bs, kc, lane, w, ni, nj);
     __syncthreads();
   }
 #pragma unroll
@@ -975,9 +992,9 @@ __global__ void __launch_bounds__(THREADS) k_trtri(const SNode *__restrict__ sn,
   const int ts = min(NB, sj.ncols - s * NB);
   const T *D = Lx + sj.lx + (int64_t)(s * NB) * sj.nrows + s * NB;
   const int tid = threadIdx.x;
-  for (int idx = tid; idx < NB * NB; idx += THREADS) {
-    int r = idx % NB, c = idx / NB;
-    a[c][r] = (r < ts && c < ts && r >= c) ? (double)D[(int64_t)c * sj.nrows + r] : 0.0;
+  for (int idx = tid; idx < ts * ts; idx += THREADS) {
+    int r = idx % ts, c = idx / ts;
+    a[c][r] = r >= c ? (double)D[(int64_t)c * sj.nrows + r] : 0.0;
     x[c][r] = r == c ? 1.0 : 0.0;
   }
   __syncthreads();
