@@ -201,8 +201,8 @@ def run_reference(args):
 
 
 def bench_mixed(S, torch, M, B, flops, args, stream, barrier, world):
-    """The mixed-precision form on the same matrix and right-hand sides: FP32 factor (FP64
-    diagonal-tile pivots) + FP64 conjugate gradients preconditioned by it, to backward error
+    """The mixed-precision form on the same matrix and right-hand sides: FP32 factor + FP64
+    conjugate gradients preconditioned by it, to backward error
     <= 1e-12 on every right-hand side. Timed like the main step (scatter + factor + solve)."""
     s = S.Solver(M.n, M.Ap, M.Ai, M.perm, precision="mixed")
     s.set_stream(stream)

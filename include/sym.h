@@ -47,7 +47,7 @@ extern "C" {
 
 /* Precision of the factor (sym_options.precision). */
 #define SYM_PREC_FP64 0  /* FP64 factor and FP64 solves (the plain path) */
-#define SYM_PREC_MIXED 1 /* FP32 factor (FP64 diagonal-tile pivots); solves refined in FP64 by
+#define SYM_PREC_MIXED 1 /* FP32 factor (all arithmetic FP32); solves refined in FP64 by
                             conjugate gradients preconditioned with the FP32 factor, to a normwise
                             backward error <= the refinement tolerance (default 1e-12) */
 

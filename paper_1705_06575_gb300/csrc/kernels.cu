@@ -114,6 +114,16 @@ __device__ __forceinline__ double rsqrt_newton(double d) {
   return fma(x0 * e, p, x0);
 }
 
+// The same in FP32: the single-precision seed plus one Newton step x <- x (3 - d x^2) / 2.
+__device__ __forceinline__ float rsqrt_newton(float d) {
+  const float x = rsqrtf(d);
+  return x * fmaf(-0.5f * d * x, x, 1.5f);
+}
+template <typename T>
+__device__ __forceinline__ T rsqrt_of(T d) {
+  return rsqrt_newton(d);
+}
+
 // ---------------------------------------------------------------------------------------------
 // Scatter of A into the zeroed panels (the temporary block storage of Sec. 2.3.2).
 template <typename T>
@@ -340,9 +350,10 @@ __global__ void __launch_bounds__(THREADS) k_potrf(const SNode *__restrict__ sn,
                                                    int64_t toff, const Batch bt) {
   Lx += blockIdx.y * bt.lx;
   status += blockIdx.y;
-  // The diagonal tile is factored in FP64 whatever the storage type T (for an FP32 factor the
-  // pivots and this tile stay accurate; the result is rounded to T once).
-  __shared__ double a[NB][NB + 1];                 // [col][row]
+  // The tile is factored in the storage type: an FP32 factor is a preconditioner whose accuracy
+  // the FP64 refinement restores, and FP32 keeps its serial pivot chain short (an FP64 operation
+  // waits 64 cycles for the previous one on this part).
+  __shared__ T a[NB][NB + 1];                      // [col][row]
   __shared__ unsigned short tri[NB * (NB - 1) / 2];  // packed lower triangle: (i << 8) | j, i >= j
   const Int4 t = tasks[toff + blockIdx.x];
   const SNode sj = sn[t.a];
@@ -352,7 +363,7 @@ __global__ void __launch_bounds__(THREADS) k_potrf(const SNode *__restrict__ sn,
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int idx = tid; idx < ts * ts; idx += THREADS) {  // only the lower triangle is read
     int rr = idx % ts, c = idx / ts;
-    if (rr >= c) a[c][rr] = (double)D[(int64_t)c * sj.nrows + rr];
+    if (rr >= c) a[c][rr] = D[(int64_t)c * sj.nrows + rr];
   }
   // Row-major packed index of the lower triangle: idx = i (i + 1) / 2 + j. The first
   // m (m + 1) / 2 entries are the triangle of order m, whatever m is; the largest trailing
@@ -366,12 +377,12 @@ __global__ void __launch_bounds__(THREADS) k_potrf(const SNode *__restrict__ sn,
   __syncthreads();
   // warp 0: pivot of column c (already updated by columns < c) and scaling of the column
   auto finish_column = [&](int c) {
-    double d = a[c][c];
-    if (!(d > 0.0)) {
+    T d = a[c][c];
+    if (!(d > T(0))) {
       if (lane == 0) atomicMin(status, (long long)(sj.first + s * NB + c));
-      d = 1.0;
+      d = T(1);
     }
-    const double x = rsqrt_newton(d);
+    const T x = rsqrt_of(d);
     __syncwarp();
     for (int r = c + lane; r < ts; r += 32) a[c][r] = r == c ? d * x : a[c][r] * x;  // d x = sqrt(d)
   };
@@ -379,7 +390,7 @@ __global__ void __launch_bounds__(THREADS) k_potrf(const SNode *__restrict__ sn,
   __syncthreads();
   for (int c = 0; c + 1 < ts; ++c) {
     if (warp == 0) {
-      const double l = a[c][c + 1];
+      const T l = a[c][c + 1];
       for (int r = c + 1 + lane; r < ts; r += 32) a[c + 1][r] = fma(-a[c][r], l, a[c + 1][r]);
       __syncwarp();
       finish_column(c + 1);
@@ -396,7 +407,7 @@ __global__ void __launch_bounds__(THREADS) k_potrf(const SNode *__restrict__ sn,
   }
   for (int idx = tid; idx < ts * ts; idx += THREADS) {
     int rr = idx % ts, c = idx / ts;
-    D[(int64_t)c * sj.nrows + rr] = rr >= c ? (T)a[c][rr] : T(0);
+    D[(int64_t)c * sj.nrows + rr] = rr >= c ? a[c][rr] : T(0);
   }
 }
 

@@ -1,5 +1,5 @@
-"""GPU parity of the mixed-precision form: FP32 factor (FP64 diagonal-tile pivots) and FP64
-conjugate-gradient refinement preconditioned by it.
+"""GPU parity of the mixed-precision form: FP32 factor and FP64 conjugate-gradient refinement
+preconditioned by it.
 
 Tolerances. The FP32 factor is compared with the oracle's FP64 factor entry-wise to
 MIXED_ENTRY_RTOL = 1e-4 of max|L| (u32 = 6e-8 times the perturbation bound kappa(A) <= 1e3 for
