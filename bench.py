@@ -40,11 +40,11 @@ WORKLOADS = {
 WORKLOAD_DESC = WORKLOADS[WORKLOAD]
 NRHS = 4
 METRIC = "refactor GFLOP/s and ms/(factor+solve) vs plain FP64 GPU path at bwd err<=1e-12"
-# DRAM bytes per launch of the dominant kernel (k_update) from an ncu capture: 1638.6 MB over the
-# 17 update launches of a 48^3 factorization (profiles/k_update_conduct3d7_48.md), scaled to the
-# 64^3 workload by algorithmic flops (x 2.673e11 / 4.556e10) and divided by its 19 launches. Set to
-# None whenever k_update changes until it is captured again.
-NCU_TRAFFIC_PER_LAUNCH = 5.05e8
+# DRAM bytes per launch of the dominant kernel (k_update_flat) from an ncu capture: 1647.4 MB over
+# the 17 update launches of a 48^3 factorization (profiles/k_update_conduct3d7_48.md),
+# scaled to the 64^3 workload by algorithmic flops (x 2.672e11 / 4.556e10) and divided by its 19
+# launches. Set to None whenever the FP64 update kernel changes until it is captured again.
+NCU_TRAFFIC_PER_LAUNCH = 5.085e8
 
 CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -440,7 +440,8 @@ def run_ours(args):
     dom = max(kinds, key=lambda k: kinds[k]["ms_per_step"])
     dms, dnl, dfl = s.profile_read(S.KINDS[dom])
     achieved_tf = dfl / dms / 1e9  # flops / ms -> TFLOP/s
-    roofline = {"bound": "alu", "kernel": f"k_{dom}", "achieved": achieved_tf, "peak": peak64 / 1e3,
+    kname = {"update": "k_update_flat"}.get(dom, f"k_{dom}")  # the FP64 update kernel
+    roofline = {"bound": "alu", "kernel": kname, "achieved": achieved_tf, "peak": peak64 / 1e3,
                 "unit": "TFLOP/s", "frac": achieved_tf / (peak64 / 1e3),
                 "traffic": NCU_TRAFFIC_PER_LAUNCH if args.workload == WORKLOAD else None,
                 "peak_source": "FP64 FMA peak measured live by sym_fma_peak (152 SMs x 2 DFMA/clk)",
