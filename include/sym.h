@@ -294,9 +294,10 @@ int sym_get_factor_host(sym_handle h, double *Lx_host);
 #define SYM_EXPORT_LEVELLIST 17  /* int32[nsuper]: supernodes by level, increasing within one */
 #define SYM_EXPORT_LXPTR 18      /* int64[nsuper+1]: offset of each panel in the factor storage */
 /* The launch schedule and its task lists (raw records, for checks of the scheduler):
- * launches: int64 words {kind | level << 32, off, count, cluster | stream << 32, wait | 0 << 32}
+ * launches: int64 words {kind | level << 32, off, count, cluster | stream << 32, wait | tb << 32}
  * per launch (stream 1 = the factor's low-priority lookahead stream; wait = index of an earlier
- * launch it waits for, or -1);
+ * launch it waits for, or -1; tb = 32 when all its tiles have at most 32 columns, for updates
+ * also at most 32 rows, and run the small-tile kernels, else 0);
  * tasks: int32 words {a, b, c, d} per task (meaning per kind, see the SYM_KIND_* list);
  * update tasks: int64 words {J | bi << 32, bj, e0, e1}; update entries: int64 words
  * {K | r_lo << 32, c_lo | m << 32, n, relr, relc}. The count is in words. */

@@ -36,6 +36,16 @@ constexpr int KCU = 8;  // the same for k_update, whose accumulator tile also li
 // Chunks of the register-blocked kernels per storage type: FP64 is bound by its pipe, so small
 // chunks suffice; at the FP32 rate a chunk must carry enough multiply-adds to cover the latency
 // of staging the next one.
+// Small-tile variants: a launch whose tiles all have at most 32 rows and columns (or, for TRSM,
+// at most 32 columns) runs kernels sized for 32 x 32 tiles with 128 threads, so that many more
+// CTAs share an SM than the 64 x 64 forms allow (the batched workloads and the lower levels of the
+// supernodal tree are made of such tiles).
+constexpr int SMALL_TB = SMALL_TILE;
+template <int TB>
+struct TileCfg {
+  static constexpr int threads = TB == NB ? THREADS : 128;
+};
+
 template <typename T>
 struct Chunk {
   static constexpr int upd = KCU, gemm = KC;
@@ -219,9 +229,9 @@ __global__ void __launch_bounds__(THREADS) k_update(const SNode *__restrict__ sn
 // r[j] -= A[kk][a_j] * B[kk][b_j] for kk < kc and the first J element slots of this thread
 // (a_j = ab[j] & 0xff, b_j = ab[j] >> 8).
 constexpr int FLAT_SLOTS = 8;  // output elements per thread and pass
-template <int J, typename T>
-__device__ __forceinline__ void flat_chunk(T (&r)[FLAT_SLOTS], const int (&ab)[FLAT_SLOTS], const T (*As)[NB],
-                                           const T (*Bs)[NB], int kc) {
+template <int J, int TB, typename T>
+__device__ __forceinline__ void flat_chunk(T (&r)[FLAT_SLOTS], const int (&ab)[FLAT_SLOTS], const T (*As)[TB],
+                                           const T (*Bs)[TB], int kc) {
 #pragma unroll 2
   for (int kk = 0; kk < kc; ++kk) {
 #pragma unroll
@@ -229,12 +239,12 @@ __device__ __forceinline__ void flat_chunk(T (&r)[FLAT_SLOTS], const int (&ab)[F
   }
 }
 
-template <typename T>
+template <int TB, typename T>
 __device__ __forceinline__ void flat_chunk_dispatch(T (&r)[FLAT_SLOTS], const int (&ab)[FLAT_SLOTS],
-                                                    const T (*As)[NB], const T (*Bs)[NB], int kc, int jw) {
+                                                    const T (*As)[TB], const T (*Bs)[TB], int kc, int jw) {
 #define SYM_CASE(J) \
   case J:           \
-    flat_chunk<J>(r, ab, As, Bs, kc); \
+    flat_chunk<J, TB>(r, ab, As, Bs, kc); \
     break;
   switch (jw) {
     SYM_CASE(1) SYM_CASE(2) SYM_CASE(3) SYM_CASE(4) SYM_CASE(5) SYM_CASE(6) SYM_CASE(7) SYM_CASE(8)
@@ -254,17 +264,17 @@ __device__ __forceinline__ void flat_chunk_dispatch(T (&r)[FLAT_SLOTS], const in
 // memory, which the narrow FP64 pipe leaves ample room for (one warp-wide DFMA per
 // sub-partition every 64 cycles). The accumulation order of every element is the one of
 // k_update: the factor is bit-identical.
-template <typename T>
-__global__ void __launch_bounds__(THREADS, 3) k_update_flat(const SNode *__restrict__ sn,
-                                                            const UpdTask *__restrict__ tasks,
-                                                            const UpdEntry *__restrict__ ents,
-                                                            const int32_t *__restrict__ rel,
-                                                            T *__restrict__ Lx, int64_t toff, const Batch bt) {
+template <typename T, int TB>
+__global__ void __launch_bounds__(TileCfg<TB>::threads, TB == NB ? 3 : 6)
+    k_update_flat(const SNode *__restrict__ sn, const UpdTask *__restrict__ tasks,
+                  const UpdEntry *__restrict__ ents, const int32_t *__restrict__ rel, T *__restrict__ Lx,
+                  int64_t toff, const Batch bt) {
+  constexpr int TT = TileCfg<TB>::threads;
   Lx += blockIdx.y * bt.lx;
-  __shared__ T acc[NB][NB + 1];  // [col][row]
-  __shared__ T As[KCU][NB];
-  __shared__ T Bs[KCU][NB];
-  __shared__ int prow[NB], pcol[NB];
+  __shared__ T acc[TB][TB + 1];  // [col][row]
+  __shared__ T As[KCU][TB];
+  __shared__ T Bs[KCU][TB];
+  __shared__ int prow[TB], pcol[TB];
   const UpdTask t = tasks[toff + blockIdx.x];
   const SNode sj = sn[t.J];
   const int64_t rb = d_row_tile_base(t.bi, sj.ncols, sj.ncb);
@@ -274,7 +284,7 @@ __global__ void __launch_bounds__(THREADS, 3) k_update_flat(const SNode *__restr
   const bool diag = t.bi == t.bj;  // rows and columns of the tile are the same positions
   T *C = Lx + sj.lx + (int64_t)cb * sj.nrows + rb;
   const int tid = threadIdx.x, w = tid >> 5;
-  for (int idx = tid; idx < tm * tn; idx += THREADS) {  // only the tile's own part is read
+  for (int idx = tid; idx < tm * tn; idx += TT) {  // only the tile's own part is read
     int r = idx % tm, c = idx / tm;
     acc[c][r] = C[(int64_t)c * sj.nrows + r];
   }
@@ -282,18 +292,18 @@ __global__ void __launch_bounds__(THREADS, 3) k_update_flat(const SNode *__restr
     const UpdEntry E = ents[e];
     const SNode sk = sn[E.K];
     if (tid < E.m) prow[tid] = rel[E.relr + tid] - (int)rb;
-    if (tid >= NB && tid - NB < E.n) pcol[tid - NB] = rel[E.relc + tid - NB] - cb;
+    if (tid >= TB && tid - TB < E.n) pcol[tid - TB] = rel[E.relc + tid - TB] - cb;
     __syncthreads();
     const int cnt = diag ? E.m * (E.m + 1) / 2 : E.m * E.n;
-    for (int e0 = 0; e0 < cnt; e0 += FLAT_SLOTS * THREADS) {  // block-uniform passes
+    for (int e0 = 0; e0 < cnt; e0 += FLAT_SLOTS * TT) {  // block-uniform passes
       const int rem = cnt - e0;
-      const int nslot = min(FLAT_SLOTS, (rem + THREADS - 1) / THREADS);
-      const int jw = THREADS * (nslot - 1) + 32 * w < rem ? nslot : nslot - 1;  // warp-uniform
+      const int nslot = min(FLAT_SLOTS, (rem + TT - 1) / TT);
+      const int jw = TT * (nslot - 1) + 32 * w < rem ? nslot : nslot - 1;  // warp-uniform
       int ab[FLAT_SLOTS];
       T r[FLAT_SLOTS];
 #pragma unroll
       for (int j = 0; j < FLAT_SLOTS; ++j) {
-        const int el = e0 + tid + THREADS * j;
+        const int el = e0 + tid + TT * j;
         int a = 0, b = 0;
         if (el < cnt) {
           if (diag) {  // row-major lower triangle: el = a (a + 1) / 2 + b, b <= a
@@ -312,26 +322,26 @@ __global__ void __launch_bounds__(THREADS, 3) k_update_flat(const SNode *__restr
       const T *Kp = Lx + sk.lx;
       for (int k0 = 0; k0 < sk.ncols; k0 += KCU) {
         const int kc = min(KCU, sk.ncols - k0);
-        for (int idx = tid; idx < KCU * NB; idx += THREADS) {
-          int a = idx % NB, kk = idx / NB;
+        for (int idx = tid; idx < KCU * TB; idx += TT) {
+          int a = idx % TB, kk = idx / TB;
           const T *col = Kp + (int64_t)(k0 + kk) * sk.nrows;
           As[kk][a] = (a < E.m && kk < kc) ? col[E.r_lo + a] : T(0);
           Bs[kk][a] = (a < E.n && kk < kc) ? col[E.c_lo + a] : T(0);
         }
         __syncthreads();
-        flat_chunk_dispatch(r, ab, As, Bs, kc, jw);
+        flat_chunk_dispatch<TB>(r, ab, As, Bs, kc, jw);
         __syncthreads();
       }
 #pragma unroll
       for (int j = 0; j < FLAT_SLOTS; ++j) {
-        const int el = e0 + tid + THREADS * j;
+        const int el = e0 + tid + TT * j;
         if (el < cnt) acc[pcol[ab[j] >> 8]][prow[ab[j] & 0xff]] = r[j];
       }
     }
     __syncthreads();
   }
   __syncthreads();
-  for (int idx = tid; idx < tm * tn; idx += THREADS) {
+  for (int idx = tid; idx < tm * tn; idx += TT) {
     int r = idx % tm, c = idx / tm;
     C[(int64_t)c * sj.nrows + r] = acc[c][r];
   }
@@ -343,32 +353,33 @@ __global__ void __launch_bounds__(THREADS, 3) k_update_flat(const SNode *__restr
 // pivot and scales it, while the other warps apply column c to columns c+2.. — one barrier per
 // column. A pivot that is not positive (or NaN) records its permuted column in *status (atomic
 // min) and is replaced by 1 so the kernel finishes with finite values.
-template <typename T>
-__global__ void __launch_bounds__(THREADS) k_potrf(const SNode *__restrict__ sn,
-                                                   const Int4 *__restrict__ tasks,
-                                                   T *__restrict__ Lx, long long *status,
-                                                   int64_t toff, const Batch bt) {
+template <typename T, int TB>
+__global__ void __launch_bounds__(TileCfg<TB>::threads) k_potrf(const SNode *__restrict__ sn,
+                                                                const Int4 *__restrict__ tasks,
+                                                                T *__restrict__ Lx, long long *status,
+                                                                int64_t toff, const Batch bt) {
+  constexpr int TT = TileCfg<TB>::threads;
   Lx += blockIdx.y * bt.lx;
   status += blockIdx.y;
   // The tile is factored in the storage type: an FP32 factor is a preconditioner whose accuracy
   // the FP64 refinement restores, and FP32 keeps its serial pivot chain short (an FP64 operation
   // waits 64 cycles for the previous one on this part).
-  __shared__ T a[NB][NB + 1];                      // [col][row]
-  __shared__ unsigned short tri[NB * (NB - 1) / 2];  // packed lower triangle: (i << 8) | j, i >= j
+  __shared__ T a[TB][TB + 1];                      // [col][row]
+  __shared__ unsigned short tri[TB * (TB - 1) / 2];  // packed lower triangle: (i << 8) | j, i >= j
   const Int4 t = tasks[toff + blockIdx.x];
   const SNode sj = sn[t.a];
   const int s = t.b;
-  const int ts = min(NB, sj.ncols - s * NB);
+  const int ts = min(TB, sj.ncols - s * NB);  // a TB < NB launch holds tiles of order <= TB
   T *D = Lx + sj.lx + (int64_t)(s * NB) * sj.nrows + s * NB;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int idx = tid; idx < ts * ts; idx += THREADS) {  // only the lower triangle is read
+  for (int idx = tid; idx < ts * ts; idx += TT) {  // only the lower triangle is read
     int rr = idx % ts, c = idx / ts;
     if (rr >= c) a[c][rr] = D[(int64_t)c * sj.nrows + rr];
   }
   // Row-major packed index of the lower triangle: idx = i (i + 1) / 2 + j. The first
   // m (m + 1) / 2 entries are the triangle of order m, whatever m is; the largest trailing
   // triangle has order ts - 2.
-  for (int idx = tid; idx < ts * (ts - 1) / 2; idx += THREADS) {
+  for (int idx = tid; idx < ts * (ts - 1) / 2; idx += TT) {
     int i = (int)((sqrtf(8.0f * idx + 1.0f) - 1.0f) * 0.5f);
     while ((i + 1) * (i + 2) / 2 <= idx) ++i;
     while (i * (i + 1) / 2 > idx) --i;
@@ -397,7 +408,7 @@ __global__ void __launch_bounds__(THREADS) k_potrf(const SNode *__restrict__ sn,
     } else {
       const int m = ts - c - 2;  // trailing lower triangle of order m, rows/cols c+2..ts-1
       const int tot = m * (m + 1) / 2;
-      for (int idx = tid - 32; idx < tot; idx += THREADS - 32) {
+      for (int idx = tid - 32; idx < tot; idx += TT - 32) {
         const int ij = tri[idx];
         const int rr = c + 2 + (ij >> 8), cc = c + 2 + (ij & 0xff);
         a[cc][rr] = fma(-a[c][rr], a[c][cc], a[cc][rr]);
@@ -405,26 +416,27 @@ __global__ void __launch_bounds__(THREADS) k_potrf(const SNode *__restrict__ sn,
     }
     __syncthreads();
   }
-  for (int idx = tid; idx < ts * ts; idx += THREADS) {
+  for (int idx = tid; idx < ts * ts; idx += TT) {
     int rr = idx % ts, c = idx / ts;
     D[(int64_t)c * sj.nrows + rr] = rr >= c ? a[c][rr] : T(0);
   }
 }
 
 // (c) Tile (i, s) <- tile * L_ss^{-T}: forward substitution over the tile's columns.
-template <typename T>
-__global__ void __launch_bounds__(THREADS) k_trsm(const SNode *__restrict__ sn,
-                                                  const Int4 *__restrict__ tasks,
-                                                  T *__restrict__ Lx, int64_t toff, const Batch bt) {
+template <typename T, int TB>
+__global__ void __launch_bounds__(TileCfg<TB>::threads) k_trsm(const SNode *__restrict__ sn,
+                                                               const Int4 *__restrict__ tasks,
+                                                               T *__restrict__ Lx, int64_t toff, const Batch bt) {
+  constexpr int TT = TileCfg<TB>::threads, G = TT / NB;  // G column groups of NB rows
   Lx += blockIdx.y * bt.lx;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T(*Ls)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem_raw);           // [col][row], lower
-  T(*X)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem_raw) + NB;       // [col][row]
-  T *dinv = reinterpret_cast<T *>(smem_raw) + 2 * NB * (NB + 1);
+  T(*Ls)[TB + 1] = reinterpret_cast<T(*)[TB + 1]>(smem_raw);                        // [col][row], lower
+  T(*X)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(reinterpret_cast<T *>(smem_raw) + TB * (TB + 1));  // [col][row]
+  T *dinv = reinterpret_cast<T *>(smem_raw) + TB * (TB + 1) + TB * (NB + 1);
   const Int4 t = tasks[toff + blockIdx.x];
   const SNode sj = sn[t.a];
   const int i = t.b, s = t.c;
-  const int ts = min(NB, sj.ncols - s * NB);
+  const int ts = min(TB, sj.ncols - s * NB);  // a TB < NB launch holds tiles of <= TB columns
   int64_t rb = d_row_tile_base(i, sj.ncols, sj.ncb);
   int tm = d_row_tile_rows(i, sj.ncols, sj.nrows, sj.ncb);
   const int half = t.d >> 16;  // 0: whole tile; 1, 2: its first or second 32 rows
@@ -435,28 +447,28 @@ __global__ void __launch_bounds__(THREADS) k_trsm(const SNode *__restrict__ sn,
   const T *D = Lx + sj.lx + (int64_t)(s * NB) * sj.nrows + s * NB;
   T *B = Lx + sj.lx + (int64_t)(s * NB) * sj.nrows + rb;
   const int tid = threadIdx.x;
-  for (int idx = tid; idx < ts * ts; idx += THREADS) {  // lower triangle of L_ss
+  for (int idx = tid; idx < ts * ts; idx += TT) {  // lower triangle of L_ss
     int r = idx % ts, c = idx / ts;
     if (r >= c) Ls[c][r] = D[(int64_t)c * sj.nrows + r];
   }
-  for (int idx = tid; idx < tm * ts; idx += THREADS) {
+  for (int idx = tid; idx < tm * ts; idx += TT) {
     int r = idx % tm, c = idx / tm;
     X[c][r] = B[(int64_t)c * sj.nrows + r];
   }
   __syncthreads();
   if (tid < ts) dinv[tid] = T(1) / Ls[tid][tid];
   __syncthreads();
-  const int r = tid & (NB - 1), g = tid >> 6;  // thread owns row r, columns c+1+g, c+5+g, ...
+  const int r = tid & (NB - 1), g = tid >> 6;  // thread owns row r, columns c+1+g, c+1+g+G, ...
   for (int c = 0; c < ts; ++c) {
     if (r < tm) {
       const T xc = X[c][r] * dinv[c];  // X(r, c) is final once columns < c are applied
-      for (int cc = c + 1 + g; cc < ts; cc += 4) X[cc][r] = fma(-xc, Ls[c][cc], X[cc][r]);
+      for (int cc = c + 1 + g; cc < ts; cc += G) X[cc][r] = fma(-xc, Ls[c][cc], X[cc][r]);
     }
     __syncthreads();
     if (g == 0 && r < tm) X[c][r] *= dinv[c];
   }
   __syncthreads();
-  for (int idx = tid; idx < tm * ts; idx += THREADS) {
+  for (int idx = tid; idx < tm * ts; idx += TT) {
     int r = idx % tm, c = idx / tm;
     B[(int64_t)c * sj.nrows + r] = X[c][r];
   }
@@ -986,24 +998,25 @@ __global__ void __launch_bounds__(THREADS) k_bstep(const SNode *__restrict__ sn,
 // Inverse of diagonal tile s of J (in FP64 from the factored tile), stored column-major ts x ts
 // at Linv + dx + s NB^2. Solves L X = I row by row of X: row c is final once scaled by
 // 1 / L(c, c); it is then eliminated from the rows below.
-template <typename T>
-__global__ void __launch_bounds__(THREADS) k_trtri(const SNode *__restrict__ sn,
-                                                   const Int4 *__restrict__ tasks,
-                                                   const T *__restrict__ Lx, T *__restrict__ Linv,
-                                                   int64_t toff, const Batch bt) {
+template <typename T, int TB>
+__global__ void __launch_bounds__(TileCfg<TB>::threads) k_trtri(const SNode *__restrict__ sn,
+                                                                const Int4 *__restrict__ tasks,
+                                                                const T *__restrict__ Lx, T *__restrict__ Linv,
+                                                                int64_t toff, const Batch bt) {
+  constexpr int TT = TileCfg<TB>::threads, G = TT / TB;  // G column groups of TB rows
   Lx += blockIdx.y * bt.lx;
   Linv += blockIdx.y * bt.dinv;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double(*a)[NB + 1] = reinterpret_cast<double(*)[NB + 1]>(smem_raw);  // L, [col][row]
-  double(*x)[NB + 1] = a + NB;                                          // X, [col][row]
-  double *dinv = reinterpret_cast<double *>(smem_raw) + 2 * NB * (NB + 1);
+  double(*a)[TB + 1] = reinterpret_cast<double(*)[TB + 1]>(smem_raw);  // L, [col][row]
+  double(*x)[TB + 1] = a + TB;                                          // X, [col][row]
+  double *dinv = reinterpret_cast<double *>(smem_raw) + 2 * TB * (TB + 1);
   const Int4 t = tasks[toff + blockIdx.x];
   const SNode sj = sn[t.a];
   const int s = t.b;
-  const int ts = min(NB, sj.ncols - s * NB);
+  const int ts = min(TB, sj.ncols - s * NB);  // a TB < NB launch holds tiles of order <= TB
   const T *D = Lx + sj.lx + (int64_t)(s * NB) * sj.nrows + s * NB;
   const int tid = threadIdx.x;
-  for (int idx = tid; idx < ts * ts; idx += THREADS) {
+  for (int idx = tid; idx < ts * ts; idx += TT) {
     int r = idx % ts, c = idx / ts;
     a[c][r] = r >= c ? (double)D[(int64_t)c * sj.nrows + r] : 0.0;
     x[c][r] = r == c ? 1.0 : 0.0;
@@ -1011,27 +1024,28 @@ __global__ void __launch_bounds__(THREADS) k_trtri(const SNode *__restrict__ sn,
   __syncthreads();
   if (tid < ts) dinv[tid] = 1.0 / a[tid][tid];
   __syncthreads();
-  const int r = tid & (NB - 1), jg = tid >> 6;
+  const int r = tid % TB, jg = tid / TB;
   for (int c = 0; c < ts; ++c) {
     if (r > c && r < ts) {
       const double l = a[c][r];
-      for (int j = jg; j <= c; j += 4) x[j][r] = fma(-l, x[j][c] * dinv[c], x[j][r]);
+      for (int j = jg; j <= c; j += G) x[j][r] = fma(-l, x[j][c] * dinv[c], x[j][r]);
     }
     __syncthreads();
     if (r == c)
-      for (int j = jg; j <= c; j += 4) x[j][c] *= dinv[c];
+      for (int j = jg; j <= c; j += G) x[j][c] *= dinv[c];
   }
   __syncthreads();
   T *out = Linv + sj.dx + (int64_t)s * NB * NB;
-  for (int idx = tid; idx < ts * ts; idx += THREADS) {
+  for (int idx = tid; idx < ts * ts; idx += TT) {
     const int rr = idx % ts, c = idx / ts;
     out[(int64_t)c * ts + rr] = rr >= c ? (T)x[c][rr] : T(0);
   }
 }
 
-template <typename T>
-constexpr size_t trsm_smem() { return sizeof(T) * (2 * NB * (NB + 1) + NB); }
-constexpr size_t trtri_smem() { return sizeof(double) * (2 * NB * (NB + 1) + NB); }
+template <typename T, int TB>
+constexpr size_t trsm_smem() { return sizeof(T) * (TB * (TB + 1) + TB * (NB + 1) + TB); }
+template <int TB>
+constexpr size_t trtri_smem() { return sizeof(double) * (2 * TB * (TB + 1) + TB); }
 
 inline int grid_for(int64_t count, int per) {
   int64_t g = (count + per - 1) / per;
@@ -1043,11 +1057,12 @@ inline int grid_for(int64_t count, int per) {
 
 // Launch with a stream priority attribute (kept by CUDA-graph capture as a node priority).
 template <typename... KArgs, typename... Args>
-cudaError_t launch_prio(void (*kernel)(KArgs...), dim3 grid, size_t smem, cudaStream_t st, int prio, Args... args) {
+cudaError_t launch_prio(void (*kernel)(KArgs...), dim3 grid, int threads, size_t smem, cudaStream_t st, int prio,
+                        Args... args) {
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   cfg.gridDim = grid;
-  cfg.blockDim = dim3(THREADS, 1, 1);
+  cfg.blockDim = dim3(threads, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   attr[0].id = cudaLaunchAttributePriority;
@@ -1065,9 +1080,16 @@ inline void trace_mark(LaunchTrace *tr, int32_t kind, cudaStream_t st) {
 
 template <typename T>
 cudaError_t prepare_factor() {
-  cudaError_t e = cudaFuncSetAttribute(k_trsm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem<T>());
+  cudaError_t e = cudaFuncSetAttribute(k_trsm<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)trsm_smem<T, NB>());
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_trtri<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trtri_smem());
+  e = cudaFuncSetAttribute(k_trsm<T, SMALL_TB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)trsm_smem<T, SMALL_TB>());
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_trtri<T, SMALL_TB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)trtri_smem<SMALL_TB>());
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_trtri<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trtri_smem<NB>());
 }
 
 // Sparse right-hand side: zero the columns of the reached supernodes, scatter b, gather x.
@@ -1120,25 +1142,38 @@ cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, co
     const int prio = (dual && L.stream == 1) ? two->prio_low : two ? two->prio_high : 0;
     if (dual && L.wait >= 0) cudaStreamWaitEvent(s, (*two->events)[L.wait], 0);
     cudaError_t e = cudaSuccess;
+    const bool small = L.tb == SMALL_TB;  // every tile of the launch fits the small variant
+    constexpr int TS = TileCfg<SMALL_TB>::threads;
     switch (L.kind) {
       case K_UPDATE:
         // FP64: flat element map (the FP64 pipe is the bound and every issued DFMA should be
         // useful); FP32: register-blocked tiles (operand reuse matters at the FP32 rate)
-        e = std::is_same<T, double>::value
-                ? launch_prio(k_update_flat<T>, dim3(g, nb), 0, s, prio, d.sn, d.upd_tasks, d.upd_entries, d.rel, Lx, L.off, bt)
-                : launch_prio(k_update<T>, dim3(g, nb), 0, s, prio, d.sn, d.upd_tasks, d.upd_entries, d.rel, Lx, L.off, bt);
+        if (!std::is_same<T, double>::value)
+          e = launch_prio(k_update<T>, dim3(g, nb), THREADS, 0, s, prio, d.sn, d.upd_tasks, d.upd_entries, d.rel, Lx, L.off, bt);
+        else if (small)
+          e = launch_prio(k_update_flat<T, SMALL_TB>, dim3(g, nb), TS, 0, s, prio, d.sn, d.upd_tasks, d.upd_entries, d.rel,
+                          Lx, L.off, bt);
+        else
+          e = launch_prio(k_update_flat<T, NB>, dim3(g, nb), THREADS, 0, s, prio, d.sn, d.upd_tasks, d.upd_entries, d.rel,
+                          Lx, L.off, bt);
         break;
       case K_POTRF:
-        e = launch_prio(k_potrf<T>, dim3(g, nb), 0, s, prio, d.sn, d.tasks, Lx, status, L.off, bt);
+        e = small ? launch_prio(k_potrf<T, SMALL_TB>, dim3(g, nb), TS, 0, s, prio, d.sn, d.tasks, Lx, status, L.off, bt)
+                  : launch_prio(k_potrf<T, NB>, dim3(g, nb), THREADS, 0, s, prio, d.sn, d.tasks, Lx, status, L.off, bt);
         break;
       case K_TRSM:
-        e = launch_prio(k_trsm<T>, dim3(g, nb), trsm_smem<T>(), s, prio, d.sn, d.tasks, Lx, L.off, bt);
+        e = small ? launch_prio(k_trsm<T, SMALL_TB>, dim3(g, nb), TS, trsm_smem<T, SMALL_TB>(), s, prio, d.sn, d.tasks, Lx,
+                                L.off, bt)
+                  : launch_prio(k_trsm<T, NB>, dim3(g, nb), THREADS, trsm_smem<T, NB>(), s, prio, d.sn, d.tasks, Lx, L.off, bt);
         break;
       case K_GEMM:
-        e = launch_prio(k_gemm<T>, dim3(g, nb), 0, s, prio, d.sn, d.tasks, Lx, L.off, bt);
+        e = launch_prio(k_gemm<T>, dim3(g, nb), THREADS, 0, s, prio, d.sn, d.tasks, Lx, L.off, bt);
         break;
       case K_TRTRI:
-        e = launch_prio(k_trtri<T>, dim3(g, nb), trtri_smem(), s, prio, d.sn, d.tasks, (const T *)Lx, Linv, L.off, bt);
+        e = small ? launch_prio(k_trtri<T, SMALL_TB>, dim3(g, nb), TS, trtri_smem<SMALL_TB>(), s, prio, d.sn, d.tasks,
+                                (const T *)Lx, Linv, L.off, bt)
+                  : launch_prio(k_trtri<T, NB>, dim3(g, nb), THREADS, trtri_smem<NB>(), s, prio, d.sn, d.tasks,
+                                (const T *)Lx, Linv, L.off, bt);
         break;
       default:
         return cudaErrorInvalidValue;

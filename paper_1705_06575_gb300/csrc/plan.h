@@ -20,6 +20,8 @@ constexpr int SOLVE_BG = 16;
 constexpr int SOLVE_CW = 512;
 // Right-hand sides per pass of the solve kernels (the buffer t holds this many).
 constexpr int SOLVE_MAXRHS = 8;
+// Order bound of the tiles that the small-tile kernel variants take.
+constexpr int SMALL_TILE = 32;
 
 // One supernode as the kernels see it. Its panel is column-major, nrows x ncols, leading
 // dimension nrows, at Lx + lx. Row r of the panel is global row rows[rowp + r]; the first ncols
@@ -107,7 +109,8 @@ struct Launch {
   int32_t cluster = 1;  // CTAs per task (a thread-block cluster) where the kernel supports it
   int32_t stream = 0;   // 0: the main (high-priority) stream, 1: the auxiliary (low-priority) one
   int32_t wait = -1;    // index of an earlier launch of this list to wait for (other stream), or -1
-  int32_t pad = 0;
+  int32_t tb = 0;       // SMALL_TILE: every tile of the launch has at most SMALL_TILE columns
+                        // (update: rows and columns), run by the small-tile kernel variant; else 0
 };
 
 struct Int4 {

@@ -502,11 +502,20 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
         for (Pending &pd : pend) lt.push_back({J, pd.bi, pd.bj, pd.work, std::move(pd.ents)});
       }
       std::stable_sort(lt.begin(), lt.end(), [](const LTask &x, const LTask &y) { return x.work > y.work; });
-      if (!lt.empty()) {
-        Launch U{K_UPDATE, l, (int64_t)P.upd_tasks.size(), (int64_t)lt.size()};
-        U.wait = pending_join;
-        pending_join = -1;
-        P.factor_launches.push_back(U);
+      // A level whose update tiles all have at most SMALL_TILE rows and columns runs the
+      // small-tile kernel variant. (Splitting a mixed level into two launches, the small tiles
+      // beside the others on the auxiliary stream, measured slower at 64^3: in one launch the
+      // small tiles, sorted last, fill the tail of the large ones.)
+      auto small_tile = [&](const LTask &x) {
+        const SNode &sj = P.snodes[x.J];
+        const int64_t rb = row_tile_base(x.bi, sj.ncols, sj.ncb);
+        const int64_t tm = std::min<int64_t>(NB, (x.bi < sj.ncb ? sj.ncols : sj.nrows) - rb);
+        const int64_t tn = std::min<int32_t>(NB, sj.ncols - x.bj * NB);
+        return tm <= SMALL_TILE && tn <= SMALL_TILE;
+      };
+      const bool all_small = std::all_of(lt.begin(), lt.end(), small_tile);
+      {
+        Launch U{K_UPDATE, l, (int64_t)P.upd_tasks.size(), 0};
         for (LTask &x : lt) {
           UpdTask u;
           u.J = x.J;
@@ -517,6 +526,13 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
           P.upd_entries.insert(P.upd_entries.end(), x.ents.begin(), x.ents.end());
           u.e1 = (int64_t)P.upd_entries.size();
           P.upd_tasks.push_back(u);
+        }
+        U.count = (int64_t)P.upd_tasks.size() - U.off;
+        if (U.count > 0) {
+          U.tb = all_small ? SMALL_TILE : 0;
+          U.wait = pending_join;
+          pending_join = -1;
+          P.factor_launches.push_back(U);
         }
       }
       // Dense part of each supernode of this level: right-looking over column tiles s with
@@ -535,27 +551,41 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
           const SNode &sj = P.snodes[J];
           gen(J, sj, num_row_tiles(sj.nrows, sj.ncols, sj.ncb));
         }
-        int64_t cnt = (int64_t)P.tasks.size() - off;
-        if (cnt == 0) return -1;
-        // A short launch on the main stream (the lookahead chain) splits its tiles into row
-        // halves so that twice as many SMs share the work of this latency-critical step.
-        if (stream == 0 && (kind == K_TRSM || kind == K_GEMM) && 2 * cnt <= 152) {
-          std::vector<Int4> halves;
-          for (int64_t q = off; q < off + cnt; ++q) {
-            const Int4 a = P.tasks[q];
-            halves.push_back({a.a, a.b, a.c, a.d | (1 << 16)});
-            halves.push_back({a.a, a.b, a.c, a.d | (2 << 16)});
-          }
-          P.tasks.resize(off);
-          P.tasks.insert(P.tasks.end(), halves.begin(), halves.end());
-          cnt = (int64_t)halves.size();
+        if ((int64_t)P.tasks.size() == off) return -1;
+        // POTRF and TRSM tasks whose diagonal tile has at most SMALL_TILE columns form a second
+        // launch of the small-tile kernel variant, after the full-size one on the same stream.
+        std::vector<Int4> parts[2];
+        for (int64_t q = off; q < (int64_t)P.tasks.size(); ++q) {
+          const Int4 a = P.tasks[q];
+          const bool small = (kind == K_POTRF || kind == K_TRSM) &&
+                             std::min<int32_t>(NB, P.snodes[a.a].ncols - a.c * NB) <= SMALL_TILE;
+          parts[small ? 1 : 0].push_back(a);
         }
-        Launch L{kind, l, off, cnt};
-        L.stream = stream;
-        L.wait = wait;
-        P.factor_launches.push_back(L);
+        P.tasks.resize(off);
+        int32_t last = -1;
+        for (int part = 0; part < 2; ++part) {
+          if (parts[part].empty()) continue;
+          const int64_t o = (int64_t)P.tasks.size();
+          // A short launch on the main stream (the lookahead chain) splits its tiles into row
+          // halves so that twice as many SMs share the work of this latency-critical step.
+          const int64_t c0 = (int64_t)parts[part].size();
+          if (stream == 0 && (kind == K_TRSM || kind == K_GEMM) && 2 * c0 <= 152) {
+            for (const Int4 &a : parts[part]) {
+              P.tasks.push_back({a.a, a.b, a.c, a.d | (1 << 16)});
+              P.tasks.push_back({a.a, a.b, a.c, a.d | (2 << 16)});
+            }
+          } else {
+            P.tasks.insert(P.tasks.end(), parts[part].begin(), parts[part].end());
+          }
+          Launch L{kind, l, o, (int64_t)P.tasks.size() - o};
+          L.stream = stream;
+          L.wait = last < 0 ? wait : -1;  // the second part follows the first on its stream
+          L.tb = part == 1 ? SMALL_TILE : 0;
+          P.factor_launches.push_back(L);
+          last = (int32_t)P.factor_launches.size() - 1;
+        }
         (void)s;
-        return (int32_t)P.factor_launches.size() - 1;
+        return last;
       };
       auto potrf = [&](int32_t s) {
         return emit(K_POTRF, s, 0, -1, [&](int32_t J, const SNode &sj, int32_t) {
@@ -609,12 +639,20 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
     for (const Launch &L : P.factor_launches)
       if (L.stream == 1) final_join = (int32_t)(&L - P.factor_launches.data());
     const int64_t off = (int64_t)P.tasks.size();
-    for (int32_t J = 0; J < ns; ++J)
-      for (int32_t t = 0; t < P.snodes[J].ncb; ++t) P.tasks.push_back({J, t, t, t});
-    if ((int64_t)P.tasks.size() > off) {
-      Launch T{K_TRTRI, nlev, off, (int64_t)P.tasks.size() - off};
-      T.wait = final_join;
-      P.factor_launches.push_back(T);
+    (void)off;
+    for (int part = 0; part < 2; ++part) {  // full-size tiles, then tiles of <= SMALL_TILE columns
+      const int64_t o = (int64_t)P.tasks.size();
+      for (int32_t J = 0; J < ns; ++J)
+        for (int32_t t = 0; t < P.snodes[J].ncb; ++t)
+          if ((std::min<int32_t>(NB, P.snodes[J].ncols - t * NB) <= SMALL_TILE) == (part == 1))
+            P.tasks.push_back({J, t, t, t});
+      if ((int64_t)P.tasks.size() > o) {
+        Launch T{K_TRTRI, nlev, o, (int64_t)P.tasks.size() - o};
+        T.wait = final_join;
+        final_join = -1;
+        T.tb = part == 1 ? SMALL_TILE : 0;
+        P.factor_launches.push_back(T);
+      }
     }
   }
   // Solve schedules. Forward, per level: S_FSUM (columns subtract what their descendants
