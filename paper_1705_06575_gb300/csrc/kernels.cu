@@ -818,33 +818,34 @@ __global__ void __launch_bounds__(THREADS) k_bgather(const SNode *__restrict__ s
 
 // Shared-memory layout of the solve steps: the inverse of the diagonal tile and one panel tile,
 // each [col][row] with padding, plus the right-hand-side tile before and after the diagonal solve.
-template <typename V>
+template <typename V, int TB>
 struct StepSmem {
-  V Li[NB][NB + 1];
-  V Lt[NB][NB + 1];
-  V vs[MAXRHS][NB];
-  V ys[MAXRHS][NB];
+  V Li[TB][TB + 1];
+  V Lt[TB][TB + 1];
+  V vs[MAXRHS][TB];
+  V ys[MAXRHS][TB];
 };
-template <typename V>
-constexpr size_t step_smem() { return sizeof(StepSmem<V>); }
+template <typename V, int TB>
+constexpr size_t step_smem() { return sizeof(StepSmem<V, TB>); }
 
 // Solves one diagonal tile u of J in place in global memory: y_u <- L_uu^{-1} y_u (forward) or
 // z_u <- L_uu^{-T} z_u (backward), with the precomputed inverse staged in shared memory.
-template <typename T, typename V, bool TRANS>
-__device__ void write_solved_tile(StepSmem<V> &S, const SNode &sj, const T *__restrict__ Linv, int u,
+template <typename T, typename V, bool TRANS, int TB>
+__device__ void write_solved_tile(StepSmem<V, TB> &S, const SNode &sj, const T *__restrict__ Linv, int u,
                                   V *__restrict__ y, int64_t n, int r0, int nr) {
-  const int tu = min(NB, sj.ncols - u * NB);
+  constexpr int TT = TileCfg<TB>::threads;
+  const int tu = min(TB, sj.ncols - u * NB);
   const int64_t g0 = sj.first + u * NB;
   const int tid = threadIdx.x;
   __syncthreads();  // S may still be in use by the caller
   const T *Li = Linv + sj.dx + (int64_t)u * NB * NB;
-  for (int idx = tid; idx < tu * tu; idx += THREADS) S.Li[idx / tu][idx % tu] = (V)Li[idx];
-  for (int idx = tid; idx < MAXRHS * NB; idx += THREADS) {
-    int r = idx % NB, c = idx / NB;
+  for (int idx = tid; idx < tu * tu; idx += TT) S.Li[idx / tu][idx % tu] = (V)Li[idx];
+  for (int idx = tid; idx < MAXRHS * TB; idx += TT) {
+    int r = idx % TB, c = idx / TB;
     S.vs[c][r] = (r < tu && c < nr) ? y[(int64_t)(r0 + c) * n + g0 + r] : V(0);
   }
   __syncthreads();
-  for (int idx = tid; idx < tu * nr; idx += THREADS) {
+  for (int idx = tid; idx < tu * nr; idx += TT) {
     const int r = idx % tu, q = idx / tu;
     V a0 = V(0), a1 = V(0);
     if (!TRANS) {
@@ -872,42 +873,43 @@ __device__ void write_solved_tile(StepSmem<V> &S, const SNode &sj, const T *__re
 // step late: the CTA i = s writes the solved y_{s-1} (read by nobody now) and, for the last
 // tile of J (no readers of y_s), the solved y_s as well. Tiles are staged in shared memory with
 // all their loads in flight at once.
-template <typename T, typename V>
-__global__ void __launch_bounds__(THREADS) k_fstep(const SNode *__restrict__ sn,
-                                                   const Int4 *__restrict__ tasks,
-                                                   const T *__restrict__ Lx, const T *__restrict__ Linv,
-                                                   V *__restrict__ y, int64_t n, int r0, int nr, int64_t toff,
-                                                   const Batch bt) {
+template <typename T, typename V, int TB>
+__global__ void __launch_bounds__(TileCfg<TB>::threads) k_fstep(const SNode *__restrict__ sn,
+                                                                const Int4 *__restrict__ tasks,
+                                                                const T *__restrict__ Lx, const T *__restrict__ Linv,
+                                                                V *__restrict__ y, int64_t n, int r0, int nr,
+                                                                int64_t toff, const Batch bt) {
+  constexpr int TT = TileCfg<TB>::threads;
   Lx += blockIdx.y * bt.lx;
   Linv += blockIdx.y * bt.dinv;
   y += blockIdx.y * bt.y;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  StepSmem<V> &S = *reinterpret_cast<StepSmem<V> *>(smem_raw);
+  StepSmem<V, TB> &S = *reinterpret_cast<StepSmem<V, TB> *>(smem_raw);
   const Int4 t = tasks[toff + blockIdx.x];
   const SNode sj = sn[t.a];
   const int i = t.b, s = t.c;
   if (i == s) {
-    if (s >= 1) write_solved_tile<T, V, false>(S, sj, Linv, s - 1, y, n, r0, nr);
-    if (s == sj.ncb - 1) write_solved_tile<T, V, false>(S, sj, Linv, s, y, n, r0, nr);
+    if (s >= 1) write_solved_tile<T, V, false, TB>(S, sj, Linv, s - 1, y, n, r0, nr);
+    if (s == sj.ncb - 1) write_solved_tile<T, V, false, TB>(S, sj, Linv, s, y, n, r0, nr);
     return;
   }
-  const int ts = min(NB, sj.ncols - s * NB);
-  const int tm = min(NB, sj.ncols - i * NB);
+  const int ts = min(TB, sj.ncols - s * NB);  // a TB < NB launch holds supernodes of <= TB columns
+  const int tm = min(TB, sj.ncols - i * NB);
   const int64_t g0 = sj.first + s * NB;
   const int tid = threadIdx.x;
   const T *Li = Linv + sj.dx + (int64_t)s * NB * NB;                  // ts x ts, column-major, lower
   const T *Lt = Lx + sj.lx + (int64_t)(s * NB) * sj.nrows + i * NB;  // rows of tile i, cols of tile s
-  for (int idx = tid; idx < ts * ts; idx += THREADS) S.Li[idx / ts][idx % ts] = (V)Li[idx];
-  for (int idx = tid; idx < NB * ts; idx += THREADS) {
-    const int r = idx % NB, c = idx / NB;
+  for (int idx = tid; idx < ts * ts; idx += TT) S.Li[idx / ts][idx % ts] = (V)Li[idx];
+  for (int idx = tid; idx < TB * ts; idx += TT) {
+    const int r = idx % TB, c = idx / TB;
     if (r < tm) S.Lt[c][r] = (V)Lt[(int64_t)c * sj.nrows + r];
   }
-  for (int idx = tid; idx < MAXRHS * NB; idx += THREADS) {
-    int r = idx % NB, c = idx / NB;
+  for (int idx = tid; idx < MAXRHS * TB; idx += TT) {
+    int r = idx % TB, c = idx / TB;
     S.vs[c][r] = (r < ts && c < nr) ? y[(int64_t)(r0 + c) * n + g0 + r] : V(0);
   }
   __syncthreads();
-  for (int idx = tid; idx < ts * nr; idx += THREADS) {
+  for (int idx = tid; idx < ts * nr; idx += TT) {
     const int r = idx % ts, q = idx / ts;
     V a0 = V(0), a1 = V(0);
     int k = 0;
@@ -919,7 +921,7 @@ __global__ void __launch_bounds__(THREADS) k_fstep(const SNode *__restrict__ sn,
     S.ys[q][r] = a0 + a1;
   }
   __syncthreads();
-  for (int idx = tid; idx < tm * nr; idx += THREADS) {
+  for (int idx = tid; idx < tm * nr; idx += TT) {
     const int r = idx % tm, q = idx / tm;
     V a0 = V(0), a1 = V(0);
     int k = 0;
@@ -935,42 +937,43 @@ __global__ void __launch_bounds__(THREADS) k_fstep(const SNode *__restrict__ sn,
 // Backward step of column tile s inside J (tasks {J, i, s}, s descending): CTAs i < s form
 // zs = L_ss^{-T} z_s and apply z_i -= L_si^T zs; the CTA i = s writes the solved z_{s+1} and,
 // for tile 0, the solved z_0 (the mirror image of the forward step).
-template <typename T, typename V>
-__global__ void __launch_bounds__(THREADS) k_bstep(const SNode *__restrict__ sn,
-                                                   const Int4 *__restrict__ tasks,
-                                                   const T *__restrict__ Lx, const T *__restrict__ Linv,
-                                                   V *__restrict__ y, int64_t n, int r0, int nr, int64_t toff,
-                                                   const Batch bt) {
+template <typename T, typename V, int TB>
+__global__ void __launch_bounds__(TileCfg<TB>::threads) k_bstep(const SNode *__restrict__ sn,
+                                                                const Int4 *__restrict__ tasks,
+                                                                const T *__restrict__ Lx, const T *__restrict__ Linv,
+                                                                V *__restrict__ y, int64_t n, int r0, int nr,
+                                                                int64_t toff, const Batch bt) {
+  constexpr int TT = TileCfg<TB>::threads;
   Lx += blockIdx.y * bt.lx;
   Linv += blockIdx.y * bt.dinv;
   y += blockIdx.y * bt.y;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  StepSmem<V> &S = *reinterpret_cast<StepSmem<V> *>(smem_raw);
+  StepSmem<V, TB> &S = *reinterpret_cast<StepSmem<V, TB> *>(smem_raw);
   const Int4 t = tasks[toff + blockIdx.x];
   const SNode sj = sn[t.a];
   const int i = t.b, s = t.c;
   if (i == s) {
-    if (s + 1 < sj.ncb) write_solved_tile<T, V, true>(S, sj, Linv, s + 1, y, n, r0, nr);
-    if (s == 0) write_solved_tile<T, V, true>(S, sj, Linv, 0, y, n, r0, nr);
+    if (s + 1 < sj.ncb) write_solved_tile<T, V, true, TB>(S, sj, Linv, s + 1, y, n, r0, nr);
+    if (s == 0) write_solved_tile<T, V, true, TB>(S, sj, Linv, 0, y, n, r0, nr);
     return;
   }
-  const int ts = min(NB, sj.ncols - s * NB);
-  const int ti = min(NB, sj.ncols - i * NB);
+  const int ts = min(TB, sj.ncols - s * NB);  // a TB < NB launch holds supernodes of <= TB columns
+  const int ti = min(TB, sj.ncols - i * NB);
   const int64_t g0 = sj.first + s * NB;
   const int tid = threadIdx.x;
   const T *Li = Linv + sj.dx + (int64_t)s * NB * NB;                  // ts x ts, column-major, lower
   const T *Lt = Lx + sj.lx + (int64_t)(i * NB) * sj.nrows + s * NB;  // rows of tile s, cols of tile i
-  for (int idx = tid; idx < ts * ts; idx += THREADS) S.Li[idx / ts][idx % ts] = (V)Li[idx];
-  for (int idx = tid; idx < NB * ti; idx += THREADS) {
-    const int k = idx % NB, c = idx / NB;
+  for (int idx = tid; idx < ts * ts; idx += TT) S.Li[idx / ts][idx % ts] = (V)Li[idx];
+  for (int idx = tid; idx < TB * ti; idx += TT) {
+    const int k = idx % TB, c = idx / TB;
     if (k < ts) S.Lt[c][k] = (V)Lt[(int64_t)c * sj.nrows + k];
   }
-  for (int idx = tid; idx < MAXRHS * NB; idx += THREADS) {
-    int r = idx % NB, c = idx / NB;
+  for (int idx = tid; idx < MAXRHS * TB; idx += TT) {
+    int r = idx % TB, c = idx / TB;
     S.vs[c][r] = (r < ts && c < nr) ? y[(int64_t)(r0 + c) * n + g0 + r] : V(0);
   }
   __syncthreads();
-  for (int idx = tid; idx < ts * nr; idx += THREADS) {
+  for (int idx = tid; idx < ts * nr; idx += TT) {
     const int r = idx % ts, q = idx / ts;
     V a0 = V(0), a1 = V(0);
     int k = r;
@@ -982,7 +985,7 @@ __global__ void __launch_bounds__(THREADS) k_bstep(const SNode *__restrict__ sn,
     S.ys[q][r] = a0 + a1;
   }
   __syncthreads();
-  for (int idx = tid; idx < ti * nr; idx += THREADS) {
+  for (int idx = tid; idx < ti * nr; idx += TT) {
     const int c = idx % ti, q = idx / ti;
     V a0 = V(0), a1 = V(0);
     int k = 0;
@@ -1111,9 +1114,10 @@ __global__ void k_reach_gather(const int32_t *__restrict__ cols, int64_t nr, con
 
 template <typename T, typename V>
 cudaError_t prepare_solve() {
-  cudaError_t e = cudaFuncSetAttribute(k_fstep<T, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)step_smem<V>());
+  cudaError_t e = cudaFuncSetAttribute(k_fstep<T, V, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)step_smem<V, NB>());
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_bstep<T, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)step_smem<V>());
+  e = cudaFuncSetAttribute(k_bstep<T, V, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)step_smem<V, NB>());
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_fgather<T, V>, cudaFuncAttributeNonPortableClusterSizeAllowed, 0);
 }
@@ -1220,7 +1224,12 @@ cudaError_t run_sweeps(const DevPlan &d, const std::vector<Launch> &fwd, const s
           break;
         }
         case S_FSTEP:
-          k_fstep<T, V><<<dim3(g, nb), THREADS, step_smem<V>(), st>>>(d.sn, d.tasks, Lx, Linv, y, n, r0, nr, L.off, bt);
+          if (L.tb == SMALL_TB)
+            k_fstep<T, V, SMALL_TB><<<dim3(g, nb), TileCfg<SMALL_TB>::threads, step_smem<V, SMALL_TB>(), st>>>(
+                d.sn, d.tasks, Lx, Linv, y, n, r0, nr, L.off, bt);
+          else
+            k_fstep<T, V, NB><<<dim3(g, nb), THREADS, step_smem<V, NB>(), st>>>(d.sn, d.tasks, Lx, Linv, y, n, r0, nr,
+                                                                              L.off, bt);
           break;
         case S_FPUSH:
           SYM_NR_DISPATCH(nr, (k_fpush<T, V, NR><<<dim3(g, nb), THREADS, 0, st>>>(
@@ -1243,7 +1252,12 @@ cudaError_t run_sweeps(const DevPlan &d, const std::vector<Launch> &fwd, const s
                                   d.sn, d.rows, d.tasks, Lx, y, n, r0, L.off, bt)));
           break;
         case S_BSTEP:
-          k_bstep<T, V><<<dim3(g, nb), THREADS, step_smem<V>(), st>>>(d.sn, d.tasks, Lx, Linv, y, n, r0, nr, L.off, bt);
+          if (L.tb == SMALL_TB)
+            k_bstep<T, V, SMALL_TB><<<dim3(g, nb), TileCfg<SMALL_TB>::threads, step_smem<V, SMALL_TB>(), st>>>(
+                d.sn, d.tasks, Lx, Linv, y, n, r0, nr, L.off, bt);
+          else
+            k_bstep<T, V, NB><<<dim3(g, nb), THREADS, step_smem<V, NB>(), st>>>(d.sn, d.tasks, Lx, Linv, y, n, r0, nr,
+                                                                              L.off, bt);
           break;
         default:
           return cudaErrorInvalidValue;

@@ -669,15 +669,21 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
         for (int32_t cb = 0; cb * 256 < sj.ncols; ++cb) P.tasks.push_back({J, cb, 0, 0});
     }
     if ((int64_t)P.tasks.size() > off) P.fwd_launches.push_back({S_FSUM, l, off, (int64_t)P.tasks.size() - off});
-    for (int32_t s = 0; s < maxcb; ++s) {
-      off = (int64_t)P.tasks.size();
-      for (int32_t t = P.levelptr[l]; t < P.levelptr[l + 1]; ++t) {
-        const int32_t J = P.levellist[t];
-        const int32_t ncb = P.snodes[J].ncb;
-        for (int32_t i = s; i < ncb; ++i) P.tasks.push_back({J, i, s, s});
+    for (int32_t s = 0; s < maxcb; ++s)
+      for (int part = 0; part < 2; ++part) {  // supernodes of > SMALL_TILE columns, then the others
+        off = (int64_t)P.tasks.size();
+        for (int32_t t = P.levelptr[l]; t < P.levelptr[l + 1]; ++t) {
+          const int32_t J = P.levellist[t];
+          if ((P.snodes[J].ncols <= SMALL_TILE) != (part == 1)) continue;
+          const int32_t ncb = P.snodes[J].ncb;
+          for (int32_t i = s; i < ncb; ++i) P.tasks.push_back({J, i, s, s});
+        }
+        if ((int64_t)P.tasks.size() > off) {
+          Launch L{S_FSTEP, l, off, (int64_t)P.tasks.size() - off};
+          L.tb = part == 1 ? SMALL_TILE : 0;
+          P.fwd_launches.push_back(L);
+        }
       }
-      if ((int64_t)P.tasks.size() > off) P.fwd_launches.push_back({S_FSTEP, l, off, (int64_t)P.tasks.size() - off});
-    }
     off = (int64_t)P.tasks.size();
     for (int32_t t = P.levelptr[l]; t < P.levelptr[l + 1]; ++t) {
       const int32_t J = P.levellist[t];
@@ -699,16 +705,22 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
         for (int32_t sl = 0; sl * SOLVE_BG < sj.ncols; ++sl) P.tasks.push_back({J, sl, 0, 0});
     }
     if ((int64_t)P.tasks.size() > off) P.bwd_launches.push_back({S_BGATHER, l, off, (int64_t)P.tasks.size() - off});
-    for (int32_t s = maxcb - 1; s >= 0; --s) {
-      off = (int64_t)P.tasks.size();
-      for (int32_t t = P.levelptr[l]; t < P.levelptr[l + 1]; ++t) {
-        const int32_t J = P.levellist[t];
-        const int32_t ncb = P.snodes[J].ncb;
-        if (s >= ncb) continue;
-        for (int32_t i = s; i >= 0; --i) P.tasks.push_back({J, i, s, s});
+    for (int32_t s = maxcb - 1; s >= 0; --s)
+      for (int part = 0; part < 2; ++part) {  // supernodes of > SMALL_TILE columns, then the others
+        off = (int64_t)P.tasks.size();
+        for (int32_t t = P.levelptr[l]; t < P.levelptr[l + 1]; ++t) {
+          const int32_t J = P.levellist[t];
+          if ((P.snodes[J].ncols <= SMALL_TILE) != (part == 1)) continue;
+          const int32_t ncb = P.snodes[J].ncb;
+          if (s >= ncb) continue;
+          for (int32_t i = s; i >= 0; --i) P.tasks.push_back({J, i, s, s});
+        }
+        if ((int64_t)P.tasks.size() > off) {
+          Launch L{S_BSTEP, l, off, (int64_t)P.tasks.size() - off};
+          L.tb = part == 1 ? SMALL_TILE : 0;
+          P.bwd_launches.push_back(L);
+        }
       }
-      if ((int64_t)P.tasks.size() > off) P.bwd_launches.push_back({S_BSTEP, l, off, (int64_t)P.tasks.size() - off});
-    }
   }
   // 12. Algorithmic flops of each kernel kind (see Plan::kind_flops).
   {

@@ -38,10 +38,12 @@ class Sched:
         off = np.diff(self.rowptr).astype(np.int64) - nc
         self.tx = np.concatenate([[0], np.cumsum(off * ((nc + CW - 1) // CW))])
         self.launches = {}
+        self.tb = {}
         for k in ("factor_launches", "fwd_launches", "bwd_launches"):
             raw = s.export(k).reshape(-1, 5)
             self.launches[k] = np.stack([raw[:, 0] & 0xffffffff, raw[:, 1], raw[:, 2], raw[:, 3] >> 32,
                                          (raw[:, 4] & 0xffffffff).astype(np.uint32).astype(np.int32)], 1)
+            self.tb[k] = raw[:, 4] >> 32  # 32: small-tile kernel variant
 
     def J(self, j):
         f, l = int(self.sup[j]), int(self.sup[j + 1])
@@ -120,7 +122,7 @@ def emulate_factor(sc, panels, store):
         return store[("L", j, r, c)]
 
     record = []
-    for kind, off, count, _, _ in sc.launches["factor_launches"]:
+    for (kind, off, count, _, _), tb in zip(sc.launches["factor_launches"], sc.tb["factor_launches"]):
         kind = int(kind)
         L = Launch()
         record.append(L)
