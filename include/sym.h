@@ -348,6 +348,14 @@ int sym_profile(sym_handle h, int32_t mode);
  * Any output pointer may be NULL. */
 int sym_profile_read(sym_handle h, int32_t kind, double *ms, int64_t *launches, double *flops);
 
+/* Milliseconds of every launch of the last profiled sym_factor* (which = 0) or sym_solve*
+ * (which = 1) call, in execution order: for the factor, entry 0 is the zeroing and scatter of A
+ * and entry 1 + i is launch i of SYM_EXPORT_FACTOR_LAUNCHES; for a solve, the launches of each
+ * pass of up to 8 right-hand sides (the permutations, then the forward and backward lists).
+ * Returns the count (0 before any profiled call); ms may be NULL to query it, else it receives
+ * that many values. Errors: SYM_ERR_INVALID. */
+int64_t sym_profile_launches(sym_handle h, int32_t which, double *ms);
+
 /* Measured FMA throughput of the current device in GFLOP/s (2 flops per FMA) for precision 64
  * (FP64 pipe) or 32 (FP32 pipe): register-resident FMA chains on every SM, best of three
  * launches of about 50 ms. The denominator of the roofline fraction of the ALU-bound kernels

@@ -20,7 +20,7 @@ __all__ = [
     "sym_analyze_perm", "sym_set_stream", "sym_factor", "sym_factor_async", "sym_status",
     "sym_factor_host", "sym_solve", "sym_solve_multi", "sym_solve_host", "sym_info",
     "sym_last_error_column", "sym_get_factor_host", "sym_export", "sym_free", "load", "Solver",
-    "EXPORTS", "sym_profile", "sym_profile_read", "sym_fma_peak", "sym_solve_host_ptr", "KINDS",
+    "EXPORTS", "sym_profile", "sym_profile_read", "sym_profile_launches", "sym_fma_peak", "sym_solve_host_ptr", "KINDS",
     "sym_solve_multi_noalloc", "sym_set_refinement", "sym_refinement_info", "sym_factor_batch",
     "sym_batch_error_columns", "sym_solve_batch", "sym_get_batch_factor_host", "Reach", "MLP",
 ]
@@ -116,6 +116,7 @@ def load():
             "sym_profile_read": ([P, i32, ct.POINTER(ct.c_double), ct.POINTER(i64),
                                   ct.POINTER(ct.c_double)], I),
             "sym_fma_peak": ([i32, ct.POINTER(ct.c_double)], I),
+            "sym_profile_launches": ([P, i32, P], i64),
             "sym_solve_multi_noalloc": ([P, i32, P, i64, P, i64], I),
             "sym_set_refinement": ([P, ct.c_double, i32], I),
             "sym_factor_batch": ([P, i32, P, i64], I),
@@ -254,6 +255,18 @@ KINDS = {"scatter": 0, "update": 1, "potrf": 2, "trsm": 3, "gemm": 4, "trtri": 5
 
 def sym_profile(h, mode):
     return _check(load().sym_profile(h, int(mode)))
+
+
+def sym_profile_launches(h, which=0):
+    """Per-launch milliseconds of the last profiled factor (which=0) or solve (which=1)."""
+    lib = load()
+    cnt = lib.sym_profile_launches(h, int(which), None)
+    if cnt < 0:
+        _check(int(cnt))
+    out = np.zeros(max(int(cnt), 0), dtype=np.float64)
+    if cnt:
+        _check(int(lib.sym_profile_launches(h, int(which), out.ctypes.data)))
+    return out
 
 
 def sym_profile_read(h, kind):

@@ -79,6 +79,7 @@ struct sym_handle_s {
   bool profiling = false;
   std::vector<cudaEvent_t> events;
   double prof_ms[sym::NUM_KINDS] = {};
+  std::vector<double> last_launch_ms[2];  // per launch of the last profiled factor / solve
   int64_t prof_launches[sym::NUM_KINDS] = {};
   double prof_flops[sym::NUM_KINDS] = {};
 };
@@ -125,11 +126,14 @@ int ensure_events(sym_handle_s *h, size_t count) {
 // After the traced work has finished: add each launch's elapsed time to its kind.
 int collect_trace(sym_handle_s *h, const sym::LaunchTrace &tr, double flop_scale, bool solve) {
   CUDA_TRY(cudaStreamSynchronize(h->stream), "profile sync");
+  std::vector<double> &last = h->last_launch_ms[solve ? 1 : 0];
+  last.clear();
   for (size_t i = 0; i < tr.kinds.size(); ++i) {
     float ms = 0.f;
     CUDA_TRY(cudaEventElapsedTime(&ms, h->events[i], h->events[i + 1]), "cudaEventElapsedTime");
     h->prof_ms[tr.kinds[i]] += ms;
     h->prof_launches[tr.kinds[i]] += 1;
+    last.push_back(ms);
   }
   for (int k = 0; k < sym::NUM_KINDS; ++k) {
     const bool is_solve = k >= sym::S_FGATHER;
@@ -938,6 +942,14 @@ int sym_profile(sym_handle h, int32_t mode) {
     return fail(SYM_ERR_INVALID, "unknown profile mode");
   }
   return SYM_OK;
+}
+
+int64_t sym_profile_launches(sym_handle h, int32_t which, double *ms) {
+  if (!h) return fail(SYM_ERR_INVALID, "null handle");
+  if (which != 0 && which != 1) return fail(SYM_ERR_INVALID, "which must be 0 (factor) or 1 (solve)");
+  const std::vector<double> &v = h->last_launch_ms[which];
+  if (ms && !v.empty()) std::memcpy(ms, v.data(), v.size() * sizeof(double));
+  return (int64_t)v.size();
 }
 
 int sym_profile_read(sym_handle h, int32_t kind, double *ms, int64_t *launches, double *flops) {
