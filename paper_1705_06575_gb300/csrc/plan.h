@@ -22,6 +22,9 @@ constexpr int SOLVE_CW = 512;
 constexpr int SOLVE_MAXRHS = 8;
 // Order bound of the tiles that the small-tile kernel variants take.
 constexpr int SMALL_TILE = 32;
+// Trailing-update GEMM CTAs resident on the whole GPU at once (3 per SM on 152 SMs): the size of
+// one wave, used to split the last wave of a long launch into finer work.
+constexpr int GEMM_SLOTS = 3 * 152;
 
 // One supernode as the kernels see it. Its panel is column-major, nrows x ncols, leading
 // dimension nrows, at Lx + lx. Row r of the panel is global row rows[rowp + r]; the first ncols

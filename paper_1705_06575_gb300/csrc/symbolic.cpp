@@ -567,15 +567,22 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
           if (parts[part].empty()) continue;
           const int64_t o = (int64_t)P.tasks.size();
           // A short launch on the main stream (the lookahead chain) splits its tiles into row
-          // halves so that twice as many SMs share the work of this latency-critical step.
+          // halves so that twice as many SMs share the work of this latency-critical step. A
+          // trailing-update launch on the auxiliary stream splits its last wave's worth of tiles
+          // (GEMM_SLOTS: 3 CTAs on each of the 152 SMs) into halves, so its final wave ends
+          // within half a tile's time instead of leaving most SMs idle for up to a whole one.
           const int64_t c0 = (int64_t)parts[part].size();
-          if (stream == 0 && (kind == K_TRSM || kind == K_GEMM) && 2 * c0 <= 152) {
-            for (const Int4 &a : parts[part]) {
+          int64_t split_from = c0;  // tasks from this index on are split into row halves
+          if (stream == 0 && (kind == K_TRSM || kind == K_GEMM) && 2 * c0 <= 152) split_from = 0;
+          if (stream == 1 && kind == K_GEMM) split_from = std::max<int64_t>(0, c0 - GEMM_SLOTS);
+          for (int64_t q = 0; q < c0; ++q) {
+            const Int4 &a = parts[part][q];
+            if (q < split_from) {
+              P.tasks.push_back(a);
+            } else {
               P.tasks.push_back({a.a, a.b, a.c, a.d | (1 << 16)});
               P.tasks.push_back({a.a, a.b, a.c, a.d | (2 << 16)});
             }
-          } else {
-            P.tasks.insert(P.tasks.end(), parts[part].begin(), parts[part].end());
           }
           Launch L{kind, l, o, (int64_t)P.tasks.size() - o};
           L.stream = stream;
