@@ -165,8 +165,6 @@ def oracle_sample(M, target_flops, repeats=1):
 
 def make_workload(name):
     import workloads as w
-    if name == "conduct3d7_48":
-        return w.conduct3d(48, np.random.default_rng(1000 * 1 + 48), "star")
     return w.cfg(name)
 
 

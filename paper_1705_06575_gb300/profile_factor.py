@@ -1,0 +1,100 @@
+"""Profiling driver: factor one named workload and report where the time goes.
+
+    python -m paper_1705_06575_gb300.profile_factor --workload conduct3d7_48 [--one-stream]
+        [--no-graphs] [--levels] [--repeat N]
+
+Without --levels it factors the matrix once per repeat (after one warm-up factorization) and
+exits: a fixed, short command to run under a profiler. With --one-stream --no-graphs every launch
+of the schedule executes in list order, so a profiler's launch index equals the index in
+sym_export(FACTOR_LAUNCHES) among launches of the same kernel. With --levels it runs one
+profiled factorization (CUDA events around every launch, one stream) and prints a JSON summary:
+per level of the supernodal tree and per kernel kind the milliseconds, launches and tasks, the
+serialised total and the time a two-stream schedule would take if both streams' launches kept
+their serialised durations (an upper bound on what the lookahead can overlap).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+
+import numpy as np
+
+from . import (SYM_FLAG_NO_GRAPHS, SYM_FLAG_ONE_STREAM, SYM_PROFILE_OFF, SYM_PROFILE_ON, SYM_PROFILE_RESET,
+               Solver, sym_profile, sym_profile_launches)
+
+KIND_NAMES = {1: "update", 2: "potrf", 3: "trsm", 4: "gemm", 5: "trtri"}
+
+
+def level_summary(s, ms):
+    """Per-level breakdown of one profiled factorization (ms: sym_profile_launches(h, 0))."""
+    raw = s.export("factor_launches").reshape(-1, 5)
+    kind = raw[:, 0] & 0xffffffff
+    level = raw[:, 0] >> 32
+    count = raw[:, 2]
+    stream = raw[:, 3] >> 32
+    wait = (raw[:, 4] & 0xffffffff).astype(np.uint32).astype(np.int32)
+    if len(ms) != len(raw) + 1:
+        raise RuntimeError(f"{len(ms)} timed launches for a schedule of {len(raw)} (+1 scatter)")
+    t = np.asarray(ms[1:])
+    end = np.zeros(len(raw))
+    tail = {0: 0.0, 1: 0.0}
+    for i in range(len(raw)):
+        st = int(stream[i])
+        start = tail[st] if wait[i] < 0 else max(tail[st], end[wait[i]])
+        end[i] = start + t[i]
+        tail[st] = end[i]
+    levels = []
+    for lv in range(int(level.max()) + 1 if len(raw) else 0):
+        row = {"level": lv}
+        for k, name in KIND_NAMES.items():
+            sel = (level == lv) & (kind == k)
+            if sel.any():
+                row[name] = {"ms": round(float(t[sel].sum()), 3), "launches": int(sel.sum()),
+                             "tasks": int(count[sel].sum())}
+        row["aux_stream_ms"] = round(float(t[(level == lv) & (stream == 1)].sum()), 3)
+        levels.append(row)
+    return {"scatter_ms": float(ms[0]), "serialised_ms": float(t.sum()),
+            "two_stream_bound_ms": float(max(tail.values())), "levels": levels}
+
+
+def main(argv=None):
+    import torch
+
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import workloads as w
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="conduct3d7_48")
+    ap.add_argument("--one-stream", action="store_true")
+    ap.add_argument("--no-graphs", action="store_true")
+    ap.add_argument("--levels", action="store_true")
+    ap.add_argument("--repeat", type=int, default=1)
+    args = ap.parse_args(argv)
+    M = w.cfg(args.workload)
+    flags = (SYM_FLAG_ONE_STREAM if args.one_stream else 0) | (SYM_FLAG_NO_GRAPHS if args.no_graphs else 0)
+    s = Solver(M.n, M.Ap, M.Ai, M.perm, flags=flags)
+    Ax = torch.from_numpy(M.Ax).cuda()
+    s.factor(Ax)  # warm-up (and graph capture unless --no-graphs)
+    torch.cuda.synchronize()
+    if args.levels:
+        sym_profile(s.h, SYM_PROFILE_RESET)
+        sym_profile(s.h, SYM_PROFILE_ON)
+        s.factor(Ax)
+        torch.cuda.synchronize()
+        sym_profile(s.h, SYM_PROFILE_OFF)
+        out = level_summary(s, sym_profile_launches(s.h, 0))
+        out["workload"] = args.workload
+        print(json.dumps(out))
+    else:
+        for _ in range(args.repeat):
+            s.factor(Ax)
+        torch.cuda.synchronize()
+        print(json.dumps({"workload": args.workload, "factorizations": args.repeat + 1, "status": "ok"}))
+    s.close()
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())

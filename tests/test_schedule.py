@@ -406,3 +406,20 @@ def test_lookahead_streams_are_used_and_ordered():
     assert all(L[i][4] >= 0 for i in aux)
     pairs = concurrent_pairs(L)
     assert any(int(L[i][0]) == K_POTRF or int(L[j][0]) == K_POTRF for i, j in pairs)
+
+
+def test_level_summary_of_the_profiling_driver():
+    """The profiling driver's two-stream bound follows the schedule's streams and waits: with
+    every launch taking 1 ms it equals the longest chain of dependent launches, at most the
+    serialised total, and each level's kinds add up to the schedule."""
+    from paper_1705_06575_gb300.profile_factor import level_summary
+    M = w.conduct3d(16, np.random.default_rng(5), "star")
+    s = S.Solver(M.n, M.Ap, M.Ai, M.perm, host_only=True)
+    raw = s.export("factor_launches").reshape(-1, 5)
+    out = level_summary(s, np.ones(len(raw) + 1))
+    assert out["serialised_ms"] == len(raw)
+    assert out["two_stream_bound_ms"] <= out["serialised_ms"]
+    assert sum(v["launches"] for r in out["levels"] for k, v in r.items() if isinstance(v, dict)) == len(raw)
+    stream = raw[:, 3] >> 32
+    if (stream == 1).any():
+        assert out["two_stream_bound_ms"] < out["serialised_ms"]

@@ -387,6 +387,8 @@ def cfg(name, matrix_index=0):
         return laplace2d5(64, _seed(0, matrix_index))
     if name == "conduct3d7_64":
         return conduct3d(64, _seed(1, matrix_index), "star")
+    if name == "conduct3d7_48":  # the smaller case of the same family, for profiler captures
+        return conduct3d(48, _seed(1, 48 + matrix_index), "star")
     if name == "conduct3d27_40":
         return conduct3d(40, _seed(1, 1 + matrix_index), "box")
     if name == "dd2d9_128":
