@@ -32,10 +32,7 @@ namespace {
 
 constexpr int THREADS = 256;
 constexpr int KC = 16;  // inner-dimension chunk staged in shared memory (k_gemm)
-constexpr int KCU = 8;  // the same for k_update, whose accumulator tile also lives in shared memory
-// Chunks of the register-blocked kernels per storage type: FP64 is bound by its pipe, so small
-// chunks suffice; at the FP32 rate a chunk must carry enough multiply-adds to cover the latency
-// of staging the next one.
+constexpr int KCU = 8;  // the same for the FP64 update kernels (accumulator tile in shared memory)
 // Small-tile variants: a launch whose tiles all have at most 32 rows and columns (or, for TRSM,
 // at most 32 columns) runs kernels sized for 32 x 32 tiles with 128 threads, so that many more
 // CTAs share an SM than the 64 x 64 forms allow (the batched workloads and the lower levels of the
@@ -46,9 +43,11 @@ struct TileCfg {
   static constexpr int threads = TB == NB ? THREADS : 128;
 };
 
+// Inner-dimension chunks per storage type: FP64 is bound by its pipe, so small chunks suffice; at
+// the FP32 rate a chunk must carry enough multiply-adds to cover the latency of staging the next.
 template <typename T>
 struct Chunk {
-  static constexpr int upd = KCU, gemm = KC;
+  static constexpr int gemm = KC;
 };
 template <>
 struct Chunk<float> {
@@ -158,19 +157,41 @@ __global__ void k_scatter(const double *__restrict__ Ax, const int64_t *__restri
 }
 
 // ---------------------------------------------------------------------------------------------
-// (a) External update of one tile (bi, bj) of supernode J by all its descendant entries.
-// Thread layout: warp w owns tile columns w + 8j (j < 8), lane owns rows lane and lane + 32.
-template <typename T>
-__global__ void __launch_bounds__(THREADS) k_update(const SNode *__restrict__ sn,
-                                                    const UpdTask *__restrict__ tasks,
-                                                    const UpdEntry *__restrict__ ents,
-                                                    const int32_t *__restrict__ rel,
-                                                    T *__restrict__ Lx, int64_t toff, const Batch bt) {
+// (a) External update of one tile (bi, bj) of supernode J by all its descendant entries: FP32
+// factors use the 4 x 8 register tile below, FP64 factors the flat element map further down.
+// FP32 register tile: r[i][j] -= A[kk][4 rg + i] * B[kk][8 cg + j] for kk < kc, with one 16-byte
+// load of A and two of B per step (3 shared-memory loads per 32 multiply-adds; the FP32 pipe is
+// 32 times faster than FP64 on this part, so operand traffic, not arithmetic, bounds a thinner
+// tile: the 2 x 8 form issues 10 loads per 16 multiply-adds and measured 26% FMA-pipe use).
+constexpr int F32_THREADS = 128;
+__device__ __forceinline__ void f32_chunk(float (&r)[4][8], const float (*As)[NB], const float (*Bs)[NB], int kc,
+                                          int rg, int cg) {
+#pragma unroll 4
+  for (int kk = 0; kk < kc; ++kk) {
+    const float4 a = *reinterpret_cast<const float4 *>(&As[kk][4 * rg]);
+    const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[kk][8 * cg]);
+    const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[kk][8 * cg + 4]);
+    const float av[4] = {a.x, a.y, a.z, a.w};
+    const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) r[i][j] = fmaf(-av[i], bv[j], r[i][j]);
+  }
+}
+
+// (a'') The external update for an FP32 factor: 128 threads, thread (rg, cg) = (tid % 16, tid / 16)
+// owns rows 4 rg .. 4 rg + 3 and columns 8 cg .. 8 cg + 7 of an entry's m x n block.
+__global__ void __launch_bounds__(F32_THREADS) k_update_f32(const SNode *__restrict__ sn,
+                                                            const UpdTask *__restrict__ tasks,
+                                                            const UpdEntry *__restrict__ ents,
+                                                            const int32_t *__restrict__ rel,
+                                                            float *__restrict__ Lx, int64_t toff, const Batch bt) {
+  constexpr int KU = Chunk<float>::upd;
   Lx += blockIdx.y * bt.lx;
-  __shared__ T acc[NB][NB + 1];  // [col][row]
-  constexpr int KU = Chunk<T>::upd;
-  __shared__ T As[KU][NB];
-  __shared__ T Bs[KU][NB];
+  __shared__ float acc[NB][NB + 1];  // [col][row]
+  __shared__ __align__(16) float As[KU][NB];
+  __shared__ __align__(16) float Bs[KU][NB];
   __shared__ int prow[NB], pcol[NB];
   const UpdTask t = tasks[toff + blockIdx.x];
   const SNode sj = sn[t.J];
@@ -178,9 +199,9 @@ __global__ void __launch_bounds__(THREADS) k_update(const SNode *__restrict__ sn
   const int tm = d_row_tile_rows(t.bi, sj.ncols, sj.nrows, sj.ncb);
   const int cb = t.bj * NB;
   const int tn = min(NB, sj.ncols - cb);
-  T *C = Lx + sj.lx + (int64_t)cb * sj.nrows + rb;
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  for (int idx = tid; idx < tm * tn; idx += THREADS) {  // only the tile's own part is read
+  float *C = Lx + sj.lx + (int64_t)cb * sj.nrows + rb;
+  const int tid = threadIdx.x, rg = tid & 15, cg = tid >> 4;
+  for (int idx = tid; idx < tm * tn; idx += F32_THREADS) {
     int r = idx % tm, c = idx / tm;
     acc[c][r] = C[(int64_t)c * sj.nrows + r];
   }
@@ -190,43 +211,95 @@ __global__ void __launch_bounds__(THREADS) k_update(const SNode *__restrict__ sn
     if (tid < E.m) prow[tid] = rel[E.relr + tid] - (int)rb;
     if (tid >= NB && tid - NB < E.n) pcol[tid - NB] = rel[E.relc + tid - NB] - cb;
     __syncthreads();
-    const int ni = E.m > 32 ? 2 : 1;           // row halves with at least one valid row
-    const int nj = E.n > w ? (E.n - w + 7) / 8 : 0;  // this warp's columns w + 8j < n
-    T r[2][8];
+    const bool active = 4 * rg < E.m && 8 * cg < E.n;
+    float r[4][8];
 #pragma unroll
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
-        int a = lane + 32 * i, b = w + 8 * j;
-        r[i][j] = (a < E.m && b < E.n) ? acc[pcol[b]][prow[a]] : T(0);
+        const int a = 4 * rg + i, b = 8 * cg + j;
+        r[i][j] = (a < E.m && b < E.n) ? acc[pcol[b]][prow[a]] : 0.f;
       }
-    const T *Kp = Lx + sk.lx;
+    const float *Kp = Lx + sk.lx;
     for (int k0 = 0; k0 < sk.ncols; k0 += KU) {
       const int kc = min(KU, sk.ncols - k0);
-      for (int idx = tid; idx < KU * NB; idx += THREADS) {
+      for (int idx = tid; idx < KU * NB; idx += F32_THREADS) {
         int a = idx % NB, kk = idx / NB;
-        const T *col = Kp + (int64_t)(k0 + kk) * sk.nrows;
-        As[kk][a] = (a < E.m && kk < kc) ? col[E.r_lo + a] : T(0);
-        Bs[kk][a] = (a < E.n && kk < kc) ? col[E.c_lo + a] : T(0);
+        const float *col = Kp + (int64_t)(k0 + kk) * sk.nrows;
+        As[kk][a] = (a < E.m && kk < kc) ? col[E.r_lo + a] : 0.f;
+        Bs[kk][a] = (a < E.n && kk < kc) ? col[E.c_lo + a] : 0.f;
       }
       __syncthreads();
-      fma_chunk_dispatch<KU>(r, As, Bs, kc, lane, w, ni, nj);
+      if (active) f32_chunk(r, As, Bs, kc, rg, cg);
       __syncthreads();
     }
 #pragma unroll
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
-        int a = lane + 32 * i, b = w + 8 * j;
+        const int a = 4 * rg + i, b = 8 * cg + j;
         if (a < E.m && b < E.n) acc[pcol[b]][prow[a]] = r[i][j];
       }
     __syncthreads();
   }
   __syncthreads();
-  for (int idx = tid; idx < tm * tn; idx += THREADS) {
+  for (int idx = tid; idx < tm * tn; idx += F32_THREADS) {
     int r = idx % tm, c = idx / tm;
     C[(int64_t)c * sj.nrows + r] = acc[c][r];
   }
+}
+
+// (c'') The trailing update inside J for an FP32 factor, with the same 4 x 8 register tile.
+__global__ void __launch_bounds__(F32_THREADS) k_gemm_f32(const SNode *__restrict__ sn,
+                                                          const Int4 *__restrict__ tasks,
+                                                          float *__restrict__ Lx, int64_t toff, const Batch bt) {
+  constexpr int KG = Chunk<float>::gemm;
+  Lx += blockIdx.y * bt.lx;
+  __shared__ __align__(16) float As[KG][NB];
+  __shared__ __align__(16) float Bs[KG][NB];
+  const Int4 t = tasks[toff + blockIdx.x];
+  const SNode sj = sn[t.a];
+  const int i = t.b, j = t.c, s = t.d & 0xffff;
+  int64_t rb = d_row_tile_base(i, sj.ncols, sj.ncb);
+  int tm = d_row_tile_rows(i, sj.ncols, sj.nrows, sj.ncb);
+  const int half = t.d >> 16;  // 0: whole tile; 1, 2: its first or second 32 rows
+  if (half) {
+    rb += (half - 1) * (NB / 2);
+    tm = max(0, min(NB / 2, tm - (half - 1) * (NB / 2)));
+  }
+  const int tn = min(NB, sj.ncols - j * NB);
+  const int ks = min(NB, sj.ncols - s * NB);
+  const float *P = Lx + sj.lx + (int64_t)(s * NB) * sj.nrows;  // column block s
+  float *C = Lx + sj.lx + (int64_t)(j * NB) * sj.nrows + rb;
+  const int tid = threadIdx.x, rg = tid & 15, cg = tid >> 4;
+  const bool active = 4 * rg < tm && 8 * cg < tn;
+  float r[4][8];
+#pragma unroll
+  for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) {
+      const int a = 4 * rg + ii, b = 8 * cg + jj;
+      r[ii][jj] = (a < tm && b < tn) ? C[(int64_t)b * sj.nrows + a] : 0.f;
+    }
+  for (int k0 = 0; k0 < ks; k0 += KG) {
+    const int kc = min(KG, ks - k0);
+    for (int idx = tid; idx < KG * NB; idx += F32_THREADS) {
+      int a = idx % NB, kk = idx / NB;
+      const float *col = P + (int64_t)(k0 + kk) * sj.nrows;
+      As[kk][a] = (a < tm && kk < kc) ? col[rb + a] : 0.f;
+      Bs[kk][a] = (a < tn && kk < kc) ? col[(int64_t)j * NB + a] : 0.f;
+    }
+    __syncthreads();
+    if (active) f32_chunk(r, As, Bs, kc, rg, cg);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) {
+      const int a = 4 * rg + ii, b = 8 * cg + jj;
+      if (a < tm && b < tn) C[(int64_t)b * sj.nrows + a] = r[ii][jj];
+    }
 }
 
 // r[j] -= A[kk][a_j] * B[kk][b_j] for kk < kc and the first J element slots of this thread
@@ -1154,9 +1227,10 @@ cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, co
     switch (L.kind) {
       case K_UPDATE:
         // FP64: flat element map (the FP64 pipe is the bound and every issued DFMA should be
-        // useful); FP32: register-blocked tiles (operand reuse matters at the FP32 rate)
-        if (!std::is_same<T, double>::value)
-          e = launch_prio(k_update<T>, dim3(g, nb), THREADS, 0, s, prio, d.sn, d.upd_tasks, d.upd_entries, d.rel, Lx, L.off, bt);
+        // useful); FP32: 4 x 8 register tiles (operand reuse matters at the FP32 rate)
+        if constexpr (!std::is_same<T, double>::value)
+          e = launch_prio(k_update_f32, dim3(g, nb), F32_THREADS, 0, s, prio, d.sn, d.upd_tasks, d.upd_entries, d.rel,
+                          Lx, L.off, bt);
         else if (small)
           e = launch_prio(k_update_flat<T, SMALL_TB>, dim3(g, nb), TS, 0, s, prio, d.sn, d.upd_tasks, d.upd_entries, d.rel,
                           Lx, L.off, bt);
@@ -1174,7 +1248,10 @@ cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, co
                   : launch_prio(k_trsm<T, NB>, dim3(g, nb), THREADS, trsm_smem<T, NB>(), s, prio, d.sn, d.tasks, Lx, L.off, bt);
         break;
       case K_GEMM:
-        e = launch_prio(k_gemm<T>, dim3(g, nb), THREADS, 0, s, prio, d.sn, d.tasks, Lx, L.off, bt);
+        if constexpr (std::is_same<T, double>::value)
+          e = launch_prio(k_gemm<T>, dim3(g, nb), THREADS, 0, s, prio, d.sn, d.tasks, Lx, L.off, bt);
+        else
+          e = launch_prio(k_gemm_f32, dim3(g, nb), F32_THREADS, 0, s, prio, d.sn, d.tasks, Lx, L.off, bt);
         break;
       case K_TRTRI:
         e = small ? launch_prio(k_trtri<T, SMALL_TB>, dim3(g, nb), TS, trtri_smem<SMALL_TB>(), s, prio, d.sn, d.tasks,
