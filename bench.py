@@ -287,6 +287,7 @@ def bench_batched(S, torch, args, stream, barrier, world):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
+    ms, _ = dist_aggregate(ms, 0.0, world)  # every rank factors its own batch: the slowest rank
     # per-kernel breakdown of the batched step (profiled pass, kernel by kernel)
     s.profile(S.SYM_PROFILE_RESET)
     s.profile(S.SYM_PROFILE_ON)
