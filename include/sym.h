@@ -113,7 +113,8 @@ int sym_analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, sym_handle *out
  * fundamental supernodes, amalgamation, supernodal row structure, descendant lists (the block
  * prune-set), relative row maps, level schedule, kernel task lists; then one upload of the
  * plan to the current device (unless SYM_FLAG_HOST_ONLY). Errors: SYM_ERR_INVALID for a bad
- * pattern or permutation, SYM_ERR_OOM, SYM_ERR_CUDA. On error *out is NULL. */
+ * pattern or permutation, SYM_ERR_LIMIT when the forward solve's push buffer would hold 2^31
+ * entries or more (see SYM_EXPORT_CONTRIB), SYM_ERR_OOM, SYM_ERR_CUDA. On error *out is NULL. */
 int sym_analyze_perm(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm,
                      const sym_options *opt, sym_handle *out);
 
