@@ -329,6 +329,90 @@ def bench_batched(S, torch, args, stream, barrier, world):
             "definition": "512 x (factor + 1-RHS solve) of the 128^2 9-point pattern per step"}
 
 
+def _event_ms(torch, stream, fn, reps):
+    """Milliseconds per call of fn over reps calls, CUDA events on stream (after 3 warm-ups)."""
+    for _ in range(3):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def bench_small_latency(S, torch, stream):
+    """The small 2D case (64^2 5-point, n = 4096, one right-hand side): launch- and
+    latency-bound, reported in microseconds per factor + solve with its level count."""
+    import workloads as w
+    M = w.cfg("laplace2d5_64")
+    s = S.Solver(M.n, M.Ap, M.Ai, M.perm)
+    s.set_stream(stream)
+    info = s.info()
+    Ax = torch.from_numpy(M.Ax).cuda()
+    b = torch.from_numpy(w.rhs(M.n, 1, np.random.default_rng(7))[:, 0].copy()).cuda()
+    x = torch.empty_like(b)
+    us_f = 1e3 * _event_ms(torch, stream, lambda: s.factor(Ax), 50)
+    us_s = 1e3 * _event_ms(torch, stream, lambda: S.sym_solve(s.h, b, x), 50)
+    us = 1e3 * _event_ms(torch, stream, lambda: (s.factor(Ax), S.sym_solve(s.h, b, x)), 50)
+    berr = backward_error(M, b.cpu().numpy()[:, None], x.cpu().numpy()[:, None])
+    s.close()
+    return {"us_per_step": us, "us_factor": us_f, "us_solve": us_s, "levels": info.nlevels,
+            "launches_per_step": int(info.nlaunch_factor + info.nlaunch_solve), "flops": info.flops,
+            "backward_error": berr, "definition": "64^2 5-point, FP64 factor + 1-RHS solve, CUDA graphs"}
+
+
+def bench_uneven_batch(S, torch, stream):
+    """An uneven batch: 256 independent 5-point grids with sides uniform in 32..256, factored and
+    solved (one right-hand side) as one block-diagonal matrix with one plan."""
+    import workloads as w
+    mats, sides = w.uneven_grid_batch(256, np.random.default_rng(3000))
+    U = w.block_diagonal(mats)
+    s = S.Solver(U.n, U.Ap, U.Ai, U.perm)
+    s.set_stream(stream)
+    info = s.info()
+    Ax = torch.from_numpy(U.Ax).cuda()
+    b = torch.from_numpy(w.rhs(U.n, 1, np.random.default_rng(8))[:, 0].copy()).cuda()
+    x = torch.empty_like(b)
+    ms = _event_ms(torch, stream, lambda: (s.factor(Ax), S.sym_solve(s.h, b, x)), 5)
+    berr = backward_error(U, b.cpu().numpy()[:, None], x.cpu().numpy()[:, None])
+    s.close()
+    return {"value": info.flops / (ms * 1e-3) / 1e9, "unit": "GFLOP/s", "ms_per_step": ms, "matrices": 256,
+            "n": U.n, "nnz_l": info.nnz_l, "sides": [int(sides.min()), int(sides.max())], "backward_error": berr,
+            "dtype": "f64", "definition": "FP64 factor + 1-RHS solve of the block-diagonal union per step"}
+
+
+def bench_mixed_vector(S, torch, stream):
+    """The 3-dof vector problem (48^3 nodes x 3, 27-point coupling, coefficients 1 / 1e2 / 1e4 by
+    subdomain): FP32 factor + FP64 conjugate-gradient refinement to backward error <= 1e-12 for
+    one right-hand side, with the refinement's iteration count, against one FP64 factorization."""
+    import workloads as w
+    M = w.cfg("vector3d27_48")
+    b = torch.from_numpy(w.rhs(M.n, 1, np.random.default_rng(9))[:, 0].copy()).cuda()
+    x = torch.empty_like(b)
+    Ax = torch.from_numpy(M.Ax).cuda()
+    s = S.Solver(M.n, M.Ap, M.Ai, M.perm, precision="mixed")
+    s.set_stream(stream)
+    s.set_refinement(1e-12, 200)
+    info = s.info()
+    ms_f = _event_ms(torch, stream, lambda: s.factor(Ax), 3)
+    ms = _event_ms(torch, stream, lambda: (s.factor(Ax), S.sym_solve(s.h, b, x)), 3)
+    it, _ = s.refinement_info()
+    berr = backward_error(M, b.cpu().numpy()[:, None], x.cpu().numpy()[:, None])
+    s.close()
+    d = S.Solver(M.n, M.Ap, M.Ai, M.perm)
+    d.set_stream(stream)
+    ms_f64 = _event_ms(torch, stream, lambda: d.factor(Ax), 1)
+    d.close()
+    return {"value": info.flops / (ms * 1e-3) / 1e9, "unit": "GFLOP/s", "ms_per_step": ms, "ms_factor_fp32": ms_f,
+            "ms_refined_solve": ms - ms_f, "refinement_iterations": it, "backward_error": berr,
+            "ms_factor_fp64": ms_f64, "n": M.n, "nnz_l": info.nnz_l, "factor_flops": info.flops,
+            "dtype": "f32 factor + f64 refinement",
+            "definition": "FP32 factor + refined 1-RHS solve per step; value = factor flops / step time"}
+
+
 def bench_sparse_rhs(S, torch, s, M, args, stream):
     """Forward solve L y = P b for sparse b over the reach set (VI-Prune + VS-Block) on the
     benchmark matrix: b = one column of A (a local source) and b with 1% random nonzeros, each
@@ -475,6 +559,12 @@ def run_ours(args):
         variants["mixed_fp32_pcg"] = bench_mixed(S, torch, M, B, info.flops, args, stream, barrier, world)
         if args.batch > 0:
             variants["batched_512x_dd2d9_128"] = bench_batched(S, torch, args, stream, barrier, world)
+        for key, fn in (("latency_laplace2d5_64", bench_small_latency), ("uneven_batch_256_grids", bench_uneven_batch),
+                        ("mixed_vector3d27_48", bench_mixed_vector)):
+            try:
+                variants[key] = fn(S, torch, stream)
+            except S.SymError as e:  # a library error is reported, not fatal to the main line
+                variants[key] = {"error": str(e)}
     clocks = read_clocks(clock_path, local) if rank == 0 else None
     flops = info.flops
     value = total_flops / (ms_step * 1e-3) / 1e9
