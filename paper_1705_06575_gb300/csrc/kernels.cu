@@ -340,8 +340,8 @@ __device__ __forceinline__ void flat_chunk_dispatch(T (&r)[FLAT_SLOTS], const in
 // memory, which the narrow FP64 pipe leaves ample room for (one warp-wide DFMA per
 // sub-partition every 64 cycles). The accumulation order of every element is the one of
 // k_update: the factor is bit-identical.
-template <typename T, int TB>
-__global__ void __launch_bounds__(TileCfg<TB>::threads, TB == NB ? 3 : 6)
+template <typename T, int TB, bool CLUSTER>
+__global__ void __launch_bounds__(TileCfg<TB>::threads, TB == NB ? (CLUSTER ? 2 : 3) : 6)
     k_update_flat(const SNode *__restrict__ sn, const UpdTask *__restrict__ tasks,
                   const UpdEntry *__restrict__ ents, const int32_t *__restrict__ rel, T *__restrict__ Lx,
                   int64_t toff, const Batch bt) {
@@ -351,7 +351,15 @@ __global__ void __launch_bounds__(TileCfg<TB>::threads, TB == NB ? 3 : 6)
   __shared__ T As[KCU][TB];
   __shared__ T Bs[KCU][TB];
   __shared__ int prow[TB], pcol[TB];
-  const UpdTask t = tasks[toff + blockIdx.x];
+  // A launch with few tiles runs each tile on a thread-block cluster: rank r applies entries
+  // r, r + cs, ... to its own accumulator (rank 0 starts from the tile, the others from zero) and
+  // rank 0 adds the others' partial tiles in rank order through distributed shared memory, so the
+  // result does not depend on scheduling.
+  // (CLUSTER = false: one CTA per tile, without the cluster bookkeeping and its registers.)
+  cg::cluster_group cluster = cg::this_cluster();
+  const int cs = CLUSTER ? (int)cluster.num_blocks() : 1;
+  const int rank = CLUSTER ? (int)cluster.block_rank() : 0;
+  const UpdTask t = tasks[toff + blockIdx.x / cs];
   const SNode sj = sn[t.J];
   const int64_t rb = d_row_tile_base(t.bi, sj.ncols, sj.ncb);
   const int tm = d_row_tile_rows(t.bi, sj.ncols, sj.nrows, sj.ncb);
@@ -362,9 +370,9 @@ __global__ void __launch_bounds__(TileCfg<TB>::threads, TB == NB ? 3 : 6)
   const int tid = threadIdx.x, w = tid >> 5;
   for (int idx = tid; idx < tm * tn; idx += TT) {  // only the tile's own part is read
     int r = idx % tm, c = idx / tm;
-    acc[c][r] = C[(int64_t)c * sj.nrows + r];
+    acc[c][r] = rank == 0 ? C[(int64_t)c * sj.nrows + r] : T(0);
   }
-  for (int64_t e = t.e0; e < t.e1; ++e) {
+  for (int64_t e = t.e0 + rank; e < t.e1; e += cs) {
     const UpdEntry E = ents[e];
     const SNode sk = sn[E.K];
     if (tid < E.m) prow[tid] = rel[E.relr + tid] - (int)rb;
@@ -416,11 +424,24 @@ __global__ void __launch_bounds__(TileCfg<TB>::threads, TB == NB ? 3 : 6)
     }
     __syncthreads();
   }
-  __syncthreads();
-  for (int idx = tid; idx < tm * tn; idx += TT) {
-    int r = idx % tm, c = idx / tm;
-    C[(int64_t)c * sj.nrows + r] = acc[c][r];
+  if (!CLUSTER) {
+    __syncthreads();
+    for (int idx = tid; idx < tm * tn; idx += TT) {
+      int r = idx % tm, c = idx / tm;
+      C[(int64_t)c * sj.nrows + r] = acc[c][r];
+    }
+    return;
   }
+  cluster.sync();  // every rank's partial tile is complete
+  if (rank == 0) {
+    for (int idx = tid; idx < tm * tn; idx += TT) {
+      int r = idx % tm, c = idx / tm;
+      T v = acc[c][r];
+      for (int o = 1; o < cs; ++o) v += cluster.map_shared_rank(&acc[0][0], o)[c * (TB + 1) + r];
+      C[(int64_t)c * sj.nrows + r] = v;
+    }
+  }
+  cluster.sync();  // keep the other ranks' shared memory alive until rank 0 has read it
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1203,6 +1224,27 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, int threads, size_t 
   return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
+// Launch of thread-block clusters of cs CTAs along x, with a stream priority.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_cluster_prio(void (*kernel)(KArgs...), dim3 grid, int threads, int cs, cudaStream_t st, int prio,
+                                Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[2];
+  cfg.gridDim = dim3(grid.x * (unsigned)cs, grid.y, grid.z);
+  cfg.blockDim = dim3(threads, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  attr[0].id = cudaLaunchAttributePriority;
+  attr[0].val.priority = prio;
+  attr[1].id = cudaLaunchAttributeClusterDimension;
+  attr[1].val.clusterDim.x = (unsigned)cs;
+  attr[1].val.clusterDim.y = 1;
+  attr[1].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = cs > 1 ? 2 : 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 inline void trace_mark(LaunchTrace *tr, int32_t kind, cudaStream_t st) {
   if (!tr) return;
   cudaEventRecord((*tr->events)[tr->used++], st);
@@ -1284,11 +1326,14 @@ cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, co
           e = launch_prio(k_update_f32, dim3(g, nb), F32_THREADS, 0, s, prio, d.sn, d.upd_tasks, d.upd_entries, d.rel,
                           Lx, L.off, bt);
         else if (small)
-          e = launch_prio(k_update_flat<T, SMALL_TB>, dim3(g, nb), TS, 0, s, prio, d.sn, d.upd_tasks, d.upd_entries, d.rel,
-                          Lx, L.off, bt);
+          e = launch_prio(k_update_flat<T, SMALL_TB, false>, dim3(g, nb), TS, 0, s, prio, d.sn, d.upd_tasks,
+                          d.upd_entries, d.rel, Lx, L.off, bt);
+        else if (L.cluster > 1 && nb == 1)  // (a batch already fills the GPU through blockIdx.y)
+          e = launch_cluster_prio(k_update_flat<T, NB, true>, dim3(g, nb), THREADS, L.cluster, s, prio, d.sn,
+                                  d.upd_tasks, d.upd_entries, d.rel, Lx, L.off, bt);
         else
-          e = launch_prio(k_update_flat<T, NB>, dim3(g, nb), THREADS, 0, s, prio, d.sn, d.upd_tasks, d.upd_entries, d.rel,
-                          Lx, L.off, bt);
+          e = launch_prio(k_update_flat<T, NB, false>, dim3(g, nb), THREADS, 0, s, prio, d.sn, d.upd_tasks,
+                          d.upd_entries, d.rel, Lx, L.off, bt);
         break;
       case K_POTRF:
         e = small ? launch_prio(k_potrf<T, SMALL_TB>, dim3(g, nb), TS, 0, s, prio, d.sn, d.tasks, Lx, status, L.off, bt)

@@ -530,6 +530,11 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
         U.count = (int64_t)P.upd_tasks.size() - U.off;
         if (U.count > 0) {
           U.tb = all_small ? SMALL_TILE : 0;
+          // Few tiles (the top of the tree, small matrices): spread each tile's descendant entries
+          // over a thread-block cluster of up to 8 CTAs while the launch still fits one wave.
+          U.cluster = 1;
+          if (!all_small)
+            while (U.cluster < 8 && U.count * U.cluster * 2 <= GEMM_SLOTS) U.cluster *= 2;
           U.wait = pending_join;
           pending_join = -1;
           P.factor_launches.push_back(U);

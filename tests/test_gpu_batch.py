@@ -47,10 +47,15 @@ def test_batch_matches_single_factorizations(torch_cuda):
         Lb, outside = panels_on_pattern(sx, S.sym_get_batch_factor_host(s.h, b), o.Lp, o.Li)
         assert outside == 0.0
         assert np.abs(Lb - o.Lx).max() <= ENTRY_RTOL * np.abs(o.Lx).max()
-    # a single factorization of matrix 4 gives the same panels as the batch
+    # a single factorization of matrix 4 gives the batch's panels up to rounding: a lone matrix
+    # spreads the tiles of its short update launches over thread-block clusters (partial sums
+    # added in rank order), the batch keeps one CTA per tile; each is deterministic
     single = S.Solver(M.n, M.Ap, M.Ai, M.perm)
     single.factor(torch.from_numpy(vals[4]).cuda())
-    assert np.array_equal(single.factor_panels(), S.sym_get_batch_factor_host(s.h, 4))
+    a, b = single.factor_panels(), S.sym_get_batch_factor_host(s.h, 4)
+    assert np.abs(a - b).max() <= 1e-13 * np.abs(b).max()
+    single.factor(torch.from_numpy(vals[4]).cuda())
+    assert np.array_equal(single.factor_panels(), a)
 
 
 def test_batch_reports_each_failing_matrix(torch_cuda):
