@@ -47,15 +47,20 @@ extern "C" {
 
 /* Precision of the factor (sym_options.precision). */
 #define SYM_PREC_FP64 0  /* FP64 factor and FP64 solves (the plain path) */
-#define SYM_PREC_MIXED 1 /* FP32 factor (all arithmetic FP32); solves refined in FP64 by
-                            conjugate gradients preconditioned with the FP32 factor, to a normwise
-                            backward error <= the refinement tolerance (default 1e-12) */
+#define SYM_PREC_MIXED 1 /* FP32 factor (FP32 storage and arithmetic; the external updates of
+                            64-wide tiles run on the tensor cores as TF32 splits, see
+                            SYM_FLAG_NO_TENSOR_CORES); solves refined in FP64 by conjugate
+                            gradients preconditioned with the FP32 factor, to a normwise backward
+                            error <= the refinement tolerance (default 1e-12) */
 
 /* Option flags. */
 #define SYM_FLAG_HOST_ONLY 1u /* run the inspector only; no device memory, no factor/solve */
 #define SYM_FLAG_NO_GRAPHS 2u /* launch kernel by kernel instead of replaying CUDA graphs */
 #define SYM_FLAG_ONE_STREAM 4u /* run every factor launch on the handle's stream in list order
                                   (no lookahead overlap; results are identical either way) */
+#define SYM_FLAG_NO_TENSOR_CORES 8u /* SYM_PREC_MIXED: external updates in FP32 on the SIMT
+                                       pipes instead of tcgen05 TF32 splits (x = hi + lo, all four
+                                       partial products accumulated in FP32) */
 
 typedef struct sym_handle_s *sym_handle;
 
@@ -133,7 +138,8 @@ int sym_set_stream(sym_handle h, void *stream);
  * supernodal panels and the level-by-level update / POTRF / TRSM kernels on the handle's stream,
  * then waits for them and reads the pivot status. Returns SYM_ERR_NOT_SPD when a pivot is not
  * positive (or is NaN); sym_last_error_column then gives the first failing column in the
- * caller's numbering and the factor is not usable. */
+ * caller's numbering and the factor is not usable. Returns SYM_ERR_TIMEOUT (factor not usable)
+ * when a tensor-core update of SYM_PREC_MIXED waited about a second for its MMAs in vain. */
 int sym_factor(sym_handle h, const double *Ax);
 
 /* As sym_factor but returns right after enqueueing (no wait, no status check). Call
@@ -356,6 +362,16 @@ int sym_profile_read(sym_handle h, int32_t kind, double *ms, int64_t *launches, 
  * Returns the count (0 before any profiled call); ms may be NULL to query it, else it receives
  * that many values. Errors: SYM_ERR_INVALID. */
 int64_t sym_profile_launches(sym_handle h, int32_t which, double *ms);
+
+/* Layout check of the tensor-core path (no counterpart in the paper): one CTA stages A (128 x 32)
+ * and B (64 x 32), row-major float32 HOST arrays whose values TF32 represents exactly, in the
+ * K-major core-matrix layout of the FP32 update, runs four kind::tf32 MMAs (M = 128, N = 64,
+ * K = 8) with shared-memory descriptors of leading / stride byte offsets lbo / sbo (128 and 1024
+ * in either order: the library's layout has lbo = 128, sbo = 1024), and writes D = A B^T
+ * (128 x 64, row-major) to the HOST array D. Both orders keep every address the MMAs read inside
+ * the staged operands. Errors: SYM_ERR_INVALID,
+ * SYM_ERR_CUDA, SYM_ERR_OOM, SYM_ERR_TIMEOUT (the MMAs did not complete within about a second). */
+int sym_tc_probe(const float *A, const float *B, float *D, uint32_t lbo, uint32_t sbo);
 
 /* Measured FMA throughput of the current device in GFLOP/s (2 flops per FMA) for precision 64
  * (FP64 pipe) or 32 (FP32 pipe): register-resident FMA chains on every SM, best of three

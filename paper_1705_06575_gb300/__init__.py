@@ -20,7 +20,7 @@ __all__ = [
     "sym_analyze_perm", "sym_set_stream", "sym_factor", "sym_factor_async", "sym_status",
     "sym_factor_host", "sym_solve", "sym_solve_multi", "sym_solve_host", "sym_info",
     "sym_last_error_column", "sym_get_factor_host", "sym_export", "sym_free", "load", "Solver",
-    "EXPORTS", "sym_profile", "sym_profile_read", "sym_profile_launches", "sym_fma_peak", "sym_solve_host_ptr", "KINDS",
+    "EXPORTS", "sym_profile", "sym_profile_read", "sym_profile_launches", "sym_fma_peak", "sym_tc_probe", "sym_solve_host_ptr", "KINDS",
     "sym_solve_multi_noalloc", "sym_set_refinement", "sym_refinement_info", "sym_factor_batch",
     "sym_batch_error_columns", "sym_solve_batch", "sym_get_batch_factor_host", "Reach", "MLP",
 ]
@@ -41,6 +41,7 @@ SYM_ORDER_GIVEN = 1
 SYM_FLAG_HOST_ONLY = 1
 SYM_FLAG_NO_GRAPHS = 2
 SYM_FLAG_ONE_STREAM = 4
+SYM_FLAG_NO_TENSOR_CORES = 8
 
 # name -> (code, numpy dtype)
 EXPORTS = {
@@ -116,6 +117,7 @@ def load():
             "sym_profile_read": ([P, i32, ct.POINTER(ct.c_double), ct.POINTER(i64),
                                   ct.POINTER(ct.c_double)], I),
             "sym_fma_peak": ([i32, ct.POINTER(ct.c_double)], I),
+            "sym_tc_probe": ([P, P, P, ct.c_uint32, ct.c_uint32], I),
             "sym_profile_launches": ([P, i32, P], i64),
             "sym_solve_multi_noalloc": ([P, i32, P, i64, P, i64], I),
             "sym_set_refinement": ([P, ct.c_double, i32], I),
@@ -280,6 +282,17 @@ def sym_fma_peak(precision=64):
     g = ct.c_double()
     _check(load().sym_fma_peak(int(precision), ct.byref(g)))
     return g.value
+
+
+def sym_tc_probe(A, B, lbo=128, sbo=1024):
+    """D = A B^T through one tcgen05 kind::tf32 tile product (A: 128 x 32, B: 64 x 32 float32)."""
+    A = np.ascontiguousarray(A, dtype=np.float32)
+    B = np.ascontiguousarray(B, dtype=np.float32)
+    if A.shape != (128, 32) or B.shape != (64, 32):
+        raise ValueError("A must be 128 x 32 and B 64 x 32")
+    D = np.empty((128, 64), dtype=np.float32)
+    _check(load().sym_tc_probe(A.ctypes.data, B.ctypes.data, D.ctypes.data, int(lbo), int(sbo)))
+    return D
 
 
 def sym_set_refinement(h, tol, max_iter):

@@ -338,6 +338,11 @@ int finish_status(sym_handle_s *h) {
   h->batch_err.assign(nb, -1);
   h->err_col = -1;
   int32_t bad = 0;
+  for (int32_t b = 0; b < nb; ++b)
+    if (h->h_status[h->bcap + b] == -1) {
+      h->factored = false;
+      return fail(SYM_ERR_TIMEOUT, "a bounded device wait of the factorization ran out");
+    }
   for (int32_t b = 0; b < nb; ++b) {
     const long long s = h->h_status[h->bcap + b];
     if (s != LLONG_MAX) {
@@ -504,6 +509,7 @@ int sym_analyze_perm(int64_t n, const int64_t *Ap, const int32_t *Ai, const int3
     h->dp.n = P.n;
     h->dp.nnz_a = P.nnz_a;
     h->dp.storage = P.storage();
+    h->dp.tensor_cores = (opt.flags & SYM_FLAG_NO_TENSOR_CORES) == 0;
   }
   *out = h;
   return SYM_OK;

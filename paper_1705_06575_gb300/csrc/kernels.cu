@@ -1262,6 +1262,10 @@ cudaError_t prepare_factor() {
   e = cudaFuncSetAttribute(k_trtri<T, SMALL_TB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)trtri_smem<SMALL_TB>());
   if (e != cudaSuccess) return e;
+  if constexpr (std::is_same<T, float>::value) {
+    e = prepare_update_tc();
+    if (e != cudaSuccess) return e;
+  }
   return cudaFuncSetAttribute(k_trtri<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trtri_smem<NB>());
 }
 
@@ -1322,9 +1326,13 @@ cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, co
       case K_UPDATE:
         // FP64: flat element map (the FP64 pipe is the bound and every issued DFMA should be
         // useful); FP32: 4 x 8 register tiles (operand reuse matters at the FP32 rate)
-        if constexpr (!std::is_same<T, double>::value)
-          e = launch_prio(k_update_f32, dim3(g, nb), F32_THREADS, 0, s, prio, d.sn, d.upd_tasks, d.upd_entries, d.rel,
-                          Lx, L.off, bt);
+        if constexpr (!std::is_same<T, double>::value) {
+          if (d.tensor_cores && !small)
+            e = launch_update_tc(dim3(g, nb), s, prio, d, Lx, L.off, bt, status);
+          else
+            e = launch_prio(k_update_f32, dim3(g, nb), F32_THREADS, 0, s, prio, d.sn, d.upd_tasks, d.upd_entries,
+                            d.rel, Lx, L.off, bt);
+        }
         else if (small)
           e = launch_prio(k_update_flat<T, SMALL_TB, false>, dim3(g, nb), TS, 0, s, prio, d.sn, d.upd_tasks,
                           d.upd_entries, d.rel, Lx, L.off, bt);

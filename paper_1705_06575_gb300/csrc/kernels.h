@@ -24,6 +24,7 @@ struct DevPlan {
   int64_t n = 0;
   int64_t nnz_a = 0;
   int64_t storage = 0;
+  bool tensor_cores = true;          // FP32 updates on tcgen05 (false: the FP32 SIMT kernel)
 };
 
 // Several matrices with one pattern (blockIdx.y = matrix): offsets, in elements, from one matrix to
@@ -63,8 +64,16 @@ cudaError_t prepare_factor();
 template <typename T, typename V>
 cudaError_t prepare_solve();
 
+// External updates of FP32 factors on the tensor cores (tc_update.cu): the attribute the kernel
+// needs (once per device, outside capture), and one launch of grid.x tiles of the UpdTask list
+// from toff. A bounded wait that runs out records -1 in status.
+cudaError_t prepare_update_tc();
+cudaError_t launch_update_tc(dim3 grid, cudaStream_t st, int prio, const DevPlan &d, float *Lx, int64_t toff,
+                             const Batch &bt, long long *status);
+
 // Numeric factorization: scatter A into the zeroed panels, then run the launch schedule.
-// status: device int64, receives the smallest failing (permuted) column, or stays INT64_MAX.
+// status: device int64, receives the smallest failing (permuted) column, or stays INT64_MAX;
+// -1 when a bounded device wait ran out.
 template <typename T>
 cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, const double *Ax,
                        T *Lx, T *Linv, long long *status, cudaStream_t st, LaunchTrace *trace = nullptr,

@@ -1,7 +1,7 @@
 """Profiling driver: factor one named workload and report where the time goes.
 
     python -m paper_1705_06575_gb300.profile_factor --workload conduct3d7_48 [--one-stream]
-        [--no-graphs] [--mixed] [--levels] [--repeat N]
+        [--no-graphs] [--mixed [--no-tensor-cores]] [--levels] [--repeat N]
 
 Without --levels it factors the matrix once per repeat (after one warm-up factorization) and
 exits: a fixed, short command to run under a profiler. With --one-stream --no-graphs every launch
@@ -21,8 +21,8 @@ import sys
 
 import numpy as np
 
-from . import (SYM_FLAG_NO_GRAPHS, SYM_FLAG_ONE_STREAM, SYM_PROFILE_OFF, SYM_PROFILE_ON, SYM_PROFILE_RESET,
-               Solver, sym_profile, sym_profile_launches)
+from . import (SYM_FLAG_NO_GRAPHS, SYM_FLAG_NO_TENSOR_CORES, SYM_FLAG_ONE_STREAM, SYM_PROFILE_OFF,
+               SYM_PROFILE_ON, SYM_PROFILE_RESET, Solver, sym_profile, sym_profile_launches)
 
 KIND_NAMES = {1: "update", 2: "potrf", 3: "trsm", 4: "gemm", 5: "trtri"}
 
@@ -70,11 +70,13 @@ def main(argv=None):
     ap.add_argument("--one-stream", action="store_true")
     ap.add_argument("--no-graphs", action="store_true")
     ap.add_argument("--mixed", action="store_true", help="FP32 factor (SYM_PREC_MIXED)")
+    ap.add_argument("--no-tensor-cores", action="store_true", help="FP32 updates on the SIMT pipes")
     ap.add_argument("--levels", action="store_true")
     ap.add_argument("--repeat", type=int, default=1)
     args = ap.parse_args(argv)
     M = w.cfg(args.workload)
-    flags = (SYM_FLAG_ONE_STREAM if args.one_stream else 0) | (SYM_FLAG_NO_GRAPHS if args.no_graphs else 0)
+    flags = ((SYM_FLAG_ONE_STREAM if args.one_stream else 0) | (SYM_FLAG_NO_GRAPHS if args.no_graphs else 0) |
+             (SYM_FLAG_NO_TENSOR_CORES if args.no_tensor_cores else 0))
     s = Solver(M.n, M.Ap, M.Ai, M.perm, flags=flags, precision="mixed" if args.mixed else None)
     Ax = torch.from_numpy(M.Ax).cuda()
     s.factor(Ax)  # warm-up (and graph capture unless --no-graphs)
