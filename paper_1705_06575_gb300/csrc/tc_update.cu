@@ -110,7 +110,7 @@ __device__ __forceinline__ void fetch(Prefetch &f, const float *__restrict__ Lx,
 // segment runs on the other accumulator. Long sums are thus rounded to nearest in FP32 as in the
 // SIMT form; inside the tensor core a sum runs over at most 8 SEG K = 8 steps.
 // A wait that runs out (about a second) records -1 in *status and leaves the tile unwritten.
-constexpr int SEG = 4;
+constexpr int SEG = 8;
 
 __global__ void __launch_bounds__(TC_THREADS, 3) k_update_tc(const SNode *__restrict__ sn,
                                                              const UpdTask *__restrict__ tasks,

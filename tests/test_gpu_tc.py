@@ -7,7 +7,7 @@
   split into two TF32 values, hi = RN(x) and lo = RN(x - hi) with 11 significant bits each, so
   |x - hi - lo| <= 2^-22 |x| and a product a b is formed with relative error <= 2^-21 (all four
   partial products are exact), against 2^-24 for an FP32 multiply; the tensor core's sums run
-  over at most 32 MMAs of K = 8 before they are added in FP32. The backward-stable measure scales
+  over at most 64 MMAs of K = 8 before they are added in FP32. The backward-stable measure scales
   with that unit: ||L L^T - A||_F / ||A||_F <= MIXED_FACTOR_TOL = 1e-6 for the SIMT factor and
   8 times that, TC_FACTOR_TOL = 8e-6, for the split. The entry-wise difference from the exact
   factor is a forward error, about kappa(A) u, and kappa reaches ~1e4 on these 3D grids with
