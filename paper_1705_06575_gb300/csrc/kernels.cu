@@ -3,7 +3,9 @@
 //
 // Paper mapping (Sec. 3.2, VS-Block + VI-Prune on left-looking Cholesky): for each supernode J,
 //   (a) update: L_J -= sum over descendants K (the block prune-set) of L_K[R1,:] L_K[R0,:]^T,
-//       scattered through the relative row maps — k_update, one CTA per NB x NB tile of J;
+//       scattered through the relative row maps, one CTA (or cluster) per NB x NB tile of J —
+//       k_update_flat (FP64), k_update_f32 (FP32), k_update_tc (FP32 on the tensor cores,
+//       tc_update.cu);
 //   (b) dense Cholesky of the diagonal block — k_potrf (per diagonal tile) and
 //   (c) dense triangular solves on the rows below it — k_trsm, with k_gemm applying the
 //       trailing updates inside J when J is wider than one tile.
@@ -13,10 +15,11 @@
 // from the rows below the diagonal block.
 //
 // The FP64 path is bound by the FP64 FMA pipe (about 2 DFMA per clock per SM on GB300), so the
-// kernels keep that pipe busy: register tiles of 2 x 8 outputs per thread, operand chunks staged
-// in shared memory, warp-uniform guards that skip whole warps outside ragged tiles, and no
-// atomics in the factorization (every tile is owned by one CTA, descendants are applied in a
-// fixed order, so results are deterministic).
+// kernels keep that pipe busy with useful work: a flat map of output elements onto threads for
+// the updates, register tiles of 2 x 8 outputs per thread for the in-supernode GEMM, operand
+// chunks staged in shared memory, warp-uniform guards that skip whole warps outside ragged
+// tiles, and no atomics in the factorization (every tile is owned by one CTA or cluster,
+// descendants are applied in a fixed order, so results are deterministic).
 #include <cooperative_groups.h>
 #include <type_traits>
 
@@ -334,12 +337,11 @@ __device__ __forceinline__ void flat_chunk_dispatch(T (&r)[FLAT_SLOTS], const in
 // elements onto the threads: element e of an entry (e < m n, or e < m (m + 1) / 2 on a diagonal
 // tile, whose strictly upper part is never needed) goes to thread e % 256, slot e / 256; slots
 // are taken 8 at a time (one pass over ncols(K) per 2048 elements) to keep three CTAs per SM.
-// Every multiply-add is then useful except in the last slot of a partial warp (the
-// register-blocked k_update computes whole 32-row halves and full squares on diagonal tiles:
-// 92% useful on the 64^3 workload). Each multiply-add takes its own two operands from shared
-// memory, which the narrow FP64 pipe leaves ample room for (one warp-wide DFMA per
-// sub-partition every 64 cycles). The accumulation order of every element is the one of
-// k_update: the factor is bit-identical.
+// Every multiply-add is then useful except in the last slot of a partial warp (a register-
+// blocked form, computing whole 32-row halves and full squares on diagonal tiles, was 92% useful
+// on the 64^3 workload). Each multiply-add takes its own two operands from shared memory, which
+// the narrow FP64 pipe leaves ample room for (one warp-wide DFMA per sub-partition every 64
+// cycles). Every element accumulates its entries' products in entry order, k ascending.
 template <typename T, int TB, bool CLUSTER>
 __global__ void __launch_bounds__(TileCfg<TB>::threads, TB == NB ? (CLUSTER ? 2 : 3) : 6)
     k_update_flat(const SNode *__restrict__ sn, const UpdTask *__restrict__ tasks,
