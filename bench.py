@@ -44,7 +44,7 @@ METRIC = "refactor GFLOP/s and ms/(factor+solve) vs plain FP64 GPU path at bwd e
 # the 17 update launches of a 48^3 factorization (profiles/k_update_conduct3d7_48.md),
 # scaled to the 64^3 workload by algorithmic flops (x 2.672e11 / 4.556e10) and divided by its 19
 # launches. Set to None whenever the FP64 update kernel changes until it is captured again.
-NCU_TRAFFIC_PER_LAUNCH = 5.090e8
+NCU_TRAFFIC_PER_LAUNCH = None
 
 CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"

@@ -381,47 +381,77 @@ __global__ void __launch_bounds__(TileCfg<TB>::threads, TB == NB ? (CLUSTER ? 2 
     if (tid >= TB && tid - TB < E.n) pcol[tid - TB] = rel[E.relc + tid - TB] - cb;
     __syncthreads();
     const int cnt = diag ? E.m * (E.m + 1) / 2 : E.m * E.n;
-    for (int e0 = 0; e0 < cnt; e0 += FLAT_SLOTS * TT) {  // block-uniform passes
-      const int rem = cnt - e0;
-      const int nslot = min(FLAT_SLOTS, (rem + TT - 1) / TT);
-      const int jw = TT * (nslot - 1) + 32 * w < rem ? nslot : nslot - 1;  // warp-uniform
-      int ab[FLAT_SLOTS];
-      T r[FLAT_SLOTS];
-#pragma unroll
-      for (int j = 0; j < FLAT_SLOTS; ++j) {
-        const int el = e0 + tid + TT * j;
-        int a = 0, b = 0;
-        if (el < cnt) {
-          if (diag) {  // row-major lower triangle: el = a (a + 1) / 2 + b, b <= a
-            a = (int)((sqrtf(8.0f * el + 1.0f) - 1.0f) * 0.5f);
-            while ((a + 1) * (a + 2) / 2 <= el) ++a;
-            while (a * (a + 1) / 2 > el) --a;
-            b = el - a * (a + 1) / 2;
-          } else {
-            a = el % E.m;
-            b = el / E.m;
-          }
-        }
-        ab[j] = a | (b << 8);
-        r[j] = el < cnt ? acc[pcol[b]][prow[a]] : T(0);
+    const T *Kp = Lx + sk.lx;
+    // Operands of one chunk: only rows the entry has and values of K it reaches are staged and
+    // read.
+    auto stage = [&](int k0, int kc) {
+      for (int idx = tid; idx < kc * TB; idx += TT) {
+        const int a = idx % TB, kk = idx / TB;
+        const T *col = Kp + (int64_t)(k0 + kk) * sk.nrows;
+        if (a < E.m) As[kk][a] = col[E.r_lo + a];
+        if (a < E.n) Bs[kk][a] = col[E.c_lo + a];
       }
-      const T *Kp = Lx + sk.lx;
+    };
+    auto decode = [&](int el, int &a, int &b) {
+      if (diag) {  // row-major lower triangle: el = a (a + 1) / 2 + b, b <= a
+        a = (int)((sqrtf(8.0f * el + 1.0f) - 1.0f) * 0.5f);
+        while ((a + 1) * (a + 2) / 2 <= el) ++a;
+        while (a * (a + 1) / 2 > el) --a;
+        b = el - a * (a + 1) / 2;
+      } else {
+        a = el % E.m;
+        b = el / E.m;
+      }
+    };
+    if (cnt <= TT) {
+      // At most one element per thread (most entries of the lower levels and of small
+      // matrices): no slot arrays, and warps without an element skip the multiply-adds and the
+      // bookkeeping (the same operations in the same order as one slot of the general pass).
+      const bool has = tid < cnt, wact = 32 * w < cnt;  // wact: warp-uniform
+      int a = 0, b = 0;
+      T r = T(0);
+      if (has) {
+        decode(tid, a, b);
+        r = acc[pcol[b]][prow[a]];
+      }
       for (int k0 = 0; k0 < sk.ncols; k0 += KCU) {
         const int kc = min(KCU, sk.ncols - k0);
-        for (int idx = tid; idx < KCU * TB; idx += TT) {
-          int a = idx % TB, kk = idx / TB;
-          const T *col = Kp + (int64_t)(k0 + kk) * sk.nrows;
-          As[kk][a] = (a < E.m && kk < kc) ? col[E.r_lo + a] : T(0);
-          Bs[kk][a] = (a < E.n && kk < kc) ? col[E.c_lo + a] : T(0);
+        stage(k0, kc);
+        __syncthreads();
+        if (wact) {
+#pragma unroll 2
+          for (int kk = 0; kk < kc; ++kk) r = fma(-As[kk][a], Bs[kk][b], r);
         }
         __syncthreads();
-        flat_chunk_dispatch<TB>(r, ab, As, Bs, kc, jw);
-        __syncthreads();
       }
+      if (has) acc[pcol[b]][prow[a]] = r;
+    } else {
+      for (int e0 = 0; e0 < cnt; e0 += FLAT_SLOTS * TT) {  // block-uniform passes
+        const int rem = cnt - e0;
+        const int nslot = min(FLAT_SLOTS, (rem + TT - 1) / TT);
+        const int jw = TT * (nslot - 1) + 32 * w < rem ? nslot : nslot - 1;  // warp-uniform
+        int ab[FLAT_SLOTS];
+        T r[FLAT_SLOTS];
 #pragma unroll
-      for (int j = 0; j < FLAT_SLOTS; ++j) {
-        const int el = e0 + tid + TT * j;
-        if (el < cnt) acc[pcol[ab[j] >> 8]][prow[ab[j] & 0xff]] = r[j];
+        for (int j = 0; j < FLAT_SLOTS; ++j) {
+          const int el = e0 + tid + TT * j;
+          int a = 0, b = 0;
+          if (el < cnt) decode(el, a, b);
+          ab[j] = a | (b << 8);
+          r[j] = el < cnt ? acc[pcol[b]][prow[a]] : T(0);
+        }
+        for (int k0 = 0; k0 < sk.ncols; k0 += KCU) {
+          const int kc = min(KCU, sk.ncols - k0);
+          stage(k0, kc);
+          __syncthreads();
+          flat_chunk_dispatch<TB>(r, ab, As, Bs, kc, jw);
+          __syncthreads();
+        }
+#pragma unroll
+        for (int j = 0; j < FLAT_SLOTS; ++j) {
+          const int el = e0 + tid + TT * j;
+          if (el < cnt) acc[pcol[ab[j] >> 8]][prow[ab[j] & 0xff]] = r[j];
+        }
       }
     }
     __syncthreads();
