@@ -40,11 +40,11 @@ WORKLOADS = {
 WORKLOAD_DESC = WORKLOADS[WORKLOAD]
 NRHS = 4
 METRIC = "refactor GFLOP/s and ms/(factor+solve) vs plain FP64 GPU path at bwd err<=1e-12"
-# DRAM bytes per launch of the dominant kernel (k_update_flat) from an ncu capture: 1649.1 MB over
+# DRAM bytes per launch of the dominant kernel (k_update_flat) from an ncu capture: 1650.9 MB over
 # the 17 update launches of a 48^3 factorization (profiles/k_update_conduct3d7_48.md),
 # scaled to the 64^3 workload by algorithmic flops (x 2.672e11 / 4.556e10) and divided by its 19
 # launches. Set to None whenever the FP64 update kernel changes until it is captured again.
-NCU_TRAFFIC_PER_LAUNCH = None
+NCU_TRAFFIC_PER_LAUNCH = 5.096e8
 
 CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
