@@ -556,7 +556,7 @@ template <typename T, int TB>
 __global__ void __launch_bounds__(TileCfg<TB>::threads) k_trsm(const SNode *__restrict__ sn,
                                                                const Int4 *__restrict__ tasks,
                                                                T *__restrict__ Lx, int64_t toff, const Batch bt) {
-  constexpr int TT = TileCfg<TB>::threads, G = TT / NB;  // G column groups of NB rows
+  constexpr int TT = TileCfg<TB>::threads;
   Lx += blockIdx.y * bt.lx;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T(*Ls)[TB + 1] = reinterpret_cast<T(*)[TB + 1]>(smem_raw);                        // [col][row], lower
@@ -587,14 +587,18 @@ __global__ void __launch_bounds__(TileCfg<TB>::threads) k_trsm(const SNode *__re
   __syncthreads();
   if (tid < ts) dinv[tid] = T(1) / Ls[tid][tid];
   __syncthreads();
-  const int r = tid & (NB - 1), g = tid >> 6;  // thread owns row r, columns c+1+g, c+1+g+G, ...
+  // Thread (r, g) owns row r and columns c+1+g, c+1+g+GR, ...: the tile's rows are spread over
+  // GR = TT / tm column groups, so the threads of a warp are all busy whatever tm is (a warp-wide
+  // FP64 instruction costs its pipe slot however few lanes are active).
+  const int GR = tm > 0 ? TT / tm : 1;
+  const int r = tm > 0 ? tid % tm : 0, g = tm > 0 ? tid / tm : GR;  // g >= GR: idle
   for (int c = 0; c < ts; ++c) {
-    if (r < tm) {
+    if (g < GR) {
       const T xc = X[c][r] * dinv[c];  // X(r, c) is final once columns < c are applied
-      for (int cc = c + 1 + g; cc < ts; cc += G) X[cc][r] = fma(-xc, Ls[c][cc], X[cc][r]);
+      for (int cc = c + 1 + g; cc < ts; cc += GR) X[cc][r] = fma(-xc, Ls[c][cc], X[cc][r]);
     }
     __syncthreads();
-    if (g == 0 && r < tm) X[c][r] *= dinv[c];
+    if (g == 0) X[c][r] *= dinv[c];
   }
   __syncthreads();
   for (int idx = tid; idx < tm * ts; idx += TT) {
