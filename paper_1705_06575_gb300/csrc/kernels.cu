@@ -951,7 +951,7 @@ __global__ void __launch_bounds__(THREADS) k_bgather(const SNode *__restrict__ s
       if (rr < rc) zg[q][rr] = y[(int64_t)(r0 + q) * n + R[rc0 + rr]];
     }
     __syncthreads();
-    if (ca < tn) {
+    if (cb < tn) {  // both columns of the warp (warp-uniform branches)
 #pragma unroll 4
       for (int rr = lane; rr < rc; rr += 32) {
         const V la = (V)cola[rc0 + rr], lb = (V)colb[rc0 + rr];
@@ -961,6 +961,13 @@ __global__ void __launch_bounds__(THREADS) k_bgather(const SNode *__restrict__ s
           sa[q] = fma(la, z, sa[q]);
           sb[q] = fma(lb, z, sb[q]);
         }
+      }
+    } else if (ca < tn) {  // slices of at most 8 columns: no work for an absent second column
+#pragma unroll 4
+      for (int rr = lane; rr < rc; rr += 32) {
+        const V la = (V)cola[rc0 + rr];
+#pragma unroll
+        for (int q = 0; q < NR; ++q) sa[q] = fma(la, zg[q][rr], sa[q]);
       }
     }
     __syncthreads();
