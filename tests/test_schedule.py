@@ -423,3 +423,56 @@ def test_level_summary_of_the_profiling_driver():
     stream = raw[:, 3] >> 32
     if (stream == 1).any():
         assert out["two_stream_bound_ms"] < out["serialised_ms"]
+
+
+@pytest.mark.parametrize("maker", [
+    lambda: w.dd2d9(128, np.random.default_rng(2000)),                       # the batched pattern
+    lambda: w.laplace2d5(64, np.random.default_rng(0)),                      # the latency case
+    lambda: w.conduct3d(16, np.random.default_rng(6), "star"),
+    lambda: w.random_spd_pattern(300, 0.02, np.random.default_rng(7)),
+])
+def test_small_tile_launches_fit_their_kernels(maker):
+    """Launches marked for the small-tile kernels (tb = 32) hold only what those kernels handle:
+    diagonal tiles of order <= 32 for POTRF and TRTRI (one-warp forms keep a packed triangle of
+    order 32), TRSM tiles of <= 32 columns and <= 64 rows, update tiles of <= 32 rows and columns;
+    no trailing-GEMM launch is marked. Unmarked update tiles and TRSM row tiles stay within one
+    64 x 64 tile, and every update entry within the rows and columns of its tile (the tensor-core
+    update expands entries to tile positions 0..63)."""
+    M = maker()
+    s = S.Solver(M.n, M.Ap, M.Ai, M.perm, host_only=True)
+    sc = Sched(s)
+    small_seen = 0
+    for (kind, off, count, _, _), tb in zip(sc.launches["factor_launches"], sc.tb["factor_launches"]):
+        kind, off, count, tb = int(kind), int(off), int(count), int(tb)
+        assert tb in (0, 32)
+        if tb == 32:
+            small_seen += 1
+            assert kind != K_GEMM
+        for t in range(off, off + count):
+            if kind == K_UPDATE:
+                j, bi, bj, e0, e1 = (int(v) for v in sc.ut[t])
+                rs, cs = sc.tile(j, bi, bj)
+                tm, tn = rs.stop - rs.start, cs.stop - cs.start
+                assert 0 < tm <= NB and 0 < tn <= NB
+                if tb == 32:
+                    assert tm <= 32 and tn <= 32
+                for e in range(e0, e1):
+                    K, r_lo, c_lo, m, n, relr, relc = (int(v) for v in sc.ue[e])
+                    assert 0 < m <= tm and 0 < n <= tn
+                    pr = sc.rel[relr:relr + m] - sc.row_base(j, bi)
+                    pc = sc.rel[relc:relc + n] - bj * NB
+                    assert pr.min() >= 0 and pr.max() < tm and len(set(pr.tolist())) == m
+                    assert pc.min() >= 0 and pc.max() < tn and len(set(pc.tolist())) == n
+            elif kind in (K_POTRF, K_TRTRI, K_TRSM):
+                j, ti, tj, d = (int(v) for v in sc.tasks[t])
+                _, nc, _, _ = sc.J(j)
+                s_ = tj if kind == K_TRSM else ti
+                ts = min(NB, nc - s_ * NB)
+                assert 0 < ts <= NB
+                if kind == K_TRSM:
+                    tm = sc.row_len(j, ti)
+                    assert 0 < tm <= NB and (d >> 16) in (0, 1, 2)
+                if tb == 32:
+                    assert ts <= 32
+    if M.n >= 4096:
+        assert small_seen > 0  # the grids exercise the small-tile forms
