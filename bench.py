@@ -21,6 +21,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -482,8 +483,11 @@ def run_ours(args):
             import torch.distributed as dist
             dist.barrier()
 
-    clock_path = os.path.join(ROOT, "gpurun_out", f"bench_clocks_r{rank}.csv")
-    os.makedirs(os.path.dirname(clock_path), exist_ok=True)
+    # raw nvidia-smi samples of the timed region (summarised in the line's "clocks"); the
+    # directory can be chosen with SYM_BENCH_CLOCKS_DIR
+    clock_dir = os.environ.get("SYM_BENCH_CLOCKS_DIR", tempfile.gettempdir())
+    clock_path = os.path.join(clock_dir, f"bench_clocks_r{rank}.csv")
+    os.makedirs(clock_dir, exist_ok=True)
     sampler = start_clock_sampler(clock_path) if rank == 0 else None
     time.sleep(0.3 if sampler else 0)
     barrier()

@@ -202,7 +202,7 @@ def main(argv=None):
     ap.add_argument("--patterns", type=int, default=240)
     ap.add_argument("--holdout", type=float, default=0.2)
     ap.add_argument("--seed", type=int, default=5000)
-    ap.add_argument("--out", default="gpurun_out/costmodel")
+    ap.add_argument("--out", default="costmodel_out")
     args = ap.parse_args(argv)
     os.makedirs(args.out, exist_ok=True)
     t0 = time.time()
