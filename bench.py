@@ -41,15 +41,29 @@ WORKLOADS = {
 WORKLOAD_DESC = WORKLOADS[WORKLOAD]
 NRHS = 4
 METRIC = "refactor GFLOP/s and ms/(factor+solve) vs plain FP64 GPU path at bwd err<=1e-12"
-# DRAM bytes per launch of the dominant kernel (k_update_flat) from an ncu capture: 1650.9 MB over
-# the 17 update launches of a 48^3 factorization (profiles/k_update_conduct3d7_48.md),
-# scaled to the 64^3 workload by algorithmic flops (x 2.672e11 / 4.556e10) and divided by its 19
-# launches. Set to None whenever the FP64 update kernel changes until it is captured again.
-NCU_TRAFFIC_PER_LAUNCH = 5.096e8
+# DRAM traffic of the dominant kernel (the FP64 update, k_update_flat) per launch of the 64^3
+# step, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum averaged over the 19
+# update launches of one step). It holds only for the kernel source it was taken on: the
+# sha256 (first 16 hex digits) of the kernel's definition text in csrc/kernels.cu. When that
+# text changes, the line reports null until the traffic is captured again.
+UPDATE_TRAFFIC = {"bytes_per_launch": None, "kernel_sha16": None}
 
 CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def kernel_source_sha16(name="k_update_flat"):
+    """sha256 (16 hex digits) of the definition of a kernel template in csrc/kernels.cu: from the
+    template line before the kernel's name to the first closing brace at column 0."""
+    import hashlib
+    import re
+    src = open(os.path.join(ROOT, "paper_1705_06575_gb300", "csrc", "kernels.cu")).read()
+    m = re.search(r"\ntemplate <[^\n]*>\n[^\n]*\n\s*" + re.escape(name) + r"\(", src)
+    if not m:
+        return None
+    end = src.index("\n}\n", m.start())
+    return hashlib.sha256(src[m.start():end + 3].encode()).hexdigest()[:16]
 
 
 def dist_env():
@@ -150,7 +164,7 @@ def leading_block(o, target_flops):
 
 def oracle_sample(M, target_flops, repeats=1):
     """Time the CPU oracle (single thread) on the leading block of the matrix whose factor has
-    about target_flops flops. Returns (GFLOP/s, seconds per run, kmax, sample flops)."""
+    about target_flops flops. Returns (GFLOP/s, seconds per run, kmax, sample flops, oracle)."""
     import oracle
     o = oracle.Oracle(M.n, M.Ap, M.Ai, M.perm)
     kmax, fl = leading_block(o, target_flops)
@@ -161,12 +175,48 @@ def oracle_sample(M, target_flops, repeats=1):
         times.append(time.perf_counter() - t0)
         assert rc == 0
     t = float(np.median(times))
-    return fl / t / 1e9, t, kmax, fl
+    return fl / t / 1e9, t, kmax, fl, o
+
+
+def block_entry_error(o, kmax, sx, Lx):
+    """max |L_gpu - L_oracle| / max |L_oracle| over the entries of the leading kmax x kmax block,
+    which the oracle's up-looking factorization computed exactly. sx: the library's exports
+    (super, rowptr, rows, lxptr); Lx: its panels (widened to float64)."""
+    sup, rowptr, rows, lxptr = sx["super"], sx["rowptr"], sx["rows"], sx["lxptr"]
+    err = ref_max = 0.0
+    for J in range(sup.size - 1):
+        f, l = int(sup[J]), int(sup[J + 1])
+        if f >= kmax:
+            break
+        l2 = min(l, kmax)
+        R = rows[rowptr[J]:rowptr[J + 1]]
+        panel = Lx[lxptr[J]:lxptr[J + 1]].reshape(l - f, R.size)
+        lo, hi = int(o.Lp[f]), int(o.Lp[l2])
+        rr = o.Li[lo:hi]
+        cc = np.repeat(np.arange(l2 - f), np.diff(o.Lp[f:l2 + 1]))
+        keep = rr < kmax
+        got = panel[cc[keep], np.searchsorted(R, rr[keep])]
+        ref = o.Lx[lo:hi][keep]
+        if ref.size:
+            err = max(err, float(np.abs(got - ref).max()))
+            ref_max = max(ref_max, float(np.abs(ref).max()))
+    return err / ref_max if ref_max > 0 else 0.0
+
+
+def solver_exports(s):
+    return {k: s.export(k) for k in ("super", "rowptr", "rows", "lxptr")}
 
 
 def make_workload(name):
     import workloads as w
     return w.cfg(name)
+
+
+def line_config(M, workload, world):
+    """The config object of the line, identical for both arms."""
+    return {"workload": workload, "description": WORKLOADS[workload], "n": int(M.n), "nnz_a_lower": int(M.nnz),
+            "nrhs": NRHS, "parallelism": f"replicas x{world}",
+            "l2": "no flush: the factor's 1.57 GB working set exceeds the 129 MB L2"}
 
 
 def run_reference(args):
@@ -192,17 +242,39 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "description": WORKLOADS[args.workload], "sample_rows": kmax},
-            "cpu_baseline": {"value": val, "unit": "GFLOP/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "config": line_config(M, args.workload, world),
+            "cpu_baseline": {"value": val, "unit": "GFLOP/s", "cores": 1, "host_cores": os.cpu_count(),
+                             "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
-def bench_mixed(S, torch, M, B, flops, args, stream, barrier, world):
+def profile_kinds(S, s, fn, steps, names=None):
+    """Per-kind CUDA-event milliseconds of steps calls of fn, launched kernel by kernel."""
+    s.profile(S.SYM_PROFILE_RESET)
+    s.profile(S.SYM_PROFILE_ON)
+    for _ in range(steps):
+        fn()
+    import torch
+    torch.cuda.synchronize()
+    s.profile(S.SYM_PROFILE_OFF)
+    kinds = {}
+    for name, kid in S.KINDS.items():
+        if names and name not in names:
+            continue
+        kms, knl, kfl = s.profile_read(kid)
+        if knl:
+            kinds[name] = {"ms_per_step": kms / steps, "launches_per_step": knl / steps,
+                           "gflops_alg": kfl / kms / 1e6 if kms > 0 else None}
+    return kinds
+
+
+def bench_mixed(S, torch, M, B, flops, args, stream, barrier, world, ref=None):
     """The mixed-precision form on the same matrix and right-hand sides: FP32 factor + FP64
-    conjugate gradients preconditioned by it, to backward error
-    <= 1e-12 on every right-hand side. Timed like the main step (scatter + factor + solve)."""
+    conjugate gradients preconditioned by it, to backward error <= 1e-12 on every right-hand
+    side. Timed like the main step (scatter + factor + solve). ref = (oracle, kmax) gives the FP32
+    factor's entry-wise error against the oracle on the leading block it factored."""
     s = S.Solver(M.n, M.Ap, M.Ai, M.perm, precision="mixed")
     s.set_stream(stream)
     s.set_refinement(1e-12, 100)
@@ -227,36 +299,17 @@ def bench_mixed(S, torch, M, B, flops, args, stream, barrier, world):
     barrier()
     ms = e0.elapsed_time(e1) / args.steps
     ms, _ = dist_aggregate(ms, 0.0, world)
-    it, be_dev = s.refinement_info()
+    it, _ = s.refinement_info()
     X = Xt.cpu().numpy().T
     berr = backward_error(M, B, X)
-    # factor alone
-    torch.cuda.synchronize()
-    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    f0.record(stream)
-    for _ in range(args.steps):
-        s.factor(Ax)
-    f1.record(stream)
-    torch.cuda.synchronize()
-    ms_f = f0.elapsed_time(f1) / args.steps
-    # per-kernel breakdown of the FP32 factor (profiled pass, kernel by kernel)
-    s.profile(S.SYM_PROFILE_RESET)
-    s.profile(S.SYM_PROFILE_ON)
-    for _ in range(args.steps):
-        s.factor(Ax)
-    torch.cuda.synchronize()
-    s.profile(S.SYM_PROFILE_OFF)
-    kinds = {}
-    for name in ("scatter", "update", "potrf", "trsm", "gemm", "trtri"):
-        kms, knl, kfl = s.profile_read(S.KINDS[name])
-        if knl:
-            kinds[name] = {"ms_per_step": kms / args.steps, "gflops_alg": kfl / kms / 1e6 if kms > 0 else None}
+    ms_f = _event_ms(torch, stream, lambda: s.factor(Ax), args.steps)
+    kinds = profile_kinds(S, s, lambda: s.factor(Ax), args.steps,
+                          ("scatter", "update", "potrf", "trsm", "gemm", "trtri"))
+    out = {"ms": ms, "ms_factor": ms_f, "ms_solve": ms - ms_f, "it": it, "berr": berr}
+    if ref is not None:
+        out["factor_err_vs_oracle"] = block_entry_error(ref[0], ref[1], solver_exports(s), s.factor_panels())
     s.close()
-    return {"value": flops * world / (ms * 1e-3) / 1e9, "unit": "GFLOP/s", "ms_per_step": ms,
-            "ms_factor": ms_f, "ms_refined_solve": ms - ms_f, "refinement_iterations": it,
-            "factor_kernels": kinds,
-            "backward_error": berr, "dtype": "f32 factor + f64 refinement",
-            "definition": "same step as the main line; value = factor flops / step time"}
+    return out, kinds
 
 
 def bench_batched(S, torch, args, stream, barrier, world):
@@ -289,18 +342,7 @@ def bench_batched(S, torch, args, stream, barrier, world):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
     ms, _ = dist_aggregate(ms, 0.0, world)  # every rank factors its own batch: the slowest rank
-    # per-kernel breakdown of the batched step (profiled pass, kernel by kernel)
-    s.profile(S.SYM_PROFILE_RESET)
-    s.profile(S.SYM_PROFILE_ON)
-    for _ in range(args.steps):
-        step()
-    torch.cuda.synchronize()
-    s.profile(S.SYM_PROFILE_OFF)
-    kinds = {}
-    for name, kid in S.KINDS.items():
-        kms, knl, kfl = s.profile_read(kid)
-        if knl:
-            kinds[name] = {"ms_per_step": kms / args.steps, "launches_per_step": knl / args.steps}
+    kinds = profile_kinds(S, s, step, args.steps)
     Xh = X.cpu().numpy()
     worst = 0.0
     for b in (0, nb // 2, nb - 1):
@@ -324,10 +366,8 @@ def bench_batched(S, torch, args, stream, barrier, world):
     ms_seq = e0.elapsed_time(e1) / nseq * nb
     s.close()
     one.close()
-    return {"value": info.flops * nb * world / (ms * 1e-3) / 1e9, "unit": "GFLOP/s", "ms_per_step": ms,
-            "matrices": nb, "n": M.n, "nnz_l_per_matrix": info.nnz_l, "backward_error": worst,
-            "ms_sequential_calls": ms_seq, "speedup_vs_sequential": ms_seq / ms, "kernels": kinds, "dtype": "f64",
-            "definition": "512 x (factor + 1-RHS solve) of the 128^2 9-point pattern per step"}
+    return {"ms": ms, "gflops": info.flops * nb * world / (ms * 1e-3) / 1e9, "x_seq": ms_seq / ms,
+            "berr": worst}, kinds
 
 
 def _event_ms(torch, stream, fn, reps):
@@ -360,19 +400,21 @@ def bench_small_latency(S, torch, stream):
     us = 1e3 * _event_ms(torch, stream, lambda: (s.factor(Ax), S.sym_solve(s.h, b, x)), 50)
     berr = backward_error(M, b.cpu().numpy()[:, None], x.cpu().numpy()[:, None])
     s.close()
-    return {"us_per_step": us, "us_factor": us_f, "us_solve": us_s, "levels": info.nlevels,
-            "launches_per_step": int(info.nlaunch_factor + info.nlaunch_solve), "flops": info.flops,
-            "backward_error": berr, "definition": "64^2 5-point, FP64 factor + 1-RHS solve, CUDA graphs"}
+    return {"us": us, "us_factor": us_f, "us_solve": us_s, "levels": info.nlevels,
+            "launches": int(info.nlaunch_factor + info.nlaunch_solve), "berr": berr}
 
 
-def bench_uneven_batch(S, torch, stream):
+def bench_uneven_batch(S, torch, stream, precision="fp64"):
     """An uneven batch: 256 independent 5-point grids with sides uniform in 32..256, factored and
-    solved (one right-hand side) as one block-diagonal matrix with one plan."""
+    solved (one right-hand side) as one block-diagonal matrix with one plan, in FP64 or as the
+    mixed-precision form (FP32 factor, FP64 refinement to backward error <= 1e-12)."""
     import workloads as w
     mats, sides = w.uneven_grid_batch(256, np.random.default_rng(3000))
     U = w.block_diagonal(mats)
-    s = S.Solver(U.n, U.Ap, U.Ai, U.perm)
+    s = S.Solver(U.n, U.Ap, U.Ai, U.perm, precision=precision)
     s.set_stream(stream)
+    if precision == "mixed":
+        s.set_refinement(1e-12, 100)
     info = s.info()
     Ax = torch.from_numpy(U.Ax).cuda()
     b = torch.from_numpy(w.rhs(U.n, 1, np.random.default_rng(8))[:, 0].copy()).cuda()
@@ -380,9 +422,7 @@ def bench_uneven_batch(S, torch, stream):
     ms = _event_ms(torch, stream, lambda: (s.factor(Ax), S.sym_solve(s.h, b, x)), 5)
     berr = backward_error(U, b.cpu().numpy()[:, None], x.cpu().numpy()[:, None])
     s.close()
-    return {"value": info.flops / (ms * 1e-3) / 1e9, "unit": "GFLOP/s", "ms_per_step": ms, "matrices": 256,
-            "n": U.n, "nnz_l": info.nnz_l, "sides": [int(sides.min()), int(sides.max())], "backward_error": berr,
-            "dtype": "f64", "definition": "FP64 factor + 1-RHS solve of the block-diagonal union per step"}
+    return {"ms": ms, "gflops": info.flops / (ms * 1e-3) / 1e9, "berr": berr}
 
 
 def bench_mixed_vector(S, torch, stream):
@@ -397,7 +437,6 @@ def bench_mixed_vector(S, torch, stream):
     s = S.Solver(M.n, M.Ap, M.Ai, M.perm, precision="mixed")
     s.set_stream(stream)
     s.set_refinement(1e-12, 200)
-    info = s.info()
     ms_f = _event_ms(torch, stream, lambda: s.factor(Ax), 3)
     ms = _event_ms(torch, stream, lambda: (s.factor(Ax), S.sym_solve(s.h, b, x)), 3)
     it, _ = s.refinement_info()
@@ -407,11 +446,25 @@ def bench_mixed_vector(S, torch, stream):
     d.set_stream(stream)
     ms_f64 = _event_ms(torch, stream, lambda: d.factor(Ax), 1)
     d.close()
-    return {"value": info.flops / (ms * 1e-3) / 1e9, "unit": "GFLOP/s", "ms_per_step": ms, "ms_factor_fp32": ms_f,
-            "ms_refined_solve": ms - ms_f, "refinement_iterations": it, "backward_error": berr,
-            "ms_factor_fp64": ms_f64, "n": M.n, "nnz_l": info.nnz_l, "factor_flops": info.flops,
-            "dtype": "f32 factor + f64 refinement",
-            "definition": "FP32 factor + refined 1-RHS solve per step; value = factor flops / step time"}
+    return {"ms": ms, "ms_f32": ms_f, "ms_f64_factor": ms_f64, "it": it, "berr": berr}
+
+
+def bench_conduct27(S, torch, stream):
+    """The 27-point 40^3 conductivity matrix (n = 64,000; dense separators of up to ~2400
+    columns): FP64 factor + 4-RHS solve per step."""
+    import workloads as w
+    M = w.cfg("conduct3d27_40")
+    s = S.Solver(M.n, M.Ap, M.Ai, M.perm)
+    s.set_stream(stream)
+    info = s.info()
+    Ax = torch.from_numpy(M.Ax).cuda()
+    B = w.rhs(M.n, NRHS, np.random.default_rng(11))
+    Bt = torch.from_numpy(np.ascontiguousarray(B.T)).cuda()
+    Xt = torch.empty_like(Bt)
+    ms = _event_ms(torch, stream, lambda: (s.factor(Ax), S.sym_solve_multi(s.h, NRHS, Bt, M.n, Xt, M.n)), 10)
+    berr = backward_error(M, B, Xt.cpu().numpy().T)
+    s.close()
+    return {"ms": ms, "gflops": info.flops / (ms * 1e-3) / 1e9, "berr": berr}
 
 
 def bench_sparse_rhs(S, torch, s, M, args, stream):
@@ -420,27 +473,17 @@ def bench_sparse_rhs(S, torch, s, M, args, stream):
     against the same solve for a full b (every supernode visited, i.e. no pruning)."""
     rng = np.random.default_rng(77)
     j = M.n // 3
-    cases = {"column_of_A": M.Ai[M.Ap[j]:M.Ap[j + 1]].astype(np.int32),
-             "random_1pct": rng.choice(M.n, size=M.n // 100, replace=False).astype(np.int32),
+    cases = {"colA": M.Ai[M.Ap[j]:M.Ap[j + 1]].astype(np.int32),
+             "rand1pct": rng.choice(M.n, size=M.n // 100, replace=False).astype(np.int32),
              "full": np.arange(M.n, dtype=np.int32)}
     out = {}
     for name, bidx in cases.items():
         r = S.Reach(s.h, bidx)
         bv = torch.from_numpy(rng.standard_normal(bidx.size)).cuda()
         xv = torch.empty(r.size(), dtype=torch.float64, device="cuda")
-        for _ in range(args.warmup):
-            r.solve(bv, xv)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            r.solve(bv, xv)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        out[name] = {"nnz_b": int(bidx.size), "reach_columns": r.size(), "ms": e0.elapsed_time(e1) / args.steps}
+        out[name + "_ms"] = _event_ms(torch, stream, lambda: r.solve(bv, xv), args.steps)
+        out[name + "_reach"] = r.size()
         r.close()
-    for name in ("column_of_A", "random_1pct"):
-        out[name]["speedup_vs_full"] = out["full"]["ms"] / out[name]["ms"]
     return out
 
 
@@ -505,32 +548,31 @@ def run_ours(args):
     ms_step = ev0.elapsed_time(ev1) / args.steps
     # Per-kernel breakdown: the same K steps again, launched kernel by kernel with a CUDA event
     # after every launch on the launching stream (the timed steps above replay CUDA graphs).
-    s.profile(S.SYM_PROFILE_RESET)
-    s.profile(S.SYM_PROFILE_ON)
-    for _ in range(args.steps):
-        step()
-    torch.cuda.synchronize()
-    s.profile(S.SYM_PROFILE_OFF)
+    kinds = profile_kinds(S, s, step, args.steps)
     ms_step, total_flops = dist_aggregate(ms_step, info.flops, world)
     X = Xt.cpu().numpy().T
     berr = backward_error(M, B, X)
 
-    kinds = {}
-    for name, kid in S.KINDS.items():
-        ms, nl, fl = s.profile_read(kid)
-        if nl:
-            kinds[name] = {"ms_per_step": ms / args.steps, "launches_per_step": nl / args.steps,
-                           "gflops_alg": fl / ms / 1e6 if ms > 0 else None}
     factor_kinds = ("scatter", "update", "potrf", "trsm", "gemm", "trtri")
     ms_factor = sum(kinds[k]["ms_per_step"] for k in factor_kinds if k in kinds)
     ms_solve = sum(v["ms_per_step"] for k, v in kinds.items() if k not in factor_kinds)
     dom = max(kinds, key=lambda k: kinds[k]["ms_per_step"])
     dms, dnl, dfl = s.profile_read(S.KINDS[dom])
-    achieved_tf = dfl / dms / 1e9  # flops / ms -> TFLOP/s
+    peak_tf = peak64 / 1e3
+    exec_tf = dfl / dms / 1e9  # executed flops (explicit zeros of amalgamated panels included) / ms
+    # The method's useful work: for the update kernel the exact-pattern share of sum c_j^2
+    # (sym_stats.update_flops); other kernels have no such split and report executed flops.
+    useful = info.update_flops * args.steps if dom == "update" else dfl
+    achieved_tf = useful / dms / 1e9
     kname = {"update": "k_update_flat"}.get(dom, f"k_{dom}")  # the FP64 update kernel
-    roofline = {"bound": "alu", "kernel": kname, "achieved": achieved_tf, "peak": peak64 / 1e3,
-                "unit": "TFLOP/s", "frac": achieved_tf / (peak64 / 1e3),
-                "traffic": NCU_TRAFFIC_PER_LAUNCH if args.workload == WORKLOAD else None,
+    traffic = None
+    if (dom == "update" and args.workload == WORKLOAD and UPDATE_TRAFFIC["bytes_per_launch"] is not None
+            and UPDATE_TRAFFIC["kernel_sha16"] == kernel_source_sha16("k_update_flat")):
+        traffic = UPDATE_TRAFFIC["bytes_per_launch"]
+    roofline = {"bound": "alu", "kernel": kname, "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
+                "frac": achieved_tf / peak_tf, "frac_executed": exec_tf / peak_tf,
+                "flops": "useful (exact pattern, no amalgamation zeros); frac_executed counts executed flops",
+                "traffic": traffic, "launches_per_step": dnl / args.steps,
                 "peak_source": "FP64 FMA peak measured live by sym_fma_peak (152 SMs x 2 DFMA/clk)",
                 "share_of_step": dms / args.steps / ms_step,
                 "timing": "kernel time from CUDA events in a profiled pass of the same K steps"}
@@ -557,49 +599,69 @@ def run_ours(args):
     t_e2e, _ = dist_aggregate(t_e2e, 0.0, world)
     berr_e2e = backward_error(M, B, X_h.numpy().T)
 
-    variants = {}
+    cpu = None
+    ref = None
+    factor_vs_oracle = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        g, t, kmax, fl, o = oracle_sample(M, args.cpu_flops)
+        cpu = {"value": g, "unit": "GFLOP/s", "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
+               "sample": (f"up-looking FP64 oracle factor of the leading {kmax} x {kmax} block of the "
+                          f"workload matrix ({fl:.3g} flops, {t:.1f} s), single thread")}
+        ref = (o, kmax)
+        s.factor(Ax)
+        torch.cuda.synchronize()
+        factor_vs_oracle = {"block": kmax,
+                            "fp64": block_entry_error(o, kmax, solver_exports(s), s.factor_panels())}
+
+    variants, detail = {}, {"kernels": kinds}
     if not args.no_variants:
-        variants["sparse_rhs_forward"] = bench_sparse_rhs(S, torch, s, M, args, stream)
-        variants["mixed_fp32_pcg"] = bench_mixed(S, torch, M, B, info.flops, args, stream, barrier, world)
+        variants["mixed_64"], detail["mixed_64_factor_kernels"] = bench_mixed(
+            S, torch, M, B, info.flops, args, stream, barrier, world, ref)
+        variants["mixed_64"]["x_vs_fp64"] = ms_step / variants["mixed_64"]["ms"]
+        if factor_vs_oracle is not None and "factor_err_vs_oracle" in variants["mixed_64"]:
+            factor_vs_oracle["fp32_mixed"] = variants["mixed_64"].pop("factor_err_vs_oracle")
         if args.batch > 0:
-            variants["batched_512x_dd2d9_128"] = bench_batched(S, torch, args, stream, barrier, world)
-        for key, fn in (("latency_laplace2d5_64", bench_small_latency), ("uneven_batch_256_grids", bench_uneven_batch),
-                        ("mixed_vector3d27_48", bench_mixed_vector)):
+            variants["batch_512x128sq"], detail["batch_kernels"] = bench_batched(S, torch, args, stream, barrier,
+                                                                                 world)
+        variants["sparse_rhs"] = bench_sparse_rhs(S, torch, s, M, args, stream)
+        for key, fn in (("lat_64sq", bench_small_latency), ("uneven_256", bench_uneven_batch),
+                        ("uneven_256_mixed", lambda S_, t_, st_: bench_uneven_batch(S_, t_, st_, "mixed")),
+                        ("c27_40", bench_conduct27), ("vec48_mixed", bench_mixed_vector)):
             try:
                 variants[key] = fn(S, torch, stream)
             except S.SymError as e:  # a library error is reported, not fatal to the main line
                 variants[key] = {"error": str(e)}
     clocks = read_clocks(clock_path, local) if rank == 0 else None
-    flops = info.flops
     value = total_flops / (ms_step * 1e-3) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "description": WORKLOADS[args.workload], "n": M.n, "nnz_a_lower": M.nnz,
-                   "nnz_l": info.nnz_l, "factor_flops": flops, "nrhs": NRHS, "supernodes": info.nsuper,
-                   "levels": info.nlevels, "parallelism": f"replicas x{world}",
-                   "l2": "no flush: the factor's 1.57 GB working set exceeds the 129 MB L2"},
-        "value_definition": "factor flops / (factor + solve) time per step",
-        "ms_factor": ms_factor, "ms_solve": ms_solve,
-        "factor_gflops": flops / (ms_factor * 1e-3) / 1e9,
-        "factor_frac_of_fp64_peak": flops / (ms_factor * 1e-3) / 1e9 / peak64,
-        "analyze_s": analyze_s, "backward_error": berr, "backward_error_e2e": berr_e2e,
-        "kernels": kinds,
-        "roofline": roofline,
-        "e2e": {"value": total_flops / t_e2e / 1e9, "unit": "GFLOP/s", "ms_per_step": t_e2e * 1e3,
-                "h2d_bytes_per_step": 8 * (M.nnz + M.n * NRHS), "d2h_bytes_per_step": 8 * M.n * NRHS},
+        "config": line_config(M, args.workload, world),
         "gpu_launches": int(args.steps * (info.nlaunch_factor + info.nlaunch_solve)),
         "clocks": clocks,
-        "variants": variants,
+        "e2e": {"value": total_flops / t_e2e / 1e9, "unit": "GFLOP/s", "ms_per_step": t_e2e * 1e3,
+                "h2d_bytes_per_step": 8 * (M.nnz + M.n * NRHS), "d2h_bytes_per_step": 8 * M.n * NRHS},
+        "roofline": roofline,
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        g, t, kmax, fl = oracle_sample(M, args.cpu_flops)
-        line["cpu_baseline"] = {
-            "value": g, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
-            "sample": (f"up-looking FP64 oracle factor of the leading {kmax} x {kmax} block of the "
-                       f"workload matrix ({fl:.3g} flops, {t:.1f} s), single thread")}
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    line.update({
+        "ms_factor": ms_factor, "ms_solve": ms_solve, "analyze_s": analyze_s,
+        "backward_error": berr, "backward_error_e2e": berr_e2e, "factor_vs_oracle": factor_vs_oracle,
+        "workload_stats": {"nnz_l": info.nnz_l, "factor_flops": info.flops, "update_flops": info.update_flops,
+                           "exec_flops": info.exec_flops, "supernodes": info.nsuper, "levels": info.nlevels},
+        "value_definition": "factor flops (sum c_j^2) / (factor + solve) time per step",
+        "variants_note": "ms per step of each variant (definitions in bench.py); per-kernel times on stderr",
+        "variants": variants,
+    })
     if rank == 0:
+        detail_dir = os.environ.get("SYM_BENCH_DETAIL_DIR", tempfile.gettempdir())
+        os.makedirs(detail_dir, exist_ok=True)
+        with open(os.path.join(detail_dir, "bench_detail.json"), "w") as f:
+            json.dump(detail, f, indent=1)
+        print(json.dumps({"per_kernel_ms": {k: round(v["ms_per_step"], 3) for k, v in kinds.items()}}),
+              file=sys.stderr, flush=True)
         print(json.dumps(line), flush=True)
     s.close()
     if world > 1:

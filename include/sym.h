@@ -102,6 +102,9 @@ typedef struct {
   int64_t upd_entries;      /* (tile, descendant) update entries */
   int64_t dense_tasks;      /* POTRF + TRSM + GEMM + inverse tile tasks */
   double exec_flops;        /* factor flops the kernels execute (explicit zeros included) */
+  double update_flops;      /* the part of `flops` that descendant updates (SYM_KIND_UPDATE)
+                               carry: column k updates column j in another supernode with
+                               2 |{i in L_k : i >= j}| flops, summed over the exact pattern */
 } sym_stats;
 
 /* Fill *opt with the defaults (SYM_ORDER_GIVEN with a NULL perm means natural order). */
@@ -193,7 +196,10 @@ int sym_solve_multi(sym_handle h, int32_t nrhs, const double *B, int64_t ldb, do
  *     overlaps on the GPU race and give wrong results, so serialize them (one stream, or events);
  *   - the array keeps the previous call's contents; the solve overwrites every element it reads,
  *     so no clearing is needed;
- *   - sym_profile does not time this entry point.
+ *   - sym_profile does not time this entry point;
+ *   - it needs an FP64 factor: a SYM_PREC_MIXED handle (whose solve refines in FP64 and needs
+ *     more work memory) returns SYM_ERR_STATE, as does a call before a successful factorization
+ *     or with another device current; these checks come before the array's address is looked up.
  * Other arguments, errors and results as sym_solve_multi (DEVICE pointers). */
 #define SYM_NOALLOC_MAX_WORK 1048576
 int sym_solve_multi_noalloc(sym_handle h, int32_t nrhs, const double *B, int64_t ldb, double *X,

@@ -19,7 +19,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "_build", "liborc.so")
 _lock = threading.Lock()
-_lib = None
+_libs = {}
 
 # Amalgamation parameters: nrelax0..2 (column counts), zrelax0..2 (zero fraction, per mille).
 DEFAULT_RELAX = (4, 16, 48, 800, 100, 50)
@@ -28,24 +28,27 @@ ERR_INVALID = -1
 ERR_NOT_SPD = -2
 
 
-def build(force=False):
-    """Compile the oracle with gcc (no CUDA involved)."""
-    os.makedirs(os.path.dirname(_SO), exist_ok=True)
+def build(force=False, defines=()):
+    """Compile the oracle with gcc (no CUDA involved). ``defines`` builds a separate copy with
+    those preprocessor symbols (the planted-mistake copies the pin tests use)."""
+    so = _SO if not defines else os.path.join(_HERE, "_build", "liborc_" + "_".join(defines).lower() + ".so")
+    os.makedirs(os.path.dirname(so), exist_ok=True)
     src = os.path.join(_HERE, "sym_oracle.c")
-    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(src):
-        return _SO
-    tmp = _SO + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, src, "-lm"])
-    os.replace(tmp, _SO)
-    return _SO
+    if not force and os.path.exists(so) and os.path.getmtime(so) >= os.path.getmtime(src):
+        return so
+    tmp = so + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC"] + [f"-D{d}" for d in defines] +
+                          ["-o", tmp, src, "-lm"])
+    os.replace(tmp, so)
+    return so
 
 
-def _load():
-    global _lib
+def _load(defines=()):
+    key = tuple(defines)
     with _lock:
-        if _lib is not None:
-            return _lib
-        lib = ct.CDLL(build())
+        if key in _libs:
+            return _libs[key]
+        lib = ct.CDLL(build(defines=key))
         P = ct.c_void_p
         i64, i32 = ct.c_int64, ct.c_int32
         lib.orc_validate.argtypes = [i64, P, P]
@@ -70,17 +73,17 @@ def _load():
         lib.orc_row_patterns_check.argtypes = [P]
         lib.orc_row_patterns_check.restype = ct.c_int
         for name, rt in [("n", i64), ("nnzL", i64), ("nfsn", i32), ("nsn", i32), ("nsrows", i64),
-                         ("npairs", i64), ("nrel", i64), ("nlev", i32), ("err_col", i64)]:
+                         ("npairs", i64), ("nrel", i64), ("nlev", i32), ("err_col", i64), ("nmerge", i64)]:
             f = getattr(lib, "orc_" + name)
             f.argtypes = [P]
             f.restype = rt
         for name in ["perm", "parent", "Lp", "Li", "Lx", "Cp", "Ci", "Cmap", "fsn", "sn", "srp",
                      "sri", "sparent", "dp", "dk", "dr0", "dnin", "relp", "rel", "level", "lvp",
-                     "lvl"]:
+                     "lvl", "merges"]:
             f = getattr(lib, "orc_" + name)
             f.argtypes = [P]
             f.restype = P
-        _lib = lib
+        _libs[key] = lib
         return lib
 
 
@@ -105,8 +108,8 @@ def validate(n, Ap, Ai):
 class Oracle:
     """Symbolic analysis (every integer output of the inspector) plus the numeric factor."""
 
-    def __init__(self, n, Ap, Ai, perm0=None, relax=DEFAULT_RELAX, want_rel=False):
-        lib = _load()
+    def __init__(self, n, Ap, Ai, perm0=None, relax=DEFAULT_RELAX, want_rel=False, defines=()):
+        lib = _load(defines)
         self._lib = lib
         self.n = int(n)
         self.Ap = np.ascontiguousarray(Ap, dtype=np.int64)
@@ -154,6 +157,9 @@ class Oracle:
         self.nlev = nl
         self.lvp = _view(lib.orc_lvp(h), nl + 1, np.int32)
         self.lvl = _view(lib.orc_lvl(h), ns, np.int32)
+        # amalgamation log: (first column of the absorbed supernode, first column of the one it
+        # merged into, at the time of the merge), in the order the merges were made
+        self.merges = _view(lib.orc_merges(h), 2 * lib.orc_nmerge(h), np.int32).reshape(-1, 2)
         self.flops = int(np.sum(self.colcount.astype(np.float64) ** 2))
         self.flops_exact = int(np.sum(self.colcount.astype(np.int64) ** 2))
         self.Lx = None

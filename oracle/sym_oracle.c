@@ -25,6 +25,10 @@
  *     sweep with L^T is the textbook one, the paper does not describe it);
  *   - checks: ||L L^T - C||_F / ||C||_F and the normwise backward error of a solve.
  *
+ * The amalgamation keeps a log of its merges (which supernode was absorbed into which, in
+ * order), so that a test can replay them and re-derive each merge's zero count from the dense
+ * filled pattern.
+ *
  * Where the paper is silent the oracle follows these readings:
  *   - postorder of the etree: children in increasing index order, roots in increasing order;
  *   - a non-positive or NaN pivot stops the factorization and reports the column;
@@ -73,6 +77,10 @@ typedef struct {
   int32_t *level;   /* per supernode */
   int32_t nlev;
   int32_t *lvp, *lvl; /* level pointers (nlev+1) and supernodes by level, ascending */
+  /* amalgamation log: merge t absorbed the supernode starting at column merges[2t] into the
+   * next one, which started at column merges[2t+1] when the merge was made */
+  int64_t nmerge;
+  int32_t *merges;
   /* numeric factor on the pattern Lp/Li */
   double *Lx;
   int64_t err_col;
@@ -242,6 +250,7 @@ void orc_free(orc_t *o) {
   free(o->parent); free(o->Lp); free(o->Li); free(o->fsn); free(o->sn); free(o->srp);
   free(o->sri); free(o->sparent); free(o->dp); free(o->dk); free(o->dr0); free(o->dnin);
   free(o->relp); free(o->rel); free(o->level); free(o->lvp); free(o->lvl); free(o->Lx);
+  free(o->merges);
   free(o);
 }
 
@@ -336,6 +345,9 @@ int orc_analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *
     nrows[s] = len;
   }
   int32_t head = 0;
+  /* at most ns - 1 merges: each one removes a supernode */
+  o->merges = xcalloc(2 * (size_t)(ns > 0 ? ns : 1), sizeof(int32_t));
+  o->nmerge = 0;
   if (relax) {
     int changed = 1;
     while (changed) {
@@ -349,10 +361,25 @@ int orc_analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *
           int64_t nc = (int64_t)last[P] - first[i] + 1;
           int64_t total = nc * m - nc * (nc - 1) / 2;
           int64_t z = total - (truennz[i] + truennz[P]);
+#if defined(ORC_PLANT_DROP_Z_CLAUSE)
+          /* deliberately wrong rules, compiled only into the copies the tests use to show that
+           * the amalgamation pin catches over-merging: the zero-fraction clause of the third
+           * size class dropped, or || written for && in the second */
+          int accept = nc <= relax[0] || (nc <= relax[1] && z * 1000 <= (int64_t)relax[3] * total) ||
+                       nc <= relax[2] || z * 1000 <= (int64_t)relax[5] * total;
+#elif defined(ORC_PLANT_OR_FOR_AND)
+          int accept = nc <= relax[0] || (nc <= relax[1] || z * 1000 <= (int64_t)relax[3] * total) ||
+                       (nc <= relax[2] && z * 1000 <= (int64_t)relax[4] * total) ||
+                       z * 1000 <= (int64_t)relax[5] * total;
+#else
           int accept = nc <= relax[0] || (nc <= relax[1] && z * 1000 <= (int64_t)relax[3] * total) ||
                        (nc <= relax[2] && z * 1000 <= (int64_t)relax[4] * total) ||
                        z * 1000 <= (int64_t)relax[5] * total;
+#endif
           if (accept) {
+            o->merges[2 * o->nmerge] = first[i];
+            o->merges[2 * o->nmerge + 1] = first[P];
+            o->nmerge++;
             free(rows[P]);
             rows[P] = xcalloc(m, sizeof(int32_t));
             memcpy(rows[P], tmp, sizeof(int32_t) * m);
@@ -770,6 +797,8 @@ int64_t orc_nsrows(const orc_t *o) { return o->srp[o->nsn]; }
 int64_t orc_npairs(const orc_t *o) { return o->dp[o->nsn]; }
 int64_t orc_nrel(const orc_t *o) { return o->rel ? o->relp[o->dp[o->nsn]] : 0; }
 int32_t orc_nlev(const orc_t *o) { return o->nlev; }
+int64_t orc_nmerge(const orc_t *o) { return o->nmerge; }
+const int32_t *orc_merges(const orc_t *o) { return o->merges; }
 int64_t orc_err_col(const orc_t *o) { return o->err_col; }
 const int32_t *orc_perm(const orc_t *o) { return o->perm; }
 const int32_t *orc_parent(const orc_t *o) { return o->parent; }

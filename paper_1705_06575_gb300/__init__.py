@@ -76,7 +76,7 @@ class sym_stats(ct.Structure):
                 ("max_ncols", ct.c_int32), ("npairs", ct.c_int64), ("nlaunch_factor", ct.c_int64),
                 ("nlaunch_solve", ct.c_int64), ("analyze_seconds", ct.c_double),
                 ("device_bytes", ct.c_int64), ("upd_tasks", ct.c_int64), ("upd_entries", ct.c_int64),
-                ("dense_tasks", ct.c_int64), ("exec_flops", ct.c_double)]
+                ("dense_tasks", ct.c_int64), ("exec_flops", ct.c_double), ("update_flops", ct.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

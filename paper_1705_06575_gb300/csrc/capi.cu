@@ -747,14 +747,22 @@ int sym_solve_multi(sym_handle h, int32_t nrhs, const double *B, int64_t ldb, do
 }  // extern "C"
 
 namespace sym {
-// Solve with a work array supplied by the caller (at least n * nrhs doubles); performs no
-// allocation and records no profile events.
-int solve_with_work(sym_handle h, int32_t nrhs, const double *B, int64_t ldb, double *X, int64_t ldx,
-                    double *work) {
+// What a solve with a caller-supplied work array needs of the handle: a device handle whose
+// device is current, a successful factorization, and an FP64 factor.
+int check_solve_ready(sym_handle h) {
   int rc = check_device(h);
   if (rc) return rc;
   if (!h->factored) return fail(SYM_ERR_STATE, "no successful factorization to solve with");
   if (h->precision != SYM_PREC_FP64) return fail(SYM_ERR_STATE, "this entry point needs an FP64 factor");
+  return SYM_OK;
+}
+
+// Solve with a work array supplied by the caller (at least n * nrhs doubles); performs no
+// allocation and records no profile events.
+int solve_with_work(sym_handle h, int32_t nrhs, const double *B, int64_t ldb, double *X, int64_t ldx,
+                    double *work) {
+  int rc = check_solve_ready(h);
+  if (rc) return rc;
   if (!h->solve_prepared) {
     CUDA_TRY((sym::prepare_solve<double, double>()), "solve set-up");
     h->solve_prepared = true;
@@ -824,6 +832,7 @@ int sym_info(sym_handle h, sym_stats *s) {
   s->dense_tasks = dense;
   s->exec_flops = 0.0;
   for (int k = sym::K_SCATTER; k <= sym::K_TRTRI; ++k) s->exec_flops += P.kind_flops[k];
+  s->update_flops = P.update_flops;
   return SYM_OK;
 }
 

@@ -13,6 +13,7 @@
 #include "sym.h"
 
 namespace sym {
+int check_solve_ready(sym_handle h);
 int solve_with_work(sym_handle h, int32_t nrhs, const double *B, int64_t ldb, double *X, int64_t ldx,
                     double *work);
 int set_error(int code, const char *msg);
@@ -56,8 +57,12 @@ extern "C" int sym_solve_multi_noalloc(sym_handle h, int32_t nrhs, const double 
   if (nrhs < 0) return sym::set_error(SYM_ERR_INVALID, "bad solve arguments");
   if (n * (int64_t)nrhs > (int64_t)SYM_NOALLOC_MAX_WORK)
     return sym::set_error(SYM_ERR_LIMIT, "sym_solve_multi_noalloc: n * nrhs exceeds SYM_NOALLOC_MAX_WORK");
+  // the handle and its device are checked before the array's address is looked up, so a call
+  // refused for a wrong current device does not touch that device
+  int rc = sym::check_solve_ready(h);
+  if (rc) return rc;
   double *work = nullptr;
-  int rc = work_address(&work);
+  rc = work_address(&work);
   if (rc) return rc;
   return sym::solve_with_work(h, nrhs, B, ldb, X, ldx, work);
 }

@@ -167,6 +167,9 @@ struct Plan {
   // useful multiply-adds (x2), square roots and divisions, excluding the strict upper part of
   // diagonal tiles; explicit zeros of amalgamated panels are included.
   double kind_flops[NUM_KINDS] = {};
+  // Useful flops of the external updates (K_UPDATE) on the exact pattern of L: the share of the
+  // factor's sum of c_j^2 that descendant updates carry (no explicit zeros of amalgamation).
+  double update_flops = 0.0;
 
   int32_t nsuper() const { return (int32_t)super.size() - 1; }
   int64_t storage() const { return lxptr.empty() ? 0 : lxptr.back(); }

@@ -242,6 +242,12 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
       std::sort(R.begin() + (l - f + 1), R.end());
     }
   }
+  // The exact pattern of column k of fundamental supernode F is the suffix of rows(F) from k;
+  // keep the rows below each F to split the useful flops by kernel once the final supernodes
+  // are known.
+  std::vector<std::vector<int32_t>> fbelow(nf);
+  for (int32_t s = 0; s < nf; ++s)
+    fbelow[s].assign(srows[s].begin() + (P.fsuper[s + 1] - P.fsuper[s]), srows[s].end());
   // 6. Relaxed amalgamation (this library's rule; the paper runs without it, Sec. 4.1).
   std::vector<int64_t> ccum(n + 1, 0);
   for (int64_t j = 0; j < n; ++j) ccum[j + 1] = ccum[j] + P.colcount[j];
@@ -308,6 +314,19 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
     int32_t pl = P.parent[P.super[J + 1] - 1];
     P.sparent[J] = pl < 0 ? -1 : col2s[pl];
   }
+  // Useful flops of the external updates: column k of F (pattern rows(F) from k, c_k entries)
+  // updates column j = its t-th row with the c_k - t entries at or below j, 2 (c_k - t) flops;
+  // for a row at position q of rows(F) this is 2 (|rows(F)| - q) for each of F's columns, and
+  // it is an external update when j lies in another final supernode.
+  P.update_flops = 0.0;
+  for (int32_t s = 0; s < nf; ++s) {
+    const int64_t nc = P.fsuper[s + 1] - P.fsuper[s];
+    const int64_t m = nc + (int64_t)fbelow[s].size();
+    const int32_t home = col2s[P.fsuper[s]];
+    for (size_t t = 0; t < fbelow[s].size(); ++t)
+      if (col2s[fbelow[s][t]] != home) P.update_flops += 2.0 * (double)(m - (nc + (int64_t)t)) * (double)nc;
+  }
+  std::vector<std::vector<int32_t>>().swap(fbelow);
   // 7. Descendant lists: every K whose rows reach into the columns of J (the block-level
   //    prune-set), with the first row position r0 at or after first(J) and the count nin of
   //    K's rows inside cols(J). Scanning K in increasing order keeps each list sorted.

@@ -241,10 +241,13 @@ def test_lookahead_matches_one_stream_bit_for_bit(torch_cuda):
     check_matrix(torch, M, nrhs=1)
 
 
-def test_conduct3d27_40_sampled(torch_cuda):
-    """27-point 40^3 (dense separators up to ~2400 columns): leading 12000 columns entry-wise,
-    the full solve by backward error."""
-    check_matrix(torch_cuda, w.cfg("conduct3d27_40"), nrhs=1, kmax=12000, solve_oracle=False)
+def test_conduct3d27_40_full(torch_cuda):
+    """27-point 40^3 (n = 64,000; dense separator supernodes up to ~2400 columns, where the
+    lookahead chain, the row-half split and the cluster updates run at full size): the whole
+    factor entry-wise against the oracle's complete up-looking factorization (2.6e10 flops),
+    the full factor residual, and the solve by backward error and against the oracle's x."""
+    r = check_matrix(torch_cuda, w.cfg("conduct3d27_40"), nrhs=2)
+    assert r["x_vs_oracle"] < 1e-10, r
 
 
 def test_conduct3d7_64_full_size(torch_cuda):

@@ -212,3 +212,26 @@ def test_update_entries_against_their_definition(maker):
             assert set(RK[c_lo:c_lo + n].tolist()) == tile_cols & set(RK.tolist())
             if bi == bj:
                 assert m == n and r_lo == c_lo
+
+
+@pytest.mark.parametrize("maker", [lambda r: w.laplace2d5(20, r), lambda r: w.conduct3d(8, r, "box"),
+                                   lambda r: w.random_spd_pattern(300, 0.02, r)])
+def test_update_flops_split_of_sum_c_squared(maker):
+    """sym_stats.update_flops is the share of sum c_j^2 that descendant updates carry: counted
+    here entry by entry on the oracle's exact column patterns (column k adds 2 (c_k - t) flops to
+    the column of its t-th row when that column lies in another supernode)."""
+    M = maker(np.random.default_rng(23))
+    s = S.Solver(M.n, M.Ap, M.Ai, M.perm, flags=S.SYM_FLAG_HOST_ONLY)
+    info = s.info()
+    sup = s.export("super")
+    o = oracle.Oracle(M.n, M.Ap, M.Ai, s.export("perm"))
+    col2s = np.repeat(np.arange(sup.size - 1), np.diff(sup))
+    total = 0
+    for k in range(M.n):
+        rows = o.Li[o.Lp[k]:o.Lp[k + 1]]
+        c = rows.size
+        t = np.arange(1, c)
+        ext = col2s[rows[1:]] != col2s[k]
+        total += int(np.sum(2 * (c - t)[ext]))
+    assert info.update_flops == total
+    assert info.update_flops < info.flops == o.flops_exact

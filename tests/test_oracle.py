@@ -300,6 +300,125 @@ def test_amalgamation_rule_brute_force():
             assert not ok, (J, nc, z, total)
 
 
+def _rule(relax, nc, z, total):
+    """The amalgamation rule as stated in the library's interface (sym_options)."""
+    return (nc <= relax[0] or (nc <= relax[1] and z * 1000 <= relax[3] * total) or
+            (nc <= relax[2] and z * 1000 <= relax[4] * total) or z * 1000 <= relax[5] * total)
+
+
+def _replay_merges(o, P, relax):
+    """Apply the oracle's logged merges to its fundamental supernodes in log order. For each
+    merge, check that the two supernodes are adjacent and eligible (the absorbed one's last
+    column has the other's first column as etree parent), and re-derive from the dense filled
+    pattern P the merged column count, the trapezoid size and its explicit zeros. Returns the
+    merges the rule does not accept and the partition the replay ends with."""
+    n = o.n
+    starts = [int(x) for x in o.fsn[:-1]]
+    rejected = []
+    for fS, fP in o.merges.tolist():
+        i = starts.index(fS)
+        assert i + 1 < len(starts) and starts[i + 1] == fP, "merge of non-adjacent supernodes"
+        assert o.parent[fP - 1] == fP, "merge of a supernode whose last column's parent is elsewhere"
+        end = starts[i + 2] if i + 2 < len(starts) else n
+        rows = np.nonzero(P[:, fS:end].any(1))[0]
+        nc = end - fS
+        total = _storage(rows.size, nc)
+        z = total - int(P[:, fS:end].sum())
+        if not _rule(relax, nc, z, total):
+            rejected.append((fS, fP, nc, z, total))
+        del starts[i + 1]
+    return rejected, starts + [n]
+
+
+def _amalgamation_cases():
+    rng = np.random.default_rng(53)
+    cases = []
+    for trial in range(6):
+        M = w.random_spd_pattern(70, 0.03 + 0.015 * trial, rng)
+        cases.append((M, rng.permutation(70).astype(np.int32)))
+    for side in (9, 13):
+        M = w.laplace2d5(side, rng)
+        cases.append((M, M.perm))
+    M = w.conduct3d(6, rng, "box")
+    cases.append((M, M.perm))
+    return cases
+
+
+def test_amalgamation_merges_replay():
+    """Accept side of the amalgamation rule: every merge the oracle made, replayed from the
+    fundamental supernodes in its order, is one the rule accepts on the zero counts of the dense
+    filled pattern (brute-force elimination), and the replay ends at the oracle's partition.
+    With the fixed-point test below (reject side), a wrong merge in either direction fails."""
+    relax = oracle.DEFAULT_RELAX
+    total_merges = 0
+    for M, perm in _amalgamation_cases():
+        o = oracle.Oracle(M.n, M.Ap, M.Ai, perm, relax=relax)
+        P = brute_fill(permuted_dense(M, o.perm))
+        assert np.array_equal(P, oracle_pattern(o))
+        rejected, part = _replay_merges(o, P, relax)
+        assert rejected == []
+        assert np.array_equal(np.array(part), o.sn)
+        total_merges += len(o.merges)
+    assert total_merges > 50  # the cases exercise the rule, not just fundamental supernodes
+
+
+@pytest.mark.parametrize("plant", ["ORC_PLANT_DROP_Z_CLAUSE", "ORC_PLANT_OR_FOR_AND"])
+def test_amalgamation_planted_over_merge_is_caught(plant):
+    """Copies of the oracle compiled with a wrong rule (a zero-fraction clause dropped, or || for
+    &&) make merges that the replay flags."""
+    relax = oracle.DEFAULT_RELAX
+    caught = 0
+    for M, perm in _amalgamation_cases():
+        o = oracle.Oracle(M.n, M.Ap, M.Ai, perm, relax=relax, defines=(plant,))
+        P = brute_fill(permuted_dense(M, o.perm))
+        rejected, _ = _replay_merges(o, P, relax)
+        caught += len(rejected)
+    assert caught > 0
+
+
+def test_amalgamation_limits():
+    """Closed forms of the rule's extremes. Column thresholds of n accept every eligible merge, so
+    supernodes end exactly where the next column is not the etree parent of the last one. All
+    thresholds zero accept only merges that add no explicit zero."""
+    rng = np.random.default_rng(59)
+    for M, perm in _amalgamation_cases():
+        n = M.n
+        o = oracle.Oracle(M.n, M.Ap, M.Ai, perm, relax=(n, n, n, 0, 0, 0))
+        breaks = [0] + [j for j in range(1, n) if o.parent[j - 1] != j] + [n]
+        assert np.array_equal(o.sn, np.array(breaks))
+        o0 = oracle.Oracle(M.n, M.Ap, M.Ai, perm, relax=(0, 0, 0, 0, 0, 0))
+        P = brute_fill(permuted_dense(M, o0.perm))
+        for f, l in zip(o0.sn[:-1], o0.sn[1:]):
+            rows = np.nonzero(P[:, f:l].any(1))[0]
+            assert _storage(rows.size, l - f) == int(P[:, f:l].sum())  # no explicit zeros
+        rejected, part = _replay_merges(o0, P, (0, 0, 0, 0, 0, 0))
+        assert rejected == [] and np.array_equal(np.array(part), o0.sn)
+
+
+def test_row_patterns_check_rejects_corrupted_structure():
+    """The etree row-walk check returns a mismatch when the etree or a column pattern is wrong
+    (the mistake is planted in the oracle's own arrays, on the CPU)."""
+    import ctypes as ct
+    rng = np.random.default_rng(61)
+    M = w.laplace2d5(10, rng)
+    for what in ("parent", "Li"):
+        o = oracle.Oracle(M.n, M.Ap, M.Ai, M.perm)
+        assert o.row_patterns_agree()
+        if what == "parent":
+            # re-hang a column with a non-root parent onto a later column
+            j = int(np.nonzero(o.parent[:-2] >= 0)[0][3])
+            arr = (ct.c_int32 * o.n).from_address(o._lib.orc_parent(o._h))
+            arr[j] = min(int(o.parent[j]) + 1, o.n - 1) if o.parent[j] + 1 < o.n else int(o.parent[j]) - 1
+        else:
+            # move one off-diagonal row index of a column to another row below the diagonal
+            j = next(c for c in range(o.n) if o.Lp[c + 1] - o.Lp[c] >= 3)
+            arr = (ct.c_int32 * int(o.nnzL)).from_address(o._lib.orc_Li(o._h))
+            p = int(o.Lp[j]) + 1
+            free_rows = np.setdiff1d(np.arange(j + 1, o.n), o.Li[o.Lp[j]:o.Lp[j + 1]])
+            arr[p] = int(free_rows[0])
+        assert not o.row_patterns_agree(), what
+
+
 def test_descendants_maps_levels():
     rng = np.random.default_rng(41)
     M = w.laplace2d5(18, rng)
