@@ -207,6 +207,17 @@ def solver_exports(s):
     return {k: s.export(k) for k in ("super", "rowptr", "rows", "lxptr")}
 
 
+def sig4(x):
+    """Floats of a nested result rounded to 4 significant digits (keeps the line short)."""
+    if isinstance(x, float):
+        return float(f"{x:.4g}")
+    if isinstance(x, dict):
+        return {k: sig4(v) for k, v in x.items()}
+    if isinstance(x, (list, tuple)):
+        return [sig4(v) for v in x]
+    return x
+
+
 def make_workload(name):
     import workloads as w
     return w.cfg(name)
@@ -653,7 +664,7 @@ def run_ours(args):
                            "exec_flops": info.exec_flops, "supernodes": info.nsuper, "levels": info.nlevels},
         "value_definition": "factor flops (sum c_j^2) / (factor + solve) time per step",
         "variants_note": "ms per step of each variant (definitions in bench.py); per-kernel times on stderr",
-        "variants": variants,
+        "variants": sig4(variants),
     })
     if rank == 0:
         detail_dir = os.environ.get("SYM_BENCH_DETAIL_DIR", tempfile.gettempdir())

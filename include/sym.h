@@ -220,6 +220,33 @@ int sym_set_refinement(sym_handle h, double tol, int32_t max_iter);
  * reached above tolerance. */
 int sym_refinement_info(sym_handle h, int32_t *iterations, double *backward_error);
 
+/* Mixed precision only: the breakdown measure of the last factorization's FP32 factor. Its POTRF
+ * kernels carry every pivot in FP64 (the diagonal entry as the external updates left it, minus
+ * the squares of the tile's own column entries, subtracted in FP64; the reciprocal square root in
+ * FP64; the column scaling in FP32), following the spec reading that the diagonal pivots
+ * stay FP64 and that their ratio flags breakdown. For matrix `index` of the last batch (0 after
+ * sym_factor): *min_ratio = min_k d_k / C_kk over the FP64 pivots d_k and the diagonal entries of
+ * C = P A P^T, *column = that column (caller's numbering), and *breakdown = 1 when the ratio is
+ * below the threshold (default 2^-16: cancellation has then taken 16 of FP32's 24 significand
+ * bits from the pivot, so the factor may be a poor preconditioner and the matrix is close to
+ * singular at FP32 precision), else 0. A flagged factor stays usable: the FP64 refinement still
+ * runs and reports SYM_ERR_NO_CONVERGENCE if it cannot reach its tolerance. Output pointers may be
+ * NULL. Errors: SYM_ERR_STATE for an FP64 handle or before any factorization, SYM_ERR_INVALID
+ * for a bad index. */
+int sym_pivot_info(sym_handle h, int32_t index, double *min_ratio, int64_t *column, int32_t *breakdown);
+
+/* The breakdown threshold of sym_pivot_info (0 <= threshold <= 1). */
+int sym_set_pivot_threshold(sym_handle h, double threshold);
+
+/* Bounded waits of the tensor-core update (SYM_PREC_MIXED; no counterpart in the paper). Each
+ * wait of a CTA on its MMAs gives up after limit_ns nanoseconds (1e3 .. 1e10; default 1e9); the
+ * kernel then waits (with the same limit) for anything it still has in flight, frees its tensor
+ * memory and records the failure, and the factorization returns SYM_ERR_TIMEOUT with the handle
+ * still usable. withhold_mma = 1 is the failure-path test: the update issues no MMA and no
+ * commit, so its first wait runs out and nothing is in flight when the tensor memory is freed;
+ * 0 restores normal operation. Either change drops the captured factor graph. */
+int sym_set_tc_wait(sym_handle h, uint64_t limit_ns, int32_t withhold_mma);
+
 /* Sparse right-hand sides (Sec. 1.1 and Sec. 3.1 of the paper: decoupled sparse triangular
  * solve over the reach-set, with VI-Prune and VS-Block). For L y = P b with b nonzero only at
  * bidx (nnzb distinct indices, caller's numbering, host), sym_reach_analyze computes once per

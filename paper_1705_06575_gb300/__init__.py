@@ -21,7 +21,8 @@ __all__ = [
     "sym_factor_host", "sym_solve", "sym_solve_multi", "sym_solve_host", "sym_info",
     "sym_last_error_column", "sym_get_factor_host", "sym_export", "sym_free", "load", "Solver",
     "EXPORTS", "sym_profile", "sym_profile_read", "sym_profile_launches", "sym_fma_peak", "sym_tc_probe", "sym_solve_host_ptr", "KINDS",
-    "sym_solve_multi_noalloc", "sym_set_refinement", "sym_refinement_info", "sym_factor_batch",
+    "sym_solve_multi_noalloc", "sym_set_refinement", "sym_refinement_info", "sym_pivot_info",
+    "sym_set_pivot_threshold", "sym_set_tc_wait", "sym_factor_batch",
     "sym_batch_error_columns", "sym_solve_batch", "sym_get_batch_factor_host", "Reach", "MLP",
 ]
 
@@ -140,6 +141,9 @@ def load():
             "sym_solve_batch": ([P, i32, i32, P, i64, i64, P, i64, i64], I),
             "sym_get_batch_factor_host": ([P, i32, P], I),
             "sym_refinement_info": ([P, ct.POINTER(i32), ct.POINTER(ct.c_double)], I),
+            "sym_pivot_info": ([P, i32, ct.POINTER(ct.c_double), ct.POINTER(i64), ct.POINTER(i32)], I),
+            "sym_set_pivot_threshold": ([P, ct.c_double], I),
+            "sym_set_tc_wait": ([P, ct.c_uint64, i32], I),
         }
         for name, (args, res) in sigs.items():
             f = getattr(lib, name)
@@ -304,6 +308,21 @@ def sym_refinement_info(h):
     it, be = ct.c_int32(), ct.c_double()
     _check(load().sym_refinement_info(h, ct.byref(it), ct.byref(be)))
     return it.value, be.value
+
+
+def sym_pivot_info(h, index=0):
+    """(min_k d_k / C_kk, its column, breakdown flag) of the last mixed-precision factorization."""
+    r, col, bd = ct.c_double(), ct.c_int64(), ct.c_int32()
+    _check(load().sym_pivot_info(h, int(index), ct.byref(r), ct.byref(col), ct.byref(bd)))
+    return r.value, col.value, bool(bd.value)
+
+
+def sym_set_pivot_threshold(h, threshold):
+    return _check(load().sym_set_pivot_threshold(h, float(threshold)))
+
+
+def sym_set_tc_wait(h, limit_ns, withhold_mma=0):
+    return _check(load().sym_set_tc_wait(h, int(limit_ns), int(withhold_mma)))
 
 
 def sym_factor_batch(h, nbatch, Ax, stride):
@@ -519,6 +538,9 @@ class Solver:
 
     def refinement_info(self):
         return sym_refinement_info(self.h)
+
+    def pivot_info(self, index=0):
+        return sym_pivot_info(self.h, index)
 
     def error_column(self):
         return sym_last_error_column(self.h)

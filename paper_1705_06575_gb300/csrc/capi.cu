@@ -36,6 +36,7 @@ struct sym_handle_s {
   int64_t stage_cap = 0;
   int64_t device_bytes = 0;
   bool factored = false;
+  bool pivots_valid = false;  // a factorization of a mixed-precision handle has been enqueued
   int64_t err_col = -1;
   // batches of matrices with this pattern: capacity (matrices whose factor fits), the size of
   // the last factored batch and its per-matrix failing columns
@@ -65,6 +66,12 @@ struct sym_handle_s {
   double *d_rwork = nullptr;
   int64_t rwork_cap = 0;
   double *h_eta = nullptr;  // pinned, 256 doubles
+  // FP64 pivots of the FP32 factor and their breakdown ratio min_k d_k / C_kk per matrix
+  double *d_piv = nullptr;             // n per matrix
+  void *d_dpos = nullptr;              // int64[n]: index in Ax of C_kk
+  sym::PivotInfo *d_pivinfo = nullptr; // per matrix
+  sym::PivotInfo *h_pivinfo = nullptr; // pinned copy, per matrix
+  double pivot_threshold = 1.0 / 65536.0;
   double refine_tol = 1e-12;
   int32_t refine_max_iter = 100;
   int32_t last_iterations = 0;
@@ -148,10 +155,12 @@ void release_device(sym_handle_s *h) {
   if (h->la_join) cudaEventDestroy(h->la_join);
   if (h->aux_stream) cudaStreamDestroy(h->aux_stream);
   {
-    void *mp[] = {h->d_Linv, h->d_Lfinv, h->d_Lf, h->d_Axc, h->d_anorm, h->d_anorm_work, h->d_csr_p, h->d_csr_i, h->d_csr_map, h->d_rwork};
+    void *mp[] = {h->d_Linv, h->d_Lfinv, h->d_Lf, h->d_Axc, h->d_anorm, h->d_anorm_work, h->d_csr_p, h->d_csr_i,
+                  h->d_csr_map, h->d_rwork, h->d_piv, h->d_dpos, h->d_pivinfo};
     for (void *p : mp)
       if (p) cudaFree(p);
     if (h->h_eta) cudaFreeHost(h->h_eta);
+    if (h->h_pivinfo) cudaFreeHost(h->h_pivinfo);
   }
   for (cudaEvent_t e : h->events) cudaEventDestroy(e);
   if (h->fgraph) cudaGraphExecDestroy(h->fgraph);
@@ -199,6 +208,7 @@ sym::Batch factor_batch(const sym_handle_s *h, int32_t nbatch, int64_t stride) {
   bt.lx = h->plan.storage();
   bt.ax = stride;
   bt.dinv = h->plan.dinv_storage;
+  bt.piv = h->plan.n;
   return bt;
 }
 
@@ -219,7 +229,8 @@ cudaError_t enqueue_factor(sym_handle_s *h, const double *Ax, int32_t nbatch, in
       e = sym::refine_anorm(refine_ctx(h, b), st);
       if (e != cudaSuccess) return e;
     }
-    return cudaSuccess;
+    return sym::pivot_ratio(h->d_piv, h->plan.n, h->d_Axc, h->plan.nnz_a, (const int64_t *)h->d_dpos, nbatch,
+                            h->d_pivinfo, st);
   }
   return sym::run_factor<double>(h->dp, h->plan.factor_launches, Ax, h->d_Lx, h->d_Linv, h->d_status, st, tr, bt,
                                  h->aux_stream ? &h->two : nullptr);
@@ -256,6 +267,15 @@ int ensure_batch(sym_handle_s *h, int32_t nbatch) {
     if (!rc) rc = regrow((void **)&h->d_Lfinv, sizeof(float) * P.dinv_storage * nb, "cudaMalloc(inverses batch)");
     if (!rc) rc = regrow((void **)&h->d_Axc, sizeof(double) * P.nnz_a * nb, "cudaMalloc(A copies)");
     if (!rc) rc = regrow((void **)&h->d_anorm, sizeof(double) * nb, "cudaMalloc(norms)");
+    if (!rc) rc = regrow((void **)&h->d_piv, sizeof(double) * P.n * nb, "cudaMalloc(pivots)");
+    if (!rc) rc = regrow((void **)&h->d_pivinfo, sizeof(sym::PivotInfo) * nb, "cudaMalloc(pivot ratios)");
+    if (!rc) {
+      if (h->h_pivinfo) cudaFreeHost(h->h_pivinfo);
+      h->h_pivinfo = nullptr;
+      cudaError_t e = cudaMallocHost(&h->h_pivinfo, sizeof(sym::PivotInfo) * nb);
+      if (e != cudaSuccess) rc = cuda_fail(e, "cudaMallocHost(pivot ratios)");
+    }
+    h->dp.piv = h->d_piv;
   }
   if (!rc) rc = regrow((void **)&h->d_status, sizeof(long long) * nb, "cudaMalloc(status batch)");
   if (!rc) rc = regrow((void **)&h->d_t, sizeof(double) * sym::SOLVE_MAXRHS * P.tsize * nb, "cudaMalloc(solve buffer batch)");
@@ -479,6 +499,24 @@ int sym_analyze_perm(int64_t n, const int64_t *Ap, const int32_t *Ai, const int3
         if (e != cudaSuccess) rc = cuda_fail(e, "cudaMallocHost(refinement)");
       }
       if (!rc) rc = ensure_rwork(h, sym::refine_work_doubles(P.n, 1));
+      if (!rc) {
+        std::vector<int64_t> dpos(P.n);
+        for (int64_t k = 0; k < P.n; ++k) dpos[k] = Ap[P.perm[k]];  // the diagonal leads each column
+        rc = upload(dpos, &h->d_dpos, bytes);
+      }
+      if (!rc) {
+        e = cudaMalloc(&h->d_piv, sizeof(double) * (P.n > 0 ? P.n : 1));
+        if (e != cudaSuccess) rc = cuda_fail(e, "cudaMalloc(pivots)");
+        else bytes += sizeof(double) * P.n;
+      }
+      if (!rc) {
+        e = cudaMalloc(&h->d_pivinfo, sizeof(sym::PivotInfo));
+        if (e != cudaSuccess) rc = cuda_fail(e, "cudaMalloc(pivot ratio)");
+      }
+      if (!rc) {
+        e = cudaMallocHost(&h->h_pivinfo, sizeof(sym::PivotInfo));
+        if (e != cudaSuccess) rc = cuda_fail(e, "cudaMallocHost(pivot ratio)");
+      }
     }
     if (!rc) {
       e = cudaMalloc(&h->d_status, sizeof(long long));
@@ -510,6 +548,7 @@ int sym_analyze_perm(int64_t n, const int64_t *Ap, const int32_t *Ai, const int3
     h->dp.nnz_a = P.nnz_a;
     h->dp.storage = P.storage();
     h->dp.tensor_cores = (opt.flags & SYM_FLAG_NO_TENSOR_CORES) == 0;
+    h->dp.piv = h->d_piv;
   }
   *out = h;
   return SYM_OK;
@@ -588,6 +627,11 @@ int factor_impl(sym_handle h, int32_t nbatch, const double *Ax, int64_t stride) 
   CUDA_TRY(cudaMemcpyAsync(h->h_status + h->bcap, h->d_status, sizeof(long long) * nbatch, cudaMemcpyDeviceToHost,
                            h->stream),
            "status read");
+  if (h->precision == SYM_PREC_MIXED && h->plan.n > 0)
+    CUDA_TRY(cudaMemcpyAsync(h->h_pivinfo, h->d_pivinfo, sizeof(sym::PivotInfo) * nbatch, cudaMemcpyDeviceToHost,
+                             h->stream),
+             "pivot ratio read");
+  h->pivots_valid = h->precision == SYM_PREC_MIXED;
   return SYM_OK;
 }
 
@@ -940,6 +984,37 @@ int sym_refinement_info(sym_handle h, int32_t *iterations, double *backward_erro
   if (!h) return fail(SYM_ERR_INVALID, "null handle");
   if (iterations) *iterations = h->last_iterations;
   if (backward_error) *backward_error = h->last_berr;
+  return SYM_OK;
+}
+
+int sym_pivot_info(sym_handle h, int32_t index, double *min_ratio, int64_t *column, int32_t *breakdown) {
+  if (!h) return fail(SYM_ERR_INVALID, "null handle");
+  if (h->precision != SYM_PREC_MIXED) return fail(SYM_ERR_STATE, "pivot ratios belong to mixed-precision handles");
+  if (!h->pivots_valid) return fail(SYM_ERR_STATE, "no factorization yet");
+  if (index < 0 || index >= h->nbatch) return fail(SYM_ERR_INVALID, "matrix index out of range");
+  CUDA_TRY(cudaStreamSynchronize(h->stream), "pivot ratio");
+  const sym::PivotInfo &pi = h->h_pivinfo[index];
+  const bool any = h->plan.n > 0 && pi.column >= 0;
+  if (min_ratio) *min_ratio = any ? pi.min_ratio : 1.0;
+  if (column) *column = any ? h->plan.perm[pi.column] : -1;
+  if (breakdown) *breakdown = any && pi.min_ratio < h->pivot_threshold ? 1 : 0;
+  return SYM_OK;
+}
+
+int sym_set_tc_wait(sym_handle h, uint64_t limit_ns, int32_t withhold_mma) {
+  if (!h) return fail(SYM_ERR_INVALID, "null handle");
+  if (limit_ns < 1000 || limit_ns > 10000000000ull) return fail(SYM_ERR_INVALID, "wait limit outside [1 us, 10 s]");
+  if (withhold_mma != 0 && withhold_mma != 1) return fail(SYM_ERR_INVALID, "withhold_mma must be 0 or 1");
+  if (h->dp.tc_wait_ns != limit_ns || h->dp.tc_withhold != withhold_mma) drop_graphs(h);  // baked-in arguments
+  h->dp.tc_wait_ns = limit_ns;
+  h->dp.tc_withhold = withhold_mma;
+  return SYM_OK;
+}
+
+int sym_set_pivot_threshold(sym_handle h, double threshold) {
+  if (!h) return fail(SYM_ERR_INVALID, "null handle");
+  if (!(threshold >= 0.0 && threshold <= 1.0)) return fail(SYM_ERR_INVALID, "threshold outside [0, 1]");
+  h->pivot_threshold = threshold;
   return SYM_OK;
 }
 

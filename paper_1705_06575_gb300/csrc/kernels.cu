@@ -23,6 +23,8 @@
 #include <cooperative_groups.h>
 #include <type_traits>
 
+#include <cmath>
+
 #include <cstdint>
 #include <utility>
 
@@ -482,19 +484,25 @@ __global__ void __launch_bounds__(TileCfg<TB>::threads, TB == NB ? (CLUSTER ? 2 
 // pivot and scales it, while the other warps apply column c to columns c+2.. — one barrier per
 // column. A pivot that is not positive (or NaN) records its permuted column in *status (atomic
 // min) and is replaced by 1 so the kernel finishes with finite values.
+//
+// An FP32 factor keeps its pivot chain in FP64: each diagonal entry is carried in FP64 from the
+// value the external updates left (dd), the tile's own updates l^2 are subtracted in FP64, and
+// the pivot's reciprocal square root is taken in FP64; the off-diagonal entries and the column
+// scaling stay in FP32. Every pivot d_k is stored in piv (FP64), from which the factorization's
+// breakdown ratio min_k d_k / C_kk is formed.
 template <typename T, int TB>
 __global__ void __launch_bounds__(TileCfg<TB>::threads) k_potrf(const SNode *__restrict__ sn,
                                                                 const Int4 *__restrict__ tasks,
                                                                 T *__restrict__ Lx, long long *status,
-                                                                int64_t toff, const Batch bt) {
+                                                                double *__restrict__ piv, int64_t toff,
+                                                                const Batch bt) {
   constexpr int TT = TileCfg<TB>::threads;
+  constexpr bool F64PIV = std::is_same<T, float>::value;
   Lx += blockIdx.y * bt.lx;
   status += blockIdx.y;
-  // The tile is factored in the storage type: an FP32 factor is a preconditioner whose accuracy
-  // the FP64 refinement restores, and FP32 keeps its serial pivot chain short (an FP64 operation
-  // waits 64 cycles for the previous one on this part).
   __shared__ T a[TB][TB + 1];                      // [col][row]
   __shared__ unsigned short tri[TB * (TB - 1) / 2];  // packed lower triangle: (i << 8) | j, i >= j
+  __shared__ double dd[F64PIV ? TB : 1];             // FP64 diagonal (FP32 factors)
   const Int4 t = tasks[toff + blockIdx.x];
   const SNode sj = sn[t.a];
   const int s = t.b;
@@ -503,7 +511,11 @@ __global__ void __launch_bounds__(TileCfg<TB>::threads) k_potrf(const SNode *__r
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int idx = tid; idx < ts * ts; idx += TT) {  // only the lower triangle is read
     int rr = idx % ts, c = idx / ts;
-    if (rr >= c) a[c][rr] = D[(int64_t)c * sj.nrows + rr];
+    if (rr >= c) {
+      const T v = D[(int64_t)c * sj.nrows + rr];
+      a[c][rr] = v;
+      if (F64PIV && rr == c) dd[c] = (double)v;
+    }
   }
   // Row-major packed index of the lower triangle: idx = i (i + 1) / 2 + j. The first
   // m (m + 1) / 2 entries are the triangle of order m, whatever m is; the largest trailing
@@ -517,21 +529,37 @@ __global__ void __launch_bounds__(TileCfg<TB>::threads) k_potrf(const SNode *__r
   __syncthreads();
   // warp 0: pivot of column c (already updated by columns < c) and scaling of the column
   auto finish_column = [&](int c) {
-    T d = a[c][c];
-    if (!(d > T(0))) {
-      if (lane == 0) atomicMin(status, (long long)(sj.first + s * NB + c));
-      d = T(1);
+    if constexpr (F64PIV) {
+      double d = dd[c];
+      if (!(d > 0.0)) {
+        if (lane == 0) atomicMin(status, (long long)(sj.first + s * NB + c));
+        d = 1.0;
+      }
+      if (lane == 0 && piv) piv[blockIdx.y * bt.piv + sj.first + s * NB + c] = d;
+      const double x = rsqrt_newton(d);
+      const T xf = (T)x;
+      __syncwarp();
+      for (int r = c + lane; r < ts; r += 32) a[c][r] = r == c ? (T)(d * x) : a[c][r] * xf;  // d x = sqrt(d)
+    } else {
+      T d = a[c][c];
+      if (!(d > T(0))) {
+        if (lane == 0) atomicMin(status, (long long)(sj.first + s * NB + c));
+        d = T(1);
+      }
+      const T x = rsqrt_of(d);
+      __syncwarp();
+      for (int r = c + lane; r < ts; r += 32) a[c][r] = r == c ? d * x : a[c][r] * x;  // d x = sqrt(d)
     }
-    const T x = rsqrt_of(d);
-    __syncwarp();
-    for (int r = c + lane; r < ts; r += 32) a[c][r] = r == c ? d * x : a[c][r] * x;  // d x = sqrt(d)
   };
   if (warp == 0 && ts > 0) finish_column(0);
   __syncthreads();
   for (int c = 0; c + 1 < ts; ++c) {
     if (warp == 0) {
       const T l = a[c][c + 1];
-      for (int r = c + 1 + lane; r < ts; r += 32) a[c + 1][r] = fma(-a[c][r], l, a[c + 1][r]);
+      for (int r = c + 1 + lane; r < ts; r += 32) {
+        if (F64PIV && r == c + 1) dd[r] = fma(-(double)l, (double)l, dd[r]);
+        else a[c + 1][r] = fma(-a[c][r], l, a[c + 1][r]);
+      }
       __syncwarp();
       finish_column(c + 1);
     } else {
@@ -540,7 +568,8 @@ __global__ void __launch_bounds__(TileCfg<TB>::threads) k_potrf(const SNode *__r
       for (int idx = tid - 32; idx < tot; idx += TT - 32) {
         const int ij = tri[idx];
         const int rr = c + 2 + (ij >> 8), cc = c + 2 + (ij & 0xff);
-        a[cc][rr] = fma(-a[c][rr], a[c][cc], a[cc][rr]);
+        if (F64PIV && rr == cc) dd[rr] = fma(-(double)a[c][rr], (double)a[c][rr], dd[rr]);
+        else a[cc][rr] = fma(-a[c][rr], a[c][cc], a[cc][rr]);
       }
     }
     __syncthreads();
@@ -1245,10 +1274,12 @@ __device__ __forceinline__ void tri_decode(int el, int &a, int &b) {
 template <typename T>
 __global__ void __launch_bounds__(32 * WT_WARPS) k_potrf_w(const SNode *__restrict__ sn, const Int4 *__restrict__ tasks,
                                                            int64_t ntask, T *__restrict__ Lx, long long *status,
-                                                           int64_t toff, const Batch bt) {
+                                                           double *__restrict__ piv, int64_t toff, const Batch bt) {
+  constexpr bool F64PIV = std::is_same<T, float>::value;  // FP64 pivot chain of FP32 factors (k_potrf)
   Lx += blockIdx.y * bt.lx;
   status += blockIdx.y;
   __shared__ T tri[WT_WARPS][WT_PACK];
+  __shared__ double ddw[WT_WARPS][F64PIV ? SMALL_TILE : 1];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t task = (int64_t)blockIdx.x * WT_WARPS + w;
   if (task >= ntask) return;  // warp-uniform; only warp-level synchronization below
@@ -1258,25 +1289,44 @@ __global__ void __launch_bounds__(32 * WT_WARPS) k_potrf_w(const SNode *__restri
   const int ts = min(SMALL_TILE, sj.ncols - s * NB);
   T *D = Lx + sj.lx + (int64_t)(s * NB) * sj.nrows + s * NB;
   T *a = tri[w];
+  double *dd = ddw[w];
   for (int c = 0; c < ts; ++c)
-    if (lane >= c && lane < ts) a[pk(ts, c, lane)] = D[(int64_t)c * sj.nrows + lane];
+    if (lane >= c && lane < ts) {
+      const T v = D[(int64_t)c * sj.nrows + lane];
+      a[pk(ts, c, lane)] = v;
+      if (F64PIV && lane == c) dd[c] = (double)v;
+    }
   __syncwarp();
   for (int c = 0; c < ts; ++c) {
-    T d = a[pk(ts, c, c)];
-    if (!(d > T(0))) {
-      if (lane == 0) atomicMin(status, (long long)(sj.first + s * NB + c));
-      d = T(1);
+    if constexpr (F64PIV) {
+      double d = dd[c];
+      if (!(d > 0.0)) {
+        if (lane == 0) atomicMin(status, (long long)(sj.first + s * NB + c));
+        d = 1.0;
+      }
+      if (lane == 0 && piv) piv[blockIdx.y * bt.piv + sj.first + s * NB + c] = d;
+      const double x = rsqrt_newton(d);
+      const T xf = (T)x;
+      __syncwarp();  // every lane has read the pivot
+      if (lane >= c && lane < ts) a[pk(ts, c, lane)] = lane == c ? (T)(d * x) : a[pk(ts, c, lane)] * xf;
+    } else {
+      T d = a[pk(ts, c, c)];
+      if (!(d > T(0))) {
+        if (lane == 0) atomicMin(status, (long long)(sj.first + s * NB + c));
+        d = T(1);
+      }
+      const T x = rsqrt_of(d);
+      __syncwarp();  // every lane has read the pivot
+      if (lane >= c && lane < ts) a[pk(ts, c, lane)] = lane == c ? d * x : a[pk(ts, c, lane)] * x;
     }
-    const T x = rsqrt_of(d);
-    __syncwarp();  // every lane has read the pivot
-    if (lane >= c && lane < ts) a[pk(ts, c, lane)] = lane == c ? d * x : a[pk(ts, c, lane)] * x;
     __syncwarp();
     const int m = ts - 1 - c;  // trailing triangle: rows and columns c+1 .. ts-1
     for (int el = lane; el < m * (m + 1) / 2; el += 32) {
       int ia, ib;
       tri_decode(el, ia, ib);
       const int rr = c + 1 + ia, cc = c + 1 + ib;
-      a[pk(ts, cc, rr)] = fma(-a[pk(ts, c, rr)], a[pk(ts, c, cc)], a[pk(ts, cc, rr)]);
+      if (F64PIV && rr == cc) dd[rr] = fma(-(double)a[pk(ts, c, rr)], (double)a[pk(ts, c, rr)], dd[rr]);
+      else a[pk(ts, cc, rr)] = fma(-a[pk(ts, c, rr)], a[pk(ts, c, cc)], a[pk(ts, cc, rr)]);
     }
     __syncwarp();
   }
@@ -1432,6 +1482,45 @@ __global__ void k_reach_gather(const int32_t *__restrict__ cols, int64_t nr, con
   if (t < nr) x[t] = y[cols[t]];
 }
 
+// Breakdown measure of an FP32 factor: one CTA per matrix scans the pivots in a fixed order and
+// reduces (ratio, column) pairs in shared memory (smallest ratio, then smallest column).
+__global__ void __launch_bounds__(1024) k_pivot_ratio(const double *__restrict__ piv, int64_t n,
+                                                      const double *__restrict__ Ax, int64_t axstride,
+                                                      const int64_t *__restrict__ dpos, PivotInfo *out) {
+  __shared__ double rs[1024];
+  __shared__ int64_t ks[1024];
+  piv += blockIdx.x * n;
+  Ax += blockIdx.x * axstride;
+  double best = INFINITY;
+  int64_t bk = -1;
+  for (int64_t k = threadIdx.x; k < n; k += blockDim.x) {
+    const double akk = Ax[dpos[k]];
+    const double r = akk > 0.0 ? piv[k] / akk : 0.0;
+    if (r < best) {  // k ascends within a thread: ties keep the smaller column
+      best = r;
+      bk = k;
+    }
+  }
+  rs[threadIdx.x] = best;
+  ks[threadIdx.x] = bk;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) {
+      const double r2 = rs[threadIdx.x + h];
+      const int64_t k2 = ks[threadIdx.x + h];
+      if (r2 < rs[threadIdx.x] || (r2 == rs[threadIdx.x] && k2 >= 0 && (ks[threadIdx.x] < 0 || k2 < ks[threadIdx.x]))) {
+        rs[threadIdx.x] = r2;
+        ks[threadIdx.x] = k2;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[blockIdx.x].min_ratio = rs[0];
+    out[blockIdx.x].column = ks[0];
+  }
+}
+
 template <typename T, typename V>
 cudaError_t prepare_solve() {
   cudaError_t e = cudaFuncSetAttribute(k_fstep<T, V, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1494,11 +1583,13 @@ cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, co
         // four warps shorten each column step of the tile (latency; 64^2 factor 0.96 -> 0.83 ms)
         if (small && nb > 1)
           e = launch_prio(k_potrf_w<T>, dim3((g + WT_WARPS - 1) / WT_WARPS, nb), 32 * WT_WARPS, 0, s, prio, d.sn,
-                          d.tasks, (int64_t)g, Lx, status, L.off, bt);
+                          d.tasks, (int64_t)g, Lx, status, d.piv, L.off, bt);
         else if (small)
-          e = launch_prio(k_potrf<T, SMALL_TB>, dim3(g, nb), TS, 0, s, prio, d.sn, d.tasks, Lx, status, L.off, bt);
+          e = launch_prio(k_potrf<T, SMALL_TB>, dim3(g, nb), TS, 0, s, prio, d.sn, d.tasks, Lx, status, d.piv, L.off,
+                          bt);
         else
-          e = launch_prio(k_potrf<T, NB>, dim3(g, nb), THREADS, 0, s, prio, d.sn, d.tasks, Lx, status, L.off, bt);
+          e = launch_prio(k_potrf<T, NB>, dim3(g, nb), THREADS, 0, s, prio, d.sn, d.tasks, Lx, status, d.piv, L.off,
+                          bt);
         break;
       case K_TRSM:
         // (a warp-per-tile form with the column pairs mapped flat onto the lanes made the
@@ -1641,6 +1732,13 @@ cudaError_t run_sparse_lower(const DevPlan &d, const std::vector<Launch> &fwd, c
   cudaError_t e = run_sweeps<double, double>(d, fwd, none, Lx, Linv, 1, y, st, nullptr, Batch());
   if (e != cudaSuccess) return e;
   if (nr > 0) k_reach_gather<<<(unsigned)((nr + THREADS - 1) / THREADS), THREADS, 0, st>>>(cols, nr, y, x);
+  return cudaGetLastError();
+}
+
+cudaError_t pivot_ratio(const double *piv, int64_t n, const double *Ax, int64_t axstride, const int64_t *dpos,
+                        int32_t nbatch, PivotInfo *out, cudaStream_t st) {
+  if (n == 0 || nbatch < 1) return cudaSuccess;
+  k_pivot_ratio<<<(unsigned)nbatch, 1024, 0, st>>>(piv, n, Ax, axstride, dpos, out);
   return cudaGetLastError();
 }
 

@@ -25,6 +25,11 @@ struct DevPlan {
   int64_t nnz_a = 0;
   int64_t storage = 0;
   bool tensor_cores = true;          // FP32 updates on tcgen05 (false: the FP32 SIMT kernel)
+  uint64_t tc_wait_ns = 1000000000ull;  // limit of each bounded wait of the tensor-core update
+  int32_t tc_withhold = 0;           // failure-path test: the tensor-core update issues no MMA
+                                     // and no commit, so its first wait runs out
+  double *piv = nullptr;             // FP32 factors: the FP64 pivot d_k of every permuted column k
+                                     // (n per matrix), written by the POTRF kernels; else null
 };
 
 // Several matrices with one pattern (blockIdx.y = matrix): offsets, in elements, from one matrix to
@@ -33,7 +38,7 @@ struct DevPlan {
 // default describes a single matrix.
 struct Batch {
   int32_t count = 1;
-  int64_t lx = 0, ax = 0, dinv = 0, y = 0, b = 0, x = 0, t = 0;
+  int64_t lx = 0, ax = 0, dinv = 0, y = 0, b = 0, x = 0, t = 0, piv = 0;
 };
 
 // Second stream for the factor's lookahead: aux runs the launches with stream == 1 at low
@@ -100,6 +105,17 @@ cudaError_t run_sparse_lower(const DevPlan &d, const std::vector<Launch> &fwd, c
                              const double *Linv, const int32_t *snodes, int64_t nsn, const int32_t *pbeta,
                              const double *bvals, int64_t nb, const int32_t *cols, int64_t nr, double *y,
                              double *x, cudaStream_t st);
+
+// The breakdown measure of an FP32 factor's pivots: for matrix b of the batch, the smallest
+// ratio d_k / C_kk of the FP64 pivot to the diagonal entry of C = P A P^T, and its column k
+// (smallest k on ties). Ax: A's values (matrix b at Ax + b * axstride); dpos[k]: index in Ax of
+// C_kk.
+struct PivotInfo {
+  double min_ratio;
+  int64_t column;
+};
+cudaError_t pivot_ratio(const double *piv, int64_t n, const double *Ax, int64_t axstride, const int64_t *dpos,
+                        int32_t nbatch, PivotInfo *out, cudaStream_t st);
 
 // y = P B and X = P^T y for nrhs columns.
 template <typename V>

@@ -97,9 +97,9 @@ __device__ __forceinline__ void mbar_init_fence() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-// Wait until the phase of the given parity has completed; gives up after ~1 s (globaltimer) or
-// 2^26 polls and returns false.
-__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity) {
+// Wait until the phase of the given parity has completed; gives up after limit_ns nanoseconds
+// (globaltimer; default about a second) or 2^26 polls and returns false.
+__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, uint64_t limit_ns = 1000000000ull) {
   const uint32_t a = smem_addr(mbar);
   uint64_t t0;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
@@ -116,7 +116,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity) {
     if ((i & 255) == 255) {
       uint64_t t;
       asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-      if (t - t0 > 1000000000ull) return false;
+      if (t - t0 > limit_ns) return false;
     }
   }
   return false;

@@ -109,14 +109,17 @@ __device__ __forceinline__ void fetch(Prefetch &f, const float *__restrict__ Lx,
 // owns one accumulator row: warps 0-1 the A_hi rows, warps 2-3 the A_lo rows) while the next
 // segment runs on the other accumulator. Long sums are thus rounded to nearest in FP32 as in the
 // SIMT form; inside the tensor core a sum runs over at most 8 SEG K = 8 steps.
-// A wait that runs out (about a second) records -1 in *status and leaves the tile unwritten.
+// A wait that runs out (wait_ns, about a second by default) records -1 in *status and leaves the
+// tile unwritten. withhold != 0 (a failure-path test) issues no MMA and no commit, so the first
+// wait runs out; nothing is then in flight when the tensor memory is freed.
 constexpr int SEG = 8;
 
 __global__ void __launch_bounds__(TC_THREADS, 3) k_update_tc(const SNode *__restrict__ sn,
                                                              const UpdTask *__restrict__ tasks,
                                                              const UpdEntry *__restrict__ ents,
                                                              const int32_t *__restrict__ rel, float *__restrict__ Lx,
-                                                             int64_t toff, const Batch bt, long long *status) {
+                                                             int64_t toff, const Batch bt, long long *status,
+                                                             uint64_t wait_ns, int withhold) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ EntryBatch eb;
   __shared__ __align__(8) uint64_t mbar[NSTAGE];
@@ -150,7 +153,7 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_update_tc(const SNode *__rest
   // Read back accumulator `which` (the MMAs of chunk `last` and all before it complete) and add
   // it to acc. Uniform across the CTA; false when the wait ran out.
   auto drain = [&](int which, int last) -> bool {
-    const bool ok = tc::mbar_wait(&mbar[last & 1], (uint32_t)(last >> 1) & 1u);
+    const bool ok = tc::mbar_wait(&mbar[last & 1], (uint32_t)(last >> 1) & 1u, wait_ns);
     if (__syncthreads_or(!ok)) return false;
     tc::fence_after_sync();
     float v[32];
@@ -197,7 +200,7 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_update_tc(const SNode *__rest
     while (i < ne) {
       const int st = it & 1;
       if (it >= NSTAGE) {  // the MMAs of chunk it - 2 read this stage
-        const bool ok = tc::mbar_wait(&mbar[st], (uint32_t)((it >> 1) - 1) & 1u);
+        const bool ok = tc::mbar_wait(&mbar[st], (uint32_t)((it >> 1) - 1) & 1u, wait_ns);
         if (__syncthreads_or(!ok)) {
           failed = true;
           break;
@@ -221,7 +224,7 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_update_tc(const SNode *__rest
       if (i < ne) fetch(f, Lx, eb, i, k0, p, kq0);
       __syncthreads();
       const int seg = it / SEG;
-      if (tid == 0) {
+      if (tid == 0 && !withhold) {
         tc::fence_after_sync();
         const uint32_t a0 = tc::smem_addr(A), bh0 = tc::smem_addr(Bh), bl0 = tc::smem_addr(Bl);
         const uint32_t d = tmem + (uint32_t)(seg & 1) * NB;
@@ -246,7 +249,7 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_update_tc(const SNode *__rest
   if (!failed && it > 0 && !drain(((it - 1) / SEG) & 1, it - 1)) failed = true;
   if (failed && it > 0) {  // let the MMAs in flight finish (bounded) before the memory is freed
     const int last = it - 1;
-    tc::mbar_wait(&mbar[last & 1], (uint32_t)(last >> 1) & 1u);
+    tc::mbar_wait(&mbar[last & 1], (uint32_t)(last >> 1) & 1u, wait_ns);
     __syncthreads();
     if (tid == 0) atomicMin(status, -1ll);
   } else if (it > 0) {
@@ -293,7 +296,8 @@ cudaError_t launch_update_tc(dim3 grid, cudaStream_t st, int prio, const DevPlan
   attr[0].val.priority = prio;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_update_tc, d.sn, d.upd_tasks, d.upd_entries, d.rel, Lx, toff, bt, status);
+  return cudaLaunchKernelEx(&cfg, k_update_tc, d.sn, d.upd_tasks, d.upd_entries, d.rel, Lx, toff, bt, status,
+                            d.tc_wait_ns, (int)d.tc_withhold);
 }
 
 }  // namespace sym

@@ -122,3 +122,35 @@ def test_tc_factor_is_deterministic(torch_cuda):
     L2 = s.factor_panels()
     assert np.array_equal(L1, L2)
     s.close()
+
+
+def test_tensor_core_wait_runs_out_and_handle_recovers(torch_cuda):
+    """Failure path of the bounded waits: with the MMAs withheld (nothing ever arrives on the
+    update kernel's mbarriers) and a 20 us limit, every wait runs out, the kernel frees its tensor
+    memory and the factorization returns SYM_ERR_TIMEOUT quickly; the solve is then refused, and
+    the same handle factors and solves normally once the limit is restored."""
+    import time
+
+    torch = torch_cuda
+    import paper_1705_06575_gb300 as S
+    M = w.conduct3d(16, np.random.default_rng(12), "star")
+    s = S.Solver(M.n, M.Ap, M.Ai, M.perm, precision="mixed")
+    assert max(np.diff(s.export("super"))) > 64  # 64-wide tiles: the tensor-core update runs
+    Ax = torch.from_numpy(M.Ax).cuda()
+    s.factor(Ax)
+    S.sym_set_tc_wait(s.h, 20_000, 1)
+    t0 = time.perf_counter()
+    with pytest.raises(S.SymError) as e:
+        s.factor(Ax)
+    assert e.value.code == S.SYM_ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 30.0
+    b = torch.from_numpy(w.rhs(M.n, 1, np.random.default_rng(1))[:, 0]).cuda()
+    with pytest.raises(S.SymError) as e2:
+        s.solve(b)
+    assert e2.value.code == S.SYM_ERR_STATE
+    S.sym_set_tc_wait(s.h, 1_000_000_000, 0)
+    s.set_refinement(1e-12, 100)
+    s.factor(Ax)
+    x = s.solve(b)
+    torch.cuda.synchronize()
+    assert oracle.backward_error(M.n, M.Ap, M.Ai, M.Ax, b.cpu().numpy(), x.cpu().numpy()) <= 1e-12
