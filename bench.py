@@ -46,7 +46,7 @@ METRIC = "refactor GFLOP/s and ms/(factor+solve) vs plain FP64 GPU path at bwd e
 # update launches of one step). It holds only for the kernel source it was taken on: the
 # sha256 (first 16 hex digits) of the kernel's definition text in csrc/kernels.cu. When that
 # text changes, the line reports null until the traffic is captured again.
-UPDATE_TRAFFIC = {"bytes_per_launch": None, "kernel_sha16": None}
+UPDATE_TRAFFIC = {"bytes_per_launch": 5.4518e8, "kernel_sha16": "6f9b0de4cc0dd30c"}
 
 CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"

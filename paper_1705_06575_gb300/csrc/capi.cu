@@ -209,6 +209,7 @@ sym::Batch factor_batch(const sym_handle_s *h, int32_t nbatch, int64_t stride) {
   bt.ax = stride;
   bt.dinv = h->plan.dinv_storage;
   bt.piv = h->plan.n;
+  bt.nnz = h->plan.nnz_a;
   return bt;
 }
 
@@ -266,6 +267,7 @@ int ensure_batch(sym_handle_s *h, int32_t nbatch) {
     rc = regrow((void **)&h->d_Lf, sizeof(float) * P.storage() * nb, "cudaMalloc(L batch)");
     if (!rc) rc = regrow((void **)&h->d_Lfinv, sizeof(float) * P.dinv_storage * nb, "cudaMalloc(inverses batch)");
     if (!rc) rc = regrow((void **)&h->d_Axc, sizeof(double) * P.nnz_a * nb, "cudaMalloc(A copies)");
+    h->dp.axc = h->d_Axc;
     if (!rc) rc = regrow((void **)&h->d_anorm, sizeof(double) * nb, "cudaMalloc(norms)");
     if (!rc) rc = regrow((void **)&h->d_piv, sizeof(double) * P.n * nb, "cudaMalloc(pivots)");
     if (!rc) rc = regrow((void **)&h->d_pivinfo, sizeof(sym::PivotInfo) * nb, "cudaMalloc(pivot ratios)");
@@ -549,6 +551,8 @@ int sym_analyze_perm(int64_t n, const int64_t *Ap, const int32_t *Ai, const int3
     h->dp.storage = P.storage();
     h->dp.tensor_cores = (opt.flags & SYM_FLAG_NO_TENSOR_CORES) == 0;
     h->dp.piv = h->d_piv;
+    h->dp.axc = h->d_Axc;
+    h->dp.dpos = (const int64_t *)h->d_dpos;
   }
   *out = h;
   return SYM_OK;

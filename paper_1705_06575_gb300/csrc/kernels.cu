@@ -485,16 +485,26 @@ __global__ void __launch_bounds__(TileCfg<TB>::threads, TB == NB ? (CLUSTER ? 2 
 // column. A pivot that is not positive (or NaN) records its permuted column in *status (atomic
 // min) and is replaced by 1 so the kernel finishes with finite values.
 //
-// An FP32 factor keeps its pivot chain in FP64: each diagonal entry is carried in FP64 from the
-// value the external updates left (dd), the tile's own updates l^2 are subtracted in FP64, and
-// the pivot's reciprocal square root is taken in FP64; the off-diagonal entries and the column
-// scaling stay in FP32. Every pivot d_k is stored in piv (FP64), from which the factorization's
-// breakdown ratio min_k d_k / C_kk is formed.
+// An FP32 factor keeps its pivot chain in FP64: each diagonal entry is carried in FP64 (dd) as
+// C_kk in FP64 plus the updates the earlier kernels accumulated in FP32 (the stored value minus
+// C_kk rounded to FP32, a difference formed exactly), the tile's own updates l^2 are subtracted
+// in FP64, and the pivot's reciprocal square root is taken in FP64; the off-diagonal entries and
+// the column scaling stay in FP32. Every pivot d_k is stored in piv (FP64), from which the
+// factorization's breakdown ratio min_k d_k / C_kk is formed.
+__device__ __forceinline__ double diag64(float stored, const double *__restrict__ axc, const int64_t *__restrict__ dpos,
+                                         int64_t g) {
+  if (!axc) return (double)stored;
+  const double c = axc[dpos[g]];
+  return c + ((double)stored - (double)(float)c);
+}
+
 template <typename T, int TB>
 __global__ void __launch_bounds__(TileCfg<TB>::threads) k_potrf(const SNode *__restrict__ sn,
                                                                 const Int4 *__restrict__ tasks,
                                                                 T *__restrict__ Lx, long long *status,
-                                                                double *__restrict__ piv, int64_t toff,
+                                                                double *__restrict__ piv,
+                                                                const double *__restrict__ axc,
+                                                                const int64_t *__restrict__ dpos, int64_t toff,
                                                                 const Batch bt) {
   constexpr int TT = TileCfg<TB>::threads;
   constexpr bool F64PIV = std::is_same<T, float>::value;
@@ -509,12 +519,13 @@ __global__ void __launch_bounds__(TileCfg<TB>::threads) k_potrf(const SNode *__r
   const int ts = min(TB, sj.ncols - s * NB);  // a TB < NB launch holds tiles of order <= TB
   T *D = Lx + sj.lx + (int64_t)(s * NB) * sj.nrows + s * NB;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (axc) axc += blockIdx.y * bt.nnz;
   for (int idx = tid; idx < ts * ts; idx += TT) {  // only the lower triangle is read
     int rr = idx % ts, c = idx / ts;
     if (rr >= c) {
       const T v = D[(int64_t)c * sj.nrows + rr];
       a[c][rr] = v;
-      if (F64PIV && rr == c) dd[c] = (double)v;
+      if (F64PIV && rr == c) dd[c] = diag64((float)v, axc, dpos, sj.first + s * NB + c);
     }
   }
   // Row-major packed index of the lower triangle: idx = i (i + 1) / 2 + j. The first
@@ -1274,7 +1285,9 @@ __device__ __forceinline__ void tri_decode(int el, int &a, int &b) {
 template <typename T>
 __global__ void __launch_bounds__(32 * WT_WARPS) k_potrf_w(const SNode *__restrict__ sn, const Int4 *__restrict__ tasks,
                                                            int64_t ntask, T *__restrict__ Lx, long long *status,
-                                                           double *__restrict__ piv, int64_t toff, const Batch bt) {
+                                                           double *__restrict__ piv, const double *__restrict__ axc,
+                                                           const int64_t *__restrict__ dpos, int64_t toff,
+                                                           const Batch bt) {
   constexpr bool F64PIV = std::is_same<T, float>::value;  // FP64 pivot chain of FP32 factors (k_potrf)
   Lx += blockIdx.y * bt.lx;
   status += blockIdx.y;
@@ -1290,11 +1303,12 @@ __global__ void __launch_bounds__(32 * WT_WARPS) k_potrf_w(const SNode *__restri
   T *D = Lx + sj.lx + (int64_t)(s * NB) * sj.nrows + s * NB;
   T *a = tri[w];
   double *dd = ddw[w];
+  if (axc) axc += blockIdx.y * bt.nnz;
   for (int c = 0; c < ts; ++c)
     if (lane >= c && lane < ts) {
       const T v = D[(int64_t)c * sj.nrows + lane];
       a[pk(ts, c, lane)] = v;
-      if (F64PIV && lane == c) dd[c] = (double)v;
+      if (F64PIV && lane == c) dd[c] = diag64((float)v, axc, dpos, sj.first + s * NB + c);
     }
   __syncwarp();
   for (int c = 0; c < ts; ++c) {
@@ -1583,13 +1597,13 @@ cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, co
         // four warps shorten each column step of the tile (latency; 64^2 factor 0.96 -> 0.83 ms)
         if (small && nb > 1)
           e = launch_prio(k_potrf_w<T>, dim3((g + WT_WARPS - 1) / WT_WARPS, nb), 32 * WT_WARPS, 0, s, prio, d.sn,
-                          d.tasks, (int64_t)g, Lx, status, d.piv, L.off, bt);
+                          d.tasks, (int64_t)g, Lx, status, d.piv, d.axc, d.dpos, L.off, bt);
         else if (small)
-          e = launch_prio(k_potrf<T, SMALL_TB>, dim3(g, nb), TS, 0, s, prio, d.sn, d.tasks, Lx, status, d.piv, L.off,
-                          bt);
+          e = launch_prio(k_potrf<T, SMALL_TB>, dim3(g, nb), TS, 0, s, prio, d.sn, d.tasks, Lx, status, d.piv, d.axc,
+                          d.dpos, L.off, bt);
         else
-          e = launch_prio(k_potrf<T, NB>, dim3(g, nb), THREADS, 0, s, prio, d.sn, d.tasks, Lx, status, d.piv, L.off,
-                          bt);
+          e = launch_prio(k_potrf<T, NB>, dim3(g, nb), THREADS, 0, s, prio, d.sn, d.tasks, Lx, status, d.piv, d.axc,
+                          d.dpos, L.off, bt);
         break;
       case K_TRSM:
         // (a warp-per-tile form with the column pairs mapped flat onto the lanes made the

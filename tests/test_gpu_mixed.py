@@ -136,64 +136,89 @@ def dense_matrix(A):
     return w.Matrix(n, Ap, Ai, Ax, np.arange(n, dtype=np.int32))
 
 
-def near_singular(n, target, rng):
-    """B + s I with B = G G^T of rank n - 1, s chosen by bisection (on the oracle's FP64 factor)
-    so that min_k d_k / C_kk is close to target."""
-    G = rng.standard_normal((n, n - 1))
-    Bm = G @ G.T
-    lo, hi = 0.0, 1.0
-    for _ in range(60):
-        s = 0.5 * (lo + hi)
-        M = dense_matrix(Bm + s * np.eye(n))
-        o = oracle.Oracle(M.n, M.Ap, M.Ai, M.perm)
-        assert o.factor(M.Ax) == 0
-        r = oracle_pivot_ratios(o, M).min()
-        if r > target:
-            hi = s
-        else:
-            lo = s
-    return M, o
+def arrow_block(v, s):
+    """The dense matrix [[I, v], [v^T, v.v + s]]: its exact factor is [[I, 0], [v^T, sqrt(s)]], so
+    every pivot is 1 except the last, d = s, and min_k d_k / C_kk = s / (v.v + s). With v
+    representable in FP32 the tile's multipliers are exact, and the FP64 pivot chain (C_nn in
+    FP64, the squares subtracted in FP64) recovers s to FP64 rounding of v.v; an FP32 chain would
+    lose several percent of s in the rounding of C_nn and of the sum of squares (n u32 v.v)."""
+    n = v.size + 1
+    A = np.eye(n)
+    A[-1, :-1] = v
+    A[:-1, -1] = v
+    A[-1, -1] = float(v @ v) + s
+    return dense_matrix(A)
+
+
+def fp32_values(rng, size, lo=0.5, hi=1.0):
+    return rng.uniform(lo, hi, size).astype(np.float32).astype(np.float64)
+
+
+def panel_diagonal(s):
+    """The stored diagonal L_kk of the factor (permuted order), from its panels."""
+    sup, rowptr, lxptr = s.export("super"), s.export("rowptr"), s.export("lxptr")
+    Lx = s.factor_panels()
+    d = np.empty(int(sup[-1]))
+    for J in range(sup.size - 1):
+        f, l = int(sup[J]), int(sup[J + 1])
+        nr = int(rowptr[J + 1] - rowptr[J])
+        panel = Lx[lxptr[J]:lxptr[J + 1]].reshape(l - f, nr)
+        d[f:l] = panel[np.arange(l - f), np.arange(l - f)]
+    return d
 
 
 @pytest.mark.parametrize("maker", [lambda: w.cfg("laplace2d5_64"),
                                    lambda: w.conduct3d(12, np.random.default_rng(4), "box"),
                                    lambda: w.vector3d27(10, np.random.default_rng(6), sub=3)])
 def test_pivot_ratio_matches_oracle_and_flag_clear(torch_cuda, maker):
-    """Well-conditioned and coefficient-jump cases (the latter with jumps 1 / 1e2 / 1e4): the FP64
-    pivots of the FP32 factor give min d_k / C_kk within FP32 accuracy of the oracle's exact
-    ratio, at a column whose exact ratio is that small, and the breakdown flag stays clear."""
+    """Well-conditioned and coefficient-jump cases (the last with jumps 1 / 1e2 / 1e4):
+    - the reported minimum is min_k L_kk^2 / C_kk of the factor's own stored diagonal (the FP64
+      pivot rounded once to FP32 by its square root: within 2^-22 relative), at that column;
+    - it agrees with the oracle's exact ratio within the FP32 factor's forward-error bound:
+      |L_kk - L*_kk| <= delta = 5e-4 max|L| (the bound the tensor-core factor tests use) gives
+      |ratio_k - ratio*_k| <= (2 L*_kk delta + delta^2) / C_kk;
+    - the breakdown flag stays clear."""
     torch = torch_cuda
     import paper_1705_06575_gb300 as S
     M = maker()
     s = S.Solver(M.n, M.Ap, M.Ai, M.perm, precision="mixed")
     s.factor(torch.from_numpy(M.Ax).cuda())
     r, col, bd = s.pivot_info()
+    assert not bd
+    perm = s.export("perm")
+    ckk = M.Ax[M.Ap[:-1]][perm]
+    own = panel_diagonal(s) ** 2 / ckk
+    k = int(np.nonzero(perm == col)[0][0])  # the reported column in permuted numbering
+    assert abs(r - own.min()) <= 5e-7 * own.min() and abs(own[k] - r) <= 5e-7 * r
     o = oracle.Oracle(M.n, M.Ap, M.Ai, M.perm)
     assert o.factor(M.Ax) == 0
-    ratios = oracle_pivot_ratios(o, M)
-    rmin = ratios.min()
-    tol = 1e-3 * rmin + 1e-5
-    assert abs(r - rmin) <= tol, (r, rmin)
-    k = int(np.nonzero(o.perm == col)[0][0])  # the reported column in permuted numbering
-    assert ratios[k] <= rmin + 2 * tol
-    assert not bd
+    exact = oracle_pivot_ratios(o, M)
+    delta = 5e-4 * np.abs(o.Lx).max()
+    lkk = o.Lx[o.Lp[:-1]]
+    bound = float(np.max((2 * lkk * delta + delta ** 2) / ckk))
+    assert abs(r - exact.min()) <= bound, (r, exact.min(), bound)
 
 
-def test_pivot_breakdown_flag_on_near_singular_matrix(torch_cuda):
-    """A dense 48 x 48 matrix shifted just off singularity (exact min d_k / C_kk = 3e-6, below the
-    default threshold 2^-16): the FP64 pivot chain reports a ratio close to the exact one, the
-    flag trips, the FP64 refinement still reaches the backward-error bound, and a lower
-    threshold clears the flag."""
+@pytest.mark.parametrize("n", [48, 64])
+def test_pivot_breakdown_flag_on_near_singular_matrix(torch_cuda, n):
+    """A dense matrix one pivot away from singular (exact ratio s / C_nn = 3e-6, below the
+    default threshold 2^-16): the FP64 pivot chain of the FP32 factor reports the exact ratio to
+    FP64 rounding of v.v relative to s (1e-8; an FP32 chain is off by percents here), flags
+    breakdown at the last column, the FP64 refinement still reaches the backward-error bound, and
+    a lower threshold clears the flag."""
     torch = torch_cuda
     import paper_1705_06575_gb300 as S
-    M, o = near_singular(48, 3e-6, np.random.default_rng(21))
-    rmin = oracle_pivot_ratios(o, M).min()
+    v = fp32_values(np.random.default_rng(21 + n), n - 1)
+    vv = float(v @ v)
+    sh = 3e-6 * vv / (1 - 3e-6)
+    M = arrow_block(v, sh)
+    exact = sh / (vv + sh)
     s = S.Solver(M.n, M.Ap, M.Ai, M.perm, precision="mixed")
     s.set_refinement(1e-12, 300)
     s.factor(torch.from_numpy(M.Ax).cuda())
     r, col, bd = s.pivot_info()
-    assert bd
-    assert abs(r - rmin) <= 0.3 * rmin, (r, rmin)
+    assert bd and col == n - 1
+    assert abs(r - exact) <= 1e-8 * exact, (r, exact)
     B, X = solve_refined(torch, s, M, 1, seed=3)
     assert oracle.backward_error(M.n, M.Ap, M.Ai, M.Ax, B, X) <= REFINED_BERR
     S.sym_set_pivot_threshold(s.h, 1e-7)
@@ -202,21 +227,20 @@ def test_pivot_breakdown_flag_on_near_singular_matrix(torch_cuda):
 
 def test_pivot_ratio_per_matrix_of_a_batch(torch_cuda):
     """A batch of two 24 x 24 dense matrices (diagonal tiles of order <= 32: the warp-per-tile
-    POTRF with its own FP64 pivot chain): the near-singular one is flagged, the other is not,
-    each with its own ratio."""
+    POTRF with its own FP64 pivot chain): the near-singular one is flagged at its last column,
+    the well-conditioned one is not; each ratio matches its exact value."""
     torch = torch_cuda
     import paper_1705_06575_gb300 as S
-    M1, o1 = near_singular(24, 2e-6, np.random.default_rng(22))
-    G = np.random.default_rng(23).standard_normal((24, 24))
-    M2 = dense_matrix(G @ G.T + 24 * np.eye(24))
-    o2 = oracle.Oracle(M2.n, M2.Ap, M2.Ai, M2.perm)
-    assert o2.factor(M2.Ax) == 0
+    v = fp32_values(np.random.default_rng(22), 23)
+    vv = float(v @ v)
+    sh = 2e-6 * vv / (1 - 2e-6)
+    M1 = arrow_block(v, sh)
+    M2 = arrow_block(v, 4.0 * vv)  # last pivot 4 v.v: ratio 0.8; the others 1
     s = S.Solver(M1.n, M1.Ap, M1.Ai, M1.perm, precision="mixed")
     vals = torch.from_numpy(np.stack([M1.Ax, M2.Ax])).cuda()
     S.sym_factor_batch(s.h, 2, vals, M1.nnz)
-    r1, _, bd1 = S.sym_pivot_info(s.h, 0)
-    r2, _, bd2 = S.sym_pivot_info(s.h, 1)
-    e1 = oracle_pivot_ratios(o1, M1).min()
-    e2 = oracle_pivot_ratios(o2, M2).min()
-    assert bd1 and not bd2
-    assert abs(r1 - e1) <= 0.3 * e1 and abs(r2 - e2) <= 1e-4 * e2, (r1, e1, r2, e2)
+    r1, c1, bd1 = S.sym_pivot_info(s.h, 0)
+    r2, c2, bd2 = S.sym_pivot_info(s.h, 1)
+    assert bd1 and c1 == 23 and not bd2 and c2 == 23
+    assert abs(r1 - sh / (vv + sh)) <= 1e-8 * r1
+    assert abs(r2 - 0.8) <= 1e-6
