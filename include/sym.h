@@ -44,6 +44,17 @@ extern "C" {
 /* Orderings for sym_analyze_perm. */
 #define SYM_ORDER_NATURAL 0 /* identity (then etree postorder) */
 #define SYM_ORDER_GIVEN 1   /* the caller's perm (then etree postorder) */
+#define SYM_ORDER_AUTO 2    /* computed from the pattern alone (the paper takes the ordering as
+                               given; this is the library's addition): an approximate minimum-degree
+                               ordering (quotient graph, supervariables, element absorption and the
+                               approximate external degree of Amestoy, Davis and Duff) and a nested
+                               dissection by breadth-first level structures (George and Liu; parts
+                               of at most 96 nodes by minimum degree) are both computed and the one
+                               whose factor has fewer flops (sum c_j^2) is kept; then etree
+                               postorder. perm is ignored. */
+/* How the ordering of a handle was obtained (sym_stats.ordering_method). */
+#define SYM_ORDER_METHOD_MD 3 /* SYM_ORDER_AUTO chose minimum degree */
+#define SYM_ORDER_METHOD_ND 4 /* SYM_ORDER_AUTO chose nested dissection */
 
 /* Precision of the factor (sym_options.precision). */
 #define SYM_PREC_FP64 0  /* FP64 factor and FP64 solves (the plain path) */
@@ -105,6 +116,10 @@ typedef struct {
   double update_flops;      /* the part of `flops` that descendant updates (SYM_KIND_UPDATE)
                                carry: column k updates column j in another supernode with
                                2 |{i in L_k : i >= j}| flops, summed over the exact pattern */
+  int32_t ordering_method;  /* SYM_ORDER_NATURAL, SYM_ORDER_GIVEN, SYM_ORDER_METHOD_MD or _ND */
+  int32_t reserved0;
+  double ordering_flops_md; /* SYM_ORDER_AUTO: factor flops under minimum degree, else 0 */
+  double ordering_flops_nd; /* SYM_ORDER_AUTO: factor flops under nested dissection, else 0 */
 } sym_stats;
 
 /* Fill *opt with the defaults (SYM_ORDER_GIVEN with a NULL perm means natural order). */

@@ -39,6 +39,9 @@ SYM_PREC_FP64 = 0
 SYM_PREC_MIXED = 1
 SYM_ORDER_NATURAL = 0
 SYM_ORDER_GIVEN = 1
+SYM_ORDER_AUTO = 2
+SYM_ORDER_METHOD_MD = 3
+SYM_ORDER_METHOD_ND = 4
 SYM_FLAG_HOST_ONLY = 1
 SYM_FLAG_NO_GRAPHS = 2
 SYM_FLAG_ONE_STREAM = 4
@@ -77,7 +80,9 @@ class sym_stats(ct.Structure):
                 ("max_ncols", ct.c_int32), ("npairs", ct.c_int64), ("nlaunch_factor", ct.c_int64),
                 ("nlaunch_solve", ct.c_int64), ("analyze_seconds", ct.c_double),
                 ("device_bytes", ct.c_int64), ("upd_tasks", ct.c_int64), ("upd_entries", ct.c_int64),
-                ("dense_tasks", ct.c_int64), ("exec_flops", ct.c_double), ("update_flops", ct.c_double)]
+                ("dense_tasks", ct.c_int64), ("exec_flops", ct.c_double), ("update_flops", ct.c_double),
+                ("ordering_method", ct.c_int32), ("reserved0", ct.c_int32), ("ordering_flops_md", ct.c_double),
+                ("ordering_flops_nd", ct.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -476,7 +481,9 @@ def sym_free(h):
 class Solver:
     """Owning wrapper of one handle: analyze on construction, free on close."""
 
-    def __init__(self, n, Ap, Ai, perm=None, opt=None, host_only=False, precision=None, flags=0):
+    def __init__(self, n, Ap, Ai, perm=None, opt=None, host_only=False, precision=None, flags=0, ordering=None):
+        """perm: a fill-reducing ordering (SYM_ORDER_GIVEN); ordering="auto" lets the inspector
+        compute one (SYM_ORDER_AUTO)."""
         if opt is None:
             opt = sym_options_default()
         opt.flags |= int(flags)
@@ -484,6 +491,9 @@ class Solver:
             opt.precision = SYM_PREC_MIXED if precision in ("mixed", SYM_PREC_MIXED) else SYM_PREC_FP64
         if perm is not None:
             opt.ordering = SYM_ORDER_GIVEN
+        if ordering in ("auto", SYM_ORDER_AUTO):
+            opt.ordering = SYM_ORDER_AUTO
+            perm = None
         if host_only:
             opt.flags |= SYM_FLAG_HOST_ONLY
         self.n = int(n)

@@ -15,8 +15,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libsym.so")
-SOURCES = ["symbolic.cpp", "reach.cpp", "kernels.cu", "tc_update.cu", "capi.cu", "probe.cu", "noalloc.cu", "refine.cu", "mlp.cu"]
-HEADERS = ["plan.h", "kernels.h", "refine.h", "reach.h", "tc.cuh"]
+SOURCES = ["symbolic.cpp", "ordering.cpp", "reach.cpp", "kernels.cu", "tc_update.cu", "capi.cu", "probe.cu", "noalloc.cu", "refine.cu", "mlp.cu"]
+HEADERS = ["plan.h", "kernels.h", "refine.h", "reach.h", "tc.cuh", "ordering.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -411,7 +411,7 @@ int sym_analyze_perm(int64_t n, const int64_t *Ap, const int32_t *Ai, const int3
   sym_options opt;
   if (opt_in) opt = *opt_in;
   else sym_options_default(&opt);
-  if (opt.ordering != SYM_ORDER_NATURAL && opt.ordering != SYM_ORDER_GIVEN)
+  if (opt.ordering != SYM_ORDER_NATURAL && opt.ordering != SYM_ORDER_GIVEN && opt.ordering != SYM_ORDER_AUTO)
     return fail(SYM_ERR_INVALID, "unknown ordering");
   if (opt.precision != SYM_PREC_FP64 && opt.precision != SYM_PREC_MIXED)
     return fail(SYM_ERR_INVALID, "unknown precision");
@@ -881,6 +881,9 @@ int sym_info(sym_handle h, sym_stats *s) {
   s->exec_flops = 0.0;
   for (int k = sym::K_SCATTER; k <= sym::K_TRTRI; ++k) s->exec_flops += P.kind_flops[k];
   s->update_flops = P.update_flops;
+  s->ordering_method = P.ordering_method;
+  s->ordering_flops_md = P.ordering_flops[0];
+  s->ordering_flops_nd = P.ordering_flops[1];
   return SYM_OK;
 }
 

@@ -170,6 +170,10 @@ struct Plan {
   // Useful flops of the external updates (K_UPDATE) on the exact pattern of L: the share of the
   // factor's sum of c_j^2 that descendant updates carry (no explicit zeros of amalgamation).
   double update_flops = 0.0;
+  // How the ordering was obtained (SYM_ORDER_NATURAL, SYM_ORDER_GIVEN, SYM_ORDER_METHOD_MD or
+  // SYM_ORDER_METHOD_ND) and, for SYM_ORDER_AUTO, the flops of both candidates.
+  int32_t ordering_method = SYM_ORDER_NATURAL;
+  double ordering_flops[2] = {0.0, 0.0};
 
   int32_t nsuper() const { return (int32_t)super.size() - 1; }
   int64_t storage() const { return lxptr.empty() ? 0 : lxptr.back(); }

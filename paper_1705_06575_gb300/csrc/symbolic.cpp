@@ -12,6 +12,7 @@
 #include <functional>
 #include <numeric>
 
+#include "ordering.h"
 #include "plan.h"
 
 namespace sym {
@@ -136,6 +137,32 @@ void build_permuted_csr(const int64_t *Ap, const int32_t *Ai, Plan &P) {
     }
 }
 
+namespace {
+// Flops sum_j c_j^2 of the factor of A permuted by p0 (etree of that ordering, then column counts
+// by row subtrees; the fill does not depend on the etree postorder applied later).
+double ordering_flops(int64_t n, const int64_t *Ap, const int32_t *Ai, const std::vector<int32_t> &p0) {
+  std::vector<int32_t> ip(n);
+  for (int64_t k = 0; k < n; ++k) ip[p0[k]] = (int32_t)k;
+  std::vector<int64_t> rp;
+  std::vector<int32_t> rj, parent;
+  rows_of_permuted(n, Ap, Ai, ip, rp, rj);
+  etree_liu(n, rp, rj, parent);
+  std::vector<int64_t> cc(n, 1);
+  std::vector<int32_t> mark(n, -1);
+  for (int64_t i = 0; i < n; ++i) {
+    mark[i] = (int32_t)i;
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p)
+      for (int32_t j = rj[p]; mark[j] != i; j = parent[j]) {
+        mark[j] = (int32_t)i;
+        cc[j]++;
+      }
+  }
+  double f = 0.0;
+  for (int64_t j = 0; j < n; ++j) f += (double)cc[j] * (double)cc[j];
+  return f;
+}
+}  // namespace
+
 int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm_in,
             const sym_options &opt, Plan &P, std::string &err) {
   Timer timer;
@@ -144,10 +171,27 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
   P.n = n;
   P.nnz_a = Ap[n];
 
-  // 1. Given ordering.
+  // 1. Given ordering, or (SYM_ORDER_AUTO) the better of minimum degree and nested dissection
+  //    by the flops of the factor each produces.
   std::vector<int32_t> p0(n), ip0(n, -1);
+  std::vector<int32_t> automatic;
+  P.ordering_method = opt.ordering == SYM_ORDER_GIVEN && perm_in ? SYM_ORDER_GIVEN : SYM_ORDER_NATURAL;
+  if (opt.ordering == SYM_ORDER_AUTO && n > 0) {
+    std::vector<int64_t> xadj;
+    std::vector<int32_t> adj, pmd, pnd;
+    pattern_graph(n, Ap, Ai, xadj, adj);
+    order_min_degree(n, xadj, adj, pmd);
+    order_nested_dissection(n, xadj, adj, pnd);
+    const double fmd = ordering_flops(n, Ap, Ai, pmd), fnd = ordering_flops(n, Ap, Ai, pnd);
+    P.ordering_flops[0] = fmd;
+    P.ordering_flops[1] = fnd;
+    const bool nd = fnd < fmd;
+    automatic.swap(nd ? pnd : pmd);
+    P.ordering_method = nd ? SYM_ORDER_METHOD_ND : SYM_ORDER_METHOD_MD;
+  }
   for (int64_t k = 0; k < n; ++k) {
-    int32_t v = (opt.ordering == SYM_ORDER_GIVEN && perm_in) ? perm_in[k] : (int32_t)k;
+    int32_t v = !automatic.empty() ? automatic[k]
+                : (opt.ordering == SYM_ORDER_GIVEN && perm_in) ? perm_in[k] : (int32_t)k;
     if (v < 0 || v >= n || ip0[v] != -1) { err = "perm is not a permutation"; return SYM_ERR_INVALID; }
     p0[k] = v;
     ip0[v] = (int32_t)k;

@@ -255,3 +255,26 @@ def test_conduct3d7_64_full_size(torch_cuda):
     benchmark times: leading 20000 columns entry-wise against the oracle, the leading-block
     factor residual, and the backward error of all four solves."""
     check_matrix(torch_cuda, w.cfg("conduct3d7_64"), nrhs=4, kmax=20000, solve_oracle=False)
+
+
+@pytest.mark.parametrize("maker", [lambda r: w.erdos_renyi(3000, 8, r), lambda r: w.conduct3d(18, r, "star")])
+def test_auto_ordering_factor_and_solve(torch_cuda, maker):
+    """The inspector's own ordering (SYM_ORDER_AUTO) on a graph without geometry and on a grid:
+    the factor entry-wise against the oracle run with the same final permutation, and the solve."""
+    torch = torch_cuda
+    S = _lib()
+    M = maker(np.random.default_rng(31))
+    s = S.Solver(M.n, M.Ap, M.Ai, ordering="auto")
+    perm = s.export("perm")
+    o = oracle.Oracle(M.n, M.Ap, M.Ai, perm)
+    assert np.array_equal(s.export("super"), o.sn)
+    s.factor(torch.from_numpy(M.Ax).cuda())
+    assert o.factor(M.Ax) == 0
+    vals, outside = panels_on_pattern(exports(s), s.factor_panels(), o.Lp, o.Li)
+    assert outside == 0.0
+    assert np.abs(vals - o.Lx).max() <= ENTRY_RTOL * np.abs(o.Lx).max()
+    assert o.factor_residual_with(M.Ax, vals) <= FACTOR_TOL
+    B = w.rhs(M.n, 2, np.random.default_rng(2))
+    X = s.solve_host(B)
+    assert oracle.backward_error(M.n, M.Ap, M.Ai, M.Ax, B, X) <= BERR_TOL
+    s.close()

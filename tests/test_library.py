@@ -235,3 +235,62 @@ def test_update_flops_split_of_sum_c_squared(maker):
         total += int(np.sum(2 * (c - t)[ext]))
     assert info.update_flops == total
     assert info.update_flops < info.flops == o.flops_exact
+
+
+def _auto(M):
+    return S.Solver(M.n, M.Ap, M.Ai, flags=S.SYM_FLAG_HOST_ONLY, ordering="auto")
+
+
+@pytest.mark.parametrize("maker", [lambda r: w.laplace2d5(40, r), lambda r: w.conduct3d(14, r, "star"),
+                                   lambda r: w.conduct3d(10, r, "box"), lambda r: w.dd2d9(40, r),
+                                   lambda r: w.erdos_renyi(1500, 6, r), lambda r: w.random_spd_pattern(400, 0.01, r)])
+def test_auto_ordering_symbolic_bit_exact(maker):
+    """SYM_ORDER_AUTO yields a permutation; given that permutation, the independent oracle
+    reproduces every integer output of the inspector bit for bit."""
+    M = maker(np.random.default_rng(71))
+    s = _auto(M)
+    info = s.info()
+    perm = s.export("perm")
+    assert np.array_equal(np.sort(perm), np.arange(M.n))
+    assert info.ordering_method in (S.SYM_ORDER_METHOD_MD, S.SYM_ORDER_METHOD_ND)
+    assert info.flops == min(info.ordering_flops_md, info.ordering_flops_nd)
+    o = oracle.Oracle(M.n, M.Ap, M.Ai, perm, want_rel=True)
+    for mine, theirs in PAIRS:
+        a = s.export(mine)
+        b = getattr(o, theirs)
+        assert np.array_equal(a, b), mine
+
+
+def test_auto_ordering_fill_against_references():
+    """Fill (nnz(L)) of the automatic ordering: on 2D and 3D stencil grids at most 1.5x that of the
+    geometric nested dissection the workloads use, and on Erdos-Renyi graphs (no geometry) below
+    that of reverse Cuthill-McKee."""
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import reverse_cuthill_mckee
+    rng = np.random.default_rng(73)
+    for M in (w.laplace2d5(96, rng), w.dd2d9(64, rng), w.conduct3d(24, rng, "star"), w.conduct3d(16, rng, "box")):
+        auto = _auto(M).info().nnz_l
+        geom = S.Solver(M.n, M.Ap, M.Ai, M.perm, flags=S.SYM_FLAG_HOST_ONLY).info().nnz_l
+        assert auto <= 1.5 * geom, (auto, geom)
+    for n, d in ((3000, 4), (3000, 12)):
+        M = w.erdos_renyi(n, d, rng)
+        L = sp.csc_matrix((M.Ax, M.Ai, M.Ap), shape=(n, n))
+        rcm = reverse_cuthill_mckee((L + L.T).tocsr(), symmetric_mode=True).astype(np.int32)
+        auto = _auto(M).info().nnz_l
+        ref = S.Solver(M.n, M.Ap, M.Ai, rcm, flags=S.SYM_FLAG_HOST_ONLY).info().nnz_l
+        assert auto < ref, (auto, ref)
+
+
+def test_auto_ordering_special_structures():
+    """Degenerate patterns: empty, diagonal (no edges), a path, and a dense matrix."""
+    s = S.Solver(0, np.zeros(1, np.int64), np.zeros(0, np.int32), flags=S.SYM_FLAG_HOST_ONLY, ordering="auto")
+    assert s.info().n == 0
+    n = 50
+    diag = _auto(w.Matrix(n, np.arange(n + 1, dtype=np.int64), np.arange(n, dtype=np.int32), np.ones(n)))
+    assert diag.info().nnz_l == n
+    u = np.arange(n - 1)
+    Ap, Ai, Ax = w.lower_csc(n, u, u + 1, -np.ones(n - 1), 3 * np.ones(n))
+    path = _auto(w.Matrix(n, Ap, Ai, Ax)).info()
+    assert path.nnz_l == 2 * n - 1  # a path orders without fill
+    M = w.random_spd_pattern(40, 1.0, np.random.default_rng(3))
+    assert _auto(M).info().nnz_l == 40 * 41 // 2
