@@ -478,6 +478,24 @@ def bench_conduct27(S, torch, stream):
     return {"ms": ms, "gflops": info.flops / (ms * 1e-3) / 1e9, "berr": berr}
 
 
+def bench_auto_order(S, torch, M, B, stream):
+    """The benchmark matrix under the inspector's own ordering (SYM_ORDER_AUTO) instead of the
+    geometric nested dissection: analysis time, factor flops, and FP64 factor + 4-RHS solve."""
+    t0 = time.perf_counter()
+    s = S.Solver(M.n, M.Ap, M.Ai, ordering="auto")
+    analyze_s = time.perf_counter() - t0
+    s.set_stream(stream)
+    info = s.info()
+    Ax = torch.from_numpy(M.Ax).cuda()
+    Bt = torch.from_numpy(np.ascontiguousarray(B.T)).cuda()
+    Xt = torch.empty_like(Bt)
+    ms = _event_ms(torch, stream, lambda: (s.factor(Ax), S.sym_solve_multi(s.h, NRHS, Bt, M.n, Xt, M.n)), 5)
+    berr = backward_error(M, B, Xt.cpu().numpy().T)
+    s.close()
+    return {"ms": ms, "flops": info.flops, "gflops": info.flops / (ms * 1e-3) / 1e9, "analyze_s": analyze_s,
+            "method": "nd" if info.ordering_method == S.SYM_ORDER_METHOD_ND else "md", "berr": berr}
+
+
 def bench_sparse_rhs(S, torch, s, M, args, stream):
     """Forward solve L y = P b for sparse b over the reach set (VI-Prune + VS-Block) on the
     benchmark matrix: b = one column of A (a local source) and b with 1% random nonzeros, each
@@ -635,6 +653,7 @@ def run_ours(args):
             variants["batch_512x128sq"], detail["batch_kernels"] = bench_batched(S, torch, args, stream, barrier,
                                                                                  world)
         variants["sparse_rhs"] = bench_sparse_rhs(S, torch, s, M, args, stream)
+        variants["auto_order_64"] = bench_auto_order(S, torch, M, B, stream)
         for key, fn in (("lat_64sq", bench_small_latency), ("uneven_256", bench_uneven_batch),
                         ("uneven_256_mixed", lambda S_, t_, st_: bench_uneven_batch(S_, t_, st_, "mixed")),
                         ("c27_40", bench_conduct27), ("vec48_mixed", bench_mixed_vector)):

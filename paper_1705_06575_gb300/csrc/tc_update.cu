@@ -2,16 +2,19 @@
 //
 // The left-looking update of Sec. 3.2 restricted to one 64 x 64 tile (bi, bj) of supernode J:
 // for every descendant entry, C -= L_K(R1, :) L_K(R0, :)^T scattered through the relative maps.
-// Here each entry's two operands are expanded to the tile's coordinates while they are staged in
-// shared memory (row a of the entry lands at tile row rel(a); rows the entry does not touch are
-// zero), so every entry of the tile accumulates in the tile's coordinates: in tensor memory for
-// a few chunks at a time, then in FP32 registers, and the tile is written once.
+// Each entry is a compact GEMM: its m rows R1 and n rows R0 are contiguous rows of K's panel, so
+// they are staged as they are (rows 0..m-1 and 0..n-1 of the operands) from K's TF32 split copy,
+// which the TRSM kernels wrote once, transposed (each row's k values contiguous) and already
+// split, when K's panel became final. The tensor core forms the m x n product in tensor memory;
+// the relative maps are applied only on the way out, when the product is subtracted from the
+// tile, which sits in shared memory for the whole CTA and is written back once.
 //
 // Precision. An FP32 value x is split into two TF32 values hi = tf32(x) and lo = tf32(x - hi)
 // (|x - hi - lo| <= 2^-22 |x|). The A operand is staged as the 128-row matrix [A_hi; A_lo] and
-// multiplied by B_hi and by B_lo (two M = 128, N = 64, K = 8 MMAs per step): rows 0-63 of the
-// accumulator receive A_hi B^T, rows 64-127 A_lo B^T, and their sum is A B^T with all four
-// partial products, each formed exactly.
+// multiplied by B_hi and by B_lo (two M = 128, K = 8 MMAs per step, N = n rounded up to 16):
+// accumulator rows 0-63 receive A_hi B^T, rows 64-127 A_lo B^T, all four partial products formed
+// exactly. Sums run in tensor memory over at most SEG chunks of 32 values of k and are then
+// added in FP32 registers (a long sum inside the tensor core loses accuracy), as in the SIMT form.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -23,13 +26,15 @@ namespace sym {
 namespace {
 
 constexpr int TC_THREADS = 128;
-constexpr uint32_t A_BYTES = 128 * tc::KC * 4;  // [A_hi; A_lo]: 16 KB
-constexpr uint32_t B_BYTES = 64 * tc::KC * 4;   // B_hi or B_lo: 8 KB
+constexpr int KC = tc::KC;                      // values of k per staged chunk (32)
+constexpr uint32_t A_BYTES = 128 * KC * 4;      // [A_hi; A_lo]: 16 KB
+constexpr uint32_t B_BYTES = 64 * KC * 4;       // B_hi or B_lo: 8 KB
 constexpr uint32_t STAGE_BYTES = A_BYTES + 2 * B_BYTES;
 constexpr int NSTAGE = 2;
-constexpr size_t SMEM_BYTES = NSTAGE * STAGE_BYTES + 128;  // + room to align the stages to 128 B
-constexpr uint32_t TMEM_COLS = 2 * NB;  // two FP32 accumulators of 128 x 64
-constexpr uint32_t IDESC = tc::idesc_tf32<128, 64>();
+constexpr int TILE_LD = NB + 1;                 // the tile in shared memory, [col][row]
+constexpr size_t SMEM_BYTES = NSTAGE * STAGE_BYTES + 128 + sizeof(float) * NB * TILE_LD;
+constexpr uint32_t TMEM_COLS = 2 * NB;          // two FP32 accumulators of 128 x 64
+constexpr int SEG = 8;                          // chunks per tensor-memory sum
 
 __device__ __forceinline__ int64_t tile_base(int32_t i, int32_t ncols, int32_t ncb) {
   return i < ncb ? (int64_t)i * NB : (int64_t)ncols + (int64_t)(i - ncb) * NB;
@@ -40,93 +45,85 @@ __device__ __forceinline__ int tile_rows(int32_t i, int32_t ncols, int32_t nrows
   return (int)(r < NB ? r : NB);
 }
 
-// Four consecutive k values (k0 + 4 kq ..) of panel row `row` of K (column-major, ld nrows),
-// zero past kc or when the tile position has no row of the entry (row < 0).
-__device__ __forceinline__ float4 load4(const float *Kp, int64_t ld, int row, int k0, int k, int kc) {
-  float v[4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) v[i] = (row >= 0 && k + i < kc) ? Kp[(int64_t)(k0 + k + i) * ld + row] : 0.f;
-  return make_float4(v[0], v[1], v[2], v[3]);
-}
-__device__ __forceinline__ void split_store(uint8_t *hi_buf, uint8_t *lo_buf, uint32_t o, float4 x) {
-  const float4 h = make_float4(tc::to_tf32(x.x), tc::to_tf32(x.y), tc::to_tf32(x.z), tc::to_tf32(x.w));
-  const float4 l = make_float4(tc::to_tf32(x.x - h.x), tc::to_tf32(x.y - h.y), tc::to_tf32(x.z - h.z),
-                               tc::to_tf32(x.w - h.w));
-  *reinterpret_cast<float4 *>(hi_buf + o) = h;
-  *reinterpret_cast<float4 *>(lo_buf + o) = l;
+// kind::tf32 instruction descriptor with M = 128 and n rounded up to a multiple of 16.
+__device__ __forceinline__ uint32_t idesc_for(int n) {
+  const uint32_t N = (uint32_t)((n + 15) & ~15);
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((N >> 3) << 17) | ((128u >> 4) << 24);
 }
 
-// Entries are taken in batches of EB: their descriptors and inverse row maps (tile position ->
-// entry row, or -1) are loaded into shared memory first, so that the operand loads of the next
-// chunk depend on shared memory only and can be issued while the current chunk is staged.
+__device__ __forceinline__ void cp_async16(uint32_t saddr, const void *g) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Entries are taken in batches of EB: their descriptors and relative maps are loaded into shared
+// memory first, so that staging and the output side depend on shared memory only.
 constexpr int EB = 32;
-
 struct EntryBatch {
-  int64_t kp[EB];                       // offset of K's panel in Lx
-  int32_t ld[EB], kc[EB], rlo[EB], clo[EB];
-  int8_t inv_r[EB][NB], inv_c[EB][NB];  // tile row / column position -> entry row, or -1
+  int64_t a_off[EB];   // offset of the entry's first R1 row in K's split copies
+  int64_t b_off[EB];   // offset of its first R0 row
+  int32_t pitch[EB];   // row length of K's split copies
+  int32_t nch[EB];     // chunks of KC values of k
+  int32_t m[EB], n[EB];
+  int8_t prow[EB][NB], pcol[EB][NB];  // tile row / column of the entry's row a / column b
 };
 
-// Operand values of one chunk for this thread: tile position p, k = 4 (kq0 + 2 j) + i.
-struct Prefetch {
-  float a[4][4], b[4][4];
-};
-__device__ __forceinline__ void fetch(Prefetch &f, const float *__restrict__ Lx, const EntryBatch &eb, int i, int k0,
-                                      int p, int kq0) {
-  const int ar = eb.inv_r[i][p], bc = eb.inv_c[i][p];
-  const int64_t ld = eb.ld[i];
-  const int rem = eb.kc[i] - k0;
-  const float *pa = Lx + eb.kp[i] + (int64_t)k0 * ld + eb.rlo[i] + max(ar, 0);
-  const float *pb = Lx + eb.kp[i] + (int64_t)k0 * ld + eb.clo[i] + max(bc, 0);
-  if (rem >= tc::KC) {  // a whole chunk: only the row predicates
-#pragma unroll
-    for (int j = 0; j < tc::KC / 8; ++j)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int k = 4 * (kq0 + 2 * j) + q;
-        f.a[j][q] = ar >= 0 ? pa[k * ld] : 0.f;
-        f.b[j][q] = bc >= 0 ? pb[k * ld] : 0.f;
-      }
-  } else {
-#pragma unroll
-    for (int j = 0; j < tc::KC / 8; ++j)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int k = 4 * (kq0 + 2 * j) + q;
-        f.a[j][q] = (ar >= 0 && k < rem) ? pa[k * ld] : 0.f;
-        f.b[j][q] = (bc >= 0 && k < rem) ? pb[k * ld] : 0.f;
-      }
+// Issue the copies of chunk c of entry i into a stage: rows of [A_hi; A_lo] and B_hi, B_lo, in
+// 16-byte units (4 values of k), each landing in its K-major core-matrix position.
+__device__ __forceinline__ void stage_chunk(uint8_t *stage, const float *__restrict__ shi,
+                                            const float *__restrict__ slo, const EntryBatch &eb, int i, int c,
+                                            int tid) {
+  const uint32_t A = tc::smem_addr(stage), Bh = A + A_BYTES, Bl = Bh + B_BYTES;
+  const int m = eb.m[i], n = eb.n[i];
+  const int64_t k0 = (int64_t)c * KC;
+  // A: 2 m rows x 8 units (hi rows 0..m-1, lo rows 64..64+m-1); B: 2 n rows x 8 units
+  const int ua = 2 * m * 8, ub = 2 * n * 8;
+  for (int u = tid; u < ua + ub; u += TC_THREADS) {
+    if (u < ua) {
+      const int half = u / (m * 8), v = u - half * m * 8, r = v >> 3, q = v & 7;
+      const float *src = (half ? slo : shi) + eb.a_off[i] + (int64_t)r * eb.pitch[i] + k0 + 4 * q;
+      cp_async16(A + tc::off(r + 64 * half, 4 * q), src);
+    } else {
+      const int w = u - ua, half = w / (n * 8), v = w - half * n * 8, r = v >> 3, q = v & 7;
+      const float *src = (half ? slo : shi) + eb.b_off[i] + (int64_t)r * eb.pitch[i] + k0 + 4 * q;
+      cp_async16((half ? Bl : Bh) + tc::off(r, 4 * q), src);
+    }
   }
 }
 
-// One CTA (4 warps) per tile, three CTAs per SM. Thread 0 issues the MMAs; all threads stage
-// operands, two stages deep: the loads of chunk c + 1 are in flight while chunk c is converted
-// and stored, and the MMAs of chunk c run while chunk c + 1 is staged.
-//
-// Accumulation. The tensor core accumulates into tensor memory; the MMAs of SEG consecutive
-// chunks (one segment, across entry boundaries: every entry lands in the tile's coordinates) go
-// to one of two accumulators, which is then read back and added to FP32 registers (each thread
-// owns one accumulator row: warps 0-1 the A_hi rows, warps 2-3 the A_lo rows) while the next
-// segment runs on the other accumulator. Long sums are thus rounded to nearest in FP32 as in the
-// SIMT form; inside the tensor core a sum runs over at most 8 SEG K = 8 steps.
-// A wait that runs out (wait_ns, about a second by default) records -1 in *status and leaves the
-// tile unwritten. withhold != 0 (a failure-path test) issues no MMA and no commit, so the first
-// wait runs out; nothing is then in flight when the tensor memory is freed.
-constexpr int SEG = 8;
-
-__global__ void __launch_bounds__(TC_THREADS, 3) k_update_tc(const SNode *__restrict__ sn,
+// One CTA (4 warps) per tile, two CTAs per SM. Every thread stages, thread 0 issues the MMAs, all
+// threads read the accumulators back. The tile's chunks (every entry's chunks in entry order)
+// form one sequence: the copies of chunk c + 1 are in flight while the MMAs of chunk c run.
+// A segment (at most SEG chunks of one entry) accumulates in one of two tensor-memory
+// accumulators; once the MMAs of the next segment are issued, the finished segment is read back
+// into FP32 registers (each thread one accumulator row: warps 0-1 the A_hi rows, warps 2-3 the
+// A_lo rows), and an entry's last segment is then subtracted from the tile through the entry's
+// relative maps (hi rows first, then lo rows, so no two threads write one element at once).
+// Waits are bounded (wait_ns, about a second by default): one that runs out records -1 in *status
+// and leaves the tile unwritten. withhold != 0 (a failure-path test) issues no MMA and no commit,
+// so the first wait runs out; nothing is then in flight when the tensor memory is freed.
+__global__ void __launch_bounds__(TC_THREADS, 2) k_update_tc(const SNode *__restrict__ sn,
                                                              const UpdTask *__restrict__ tasks,
                                                              const UpdEntry *__restrict__ ents,
                                                              const int32_t *__restrict__ rel, float *__restrict__ Lx,
-                                                             int64_t toff, const Batch bt, long long *status,
-                                                             uint64_t wait_ns, int withhold) {
+                                                             const float *__restrict__ shi,
+                                                             const float *__restrict__ slo, int64_t toff,
+                                                             const Batch bt, long long *status, uint64_t wait_ns,
+                                                             int withhold) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ EntryBatch eb;
   __shared__ __align__(8) uint64_t mbar[NSTAGE];
   __shared__ uint32_t tmem_slot;
   Lx += blockIdx.y * bt.lx;
+  shi += blockIdx.y * bt.sx;
+  slo += blockIdx.y * bt.sx;
   status += blockIdx.y;
   uint8_t *stage0 = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  float *tile = reinterpret_cast<float *>(stage0 + NSTAGE * STAGE_BYTES);  // [col][row], TILE_LD
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   const UpdTask t = tasks[toff + blockIdx.x];
@@ -135,139 +132,166 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_update_tc(const SNode *__rest
   const int tm = tile_rows(t.bi, sj.ncols, sj.nrows, sj.ncb);
   const int cb = t.bj * NB;
   const int tn = min(NB, sj.ncols - cb);
+  float *C = Lx + sj.lx + (int64_t)cb * sj.nrows + rb;
 
   if (warp == 0) tc::tmem_alloc(&tmem_slot, TMEM_COLS);
   if (tid == 0) {
     for (int b = 0; b < NSTAGE; ++b) tc::mbar_init(&mbar[b], 1);
     tc::mbar_init_fence();
   }
+  for (int idx = tid; idx < tm * tn; idx += TC_THREADS) {
+    const int r = idx % tm, c = idx / tm;
+    tile[c * TILE_LD + r] = C[(int64_t)c * sj.nrows + r];
+  }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = tmem_slot;
   const uint32_t row_addr = (uint32_t)(32 * warp) << 16;
+  const int arow = 32 * (warp & 1) + lane;  // this thread's accumulator row within A_hi or A_lo
 
-  float acc[NB];
+  float racc[NB];
 #pragma unroll
-  for (int q = 0; q < NB; ++q) acc[q] = 0.f;
-  // Read back accumulator `which` (the MMAs of chunk `last` and all before it complete) and add
-  // it to acc. Uniform across the CTA; false when the wait ran out.
-  auto drain = [&](int which, int last) -> bool {
+  for (int q = 0; q < NB; ++q) racc[q] = 0.f;
+
+  // Read back accumulator `which` once the MMAs of chunk `last` (and all before) completed, and
+  // add its first n columns to racc; with `scatter`, subtract racc from the tile through the
+  // entry's maps and clear it. Uniform across the CTA; false when the wait ran out.
+  auto drain = [&](int which, int last, int ei, bool scatter) -> bool {
     const bool ok = tc::mbar_wait(&mbar[last & 1], (uint32_t)(last >> 1) & 1u, wait_ns);
     if (__syncthreads_or(!ok)) return false;
     tc::fence_after_sync();
+    const int n = eb.n[ei];
     float v[32];
     tc::ld32(tmem + row_addr + which * NB, v);
 #pragma unroll
-    for (int q = 0; q < 32; ++q) acc[q] += v[q];
-    tc::ld32(tmem + row_addr + which * NB + 32, v);
+    for (int q = 0; q < 32; ++q) racc[q] += v[q];
+    if (n > 32) {
+      tc::ld32(tmem + row_addr + which * NB + 32, v);
 #pragma unroll
-    for (int q = 0; q < 32; ++q) acc[32 + q] += v[q];
+      for (int q = 0; q < 32; ++q) racc[32 + q] += v[q];
+    }
     tc::fence_before_sync();
+    if (scatter) {
+      const int m = eb.m[ei];
+      for (int phase = 0; phase < 2; ++phase) {
+        if ((warp >> 1) == phase && arow < m) {
+          const int r = eb.prow[ei][arow];
+#pragma unroll
+          for (int q = 0; q < NB; ++q)
+            if (q < n) tile[eb.pcol[ei][q] * TILE_LD + r] -= racc[q];
+        }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int q = 0; q < NB; ++q) racc[q] = 0.f;
+    }
     return true;
   };
 
-  int it = 0;          // chunks issued (chunk it uses stage it % 2, accumulator (it / SEG) % 2)
+  int it = 0;   // chunks issued over the whole tile (chunk it uses stage it & 1)
+  int sg = -1;  // segments started (segment sg uses accumulator sg & 1)
   bool failed = false;
-  const int p = tid & (NB - 1), kq0 = tid >> 6;
-  Prefetch f;
+  // the open segment: its entry (batch slot) and last chunk
+  int seg_entry = -1, seg_last = -1;
   for (int64_t e0 = t.e0; e0 < t.e1 && !failed; e0 += EB) {
     const int ne = (int)min((int64_t)EB, t.e1 - e0);
-    // (every thread has finished staging from the previous batch: a barrier follows each store)
-    for (int idx = tid; idx < ne * NB; idx += TC_THREADS) {
-      (&eb.inv_r[0][0])[idx] = -1;
-      (&eb.inv_c[0][0])[idx] = -1;
-    }
+    // (the previous batch's last segment was drained: its maps are no longer needed)
     if (tid < ne) {
       const UpdEntry E = ents[e0 + tid];
       const SNode sk = sn[E.K];
-      eb.kp[tid] = sk.lx;
-      eb.ld[tid] = sk.nrows;
-      eb.kc[tid] = sk.ncols;
-      eb.rlo[tid] = E.r_lo;
-      eb.clo[tid] = E.c_lo;
+      const int64_t pitch = split_pitch(sk.ncols);
+      eb.a_off[tid] = sk.sx + (int64_t)E.r_lo * pitch;
+      eb.b_off[tid] = sk.sx + (int64_t)E.c_lo * pitch;
+      eb.pitch[tid] = (int32_t)pitch;
+      eb.nch[tid] = (sk.ncols + KC - 1) / KC;
+      eb.m[tid] = E.m;
+      eb.n[tid] = E.n;
     }
-    __syncthreads();
     for (int idx = tid; idx < ne * NB; idx += TC_THREADS) {
       const int i = idx / NB, a = idx % NB;
       const UpdEntry &E = ents[e0 + i];
-      if (a < E.m) eb.inv_r[i][rel[E.relr + a] - (int)rb] = (int8_t)a;
-      if (a < E.n) eb.inv_c[i][rel[E.relc + a] - cb] = (int8_t)a;
+      if (a < E.m) eb.prow[i][a] = (int8_t)(rel[E.relr + a] - (int)rb);
+      if (a < E.n) eb.pcol[i][a] = (int8_t)(rel[E.relc + a] - cb);
     }
     __syncthreads();
-    int i = 0, k0 = 0;
-    fetch(f, Lx, eb, i, k0, p, kq0);
+    // chunks of this batch: (entry i, chunk c). Per chunk: its copies (issued one chunk ahead)
+    // land, thread 0 queues its MMAs behind those of the previous chunk, the previous chunk's
+    // MMAs are awaited, which frees the other stage for the next chunk's copies, and a finished
+    // segment is read back while the current chunk's MMAs run.
+    int i = 0, c = 0;
+    stage_chunk(stage0 + (it & 1) * STAGE_BYTES, shi, slo, eb, 0, 0, tid);
+    cp_async_commit();
     while (i < ne) {
-      const int st = it & 1;
-      if (it >= NSTAGE) {  // the MMAs of chunk it - 2 read this stage
-        const bool ok = tc::mbar_wait(&mbar[st], (uint32_t)((it >> 1) - 1) & 1u, wait_ns);
+      int ni = i, nc = c + 1;
+      if (nc >= eb.nch[i]) {
+        ++ni;
+        nc = 0;
+      }
+      const bool more = ni < ne;
+      cp_async_wait<0>();
+      tc::fence_smem_to_async();
+      __syncthreads();
+      const bool new_seg = c % SEG == 0;
+      if (new_seg) ++sg;
+      if (tid == 0 && !withhold) {
+        tc::fence_after_sync();
+        const uint32_t a0 = tc::smem_addr(stage0 + (it & 1) * STAGE_BYTES);
+        const uint32_t bh0 = a0 + A_BYTES, bl0 = bh0 + B_BYTES;
+        const uint32_t d = tmem + (uint32_t)(sg & 1) * NB;
+        const uint32_t idesc = idesc_for(eb.n[i]);
+        uint32_t accumulate = new_seg ? 0u : 1u;
+        for (int ks = 0; ks < KC / 8; ++ks) {
+          const uint32_t o = ks * tc::KSTEP;
+          tc::mma_tf32(d, tc::desc(a0 + o), tc::desc(bh0 + o), idesc, accumulate);
+          tc::mma_tf32(d, tc::desc(a0 + o), tc::desc(bl0 + o), idesc, 1u);
+          accumulate = 1u;
+        }
+        tc::commit(&mbar[it & 1]);
+      }
+      const bool drain_prev = new_seg && seg_entry >= 0;
+      if (it >= 1 && (more || drain_prev)) {  // the MMAs of chunk it - 1 read the other stage
+        const int prev = it - 1;
+        const bool ok = tc::mbar_wait(&mbar[prev & 1], (uint32_t)(prev >> 1) & 1u, wait_ns);
         if (__syncthreads_or(!ok)) {
           failed = true;
           break;
         }
       }
-      uint8_t *A = stage0 + st * STAGE_BYTES, *Bh = A + A_BYTES, *Bl = Bh + B_BYTES;
-#pragma unroll
-      for (int j = 0; j < tc::KC / 8; ++j) {
-        const uint32_t o = tc::off(p, 4 * (kq0 + 2 * j));
-        split_store(A, A + tc::off(NB, 0), o, make_float4(f.a[j][0], f.a[j][1], f.a[j][2], f.a[j][3]));
-        split_store(Bh, Bl, o, make_float4(f.b[j][0], f.b[j][1], f.b[j][2], f.b[j][3]));
+      if (more) {
+        stage_chunk(stage0 + ((it + 1) & 1) * STAGE_BYTES, shi, slo, eb, ni, nc, tid);
+        cp_async_commit();
       }
-      tc::fence_smem_to_async();
-      const int kc_now = min(tc::KC, eb.kc[i] - k0);
-      // advance to the next chunk of this batch and start its loads
-      k0 += tc::KC;
-      if (k0 >= eb.kc[i]) {
-        ++i;
-        k0 = 0;
-      }
-      if (i < ne) fetch(f, Lx, eb, i, k0, p, kq0);
-      __syncthreads();
-      const int seg = it / SEG;
-      if (tid == 0 && !withhold) {
-        tc::fence_after_sync();
-        const uint32_t a0 = tc::smem_addr(A), bh0 = tc::smem_addr(Bh), bl0 = tc::smem_addr(Bl);
-        const uint32_t d = tmem + (uint32_t)(seg & 1) * NB;
-        uint32_t accumulate = it % SEG != 0;
-        for (int ks = 0; ks < (kc_now + 7) / 8; ++ks) {
-          const uint32_t o = ks * tc::KSTEP;
-          tc::mma_tf32(d, tc::desc(a0 + o), tc::desc(bh0 + o), IDESC, accumulate);
-          tc::mma_tf32(d, tc::desc(a0 + o), tc::desc(bl0 + o), IDESC, 1u);
-          accumulate = 1u;
-        }
-        tc::commit(&mbar[st]);
-      }
-      ++it;
-      // a new segment just started on the other accumulator: add up the finished one
-      if ((it - 1) % SEG == 0 && it > 1 && !drain((seg - 1) & 1, it - 2)) {
+      // a new segment started on the other accumulator: read the finished one back (and
+      // subtract it from the tile when it closed its entry)
+      if (drain_prev && !drain((sg - 1) & 1, seg_last, seg_entry, seg_entry != i)) {
         failed = true;
         break;
       }
+      seg_entry = i;
+      seg_last = it;
+      ++it;
+      i = ni;
+      c = nc;
     }
+    // the batch's last segment closes its entry: drain it before the batch's maps are replaced
+    if (!failed && seg_entry >= 0) {
+      if (!drain(sg & 1, seg_last, seg_entry, true)) failed = true;
+      seg_entry = -1;
+    }
+    cp_async_wait<0>();
+    __syncthreads();
   }
-  // (it and failed are uniform across the CTA.) The open segment ends with the last chunk.
-  if (!failed && it > 0 && !drain(((it - 1) / SEG) & 1, it - 1)) failed = true;
   if (failed && it > 0) {  // let the MMAs in flight finish (bounded) before the memory is freed
     const int last = it - 1;
     tc::mbar_wait(&mbar[last & 1], (uint32_t)(last >> 1) & 1u, wait_ns);
+    cp_async_wait<0>();
     __syncthreads();
     if (tid == 0) atomicMin(status, -1ll);
-  } else if (it > 0) {
-    float *red = reinterpret_cast<float *>(stage0);  // [col][row]: the A_lo rows' sums
-    if (warp >= 2) {
-      const int r = 32 * (warp - 2) + lane;
-#pragma unroll
-      for (int q = 0; q < NB; ++q) red[q * (NB + 1) + r] = acc[q];
-    }
-    __syncthreads();
-    if (warp < 2) {
-      const int r = 32 * warp + lane;
-      if (r < tm) {
-        float *C = Lx + sj.lx + (int64_t)cb * sj.nrows + rb + r;
-#pragma unroll
-        for (int q = 0; q < NB; ++q)
-          if (q < tn) C[(int64_t)q * sj.nrows] -= acc[q] + red[q * (NB + 1) + r];
-      }
+  } else {
+    for (int idx = tid; idx < tm * tn; idx += TC_THREADS) {
+      const int r = idx % tm, c = idx / tm;
+      C[(int64_t)c * sj.nrows + r] = tile[c * TILE_LD + r];
     }
   }
   tc::fence_before_sync();
@@ -296,8 +320,8 @@ cudaError_t launch_update_tc(dim3 grid, cudaStream_t st, int prio, const DevPlan
   attr[0].val.priority = prio;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_update_tc, d.sn, d.upd_tasks, d.upd_entries, d.rel, Lx, toff, bt, status,
-                            d.tc_wait_ns, (int)d.tc_withhold);
+  return cudaLaunchKernelEx(&cfg, k_update_tc, d.sn, d.upd_tasks, d.upd_entries, d.rel, Lx, (const float *)d.shi,
+                            (const float *)d.slo, toff, bt, status, d.tc_wait_ns, (int)d.tc_withhold);
 }
 
 }  // namespace sym
