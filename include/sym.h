@@ -141,6 +141,19 @@ int sym_analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, sym_handle *out
 int sym_analyze_perm(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm,
                      const sym_options *opt, sym_handle *out);
 
+/* Inspector with one amalgamation rule per fundamental supernode (the learned schedule's
+ * per-supernode choice; the paper tunes such thresholds by hand, Sec. 2.4 and Sec. 4.2). rules:
+ * nrules records of 7 int32 {amalgamate, nrelax[3], zrelax_permille[3]} (amalgamate = 0 never
+ * merges; otherwise the rule of sym_options). fund_rule: nfund rule indices, one per fundamental
+ * supernode of this pattern under this ordering (SYM_EXPORT_FSUPER of a handle analyzed with the
+ * same pattern, perm and ordering); a candidate merge of S into the next supernode follows the
+ * rule of the fundamental supernode that holds the last column of S. opt's own amalgamation
+ * fields are ignored. Errors as sym_analyze_perm, and SYM_ERR_INVALID for a bad rule, an index out
+ * of range or an nfund that does not match. */
+int sym_analyze_rules(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm,
+                      const sym_options *opt, int32_t nrules, const int32_t *rules, int64_t nfund,
+                      const int32_t *fund_rule, sym_handle *out);
+
 /* Use this CUDA stream (a cudaStream_t passed as void*) for all later work of the handle. */
 int sym_set_stream(sym_handle h, void *stream);
 

@@ -55,6 +55,8 @@ def _load(defines=()):
         lib.orc_validate.restype = ct.c_int
         lib.orc_analyze.argtypes = [i64, P, P, P, P, ct.c_int, ct.POINTER(P)]
         lib.orc_analyze.restype = ct.c_int
+        lib.orc_analyze_rules.argtypes = [i64, P, P, P, P, i32, P, i64, ct.c_int, ct.POINTER(P)]
+        lib.orc_analyze_rules.restype = ct.c_int
         lib.orc_free.argtypes = [P]
         lib.orc_factor.argtypes = [P, P, i64]
         lib.orc_factor.restype = ct.c_int
@@ -108,7 +110,10 @@ def validate(n, Ap, Ai):
 class Oracle:
     """Symbolic analysis (every integer output of the inspector) plus the numeric factor."""
 
-    def __init__(self, n, Ap, Ai, perm0=None, relax=DEFAULT_RELAX, want_rel=False, defines=()):
+    def __init__(self, n, Ap, Ai, perm0=None, relax=DEFAULT_RELAX, want_rel=False, defines=(), rules=None,
+                 fund_rule=None):
+        """rules (records {amalgamate, nrelax0..2, zrelax0..2}) with fund_rule (one index per
+        fundamental supernode) replace relax by per-supernode amalgamation rules."""
         lib = _load(defines)
         self._lib = lib
         self.n = int(n)
@@ -117,8 +122,14 @@ class Oracle:
         p0 = None if perm0 is None else np.ascontiguousarray(perm0, dtype=np.int32)
         rl = None if relax is None else np.ascontiguousarray(relax, dtype=np.int32)
         h = ct.c_void_p()
-        rc = lib.orc_analyze(self.n, _ptr(self.Ap), _ptr(self.Ai), _ptr(p0), _ptr(rl),
-                             1 if want_rel else 0, ct.byref(h))
+        if rules is not None:
+            R = np.ascontiguousarray(rules, dtype=np.int32).reshape(-1, 7)
+            F = np.ascontiguousarray(fund_rule, dtype=np.int32)
+            rc = lib.orc_analyze_rules(self.n, _ptr(self.Ap), _ptr(self.Ai), _ptr(p0), _ptr(R), R.shape[0], _ptr(F),
+                                       F.size, 1 if want_rel else 0, ct.byref(h))
+        else:
+            rc = lib.orc_analyze(self.n, _ptr(self.Ap), _ptr(self.Ai), _ptr(p0), _ptr(rl),
+                                 1 if want_rel else 0, ct.byref(h))
         if rc != 0:
             raise ValueError(f"oracle analyze failed: {rc}")
         self._h = h

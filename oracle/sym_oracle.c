@@ -265,10 +265,30 @@ static int64_t merge_union(const int32_t *a, int64_t na, const int32_t *b, int64
   return k;
 }
 
+static int analyze_impl(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm0,
+                        const int32_t *relax, const int32_t *rules, int32_t nrules, const int32_t *fund_rule,
+                        int64_t nfund, int want_rel, orc_t **out);
+
 /* Run every symbolic step. perm0 may be NULL (natural order). relax = {nrelax0..2, zrelax0..2
  * per mille}, or NULL for no amalgamation. want_rel != 0 also builds the relative row maps. */
 int orc_analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm0,
                 const int32_t *relax, int want_rel, orc_t **out) {
+  return analyze_impl(n, Ap, Ai, perm0, relax, NULL, 0, NULL, 0, want_rel, out);
+}
+
+/* The same with one amalgamation rule per fundamental supernode: rules holds nrules records
+ * {amalgamate, nrelax0..2, zrelax0..2 per mille}; the merge of supernode i into the next one
+ * follows rules[fund_rule[f]] with f the fundamental supernode that holds the last column of i.
+ * Returns ORC_ERR_INVALID when nfund is not the number of fundamental supernodes. */
+int orc_analyze_rules(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm0,
+                      const int32_t *rules, int32_t nrules, const int32_t *fund_rule, int64_t nfund,
+                      int want_rel, orc_t **out) {
+  return analyze_impl(n, Ap, Ai, perm0, NULL, rules, nrules, fund_rule, nfund, want_rel, out);
+}
+
+static int analyze_impl(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm0,
+                        const int32_t *relax, const int32_t *rules, int32_t nrules, const int32_t *fund_rule,
+                        int64_t nfund, int want_rel, orc_t **out) {
   *out = NULL;
   int rc = orc_validate(n, Ap, Ai);
   if (rc) return rc;
@@ -348,7 +368,15 @@ int orc_analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *
   /* at most ns - 1 merges: each one removes a supernode */
   o->merges = xcalloc(2 * (size_t)(ns > 0 ? ns : 1), sizeof(int32_t));
   o->nmerge = 0;
-  if (relax) {
+  int bad_rule = 0;
+  for (int64_t f = 0; fund_rule && f < nfund; ++f) bad_rule |= fund_rule[f] < 0 || fund_rule[f] >= nrules;
+  if (fund_rule && (nfund != ns || bad_rule)) {
+    for (int32_t s = 0; s < ns; ++s) free(rows[s]);
+    free(rows); free(first); free(last); free(nxt); free(nrows); free(truennz); free(tmp);
+    orc_free(o);
+    return ORC_ERR_INVALID;
+  }
+  if (relax || fund_rule) {
     int changed = 1;
     while (changed) {
       changed = 0;
@@ -361,6 +389,14 @@ int orc_analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *
           int64_t nc = (int64_t)last[P] - first[i] + 1;
           int64_t total = nc * m - nc * (nc - 1) / 2;
           int64_t z = total - (truennz[i] + truennz[P]);
+          /* slot i is the fundamental supernode holding the last column of supernode i */
+          int32_t rule_buf[6];
+          if (fund_rule) {
+            const int32_t *q = rules + 7 * fund_rule[i];
+            if (!q[0]) { prev = i; i = P; continue; } /* this rule never merges */
+            for (int t = 0; t < 6; ++t) rule_buf[t] = q[1 + t];
+            relax = rule_buf;
+          }
 #if defined(ORC_PLANT_DROP_Z_CLAUSE)
           /* deliberately wrong rules, compiled only into the copies the tests use to show that
            * the amalgamation pin catches over-merging: the zero-fraction clause of the third

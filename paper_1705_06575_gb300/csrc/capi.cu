@@ -6,6 +6,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "kernels.h"
 #include "plan.h"
@@ -417,8 +418,41 @@ int sym_analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, sym_handle *out
   return sym_analyze_perm(n, Ap, Ai, nullptr, nullptr, out);
 }
 
+static int analyze_impl(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm,
+                        const sym_options *opt_in, sym_handle *out,
+                        const std::vector<sym::AmalgamationRule> *rules, const std::vector<int32_t> *fund_rule);
+
 int sym_analyze_perm(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm,
                      const sym_options *opt_in, sym_handle *out) {
+  return analyze_impl(n, Ap, Ai, perm, opt_in, out, nullptr, nullptr);
+}
+
+int sym_analyze_rules(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm,
+                      const sym_options *opt, int32_t nrules, const int32_t *rules, int64_t nfund,
+                      const int32_t *fund_rule, sym_handle *out) {
+  if (!out) return fail(SYM_ERR_INVALID, "null output handle");
+  *out = nullptr;
+  if (nrules < 1 || !rules || nfund < 0 || (nfund > 0 && !fund_rule))
+    return fail(SYM_ERR_INVALID, "bad amalgamation rule table");
+  std::vector<sym::AmalgamationRule> R(nrules);
+  for (int32_t r = 0; r < nrules; ++r) {
+    const int32_t *q = rules + 7 * r;
+    R[r].amalgamate = q[0];
+    for (int i = 0; i < 3; ++i) {
+      R[r].nrelax[i] = q[1 + i];
+      R[r].zrelax_permille[i] = q[4 + i];
+      if (q[1 + i] < 0 || q[4 + i] < 0 || q[4 + i] > 1000) return fail(SYM_ERR_INVALID, "bad amalgamation rule");
+    }
+  }
+  std::vector<int32_t> F(fund_rule, fund_rule + nfund);
+  for (int32_t f : F)
+    if (f < 0 || f >= nrules) return fail(SYM_ERR_INVALID, "rule index out of range");
+  return analyze_impl(n, Ap, Ai, perm, opt, out, &R, &F);
+}
+
+static int analyze_impl(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm,
+                        const sym_options *opt_in, sym_handle *out,
+                        const std::vector<sym::AmalgamationRule> *rules, const std::vector<int32_t> *fund_rule) {
   if (!out) return fail(SYM_ERR_INVALID, "null output handle");
   *out = nullptr;
   sym_options opt;
@@ -435,7 +469,7 @@ int sym_analyze_perm(int64_t n, const int64_t *Ap, const int32_t *Ai, const int3
   if (!h) return fail(SYM_ERR_OOM, "host allocation");
   try {
     std::string err;
-    int rc = sym::analyze(n, Ap, Ai, perm, opt, h->plan, err);
+    int rc = sym::analyze(n, Ap, Ai, perm, opt, h->plan, err, rules, fund_rule);
     if (rc != SYM_OK) {
       delete h;
       return fail(rc, err);

@@ -541,16 +541,18 @@ __global__ void __launch_bounds__(TileCfg<TB>::threads) k_potrf(const SNode *__r
   // warp 0: pivot of column c (already updated by columns < c) and scaling of the column
   auto finish_column = [&](int c) {
     if constexpr (F64PIV) {
+      // the pivot in FP64; its reciprocal square root only to FP32 accuracy, which is all the
+      // FP32 column scaling can use (a further FP64 chain would only lengthen the serial path)
       double d = dd[c];
       if (!(d > 0.0)) {
         if (lane == 0) atomicMin(status, (long long)(sj.first + s * NB + c));
         d = 1.0;
       }
       if (lane == 0 && piv) piv[blockIdx.y * bt.piv + sj.first + s * NB + c] = d;
-      const double x = rsqrt_newton(d);
-      const T xf = (T)x;
+      const float df = (float)d;
+      const float xf = rsqrt_newton(df);
       __syncwarp();
-      for (int r = c + lane; r < ts; r += 32) a[c][r] = r == c ? (T)(d * x) : a[c][r] * xf;  // d x = sqrt(d)
+      for (int r = c + lane; r < ts; r += 32) a[c][r] = r == c ? (T)(df * xf) : a[c][r] * xf;  // d x = sqrt(d)
     } else {
       T d = a[c][c];
       if (!(d > T(0))) {
@@ -573,14 +575,16 @@ __global__ void __launch_bounds__(TileCfg<TB>::threads) k_potrf(const SNode *__r
       }
       __syncwarp();
       finish_column(c + 1);
+    } else if (F64PIV && warp == 1) {  // the FP64 diagonal of the trailing columns, one warp
+      for (int rr = c + 2 + lane; rr < ts; rr += 32) dd[rr] = fma(-(double)a[c][rr], (double)a[c][rr], dd[rr]);
     } else {
       const int m = ts - c - 2;  // trailing lower triangle of order m, rows/cols c+2..ts-1
       const int tot = m * (m + 1) / 2;
-      for (int idx = tid - 32; idx < tot; idx += TT - 32) {
+      const int w0 = F64PIV ? 64 : 32;  // threads below w0 have other work
+      for (int idx = tid - w0; idx < tot; idx += TT - w0) {
         const int ij = tri[idx];
         const int rr = c + 2 + (ij >> 8), cc = c + 2 + (ij & 0xff);
-        if (F64PIV && rr == cc) dd[rr] = fma(-(double)a[c][rr], (double)a[c][rr], dd[rr]);
-        else a[cc][rr] = fma(-a[c][rr], a[c][cc], a[cc][rr]);
+        if (!F64PIV || rr != cc) a[cc][rr] = fma(-a[c][rr], a[c][cc], a[cc][rr]);
       }
     }
     __syncthreads();
@@ -1334,17 +1338,17 @@ __global__ void __launch_bounds__(32 * WT_WARPS) k_potrf_w(const SNode *__restri
     }
   __syncwarp();
   for (int c = 0; c < ts; ++c) {
-    if constexpr (F64PIV) {
+    if constexpr (F64PIV) {  // FP64 pivot, FP32 reciprocal square root (as in k_potrf)
       double d = dd[c];
       if (!(d > 0.0)) {
         if (lane == 0) atomicMin(status, (long long)(sj.first + s * NB + c));
         d = 1.0;
       }
       if (lane == 0 && piv) piv[blockIdx.y * bt.piv + sj.first + s * NB + c] = d;
-      const double x = rsqrt_newton(d);
-      const T xf = (T)x;
+      const float df = (float)d;
+      const float xf = rsqrt_newton(df);
       __syncwarp();  // every lane has read the pivot
-      if (lane >= c && lane < ts) a[pk(ts, c, lane)] = lane == c ? (T)(d * x) : a[pk(ts, c, lane)] * xf;
+      if (lane >= c && lane < ts) a[pk(ts, c, lane)] = lane == c ? (T)(df * xf) : a[pk(ts, c, lane)] * xf;
     } else {
       T d = a[pk(ts, c, c)];
       if (!(d > T(0))) {
@@ -1357,12 +1361,13 @@ __global__ void __launch_bounds__(32 * WT_WARPS) k_potrf_w(const SNode *__restri
     }
     __syncwarp();
     const int m = ts - 1 - c;  // trailing triangle: rows and columns c+1 .. ts-1
+    if (F64PIV && lane >= c + 1 && lane < ts)  // the FP64 diagonal, one lane per trailing column
+      dd[lane] = fma(-(double)a[pk(ts, c, lane)], (double)a[pk(ts, c, lane)], dd[lane]);
     for (int el = lane; el < m * (m + 1) / 2; el += 32) {
       int ia, ib;
       tri_decode(el, ia, ib);
       const int rr = c + 1 + ia, cc = c + 1 + ib;
-      if (F64PIV && rr == cc) dd[rr] = fma(-(double)a[pk(ts, c, rr)], (double)a[pk(ts, c, rr)], dd[rr]);
-      else a[pk(ts, cc, rr)] = fma(-a[pk(ts, c, rr)], a[pk(ts, c, cc)], a[pk(ts, cc, rr)]);
+      if (!F64PIV || rr != cc) a[pk(ts, cc, rr)] = fma(-a[pk(ts, c, rr)], a[pk(ts, c, cc)], a[pk(ts, cc, rr)]);
     }
     __syncwarp();
   }

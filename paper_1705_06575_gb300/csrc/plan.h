@@ -192,8 +192,17 @@ struct Plan {
 // Build P.csr_* from the pattern (after analyze).
 void build_permuted_csr(const int64_t *Ap, const int32_t *Ai, Plan &P);
 
-// Run the inspector. Returns SYM_OK or an error code with a message in err.
+// One amalgamation rule: amalgamate (0: never merge), nrelax[3], zrelax_permille[3].
+struct AmalgamationRule {
+  int32_t amalgamate, nrelax[3], zrelax_permille[3];
+};
+
+// Run the inspector. Returns SYM_OK or an error code with a message in err. With fund_rule
+// (one rule index per fundamental supernode, nfund of them), a candidate merge of S into the
+// next supernode follows rules[fund_rule[f]], f the fundamental supernode holding last(S);
+// otherwise every merge follows opt's rule.
 int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm,
-            const sym_options &opt, Plan &P, std::string &err);
+            const sym_options &opt, Plan &P, std::string &err,
+            const std::vector<AmalgamationRule> *rules = nullptr, const std::vector<int32_t> *fund_rule = nullptr);
 
 }  // namespace sym

@@ -164,7 +164,8 @@ double ordering_flops(int64_t n, const int64_t *Ap, const int32_t *Ai, const std
 }  // namespace
 
 int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm_in,
-            const sym_options &opt, Plan &P, std::string &err) {
+            const sym_options &opt, Plan &P, std::string &err, const std::vector<AmalgamationRule> *rules,
+            const std::vector<int32_t> *fund_rule) {
   Timer timer;
   if (!valid_pattern(n, Ap, Ai, err)) return SYM_ERR_INVALID;
   P = Plan();
@@ -300,7 +301,11 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
   std::vector<int32_t> nxt(nf);
   for (int32_t s = 0; s < nf; ++s) { sl[s] = P.fsuper[s + 1] - 1; nxt[s] = s + 1; }
   int32_t head = nf > 0 ? 0 : nf;
-  if (opt.amalgamate) {
+  if (fund_rule && (int64_t)fund_rule->size() != nf) {
+    err = "one amalgamation rule per fundamental supernode expected (" + std::to_string(nf) + ")";
+    return SYM_ERR_INVALID;
+  }
+  if (opt.amalgamate || fund_rule) {
     std::vector<int32_t> merged;
     for (bool changed = true; changed;) {
       changed = false;
@@ -315,10 +320,15 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
           const int64_t nc = (int64_t)sl[t] - sf[s] + 1;
           const int64_t total = nc * m - nc * (nc - 1) / 2;
           const int64_t z = total - (ccum[sl[t] + 1] - ccum[sf[s]]);
-          const bool ok = nc <= opt.nrelax[0] ||
-                          (nc <= opt.nrelax[1] && z * 1000 <= (int64_t)opt.zrelax_permille[0] * total) ||
-                          (nc <= opt.nrelax[2] && z * 1000 <= (int64_t)opt.zrelax_permille[1] * total) ||
-                          z * 1000 <= (int64_t)opt.zrelax_permille[2] * total;
+          // the rule of the fundamental supernode holding last(S): slot s is that supernode
+          AmalgamationRule R{1, {opt.nrelax[0], opt.nrelax[1], opt.nrelax[2]},
+                             {opt.zrelax_permille[0], opt.zrelax_permille[1], opt.zrelax_permille[2]}};
+          if (fund_rule) R = (*rules)[(*fund_rule)[s]];
+          const bool ok = R.amalgamate &&
+                          (nc <= R.nrelax[0] ||
+                           (nc <= R.nrelax[1] && z * 1000 <= (int64_t)R.zrelax_permille[0] * total) ||
+                           (nc <= R.nrelax[2] && z * 1000 <= (int64_t)R.zrelax_permille[1] * total) ||
+                           z * 1000 <= (int64_t)R.zrelax_permille[2] * total);
           if (ok) {
             srows[t].swap(merged);
             std::vector<int32_t>().swap(srows[s]);

@@ -13,7 +13,7 @@
 // (|x - hi - lo| <= 2^-22 |x|). The A operand is staged as the 128-row matrix [A_hi; A_lo] and
 // multiplied by B_hi and by B_lo (two M = 128, K = 8 MMAs per step, N = n rounded up to 16):
 // accumulator rows 0-63 receive A_hi B^T, rows 64-127 A_lo B^T, all four partial products formed
-// exactly. Sums run in tensor memory over at most SEG chunks of 32 values of k and are then
+// exactly. Sums run in tensor memory over at most SEG chunks (256 values of k) and are then
 // added in FP32 registers (a long sum inside the tensor core loses accuracy), as in the SIMT form.
 #include <cuda_runtime.h>
 
@@ -26,15 +26,24 @@ namespace sym {
 namespace {
 
 constexpr int TC_THREADS = 128;
-constexpr int KC = tc::KC;                      // values of k per staged chunk (32)
-constexpr uint32_t A_BYTES = 128 * KC * 4;      // [A_hi; A_lo]: 16 KB
-constexpr uint32_t B_BYTES = 64 * KC * 4;       // B_hi or B_lo: 8 KB
+// Operand chunks of KC = 16 values of k, K-major core matrices without swizzle (8 rows x 16 bytes
+// each; the next 4 values of k LBO = 128 bytes on, the next 8 rows SBO = 512 bytes on), in
+// NSTAGE = 4 stages: the copies of three chunks are in flight while one chunk's MMAs run.
+constexpr int KC = 16;
+constexpr uint32_t LBO = 128, SBO = (KC / 4) * 128;
+constexpr uint32_t A_BYTES = 128 * KC * 4;      // [A_hi; A_lo]: 8 KB
+constexpr uint32_t B_BYTES = 64 * KC * 4;       // B_hi or B_lo: 4 KB
 constexpr uint32_t STAGE_BYTES = A_BYTES + 2 * B_BYTES;
-constexpr int NSTAGE = 2;
+constexpr int NSTAGE = 4;
 constexpr int TILE_LD = NB + 1;                 // the tile in shared memory, [col][row]
 constexpr size_t SMEM_BYTES = NSTAGE * STAGE_BYTES + 128 + sizeof(float) * NB * TILE_LD;
 constexpr uint32_t TMEM_COLS = 2 * NB;          // two FP32 accumulators of 128 x 64
-constexpr int SEG = 8;                          // chunks per tensor-memory sum
+constexpr int SEG = 16;                         // chunks per tensor-memory sum (256 values of k)
+
+// Byte offset of element (row r, k) of an operand chunk.
+__device__ __forceinline__ uint32_t off(int r, int k) {
+  return (uint32_t)(r >> 3) * SBO + (uint32_t)(k >> 2) * LBO + (uint32_t)(r & 7) * 16u + (uint32_t)(k & 3) * 4u;
+}
 
 __device__ __forceinline__ int64_t tile_base(int32_t i, int32_t ncols, int32_t ncb) {
   return i < ncb ? (int64_t)i * NB : (int64_t)ncols + (int64_t)(i - ncb) * NB;
@@ -73,31 +82,34 @@ struct EntryBatch {
 };
 
 // Issue the copies of chunk c of entry i into a stage: rows of [A_hi; A_lo] and B_hi, B_lo, in
-// 16-byte units (4 values of k), each landing in its K-major core-matrix position.
+// 16-byte units (4 values of k), each landing in its K-major core-matrix position. Thread t copies
+// unit q = t % 4 of rows t / 4 and t / 4 + 32 of each of the four operands.
 __device__ __forceinline__ void stage_chunk(uint8_t *stage, const float *__restrict__ shi,
                                             const float *__restrict__ slo, const EntryBatch &eb, int i, int c,
                                             int tid) {
   const uint32_t A = tc::smem_addr(stage), Bh = A + A_BYTES, Bl = Bh + B_BYTES;
-  const int m = eb.m[i], n = eb.n[i];
-  const int64_t k0 = (int64_t)c * KC;
-  // A: 2 m rows x 8 units (hi rows 0..m-1, lo rows 64..64+m-1); B: 2 n rows x 8 units
-  const int ua = 2 * m * 8, ub = 2 * n * 8;
-  for (int u = tid; u < ua + ub; u += TC_THREADS) {
-    if (u < ua) {
-      const int half = u / (m * 8), v = u - half * m * 8, r = v >> 3, q = v & 7;
-      const float *src = (half ? slo : shi) + eb.a_off[i] + (int64_t)r * eb.pitch[i] + k0 + 4 * q;
-      cp_async16(A + tc::off(r + 64 * half, 4 * q), src);
-    } else {
-      const int w = u - ua, half = w / (n * 8), v = w - half * n * 8, r = v >> 3, q = v & 7;
-      const float *src = (half ? slo : shi) + eb.b_off[i] + (int64_t)r * eb.pitch[i] + k0 + 4 * q;
-      cp_async16((half ? Bl : Bh) + tc::off(r, 4 * q), src);
+  const int m = eb.m[i], n = eb.n[i], q = tid & 3, r0 = tid >> 2;
+  const int64_t pitch = eb.pitch[i], k = (int64_t)c * KC + 4 * q;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int r = r0 + 32 * h;
+    if (r < m) {
+      const int64_t o = eb.a_off[i] + r * pitch + k;
+      cp_async16(A + off(r, 4 * q), shi + o);
+      cp_async16(A + off(r + 64, 4 * q), slo + o);
+    }
+    if (r < n) {
+      const int64_t o = eb.b_off[i] + r * pitch + k;
+      cp_async16(Bh + off(r, 4 * q), shi + o);
+      cp_async16(Bl + off(r, 4 * q), slo + o);
     }
   }
 }
 
 // One CTA (4 warps) per tile, two CTAs per SM. Every thread stages, thread 0 issues the MMAs, all
 // threads read the accumulators back. The tile's chunks (every entry's chunks in entry order)
-// form one sequence: the copies of chunk c + 1 are in flight while the MMAs of chunk c run.
+// form one sequence: the copies of the next NSTAGE - 1 chunks are in flight while the MMAs of a
+// chunk run.
 // A segment (at most SEG chunks of one entry) accumulates in one of two tensor-memory
 // accumulators; once the MMAs of the next segment are issued, the finished segment is read back
 // into FP32 registers (each thread one accumulator row: warps 0-1 the A_hi rows, warps 2-3 the
@@ -154,12 +166,17 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_update_tc(const SNode *__rest
 #pragma unroll
   for (int q = 0; q < NB; ++q) racc[q] = 0.f;
 
+  // Chunk j of the tile uses stage j % NSTAGE and commits to mbar[j % NSTAGE], whose phase j / NSTAGE
+  // completes with it. Wait (bounded, uniform across the CTA) until chunk j's MMAs completed.
+  auto wait_chunk = [&](int j) -> bool {
+    const bool ok = tc::mbar_wait(&mbar[j % NSTAGE], (uint32_t)(j / NSTAGE) & 1u, wait_ns);
+    return !__syncthreads_or(!ok);
+  };
   // Read back accumulator `which` once the MMAs of chunk `last` (and all before) completed, and
   // add its first n columns to racc; with `scatter`, subtract racc from the tile through the
   // entry's maps and clear it. Uniform across the CTA; false when the wait ran out.
   auto drain = [&](int which, int last, int ei, bool scatter) -> bool {
-    const bool ok = tc::mbar_wait(&mbar[last & 1], (uint32_t)(last >> 1) & 1u, wait_ns);
-    if (__syncthreads_or(!ok)) return false;
+    if (!wait_chunk(last)) return false;
     tc::fence_after_sync();
     const int n = eb.n[ei];
     float v[32];
@@ -189,14 +206,14 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_update_tc(const SNode *__rest
     return true;
   };
 
-  int it = 0;   // chunks issued over the whole tile (chunk it uses stage it & 1)
+  int it = 0;   // chunks issued over the whole tile
   int sg = -1;  // segments started (segment sg uses accumulator sg & 1)
   bool failed = false;
   // the open segment: its entry (batch slot) and last chunk
   int seg_entry = -1, seg_last = -1;
   for (int64_t e0 = t.e0; e0 < t.e1 && !failed; e0 += EB) {
     const int ne = (int)min((int64_t)EB, t.e1 - e0);
-    // (the previous batch's last segment was drained: its maps are no longer needed)
+    // (the previous batch's chunks have all completed: its maps and stages are free)
     if (tid < ne) {
       const UpdEntry E = ents[e0 + tid];
       const SNode sk = sn[E.K];
@@ -215,53 +232,57 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_update_tc(const SNode *__rest
       if (a < E.n) eb.pcol[i][a] = (int8_t)(rel[E.relc + a] - cb);
     }
     __syncthreads();
-    // chunks of this batch: (entry i, chunk c). Per chunk: its copies (issued one chunk ahead)
-    // land, thread 0 queues its MMAs behind those of the previous chunk, the previous chunk's
-    // MMAs are awaited, which frees the other stage for the next chunk's copies, and a finished
-    // segment is read back while the current chunk's MMAs run.
+    // The copies run NSTAGE - 1 chunks ahead of the MMAs: (si, sc) is the next chunk to stage,
+    // `staged` its index in the tile's sequence. Every call commits one copy group (an empty one
+    // once the batch is exhausted), so chunk it's group is complete when at most NSTAGE - 2
+    // newer ones are pending.
+    int si = 0, sc = 0, staged = it;
+    auto stage_next = [&]() {
+      if (si < ne) {
+        stage_chunk(stage0 + (staged % NSTAGE) * STAGE_BYTES, shi, slo, eb, si, sc, tid);
+        if (++sc >= eb.nch[si]) {
+          ++si;
+          sc = 0;
+        }
+        ++staged;
+      }
+      cp_async_commit();
+    };
+    for (int p = 0; p < NSTAGE - 1; ++p) stage_next();
     int i = 0, c = 0;
-    stage_chunk(stage0 + (it & 1) * STAGE_BYTES, shi, slo, eb, 0, 0, tid);
-    cp_async_commit();
     while (i < ne) {
       int ni = i, nc = c + 1;
       if (nc >= eb.nch[i]) {
         ++ni;
         nc = 0;
       }
-      const bool more = ni < ne;
-      cp_async_wait<0>();
+      cp_async_wait<NSTAGE - 2>();
       tc::fence_smem_to_async();
       __syncthreads();
       const bool new_seg = c % SEG == 0;
       if (new_seg) ++sg;
       if (tid == 0 && !withhold) {
         tc::fence_after_sync();
-        const uint32_t a0 = tc::smem_addr(stage0 + (it & 1) * STAGE_BYTES);
+        const uint32_t a0 = tc::smem_addr(stage0 + (it % NSTAGE) * STAGE_BYTES);
         const uint32_t bh0 = a0 + A_BYTES, bl0 = bh0 + B_BYTES;
         const uint32_t d = tmem + (uint32_t)(sg & 1) * NB;
         const uint32_t idesc = idesc_for(eb.n[i]);
         uint32_t accumulate = new_seg ? 0u : 1u;
         for (int ks = 0; ks < KC / 8; ++ks) {
-          const uint32_t o = ks * tc::KSTEP;
-          tc::mma_tf32(d, tc::desc(a0 + o), tc::desc(bh0 + o), idesc, accumulate);
-          tc::mma_tf32(d, tc::desc(a0 + o), tc::desc(bl0 + o), idesc, 1u);
+          const uint32_t o = ks * 2 * LBO;  // K = 8: two core matrices along k
+          tc::mma_tf32(d, tc::desc(a0 + o, LBO, SBO), tc::desc(bh0 + o, LBO, SBO), idesc, accumulate);
+          tc::mma_tf32(d, tc::desc(a0 + o, LBO, SBO), tc::desc(bl0 + o, LBO, SBO), idesc, 1u);
           accumulate = 1u;
         }
-        tc::commit(&mbar[it & 1]);
+        tc::commit(&mbar[it % NSTAGE]);
       }
       const bool drain_prev = new_seg && seg_entry >= 0;
-      if (it >= 1 && (more || drain_prev)) {  // the MMAs of chunk it - 1 read the other stage
-        const int prev = it - 1;
-        const bool ok = tc::mbar_wait(&mbar[prev & 1], (uint32_t)(prev >> 1) & 1u, wait_ns);
-        if (__syncthreads_or(!ok)) {
-          failed = true;
-          break;
-        }
+      // the stage of chunk it - 1 takes the chunk NSTAGE - 1 ahead once its MMAs completed
+      if (it >= 1 && (si < ne || drain_prev) && !wait_chunk(it - 1)) {
+        failed = true;
+        break;
       }
-      if (more) {
-        stage_chunk(stage0 + ((it + 1) & 1) * STAGE_BYTES, shi, slo, eb, ni, nc, tid);
-        cp_async_commit();
-      }
+      stage_next();
       // a new segment started on the other accumulator: read the finished one back (and
       // subtract it from the tile when it closed its entry)
       if (drain_prev && !drain((sg - 1) & 1, seg_last, seg_entry, seg_entry != i)) {
@@ -284,7 +305,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_update_tc(const SNode *__rest
   }
   if (failed && it > 0) {  // let the MMAs in flight finish (bounded) before the memory is freed
     const int last = it - 1;
-    tc::mbar_wait(&mbar[last & 1], (uint32_t)(last >> 1) & 1u, wait_ns);
+    tc::mbar_wait(&mbar[last % NSTAGE], (uint32_t)(last / NSTAGE) & 1u, wait_ns);
     cp_async_wait<0>();
     __syncthreads();
     if (tid == 0) atomicMin(status, -1ll);
