@@ -25,7 +25,6 @@
 namespace sym {
 namespace {
 
-constexpr int TC_THREADS = 128;
 // Operand chunks of KC = 16 values of k, K-major core matrices without swizzle (8 rows x 16 bytes
 // each; the next 4 values of k LBO = 128 bytes on, the next 8 rows SBO = 512 bytes on), in
 // NSTAGE = 4 stages: the copies of three chunks are in flight while one chunk's MMAs run.
@@ -63,73 +62,59 @@ __device__ __forceinline__ uint32_t idesc_for(int n) {
 __device__ __forceinline__ void cp_async16(uint32_t saddr, const void *g) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr), "l"(g) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
 
-// Entries are taken in batches of EB: their descriptors and relative maps are loaded into shared
-// memory first, so that staging and the output side depend on shared memory only.
-constexpr int EB = 32;
-struct EntryBatch {
-  int64_t a_off[EB];   // offset of the entry's first R1 row in K's split copies
-  int64_t b_off[EB];   // offset of its first R0 row
-  int32_t pitch[EB];   // row length of K's split copies
-  int32_t nch[EB];     // chunks of KC values of k
-  int32_t m[EB], n[EB];
-  int8_t prow[EB][NB], pcol[EB][NB];  // tile row / column of the entry's row a / column b
-};
-
-// Issue the copies of chunk c of entry i into a stage: rows of [A_hi; A_lo] and B_hi, B_lo, in
-// 16-byte units (4 values of k), each landing in its K-major core-matrix position. Thread t copies
-// unit q = t % 4 of rows t / 4 and t / 4 + 32 of each of the four operands.
+// Copies of chunk c (KC values of k from c KC on) of one entry into a stage, issued by the 32 lanes
+// of the producer warp: 16-byte units (4 values of k) of the rows of [A_hi; A_lo] and B_hi, B_lo,
+// each landing in its K-major core-matrix position. Unit u of an operand: row u / 4, 4 (u % 4) on.
 __device__ __forceinline__ void stage_chunk(uint8_t *stage, const float *__restrict__ shi,
-                                            const float *__restrict__ slo, const EntryBatch &eb, int i, int c,
-                                            int tid) {
+                                            const float *__restrict__ slo, int64_t a_off, int64_t b_off,
+                                            int64_t pitch, int m, int n, int c, int lane) {
   const uint32_t A = tc::smem_addr(stage), Bh = A + A_BYTES, Bl = Bh + B_BYTES;
-  const int m = eb.m[i], n = eb.n[i], q = tid & 3, r0 = tid >> 2;
-  const int64_t pitch = eb.pitch[i], k = (int64_t)c * KC + 4 * q;
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int r = r0 + 32 * h;
-    if (r < m) {
-      const int64_t o = eb.a_off[i] + r * pitch + k;
-      cp_async16(A + off(r, 4 * q), shi + o);
-      cp_async16(A + off(r + 64, 4 * q), slo + o);
-    }
-    if (r < n) {
-      const int64_t o = eb.b_off[i] + r * pitch + k;
-      cp_async16(Bh + off(r, 4 * q), shi + o);
-      cp_async16(Bl + off(r, 4 * q), slo + o);
-    }
+  const int64_t k0 = (int64_t)c * KC;
+  for (int u = lane; u < 4 * m; u += 32) {
+    const int r = u >> 2, q = u & 3;
+    const int64_t o = a_off + r * pitch + k0 + 4 * q;
+    cp_async16(A + off(r, 4 * q), shi + o);
+    cp_async16(A + off(r + 64, 4 * q), slo + o);
+  }
+  for (int u = lane; u < 4 * n; u += 32) {
+    const int r = u >> 2, q = u & 3;
+    const int64_t o = b_off + r * pitch + k0 + 4 * q;
+    cp_async16(Bh + off(r, 4 * q), shi + o);
+    cp_async16(Bl + off(r, 4 * q), slo + o);
   }
 }
 
-// One CTA (4 warps) per tile, two CTAs per SM. Every thread stages, thread 0 issues the MMAs, all
-// threads read the accumulators back. The tile's chunks (every entry's chunks in entry order)
-// form one sequence: the copies of the next NSTAGE - 1 chunks are in flight while the MMAs of a
-// chunk run.
-// A segment (at most SEG chunks of one entry) accumulates in one of two tensor-memory
-// accumulators; once the MMAs of the next segment are issued, the finished segment is read back
-// into FP32 registers (each thread one accumulator row: warps 0-1 the A_hi rows, warps 2-3 the
-// A_lo rows), and an entry's last segment is then subtracted from the tile through the entry's
-// relative maps (hi rows first, then lo rows, so no two threads write one element at once).
-// Waits are bounded (wait_ns, about a second by default): one that runs out records -1 in *status
-// and leaves the tile unwritten. withhold != 0 (a failure-path test) issues no MMA and no commit,
-// so the first wait runs out; nothing is then in flight when the tensor memory is freed.
-__global__ void __launch_bounds__(TC_THREADS, 2) k_update_tc(const SNode *__restrict__ sn,
-                                                             const UpdTask *__restrict__ tasks,
-                                                             const UpdEntry *__restrict__ ents,
-                                                             const int32_t *__restrict__ rel, float *__restrict__ Lx,
-                                                             const float *__restrict__ shi,
-                                                             const float *__restrict__ slo, int64_t toff,
-                                                             const Batch bt, long long *status, uint64_t wait_ns,
-                                                             int withhold) {
+// One CTA per tile, two CTAs per SM, with warp roles (no CTA-wide barrier inside the loop):
+//   warp 4 (producer): copies each chunk into the next free stage; a stage is free once the MMAs
+//     of the chunk it held completed (empty[st], committed by the MMA thread); its lanes arrive on
+//     full[st] when their copies have landed;
+//   warp 5, lane 0 (MMA): per chunk, waits for full[st], issues the 2 x (KC / 8) MMAs into the
+//     segment's accumulator (two alternate; it waits for the epilogue to have read one before
+//     reusing it, acc_empty) and commits to empty[st], and at a segment's end to acc_full;
+//   warps 0-3 (epilogue; warp w reads tensor-memory lanes 32 w .. 32 w + 31): per segment, add the
+//     accumulator to FP32 registers and release it; after an entry's last segment, subtract the
+//     sum from the tile through the entry's relative maps (the A_hi rows of warps 0-1 first, then
+//     the A_lo rows of warps 2-3, separated by a barrier of the four warps).
+// A segment is at most SEG chunks of one entry. Every wait is bounded (wait_ns; about a second by
+// default) and also ends when another warp has given up; then -1 goes to *status, the tile is left
+// unwritten, and the tensor memory is freed once every issued MMA has completed. withhold != 0 (a
+// failure-path test) issues no MMA and no commit, so the first waits run out.
+constexpr int EPI_WARPS = 4, PRODUCER = 4, MMA_WARP = 5;
+constexpr int TC_BLOCK = 32 * 6;
+
+__global__ void __launch_bounds__(TC_BLOCK, 2) k_update_tc(const SNode *__restrict__ sn,
+                                                           const UpdTask *__restrict__ tasks,
+                                                           const UpdEntry *__restrict__ ents,
+                                                           const int32_t *__restrict__ rel, float *__restrict__ Lx,
+                                                           const float *__restrict__ shi,
+                                                           const float *__restrict__ slo, int64_t toff,
+                                                           const Batch bt, long long *status, uint64_t wait_ns,
+                                                           int withhold) {
   extern __shared__ uint8_t smem_raw[];
-  __shared__ EntryBatch eb;
-  __shared__ __align__(8) uint64_t mbar[NSTAGE];
+  __shared__ __align__(8) uint64_t full[NSTAGE], empty[NSTAGE], acc_full[2], acc_empty[2], done;
   __shared__ uint32_t tmem_slot;
+  __shared__ volatile int fail;
   Lx += blockIdx.y * bt.lx;
   shi += blockIdx.y * bt.sx;
   slo += blockIdx.y * bt.sx;
@@ -147,11 +132,20 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_update_tc(const SNode *__rest
   float *C = Lx + sj.lx + (int64_t)cb * sj.nrows + rb;
 
   if (warp == 0) tc::tmem_alloc(&tmem_slot, TMEM_COLS);
-  if (tid == 0) {
-    for (int b = 0; b < NSTAGE; ++b) tc::mbar_init(&mbar[b], 1);
+  if (tid == 32) {
+    for (int b = 0; b < NSTAGE; ++b) {
+      tc::mbar_init(&full[b], 32);
+      tc::mbar_init(&empty[b], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&acc_full[b], 1);
+      tc::mbar_init(&acc_empty[b], EPI_WARPS);
+    }
+    tc::mbar_init(&done, 1);
+    fail = 0;
     tc::mbar_init_fence();
   }
-  for (int idx = tid; idx < tm * tn; idx += TC_THREADS) {
+  for (int idx = tid; idx < tm * tn; idx += TC_BLOCK) {
     const int r = idx % tm, c = idx / tm;
     tile[c * TILE_LD + r] = C[(int64_t)c * sj.nrows + r];
   }
@@ -159,164 +153,148 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_update_tc(const SNode *__rest
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = tmem_slot;
-  const uint32_t row_addr = (uint32_t)(32 * warp) << 16;
-  const int arow = 32 * (warp & 1) + lane;  // this thread's accumulator row within A_hi or A_lo
+  auto give_up = [&]() { fail = 1; };
 
-  float racc[NB];
-#pragma unroll
-  for (int q = 0; q < NB; ++q) racc[q] = 0.f;
-
-  // Chunk j of the tile uses stage j % NSTAGE and commits to mbar[j % NSTAGE], whose phase j / NSTAGE
-  // completes with it. Wait (bounded, uniform across the CTA) until chunk j's MMAs completed.
-  auto wait_chunk = [&](int j) -> bool {
-    const bool ok = tc::mbar_wait(&mbar[j % NSTAGE], (uint32_t)(j / NSTAGE) & 1u, wait_ns);
-    return !__syncthreads_or(!ok);
-  };
-  // Read back accumulator `which` once the MMAs of chunk `last` (and all before) completed, and
-  // add its first n columns to racc; with `scatter`, subtract racc from the tile through the
-  // entry's maps and clear it. Uniform across the CTA; false when the wait ran out.
-  auto drain = [&](int which, int last, int ei, bool scatter) -> bool {
-    if (!wait_chunk(last)) return false;
-    tc::fence_after_sync();
-    const int n = eb.n[ei];
-    float v[32];
-    tc::ld32(tmem + row_addr + which * NB, v);
-#pragma unroll
-    for (int q = 0; q < 32; ++q) racc[q] += v[q];
-    if (n > 32) {
-      tc::ld32(tmem + row_addr + which * NB + 32, v);
-#pragma unroll
-      for (int q = 0; q < 32; ++q) racc[32 + q] += v[q];
-    }
-    tc::fence_before_sync();
-    if (scatter) {
-      const int m = eb.m[ei];
-      for (int phase = 0; phase < 2; ++phase) {
-        if ((warp >> 1) == phase && arow < m) {
-          const int r = eb.prow[ei][arow];
-#pragma unroll
-          for (int q = 0; q < NB; ++q)
-            if (q < n) tile[eb.pcol[ei][q] * TILE_LD + r] -= racc[q];
-        }
-        __syncthreads();
-      }
-#pragma unroll
-      for (int q = 0; q < NB; ++q) racc[q] = 0.f;
-    }
-    return true;
-  };
-
-  int it = 0;   // chunks issued over the whole tile
-  int sg = -1;  // segments started (segment sg uses accumulator sg & 1)
-  bool failed = false;
-  // the open segment: its entry (batch slot) and last chunk
-  int seg_entry = -1, seg_last = -1;
-  for (int64_t e0 = t.e0; e0 < t.e1 && !failed; e0 += EB) {
-    const int ne = (int)min((int64_t)EB, t.e1 - e0);
-    // (the previous batch's chunks have all completed: its maps and stages are free)
-    if (tid < ne) {
-      const UpdEntry E = ents[e0 + tid];
+  if (warp == PRODUCER) {
+    int j = 0;  // chunk index over the tile's sequence
+    for (int64_t e = t.e0; e < t.e1 && !fail; ++e) {
+      const UpdEntry E = ents[e];
       const SNode sk = sn[E.K];
       const int64_t pitch = split_pitch(sk.ncols);
-      eb.a_off[tid] = sk.sx + (int64_t)E.r_lo * pitch;
-      eb.b_off[tid] = sk.sx + (int64_t)E.c_lo * pitch;
-      eb.pitch[tid] = (int32_t)pitch;
-      eb.nch[tid] = (sk.ncols + KC - 1) / KC;
-      eb.m[tid] = E.m;
-      eb.n[tid] = E.n;
-    }
-    for (int idx = tid; idx < ne * NB; idx += TC_THREADS) {
-      const int i = idx / NB, a = idx % NB;
-      const UpdEntry &E = ents[e0 + i];
-      if (a < E.m) eb.prow[i][a] = (int8_t)(rel[E.relr + a] - (int)rb);
-      if (a < E.n) eb.pcol[i][a] = (int8_t)(rel[E.relc + a] - cb);
-    }
-    __syncthreads();
-    // The copies run NSTAGE - 1 chunks ahead of the MMAs: (si, sc) is the next chunk to stage,
-    // `staged` its index in the tile's sequence. Every call commits one copy group (an empty one
-    // once the batch is exhausted), so chunk it's group is complete when at most NSTAGE - 2
-    // newer ones are pending.
-    int si = 0, sc = 0, staged = it;
-    auto stage_next = [&]() {
-      if (si < ne) {
-        stage_chunk(stage0 + (staged % NSTAGE) * STAGE_BYTES, shi, slo, eb, si, sc, tid);
-        if (++sc >= eb.nch[si]) {
-          ++si;
-          sc = 0;
+      const int nch = (sk.ncols + KC - 1) / KC;
+      for (int c = 0; c < nch; ++c, ++j) {
+        const int st = j % NSTAGE;
+        const bool free_st =
+            j < NSTAGE || tc::mbar_wait_or_abort(&empty[st], (uint32_t)(j / NSTAGE - 1) & 1u, wait_ns, &fail);
+        if (!__all_sync(0xffffffffu, free_st)) {  // the lanes agree
+          give_up();
+          break;
         }
-        ++staged;
+        stage_chunk(stage0 + st * STAGE_BYTES, shi, slo, sk.sx + (int64_t)E.r_lo * pitch,
+                    sk.sx + (int64_t)E.c_lo * pitch, pitch, E.m, E.n, c, lane);
+        tc::cp_async_arrive(&full[st]);
       }
-      cp_async_commit();
-    };
-    for (int p = 0; p < NSTAGE - 1; ++p) stage_next();
-    int i = 0, c = 0;
-    while (i < ne) {
-      int ni = i, nc = c + 1;
-      if (nc >= eb.nch[i]) {
-        ++ni;
-        nc = 0;
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+  } else if (warp == MMA_WARP) {
+    if (lane == 0) {
+      int j = 0, seg = 0;
+      bool issued = false;
+      for (int64_t e = t.e0; e < t.e1 && !fail; ++e) {
+        const UpdEntry E = ents[e];
+        const int nch = (sn[E.K].ncols + KC - 1) / KC;
+        const uint32_t idesc = idesc_for(E.n);
+        for (int c = 0; c < nch; ++c, ++j) {
+          const int st = j % NSTAGE, acc = seg & 1;
+          if (!tc::mbar_wait_or_abort(&full[st], (uint32_t)(j / NSTAGE) & 1u, wait_ns, &fail)) {
+            give_up();
+            break;
+          }
+          const bool first = c % SEG == 0;  // a segment starts: its accumulator must be free
+          if (first && seg >= 2 &&
+              !tc::mbar_wait_or_abort(&acc_empty[acc], (uint32_t)(seg / 2 - 1) & 1u, wait_ns, &fail)) {
+            give_up();
+            break;
+          }
+          tc::fence_smem_to_async();
+          tc::fence_after_sync();
+          if (!withhold) {
+            const uint32_t a0 = tc::smem_addr(stage0 + st * STAGE_BYTES);
+            const uint32_t bh0 = a0 + A_BYTES, bl0 = bh0 + B_BYTES;
+            const uint32_t d = tmem + (uint32_t)acc * NB;
+            uint32_t accumulate = first ? 0u : 1u;
+            for (int ks = 0; ks < KC / 8; ++ks) {
+              const uint32_t o = ks * 2 * LBO;  // K = 8: two core matrices along k
+              tc::mma_tf32(d, tc::desc(a0 + o, LBO, SBO), tc::desc(bh0 + o, LBO, SBO), idesc, accumulate);
+              tc::mma_tf32(d, tc::desc(a0 + o, LBO, SBO), tc::desc(bl0 + o, LBO, SBO), idesc, 1u);
+              accumulate = 1u;
+            }
+            tc::commit(&empty[st]);
+            if (c % SEG == SEG - 1 || c == nch - 1) tc::commit(&acc_full[acc]);
+            issued = true;
+          }
+          if (c % SEG == SEG - 1 || c == nch - 1) ++seg;
+        }
       }
-      cp_async_wait<NSTAGE - 2>();
-      tc::fence_smem_to_async();
-      __syncthreads();
-      const bool new_seg = c % SEG == 0;
-      if (new_seg) ++sg;
-      if (tid == 0 && !withhold) {
+      if (issued) {  // every issued MMA completes before the tensor memory can be freed
+        tc::commit(&done);
+        if (!tc::mbar_wait(&done, 0u, wait_ns)) give_up();
+      }
+    }
+  } else {  // epilogue warps 0-3
+    float racc[NB];
+#pragma unroll
+    for (int q = 0; q < NB; ++q) racc[q] = 0.f;
+    const uint32_t row_addr = (uint32_t)(32 * warp) << 16;
+    const int arow = 32 * (warp & 1) + lane;  // accumulator row within A_hi (warps 0-1) or A_lo
+    int seg = 0;
+    bool go = true;  // uniform across the four epilogue warps
+    for (int64_t e = t.e0; e < t.e1 && go; ++e) {
+      const UpdEntry E = ents[e];
+      const int nch = (sn[E.K].ncols + KC - 1) / KC;
+      const int nseg = (nch + SEG - 1) / SEG;
+      bool ok = true;
+      for (int g = 0; g < nseg; ++g, ++seg) {
+        const int acc = seg & 1;
+        // the lanes agree before the warp-wide tensor-memory loads
+        if (!__all_sync(0xffffffffu, tc::mbar_wait_or_abort(&acc_full[acc], (uint32_t)(seg / 2) & 1u, wait_ns,
+                                                            &fail))) {
+          ok = false;
+          break;
+        }
         tc::fence_after_sync();
-        const uint32_t a0 = tc::smem_addr(stage0 + (it % NSTAGE) * STAGE_BYTES);
-        const uint32_t bh0 = a0 + A_BYTES, bl0 = bh0 + B_BYTES;
-        const uint32_t d = tmem + (uint32_t)(sg & 1) * NB;
-        const uint32_t idesc = idesc_for(eb.n[i]);
-        uint32_t accumulate = new_seg ? 0u : 1u;
-        for (int ks = 0; ks < KC / 8; ++ks) {
-          const uint32_t o = ks * 2 * LBO;  // K = 8: two core matrices along k
-          tc::mma_tf32(d, tc::desc(a0 + o, LBO, SBO), tc::desc(bh0 + o, LBO, SBO), idesc, accumulate);
-          tc::mma_tf32(d, tc::desc(a0 + o, LBO, SBO), tc::desc(bl0 + o, LBO, SBO), idesc, 1u);
-          accumulate = 1u;
+        float v[32];
+        tc::ld32(tmem + row_addr + acc * NB, v);
+#pragma unroll
+        for (int q = 0; q < 32; ++q) racc[q] += v[q];
+        if (E.n > 32) {
+          tc::ld32(tmem + row_addr + acc * NB + 32, v);
+#pragma unroll
+          for (int q = 0; q < 32; ++q) racc[32 + q] += v[q];
         }
-        tc::commit(&mbar[it % NSTAGE]);
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&acc_empty[acc]);
       }
-      const bool drain_prev = new_seg && seg_entry >= 0;
-      // the stage of chunk it - 1 takes the chunk NSTAGE - 1 ahead once its MMAs completed
-      if (it >= 1 && (si < ne || drain_prev) && !wait_chunk(it - 1)) {
-        failed = true;
-        break;
+      // (an epilogue warp that gave up still joins both barriers of the four warps below)
+      if (!ok) give_up();
+      const int r = arow < E.m ? rel[E.relr + arow] - (int)rb : -1;
+      if (ok && (warp >> 1) == 0 && r >= 0) {  // A_hi rows first
+#pragma unroll
+        for (int q = 0; q < NB; ++q)
+          if (q < E.n) tile[(rel[E.relc + q] - cb) * TILE_LD + r] -= racc[q];
       }
-      stage_next();
-      // a new segment started on the other accumulator: read the finished one back (and
-      // subtract it from the tile when it closed its entry)
-      if (drain_prev && !drain((sg - 1) & 1, seg_last, seg_entry, seg_entry != i)) {
-        failed = true;
-        break;
+      asm volatile("bar.sync 1, %0;" ::"n"(32 * EPI_WARPS) : "memory");
+      if (ok && (warp >> 1) == 1 && r >= 0) {  // then the A_lo rows
+#pragma unroll
+        for (int q = 0; q < NB; ++q)
+          if (q < E.n) tile[(rel[E.relc + q] - cb) * TILE_LD + r] -= racc[q];
       }
-      seg_entry = i;
-      seg_last = it;
-      ++it;
-      i = ni;
-      c = nc;
-    }
-    // the batch's last segment closes its entry: drain it before the batch's maps are replaced
-    if (!failed && seg_entry >= 0) {
-      if (!drain(sg & 1, seg_last, seg_entry, true)) failed = true;
-      seg_entry = -1;
-    }
-    cp_async_wait<0>();
-    __syncthreads();
-  }
-  if (failed && it > 0) {  // let the MMAs in flight finish (bounded) before the memory is freed
-    const int last = it - 1;
-    tc::mbar_wait(&mbar[last % NSTAGE], (uint32_t)(last / NSTAGE) & 1u, wait_ns);
-    cp_async_wait<0>();
-    __syncthreads();
-    if (tid == 0) atomicMin(status, -1ll);
-  } else {
-    for (int idx = tid; idx < tm * tn; idx += TC_THREADS) {
-      const int r = idx % tm, c = idx / tm;
-      C[(int64_t)c * sj.nrows + r] = tile[c * TILE_LD + r];
+      // the four warps continue together: unless any of them has seen a failure
+      uint32_t stop;
+      asm volatile(
+          "{\n\t.reg .pred p, q;\n\t"
+          "setp.ne.u32 p, %1, 0;\n\t"
+          "barrier.cta.red.or.pred q, 1, %2, p;\n\t"
+          "selp.u32 %0, 1, 0, q;\n\t}"
+          : "=r"(stop)
+          : "r"((uint32_t)(fail != 0 || !ok)), "n"(32 * EPI_WARPS)
+          : "memory");
+      go = stop == 0;
+#pragma unroll
+      for (int q = 0; q < NB; ++q) racc[q] = 0.f;
     }
   }
   tc::fence_before_sync();
   __syncthreads();
+  if (fail) {
+    if (tid == 0) atomicMin(status, -1ll);
+  } else {
+    for (int idx = tid; idx < tm * tn; idx += TC_BLOCK) {
+      const int r = idx % tm, c = idx / tm;
+      C[(int64_t)c * sj.nrows + r] = tile[c * TILE_LD + r];
+    }
+  }
   if (warp == 0) {
     tc::fence_after_sync();
     tc::tmem_free(tmem, TMEM_COLS);
@@ -334,7 +312,7 @@ cudaError_t launch_update_tc(dim3 grid, cudaStream_t st, int prio, const DevPlan
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   cfg.gridDim = grid;
-  cfg.blockDim = dim3(TC_THREADS, 1, 1);
+  cfg.blockDim = dim3(TC_BLOCK, 1, 1);
   cfg.dynamicSmemBytes = SMEM_BYTES;
   cfg.stream = st;
   attr[0].id = cudaLaunchAttributePriority;
