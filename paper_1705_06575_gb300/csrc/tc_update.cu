@@ -115,6 +115,7 @@ __global__ void __launch_bounds__(TC_BLOCK, 2) k_update_tc(const SNode *__restri
   __shared__ __align__(8) uint64_t full[NSTAGE], empty[NSTAGE], acc_full[2], acc_empty[2], done;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int fail;
+  __shared__ int8_t pcol[NB];  // tile column of each column of the epilogue's current entry
   Lx += blockIdx.y * bt.lx;
   shi += blockIdx.y * bt.sx;
   slo += blockIdx.y * bt.sx;
@@ -157,9 +158,11 @@ __global__ void __launch_bounds__(TC_BLOCK, 2) k_update_tc(const SNode *__restri
 
   if (warp == PRODUCER) {
     int j = 0;  // chunk index over the tile's sequence
+    UpdEntry En = t.e0 < t.e1 ? ents[t.e0] : UpdEntry{};  // the next entry, loaded one ahead
     for (int64_t e = t.e0; e < t.e1 && !fail; ++e) {
-      const UpdEntry E = ents[e];
+      const UpdEntry E = En;
       const SNode sk = sn[E.K];
+      if (e + 1 < t.e1) En = ents[e + 1];
       const int64_t pitch = split_pitch(sk.ncols);
       const int nch = (sk.ncols + KC - 1) / KC;
       for (int c = 0; c < nch; ++c, ++j) {
@@ -180,10 +183,21 @@ __global__ void __launch_bounds__(TC_BLOCK, 2) k_update_tc(const SNode *__restri
     if (lane == 0) {
       int j = 0, seg = 0;
       bool issued = false;
+      // the next entry's column count and width, loaded one entry ahead
+      int nxt_n = 0, nxt_k = 0;
+      if (t.e0 < t.e1) {
+        const UpdEntry E0 = ents[t.e0];
+        nxt_n = E0.n;
+        nxt_k = sn[E0.K].ncols;
+      }
       for (int64_t e = t.e0; e < t.e1 && !fail; ++e) {
-        const UpdEntry E = ents[e];
-        const int nch = (sn[E.K].ncols + KC - 1) / KC;
-        const uint32_t idesc = idesc_for(E.n);
+        const int nch = (nxt_k + KC - 1) / KC;
+        const uint32_t idesc = idesc_for(nxt_n);
+        if (e + 1 < t.e1) {
+          const UpdEntry E1 = ents[e + 1];
+          nxt_n = E1.n;
+          nxt_k = sn[E1.K].ncols;
+        }
         for (int c = 0; c < nch; ++c, ++j) {
           const int st = j % NSTAGE, acc = seg & 1;
           if (!tc::mbar_wait_or_abort(&full[st], (uint32_t)(j / NSTAGE) & 1u, wait_ns, &fail)) {
@@ -233,6 +247,10 @@ __global__ void __launch_bounds__(TC_BLOCK, 2) k_update_tc(const SNode *__restri
       const UpdEntry E = ents[e];
       const int nch = (sn[E.K].ncols + KC - 1) / KC;
       const int nseg = (nch + SEG - 1) / SEG;
+      // the entry's relative maps, loaded while its MMAs run: this thread's row, and the columns
+      // into shared memory (the previous entry's scatter ended with a barrier of the four warps)
+      const int r = arow < E.m ? rel[E.relr + arow] - (int)rb : -1;
+      if (tid < E.n) pcol[tid] = (int8_t)(rel[E.relc + tid] - cb);
       bool ok = true;
       for (int g = 0; g < nseg; ++g, ++seg) {
         const int acc = seg & 1;
@@ -256,19 +274,19 @@ __global__ void __launch_bounds__(TC_BLOCK, 2) k_update_tc(const SNode *__restri
         __syncwarp();
         if (lane == 0) tc::mbar_arrive(&acc_empty[acc]);
       }
-      // (an epilogue warp that gave up still joins both barriers of the four warps below)
+      // (an epilogue warp that gave up still joins the barriers of the four warps below)
       if (!ok) give_up();
-      const int r = arow < E.m ? rel[E.relr + arow] - (int)rb : -1;
+      asm volatile("bar.sync 1, %0;" ::"n"(32 * EPI_WARPS) : "memory");  // pcol is complete
       if (ok && (warp >> 1) == 0 && r >= 0) {  // A_hi rows first
 #pragma unroll
         for (int q = 0; q < NB; ++q)
-          if (q < E.n) tile[(rel[E.relc + q] - cb) * TILE_LD + r] -= racc[q];
+          if (q < E.n) tile[pcol[q] * TILE_LD + r] -= racc[q];
       }
       asm volatile("bar.sync 1, %0;" ::"n"(32 * EPI_WARPS) : "memory");
       if (ok && (warp >> 1) == 1 && r >= 0) {  // then the A_lo rows
 #pragma unroll
         for (int q = 0; q < NB; ++q)
-          if (q < E.n) tile[(rel[E.relc + q] - cb) * TILE_LD + r] -= racc[q];
+          if (q < E.n) tile[pcol[q] * TILE_LD + r] -= racc[q];
       }
       // the four warps continue together: unless any of them has seen a failure
       uint32_t stop;
