@@ -10,10 +10,10 @@
 // tile, which sits in shared memory for the whole CTA and is written back once.
 //
 // Precision. An FP32 value x is split into two TF32 values hi = tf32(x) and lo = tf32(x - hi)
-// (|x - hi - lo| <= 2^-22 |x|). The A operand is staged as the 128-row matrix [A_hi; A_lo] and
-// multiplied by B_hi and by B_lo (two M = 128, K = 8 MMAs per step, N = n rounded up to 16):
-// accumulator rows 0-63 receive A_hi B^T, rows 64-127 A_lo B^T, all four partial products formed
-// exactly. Sums run in tensor memory over at most SEG chunks (256 values of k) and are then
+// (|x - hi - lo| <= 2^-22 |x|). The A operand is staged as the 128-row matrix [A_hi; A_lo]; per
+// K = 8 step three MMAs (M = 128, N = n rounded up to 16) add A_hi B_hi^T, A_hi B_lo^T and
+// A_lo B_hi^T, each formed exactly, to accumulator rows 0-63 (A_lo B_lo^T, below 2^-22 |A| |B|,
+// is left out). Sums run in tensor memory over at most SEG chunks (256 values of k) and are then
 // added in FP32 registers (a long sum inside the tensor core loses accuracy), as in the SIMT form.
 #include <cuda_runtime.h>
 
@@ -86,22 +86,27 @@ __device__ __forceinline__ void stage_chunk(uint8_t *stage, const float *__restr
 }
 
 // One CTA per tile, two CTAs per SM, with warp roles (no CTA-wide barrier inside the loop):
-//   warp 4 (producer): copies each chunk into the next free stage; a stage is free once the MMAs
+//   warp 2 (producer): copies each chunk into the next free stage; a stage is free once the MMAs
 //     of the chunk it held completed (empty[st], committed by the MMA thread); its lanes arrive on
 //     full[st] when their copies have landed;
-//   warp 5, lane 0 (MMA): per chunk, waits for full[st], issues the 2 x (KC / 8) MMAs into the
+//   warp 3, lane 0 (MMA): per chunk, waits for full[st], issues 3 x (KC / 8) MMAs into the
 //     segment's accumulator (two alternate; it waits for the epilogue to have read one before
 //     reusing it, acc_empty) and commits to empty[st], and at a segment's end to acc_full;
-//   warps 0-3 (epilogue; warp w reads tensor-memory lanes 32 w .. 32 w + 31): per segment, add the
-//     accumulator to FP32 registers and release it; after an entry's last segment, subtract the
-//     sum from the tile through the entry's relative maps (the A_hi rows of warps 0-1 first, then
-//     the A_lo rows of warps 2-3, separated by a barrier of the four warps).
+//   warps 0-1 (epilogue; warp w reads tensor-memory lanes 32 w .. 32 w + 31, one accumulator row
+//     per thread): per segment, add the accumulator to FP32 registers and release it; after an
+//     entry's last segment, subtract the sum from the tile through the entry's relative maps, then
+//     meet at a barrier of the two warps (the next entry may write the same tile elements).
+// Per K = 8 step the accumulator rows 0-63 receive A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T: the
+// third MMA takes its A operand from the A_lo rows (rows 64.. of the staged [A_hi; A_lo], its rows
+// beyond 64 then read the B operands and land in accumulator rows 64-127, which nobody reads). The
+// dropped A_lo B_lo^T is below 2^-22 |A| |B|, the size of the split's own error.
 // A segment is at most SEG chunks of one entry. Every wait is bounded (wait_ns; about a second by
 // default) and also ends when another warp has given up; then -1 goes to *status, the tile is left
 // unwritten, and the tensor memory is freed once every issued MMA has completed. withhold != 0 (a
 // failure-path test) issues no MMA and no commit, so the first waits run out.
-constexpr int EPI_WARPS = 4, PRODUCER = 4, MMA_WARP = 5;
-constexpr int TC_BLOCK = 32 * 6;
+constexpr int EPI_WARPS = 2, PRODUCER = 2, MMA_WARP = 3;
+constexpr int TC_BLOCK = 32 * 4;
+constexpr uint32_t LO_ROWS = 8 * SBO;  // byte offset of row 64 (the A_lo rows) in an A operand
 
 __global__ void __launch_bounds__(TC_BLOCK, 2) k_update_tc(const SNode *__restrict__ sn,
                                                            const UpdTask *__restrict__ tasks,
@@ -115,7 +120,7 @@ __global__ void __launch_bounds__(TC_BLOCK, 2) k_update_tc(const SNode *__restri
   __shared__ __align__(8) uint64_t full[NSTAGE], empty[NSTAGE], acc_full[2], acc_empty[2], done;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int fail;
-  __shared__ int8_t pcol[NB];  // tile column of each column of the epilogue's current entry
+  __shared__ int8_t pcol[2][NB];  // tile column of each column of an entry (by entry parity)
   Lx += blockIdx.y * bt.lx;
   shi += blockIdx.y * bt.sx;
   slo += blockIdx.y * bt.sx;
@@ -149,6 +154,10 @@ __global__ void __launch_bounds__(TC_BLOCK, 2) k_update_tc(const SNode *__restri
   for (int idx = tid; idx < tm * tn; idx += TC_BLOCK) {
     const int r = idx % tm, c = idx / tm;
     tile[c * TILE_LD + r] = C[(int64_t)c * sj.nrows + r];
+  }
+  if (t.e0 < t.e1 && tid < NB) {  // the first entry's column map
+    const UpdEntry E0 = ents[t.e0];
+    if (tid < E0.n) pcol[0][tid] = (int8_t)(rel[E0.relc + tid] - cb);
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -221,6 +230,7 @@ __global__ void __launch_bounds__(TC_BLOCK, 2) k_update_tc(const SNode *__restri
               const uint32_t o = ks * 2 * LBO;  // K = 8: two core matrices along k
               tc::mma_tf32(d, tc::desc(a0 + o, LBO, SBO), tc::desc(bh0 + o, LBO, SBO), idesc, accumulate);
               tc::mma_tf32(d, tc::desc(a0 + o, LBO, SBO), tc::desc(bl0 + o, LBO, SBO), idesc, 1u);
+              tc::mma_tf32(d, tc::desc(a0 + LO_ROWS + o, LBO, SBO), tc::desc(bh0 + o, LBO, SBO), idesc, 1u);
               accumulate = 1u;
             }
             tc::commit(&empty[st]);
@@ -235,22 +245,27 @@ __global__ void __launch_bounds__(TC_BLOCK, 2) k_update_tc(const SNode *__restri
         if (!tc::mbar_wait(&done, 0u, wait_ns)) give_up();
       }
     }
-  } else {  // epilogue warps 0-3
+  } else {  // epilogue warps 0-1: accumulator row tid
     float racc[NB];
 #pragma unroll
     for (int q = 0; q < NB; ++q) racc[q] = 0.f;
     const uint32_t row_addr = (uint32_t)(32 * warp) << 16;
-    const int arow = 32 * (warp & 1) + lane;  // accumulator row within A_hi (warps 0-1) or A_lo
-    int seg = 0;
-    bool go = true;  // uniform across the four epilogue warps
-    for (int64_t e = t.e0; e < t.e1 && go; ++e) {
-      const UpdEntry E = ents[e];
+    int seg = 0, par = 0;
+    bool go = true;  // uniform across the two epilogue warps
+    UpdEntry E = t.e0 < t.e1 ? ents[t.e0] : UpdEntry{};
+    int r = (t.e0 < t.e1 && tid < E.m) ? rel[E.relr + tid] - (int)rb : -1;
+    for (int64_t e = t.e0; e < t.e1 && go; ++e, par ^= 1) {
       const int nch = (sn[E.K].ncols + KC - 1) / KC;
       const int nseg = (nch + SEG - 1) / SEG;
-      // the entry's relative maps, loaded while its MMAs run: this thread's row, and the columns
-      // into shared memory (the previous entry's scatter ended with a barrier of the four warps)
-      const int r = arow < E.m ? rel[E.relr + arow] - (int)rb : -1;
-      if (tid < E.n) pcol[tid] = (int8_t)(rel[E.relc + tid] - cb);
+      // the next entry's maps, loaded while this one's MMAs run (its column map into the other
+      // buffer, which the barrier closing this entry publishes)
+      UpdEntry En = E;
+      int rn = -1;
+      if (e + 1 < t.e1) {
+        En = ents[e + 1];
+        if (tid < En.n) pcol[par ^ 1][tid] = (int8_t)(rel[En.relc + tid] - cb);
+        if (tid < En.m) rn = rel[En.relr + tid] - (int)rb;
+      }
       bool ok = true;
       for (int g = 0; g < nseg; ++g, ++seg) {
         const int acc = seg & 1;
@@ -274,21 +289,15 @@ __global__ void __launch_bounds__(TC_BLOCK, 2) k_update_tc(const SNode *__restri
         __syncwarp();
         if (lane == 0) tc::mbar_arrive(&acc_empty[acc]);
       }
-      // (an epilogue warp that gave up still joins the barriers of the four warps below)
       if (!ok) give_up();
-      asm volatile("bar.sync 1, %0;" ::"n"(32 * EPI_WARPS) : "memory");  // pcol is complete
-      if (ok && (warp >> 1) == 0 && r >= 0) {  // A_hi rows first
+      if (ok && r >= 0) {
 #pragma unroll
         for (int q = 0; q < NB; ++q)
-          if (q < E.n) tile[pcol[q] * TILE_LD + r] -= racc[q];
+          if (q < E.n) tile[pcol[par][q] * TILE_LD + r] -= racc[q];
       }
-      asm volatile("bar.sync 1, %0;" ::"n"(32 * EPI_WARPS) : "memory");
-      if (ok && (warp >> 1) == 1 && r >= 0) {  // then the A_lo rows
 #pragma unroll
-        for (int q = 0; q < NB; ++q)
-          if (q < E.n) tile[pcol[q] * TILE_LD + r] -= racc[q];
-      }
-      // the four warps continue together: unless any of them has seen a failure
+      for (int q = 0; q < NB; ++q) racc[q] = 0.f;
+      // the two warps continue together, unless either has seen a failure
       uint32_t stop;
       asm volatile(
           "{\n\t.reg .pred p, q;\n\t"
@@ -299,8 +308,8 @@ __global__ void __launch_bounds__(TC_BLOCK, 2) k_update_tc(const SNode *__restri
           : "r"((uint32_t)(fail != 0 || !ok)), "n"(32 * EPI_WARPS)
           : "memory");
       go = stop == 0;
-#pragma unroll
-      for (int q = 0; q < NB; ++q) racc[q] = 0.f;
+      E = En;
+      r = rn;
     }
   }
   tc::fence_before_sync();
