@@ -3,19 +3,18 @@
 // The left-looking update of Sec. 3.2 restricted to one 64 x 64 tile (bi, bj) of supernode J:
 // for every descendant entry, C -= L_K(R1, :) L_K(R0, :)^T scattered through the relative maps.
 // Each entry is a compact GEMM: its m rows R1 and n rows R0 are contiguous rows of K's panel, so
-// they are staged as they are (rows 0..m-1 and 0..n-1 of the operands) from K's transposed copy,
-// which the TRSM kernels wrote once (each row's k values contiguous) when K's panel became final.
-// The tensor core forms the m x n product in tensor memory; the relative maps are applied only on
-// the way out, when the product is subtracted from the tile, which sits in shared memory for the
-// whole CTA and is written back once.
+// they are staged as they are (rows 0..m-1 and 0..n-1 of the operands) from K's TF32 split copy,
+// which the TRSM kernels wrote once, transposed (each row's k values contiguous) and already
+// split, when K's panel became final. The tensor core forms the m x n product in tensor memory;
+// the relative maps are applied only on the way out, when the product is subtracted from the
+// tile, which sits in shared memory for the whole CTA and is written back once.
 //
 // Precision. An FP32 value x is split into two TF32 values hi = tf32(x) and lo = tf32(x - hi)
-// (|x - hi - lo| <= 2^-22 |x|) in shared memory, after the copy. The A operand is held as the
-// 128-row matrix [A_hi; A_lo]; per K = 8 step three MMAs (M = 128, N = n rounded up to 16) add
-// A_hi B_hi^T, A_hi B_lo^T and A_lo B_hi^T, each formed exactly, to accumulator rows 0-63
-// (A_lo B_lo^T, below 2^-22 |A| |B|, is left out). Sums run in tensor memory over at most SEG
-// chunks (256 values of k) and are then added in FP32 registers (a long sum inside the tensor
-// core loses accuracy), as in the SIMT form.
+// (|x - hi - lo| <= 2^-22 |x|). The A operand is staged as the 128-row matrix [A_hi; A_lo]; per
+// K = 8 step three MMAs (M = 128, N = n rounded up to 16) add A_hi B_hi^T, A_hi B_lo^T and
+// A_lo B_hi^T, each formed exactly, to accumulator rows 0-63 (A_lo B_lo^T, below 2^-22 |A| |B|,
+// is left out). Sums run in tensor memory over at most SEG chunks (256 values of k) and are then
+// added in FP32 registers (a long sum inside the tensor core loses accuracy), as in the SIMT form.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -65,36 +64,24 @@ __device__ __forceinline__ void cp_async16(uint32_t saddr, const void *g) {
 }
 
 // Copies of chunk c (KC values of k from c KC on) of one entry into a stage, issued by the 32 lanes
-// of the producer warp: 16-byte units (4 FP32 values of k) of the entry's rows, into the A_hi rows
-// and the B_hi rows, each landing in its K-major core-matrix position. Unit u: row u / 4, values
-// 4 (u % 4) on.
-__device__ __forceinline__ void stage_chunk(uint8_t *stage, const float *__restrict__ ltr, int64_t a_off,
-                                            int64_t b_off, int64_t pitch, int m, int n, int c, int lane) {
-  const uint32_t A = tc::smem_addr(stage), Bh = A + A_BYTES;
+// of the producer warp: 16-byte units (4 values of k) of the rows of [A_hi; A_lo] and B_hi, B_lo,
+// each landing in its K-major core-matrix position. Unit u of an operand: row u / 4, 4 (u % 4) on.
+__device__ __forceinline__ void stage_chunk(uint8_t *stage, const float *__restrict__ shi,
+                                            const float *__restrict__ slo, int64_t a_off, int64_t b_off,
+                                            int64_t pitch, int m, int n, int c, int lane) {
+  const uint32_t A = tc::smem_addr(stage), Bh = A + A_BYTES, Bl = Bh + B_BYTES;
   const int64_t k0 = (int64_t)c * KC;
   for (int u = lane; u < 4 * m; u += 32) {
     const int r = u >> 2, q = u & 3;
-    cp_async16(A + off(r, 4 * q), ltr + a_off + r * pitch + k0 + 4 * q);
+    const int64_t o = a_off + r * pitch + k0 + 4 * q;
+    cp_async16(A + off(r, 4 * q), shi + o);
+    cp_async16(A + off(r + 64, 4 * q), slo + o);
   }
   for (int u = lane; u < 4 * n; u += 32) {
     const int r = u >> 2, q = u & 3;
-    cp_async16(Bh + off(r, 4 * q), ltr + b_off + r * pitch + k0 + 4 * q);
-  }
-}
-
-// Split a staged chunk in place: hi = tf32(x) over x, lo = tf32(x - hi) into the A_lo rows
-// (64 on) and B_lo, one 16-byte unit per step of the 128 converter threads.
-__device__ __forceinline__ void split_chunk(uint8_t *stage, int m, int n, int t) {
-  uint8_t *A = stage, *Bh = A + A_BYTES, *Bl = Bh + B_BYTES;
-  for (int u = t; u < 4 * (m + n); u += 128) {
-    const bool isa = u < 4 * m;
-    const int v = isa ? u : u - 4 * m, r = v >> 2, q = v & 3;
-    float4 *hi = reinterpret_cast<float4 *>((isa ? A : Bh) + off(r, 4 * q));
-    float4 *lo = reinterpret_cast<float4 *>(isa ? A + off(r + 64, 4 * q) : Bl + off(r, 4 * q));
-    const float4 x = *hi;
-    const float4 h = make_float4(tc::to_tf32(x.x), tc::to_tf32(x.y), tc::to_tf32(x.z), tc::to_tf32(x.w));
-    *lo = make_float4(tc::to_tf32(x.x - h.x), tc::to_tf32(x.y - h.y), tc::to_tf32(x.z - h.z), tc::to_tf32(x.w - h.w));
-    *hi = h;
+    const int64_t o = b_off + r * pitch + k0 + 4 * q;
+    cp_async16(Bh + off(r, 4 * q), shi + o);
+    cp_async16(Bl + off(r, 4 * q), slo + o);
   }
 }
 
@@ -102,9 +89,7 @@ __device__ __forceinline__ void split_chunk(uint8_t *stage, int m, int n, int t)
 //   warp 2 (producer): copies each chunk into the next free stage; a stage is free once the MMAs
 //     of the chunk it held completed (empty[st], committed by the MMA thread); its lanes arrive on
 //     full[st] when their copies have landed;
-//   warps 4-7 (converters): split each landed chunk into TF32 hi and lo in place and arrive on
-//     ready[st];
-//   warp 3, lane 0 (MMA): per chunk, waits for ready[st], issues 3 x (KC / 8) MMAs into the
+//   warp 3, lane 0 (MMA): per chunk, waits for full[st], issues 3 x (KC / 8) MMAs into the
 //     segment's accumulator (two alternate; it waits for the epilogue to have read one before
 //     reusing it, acc_empty) and commits to empty[st], and at a segment's end to acc_full;
 //   warps 0-1 (epilogue; warp w reads tensor-memory lanes 32 w .. 32 w + 31, one accumulator row
@@ -112,30 +97,33 @@ __device__ __forceinline__ void split_chunk(uint8_t *stage, int m, int n, int t)
 //     entry's last segment, subtract the sum from the tile through the entry's relative maps, then
 //     meet at a barrier of the two warps (the next entry may write the same tile elements).
 // Per K = 8 step the accumulator rows 0-63 receive A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T: the
-// third MMA takes its A operand from the A_lo rows (rows 64.. of the staged [A_hi; A_lo]; its rows
-// beyond 64 then read the B operands and land in accumulator rows 64-127, which nobody reads).
+// third MMA takes its A operand from the A_lo rows (rows 64.. of the staged [A_hi; A_lo], its rows
+// beyond 64 then read the B operands and land in accumulator rows 64-127, which nobody reads). The
+// dropped A_lo B_lo^T is below 2^-22 |A| |B|, the size of the split's own error.
 // A segment is at most SEG chunks of one entry. Every wait is bounded (wait_ns; about a second by
 // default) and also ends when another warp has given up; then -1 goes to *status, the tile is left
 // unwritten, and the tensor memory is freed once every issued MMA has completed. withhold != 0 (a
 // failure-path test) issues no MMA and no commit, so the first waits run out.
-constexpr int EPI_WARPS = 2, PRODUCER = 2, MMA_WARP = 3, CONVERTERS = 4;
-constexpr int TC_BLOCK = 32 * 8;
+constexpr int EPI_WARPS = 2, PRODUCER = 2, MMA_WARP = 3;
+constexpr int TC_BLOCK = 32 * 4;
 constexpr uint32_t LO_ROWS = 8 * SBO;  // byte offset of row 64 (the A_lo rows) in an A operand
 
 __global__ void __launch_bounds__(TC_BLOCK, 2) k_update_tc(const SNode *__restrict__ sn,
                                                            const UpdTask *__restrict__ tasks,
                                                            const UpdEntry *__restrict__ ents,
                                                            const int32_t *__restrict__ rel, float *__restrict__ Lx,
-                                                           const float *__restrict__ ltr, int64_t toff,
+                                                           const float *__restrict__ shi,
+                                                           const float *__restrict__ slo, int64_t toff,
                                                            const Batch bt, long long *status, uint64_t wait_ns,
                                                            int withhold) {
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t full[NSTAGE], ready[NSTAGE], empty[NSTAGE], acc_full[2], acc_empty[2], done;
+  __shared__ __align__(8) uint64_t full[NSTAGE], empty[NSTAGE], acc_full[2], acc_empty[2], done;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int fail;
   __shared__ int8_t pcol[2][NB];  // tile column of each column of an entry (by entry parity)
   Lx += blockIdx.y * bt.lx;
-  ltr += blockIdx.y * bt.sx;
+  shi += blockIdx.y * bt.sx;
+  slo += blockIdx.y * bt.sx;
   status += blockIdx.y;
   uint8_t *stage0 = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   float *tile = reinterpret_cast<float *>(stage0 + NSTAGE * STAGE_BYTES);  // [col][row], TILE_LD
@@ -153,7 +141,6 @@ __global__ void __launch_bounds__(TC_BLOCK, 2) k_update_tc(const SNode *__restri
   if (tid == 32) {
     for (int b = 0; b < NSTAGE; ++b) {
       tc::mbar_init(&full[b], 32);
-      tc::mbar_init(&ready[b], CONVERTERS);
       tc::mbar_init(&empty[b], 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -195,7 +182,7 @@ __global__ void __launch_bounds__(TC_BLOCK, 2) k_update_tc(const SNode *__restri
           give_up();
           break;
         }
-        stage_chunk(stage0 + st * STAGE_BYTES, ltr, sk.sx + (int64_t)E.r_lo * pitch,
+        stage_chunk(stage0 + st * STAGE_BYTES, shi, slo, sk.sx + (int64_t)E.r_lo * pitch,
                     sk.sx + (int64_t)E.c_lo * pitch, pitch, E.m, E.n, c, lane);
         tc::cp_async_arrive(&full[st]);
       }
@@ -222,7 +209,7 @@ __global__ void __launch_bounds__(TC_BLOCK, 2) k_update_tc(const SNode *__restri
         }
         for (int c = 0; c < nch; ++c, ++j) {
           const int st = j % NSTAGE, acc = seg & 1;
-          if (!tc::mbar_wait_or_abort(&ready[st], (uint32_t)(j / NSTAGE) & 1u, wait_ns, &fail)) {
+          if (!tc::mbar_wait_or_abort(&full[st], (uint32_t)(j / NSTAGE) & 1u, wait_ns, &fail)) {
             give_up();
             break;
           }
@@ -256,29 +243,6 @@ __global__ void __launch_bounds__(TC_BLOCK, 2) k_update_tc(const SNode *__restri
       if (issued) {  // every issued MMA completes before the tensor memory can be freed
         tc::commit(&done);
         if (!tc::mbar_wait(&done, 0u, wait_ns)) give_up();
-      }
-    }
-  } else if (warp >= 4) {  // converters
-    const int ct = tid - 128;
-    int j = 0;
-    UpdEntry En = t.e0 < t.e1 ? ents[t.e0] : UpdEntry{};
-    bool ok = true;
-    for (int64_t e = t.e0; e < t.e1 && ok && !fail; ++e) {
-      const UpdEntry E = En;
-      const int nch = (sn[E.K].ncols + KC - 1) / KC;
-      if (e + 1 < t.e1) En = ents[e + 1];
-      for (int c = 0; c < nch; ++c, ++j) {
-        const int st = j % NSTAGE;
-        if (!__all_sync(0xffffffffu, tc::mbar_wait_or_abort(&full[st], (uint32_t)(j / NSTAGE) & 1u, wait_ns,
-                                                            &fail))) {
-          give_up();
-          ok = false;
-          break;
-        }
-        split_chunk(stage0 + st * STAGE_BYTES, E.m, E.n, ct);
-        tc::fence_smem_to_async();  // the tensor core reads these stores
-        __syncwarp();
-        if (lane == 0) tc::mbar_arrive(&ready[st]);
       }
     }
   } else {  // epilogue warps 0-1: accumulator row tid
@@ -382,8 +346,8 @@ cudaError_t launch_update_tc(dim3 grid, cudaStream_t st, int prio, const DevPlan
   attr[0].val.priority = prio;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_update_tc, d.sn, d.upd_tasks, d.upd_entries, d.rel, Lx, (const float *)d.ltr,
-                            toff, bt, status, d.tc_wait_ns, (int)d.tc_withhold);
+  return cudaLaunchKernelEx(&cfg, k_update_tc, d.sn, d.upd_tasks, d.upd_entries, d.rel, Lx, (const float *)d.shi,
+                            (const float *)d.slo, toff, bt, status, d.tc_wait_ns, (int)d.tc_withhold);
 }
 
 }  // namespace sym
