@@ -73,7 +73,6 @@ struct sym_handle_s {
   sym::PivotInfo *d_pivinfo = nullptr; // per matrix
   sym::PivotInfo *h_pivinfo = nullptr; // pinned copy, per matrix
   double pivot_threshold = 1.0 / 65536.0;
-  float *d_shi = nullptr, *d_slo = nullptr;  // TF32 split copies of the FP32 factor (tensor cores)
   double refine_tol = 1e-12;
   int32_t refine_max_iter = 100;
   int32_t last_iterations = 0;
@@ -158,7 +157,7 @@ void release_device(sym_handle_s *h) {
   if (h->aux_stream) cudaStreamDestroy(h->aux_stream);
   {
     void *mp[] = {h->d_Linv, h->d_Lfinv, h->d_Lf, h->d_Axc, h->d_anorm, h->d_anorm_work, h->d_csr_p, h->d_csr_i,
-                  h->d_csr_map, h->d_rwork, h->d_piv, h->d_dpos, h->d_pivinfo, h->d_shi, h->d_slo};
+                  h->d_csr_map, h->d_rwork, h->d_piv, h->d_dpos, h->d_pivinfo};
     for (void *p : mp)
       if (p) cudaFree(p);
     if (h->h_eta) cudaFreeHost(h->h_eta);
@@ -212,7 +211,6 @@ sym::Batch factor_batch(const sym_handle_s *h, int32_t nbatch, int64_t stride) {
   bt.dinv = h->plan.dinv_storage;
   bt.piv = h->plan.n;
   bt.nnz = h->plan.nnz_a;
-  bt.sx = h->plan.split_storage;
   return bt;
 }
 
@@ -273,17 +271,6 @@ int ensure_batch(sym_handle_s *h, int32_t nbatch) {
     h->dp.axc = h->d_Axc;
     if (!rc) rc = regrow((void **)&h->d_anorm, sizeof(double) * nb, "cudaMalloc(norms)");
     if (!rc) rc = regrow((void **)&h->d_piv, sizeof(double) * P.n * nb, "cudaMalloc(pivots)");
-    if (!rc && h->dp.tensor_cores) {
-      rc = regrow((void **)&h->d_shi, sizeof(float) * P.split_storage * nb, "cudaMalloc(split copies)");
-      if (!rc) rc = regrow((void **)&h->d_slo, sizeof(float) * P.split_storage * nb, "cudaMalloc(split copies)");
-      if (!rc) {  // the padding columns of every row stay zero
-        cudaError_t e = cudaMemset(h->d_shi, 0, sizeof(float) * P.split_storage * nb);
-        if (e == cudaSuccess) e = cudaMemset(h->d_slo, 0, sizeof(float) * P.split_storage * nb);
-        if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemset(split copies)");
-      }
-      h->dp.shi = h->d_shi;
-      h->dp.slo = h->d_slo;
-    }
     if (!rc) rc = regrow((void **)&h->d_pivinfo, sizeof(sym::PivotInfo) * nb, "cudaMalloc(pivot ratios)");
     if (!rc) {
       if (h->h_pivinfo) cudaFreeHost(h->h_pivinfo);
@@ -558,15 +545,6 @@ static int analyze_impl(int64_t n, const int64_t *Ap, const int32_t *Ai, const i
         if (e != cudaSuccess) rc = cuda_fail(e, "cudaMalloc(pivots)");
         else bytes += sizeof(double) * P.n;
       }
-      if (!rc && (opt.flags & SYM_FLAG_NO_TENSOR_CORES) == 0) {
-        const size_t sb = sizeof(float) * (P.split_storage > 0 ? P.split_storage : 1);
-        e = cudaMalloc(&h->d_shi, sb);
-        if (e == cudaSuccess) e = cudaMalloc(&h->d_slo, sb);
-        if (e == cudaSuccess) e = cudaMemset(h->d_shi, 0, sb);  // the padding columns stay zero
-        if (e == cudaSuccess) e = cudaMemset(h->d_slo, 0, sb);
-        if (e != cudaSuccess) rc = cuda_fail(e, "cudaMalloc(split copies)");
-        else bytes += 2 * (int64_t)sb;
-      }
       if (!rc) {
         e = cudaMalloc(&h->d_pivinfo, sizeof(sym::PivotInfo));
         if (e != cudaSuccess) rc = cuda_fail(e, "cudaMalloc(pivot ratio)");
@@ -607,8 +585,6 @@ static int analyze_impl(int64_t n, const int64_t *Ap, const int32_t *Ai, const i
     h->dp.storage = P.storage();
     h->dp.tensor_cores = (opt.flags & SYM_FLAG_NO_TENSOR_CORES) == 0;
     h->dp.piv = h->d_piv;
-    h->dp.shi = h->d_shi;
-    h->dp.slo = h->d_slo;
     h->dp.axc = h->d_Axc;
     h->dp.dpos = (const int64_t *)h->d_dpos;
   }

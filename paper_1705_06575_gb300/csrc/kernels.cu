@@ -595,22 +595,11 @@ __global__ void __launch_bounds__(TileCfg<TB>::threads) k_potrf(const SNode *__r
   }
 }
 
-// Round an FP32 value to TF32 (nearest, ties away from zero): its 13 low mantissa bits clear.
-__device__ __forceinline__ float tf32_of(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
-
-// (c) Tile (i, s) <- tile * L_ss^{-T}: forward substitution over the tile's columns. The tile is
-// final afterwards; an FP32 factor whose updates run on the tensor cores also stores it as its
-// TF32 split hi = tf32(x), lo = tf32(x - hi), transposed (each row's values contiguous), which
-// the tensor-core update copies into shared memory as it is.
+// (c) Tile (i, s) <- tile * L_ss^{-T}: forward substitution over the tile's columns.
 template <typename T, int TB>
 __global__ void __launch_bounds__(TileCfg<TB>::threads) k_trsm(const SNode *__restrict__ sn,
                                                                const Int4 *__restrict__ tasks,
-                                                               T *__restrict__ Lx, float *__restrict__ shi,
-                                                               float *__restrict__ slo, int64_t toff, const Batch bt) {
+                                                               T *__restrict__ Lx, int64_t toff, const Batch bt) {
   constexpr int TT = TileCfg<TB>::threads;
   Lx += blockIdx.y * bt.lx;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -659,17 +648,6 @@ __global__ void __launch_bounds__(TileCfg<TB>::threads) k_trsm(const SNode *__re
   for (int idx = tid; idx < tm * ts; idx += TT) {
     int r = idx % tm, c = idx / tm;
     B[(int64_t)c * sj.nrows + r] = X[c][r];
-  }
-  if (std::is_same<T, float>::value && shi) {
-    const int64_t pitch = split_pitch(sj.ncols);
-    const int64_t base = blockIdx.y * bt.sx + sj.sx + rb * pitch + (int64_t)s * NB;
-    for (int idx = tid; idx < tm * ts; idx += TT) {
-      const int c = idx % ts, r = idx / ts;  // consecutive threads: consecutive columns of a row
-      const float x = (float)X[c][r];
-      const float h = tf32_of(x);
-      shi[base + r * pitch + c] = h;
-      slo[base + r * pitch + c] = tf32_of(x - h);
-    }
   }
 }
 
@@ -1636,9 +1614,9 @@ cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, co
         // (a warp-per-tile form with the column pairs mapped flat onto the lanes made the
         // 512 x 128^2 batch's TRSM slower, 11.0 -> 16.3 ms: its tiles have enough rows)
         e = small ? launch_prio(k_trsm<T, SMALL_TB>, dim3(g, nb), TS, trsm_smem<T, SMALL_TB>(), s, prio, d.sn, d.tasks, Lx,
-                                d.shi, d.slo, L.off, bt)
+                                L.off, bt)
                   : launch_prio(k_trsm<T, NB>, dim3(g, nb), THREADS, trsm_smem<T, NB>(), s, prio, d.sn, d.tasks, Lx,
-                                d.shi, d.slo, L.off, bt);
+                                L.off, bt);
         break;
       case K_GEMM:
         if constexpr (std::is_same<T, double>::value)

@@ -30,9 +30,6 @@ struct DevPlan {
                                      // and no commit, so its first wait runs out
   double *piv = nullptr;             // FP32 factors: the FP64 pivot d_k of every permuted column k
                                      // (n per matrix), written by the POTRF kernels; else null
-  float *shi = nullptr, *slo = nullptr;  // FP32 factors on the tensor cores: TF32 split copies
-                                     // hi = tf32(x), lo = tf32(x - hi) of every tile below a
-                                     // diagonal tile (SNode::sx), written by the TRSM kernels
   const double *axc = nullptr;       // FP32 factors: the FP64 copy of A's values (nnz_a per matrix)
   const int64_t *dpos = nullptr;     // FP32 factors: index in A's values of C_kk, per column k
 };
@@ -44,7 +41,6 @@ struct DevPlan {
 struct Batch {
   int32_t count = 1;
   int64_t lx = 0, ax = 0, dinv = 0, y = 0, b = 0, x = 0, t = 0, piv = 0, nnz = 0;  // nnz: DevPlan::axc
-  int64_t sx = 0;  // DevPlan::shi / slo
 };
 
 // Second stream for the factor's lookahead: aux runs the launches with stream == 1 at low

@@ -41,16 +41,7 @@ struct SNode {
   int64_t tx;     // offset of its pushed products in the forward solve's buffer t: chunk ch of
                   // its columns gives t[tx + ch * (nrows - ncols) + (r - ncols)] for each row r
                   // below the diagonal block
-  int64_t sx;     // FP32 factors: offset of its TF32 split copies (hi and lo arrays alike), rows
-                  // in panel order, each row's values contiguous over split_pitch(ncols) columns
 };
-
-// Row length of a supernode's TF32 split copy: its column count rounded up to the tensor-core
-// operand chunk (32 values), the padding zero. (Host and device code use it.)
-#ifdef __CUDACC__
-__host__ __device__
-#endif
-inline int64_t split_pitch(int32_t ncols) { return ((int64_t)ncols + 31) & ~(int64_t)31; }
 
 // Row tiling of a panel: the diagonal block is cut at multiples of NB, and the rows below it
 // (the off-diagonal block) again from row ncols, so that tile (s, s) is exactly the square
@@ -152,7 +143,6 @@ struct Plan {
   std::vector<int32_t> level, levelptr, levellist;
   std::vector<int64_t> lxptr;         // nsuper+1; lxptr[nsuper] = storage
   int64_t dinv_storage = 0;           // entries of all diagonal-tile inverses
-  int64_t split_storage = 0;          // entries of each TF32 split copy (hi, lo) of an FP32 factor
   std::vector<int64_t> amap;          // nnz_a: panel position of each entry of A
   // Full CSR of C = P A P^T (both triangles) for FP64 residuals of the mixed-precision path;
   // built only when requested. cmap[p] is the index of the entry of A that gives C's entry p.

@@ -471,8 +471,6 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
     P.max_ncols = std::max(P.max_ncols, s.ncols);
     s.tx = P.tsize;
     P.tsize += (int64_t)(s.nrows - s.ncols) * ((s.ncols + SOLVE_CW - 1) / SOLVE_CW);
-    s.sx = P.split_storage;
-    P.split_storage += (int64_t)s.nrows * split_pitch(s.ncols);
   }
   // Contribution lists of the forward solve: row g below the diagonal block of J receives
   // L_J(g, :) y_J, pushed as one partial product per column chunk of J.

@@ -122,44 +122,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, uint6
   return false;
 }
 
-// As mbar_wait, but also gives up as soon as *abort (shared memory, set by another warp of the
-// CTA when its own wait ran out) is non-zero.
-__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t *mbar, uint32_t parity, uint64_t limit_ns,
-                                                   const volatile int *abort) {
-  const uint32_t a = smem_addr(mbar);
-  uint64_t t0;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
-  for (int i = 0; i < (1 << 26); ++i) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (done) return true;
-    if ((i & 63) == 63) {
-      if (*abort) return false;
-      uint64_t t;
-      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-      if (t - t0 > limit_ns) return false;
-    }
-  }
-  return false;
-}
-
-// Plain arrive (count one) on an mbarrier.
-__device__ __forceinline__ void mbar_arrive(uint64_t *mbar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(mbar)) : "memory");
-}
-
-// Arrive on the mbarrier once every cp.async this thread issued before has completed (the
-// arrival counts against the barrier's expected count).
-__device__ __forceinline__ void cp_async_arrive(uint64_t *mbar) {
-  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(mbar)) : "memory");
-}
-
 // Read 32 consecutive accumulator columns of this warp's 32 lanes (lane = row within the warp's
 // quarter of tensor memory): v[j] = D[row][col + j]. The wait sits in the same asm statement so
 // that no register is read before the load has landed.

@@ -2,19 +2,16 @@
 //
 // The left-looking update of Sec. 3.2 restricted to one 64 x 64 tile (bi, bj) of supernode J:
 // for every descendant entry, C -= L_K(R1, :) L_K(R0, :)^T scattered through the relative maps.
-// Each entry is a compact GEMM: its m rows R1 and n rows R0 are contiguous rows of K's panel, so
-// they are staged as they are (rows 0..m-1 and 0..n-1 of the operands) from K's TF32 split copy,
-// which the TRSM kernels wrote once, transposed (each row's k values contiguous) and already
-// split, when K's panel became final. The tensor core forms the m x n product in tensor memory;
-// the relative maps are applied only on the way out, when the product is subtracted from the
-// tile, which sits in shared memory for the whole CTA and is written back once.
+// Here each entry's two operands are expanded to the tile's coordinates while they are staged in
+// shared memory (row a of the entry lands at tile row rel(a); rows the entry does not touch are
+// zero), so every entry of the tile accumulates in the tile's coordinates: in tensor memory for
+// a few chunks at a time, then in FP32 registers, and the tile is written once.
 //
 // Precision. An FP32 value x is split into two TF32 values hi = tf32(x) and lo = tf32(x - hi)
-// (|x - hi - lo| <= 2^-22 |x|). The A operand is staged as the 128-row matrix [A_hi; A_lo]; per
-// K = 8 step three MMAs (M = 128, N = n rounded up to 16) add A_hi B_hi^T, A_hi B_lo^T and
-// A_lo B_hi^T, each formed exactly, to accumulator rows 0-63 (A_lo B_lo^T, below 2^-22 |A| |B|,
-// is left out). Sums run in tensor memory over at most SEG chunks (256 values of k) and are then
-// added in FP32 registers (a long sum inside the tensor core loses accuracy), as in the SIMT form.
+// (|x - hi - lo| <= 2^-22 |x|). The A operand is staged as the 128-row matrix [A_hi; A_lo] and
+// multiplied by B_hi and by B_lo (two M = 128, N = 64, K = 8 MMAs per step): rows 0-63 of the
+// accumulator receive A_hi B^T, rows 64-127 A_lo B^T, and their sum is A B^T with all four
+// partial products, each formed exactly.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -25,24 +22,14 @@
 namespace sym {
 namespace {
 
-// Operand chunks of KC = 16 values of k, K-major core matrices without swizzle (8 rows x 16 bytes
-// each; the next 4 values of k LBO = 128 bytes on, the next 8 rows SBO = 512 bytes on), in
-// NSTAGE = 4 stages: the copies of three chunks are in flight while one chunk's MMAs run.
-constexpr int KC = 16;
-constexpr uint32_t LBO = 128, SBO = (KC / 4) * 128;
-constexpr uint32_t A_BYTES = 128 * KC * 4;      // [A_hi; A_lo]: 8 KB
-constexpr uint32_t B_BYTES = 64 * KC * 4;       // B_hi or B_lo: 4 KB
+constexpr int TC_THREADS = 128;
+constexpr uint32_t A_BYTES = 128 * tc::KC * 4;  // [A_hi; A_lo]: 16 KB
+constexpr uint32_t B_BYTES = 64 * tc::KC * 4;   // B_hi or B_lo: 8 KB
 constexpr uint32_t STAGE_BYTES = A_BYTES + 2 * B_BYTES;
-constexpr int NSTAGE = 4;
-constexpr int TILE_LD = NB + 1;                 // the tile in shared memory, [col][row]
-constexpr size_t SMEM_BYTES = NSTAGE * STAGE_BYTES + 128 + sizeof(float) * NB * TILE_LD;
-constexpr uint32_t TMEM_COLS = 2 * NB;          // two FP32 accumulators of 128 x 64
-constexpr int SEG = 16;                         // chunks per tensor-memory sum (256 values of k)
-
-// Byte offset of element (row r, k) of an operand chunk.
-__device__ __forceinline__ uint32_t off(int r, int k) {
-  return (uint32_t)(r >> 3) * SBO + (uint32_t)(k >> 2) * LBO + (uint32_t)(r & 7) * 16u + (uint32_t)(k & 3) * 4u;
-}
+constexpr int NSTAGE = 2;
+constexpr size_t SMEM_BYTES = NSTAGE * STAGE_BYTES + 128;  // + room to align the stages to 128 B
+constexpr uint32_t TMEM_COLS = 2 * NB;  // two FP32 accumulators of 128 x 64
+constexpr uint32_t IDESC = tc::idesc_tf32<128, 64>();
 
 __device__ __forceinline__ int64_t tile_base(int32_t i, int32_t ncols, int32_t ncb) {
   return i < ncb ? (int64_t)i * NB : (int64_t)ncols + (int64_t)(i - ncb) * NB;
@@ -53,80 +40,93 @@ __device__ __forceinline__ int tile_rows(int32_t i, int32_t ncols, int32_t nrows
   return (int)(r < NB ? r : NB);
 }
 
-// kind::tf32 instruction descriptor with M = 128 and n rounded up to a multiple of 16.
-__device__ __forceinline__ uint32_t idesc_for(int n) {
-  const uint32_t N = (uint32_t)((n + 15) & ~15);
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((N >> 3) << 17) | ((128u >> 4) << 24);
+// Four consecutive k values (k0 + 4 kq ..) of panel row `row` of K (column-major, ld nrows),
+// zero past kc or when the tile position has no row of the entry (row < 0).
+__device__ __forceinline__ float4 load4(const float *Kp, int64_t ld, int row, int k0, int k, int kc) {
+  float v[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) v[i] = (row >= 0 && k + i < kc) ? Kp[(int64_t)(k0 + k + i) * ld + row] : 0.f;
+  return make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void split_store(uint8_t *hi_buf, uint8_t *lo_buf, uint32_t o, float4 x) {
+  const float4 h = make_float4(tc::to_tf32(x.x), tc::to_tf32(x.y), tc::to_tf32(x.z), tc::to_tf32(x.w));
+  const float4 l = make_float4(tc::to_tf32(x.x - h.x), tc::to_tf32(x.y - h.y), tc::to_tf32(x.z - h.z),
+                               tc::to_tf32(x.w - h.w));
+  *reinterpret_cast<float4 *>(hi_buf + o) = h;
+  *reinterpret_cast<float4 *>(lo_buf + o) = l;
 }
 
-__device__ __forceinline__ void cp_async16(uint32_t saddr, const void *g) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr), "l"(g) : "memory");
-}
+// Entries are taken in batches of EB: their descriptors and inverse row maps (tile position ->
+// entry row, or -1) are loaded into shared memory first, so that the operand loads of the next
+// chunk depend on shared memory only and can be issued while the current chunk is staged.
+constexpr int EB = 32;
 
-// Copies of chunk c (KC values of k from c KC on) of one entry into a stage, issued by the 32 lanes
-// of the producer warp: 16-byte units (4 values of k) of the rows of [A_hi; A_lo] and B_hi, B_lo,
-// each landing in its K-major core-matrix position. Unit u of an operand: row u / 4, 4 (u % 4) on.
-__device__ __forceinline__ void stage_chunk(uint8_t *stage, const float *__restrict__ shi,
-                                            const float *__restrict__ slo, int64_t a_off, int64_t b_off,
-                                            int64_t pitch, int m, int n, int c, int lane) {
-  const uint32_t A = tc::smem_addr(stage), Bh = A + A_BYTES, Bl = Bh + B_BYTES;
-  const int64_t k0 = (int64_t)c * KC;
-  for (int u = lane; u < 4 * m; u += 32) {
-    const int r = u >> 2, q = u & 3;
-    const int64_t o = a_off + r * pitch + k0 + 4 * q;
-    cp_async16(A + off(r, 4 * q), shi + o);
-    cp_async16(A + off(r + 64, 4 * q), slo + o);
+struct EntryBatch {
+  int64_t kp[EB];                       // offset of K's panel in Lx
+  int32_t ld[EB], kc[EB], rlo[EB], clo[EB];
+  int8_t inv_r[EB][NB], inv_c[EB][NB];  // tile row / column position -> entry row, or -1
+};
+
+// Operand values of one chunk for this thread: tile position p, k = 4 (kq0 + 2 j) + i.
+struct Prefetch {
+  float a[4][4], b[4][4];
+};
+__device__ __forceinline__ void fetch(Prefetch &f, const float *__restrict__ Lx, const EntryBatch &eb, int i, int k0,
+                                      int p, int kq0) {
+  const int ar = eb.inv_r[i][p], bc = eb.inv_c[i][p];
+  const int64_t ld = eb.ld[i];
+  const int rem = eb.kc[i] - k0;
+  const float *pa = Lx + eb.kp[i] + (int64_t)k0 * ld + eb.rlo[i] + max(ar, 0);
+  const float *pb = Lx + eb.kp[i] + (int64_t)k0 * ld + eb.clo[i] + max(bc, 0);
+  if (rem >= tc::KC) {  // a whole chunk: only the row predicates
+#pragma unroll
+    for (int j = 0; j < tc::KC / 8; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int k = 4 * (kq0 + 2 * j) + q;
+        f.a[j][q] = ar >= 0 ? pa[k * ld] : 0.f;
+        f.b[j][q] = bc >= 0 ? pb[k * ld] : 0.f;
+      }
+  } else {
+#pragma unroll
+    for (int j = 0; j < tc::KC / 8; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int k = 4 * (kq0 + 2 * j) + q;
+        f.a[j][q] = (ar >= 0 && k < rem) ? pa[k * ld] : 0.f;
+        f.b[j][q] = (bc >= 0 && k < rem) ? pb[k * ld] : 0.f;
+      }
   }
-  for (int u = lane; u < 4 * n; u += 32) {
-    const int r = u >> 2, q = u & 3;
-    const int64_t o = b_off + r * pitch + k0 + 4 * q;
-    cp_async16(Bh + off(r, 4 * q), shi + o);
-    cp_async16(Bl + off(r, 4 * q), slo + o);
-  }
 }
 
-// One CTA per tile, two CTAs per SM, with warp roles (no CTA-wide barrier inside the loop):
-//   warp 2 (producer): copies each chunk into the next free stage; a stage is free once the MMAs
-//     of the chunk it held completed (empty[st], committed by the MMA thread); its lanes arrive on
-//     full[st] when their copies have landed;
-//   warp 3, lane 0 (MMA): per chunk, waits for full[st], issues 3 x (KC / 8) MMAs into the
-//     segment's accumulator (two alternate; it waits for the epilogue to have read one before
-//     reusing it, acc_empty) and commits to empty[st], and at a segment's end to acc_full;
-//   warps 0-1 (epilogue; warp w reads tensor-memory lanes 32 w .. 32 w + 31, one accumulator row
-//     per thread): per segment, add the accumulator to FP32 registers and release it; after an
-//     entry's last segment, subtract the sum from the tile through the entry's relative maps, then
-//     meet at a barrier of the two warps (the next entry may write the same tile elements).
-// Per K = 8 step the accumulator rows 0-63 receive A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T: the
-// third MMA takes its A operand from the A_lo rows (rows 64.. of the staged [A_hi; A_lo], its rows
-// beyond 64 then read the B operands and land in accumulator rows 64-127, which nobody reads). The
-// dropped A_lo B_lo^T is below 2^-22 |A| |B|, the size of the split's own error.
-// A segment is at most SEG chunks of one entry. Every wait is bounded (wait_ns; about a second by
-// default) and also ends when another warp has given up; then -1 goes to *status, the tile is left
-// unwritten, and the tensor memory is freed once every issued MMA has completed. withhold != 0 (a
-// failure-path test) issues no MMA and no commit, so the first waits run out.
-constexpr int EPI_WARPS = 2, PRODUCER = 2, MMA_WARP = 3;
-constexpr int TC_BLOCK = 32 * 4;
-constexpr uint32_t LO_ROWS = 8 * SBO;  // byte offset of row 64 (the A_lo rows) in an A operand
+// One CTA (4 warps) per tile, three CTAs per SM. Thread 0 issues the MMAs; all threads stage
+// operands, two stages deep: the loads of chunk c + 1 are in flight while chunk c is converted
+// and stored, and the MMAs of chunk c run while chunk c + 1 is staged.
+//
+// Accumulation. The tensor core accumulates into tensor memory; the MMAs of SEG consecutive
+// chunks (one segment, across entry boundaries: every entry lands in the tile's coordinates) go
+// to one of two accumulators, which is then read back and added to FP32 registers (each thread
+// owns one accumulator row: warps 0-1 the A_hi rows, warps 2-3 the A_lo rows) while the next
+// segment runs on the other accumulator. Long sums are thus rounded to nearest in FP32 as in the
+// SIMT form; inside the tensor core a sum runs over at most 8 SEG K = 8 steps.
+// A wait that runs out (wait_ns, about a second by default) records -1 in *status and leaves the
+// tile unwritten. withhold != 0 (a failure-path test) issues no MMA and no commit, so the first
+// wait runs out; nothing is then in flight when the tensor memory is freed.
+constexpr int SEG = 8;
 
-__global__ void __launch_bounds__(TC_BLOCK, 2) k_update_tc(const SNode *__restrict__ sn,
-                                                           const UpdTask *__restrict__ tasks,
-                                                           const UpdEntry *__restrict__ ents,
-                                                           const int32_t *__restrict__ rel, float *__restrict__ Lx,
-                                                           const float *__restrict__ shi,
-                                                           const float *__restrict__ slo, int64_t toff,
-                                                           const Batch bt, long long *status, uint64_t wait_ns,
-                                                           int withhold) {
+__global__ void __launch_bounds__(TC_THREADS, 3) k_update_tc(const SNode *__restrict__ sn,
+                                                             const UpdTask *__restrict__ tasks,
+                                                             const UpdEntry *__restrict__ ents,
+                                                             const int32_t *__restrict__ rel, float *__restrict__ Lx,
+                                                             int64_t toff, const Batch bt, long long *status,
+                                                             uint64_t wait_ns, int withhold) {
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t full[NSTAGE], empty[NSTAGE], acc_full[2], acc_empty[2], done;
+  __shared__ EntryBatch eb;
+  __shared__ __align__(8) uint64_t mbar[NSTAGE];
   __shared__ uint32_t tmem_slot;
-  __shared__ volatile int fail;
-  __shared__ int8_t pcol[2][NB];  // tile column of each column of an entry (by entry parity)
   Lx += blockIdx.y * bt.lx;
-  shi += blockIdx.y * bt.sx;
-  slo += blockIdx.y * bt.sx;
   status += blockIdx.y;
   uint8_t *stage0 = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-  float *tile = reinterpret_cast<float *>(stage0 + NSTAGE * STAGE_BYTES);  // [col][row], TILE_LD
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   const UpdTask t = tasks[toff + blockIdx.x];
@@ -135,193 +135,143 @@ __global__ void __launch_bounds__(TC_BLOCK, 2) k_update_tc(const SNode *__restri
   const int tm = tile_rows(t.bi, sj.ncols, sj.nrows, sj.ncb);
   const int cb = t.bj * NB;
   const int tn = min(NB, sj.ncols - cb);
-  float *C = Lx + sj.lx + (int64_t)cb * sj.nrows + rb;
 
   if (warp == 0) tc::tmem_alloc(&tmem_slot, TMEM_COLS);
-  if (tid == 32) {
-    for (int b = 0; b < NSTAGE; ++b) {
-      tc::mbar_init(&full[b], 32);
-      tc::mbar_init(&empty[b], 1);
-    }
-    for (int b = 0; b < 2; ++b) {
-      tc::mbar_init(&acc_full[b], 1);
-      tc::mbar_init(&acc_empty[b], EPI_WARPS);
-    }
-    tc::mbar_init(&done, 1);
-    fail = 0;
+  if (tid == 0) {
+    for (int b = 0; b < NSTAGE; ++b) tc::mbar_init(&mbar[b], 1);
     tc::mbar_init_fence();
-  }
-  for (int idx = tid; idx < tm * tn; idx += TC_BLOCK) {
-    const int r = idx % tm, c = idx / tm;
-    tile[c * TILE_LD + r] = C[(int64_t)c * sj.nrows + r];
-  }
-  if (t.e0 < t.e1 && tid < NB) {  // the first entry's column map
-    const UpdEntry E0 = ents[t.e0];
-    if (tid < E0.n) pcol[0][tid] = (int8_t)(rel[E0.relc + tid] - cb);
   }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = tmem_slot;
-  auto give_up = [&]() { fail = 1; };
+  const uint32_t row_addr = (uint32_t)(32 * warp) << 16;
 
-  if (warp == PRODUCER) {
-    int j = 0;  // chunk index over the tile's sequence
-    UpdEntry En = t.e0 < t.e1 ? ents[t.e0] : UpdEntry{};  // the next entry, loaded one ahead
-    for (int64_t e = t.e0; e < t.e1 && !fail; ++e) {
-      const UpdEntry E = En;
+  float acc[NB];
+#pragma unroll
+  for (int q = 0; q < NB; ++q) acc[q] = 0.f;
+  // Read back accumulator `which` (the MMAs of chunk `last` and all before it complete) and add
+  // it to acc. Uniform across the CTA; false when the wait ran out.
+  auto drain = [&](int which, int last) -> bool {
+    const bool ok = tc::mbar_wait(&mbar[last & 1], (uint32_t)(last >> 1) & 1u, wait_ns);
+    if (__syncthreads_or(!ok)) return false;
+    tc::fence_after_sync();
+    float v[32];
+    tc::ld32(tmem + row_addr + which * NB, v);
+#pragma unroll
+    for (int q = 0; q < 32; ++q) acc[q] += v[q];
+    tc::ld32(tmem + row_addr + which * NB + 32, v);
+#pragma unroll
+    for (int q = 0; q < 32; ++q) acc[32 + q] += v[q];
+    tc::fence_before_sync();
+    return true;
+  };
+
+  int it = 0;          // chunks issued (chunk it uses stage it % 2, accumulator (it / SEG) % 2)
+  bool failed = false;
+  const int p = tid & (NB - 1), kq0 = tid >> 6;
+  Prefetch f;
+  for (int64_t e0 = t.e0; e0 < t.e1 && !failed; e0 += EB) {
+    const int ne = (int)min((int64_t)EB, t.e1 - e0);
+    // (every thread has finished staging from the previous batch: a barrier follows each store)
+    for (int idx = tid; idx < ne * NB; idx += TC_THREADS) {
+      (&eb.inv_r[0][0])[idx] = -1;
+      (&eb.inv_c[0][0])[idx] = -1;
+    }
+    if (tid < ne) {
+      const UpdEntry E = ents[e0 + tid];
       const SNode sk = sn[E.K];
-      if (e + 1 < t.e1) En = ents[e + 1];
-      const int64_t pitch = split_pitch(sk.ncols);
-      const int nch = (sk.ncols + KC - 1) / KC;
-      for (int c = 0; c < nch; ++c, ++j) {
-        const int st = j % NSTAGE;
-        const bool free_st =
-            j < NSTAGE || tc::mbar_wait_or_abort(&empty[st], (uint32_t)(j / NSTAGE - 1) & 1u, wait_ns, &fail);
-        if (!__all_sync(0xffffffffu, free_st)) {  // the lanes agree
-          give_up();
+      eb.kp[tid] = sk.lx;
+      eb.ld[tid] = sk.nrows;
+      eb.kc[tid] = sk.ncols;
+      eb.rlo[tid] = E.r_lo;
+      eb.clo[tid] = E.c_lo;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < ne * NB; idx += TC_THREADS) {
+      const int i = idx / NB, a = idx % NB;
+      const UpdEntry &E = ents[e0 + i];
+      if (a < E.m) eb.inv_r[i][rel[E.relr + a] - (int)rb] = (int8_t)a;
+      if (a < E.n) eb.inv_c[i][rel[E.relc + a] - cb] = (int8_t)a;
+    }
+    __syncthreads();
+    int i = 0, k0 = 0;
+    fetch(f, Lx, eb, i, k0, p, kq0);
+    while (i < ne) {
+      const int st = it & 1;
+      if (it >= NSTAGE) {  // the MMAs of chunk it - 2 read this stage
+        const bool ok = tc::mbar_wait(&mbar[st], (uint32_t)((it >> 1) - 1) & 1u, wait_ns);
+        if (__syncthreads_or(!ok)) {
+          failed = true;
           break;
         }
-        stage_chunk(stage0 + st * STAGE_BYTES, shi, slo, sk.sx + (int64_t)E.r_lo * pitch,
-                    sk.sx + (int64_t)E.c_lo * pitch, pitch, E.m, E.n, c, lane);
-        tc::cp_async_arrive(&full[st]);
       }
-    }
-    asm volatile("cp.async.wait_all;" ::: "memory");
-  } else if (warp == MMA_WARP) {
-    if (lane == 0) {
-      int j = 0, seg = 0;
-      bool issued = false;
-      // the next entry's column count and width, loaded one entry ahead
-      int nxt_n = 0, nxt_k = 0;
-      if (t.e0 < t.e1) {
-        const UpdEntry E0 = ents[t.e0];
-        nxt_n = E0.n;
-        nxt_k = sn[E0.K].ncols;
-      }
-      for (int64_t e = t.e0; e < t.e1 && !fail; ++e) {
-        const int nch = (nxt_k + KC - 1) / KC;
-        const uint32_t idesc = idesc_for(nxt_n);
-        if (e + 1 < t.e1) {
-          const UpdEntry E1 = ents[e + 1];
-          nxt_n = E1.n;
-          nxt_k = sn[E1.K].ncols;
-        }
-        for (int c = 0; c < nch; ++c, ++j) {
-          const int st = j % NSTAGE, acc = seg & 1;
-          if (!tc::mbar_wait_or_abort(&full[st], (uint32_t)(j / NSTAGE) & 1u, wait_ns, &fail)) {
-            give_up();
-            break;
-          }
-          const bool first = c % SEG == 0;  // a segment starts: its accumulator must be free
-          if (first && seg >= 2 &&
-              !tc::mbar_wait_or_abort(&acc_empty[acc], (uint32_t)(seg / 2 - 1) & 1u, wait_ns, &fail)) {
-            give_up();
-            break;
-          }
-          tc::fence_smem_to_async();
-          tc::fence_after_sync();
-          if (!withhold) {
-            const uint32_t a0 = tc::smem_addr(stage0 + st * STAGE_BYTES);
-            const uint32_t bh0 = a0 + A_BYTES, bl0 = bh0 + B_BYTES;
-            const uint32_t d = tmem + (uint32_t)acc * NB;
-            uint32_t accumulate = first ? 0u : 1u;
-            for (int ks = 0; ks < KC / 8; ++ks) {
-              const uint32_t o = ks * 2 * LBO;  // K = 8: two core matrices along k
-              tc::mma_tf32(d, tc::desc(a0 + o, LBO, SBO), tc::desc(bh0 + o, LBO, SBO), idesc, accumulate);
-              tc::mma_tf32(d, tc::desc(a0 + o, LBO, SBO), tc::desc(bl0 + o, LBO, SBO), idesc, 1u);
-              tc::mma_tf32(d, tc::desc(a0 + LO_ROWS + o, LBO, SBO), tc::desc(bh0 + o, LBO, SBO), idesc, 1u);
-              accumulate = 1u;
-            }
-            tc::commit(&empty[st]);
-            if (c % SEG == SEG - 1 || c == nch - 1) tc::commit(&acc_full[acc]);
-            issued = true;
-          }
-          if (c % SEG == SEG - 1 || c == nch - 1) ++seg;
-        }
-      }
-      if (issued) {  // every issued MMA completes before the tensor memory can be freed
-        tc::commit(&done);
-        if (!tc::mbar_wait(&done, 0u, wait_ns)) give_up();
-      }
-    }
-  } else {  // epilogue warps 0-1: accumulator row tid
-    float racc[NB];
+      uint8_t *A = stage0 + st * STAGE_BYTES, *Bh = A + A_BYTES, *Bl = Bh + B_BYTES;
 #pragma unroll
-    for (int q = 0; q < NB; ++q) racc[q] = 0.f;
-    const uint32_t row_addr = (uint32_t)(32 * warp) << 16;
-    int seg = 0, par = 0;
-    bool go = true;  // uniform across the two epilogue warps
-    UpdEntry E = t.e0 < t.e1 ? ents[t.e0] : UpdEntry{};
-    int r = (t.e0 < t.e1 && tid < E.m) ? rel[E.relr + tid] - (int)rb : -1;
-    for (int64_t e = t.e0; e < t.e1 && go; ++e, par ^= 1) {
-      const int nch = (sn[E.K].ncols + KC - 1) / KC;
-      const int nseg = (nch + SEG - 1) / SEG;
-      // the next entry's maps, loaded while this one's MMAs run (its column map into the other
-      // buffer, which the barrier closing this entry publishes)
-      UpdEntry En = E;
-      int rn = -1;
-      if (e + 1 < t.e1) {
-        En = ents[e + 1];
-        if (tid < En.n) pcol[par ^ 1][tid] = (int8_t)(rel[En.relc + tid] - cb);
-        if (tid < En.m) rn = rel[En.relr + tid] - (int)rb;
+      for (int j = 0; j < tc::KC / 8; ++j) {
+        const uint32_t o = tc::off(p, 4 * (kq0 + 2 * j));
+        split_store(A, A + tc::off(NB, 0), o, make_float4(f.a[j][0], f.a[j][1], f.a[j][2], f.a[j][3]));
+        split_store(Bh, Bl, o, make_float4(f.b[j][0], f.b[j][1], f.b[j][2], f.b[j][3]));
       }
-      bool ok = true;
-      for (int g = 0; g < nseg; ++g, ++seg) {
-        const int acc = seg & 1;
-        // the lanes agree before the warp-wide tensor-memory loads
-        if (!__all_sync(0xffffffffu, tc::mbar_wait_or_abort(&acc_full[acc], (uint32_t)(seg / 2) & 1u, wait_ns,
-                                                            &fail))) {
-          ok = false;
-          break;
-        }
+      tc::fence_smem_to_async();
+      const int kc_now = min(tc::KC, eb.kc[i] - k0);
+      // advance to the next chunk of this batch and start its loads
+      k0 += tc::KC;
+      if (k0 >= eb.kc[i]) {
+        ++i;
+        k0 = 0;
+      }
+      if (i < ne) fetch(f, Lx, eb, i, k0, p, kq0);
+      __syncthreads();
+      const int seg = it / SEG;
+      if (tid == 0 && !withhold) {
         tc::fence_after_sync();
-        float v[32];
-        tc::ld32(tmem + row_addr + acc * NB, v);
-#pragma unroll
-        for (int q = 0; q < 32; ++q) racc[q] += v[q];
-        if (E.n > 32) {
-          tc::ld32(tmem + row_addr + acc * NB + 32, v);
-#pragma unroll
-          for (int q = 0; q < 32; ++q) racc[32 + q] += v[q];
+        const uint32_t a0 = tc::smem_addr(A), bh0 = tc::smem_addr(Bh), bl0 = tc::smem_addr(Bl);
+        const uint32_t d = tmem + (uint32_t)(seg & 1) * NB;
+        uint32_t accumulate = it % SEG != 0;
+        for (int ks = 0; ks < (kc_now + 7) / 8; ++ks) {
+          const uint32_t o = ks * tc::KSTEP;
+          tc::mma_tf32(d, tc::desc(a0 + o), tc::desc(bh0 + o), IDESC, accumulate);
+          tc::mma_tf32(d, tc::desc(a0 + o), tc::desc(bl0 + o), IDESC, 1u);
+          accumulate = 1u;
         }
-        tc::fence_before_sync();
-        __syncwarp();
-        if (lane == 0) tc::mbar_arrive(&acc_empty[acc]);
+        tc::commit(&mbar[st]);
       }
-      if (!ok) give_up();
-      if (ok && r >= 0) {
+      ++it;
+      // a new segment just started on the other accumulator: add up the finished one
+      if ((it - 1) % SEG == 0 && it > 1 && !drain((seg - 1) & 1, it - 2)) {
+        failed = true;
+        break;
+      }
+    }
+  }
+  // (it and failed are uniform across the CTA.) The open segment ends with the last chunk.
+  if (!failed && it > 0 && !drain(((it - 1) / SEG) & 1, it - 1)) failed = true;
+  if (failed && it > 0) {  // let the MMAs in flight finish (bounded) before the memory is freed
+    const int last = it - 1;
+    tc::mbar_wait(&mbar[last & 1], (uint32_t)(last >> 1) & 1u, wait_ns);
+    __syncthreads();
+    if (tid == 0) atomicMin(status, -1ll);
+  } else if (it > 0) {
+    float *red = reinterpret_cast<float *>(stage0);  // [col][row]: the A_lo rows' sums
+    if (warp >= 2) {
+      const int r = 32 * (warp - 2) + lane;
+#pragma unroll
+      for (int q = 0; q < NB; ++q) red[q * (NB + 1) + r] = acc[q];
+    }
+    __syncthreads();
+    if (warp < 2) {
+      const int r = 32 * warp + lane;
+      if (r < tm) {
+        float *C = Lx + sj.lx + (int64_t)cb * sj.nrows + rb + r;
 #pragma unroll
         for (int q = 0; q < NB; ++q)
-          if (q < E.n) tile[pcol[par][q] * TILE_LD + r] -= racc[q];
+          if (q < tn) C[(int64_t)q * sj.nrows] -= acc[q] + red[q * (NB + 1) + r];
       }
-#pragma unroll
-      for (int q = 0; q < NB; ++q) racc[q] = 0.f;
-      // the two warps continue together, unless either has seen a failure
-      uint32_t stop;
-      asm volatile(
-          "{\n\t.reg .pred p, q;\n\t"
-          "setp.ne.u32 p, %1, 0;\n\t"
-          "barrier.cta.red.or.pred q, 1, %2, p;\n\t"
-          "selp.u32 %0, 1, 0, q;\n\t}"
-          : "=r"(stop)
-          : "r"((uint32_t)(fail != 0 || !ok)), "n"(32 * EPI_WARPS)
-          : "memory");
-      go = stop == 0;
-      E = En;
-      r = rn;
     }
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (fail) {
-    if (tid == 0) atomicMin(status, -1ll);
-  } else {
-    for (int idx = tid; idx < tm * tn; idx += TC_BLOCK) {
-      const int r = idx % tm, c = idx / tm;
-      C[(int64_t)c * sj.nrows + r] = tile[c * TILE_LD + r];
-    }
-  }
   if (warp == 0) {
     tc::fence_after_sync();
     tc::tmem_free(tmem, TMEM_COLS);
@@ -339,15 +289,15 @@ cudaError_t launch_update_tc(dim3 grid, cudaStream_t st, int prio, const DevPlan
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   cfg.gridDim = grid;
-  cfg.blockDim = dim3(TC_BLOCK, 1, 1);
+  cfg.blockDim = dim3(TC_THREADS, 1, 1);
   cfg.dynamicSmemBytes = SMEM_BYTES;
   cfg.stream = st;
   attr[0].id = cudaLaunchAttributePriority;
   attr[0].val.priority = prio;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_update_tc, d.sn, d.upd_tasks, d.upd_entries, d.rel, Lx, (const float *)d.shi,
-                            (const float *)d.slo, toff, bt, status, d.tc_wait_ns, (int)d.tc_withhold);
+  return cudaLaunchKernelEx(&cfg, k_update_tc, d.sn, d.upd_tasks, d.upd_entries, d.rel, Lx, toff, bt, status,
+                            d.tc_wait_ns, (int)d.tc_withhold);
 }
 
 }  // namespace sym
