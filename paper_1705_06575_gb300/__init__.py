@@ -22,7 +22,7 @@ __all__ = [
     "sym_last_error_column", "sym_get_factor_host", "sym_export", "sym_free", "load", "Solver",
     "EXPORTS", "sym_profile", "sym_profile_read", "sym_profile_launches", "sym_fma_peak", "sym_tc_probe", "sym_solve_host_ptr", "KINDS",
     "sym_solve_multi_noalloc", "sym_set_refinement", "sym_refinement_info", "sym_pivot_info",
-    "sym_set_pivot_threshold", "sym_set_tc_wait", "sym_factor_batch",
+    "sym_set_pivot_threshold", "sym_set_tc_wait", "sym_analyze_rules", "sym_factor_batch",
     "sym_batch_error_columns", "sym_solve_batch", "sym_get_batch_factor_host", "Reach", "MLP",
 ]
 
@@ -149,6 +149,7 @@ def load():
             "sym_pivot_info": ([P, i32, ct.POINTER(ct.c_double), ct.POINTER(i64), ct.POINTER(i32)], I),
             "sym_set_pivot_threshold": ([P, ct.c_double], I),
             "sym_set_tc_wait": ([P, ct.c_uint64, i32], I),
+            "sym_analyze_rules": ([i64, P, P, P, ct.POINTER(sym_options), i32, P, i64, P, ct.POINTER(P)], I),
         }
         for name, (args, res) in sigs.items():
             f = getattr(lib, name)
@@ -198,6 +199,21 @@ def sym_analyze_perm(n, Ap, Ai, perm=None, opt=None):
     _check(load().sym_analyze_perm(int(n), Ap.ctypes.data, Ai.ctypes.data,
                                    None if pp is None else pp.ctypes.data,
                                    None if opt is None else ct.byref(opt), ct.byref(h)))
+    return h
+
+
+def sym_analyze_rules(n, Ap, Ai, perm, opt, rules, fund_rule):
+    """Inspector with one amalgamation rule per fundamental supernode: rules is an (R, 7) int32
+    table {amalgamate, nrelax[3], zrelax_permille[3]}, fund_rule one row index per fundamental
+    supernode of this pattern and ordering."""
+    Ap, Ai = _host(Ap, np.int64), _host(Ai, np.int32)
+    pp = None if perm is None else _host(perm, np.int32)
+    R = np.ascontiguousarray(rules, dtype=np.int32).reshape(-1, 7)
+    F = np.ascontiguousarray(fund_rule, dtype=np.int32)
+    h = ct.c_void_p()
+    _check(load().sym_analyze_rules(int(n), Ap.ctypes.data, Ai.ctypes.data, None if pp is None else pp.ctypes.data,
+                                    None if opt is None else ct.byref(opt), int(R.shape[0]), R.ctypes.data,
+                                    int(F.size), F.ctypes.data, ct.byref(h)))
     return h
 
 
@@ -481,9 +497,11 @@ def sym_free(h):
 class Solver:
     """Owning wrapper of one handle: analyze on construction, free on close."""
 
-    def __init__(self, n, Ap, Ai, perm=None, opt=None, host_only=False, precision=None, flags=0, ordering=None):
+    def __init__(self, n, Ap, Ai, perm=None, opt=None, host_only=False, precision=None, flags=0, ordering=None,
+                 rules=None):
         """perm: a fill-reducing ordering (SYM_ORDER_GIVEN); ordering="auto" lets the inspector
-        compute one (SYM_ORDER_AUTO)."""
+        compute one (SYM_ORDER_AUTO); rules = (table, fund_rule): one amalgamation rule per
+        fundamental supernode (sym_analyze_rules)."""
         if opt is None:
             opt = sym_options_default()
         opt.flags |= int(flags)
@@ -497,7 +515,10 @@ class Solver:
         if host_only:
             opt.flags |= SYM_FLAG_HOST_ONLY
         self.n = int(n)
-        self.h = sym_analyze_perm(n, Ap, Ai, perm, opt)
+        if rules is not None:
+            self.h = sym_analyze_rules(n, Ap, Ai, perm, opt, rules[0], rules[1])
+        else:
+            self.h = sym_analyze_perm(n, Ap, Ai, perm, opt)
 
     def info(self):
         return sym_info(self.h)

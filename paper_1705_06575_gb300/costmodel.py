@@ -17,7 +17,8 @@ import time
 
 import numpy as np
 
-from . import MLP, SYM_PREC_FP64, Solver, sym_options_default
+from . import (MLP, SYM_PREC_FP64, SYM_PROFILE_OFF, SYM_PROFILE_ON, SYM_PROFILE_RESET, Solver,
+               sym_options_default, sym_profile_launches)
 
 # (name, amalgamate, nrelax[3], zrelax_permille[3])
 PRESETS = [
@@ -187,8 +188,315 @@ def evaluate(model, X, Y, G, torch):
                                           for g in groups))}
 
 
+# ---------------------------------------------------------------------------------------------
+# Per-supernode rules: the network predicts, for every fundamental supernode and every preset
+# rule, the time that supernode's share of the factorization takes when that rule decides its
+# merge with the next supernode; each supernode then gets the rule with the smallest prediction
+# (sym_analyze_rules). The training targets are the launch times the executor measures
+# (sym_profile_launches, one profiled factorization per pattern and preset), spread over the
+# supernodes of each launch by their tasks' flops and from a final supernode to its fundamental
+# ones by their share of sum c_j^2.
+
+RULES = np.array([[am, *nr, *zr] for (_, am, nr, zr) in PRESETS], dtype=np.int32)
+NFEAT_SN = 21
+
+
+def fund_table(M):
+    """Per fundamental supernode of M (in SYM_EXPORT_FSUPER order): its structure and that of the
+    next supernode, with which the amalgamation rule may merge it."""
+    s = Solver(M.n, M.Ap, M.Ai, M.perm, opt=options(0), host_only=True)
+    sup = s.export("super").astype(np.int64)
+    rowptr = s.export("rowptr")
+    parent = s.export("parent")
+    level = s.export("level")
+    sparent = s.export("sparent")
+    cc = s.export("colcount").astype(np.float64)
+    s.close()
+    nf = sup.size - 1
+    ncols = np.diff(sup).astype(np.float64)
+    nrows = np.diff(rowptr).astype(np.float64)
+    csq = np.add.reduceat(cc * cc, sup[:-1]) if nf else np.zeros(0)
+    nnz = ncols * nrows - ncols * (ncols - 1) / 2
+    last = sup[1:] - 1
+    elig = np.zeros(nf, dtype=bool)
+    if nf > 1:
+        elig[:-1] = parent[last[:-1]] == last[:-1] + 1
+    nxt_c = np.zeros(nf)
+    nxt_r = np.zeros(nf)
+    nxt_c[:-1], nxt_r[:-1] = ncols[1:], nrows[1:]
+    # the merged trapezoid: the next supernode's rows plus this one's own columns
+    mc = ncols + nxt_c
+    mrows = ncols + nxt_r
+    total = mc * mrows - mc * (mc - 1) / 2
+    nnz_next = np.zeros(nf)
+    nnz_next[:-1] = nnz[1:]
+    zfrac = np.where(elig, (total - nnz - nnz_next) / np.maximum(total, 1), 0.0)
+    nchild = np.bincount(sparent[sparent >= 0], minlength=nf).astype(np.float64)
+    sub = ncols.copy()  # columns in the subtree (children precede parents)
+    for f in range(nf):
+        if sparent[f] >= 0:
+            sub[sparent[f]] += sub[f]
+    nlev = max(1, int(level.max()) + 1) if nf else 1
+    return {"nf": nf, "ncols": ncols, "nrows": nrows, "nxt_c": nxt_c, "nxt_r": nxt_r, "elig": elig,
+            "zfrac": zfrac, "nnz": nnz, "csq": csq, "level": level / nlev, "nchild": nchild, "sub": sub,
+            "n": float(M.n), "deg": float(M.nnz) / max(M.n, 1), "sup": sup}
+
+
+def sn_features(tab, rule):
+    """Feature rows of every fundamental supernode under one preset rule."""
+    lg = np.log1p
+    nf = tab["nf"]
+    am, nr, zr = PRESETS[rule][1], PRESETS[rule][2], PRESETS[rule][3]
+    cols = [lg(tab["ncols"]), lg(tab["nrows"]), lg(tab["nrows"] - tab["ncols"]), lg(tab["nxt_c"]),
+            lg(tab["nxt_r"]), tab["elig"].astype(np.float64), tab["zfrac"], lg(tab["nnz"]), lg(tab["csq"]),
+            tab["level"].astype(np.float64), lg(tab["nchild"]), lg(tab["sub"]),
+            np.full(nf, math.log1p(tab["n"])), np.full(nf, math.log1p(tab["deg"])), np.full(nf, float(am))]
+    cols += [np.full(nf, math.log1p(v)) for v in nr] + [np.full(nf, v / 1000.0) for v in zr]
+    return np.stack(cols, axis=1)
+
+
+def supernode_times(s, ms):
+    """Milliseconds of every final supernode of handle s: launch i of the factor schedule
+    (ms[i + 1]; ms[0] is the zeroing and scatter of A) spread over the supernodes of its tasks in
+    proportion to their flops (update tiles: 2 m n ncols(K) per entry; dense tiles: equal)."""
+    sup = s.export("super")
+    ncols = np.diff(sup).astype(np.float64)
+    L = s.export("factor_launches").reshape(-1, 5)
+    kinds = L[:, 0] & 0xffffffff
+    T = s.export("tasks").reshape(-1, 4)
+    U = s.export("upd_tasks").reshape(-1, 4)
+    E = s.export("upd_entries").reshape(-1, 5)
+    ew = 2.0 * (E[:, 1] >> 32).astype(np.float64) * (E[:, 2] & 0xffffffff).astype(np.float64) * \
+        ncols[(E[:, 0] & 0xffffffff)]
+    ecum = np.concatenate([[0.0], np.cumsum(ew)])
+    t = np.zeros(ncols.size)
+    for i in range(L.shape[0]):
+        off, cnt = int(L[i, 1]), int(L[i, 2])
+        if kinds[i] == 1:
+            u = U[off:off + cnt]
+            J = u[:, 0] & 0xffffffff
+            w = ecum[u[:, 3]] - ecum[u[:, 2]]
+        else:
+            J = T[off:off + cnt, 0].astype(np.int64)
+            w = np.ones(cnt)
+        tot = w.sum()
+        if tot > 0:
+            np.add.at(t, J, ms[i + 1] * w / tot)
+    return t
+
+
+def fund_times(tab, s, ms):
+    """Per fundamental supernode: its final supernode's time times its share of that supernode's
+    sum c_j^2."""
+    t = supernode_times(s, ms)
+    sup = s.export("super")
+    J = np.searchsorted(sup, tab["sup"][:-1], side="right") - 1
+    csqJ = np.bincount(J, weights=tab["csq"], minlength=sup.size - 1)
+    return t[J] * tab["csq"] / np.maximum(csqJ[J], 1e-30)
+
+
+def profiled_factor(M, torch, precision=SYM_PREC_FP64, opt=None, rules=None):
+    """(handle, per-launch milliseconds) of one profiled factorization after one warm-up."""
+    if opt is None:
+        opt = options(DEFAULT)
+    opt.precision = precision
+    s = Solver(M.n, M.Ap, M.Ai, M.perm, opt=opt, rules=rules)
+    s.set_stream(torch.cuda.current_stream())
+    Ax = torch.from_numpy(M.Ax).cuda()
+    s.factor(Ax)
+    s.profile(SYM_PROFILE_RESET)
+    s.profile(SYM_PROFILE_ON)
+    s.factor(Ax)
+    s.profile(SYM_PROFILE_OFF)
+    return s, np.asarray(sym_profile_launches(s.h, 0))
+
+
+def collect_sn(mats, torch, precision=SYM_PREC_FP64, flop_budget=4e10, log=None, max_rows=None, seed=0):
+    """Rows (features, log per-supernode milliseconds) over every (pattern, preset); patterns whose
+    default plan exceeds flop_budget are skipped (and counted)."""
+    X, Y, skipped = [], [], 0
+    for gi, M in enumerate(mats):
+        if _default_flops(M) > flop_budget:
+            skipped += 1
+            continue
+        tab = fund_table(M)
+        for p in range(len(PRESETS)):
+            s, ms = profiled_factor(M, torch, precision, opt=options(p))
+            tf = fund_times(tab, s, ms)
+            s.close()
+            X.append(sn_features(tab, p))
+            Y.append(np.log(tf + 1e-4))
+        if log:
+            log(f"{gi + 1}/{len(mats)} {M.name}: {tab['nf']} fundamental supernodes")
+    X = np.concatenate(X) if X else np.zeros((0, NFEAT_SN))
+    Y = np.concatenate(Y) if Y else np.zeros(0)
+    if max_rows and X.shape[0] > max_rows:
+        idx = np.random.default_rng(seed).choice(X.shape[0], max_rows, replace=False)
+        X, Y = X[idx], Y[idx]
+    return X, Y, skipped
+
+
+def _default_flops(M):
+    s = Solver(M.n, M.Ap, M.Ai, M.perm, opt=options(DEFAULT), host_only=True)
+    f = s.info().flops
+    s.close()
+    return f
+
+
+def choose_rules(model, M, torch):
+    """Per fundamental supernode, the preset rule with the smallest predicted time."""
+    tab = fund_table(M)
+    pred = np.stack([model.predict(sn_features(tab, p), torch) for p in range(len(PRESETS))], axis=1)
+    return np.argmin(pred, axis=1).astype(np.int32)
+
+
+def time_graph(M, torch, precision=SYM_PREC_FP64, opt=None, rules=None, reps=3, warm=2):
+    """Median CUDA-event time (ms) of sym_factor (graph replay)."""
+    if opt is None:
+        opt = options(DEFAULT)
+    opt.precision = precision
+    s = Solver(M.n, M.Ap, M.Ai, M.perm, opt=opt, rules=rules)
+    stream = torch.cuda.current_stream()
+    s.set_stream(stream)
+    Ax = torch.from_numpy(M.Ax).cuda()
+    for _ in range(warm):
+        s.factor(Ax)
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.factor(Ax)
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    s.close()
+    return float(np.median(ts))
+
+
+def evaluate_sn(model, mats, torch, precision=SYM_PREC_FP64, flop_budget=4e10, pattern_model=None, log=None):
+    """Measured factorization time per held-out pattern: fixed rule, best single preset, the
+    per-pattern choice (pattern_model, optional) and the per-supernode choice."""
+    rows, skipped = [], 0
+    for gi, M in enumerate(mats):
+        if _default_flops(M) > flop_budget:
+            skipped += 1
+            continue
+        t = [time_graph(M, torch, precision, opt=options(p)) for p in range(len(PRESETS))]
+        fr = choose_rules(model, M, torch)
+        t_sn = time_graph(M, torch, precision, rules=(RULES, fr))
+        row = {"name": M.name, "fixed": t[DEFAULT], "best_preset": min(t), "per_supernode": t_sn,
+               "rules_used": np.bincount(fr, minlength=len(PRESETS)).tolist()}
+        if pattern_model is not None:
+            row["per_pattern"] = t[pattern_model.choose(M, torch)]
+        rows.append(row)
+        if log:
+            log(f"{gi + 1}/{len(mats)} {M.name}: fixed {t[DEFAULT]:.3f} best {min(t):.3f} per-supernode {t_sn:.3f}")
+    gm = lambda a: float(np.exp(np.mean(np.log(a)))) if len(a) else None
+    fixed = np.array([r["fixed"] for r in rows])
+    out = {"patterns": len(rows), "skipped_over_budget": skipped,
+           "geomean_speedup_per_supernode": gm(fixed / np.array([r["per_supernode"] for r in rows])),
+           "geomean_speedup_best_preset": gm(fixed / np.array([r["best_preset"] for r in rows])),
+           "total_time_ratio_per_supernode": float(fixed.sum() / sum(r["per_supernode"] for r in rows)) if rows else None}
+    if pattern_model is not None and rows:
+        out["geomean_speedup_per_pattern"] = gm(fixed / np.array([r["per_pattern"] for r in rows]))
+    return out, rows
+
+
+WEIGHTS_SN = {"fp64": os.path.join(os.path.dirname(os.path.abspath(__file__)), "costmodel_sn_fp64.json"),
+              "fp32": os.path.join(os.path.dirname(os.path.abspath(__file__)), "costmodel_sn_fp32.json")}
+
+
+def pretrained_sn(arm="fp64"):
+    """The per-supernode network of one arm (fp64: FP64 factor; fp32: the mixed-precision FP32
+    factor), trained by `python -m paper_1705_06575_gb300.costmodel sn` (its evaluation is saved
+    beside the weights)."""
+    return CostModel.load(WEIGHTS_SN[arm])
+
+
+def suite5(count, seed, flop_budget, log=None):
+    """The first `count` patterns of the suite from `seed` on within the flop budget: a spec is
+    dropped when its estimate exceeds three budgets, a built pattern when its analyzed plan
+    exceeds one. Returns (patterns, dropped by estimate, dropped after analysis)."""
+    import workloads as w
+    out, est_skip, exact_skip, i = [], 0, 0, 0
+    while len(out) < count:
+        spec = w.suite5_spec(i, seed)
+        i += 1
+        if w.suite5_estimate_flops(spec) > 3 * flop_budget:
+            est_skip += 1
+            continue
+        M = w.suite5_build(spec)
+        if _default_flops(M) > flop_budget:
+            exact_skip += 1
+            continue
+        out.append(M)
+    if log:
+        log(f"suite from seed {seed}: {len(out)} patterns, {est_skip} over budget by estimate, {exact_skip} after analysis")
+    return out, est_skip, exact_skip
+
+
+def main_sn(argv=None):
+    """Per-supernode rules: collect per-supernode times on training patterns of the suite, train
+    one network per arm, evaluate on held-out patterns (disjoint seeds) by measured time.
+
+    python -m paper_1705_06575_gb300.costmodel sn --train N --holdout H [--arms fp64,fp32] --out DIR"""
+    import argparse
+    import sys
+
+    import torch
+
+    here = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, here)
+    from . import SYM_PREC_MIXED
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--train", type=int, default=300)
+    ap.add_argument("--holdout", type=int, default=400)
+    ap.add_argument("--holdout-fp32", type=int, default=None)
+    ap.add_argument("--arms", default="fp64,fp32")
+    ap.add_argument("--seed", type=int, default=50000)
+    ap.add_argument("--budget", type=float, default=4e10)
+    ap.add_argument("--max-rows", type=int, default=200000)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--out", default="costmodel_out")
+    args = ap.parse_args(argv)
+    os.makedirs(args.out, exist_ok=True)
+    log = lambda m: print(m, flush=True)
+    t0 = time.time()
+    train, tr_est, tr_exact = suite5(args.train, args.seed, args.budget, log)
+    hold, ho_est, ho_exact = suite5(args.holdout, args.seed + 1_000_000, args.budget, log)
+    result = {"suite": "2D 5/9-point and 3D 7/27-point grids of sides 32..128, Erdos-Renyi n 50k..200k, degree 4..16",
+              "flop_budget": args.budget,
+              "train_patterns": len(train), "train_skipped_estimate": tr_est, "train_skipped_analysis": tr_exact,
+              "holdout_patterns_requested": len(hold), "holdout_skipped_estimate": ho_est,
+              "holdout_skipped_analysis": ho_exact, "arms": {}}
+    for arm in args.arms.split(","):
+        prec = SYM_PREC_FP64 if arm == "fp64" else SYM_PREC_MIXED
+        X, Y, _ = collect_sn(train, torch, prec, flop_budget=args.budget, max_rows=args.max_rows,
+                             log=lambda m: None)
+        model, l0, l1 = CostModel.fit(X, Y, torch, steps=args.steps)
+        path = os.path.join(args.out, f"costmodel_sn_{arm}.json")
+        model.save(path)
+        nh = len(hold) if arm == "fp64" or args.holdout_fp32 is None else min(len(hold), args.holdout_fp32)
+        ev, rows = evaluate_sn(model, hold[:nh], torch, prec, flop_budget=args.budget, log=log)
+        ev.update({"rows": int(X.shape[0]), "loss_initial": l0, "loss_final": l1})
+        result["arms"][arm] = ev
+        with open(os.path.join(args.out, f"eval_sn_{arm}_rows.json"), "w") as f:
+            json.dump(rows, f)
+        log(json.dumps({arm: ev}))
+    result["seconds"] = time.time() - t0
+    with open(os.path.join(args.out, "eval_sn.json"), "w") as f:
+        json.dump(result, f, indent=1)
+    print(json.dumps(result), flush=True)
+
+
 def main(argv=None):
-    """Collect, train and evaluate: python -m paper_1705_06575_gb300.costmodel --patterns N --out DIR"""
+    """Collect, train and evaluate: python -m paper_1705_06575_gb300.costmodel --patterns N --out DIR
+    (`sn` as the first argument: the per-supernode rules, see main_sn)."""
+    import sys
+    argv = sys.argv[1:] if argv is None else argv
+    if argv and argv[0] == "sn":
+        return main_sn(argv[1:])
     import argparse
     import sys
 

@@ -27,3 +27,51 @@ def test_pretrained_choice_on_host_features():
         assert np.all(np.isfinite(y))
         assert np.all((y > np.log(0.05)) & (y < np.log(1e5)))
         assert 0 <= int(np.argmin(y)) < len(cm.PRESETS)
+
+
+def test_supernode_times_distribute_every_launch():
+    """Per-supernode targets of the learned rules: each launch's time is spread over the supernodes
+    of its tasks, so the per-supernode times add up to the launch times, and every fundamental
+    supernode gets its final supernode's time in proportion to its share of sum c_j^2."""
+    import numpy as np
+
+    import paper_1705_06575_gb300 as S
+    import workloads as w
+    from paper_1705_06575_gb300 import costmodel as cm
+    M = w.conduct3d(10, np.random.default_rng(4), "star")
+    s = S.Solver(M.n, M.Ap, M.Ai, M.perm, opt=cm.options(cm.DEFAULT), host_only=True)
+    nl = s.export("factor_launches").size // 5
+    ms = np.concatenate([[5.0], np.linspace(0.1, 1.0, nl)])
+    t = cm.supernode_times(s, ms)
+    assert t.shape == (s.info().nsuper,) and np.all(t >= 0)
+    assert abs(t.sum() - ms[1:].sum()) <= 1e-9 * ms[1:].sum()
+    tab = cm.fund_table(M)
+    tf = cm.fund_times(tab, s, ms)
+    assert tf.shape == (tab["nf"],) and abs(tf.sum() - t.sum()) <= 1e-9 * t.sum()
+    X = cm.sn_features(tab, 3)
+    assert X.shape == (tab["nf"], cm.NFEAT_SN) and np.isfinite(X).all()
+
+
+def test_per_supernode_rules_reproduce_presets_and_oracle():
+    """A rule table with every fundamental supernode on one preset gives that preset's plan; a
+    random mix of rules gives the plan the oracle builds from the same rules, bit for bit."""
+    import numpy as np
+
+    import oracle
+    import paper_1705_06575_gb300 as S
+    import workloads as w
+    from paper_1705_06575_gb300 import costmodel as cm
+    M = w.dd2d9(30, np.random.default_rng(5))
+    nf = S.Solver(M.n, M.Ap, M.Ai, M.perm, host_only=True).export("fsuper").size - 1
+    for p in range(len(cm.PRESETS)):
+        a = S.Solver(M.n, M.Ap, M.Ai, M.perm, opt=cm.options(p), host_only=True)
+        b = S.Solver(M.n, M.Ap, M.Ai, M.perm, host_only=True, rules=(cm.RULES, np.full(nf, p)))
+        assert np.array_equal(a.export("super"), b.export("super"))
+    fr = np.random.default_rng(6).integers(0, len(cm.PRESETS), nf).astype(np.int32)
+    b = S.Solver(M.n, M.Ap, M.Ai, M.perm, host_only=True, rules=(cm.RULES, fr))
+    o = oracle.Oracle(M.n, M.Ap, M.Ai, b.export("perm"), rules=cm.RULES, fund_rule=fr, want_rel=True)
+    for mine, theirs in (("super", "sn"), ("rowptr", "srp"), ("rows", "sri"), ("desc", "dk"), ("rel", "rel")):
+        assert np.array_equal(b.export(mine), getattr(o, theirs)), mine
+    import pytest
+    with pytest.raises(S.SymError):  # one rule index per fundamental supernode is required
+        S.Solver(M.n, M.Ap, M.Ai, M.perm, host_only=True, rules=(cm.RULES, fr[:-1]))

@@ -381,6 +381,56 @@ def pattern_suite(count, seed):
     return out
 
 
+# The learned-schedule suite at its stated sizes: 2D 5/9-point and 3D 7/27-point grids of sides
+# 32..128 and Erdos-Renyi graphs with n in 50,000..200,000 and average degree 4..16 (made SPD by
+# a dominance factor U(1.01, 1.5)). Pattern i has seed seed + i; disjoint seed ranges give
+# disjoint sets. Specs are cheap; a matrix is built only for a spec that is kept.
+SUITE5_KINDS = ("grid2d5", "grid2d9", "grid3d7", "grid3d27", "er")
+
+
+def suite5_spec(i, seed):
+    rng = np.random.default_rng(seed + i)
+    kind = SUITE5_KINDS[i % len(SUITE5_KINDS)]
+    if kind == "er":
+        return {"kind": kind, "n": int(rng.integers(50000, 200001)), "degree": int(rng.integers(4, 17)),
+                "seed": seed + i}
+    return {"kind": kind, "side": int(rng.integers(32, 129)), "seed": seed + i}
+
+
+def suite5_estimate_flops(spec):
+    """Factor flops (sum c_j^2) of a spec before it is built, from measured anchors of the same
+    families under their orderings: 3D 7-point 5.7e9 at side 32, 3D 27-point 2.6e10 at side 40,
+    both growing as side^6 (nested dissection); 2D grids stay below 1e9 at side 128; Erdos-Renyi at
+    n = 50,000 and degree 4 (the smallest of the suite) 4.6e11 under minimum degree, larger n and
+    degree only add fill."""
+    k = spec["kind"]
+    if k == "grid3d7":
+        return 5.7e9 * (spec["side"] / 32.0) ** 6
+    if k == "grid3d27":
+        return 2.6e10 * (spec["side"] / 40.0) ** 6
+    if k == "er":
+        return 4.6e11 * (spec["n"] / 50000.0) ** 2 * (spec["degree"] / 4.0)
+    return 1e9 * (spec["side"] / 128.0) ** 3
+
+
+def suite5_build(spec):
+    rng = np.random.default_rng(spec["seed"])
+    k = spec["kind"]
+    if k == "grid2d5":
+        M = laplace2d5(spec["side"], rng)
+    elif k == "grid2d9":
+        M = dd2d9(spec["side"], rng)
+    elif k == "grid3d7":
+        M = conduct3d(spec["side"], rng, "star")
+    elif k == "grid3d27":
+        M = conduct3d(spec["side"], rng, "box")
+    else:
+        M = erdos_renyi(spec["n"], spec["degree"], rng)
+        M.perm = rcm_perm(M)
+    M.name = f"suite5_{spec['seed']}_{M.name}"
+    return M
+
+
 def cfg(name, matrix_index=0):
     """The named workloads with their seeds (1000 * config index + matrix index)."""
     if name == "laplace2d5_64":
