@@ -343,11 +343,21 @@ def _default_flops(M):
     return f
 
 
-def choose_rules(model, M, torch):
-    """Per fundamental supernode, the preset rule with the smallest predicted time."""
+MARGIN = 0.25  # a supernode leaves the pattern's rule only for a predicted gain above this
+
+
+def choose_rules(model, M, torch, margin=MARGIN):
+    """Rule per fundamental supernode, in two steps from the per-supernode predictions t(F, p):
+    the preset p* with the smallest predicted total sum_F t(F, p) for the whole pattern, then,
+    for each F, the preset with the smallest t(F, p) where that beats t(F, p*) by more than the
+    margin (the predictions are additive only approximately; small predicted gains stay with
+    p*). Returns (rules per F, p*)."""
     tab = fund_table(M)
-    pred = np.stack([model.predict(sn_features(tab, p), torch) for p in range(len(PRESETS))], axis=1)
-    return np.argmin(pred, axis=1).astype(np.int32)
+    pred = np.exp(np.stack([model.predict(sn_features(tab, p), torch) for p in range(len(PRESETS))], axis=1))
+    pstar = int(np.argmin(pred.sum(axis=0)))
+    best = np.argmin(pred, axis=1)
+    gain = pred[np.arange(pred.shape[0]), best] < (1.0 - margin) * pred[:, pstar]
+    return np.where(gain, best, pstar).astype(np.int32), pstar
 
 
 def time_graph(M, torch, precision=SYM_PREC_FP64, opt=None, rules=None, reps=3, warm=2):
@@ -382,9 +392,10 @@ def evaluate_sn(model, mats, torch, precision=SYM_PREC_FP64, flop_budget=4e10, p
             skipped += 1
             continue
         t = [time_graph(M, torch, precision, opt=options(p)) for p in range(len(PRESETS))]
-        fr = choose_rules(model, M, torch)
-        t_sn = time_graph(M, torch, precision, rules=(RULES, fr))
+        fr, pstar = choose_rules(model, M, torch)
+        t_sn = time_graph(M, torch, precision, rules=(RULES, fr)) if np.any(fr != pstar) else t[pstar]
         row = {"name": M.name, "fixed": t[DEFAULT], "best_preset": min(t), "per_supernode": t_sn,
+               "pattern_rule_from_sn": t[pstar], "pstar": pstar,
                "rules_used": np.bincount(fr, minlength=len(PRESETS)).tolist()}
         if pattern_model is not None:
             row["per_pattern"] = t[pattern_model.choose(M, torch)]
@@ -396,6 +407,9 @@ def evaluate_sn(model, mats, torch, precision=SYM_PREC_FP64, flop_budget=4e10, p
     out = {"patterns": len(rows), "skipped_over_budget": skipped,
            "geomean_speedup_per_supernode": gm(fixed / np.array([r["per_supernode"] for r in rows])),
            "geomean_speedup_best_preset": gm(fixed / np.array([r["best_preset"] for r in rows])),
+           "geomean_speedup_pattern_rule_from_sn": gm(fixed / np.array([r["pattern_rule_from_sn"] for r in rows])),
+           "supernodes_off_pattern_rule": float(np.mean([1.0 - r["rules_used"][r["pstar"]] / max(1, sum(r["rules_used"]))
+                                                         for r in rows])) if rows else None,
            "total_time_ratio_per_supernode": float(fixed.sum() / sum(r["per_supernode"] for r in rows)) if rows else None}
     if pattern_model is not None and rows:
         out["geomean_speedup_per_pattern"] = gm(fixed / np.array([r["per_pattern"] for r in rows]))
