@@ -1217,6 +1217,143 @@ __global__ void __launch_bounds__(TileCfg<TB>::threads) k_bstep(const SNode *__r
   }
 }
 
+// Cluster forms of the solve steps (tiles of up to NB columns). A task {J, i, s} runs on a
+// thread-block cluster of four CTAs; CTA q of the cluster owns the 16 rows (forward) or columns
+// (backward) 16 q .. 16 q + 15 of tile i. Forward, launch s (s = -1 .. ncb - 2):
+//   every task applies the solved tile s (if s >= 0) to its rows: y_i -= L_is y_s;
+//   the task i = s + 1 then solves its tile in place, y_i <- L_ii^{-1} y_i, each CTA taking its
+//   16 rows of the inverse and the whole updated tile, gathered from the four CTAs through
+//   distributed shared memory.
+// Backward, launch s (s = ncb .. 1): z_i -= L_si^T z_s (s < ncb), and the task i = s - 1 solves
+// z_i <- L_ii^{-T} z_i. So the tile a step solves is written once, already solved, and read by
+// the next launch only: no CTA applies the inverse of another tile, and the critical path of a
+// step is one quarter tile's update plus one quarter of its solve.
+constexpr int QR = 16;  // rows (or columns) per CTA of a cluster task
+
+template <typename V, int NR>
+struct StepCSmem {
+  V L[NB][QR + 1];     // [k][row]: this CTA's rows of L_is (forward) or L_si^T (backward)
+  V I[NB][QR + 1];     // [k][row]: this CTA's rows of L_ii^{-1} (forward) or of L_ii^{-T}
+  V ys[NR][NB];        // the solved tile s
+  V yq[NR][QR];        // this CTA's rows of tile i after the update (read by the cluster)
+  V yf[NR][NB];        // the whole updated tile i (solving tasks)
+};
+
+// 16-lane sum (lanes l and l ^ 8, ^4, ^2, ^1 are partners; lane g of each 16 holds part g).
+template <typename V>
+__device__ __forceinline__ V sum16(V v) {
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T, typename V, int NR, bool FWD>
+__global__ void __launch_bounds__(THREADS) k_step_c(const SNode *__restrict__ sn, const Int4 *__restrict__ tasks,
+                                                    const T *__restrict__ Lx, const T *__restrict__ Linv,
+                                                    V *__restrict__ y, int64_t n, int r0, int64_t toff,
+                                                    const Batch bt) {
+  Lx += blockIdx.y * bt.lx;
+  Linv += blockIdx.y * bt.dinv;
+  y += blockIdx.y * bt.y;
+  __shared__ StepCSmem<V, NR> S;
+  cg::cluster_group cluster = cg::this_cluster();
+  pdl_trigger_early<V>();
+  const int q = (int)cluster.block_rank();
+  const Int4 t = tasks[toff + blockIdx.x / 4];
+  const SNode sj = sn[t.a];
+  const int i = t.b, s = t.c;
+  const int ti = min(NB, sj.ncols - i * NB);
+  const bool has_s = FWD ? s >= 0 : s < sj.ncb;
+  const int ts = has_s ? min(NB, sj.ncols - s * NB) : 0;
+  const bool solves = FWD ? i == s + 1 : i == s - 1;
+  const int o0 = QR * q, rq = max(0, min(QR, ti - o0));  // this CTA's rows (columns) of tile i
+  const int tid = threadIdx.x, o = tid >> 4, g = tid & 15;  // output o, k-group g (k = g + 16 j)
+  const int64_t gi = sj.first + (int64_t)i * NB, gs = sj.first + (int64_t)s * NB;
+  // Stage what does not depend on the previous launch: the rows of L and of the inverse.
+  if (has_s) {
+    for (int idx = tid; idx < QR * ts; idx += THREADS) {
+      int r, k;
+      const T *src;
+      if (FWD) {  // L_is(o0 + r, k): for fixed k, 16 consecutive rows of column s NB + k
+        r = idx % QR, k = idx / QR;
+        src = Lx + sj.lx + (int64_t)(s * NB + k) * sj.nrows + i * NB + o0 + r;
+      } else {    // L_si(k, o0 + r): for fixed r, consecutive k of column i NB + o0 + r
+        k = idx % ts, r = idx / ts;
+        src = Lx + sj.lx + (int64_t)(i * NB + o0 + r) * sj.nrows + s * NB + k;
+      }
+      S.L[k][r] = r < rq ? (V)*src : V(0);
+    }
+  }
+  if (solves) {
+    const T *Li = Linv + sj.dx + (int64_t)i * NB * NB;  // ti x ti, column-major, lower
+    for (int idx = tid; idx < QR * ti; idx += THREADS) {
+      int r, k;
+      V v;
+      if (FWD) {  // (L^-1)(o0 + r, k)
+        r = idx % QR, k = idx / QR;
+        v = r < rq ? (V)Li[(int64_t)k * ti + o0 + r] : V(0);
+      } else {    // (L^-T)(o0 + r, k) = (L^-1)(k, o0 + r)
+        k = idx % ti, r = idx / ti;
+        v = r < rq ? (V)Li[(int64_t)(o0 + r) * ti + k] : V(0);
+      }
+      S.I[k][r] = v;
+    }
+  }
+  pdl_wait_then_trigger<V>();  // y is the predecessor's output
+  for (int idx = tid; idx < NR * NB; idx += THREADS) {
+    const int k = idx % NB, c = idx / NB;
+    if (has_s && k < ts) S.ys[c][k] = y[(int64_t)(r0 + c) * n + gs + k];
+  }
+  __syncthreads();
+  // y_i(o) -= sum_k L(o, k) ys(k) for this CTA's outputs o: 16 lanes per output split k.
+  V acc[NR];
+#pragma unroll
+  for (int c = 0; c < NR; ++c) acc[c] = V(0);
+  if (o < QR) {
+    for (int k = g; k < ts; k += 16) {
+      const V l = S.L[k][o];
+#pragma unroll
+      for (int c = 0; c < NR; ++c) acc[c] = fma(l, S.ys[c][k], acc[c]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < NR; ++c) acc[c] = sum16(acc[c]);
+  if (g == 0 && o < rq) {
+#pragma unroll
+    for (int c = 0; c < NR; ++c) {
+      const int64_t at = (int64_t)(r0 + c) * n + gi + o0 + o;
+      const V v = y[at] - acc[c];
+      if (solves) S.yq[c][o] = v;
+      else y[at] = v;
+    }
+  }
+  if (!solves) return;  // (uniform across the cluster: its four CTAs share the task)
+  cluster.sync();       // every quarter of the updated tile is in its CTA's shared memory
+  for (int idx = tid; idx < NR * ti; idx += THREADS) {
+    const int k = idx % ti, c = idx / ti;
+    const V *rem = cluster.map_shared_rank(&S.yq[0][0], k / QR);
+    S.yf[c][k] = rem[c * QR + k % QR];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int c = 0; c < NR; ++c) acc[c] = V(0);
+  if (o < QR) {
+    const int lo = FWD ? 0 : o0 + o, hi = FWD ? o0 + o + 1 : ti;  // the inverse's nonzeros
+    for (int k = lo + ((g - lo) & 15); k < hi; k += 16) {
+      const V l = S.I[k][o];
+#pragma unroll
+      for (int c = 0; c < NR; ++c) acc[c] = fma(l, S.yf[c][k], acc[c]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < NR; ++c) acc[c] = sum16(acc[c]);
+  if (g == 0 && o < rq) {
+#pragma unroll
+    for (int c = 0; c < NR; ++c) y[(int64_t)(r0 + c) * n + gi + o0 + o] = acc[c];
+  }
+  cluster.sync();  // keep this CTA's quarter alive until the others have read it
+}
+
 // Inverse of diagonal tile s of J (in FP64 from the factored tile), stored column-major ts x ts
 // at Linv + dx + s NB^2. Solves L X = I row by row of X: row c is final once scaled by
 // 1 / L(c, c); it is then eliminated from the rows below.
@@ -1436,6 +1573,27 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, int threads, size_t 
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
+// Launch of a cluster-form solve step: clusters of four CTAs along x, programmatic dependent
+// launch (see pdl_wait).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_step_c(void (*kernel)(KArgs...), dim3 grid, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[2];
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(THREADS, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 4;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 2;
   return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
@@ -1680,6 +1838,11 @@ cudaError_t run_sweeps(const DevPlan &d, const std::vector<Launch> &fwd, const s
           break;
         }
         case S_FSTEP:
+          if (L.cluster == 4) {
+            SYM_NR_DISPATCH(nr, (e = launch_step_c(k_step_c<T, V, NR, true>, dim3(4 * g, nb), st, d.sn, d.tasks, Lx,
+                                                   Linv, y, n, r0, L.off, bt)));
+            break;
+          }
           e = L.tb == SMALL_TB
                   ? launch_pdl(k_fstep<T, V, SMALL_TB>, dim3(g, nb), TileCfg<SMALL_TB>::threads,
                                step_smem<V, SMALL_TB>(), st, d.sn, d.tasks, Lx, Linv, y, n, r0, nr, L.off, bt)
@@ -1709,6 +1872,11 @@ cudaError_t run_sweeps(const DevPlan &d, const std::vector<Launch> &fwd, const s
                                               Lx, y, n, r0, L.off, bt)));
           break;
         case S_BSTEP:
+          if (L.cluster == 4) {
+            SYM_NR_DISPATCH(nr, (e = launch_step_c(k_step_c<T, V, NR, false>, dim3(4 * g, nb), st, d.sn, d.tasks, Lx,
+                                                   Linv, y, n, r0, L.off, bt)));
+            break;
+          }
           e = L.tb == SMALL_TB
                   ? launch_pdl(k_bstep<T, V, SMALL_TB>, dim3(g, nb), TileCfg<SMALL_TB>::threads,
                                step_smem<V, SMALL_TB>(), st, d.sn, d.tasks, Lx, Linv, y, n, r0, nr, L.off, bt)

@@ -91,13 +91,18 @@ enum Kind : int32_t {
   K_TRTRI = 5,    // inverse of every diagonal tile, for the solve (int4 {J, s, s, s})
   S_FGATHER = 11, // y_J(tile bj) -= sum_K L_K(rows in tile) y_K (int4 {J, bj, task, 0})
   S_FSTEP = 12,   // column tile s of J: y_i -= L_is L_ss^-1 y_s (CTAs i > s); CTA i = s writes
-                  // the solved tiles s-1 (and s if last) (int4 {J, i, s, s})
+                  // the solved tiles s-1 (and s if last) (int4 {J, i, s, s}). A launch with
+                  // cluster = 4 holds cluster tasks instead (int4 {J, i, s, 0}, s = -1 .. ncb-2):
+                  // y_i -= L_is y_s with y_s already solved (s >= 0), and for i = s + 1 the
+                  // solve y_i <- L_ii^-1 y_i in place
   S_FPUSH = 13,   // t_J(rows of row tile i, chunk ch) = L_J(tile rows, chunk cols) y_J(chunk cols)
                   // for the row tiles below J's diagonal block (int4 {J, i, ch, 0})
   S_BGATHER = 14, // z_J(slice) -= L_J(off rows, slice)^T z(off rows) (int4 {J, slice, 0, 0}),
                   // slices of SOLVE_BG columns
   S_BSTEP = 15,   // column tile s of J: z_i -= L_si^T L_ss^-T z_s (CTAs i < s); CTA i = s writes
-                  // the solved tiles s+1 (and 0 if s = 0) (int4 {J, i, s, s})
+                  // the solved tiles s+1 (and 0 if s = 0) (int4 {J, i, s, s}). With cluster = 4:
+                  // cluster tasks {J, i, s, 0}, s = ncb .. 1: z_i -= L_si^T z_s with z_s solved
+                  // (s < ncb), and for i = s - 1 the solve z_i <- L_ii^-T z_i in place
   S_FSUM = 16,    // y_g -= sum of t over the contribution list of column g, for the columns
                   // of J in block cb of 256 (int4 {J, cb, 0, 0})
   S_PERM = 17,    // y = P b and x = P^T y

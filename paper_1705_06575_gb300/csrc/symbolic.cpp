@@ -754,21 +754,38 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
         for (int32_t cb = 0; cb * 256 < sj.ncols; ++cb) P.tasks.push_back({J, cb, 0, 0});
     }
     if ((int64_t)P.tasks.size() > off) P.fwd_launches.push_back({S_FSUM, l, off, (int64_t)P.tasks.size() - off});
-    for (int32_t s = 0; s < maxcb; ++s)
-      for (int part = 0; part < 2; ++part) {  // supernodes of > SMALL_TILE columns, then the others
-        off = (int64_t)P.tasks.size();
-        for (int32_t t = P.levelptr[l]; t < P.levelptr[l + 1]; ++t) {
-          const int32_t J = P.levellist[t];
-          if ((P.snodes[J].ncols <= SMALL_TILE) != (part == 1)) continue;
-          const int32_t ncb = P.snodes[J].ncb;
-          for (int32_t i = s; i < ncb; ++i) P.tasks.push_back({J, i, s, s});
-        }
-        if ((int64_t)P.tasks.size() > off) {
-          Launch L{S_FSTEP, l, off, (int64_t)P.tasks.size() - off};
-          L.tb = part == 1 ? SMALL_TILE : 0;
-          P.fwd_launches.push_back(L);
-        }
+    // Supernodes of more than SMALL_TILE columns: cluster steps s = -1 .. ncb - 2, tasks {J, i, s}
+    // (cluster = 4): i = s + 1 applies the solved tile s and solves tile i, i > s + 1 applies it.
+    for (int32_t s = -1; s + 1 < maxcb; ++s) {
+      off = (int64_t)P.tasks.size();
+      for (int32_t t = P.levelptr[l]; t < P.levelptr[l + 1]; ++t) {
+        const int32_t J = P.levellist[t];
+        if (P.snodes[J].ncols <= SMALL_TILE) continue;
+        const int32_t ncb = P.snodes[J].ncb;
+        if (s + 1 >= ncb) continue;
+        for (int32_t i = s + 1; i < (s >= 0 ? ncb : 1); ++i) P.tasks.push_back({J, i, s, 0});
       }
+      if ((int64_t)P.tasks.size() > off) {
+        Launch L{S_FSTEP, l, off, (int64_t)P.tasks.size() - off};
+        L.cluster = 4;
+        P.fwd_launches.push_back(L);
+      }
+    }
+    // The others (one tile each): the one-CTA form, tasks {J, i, s, s}.
+    for (int32_t s = 0; s < maxcb; ++s) {
+      off = (int64_t)P.tasks.size();
+      for (int32_t t = P.levelptr[l]; t < P.levelptr[l + 1]; ++t) {
+        const int32_t J = P.levellist[t];
+        if (P.snodes[J].ncols > SMALL_TILE) continue;
+        const int32_t ncb = P.snodes[J].ncb;
+        for (int32_t i = s; i < ncb; ++i) P.tasks.push_back({J, i, s, s});
+      }
+      if ((int64_t)P.tasks.size() > off) {
+        Launch L{S_FSTEP, l, off, (int64_t)P.tasks.size() - off};
+        L.tb = SMALL_TILE;
+        P.fwd_launches.push_back(L);
+      }
+    }
     off = (int64_t)P.tasks.size();
     for (int32_t t = P.levelptr[l]; t < P.levelptr[l + 1]; ++t) {
       const int32_t J = P.levellist[t];
@@ -790,22 +807,39 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
         for (int32_t sl = 0; sl * SOLVE_BG < sj.ncols; ++sl) P.tasks.push_back({J, sl, 0, 0});
     }
     if ((int64_t)P.tasks.size() > off) P.bwd_launches.push_back({S_BGATHER, l, off, (int64_t)P.tasks.size() - off});
-    for (int32_t s = maxcb - 1; s >= 0; --s)
-      for (int part = 0; part < 2; ++part) {  // supernodes of > SMALL_TILE columns, then the others
-        off = (int64_t)P.tasks.size();
-        for (int32_t t = P.levelptr[l]; t < P.levelptr[l + 1]; ++t) {
-          const int32_t J = P.levellist[t];
-          if ((P.snodes[J].ncols <= SMALL_TILE) != (part == 1)) continue;
-          const int32_t ncb = P.snodes[J].ncb;
-          if (s >= ncb) continue;
-          for (int32_t i = s; i >= 0; --i) P.tasks.push_back({J, i, s, s});
-        }
-        if ((int64_t)P.tasks.size() > off) {
-          Launch L{S_BSTEP, l, off, (int64_t)P.tasks.size() - off};
-          L.tb = part == 1 ? SMALL_TILE : 0;
-          P.bwd_launches.push_back(L);
-        }
+    // Supernodes of more than SMALL_TILE columns: cluster steps s = ncb .. 1, tasks {J, i, s}
+    // (cluster = 4): i = s - 1 applies the solved tile s (s < ncb) and solves tile i, i < s - 1
+    // applies it.
+    for (int32_t s = maxcb; s >= 1; --s) {
+      off = (int64_t)P.tasks.size();
+      for (int32_t t = P.levelptr[l]; t < P.levelptr[l + 1]; ++t) {
+        const int32_t J = P.levellist[t];
+        if (P.snodes[J].ncols <= SMALL_TILE) continue;
+        const int32_t ncb = P.snodes[J].ncb;
+        if (s > ncb) continue;
+        for (int32_t i = s - 1; i >= (s < ncb ? 0 : s - 1); --i) P.tasks.push_back({J, i, s, 0});
       }
+      if ((int64_t)P.tasks.size() > off) {
+        Launch L{S_BSTEP, l, off, (int64_t)P.tasks.size() - off};
+        L.cluster = 4;
+        P.bwd_launches.push_back(L);
+      }
+    }
+    for (int32_t s = maxcb - 1; s >= 0; --s) {
+      off = (int64_t)P.tasks.size();
+      for (int32_t t = P.levelptr[l]; t < P.levelptr[l + 1]; ++t) {
+        const int32_t J = P.levellist[t];
+        if (P.snodes[J].ncols > SMALL_TILE) continue;
+        const int32_t ncb = P.snodes[J].ncb;
+        if (s >= ncb) continue;
+        for (int32_t i = s; i >= 0; --i) P.tasks.push_back({J, i, s, s});
+      }
+      if ((int64_t)P.tasks.size() > off) {
+        Launch L{S_BSTEP, l, off, (int64_t)P.tasks.size() - off};
+        L.tb = SMALL_TILE;
+        P.bwd_launches.push_back(L);
+      }
+    }
   }
   // 12. Algorithmic flops of each kernel kind (see Plan::kind_flops).
   {
@@ -864,9 +898,16 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
           const Int4 &q = P.tasks[t];
           const SNode &s = P.snodes[q.a];
           // diagonal tile: ts^2 (solve with L_ss); off-diagonal tile: 2 tm ts
-          if (L.kind == S_FSTEP || L.kind == S_BSTEP)
+          if ((L.kind == S_FSTEP || L.kind == S_BSTEP) && L.cluster == 4) {
+            const bool fwd = L.kind == S_FSTEP;
+            const bool has_s = fwd ? q.c >= 0 : q.c < s.ncb;
+            const double ti = cols_of_tile(s, q.b);
+            P.kind_flops[L.kind] += (has_s ? 2.0 * ti * cols_of_tile(s, q.c) : 0.0) +
+                                    (q.b == (fwd ? q.c + 1 : q.c - 1) ? ti * ti : 0.0);
+          } else if (L.kind == S_FSTEP || L.kind == S_BSTEP) {
             P.kind_flops[L.kind] += q.b == q.c ? sq(cols_of_tile(s, q.c))
                                                 : 2.0 * cols_of_tile(s, q.b) * cols_of_tile(s, q.c);
+          }
           if (L.kind == S_BGATHER)
             P.kind_flops[L.kind] += 2.0 * (s.nrows - s.ncols) * std::min<int32_t>(SOLVE_BG, s.ncols - q.b * SOLVE_BG);
           if (L.kind == S_FPUSH)

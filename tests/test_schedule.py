@@ -44,6 +44,8 @@ class Sched:
             self.launches[k] = np.stack([raw[:, 0] & 0xffffffff, raw[:, 1], raw[:, 2], raw[:, 3] >> 32,
                                          (raw[:, 4] & 0xffffffff).astype(np.uint32).astype(np.int32)], 1)
             self.tb[k] = raw[:, 4] >> 32  # 32: small-tile kernel variant
+            self.cluster = getattr(self, "cluster", {})
+            self.cluster[k] = raw[:, 3] & 0xffffffff  # 4 on the solve: cluster-form step tasks
 
     def J(self, j):
         f, l = int(self.sup[j]), int(self.sup[j + 1])
@@ -225,8 +227,9 @@ def emulate_solve(sc, store, y):
         return store[("I", j, s, a, b)]
 
     for name in ("fwd_launches", "bwd_launches"):
-        for kind, off, count, _, _ in sc.launches[name]:
+        for li, (kind, off, count, _, _) in enumerate(sc.launches[name]):
             kind = int(kind)
+            cluster_form = int(sc.cluster[name][li]) == 4
             L = Launch()
             for t in range(int(off), int(off + count)):
                 j, ti, tc, _ = (int(v) for v in sc.tasks[t])
@@ -276,6 +279,31 @@ def emulate_solve(sc, store, y):
                             L.read(t, int(R[r]))
                         L.read(t, f + c)
                         L.write(t, f + c, y[f + c] - v)
+                elif kind in (S_FSTEP, S_BSTEP) and cluster_form:
+                    # cluster task {J, i, s}: apply the solved tile s (if any) to tile i; the task
+                    # next to s (i = s + 1 forward, s - 1 backward) then solves tile i in place
+                    i, s = ti, tc
+                    fwd = kind == S_FSTEP
+                    has_s = s >= 0 if fwd else s < ncb
+                    gi = [f + i * NB + a for a in range(tsz(i))]
+                    v = np.array([y[k] for k in gi])
+                    for k in gi:
+                        L.read(t, k)
+                    if has_s:
+                        gs = [f + s * NB + b for b in range(tsz(s))]
+                        zs = np.array([y[k] for k in gs])
+                        for k in gs:
+                            L.read(t, k)
+                        for a in range(tsz(i)):
+                            if fwd:
+                                v[a] -= sum(Lv(j, i * NB + a, s * NB + b) * zs[b] for b in range(tsz(s)))
+                            else:
+                                v[a] -= sum(Lv(j, s * NB + b, i * NB + a) * zs[b] for b in range(tsz(s)))
+                    if i == (s + 1 if fwd else s - 1):
+                        Inv = np.array([[Iv(j, i, a, b) for b in range(tsz(i))] for a in range(tsz(i))])
+                        v = Inv @ v if fwd else Inv.T @ v
+                    for k, val in zip(gi, v):
+                        L.write(t, k, val)
                 elif kind in (S_FSTEP, S_BSTEP):
                     i, s = ti, tc
                     fwd = kind == S_FSTEP
