@@ -1423,6 +1423,61 @@ __device__ __forceinline__ void tri_decode(int el, int &a, int &b) {
   b = el - a * (a + 1) / 2;
 }
 
+// External update of small tiles in a batch: one warp per (tile, matrix), the same tile of
+// WT_WARPS consecutive matrices per CTA, each warp's tile in its own shared memory. A batch's small
+// supernodes give entries of a few dozen elements; in the one-CTA-per-tile form most of the
+// CTA's warps sit idle behind its barriers. Here a warp's lanes take an entry's elements (lower
+// triangle only on diagonal tiles) and run their sums over ncols(K) with operands read through
+// L1; no barrier wider than the warp. Deterministic: entries in order, k ascending.
+template <typename T>
+__global__ void __launch_bounds__(32 * WT_WARPS) k_update_wb(const SNode *__restrict__ sn,
+                                                             const UpdTask *__restrict__ tasks,
+                                                             const UpdEntry *__restrict__ ents,
+                                                             const int32_t *__restrict__ rel, T *__restrict__ Lx,
+                                                             int64_t toff, int32_t nmat, const Batch bt) {
+  __shared__ T acc[WT_WARPS][SMALL_TILE][SMALL_TILE + 1];  // [col][row] per warp
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int32_t mat = blockIdx.y * WT_WARPS + w;
+  if (mat >= nmat) return;  // warp-uniform; only warp-level synchronization below
+  Lx += (int64_t)mat * bt.lx;
+  const UpdTask t = tasks[toff + blockIdx.x];
+  const SNode sj = sn[t.J];
+  const int64_t rb = d_row_tile_base(t.bi, sj.ncols, sj.ncb);
+  const int tm = d_row_tile_rows(t.bi, sj.ncols, sj.nrows, sj.ncb);
+  const int cb = t.bj * NB;
+  const int tn = min(NB, sj.ncols - cb);
+  const bool diag = t.bi == t.bj;
+  T(*A)[SMALL_TILE + 1] = acc[w];
+  T *C = Lx + sj.lx + (int64_t)cb * sj.nrows + rb;
+  for (int idx = lane; idx < tm * tn; idx += 32) {
+    const int r = idx % tm, c = idx / tm;
+    A[c][r] = C[(int64_t)c * sj.nrows + r];
+  }
+  __syncwarp();
+  for (int64_t e = t.e0; e < t.e1; ++e) {
+    const UpdEntry E = ents[e];
+    const SNode sk = sn[E.K];
+    const int64_t ld = sk.nrows;
+    const int cnt = diag ? E.m * (E.m + 1) / 2 : E.m * E.n;
+    for (int el = lane; el < cnt; el += 32) {
+      int a, b;
+      if (diag) tri_decode(el, a, b);
+      else a = el % E.m, b = el / E.m;
+      const int pr = rel[E.relr + a] - (int)rb, pc = rel[E.relc + b] - cb;
+      const T *pa = Lx + sk.lx + E.r_lo + a, *pb = Lx + sk.lx + E.c_lo + b;
+      T r = A[pc][pr];
+#pragma unroll 4
+      for (int k = 0; k < sk.ncols; ++k) r = fma(-pa[k * ld], pb[k * ld], r);
+      A[pc][pr] = r;
+    }
+    __syncwarp();
+  }
+  for (int idx = lane; idx < tm * tn; idx += 32) {
+    const int r = idx % tm, c = idx / tm;
+    C[(int64_t)c * sj.nrows + r] = A[c][r];
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(32 * WT_WARPS) k_potrf_w(const SNode *__restrict__ sn, const Int4 *__restrict__ tasks,
                                                            int64_t ntask, T *__restrict__ Lx, long long *status,
@@ -1745,6 +1800,9 @@ cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, co
             e = launch_prio(k_update_f32, dim3(g, nb), F32_THREADS, 0, s, prio, d.sn, d.upd_tasks, d.upd_entries,
                             d.rel, Lx, L.off, bt);
         }
+        else if (small && nb > 1)  // a batch: one warp per (tile, matrix)
+          e = launch_prio(k_update_wb<T>, dim3(g, (nb + WT_WARPS - 1) / WT_WARPS), 32 * WT_WARPS, 0, s, prio,
+                          d.sn, d.upd_tasks, d.upd_entries, d.rel, Lx, L.off, (int32_t)nb, bt);
         else if (small)
           e = launch_prio(k_update_flat<T, SMALL_TB, false>, dim3(g, nb), TS, 0, s, prio, d.sn, d.upd_tasks,
                           d.upd_entries, d.rel, Lx, L.off, bt);
