@@ -196,6 +196,18 @@ int sym_batch_error_columns(sym_handle h, int64_t *cols);
 int sym_solve_batch(sym_handle h, int32_t nbatch, int32_t nrhs, const double *B, int64_t ldb,
                     int64_t bstride, double *X, int64_t ldx, int64_t xstride);
 
+/* Batch autotuner (this library's addition; the paper picks its variants by hand, Sec. 2.4):
+ * for a batch of nbatch matrices (arguments as sym_factor_batch), every factor launch that has
+ * two kernel forms (small-tile updates, POTRF and TRTRI: one warp per (tile, matrix), four
+ * matrices per CTA, or one CTA per tile and matrix) is timed in both with CUDA events over reps
+ * kernel-by-kernel factorizations of the given values, and the faster form is stored in the
+ * plan for every later factorization of the handle (the captured graphs are rebuilt). The
+ * per-kernel profile totals are left as they were. *tuned: launches with two forms; *changed:
+ * launches now on their second form (either pointer may be NULL). Errors as sym_factor_batch,
+ * and SYM_ERR_INVALID for reps outside 1..100; the factor afterwards is that of the last run. */
+int sym_autotune(sym_handle h, int32_t nbatch, const double *Ax, int64_t stride, int32_t reps, int32_t *tuned,
+                 int32_t *changed);
+
 /* Wait for the handle's stream and return the status of the last factorization. */
 int sym_status(sym_handle h);
 

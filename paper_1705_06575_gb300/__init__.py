@@ -22,7 +22,7 @@ __all__ = [
     "sym_last_error_column", "sym_get_factor_host", "sym_export", "sym_free", "load", "Solver",
     "EXPORTS", "sym_profile", "sym_profile_read", "sym_profile_launches", "sym_fma_peak", "sym_tc_probe", "sym_solve_host_ptr", "KINDS",
     "sym_solve_multi_noalloc", "sym_set_refinement", "sym_refinement_info", "sym_pivot_info",
-    "sym_set_pivot_threshold", "sym_set_tc_wait", "sym_analyze_rules", "sym_factor_batch",
+    "sym_set_pivot_threshold", "sym_set_tc_wait", "sym_analyze_rules", "sym_autotune", "sym_factor_batch",
     "sym_batch_error_columns", "sym_solve_batch", "sym_get_batch_factor_host", "Reach", "MLP",
 ]
 
@@ -150,6 +150,7 @@ def load():
             "sym_set_pivot_threshold": ([P, ct.c_double], I),
             "sym_set_tc_wait": ([P, ct.c_uint64, i32], I),
             "sym_analyze_rules": ([i64, P, P, P, ct.POINTER(sym_options), i32, P, i64, P, ct.POINTER(P)], I),
+            "sym_autotune": ([P, i32, P, i64, i32, ct.POINTER(i32), ct.POINTER(i32)], I),
         }
         for name, (args, res) in sigs.items():
             f = getattr(lib, name)
@@ -340,6 +341,15 @@ def sym_pivot_info(h, index=0):
 
 def sym_set_pivot_threshold(h, threshold):
     return _check(load().sym_set_pivot_threshold(h, float(threshold)))
+
+
+def sym_autotune(h, nbatch, Ax, stride, reps=3):
+    """Time both kernel forms of a batch's tunable launches and keep the faster; returns
+    (tunable launches, launches switched to their second form)."""
+    tuned, changed = ct.c_int32(), ct.c_int32()
+    _check(load().sym_autotune(h, int(nbatch), _dptr(Ax), int(stride), int(reps), ct.byref(tuned),
+                               ct.byref(changed)))
+    return tuned.value, changed.value
 
 
 def sym_set_tc_wait(h, limit_ns, withhold_mma=0):

@@ -585,6 +585,7 @@ static int analyze_impl(int64_t n, const int64_t *Ap, const int32_t *Ai, const i
     h->dp.storage = P.storage();
     h->dp.tensor_cores = (opt.flags & SYM_FLAG_NO_TENSOR_CORES) == 0;
     h->dp.piv = h->d_piv;
+    h->dp.variant = h->plan.variant.data();
     h->dp.axc = h->d_Axc;
     h->dp.dpos = (const int64_t *)h->d_dpos;
   }
@@ -1040,6 +1041,52 @@ int sym_pivot_info(sym_handle h, int32_t index, double *min_ratio, int64_t *colu
   if (column) *column = any ? h->plan.perm[pi.column] : -1;
   if (breakdown) *breakdown = any && pi.min_ratio < h->pivot_threshold ? 1 : 0;
   return SYM_OK;
+}
+
+int sym_autotune(sym_handle h, int32_t nbatch, const double *Ax, int64_t stride, int32_t reps, int32_t *tuned,
+                 int32_t *changed) {
+  int rc = check_device(h);
+  if (rc) return rc;
+  if (reps < 1 || reps > 100) return fail(SYM_ERR_INVALID, "reps outside 1..100");
+  auto &P = h->plan;
+  const size_t nl = P.factor_launches.size();
+  std::vector<char> tunable(nl, 0);
+  int32_t ntun = 0;
+  for (size_t li = 0; li < nl; ++li) ntun += tunable[li] = sym::factor_launch_has_alternative(P.factor_launches[li], nbatch);
+  if (tuned) *tuned = ntun;
+  if (changed) *changed = 0;
+  if (ntun == 0) return SYM_OK;
+  // time every launch in both forms (kernel by kernel, CUDA events), keeping the user's profile
+  const bool prof0 = h->profiling;
+  double ms0[sym::NUM_KINDS], fl0[sym::NUM_KINDS];
+  int64_t nl0[sym::NUM_KINDS];
+  std::memcpy(ms0, h->prof_ms, sizeof ms0);
+  std::memcpy(fl0, h->prof_flops, sizeof fl0);
+  std::memcpy(nl0, h->prof_launches, sizeof nl0);
+  std::vector<double> t[2] = {std::vector<double>(nl, 0.0), std::vector<double>(nl, 0.0)};
+  for (int v = 0; v < 2 && !rc; ++v) {
+    for (size_t li = 0; li < nl; ++li) P.variant[li] = tunable[li] ? (int8_t)v : 0;
+    drop_graphs(h);
+    h->profiling = true;
+    for (int32_t r = 0; r < reps && !rc; ++r) {
+      rc = factor_impl(h, nbatch, Ax, stride);
+      if (!rc) rc = finish_status(h);
+      if (!rc && h->last_launch_ms[0].size() == nl + 1)
+        for (size_t li = 0; li < nl; ++li) t[v][li] += h->last_launch_ms[0][li + 1];
+    }
+  }
+  int32_t nchg = 0;
+  for (size_t li = 0; li < nl; ++li) {
+    P.variant[li] = tunable[li] && !rc && t[1][li] < t[0][li] ? 1 : 0;
+    nchg += P.variant[li];
+  }
+  h->profiling = prof0;
+  std::memcpy(h->prof_ms, ms0, sizeof ms0);
+  std::memcpy(h->prof_flops, fl0, sizeof fl0);
+  std::memcpy(h->prof_launches, nl0, sizeof nl0);
+  drop_graphs(h);
+  if (changed) *changed = nchg;
+  return rc;
 }
 
 int sym_set_tc_wait(sym_handle h, uint64_t limit_ns, int32_t withhold_mma) {

@@ -1763,6 +1763,10 @@ cudaError_t prepare_solve() {
   return cudaFuncSetAttribute(k_fgather<T, V>, cudaFuncAttributeNonPortableClusterSizeAllowed, 0);
 }
 
+bool factor_launch_has_alternative(const Launch &L, int32_t nbatch) {
+  return nbatch > 1 && L.tb == SMALL_TB && (L.kind == K_UPDATE || L.kind == K_POTRF || L.kind == K_TRTRI);
+}
+
 template <typename T>
 cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, const double *Ax,
                        T *Lx, T *Linv, long long *status, cudaStream_t st, LaunchTrace *trace, const Batch &bt,
@@ -1788,6 +1792,8 @@ cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, co
     if (dual && L.wait >= 0) cudaStreamWaitEvent(s, (*two->events)[L.wait], 0);
     cudaError_t e = cudaSuccess;
     const bool small = L.tb == SMALL_TB;  // every tile of the launch fits the small variant
+    // the autotuner's choice for this launch: false keeps the default form of a batch
+    const bool alt = d.variant && d.variant[li] != 0 && factor_launch_has_alternative(L, (int32_t)nb);
     constexpr int TS = TileCfg<SMALL_TB>::threads;
     switch (L.kind) {
       case K_UPDATE:
@@ -1796,11 +1802,14 @@ cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, co
         if constexpr (!std::is_same<T, double>::value) {
           if (d.tensor_cores && !small)
             e = launch_update_tc(dim3(g, nb), s, prio, d, Lx, L.off, bt, status);
+          else if (alt)  // a batch's small tiles: one warp per (tile, matrix)
+            e = launch_prio(k_update_wb<T>, dim3(g, (nb + WT_WARPS - 1) / WT_WARPS), 32 * WT_WARPS, 0, s, prio,
+                            d.sn, d.upd_tasks, d.upd_entries, d.rel, Lx, L.off, (int32_t)nb, bt);
           else
             e = launch_prio(k_update_f32, dim3(g, nb), F32_THREADS, 0, s, prio, d.sn, d.upd_tasks, d.upd_entries,
                             d.rel, Lx, L.off, bt);
         }
-        else if (small && nb > 1)  // a batch: one warp per (tile, matrix)
+        else if (small && nb > 1 && !alt)  // a batch: one warp per (tile, matrix)
           e = launch_prio(k_update_wb<T>, dim3(g, (nb + WT_WARPS - 1) / WT_WARPS), 32 * WT_WARPS, 0, s, prio,
                           d.sn, d.upd_tasks, d.upd_entries, d.rel, Lx, L.off, (int32_t)nb, bt);
         else if (small)
@@ -1816,7 +1825,7 @@ cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, co
       case K_POTRF:
         // small tiles of a batch: a warp per tile (throughput); of one matrix: a CTA per tile, whose
         // four warps shorten each column step of the tile (latency; 64^2 factor 0.96 -> 0.83 ms)
-        if (small && nb > 1)
+        if (small && nb > 1 && !alt)
           e = launch_prio(k_potrf_w<T>, dim3((g + WT_WARPS - 1) / WT_WARPS, nb), 32 * WT_WARPS, 0, s, prio, d.sn,
                           d.tasks, (int64_t)g, Lx, status, d.piv, d.axc, d.dpos, L.off, bt);
         else if (small)
@@ -1841,7 +1850,7 @@ cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, co
           e = launch_prio(k_gemm_f32, dim3(g, nb), F32_THREADS, 0, s, prio, d.sn, d.tasks, Lx, L.off, bt);
         break;
       case K_TRTRI:
-        if (small && nb > 1)  // (as for POTRF)
+        if (small && nb > 1 && !alt)  // (as for POTRF)
           e = launch_prio(k_trtri_w<T>, dim3((g + WT_WARPS - 1) / WT_WARPS, nb), 32 * WT_WARPS, 0, s, prio, d.sn,
                           d.tasks, (int64_t)g, (const T *)Lx, Linv, L.off, bt);
         else

@@ -158,6 +158,7 @@ struct Plan {
   std::vector<UpdTask> upd_tasks;
   std::vector<Int4> tasks;            // every other kind of task
   std::vector<Launch> factor_launches;
+  std::vector<int8_t> variant;        // per factor launch: the autotuner's kernel form (0 default)
   std::vector<Launch> fwd_launches;
   std::vector<Launch> bwd_launches;
   // Forward solve by pushes: t holds tsize entries per right-hand side; the contribution list of

@@ -112,3 +112,30 @@ def test_uneven_batch_as_block_diagonal(torch_cuda):
         seg = slice(off, off + M.n)
         assert oracle.backward_error(M.n, M.Ap, M.Ai, M.Ax, b[seg], x[seg]) <= BERR_TOL
         off += M.n
+
+
+def test_autotune_keeps_results(torch_cuda):
+    """The batch autotuner times both kernel forms of the batch's small-tile launches and keeps the
+    faster; whatever it picks, every matrix's factor still matches the oracle, and refactoring
+    with the tuned plan agrees with the untuned one up to rounding (the forms add in other
+    orders)."""
+    torch = torch_cuda
+    import paper_1705_06575_gb300 as S
+    nb = 8
+    M, vals = w.same_pattern_batch(lambda r: w.dd2d9(28, r), nb, 50)
+    V = torch.from_numpy(np.ascontiguousarray(vals)).cuda()
+    s = S.Solver(M.n, M.Ap, M.Ai, M.perm)
+    S.sym_factor_batch(s.h, nb, V, M.nnz)
+    before = [S.sym_get_batch_factor_host(s.h, b).copy() for b in range(nb)]
+    tuned, changed = S.sym_autotune(s.h, nb, V, M.nnz, 2)
+    assert tuned > 0 and 0 <= changed <= tuned
+    S.sym_factor_batch(s.h, nb, V, M.nnz)
+    o = oracle.Oracle(M.n, M.Ap, M.Ai, M.perm)
+    sx = exports(s)
+    for b in range(nb):
+        after = S.sym_get_batch_factor_host(s.h, b)
+        assert np.abs(after - before[b]).max() <= 1e-13 * np.abs(before[b]).max()
+        o.factor(vals[b])
+        Lb, outside = panels_on_pattern(sx, after, o.Lp, o.Li)
+        assert outside == 0.0 and np.abs(Lb - o.Lx).max() <= ENTRY_RTOL * np.abs(o.Lx).max()
+    assert S.sym_autotune(s.h, 1, V, M.nnz, 1) == (0, 0)  # one matrix: nothing to tune
