@@ -75,3 +75,24 @@ def test_per_supernode_rules_reproduce_presets_and_oracle():
     import pytest
     with pytest.raises(S.SymError):  # one rule index per fundamental supernode is required
         S.Solver(M.n, M.Ap, M.Ai, M.perm, host_only=True, rules=(cm.RULES, fr[:-1]))
+
+
+def test_pretrained_per_supernode_weights_and_evaluation():
+    """The packaged per-supernode networks (FP64 and mixed-precision FP32 arms) have the network
+    shape, and their predictions on host features of a fresh pattern are finite per-supernode
+    log times; the stored held-out evaluation covers both arms."""
+    import json
+    import os
+    for arm in ("fp64", "fp32"):
+        m = cm.pretrained_sn(arm)
+        assert m.mean.shape == (cm.NFEAT_SN,) and np.all(m.std > 0)
+        assert m.theta.size == ref.nparams(cm.NFEAT_SN, m.hidden) and np.all(np.isfinite(m.theta))
+        tab = cm.fund_table(w.dd2d9(40, np.random.default_rng(8)))
+        for p in range(len(cm.PRESETS)):
+            y, _ = ref.forward(m.theta.astype(np.float64), (cm.sn_features(tab, p) - m.mean) / m.std,
+                               cm.NFEAT_SN, m.hidden)
+            assert y.shape == (tab["nf"],) and np.all(np.isfinite(y)) and np.all(y < np.log(1e4))
+    ev = json.load(open(os.path.join(os.path.dirname(cm.__file__), "costmodel_sn_eval.json")))
+    for arm in ("fp64", "fp32"):
+        a = ev["arms"][arm]
+        assert a["patterns"] > 0 and a["geomean_speedup_per_supernode"] > 0

@@ -95,3 +95,40 @@ def test_pretrained_model_on_fresh_patterns(torch_cuda):
     print("packaged model on fresh patterns:", ev)
     assert ev["geomean_speedup_vs_fixed_rule"] >= 0.97
     assert ev["total_time_ratio"] >= 0.97
+
+
+def test_pretrained_per_supernode_rules_on_fresh_patterns(torch_cuda):
+    """The packaged per-supernode network (FP64 arm, trained on 200 suite patterns of another
+    seed): its predictions through the library's kernels match the FP64 reference MLP; the
+    factor under the rules it chooses equals the oracle's factor under the same rules; and on
+    fresh suite patterns its choices are not slower than the fixed rule by measured time
+    (geometric mean, 3% noise allowance)."""
+    torch = torch_cuda
+    import oracle
+    import paper_1705_06575_gb300 as S
+    import workloads as w
+    from helpers import exports, panels_on_pattern
+    from paper_1705_06575_gb300 import costmodel as cm
+    m = cm.pretrained_sn("fp64")
+    mats, _, _ = cm.suite5(8, 3_000_000, 3e9)
+    M = mats[0]
+    tab = cm.fund_table(M)
+    X = np.concatenate([cm.sn_features(tab, p) for p in range(len(cm.PRESETS))])
+    got = m.predict(X, torch)
+    want, _ = ref.forward(m.theta.astype(np.float64), (X - m.mean) / m.std, cm.NFEAT_SN, m.hidden)
+    assert np.abs(got - want).max() <= 1e-4 * max(1.0, np.abs(want).max())
+    fr, pstar = cm.choose_rules(m, M, torch)
+    assert fr.shape == (tab["nf"],) and 0 <= pstar < len(cm.PRESETS)
+    s = S.Solver(M.n, M.Ap, M.Ai, M.perm, rules=(cm.RULES, fr))
+    o = oracle.Oracle(M.n, M.Ap, M.Ai, s.export("perm"), rules=cm.RULES, fund_rule=fr)
+    assert np.array_equal(s.export("super"), o.sn)
+    s.factor(torch.from_numpy(M.Ax).cuda())
+    assert o.factor(M.Ax, -1) == 0
+    vals, outside = panels_on_pattern(exports(s), s.factor_panels(), o.Lp, o.Li)
+    assert outside == 0.0
+    assert np.abs(vals - o.Lx).max() <= 1e-10 * np.abs(o.Lx).max()
+    s.close()
+    ev, rows = cm.evaluate_sn(m, mats, torch, flop_budget=3e9)
+    print("per-supernode rules on fresh patterns:", ev)
+    assert ev["patterns"] == len(mats)
+    assert ev["geomean_speedup_per_supernode"] >= 0.97
