@@ -196,12 +196,15 @@ int sym_batch_error_columns(sym_handle h, int64_t *cols);
 int sym_solve_batch(sym_handle h, int32_t nbatch, int32_t nrhs, const double *B, int64_t ldb,
                     int64_t bstride, double *X, int64_t ldx, int64_t xstride);
 
-/* Batch autotuner (this library's addition; the paper picks its variants by hand, Sec. 2.4):
- * for a batch of nbatch matrices (arguments as sym_factor_batch), every factor launch that has
- * two kernel forms (small-tile updates, POTRF and TRTRI: one warp per (tile, matrix), four
- * matrices per CTA, or one CTA per tile and matrix) is timed in both with CUDA events over reps
- * kernel-by-kernel factorizations of the given values, and the faster form is stored in the
- * plan for every later factorization of the handle (the captured graphs are rebuilt). The
+/* Autotuner (this library's addition; the paper picks its variants by hand, Sec. 2.4): for a
+ * batch of nbatch matrices (arguments as sym_factor_batch; nbatch = 1: one matrix, Ax as for
+ * sym_factor), every factor launch that has two kernel forms is timed in both with CUDA events
+ * over reps kernel-by-kernel factorizations of the given values, and the faster form is stored
+ * in the plan for every later factorization of the handle (the captured graphs are rebuilt).
+ * Forms: in a batch, small-tile updates, POTRF and TRTRI run one warp per (tile, matrix), four
+ * matrices per CTA, or one CTA per tile and matrix; for one matrix, FP64 updates of tiles with
+ * many entries run on a thread-block cluster per tile or one CTA per tile, and small-tile POTRF
+ * and TRTRI one CTA or one warp per tile. The
  * per-kernel profile totals are left as they were. *tuned: launches with two forms; *changed:
  * launches now on their second form (either pointer may be NULL). Errors as sym_factor_batch,
  * and SYM_ERR_INVALID for reps outside 1..100; the factor afterwards is that of the last run. */

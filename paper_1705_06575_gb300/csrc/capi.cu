@@ -585,7 +585,7 @@ static int analyze_impl(int64_t n, const int64_t *Ap, const int32_t *Ai, const i
     h->dp.storage = P.storage();
     h->dp.tensor_cores = (opt.flags & SYM_FLAG_NO_TENSOR_CORES) == 0;
     h->dp.piv = h->d_piv;
-    h->dp.variant = h->plan.variant.data();
+    for (int c = 0; c < 2; ++c) h->dp.variant[c] = h->plan.variant[c].data();
     h->dp.axc = h->d_Axc;
     h->dp.dpos = (const int64_t *)h->d_dpos;
   }
@@ -1048,11 +1048,14 @@ int sym_autotune(sym_handle h, int32_t nbatch, const double *Ax, int64_t stride,
   int rc = check_device(h);
   if (rc) return rc;
   if (reps < 1 || reps > 100) return fail(SYM_ERR_INVALID, "reps outside 1..100");
+  if (nbatch < 1) return fail(SYM_ERR_INVALID, "nbatch must be at least 1");
   auto &P = h->plan;
   const size_t nl = P.factor_launches.size();
   std::vector<char> tunable(nl, 0);
+  std::vector<int8_t> &var = P.variant[nbatch > 1 ? 1 : 0];  // one matrix and batches are tuned apart
   int32_t ntun = 0;
-  for (size_t li = 0; li < nl; ++li) ntun += tunable[li] = sym::factor_launch_has_alternative(P.factor_launches[li], nbatch);
+  for (size_t li = 0; li < nl; ++li) ntun += tunable[li] = sym::factor_launch_has_alternative(P.factor_launches[li], nbatch,
+                                                                           h->precision == SYM_PREC_FP64);
   if (tuned) *tuned = ntun;
   if (changed) *changed = 0;
   if (ntun == 0) return SYM_OK;
@@ -1065,7 +1068,7 @@ int sym_autotune(sym_handle h, int32_t nbatch, const double *Ax, int64_t stride,
   std::memcpy(nl0, h->prof_launches, sizeof nl0);
   std::vector<double> t[2] = {std::vector<double>(nl, 0.0), std::vector<double>(nl, 0.0)};
   for (int v = 0; v < 2 && !rc; ++v) {
-    for (size_t li = 0; li < nl; ++li) P.variant[li] = tunable[li] ? (int8_t)v : 0;
+    for (size_t li = 0; li < nl; ++li) var[li] = tunable[li] ? (int8_t)v : 0;
     drop_graphs(h);
     h->profiling = true;
     for (int32_t r = 0; r < reps && !rc; ++r) {
@@ -1077,8 +1080,8 @@ int sym_autotune(sym_handle h, int32_t nbatch, const double *Ax, int64_t stride,
   }
   int32_t nchg = 0;
   for (size_t li = 0; li < nl; ++li) {
-    P.variant[li] = tunable[li] && !rc && t[1][li] < t[0][li] ? 1 : 0;
-    nchg += P.variant[li];
+    var[li] = tunable[li] && !rc && t[1][li] < t[0][li] ? 1 : 0;
+    nchg += var[li];
   }
   h->profiling = prof0;
   std::memcpy(h->prof_ms, ms0, sizeof ms0);

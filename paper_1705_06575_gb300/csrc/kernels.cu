@@ -1763,8 +1763,13 @@ cudaError_t prepare_solve() {
   return cudaFuncSetAttribute(k_fgather<T, V>, cudaFuncAttributeNonPortableClusterSizeAllowed, 0);
 }
 
-bool factor_launch_has_alternative(const Launch &L, int32_t nbatch) {
-  return nbatch > 1 && L.tb == SMALL_TB && (L.kind == K_UPDATE || L.kind == K_POTRF || L.kind == K_TRTRI);
+bool factor_launch_has_alternative(const Launch &L, int32_t nbatch, bool fp64) {
+  const bool small = L.tb == SMALL_TB;
+  if (nbatch > 1)  // one warp per (tile, matrix) against one CTA per tile and matrix
+    return small && (L.kind == K_UPDATE || L.kind == K_POTRF || L.kind == K_TRTRI);
+  // one matrix: a clustered FP64 update against one CTA per tile; small-tile POTRF and TRTRI
+  // with one CTA per tile against one warp per tile
+  return (fp64 && !small && L.kind == K_UPDATE && L.cluster > 1) || (small && (L.kind == K_POTRF || L.kind == K_TRTRI));
 }
 
 template <typename T>
@@ -1793,7 +1798,9 @@ cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, co
     cudaError_t e = cudaSuccess;
     const bool small = L.tb == SMALL_TB;  // every tile of the launch fits the small variant
     // the autotuner's choice for this launch: false keeps the default form of a batch
-    const bool alt = d.variant && d.variant[li] != 0 && factor_launch_has_alternative(L, (int32_t)nb);
+    const int8_t *var = d.variant[nb > 1 ? 1 : 0];
+    const bool alt = var && var[li] != 0 &&
+                     factor_launch_has_alternative(L, (int32_t)nb, std::is_same<T, double>::value);
     constexpr int TS = TileCfg<SMALL_TB>::threads;
     switch (L.kind) {
       case K_UPDATE:
@@ -1815,7 +1822,7 @@ cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, co
         else if (small)
           e = launch_prio(k_update_flat<T, SMALL_TB, false>, dim3(g, nb), TS, 0, s, prio, d.sn, d.upd_tasks,
                           d.upd_entries, d.rel, Lx, L.off, bt);
-        else if (L.cluster > 1 && nb == 1)  // (a batch already fills the GPU through blockIdx.y)
+        else if (L.cluster > 1 && nb == 1 && !alt)  // (a batch already fills the GPU through blockIdx.y)
           e = launch_cluster_prio(k_update_flat<T, NB, true>, dim3(g, nb), THREADS, L.cluster, s, prio, d.sn,
                                   d.upd_tasks, d.upd_entries, d.rel, Lx, L.off, bt);
         else
@@ -1824,8 +1831,9 @@ cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, co
         break;
       case K_POTRF:
         // small tiles of a batch: a warp per tile (throughput); of one matrix: a CTA per tile, whose
-        // four warps shorten each column step of the tile (latency; 64^2 factor 0.96 -> 0.83 ms)
-        if (small && nb > 1 && !alt)
+        // four warps shorten each column step of the tile (latency; 64^2 factor 0.96 -> 0.83 ms);
+        // the autotuner's choice (alt) swaps the two
+        if (small && (nb > 1) != alt)
           e = launch_prio(k_potrf_w<T>, dim3((g + WT_WARPS - 1) / WT_WARPS, nb), 32 * WT_WARPS, 0, s, prio, d.sn,
                           d.tasks, (int64_t)g, Lx, status, d.piv, d.axc, d.dpos, L.off, bt);
         else if (small)
@@ -1850,7 +1858,7 @@ cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, co
           e = launch_prio(k_gemm_f32, dim3(g, nb), F32_THREADS, 0, s, prio, d.sn, d.tasks, Lx, L.off, bt);
         break;
       case K_TRTRI:
-        if (small && nb > 1 && !alt)  // (as for POTRF)
+        if (small && (nb > 1) != alt)  // (as for POTRF)
           e = launch_prio(k_trtri_w<T>, dim3((g + WT_WARPS - 1) / WT_WARPS, nb), 32 * WT_WARPS, 0, s, prio, d.sn,
                           d.tasks, (int64_t)g, (const T *)Lx, Linv, L.off, bt);
         else

@@ -30,7 +30,8 @@ struct DevPlan {
                                      // and no commit, so its first wait runs out
   double *piv = nullptr;             // FP32 factors: the FP64 pivot d_k of every permuted column k
                                      // (n per matrix), written by the POTRF kernels; else null
-  const int8_t *variant = nullptr;   // HOST array, one per factor launch: 1 runs the launch's
+  const int8_t *variant[2] = {nullptr, nullptr};  // HOST arrays, one entry per factor launch,
+                                     // [0] for one matrix, [1] for batches: 1 runs the launch's
                                      // alternative kernel form (see factor_launch_has_alternative),
                                      // as the autotuner chose; null or 0: the default form
   const double *axc = nullptr;       // FP32 factors: the FP64 copy of A's values (nnz_a per matrix)
@@ -81,10 +82,12 @@ cudaError_t prepare_update_tc();
 cudaError_t launch_update_tc(dim3 grid, cudaStream_t st, int prio, const DevPlan &d, float *Lx, int64_t toff,
                              const Batch &bt, long long *status);
 
-// Whether a factor launch has a second kernel form for a batch of nbatch matrices (the batch
-// autotuner times both): small-tile updates, POTRF and TRTRI, one warp per (tile, matrix) or one
-// CTA per tile and matrix.
-bool factor_launch_has_alternative(const Launch &L, int32_t nbatch);
+// Whether a factor launch has a second kernel form (the autotuner times both). A batch
+// (nbatch > 1): small-tile updates, POTRF and TRTRI, one warp per (tile, matrix) or one CTA per
+// tile and matrix. One matrix: clustered FP64 updates or one CTA per tile; small-tile POTRF and
+// TRTRI, one CTA or one warp per tile. fp64: the factor's precision (FP32 updates have no
+// cluster form).
+bool factor_launch_has_alternative(const Launch &L, int32_t nbatch, bool fp64);
 
 // Numeric factorization: scatter A into the zeroed panels, then run the launch schedule.
 // status: device int64, receives the smallest failing (permuted) column, or stays INT64_MAX;

@@ -158,7 +158,8 @@ struct Plan {
   std::vector<UpdTask> upd_tasks;
   std::vector<Int4> tasks;            // every other kind of task
   std::vector<Launch> factor_launches;
-  std::vector<int8_t> variant;        // per factor launch: the autotuner's kernel form (0 default)
+  std::vector<int8_t> variant[2];     // per factor launch: the autotuner's kernel form (0 default),
+                                      // [0] for one matrix, [1] for batches
   std::vector<Launch> fwd_launches;
   std::vector<Launch> bwd_launches;
   // Forward solve by pushes: t holds tsize entries per right-hand side; the contribution list of

@@ -841,7 +841,7 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
       }
     }
   }
-  P.variant.assign(P.factor_launches.size(), 0);
+  for (auto &v : P.variant) v.assign(P.factor_launches.size(), 0);
   // 12. Algorithmic flops of each kernel kind (see Plan::kind_flops).
   {
     auto sq = [](double x) { return x * x; };

@@ -138,4 +138,11 @@ def test_autotune_keeps_results(torch_cuda):
         o.factor(vals[b])
         Lb, outside = panels_on_pattern(sx, after, o.Lp, o.Li)
         assert outside == 0.0 and np.abs(Lb - o.Lx).max() <= ENTRY_RTOL * np.abs(o.Lx).max()
-    assert S.sym_autotune(s.h, 1, V, M.nnz, 1) == (0, 0)  # one matrix: nothing to tune
+    # tuning the handle for one matrix keeps the batch's choice (the two are stored apart): the
+    # batch's factors are bit-identical afterwards
+    tuned_batch = [S.sym_get_batch_factor_host(s.h, b).copy() for b in range(nb)]
+    tuned1, _ = S.sym_autotune(s.h, 1, V, M.nnz, 1)
+    assert tuned1 > 0
+    S.sym_factor_batch(s.h, nb, V, M.nnz)
+    for b in range(nb):
+        assert np.array_equal(S.sym_get_batch_factor_host(s.h, b), tuned_batch[b])

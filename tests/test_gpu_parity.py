@@ -278,3 +278,32 @@ def test_auto_ordering_factor_and_solve(torch_cuda, maker):
     X = s.solve_host(B)
     assert oracle.backward_error(M.n, M.Ap, M.Ai, M.Ax, B, X) <= BERR_TOL
     s.close()
+
+
+def test_autotune_one_matrix(torch_cuda):
+    """The autotuner on one matrix: its tunable launches are exactly the schedule's clustered
+    FP64 updates and small-tile POTRF / TRTRI launches; whatever forms it keeps, the factor still
+    matches the oracle entry by entry and the solve's backward error stays within bound."""
+    torch = torch_cuda
+    S = _lib()
+    M = w.cfg("laplace2d5_64")
+    s = S.Solver(M.n, M.Ap, M.Ai, M.perm)
+    raw = s.export("factor_launches").reshape(-1, 5)
+    kind, cluster, tb = raw[:, 0] & 0xffffffff, raw[:, 3] & 0xffffffff, raw[:, 4] >> 32
+    want = int(np.sum(((kind == 1) & (cluster > 1) & (tb != 32)) | ((tb == 32) & ((kind == 2) | (kind == 5)))))
+    assert want > 0 and np.any((kind == 1) & (cluster > 1))
+    Ax = torch.from_numpy(M.Ax).cuda()
+    s.factor(Ax)
+    L0 = s.factor_panels().copy()
+    tuned, changed = S.sym_autotune(s.h, 1, Ax, M.nnz, 2)
+    assert tuned == want and 0 <= changed <= tuned
+    s.factor(Ax)
+    L1 = s.factor_panels()
+    assert np.abs(L1 - L0).max() <= 1e-13 * np.abs(L0).max()
+    o = oracle.Oracle(M.n, M.Ap, M.Ai, M.perm)
+    assert o.factor(M.Ax, -1) == 0
+    vals, outside = panels_on_pattern(exports(s), L1, o.Lp, o.Li)
+    assert outside == 0.0 and np.abs(vals - o.Lx).max() <= ENTRY_RTOL * np.abs(o.Lx).max()
+    B = w.rhs(M.n, 1, np.random.default_rng(3))
+    x = s.solve(torch.from_numpy(np.ascontiguousarray(B[:, 0])).cuda()).cpu().numpy()
+    assert oracle.backward_error(M.n, M.Ap, M.Ai, M.Ax, B, x[:, None]) <= BERR_TOL
