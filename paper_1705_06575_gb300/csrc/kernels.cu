@@ -651,6 +651,185 @@ __global__ void __launch_bounds__(TileCfg<TB>::threads) k_trsm(const SNode *__re
   }
 }
 
+// (b') FP32 diagonal tiles of order up to NB with the column chain in registers. Warp w of the
+// first eight owns the columns w, w + 8, ... (lane l: rows l and l + 32 of each), the oldest
+// unfinished one in v[0]; a column is published in shared memory once final. Step c, one barrier:
+// the owner of column c applies column c - 1 to it, takes the FP64 pivot, scales the column and
+// publishes it; every owner applies column c - 1 to its other columns right of it; warp 8
+// subtracts l(k, c - 1)^2 from the FP64 diagonal of the rows k > c. Every element and every pivot
+// sees the operations of k_potrf in the same order, so the factors are bit-identical; what
+// changes is that the trailing columns stay in registers (k_potrf looks up a packed index and
+// goes through shared memory for every update, and its barrier waits for those chains).
+constexpr int PR_OWNERS = 8, PR_THREADS = 32 * (PR_OWNERS + 1);
+
+__global__ void __launch_bounds__(PR_THREADS) k_potrf_r(const SNode *__restrict__ sn, const Int4 *__restrict__ tasks,
+                                                       float *__restrict__ Lx, long long *status,
+                                                       double *__restrict__ piv, const double *__restrict__ axc,
+                                                       const int64_t *__restrict__ dpos, int64_t toff,
+                                                       const Batch bt) {
+  Lx += blockIdx.y * bt.lx;
+  status += blockIdx.y;
+  if (axc) axc += blockIdx.y * bt.nnz;
+  __shared__ float col[NB][NB + 1];  // [c][row]: column c once final, zero above the diagonal
+  __shared__ double dd[NB];          // FP64 diagonal (see k_potrf)
+  const Int4 t = tasks[toff + blockIdx.x];
+  const SNode sj = sn[t.a];
+  const int s = t.b;
+  const int ts = min(NB, sj.ncols - s * NB);
+  const int64_t ld = sj.nrows;
+  float *D = Lx + sj.lx + (int64_t)(s * NB) * ld + s * NB;
+  const int64_t g0 = sj.first + (int64_t)s * NB;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float v[8][2];  // owners: column cn + 8 u at rows lane, lane + 32
+  int cn = warp;
+  if (warp < PR_OWNERS) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int cc = warp + 8 * u, r = lane + 32 * h;
+        v[u][h] = (cc < ts && r < ts && r >= cc) ? D[(int64_t)cc * ld + r] : 0.f;
+      }
+  } else {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int r = lane + 32 * h;
+      if (r < ts) dd[r] = diag64(D[(int64_t)r * ld + r], axc, dpos, g0 + r);
+    }
+  }
+  __syncthreads();
+  for (int c = 0; c < ts; ++c) {
+    if (warp < PR_OWNERS) {
+      float p0 = 0.f, p1 = 0.f;  // column c - 1 at this lane's rows
+      if (c > 0) {
+        p0 = col[c - 1][lane];
+        p1 = col[c - 1][lane + 32];
+      }
+      const bool own = cn == c;  // warp-uniform
+      if (own) {
+        double d = dd[c];
+        if (c > 0) {
+          const float l = col[c - 1][c];
+          v[0][0] = fma(-p0, l, v[0][0]);
+          v[0][1] = fma(-p1, l, v[0][1]);
+          d = fma(-(double)l, (double)l, d);
+        }
+        if (!(d > 0.0)) {
+          if (lane == 0) atomicMin(status, (long long)(g0 + c));
+          d = 1.0;
+        }
+        if (lane == 0 && piv) piv[blockIdx.y * bt.piv + g0 + c] = d;
+        const float df = (float)d;
+        const float xf = rsqrt_newton(df);  // d x = sqrt(d)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int r = lane + 32 * h;
+          col[c][r] = r == c ? df * xf : r > c ? v[0][h] * xf : 0.f;
+        }
+      }
+      if (c > 0) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int cc = cn + 8 * u;
+          if ((u > 0 || !own) && cc < ts) {
+            const float l = col[c - 1][cc];
+            v[u][0] = fma(-p0, l, v[u][0]);
+            v[u][1] = fma(-p1, l, v[u][1]);
+          }
+        }
+      }
+      if (own) {
+#pragma unroll
+        for (int u = 0; u < 7; ++u) {
+          v[u][0] = v[u + 1][0];
+          v[u][1] = v[u + 1][1];
+        }
+        v[7][0] = v[7][1] = 0.f;
+        cn += 8;
+      }
+    } else if (c > 0) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int k = lane + 32 * h;
+        if (k > c && k < ts) {
+          const float l = col[c - 1][k];
+          dd[k] = fma(-(double)l, (double)l, dd[k]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < ts * ts; idx += PR_THREADS) {
+    const int r = idx % ts, c = idx / ts;
+    D[(int64_t)c * ld + r] = col[c][r];
+  }
+}
+
+// (c'') FP32 panel TRSM with the tile in registers: thread (r, g) owns row r of the tile and the
+// columns g, g + 4, ... (the oldest unfinished one in x[0]). Step c, one barrier: every thread
+// applies the solved column c - 1 to its columns right of it, and the owners of column c publish
+// X(:, c) = B(:, c) / L_cc. Same operations in the same order as k_trsm (bit-identical), without
+// a shared-memory round trip per update.
+__global__ void __launch_bounds__(THREADS) k_trsm_r(const SNode *__restrict__ sn, const Int4 *__restrict__ tasks,
+                                                    float *__restrict__ Lx, int64_t toff, const Batch bt) {
+  static_assert(THREADS == 4 * NB, "four column groups of NB rows");
+  Lx += blockIdx.y * bt.lx;
+  __shared__ float Ls[NB][NB + 1];  // [col][row], lower triangle of L_ss
+  __shared__ float xs[NB][NB + 1];  // [col][row]: solved columns
+  __shared__ float dinv[NB];
+  const Int4 t = tasks[toff + blockIdx.x];
+  const SNode sj = sn[t.a];
+  const int i = t.b, s = t.c;
+  const int ts = min(NB, sj.ncols - s * NB);
+  int64_t rb = d_row_tile_base(i, sj.ncols, sj.ncb);
+  int tm = d_row_tile_rows(i, sj.ncols, sj.nrows, sj.ncb);
+  const int half = t.d >> 16;  // 0: whole tile; 1, 2: its first or second 32 rows
+  if (half) {
+    rb += (half - 1) * (NB / 2);
+    tm = max(0, min(NB / 2, tm - (half - 1) * (NB / 2)));
+  }
+  const int64_t ld = sj.nrows;
+  const float *D = Lx + sj.lx + (int64_t)(s * NB) * ld + s * NB;
+  float *B = Lx + sj.lx + (int64_t)(s * NB) * ld + rb;
+  const int tid = threadIdx.x, r = tid & (NB - 1), g = tid >> 6;
+  for (int idx = tid; idx < ts * ts; idx += THREADS) {
+    const int rr = idx % ts, c = idx / ts;
+    if (rr >= c) Ls[c][rr] = D[(int64_t)c * ld + rr];
+  }
+  float x[NB / 4];
+  int cn = g;  // the column in x[0]
+#pragma unroll
+  for (int u = 0; u < NB / 4; ++u) {
+    const int cc = g + 4 * u;
+    x[u] = (r < tm && cc < ts) ? B[(int64_t)cc * ld + r] : 0.f;
+  }
+  __syncthreads();
+  if (tid < ts) dinv[tid] = 1.f / Ls[tid][tid];
+  __syncthreads();
+  for (int c = 0; c < ts; ++c) {
+    if (c > 0) {
+      const float xp = xs[c - 1][r];
+#pragma unroll
+      for (int u = 0; u < NB / 4; ++u) {
+        const int cc = cn + 4 * u;
+        if (cc < ts) x[u] = fma(-xp, Ls[c - 1][cc], x[u]);
+      }
+    }
+    if (cn == c) {  // uniform within a warp (its lanes share g)
+      xs[c][r] = x[0] * dinv[c];
+#pragma unroll
+      for (int u = 0; u < NB / 4 - 1; ++u) x[u] = x[u + 1];
+      x[NB / 4 - 1] = 0.f;
+      cn += 4;
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < tm * ts; idx += THREADS) {
+    const int rr = idx % tm, c = idx / tm;
+    B[(int64_t)c * ld + rr] = xs[c][rr];
+  }
+}
+
 // (c') Trailing update inside J: tile (i, j) -= tile (i, s) * tile (j, s)^T.
 template <typename T>
 __global__ void __launch_bounds__(THREADS) k_gemm(const SNode *__restrict__ sn,
@@ -1839,6 +2018,9 @@ cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, co
         else if (small)
           e = launch_prio(k_potrf<T, SMALL_TB>, dim3(g, nb), TS, 0, s, prio, d.sn, d.tasks, Lx, status, d.piv, d.axc,
                           d.dpos, L.off, bt);
+        else if constexpr (std::is_same<T, float>::value)  // the column chain in registers
+          e = launch_prio(k_potrf_r, dim3(g, nb), PR_THREADS, 0, s, prio, d.sn, d.tasks, Lx, status, d.piv, d.axc,
+                          d.dpos, L.off, bt);
         else
           e = launch_prio(k_potrf<T, NB>, dim3(g, nb), THREADS, 0, s, prio, d.sn, d.tasks, Lx, status, d.piv, d.axc,
                           d.dpos, L.off, bt);
@@ -1846,10 +2028,14 @@ cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, co
       case K_TRSM:
         // (a warp-per-tile form with the column pairs mapped flat onto the lanes made the
         // 512 x 128^2 batch's TRSM slower, 11.0 -> 16.3 ms: its tiles have enough rows)
-        e = small ? launch_prio(k_trsm<T, SMALL_TB>, dim3(g, nb), TS, trsm_smem<T, SMALL_TB>(), s, prio, d.sn, d.tasks, Lx,
-                                L.off, bt)
-                  : launch_prio(k_trsm<T, NB>, dim3(g, nb), THREADS, trsm_smem<T, NB>(), s, prio, d.sn, d.tasks, Lx,
-                                L.off, bt);
+        if (small)
+          e = launch_prio(k_trsm<T, SMALL_TB>, dim3(g, nb), TS, trsm_smem<T, SMALL_TB>(), s, prio, d.sn, d.tasks, Lx,
+                          L.off, bt);
+        else if constexpr (std::is_same<T, float>::value)  // the tile in registers
+          e = launch_prio(k_trsm_r, dim3(g, nb), THREADS, 0, s, prio, d.sn, d.tasks, Lx, L.off, bt);
+        else
+          e = launch_prio(k_trsm<T, NB>, dim3(g, nb), THREADS, trsm_smem<T, NB>(), s, prio, d.sn, d.tasks, Lx, L.off,
+                          bt);
         break;
       case K_GEMM:
         if constexpr (std::is_same<T, double>::value)
