@@ -586,6 +586,7 @@ static int analyze_impl(int64_t n, const int64_t *Ap, const int32_t *Ai, const i
     h->dp.tensor_cores = (opt.flags & SYM_FLAG_NO_TENSOR_CORES) == 0;
     h->dp.piv = h->d_piv;
     for (int c = 0; c < 2; ++c) h->dp.variant[c] = h->plan.variant[c].data();
+    h->dp.batch_warp = h->plan.batch_warp.data();
     h->dp.axc = h->d_Axc;
     h->dp.dpos = (const int64_t *)h->d_dpos;
   }

@@ -6,8 +6,10 @@
 //       scattered through the relative row maps, one CTA (or cluster) per NB x NB tile of J —
 //       k_update_flat (FP64), k_update_f32 (FP32), k_update_tc (FP32 on the tensor cores,
 //       tc_update.cu);
-//   (b) dense Cholesky of the diagonal block — k_potrf (per diagonal tile) and
-//   (c) dense triangular solves on the rows below it — k_trsm, with k_gemm applying the
+//   (b) dense Cholesky of the diagonal block — k_potrf (per diagonal tile; k_potrf_r for FP32
+//       tiles of order NB) and
+//   (c) dense triangular solves on the rows below it — k_trsm (k_trsm_r for FP32 tiles of
+//       NB columns), with k_gemm applying the
 //       trailing updates inside J when J is wider than one tile.
 // Supernodes of one level of the supernodal tree are independent and run in the same launches.
 // The solve follows Sec. 3.1: diagonal block first, then the off-diagonal part; the forward
@@ -1657,6 +1659,48 @@ __global__ void __launch_bounds__(32 * WT_WARPS) k_update_wb(const SNode *__rest
   }
 }
 
+// The same for tiles of any size (batches): one warp per (tile, matrix), each element of an entry
+// read, updated and written back in global memory by one lane (the tile is not staged: a 64 x 64
+// accumulator per warp would leave room for few warps). The entries of a tile are applied in
+// order, k ascending, as in every other form (bit-identical results); __syncwarp orders one
+// entry's writes before the next entry's reads of the same elements.
+template <typename T>
+__global__ void __launch_bounds__(32 * WT_WARPS) k_update_wg(const SNode *__restrict__ sn,
+                                                             const UpdTask *__restrict__ tasks,
+                                                             const UpdEntry *__restrict__ ents,
+                                                             const int32_t *__restrict__ rel, T *__restrict__ Lx,
+                                                             int64_t toff, int32_t nmat, const Batch bt) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int32_t mat = blockIdx.y * WT_WARPS + w;
+  if (mat >= nmat) return;  // warp-uniform; only warp-level synchronization below
+  Lx += (int64_t)mat * bt.lx;
+  const UpdTask t = tasks[toff + blockIdx.x];
+  const SNode sj = sn[t.J];
+  const int64_t rb = d_row_tile_base(t.bi, sj.ncols, sj.ncb);
+  const int cb = t.bj * NB;
+  const bool diag = t.bi == t.bj;
+  T *C = Lx + sj.lx + (int64_t)cb * sj.nrows + rb;
+  for (int64_t e = t.e0; e < t.e1; ++e) {
+    const UpdEntry E = ents[e];
+    const SNode sk = sn[E.K];
+    const int64_t ld = sk.nrows;
+    const int cnt = diag ? E.m * (E.m + 1) / 2 : E.m * E.n;
+    for (int el = lane; el < cnt; el += 32) {
+      int a, b;
+      if (diag) tri_decode(el, a, b);
+      else a = el % E.m, b = el / E.m;
+      const int pr = rel[E.relr + a] - (int)rb, pc = rel[E.relc + b] - cb;
+      const T *pa = Lx + sk.lx + E.r_lo + a, *pb = Lx + sk.lx + E.c_lo + b;
+      T *cp = C + (int64_t)pc * sj.nrows + pr;
+      T r = *cp;
+#pragma unroll 4
+      for (int k = 0; k < sk.ncols; ++k) r = fma(-pa[k * ld], pb[k * ld], r);
+      *cp = r;
+    }
+    __syncwarp();
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(32 * WT_WARPS) k_potrf_w(const SNode *__restrict__ sn, const Int4 *__restrict__ tasks,
                                                            int64_t ntask, T *__restrict__ Lx, long long *status,
@@ -1945,7 +1989,8 @@ cudaError_t prepare_solve() {
 bool factor_launch_has_alternative(const Launch &L, int32_t nbatch, bool fp64) {
   const bool small = L.tb == SMALL_TB;
   if (nbatch > 1)  // one warp per (tile, matrix) against one CTA per tile and matrix
-    return small && (L.kind == K_UPDATE || L.kind == K_POTRF || L.kind == K_TRTRI);
+    return (small && (L.kind == K_UPDATE || L.kind == K_POTRF || L.kind == K_TRTRI)) ||
+           (fp64 && !small && L.kind == K_UPDATE);
   // one matrix: a clustered FP64 update against one CTA per tile; small-tile POTRF and TRTRI
   // with one CTA per tile against one warp per tile
   return (fp64 && !small && L.kind == K_UPDATE && L.cluster > 1) || (small && (L.kind == K_POTRF || L.kind == K_TRTRI));
@@ -1997,6 +2042,9 @@ cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, co
         }
         else if (small && nb > 1 && !alt)  // a batch: one warp per (tile, matrix)
           e = launch_prio(k_update_wb<T>, dim3(g, (nb + WT_WARPS - 1) / WT_WARPS), 32 * WT_WARPS, 0, s, prio,
+                          d.sn, d.upd_tasks, d.upd_entries, d.rel, Lx, L.off, (int32_t)nb, bt);
+        else if (!small && nb > 1 && (d.batch_warp && d.batch_warp[li]) != alt)  // small entries of a batch
+          e = launch_prio(k_update_wg<T>, dim3(g, (nb + WT_WARPS - 1) / WT_WARPS), 32 * WT_WARPS, 0, s, prio,
                           d.sn, d.upd_tasks, d.upd_entries, d.rel, Lx, L.off, (int32_t)nb, bt);
         else if (small)
           e = launch_prio(k_update_flat<T, SMALL_TB, false>, dim3(g, nb), TS, 0, s, prio, d.sn, d.upd_tasks,

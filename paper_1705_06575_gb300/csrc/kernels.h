@@ -30,6 +30,9 @@ struct DevPlan {
                                      // and no commit, so its first wait runs out
   double *piv = nullptr;             // FP32 factors: the FP64 pivot d_k of every permuted column k
                                      // (n per matrix), written by the POTRF kernels; else null
+  const int8_t *batch_warp = nullptr;  // HOST array, one per factor launch: a batch's default form
+                                       // of the launch is one warp per (tile, matrix) (full-tile
+                                       // FP64 updates with small entries)
   const int8_t *variant[2] = {nullptr, nullptr};  // HOST arrays, one entry per factor launch,
                                      // [0] for one matrix, [1] for batches: 1 runs the launch's
                                      // alternative kernel form (see factor_launch_has_alternative),
@@ -84,7 +87,9 @@ cudaError_t launch_update_tc(dim3 grid, cudaStream_t st, int prio, const DevPlan
 
 // Whether a factor launch has a second kernel form (the autotuner times both). A batch
 // (nbatch > 1): small-tile updates, POTRF and TRTRI, one warp per (tile, matrix) or one CTA per
-// tile and matrix. One matrix: clustered FP64 updates or one CTA per tile; small-tile POTRF and
+// tile and matrix; FP64 updates of full tiles, one CTA per tile and matrix or one warp per
+// (tile, matrix) working in global memory (the default of each is DevPlan::batch_warp; the
+// alternative is the other). One matrix: clustered FP64 updates or one CTA per tile; small-tile POTRF and
 // TRTRI, one CTA or one warp per tile. fp64: the factor's precision (FP32 updates have no
 // cluster form).
 bool factor_launch_has_alternative(const Launch &L, int32_t nbatch, bool fp64);

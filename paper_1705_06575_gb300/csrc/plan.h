@@ -22,6 +22,10 @@ constexpr int SOLVE_CW = 512;
 constexpr int SOLVE_MAXRHS = 8;
 // Order bound of the tiles that the small-tile kernel variants take.
 constexpr int SMALL_TILE = 32;
+// Batches: full-tile update launches whose entries have at most this many output elements on
+// average default to the warp-per-(tile, matrix) form (measured on a 512 x 128^2 9-point batch:
+// 1.35-4.7x faster than one CTA per tile at 34-134 elements, about equal at 175-230).
+constexpr int BATCH_WARP_ELEMS = 160;
 // Trailing-update GEMM CTAs resident on the whole GPU at once (3 per SM on 152 SMs): the size of
 // one wave, used to split the last wave of a long launch into finer work.
 constexpr int GEMM_SLOTS = 3 * 152;
@@ -160,6 +164,8 @@ struct Plan {
   std::vector<Launch> factor_launches;
   std::vector<int8_t> variant[2];     // per factor launch: the autotuner's kernel form (0 default),
                                       // [0] for one matrix, [1] for batches
+  std::vector<int8_t> batch_warp;     // per factor launch: 1 if a batch's default form of this
+                                      // full-tile update is one warp per (tile, matrix)
   std::vector<Launch> fwd_launches;
   std::vector<Launch> bwd_launches;
   // Forward solve by pushes: t holds tsize entries per right-hand side; the contribution list of

@@ -842,6 +842,24 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
     }
   }
   for (auto &v : P.variant) v.assign(P.factor_launches.size(), 0);
+  // Default form of a batch's full-tile FP64 update launches: one warp per (tile, matrix) when
+  // the launch's entries are small (at most BATCH_WARP_ELEMS output elements on average: the
+  // one-CTA form then spends its time staging and waiting at barriers), else one CTA per tile.
+  P.batch_warp.assign(P.factor_launches.size(), 0);
+  for (size_t li = 0; li < P.factor_launches.size(); ++li) {
+    const Launch &L = P.factor_launches[li];
+    if (L.kind != K_UPDATE || L.tb == SMALL_TILE) continue;
+    double elems = 0.0, cnt = 0.0;
+    for (int64_t t = L.off; t < L.off + L.count; ++t) {
+      const UpdTask &u = P.upd_tasks[t];
+      for (int64_t e = u.e0; e < u.e1; ++e) {
+        const UpdEntry &E = P.upd_entries[e];
+        elems += u.bi == u.bj ? 0.5 * E.m * (E.m + 1) : (double)E.m * E.n;
+        cnt += 1.0;
+      }
+    }
+    P.batch_warp[li] = cnt > 0.0 && elems <= BATCH_WARP_ELEMS * cnt;
+  }
   // 12. Algorithmic flops of each kernel kind (see Plan::kind_flops).
   {
     auto sq = [](double x) { return x * x; };
