@@ -1564,17 +1564,24 @@ __global__ void __launch_bounds__(TileCfg<TB>::threads) k_trtri(const SNode *__r
   __syncthreads();
   if (tid < ts) dinv[tid] = 1.0 / a[tid][tid];
   __syncthreads();
+  if (tid == 0 && ts > 0) x[0][0] *= dinv[0];  // row 0 is final
+  __syncthreads();
+  // Step c: row c of X is final and scaled; the rows below subtract l(r, c) times it, and row
+  // c + 1, now final, is scaled by 1 / L(c+1, c+1) by the threads that updated it. Each element
+  // gets the operations (and roundings) of an elimination that scales row c as it is used.
   const int r = tid % TB, jg = tid / TB;
-  for (int c = 0; c < ts; ++c) {
+  for (int c = 0; c + 1 < ts; ++c) {
     if (r > c && r < ts) {
       const double l = a[c][r];
-      for (int j = jg; j <= c; j += G) x[j][r] = fma(-l, x[j][c] * dinv[c], x[j][r]);
+      const double sc = r == c + 1 ? dinv[r] : 1.0;
+      for (int j = jg; j <= c; j += G) {
+        const double v = fma(-l, x[j][c], x[j][r]);
+        x[j][r] = r == c + 1 ? v * sc : v;
+      }
+      if (r == c + 1 && jg == (c + 1) % G) x[r][r] *= sc;
     }
     __syncthreads();
-    if (r == c)
-      for (int j = jg; j <= c; j += G) x[j][c] *= dinv[c];
   }
-  __syncthreads();
   T *out = Linv + sj.dx + (int64_t)s * NB * NB;
   for (int idx = tid; idx < ts * ts; idx += TT) {
     const int rr = idx % ts, c = idx / ts;
@@ -1792,14 +1799,17 @@ __global__ void __launch_bounds__(32 * WT_WARPS) k_trtri_w(const SNode *__restri
   __syncwarp();
   if (lane < ts) dinv[lane] = 1.0 / a[pk(ts, lane, lane)];
   __syncwarp();
-  for (int c = 0; c < ts; ++c) {
+  if (lane == 0 && ts > 0) x[pk(ts, 0, 0)] *= dinv[0];  // row 0 is final
+  __syncwarp();
+  // As in k_trtri: row c is final and scaled; row c + 1 is scaled by the lanes that update it.
+  for (int c = 0; c + 1 < ts; ++c) {
     const int m = ts - 1 - c;  // rows c+1 .. ts-1 of columns 0 .. c
     for (int el = lane; el < m * (c + 1); el += 32) {
       const int r = c + 1 + el % m, j = el / m;
-      x[pk(ts, j, r)] = fma(-a[pk(ts, c, r)], x[pk(ts, j, c)] * dinv[c], x[pk(ts, j, r)]);
+      const double v = fma(-a[pk(ts, c, r)], x[pk(ts, j, c)], x[pk(ts, j, r)]);
+      x[pk(ts, j, r)] = r == c + 1 ? v * dinv[r] : v;
     }
-    __syncwarp();
-    for (int j = lane; j <= c; j += 32) x[pk(ts, j, c)] *= dinv[c];
+    if (lane == 31) x[pk(ts, c + 1, c + 1)] *= dinv[c + 1];  // (no update touches it at step c)
     __syncwarp();
   }
   T *out = Linv + sj.dx + (int64_t)s * NB * NB;
