@@ -1817,6 +1817,182 @@ __global__ void __launch_bounds__(32 * WT_WARPS) k_trtri_w(const SNode *__restri
     if (lane < ts) out[(int64_t)c * ts + lane] = lane >= c ? (T)x[pk(ts, c, lane)] : T(0);
 }
 
+// (f) Warp forms of the solve kernels for batches, on launches whose supernodes all have at most
+// SMALL_TILE columns (the schedule marks them tb = SMALL_TILE): one warp per (task, matrix), the
+// same task of WT_WARPS consecutive matrices per CTA. A batch's leaf levels hold ~10^3 tasks of a
+// few dozen values each per matrix; one CTA per (task, matrix) spends its time being scheduled.
+// Each keeps its CTA form's order of operations (bit-identical results).
+
+// S_FSUM (k_fsum): lane c subtracts column c's contributions.
+template <typename V, int NR>
+__global__ void __launch_bounds__(32 * WT_WARPS) k_fsum_w(const SNode *__restrict__ sn, const Int4 *__restrict__ tasks,
+                                                          const int64_t *__restrict__ cptr,
+                                                          const int32_t *__restrict__ contrib,
+                                                          const V *__restrict__ t, int64_t tsize, V *__restrict__ y,
+                                                          int64_t n, int r0, int64_t toff, int32_t nmat,
+                                                          const Batch bt) {
+  pdl_trigger_early<V>();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int32_t mat = blockIdx.y * WT_WARPS + w;
+  if (mat >= nmat) return;
+  y += (int64_t)mat * bt.y;
+  t += (int64_t)mat * bt.t;
+  const Int4 tk = tasks[toff + blockIdx.x];
+  const SNode sj = sn[tk.a];
+  pdl_wait_then_trigger<V>();  // t and y are the predecessors' output
+  for (int c = lane; c < sj.ncols; c += 32) {
+    const int64_t gcol = sj.first + c;
+    V acc[NR];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) acc[q] = V(0);
+    for (int64_t p = cptr[gcol]; p < cptr[gcol + 1]; ++p) {
+      const int64_t e = contrib[p];
+#pragma unroll
+      for (int q = 0; q < NR; ++q) acc[q] += t[(int64_t)q * tsize + e];
+    }
+#pragma unroll
+    for (int q = 0; q < NR; ++q) y[(int64_t)(r0 + q) * n + gcol] -= acc[q];
+  }
+}
+
+// S_FPUSH (k_fpush): lane r owns rows r and r + 32 of the row tile; each row's product is summed
+// over the columns g, g + 4, ... in four partial sums added as ((g0 + g1) + (g2 + g3)).
+template <typename T, typename V, int NR>
+__global__ void __launch_bounds__(32 * WT_WARPS) k_fpush_w(const SNode *__restrict__ sn, const Int4 *__restrict__ tasks,
+                                                           const T *__restrict__ Lx, const V *__restrict__ y,
+                                                           V *__restrict__ t, int64_t tsize, int64_t n, int r0,
+                                                           int64_t toff, int32_t nmat, const Batch bt) {
+  pdl_trigger_early<V>();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int32_t mat = blockIdx.y * WT_WARPS + w;
+  if (mat >= nmat) return;
+  Lx += (int64_t)mat * bt.lx;
+  y += (int64_t)mat * bt.y;
+  t += (int64_t)mat * bt.t;
+  const Int4 tk = tasks[toff + blockIdx.x];
+  const SNode sj = sn[tk.a];
+  const int64_t rb = d_row_tile_base(tk.b, sj.ncols, sj.ncb);
+  const int tm = d_row_tile_rows(tk.b, sj.ncols, sj.nrows, sj.ncb);
+  const int c0 = tk.c * SOLVE_CW, cw = min(SOLVE_CW, sj.ncols - c0);
+  const int64_t base = sj.tx + (int64_t)tk.c * (sj.nrows - sj.ncols) + (rb - sj.ncols);
+  pdl_wait_then_trigger<V>();  // y_J is the predecessor's output
+  const V *yj = y + (int64_t)r0 * n + sj.first + c0;
+  for (int r = lane; r < tm; r += 32) {
+    const T *row = Lx + sj.lx + (int64_t)c0 * sj.nrows + rb + r;
+    V acc[4][NR];
+#pragma unroll
+    for (int g = 0; g < 4; ++g)
+#pragma unroll
+      for (int q = 0; q < NR; ++q) acc[g][q] = V(0);
+    for (int c = 0; c < cw; ++c) {
+      const V l = (V)row[(int64_t)c * sj.nrows];
+#pragma unroll
+      for (int q = 0; q < NR; ++q) {
+        switch (c & 3) {  // (a register array cannot be indexed by a run-time value)
+          case 0: acc[0][q] = fma(l, yj[(int64_t)q * n + c], acc[0][q]); break;
+          case 1: acc[1][q] = fma(l, yj[(int64_t)q * n + c], acc[1][q]); break;
+          case 2: acc[2][q] = fma(l, yj[(int64_t)q * n + c], acc[2][q]); break;
+          default: acc[3][q] = fma(l, yj[(int64_t)q * n + c], acc[3][q]); break;
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NR; ++q) t[(int64_t)q * tsize + base + r] = (acc[0][q] + acc[1][q]) + (acc[2][q] + acc[3][q]);
+  }
+}
+
+// S_BGATHER (k_bgather): per column of the slice, lane l sums the rows below the diagonal block
+// with index = l (mod 32) in ascending order, then the warp adds the lanes' sums by butterfly.
+template <typename T, typename V, int NR>
+__global__ void __launch_bounds__(32 * WT_WARPS) k_bgather_w(const SNode *__restrict__ sn,
+                                                             const int32_t *__restrict__ rows,
+                                                             const Int4 *__restrict__ tasks, const T *__restrict__ Lx,
+                                                             V *__restrict__ y, int64_t n, int r0, int64_t toff,
+                                                             int32_t nmat, const Batch bt) {
+  pdl_trigger_early<V>();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int32_t mat = blockIdx.y * WT_WARPS + w;
+  if (mat >= nmat) return;
+  Lx += (int64_t)mat * bt.lx;
+  y += (int64_t)mat * bt.y;
+  const Int4 tk = tasks[toff + blockIdx.x];
+  const SNode sj = sn[tk.a];
+  const int c0 = tk.b * BG;
+  const int tn = min(BG, sj.ncols - c0);
+  const int32_t *R = rows + sj.rowp;
+  pdl_wait_then_trigger<V>();  // z is the predecessor's output
+  for (int c = 0; c < tn; ++c) {
+    const T *col = Lx + sj.lx + (int64_t)(c0 + c) * sj.nrows;
+    V sa[NR];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) sa[q] = V(0);
+    for (int rr = sj.ncols + lane; rr < sj.nrows; rr += 32) {
+      const V la = (V)col[rr];
+      const int64_t g = R[rr];
+#pragma unroll
+      for (int q = 0; q < NR; ++q) sa[q] = fma(la, y[(int64_t)(r0 + q) * n + g], sa[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < NR; ++q) {
+      V v = sa[q];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      sa[q] = v;
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int q = 0; q < NR; ++q) y[(int64_t)(r0 + q) * n + sj.first + c0 + c] -= sa[q];
+    }
+  }
+}
+
+// S_FSTEP / S_BSTEP of a supernode of at most SMALL_TILE columns (one column tile, task
+// {J, 0, 0, 0}): y_J <- L_JJ^{-1} y_J (forward) or L_JJ^{-T} y_J (backward) with the precomputed
+// inverse; lane r forms row r in two partial sums as write_solved_tile does.
+template <typename T, typename V, int NR, bool TRANS>
+__global__ void __launch_bounds__(32 * WT_WARPS) k_dstep_w(const SNode *__restrict__ sn, const Int4 *__restrict__ tasks,
+                                                           const T *__restrict__ Linv, V *__restrict__ y, int64_t n,
+                                                           int r0, int64_t toff, int32_t nmat, const Batch bt) {
+  __shared__ V vs[WT_WARPS][NR][SMALL_TILE];
+  pdl_trigger_early<V>();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int32_t mat = blockIdx.y * WT_WARPS + w;
+  if (mat >= nmat) return;
+  Linv += (int64_t)mat * bt.dinv;
+  y += (int64_t)mat * bt.y;
+  const Int4 tk = tasks[toff + blockIdx.x];
+  const SNode sj = sn[tk.a];
+  const int tu = min(SMALL_TILE, sj.ncols);
+  const T *Li = Linv + sj.dx;  // tu x tu, column-major, lower
+  pdl_wait_then_trigger<V>();  // y is the predecessor's output
+#pragma unroll
+  for (int q = 0; q < NR; ++q)
+    if (lane < tu) vs[w][q][lane] = y[(int64_t)(r0 + q) * n + sj.first + lane];
+  __syncwarp();
+  if (lane < tu) {
+    const int r = lane;
+#pragma unroll
+    for (int q = 0; q < NR; ++q) {
+      V a0 = V(0), a1 = V(0);
+      if (!TRANS) {  // (L^-1)(r, k) for k <= r
+        int k = 0;
+        for (; k + 1 <= r; k += 2) {
+          a0 = fma((V)Li[(int64_t)k * tu + r], vs[w][q][k], a0);
+          a1 = fma((V)Li[(int64_t)(k + 1) * tu + r], vs[w][q][k + 1], a1);
+        }
+        if (k <= r) a0 = fma((V)Li[(int64_t)k * tu + r], vs[w][q][k], a0);
+      } else {  // (L^-1)(k, r) for k >= r
+        int k = r;
+        for (; k + 1 < tu; k += 2) {
+          a0 = fma((V)Li[(int64_t)r * tu + k], vs[w][q][k], a0);
+          a1 = fma((V)Li[(int64_t)r * tu + k + 1], vs[w][q][k + 1], a1);
+        }
+        if (k < tu) a0 = fma((V)Li[(int64_t)r * tu + k], vs[w][q][k], a0);
+      }
+      y[(int64_t)(r0 + q) * n + sj.first + r] = a0 + a1;
+    }
+  }
+}
+
 template <typename T, int TB>
 constexpr size_t trsm_smem() { return sizeof(T) * (TB * (TB + 1) + TB * (NB + 1) + TB); }
 template <int TB>
@@ -2157,6 +2333,12 @@ cudaError_t run_sweeps(const DevPlan &d, const std::vector<Launch> &fwd, const s
           break;
         }
         case S_FSTEP:
+          if (nb > 1 && L.tb == SMALL_TB) {  // a batch's supernodes of <= SMALL_TILE columns
+            SYM_NR_DISPATCH(nr, (e = launch_pdl(k_dstep_w<T, V, NR, false>, dim3(g, (nb + WT_WARPS - 1) / WT_WARPS),
+                                                32 * WT_WARPS, 0, st, d.sn, d.tasks, Linv, y, n, r0, L.off,
+                                                (int32_t)nb, bt)));
+            break;
+          }
           if (L.cluster == 4) {
             SYM_NR_DISPATCH(nr, (e = launch_step_c(k_step_c<T, V, NR, true>, dim3(4 * g, nb), st, d.sn, d.tasks, Lx,
                                                    Linv, y, n, r0, L.off, bt)));
@@ -2169,12 +2351,24 @@ cudaError_t run_sweeps(const DevPlan &d, const std::vector<Launch> &fwd, const s
                                Linv, y, n, r0, nr, L.off, bt);
           break;
         case S_FPUSH:
-          SYM_NR_DISPATCH(nr, (e = launch_pdl(k_fpush<T, V, NR>, dim3(g, nb), THREADS, 0, st, d.sn, d.tasks, Lx,
-                                              (const V *)y, tbuf, d.tsize, n, r0, L.off, bt)));
+          if (nb > 1 && L.tb == SMALL_TB) {
+            SYM_NR_DISPATCH(nr, (e = launch_pdl(k_fpush_w<T, V, NR>, dim3(g, (nb + WT_WARPS - 1) / WT_WARPS),
+                                                32 * WT_WARPS, 0, st, d.sn, d.tasks, Lx, (const V *)y, tbuf, d.tsize,
+                                                n, r0, L.off, (int32_t)nb, bt)));
+          } else {
+            SYM_NR_DISPATCH(nr, (e = launch_pdl(k_fpush<T, V, NR>, dim3(g, nb), THREADS, 0, st, d.sn, d.tasks, Lx,
+                                                (const V *)y, tbuf, d.tsize, n, r0, L.off, bt)));
+          }
           break;
         case S_FSUM:
-          SYM_NR_DISPATCH(nr, (e = launch_pdl(k_fsum<V, NR>, dim3(g, nb), THREADS, 0, st, d.sn, d.tasks, d.cptr,
-                                              d.contrib, (const V *)tbuf, d.tsize, y, n, r0, L.off, bt)));
+          if (nb > 1 && L.tb == SMALL_TB) {
+            SYM_NR_DISPATCH(nr, (e = launch_pdl(k_fsum_w<V, NR>, dim3(g, (nb + WT_WARPS - 1) / WT_WARPS),
+                                                32 * WT_WARPS, 0, st, d.sn, d.tasks, d.cptr, d.contrib,
+                                                (const V *)tbuf, d.tsize, y, n, r0, L.off, (int32_t)nb, bt)));
+          } else {
+            SYM_NR_DISPATCH(nr, (e = launch_pdl(k_fsum<V, NR>, dim3(g, nb), THREADS, 0, st, d.sn, d.tasks, d.cptr,
+                                                d.contrib, (const V *)tbuf, d.tsize, y, n, r0, L.off, bt)));
+          }
           break;
         default:
           return cudaErrorInvalidValue;
@@ -2187,10 +2381,22 @@ cudaError_t run_sweeps(const DevPlan &d, const std::vector<Launch> &fwd, const s
       cudaError_t e = cudaSuccess;
       switch (L.kind) {
         case S_BGATHER:
-          SYM_NR_DISPATCH(nr, (e = launch_pdl(k_bgather<T, V, NR>, dim3(g, nb), THREADS, 0, st, d.sn, d.rows, d.tasks,
-                                              Lx, y, n, r0, L.off, bt)));
+          if (nb > 1 && L.tb == SMALL_TB) {
+            SYM_NR_DISPATCH(nr, (e = launch_pdl(k_bgather_w<T, V, NR>, dim3(g, (nb + WT_WARPS - 1) / WT_WARPS),
+                                                32 * WT_WARPS, 0, st, d.sn, d.rows, d.tasks, Lx, y, n, r0, L.off,
+                                                (int32_t)nb, bt)));
+          } else {
+            SYM_NR_DISPATCH(nr, (e = launch_pdl(k_bgather<T, V, NR>, dim3(g, nb), THREADS, 0, st, d.sn, d.rows,
+                                                d.tasks, Lx, y, n, r0, L.off, bt)));
+          }
           break;
         case S_BSTEP:
+          if (nb > 1 && L.tb == SMALL_TB) {  // a batch's supernodes of <= SMALL_TILE columns
+            SYM_NR_DISPATCH(nr, (e = launch_pdl(k_dstep_w<T, V, NR, true>, dim3(g, (nb + WT_WARPS - 1) / WT_WARPS),
+                                                32 * WT_WARPS, 0, st, d.sn, d.tasks, Linv, y, n, r0, L.off,
+                                                (int32_t)nb, bt)));
+            break;
+          }
           if (L.cluster == 4) {
             SYM_NR_DISPATCH(nr, (e = launch_step_c(k_step_c<T, V, NR, false>, dim3(4 * g, nb), st, d.sn, d.tasks, Lx,
                                                    Linv, y, n, r0, L.off, bt)));

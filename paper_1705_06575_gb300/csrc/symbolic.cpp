@@ -743,6 +743,19 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
   // Solve schedules. Forward, per level: S_FSUM (columns subtract what their descendants
   // pushed), S_FSTEP per column tile, S_FPUSH (the level's solved supernodes push their products
   // to the rows below their diagonal blocks).
+  // A level whose supernodes all have at most SMALL_TILE columns marks its sum, push and gather
+  // launches tb = SMALL_TILE: batches run them one warp per (task, matrix).
+  auto small_level = [&](int32_t l) {
+    for (int32_t t = P.levelptr[l]; t < P.levelptr[l + 1]; ++t)
+      if (P.snodes[P.levellist[t]].ncols > SMALL_TILE) return false;
+    return true;
+  };
+  auto push_solve = [&](std::vector<Launch> &list, int32_t kind, int32_t l, int64_t off) {
+    if ((int64_t)P.tasks.size() <= off) return;
+    Launch L{kind, l, off, (int64_t)P.tasks.size() - off};
+    if (small_level(l)) L.tb = SMALL_TILE;
+    list.push_back(L);
+  };
   for (int32_t l = 0; l < nlev; ++l) {
     int64_t off = (int64_t)P.tasks.size();
     int32_t maxcb = 0;
@@ -753,7 +766,7 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
       if (P.contrib_ptr[sj.first + sj.ncols] > P.contrib_ptr[sj.first])
         for (int32_t cb = 0; cb * 256 < sj.ncols; ++cb) P.tasks.push_back({J, cb, 0, 0});
     }
-    if ((int64_t)P.tasks.size() > off) P.fwd_launches.push_back({S_FSUM, l, off, (int64_t)P.tasks.size() - off});
+    push_solve(P.fwd_launches, S_FSUM, l, off);
     // Supernodes of more than SMALL_TILE columns: cluster steps s = -1 .. ncb - 2, tasks {J, i, s}
     // (cluster = 4): i = s + 1 applies the solved tile s and solves tile i, i > s + 1 applies it.
     for (int32_t s = -1; s + 1 < maxcb; ++s) {
@@ -794,7 +807,7 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
       for (int32_t ch = 0; ch * SOLVE_CW < sj.ncols; ++ch)
         for (int32_t i = sj.ncb; i < nrb; ++i) P.tasks.push_back({J, i, ch, 0});
     }
-    if ((int64_t)P.tasks.size() > off) P.fwd_launches.push_back({S_FPUSH, l, off, (int64_t)P.tasks.size() - off});
+    push_solve(P.fwd_launches, S_FPUSH, l, off);
   }
   for (int32_t l = nlev - 1; l >= 0; --l) {
     int64_t off = (int64_t)P.tasks.size();
@@ -806,7 +819,7 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
       if (sj.nrows > sj.ncols)
         for (int32_t sl = 0; sl * SOLVE_BG < sj.ncols; ++sl) P.tasks.push_back({J, sl, 0, 0});
     }
-    if ((int64_t)P.tasks.size() > off) P.bwd_launches.push_back({S_BGATHER, l, off, (int64_t)P.tasks.size() - off});
+    push_solve(P.bwd_launches, S_BGATHER, l, off);
     // Supernodes of more than SMALL_TILE columns: cluster steps s = ncb .. 1, tasks {J, i, s}
     // (cluster = 4): i = s - 1 applies the solved tile s (s < ncb) and solves tile i, i < s - 1
     // applies it.

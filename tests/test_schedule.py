@@ -504,3 +504,46 @@ def test_small_tile_launches_fit_their_kernels(maker):
                     assert ts <= 32
     if M.n >= 4096:
         assert small_seen > 0  # the grids exercise the small-tile forms
+
+
+@pytest.mark.parametrize("maker", [
+    lambda: w.dd2d9(128, np.random.default_rng(2000)),                       # the batched pattern
+    lambda: w.conduct3d(16, np.random.default_rng(6), "star"),
+    lambda: w.random_spd_pattern(300, 0.02, np.random.default_rng(7)),
+])
+def test_small_solve_launches_fit_the_warp_forms(maker):
+    """Solve launches marked tb = 32 (run one warp per task and matrix in batches) hold only
+    supernodes of at most 32 columns: a sum task covers all of its supernode's columns with one
+    lane per column, a push task one row tile (<= 64 rows) and one column chunk, a gather task
+    one slice, and a step task is the whole one-tile diagonal block, {J, 0, 0, 0}. A level with a
+    wider supernode marks none of its sum, push and gather launches."""
+    M = maker()
+    s = S.Solver(M.n, M.Ap, M.Ai, M.perm, host_only=True)
+    sc = Sched(s)
+    level = s.export("level")
+    seen = 0
+    for key in ("fwd_launches", "bwd_launches"):
+        for (kind, off, count, _, _), tb in zip(sc.launches[key], sc.tb[key]):
+            kind, off, count, tb = int(kind), int(off), int(count), int(tb)
+            js = [int(sc.tasks[t][0]) for t in range(off, off + count)]
+            if kind in (S_FSUM, S_FPUSH, S_BGATHER):
+                lv = {int(level[j]) for j in js}
+                assert len(lv) == 1
+                wide = [j for j in np.where(level == lv.pop())[0] if sc.J(j)[1] > 32]
+                assert tb == (0 if wide else 32)
+            if tb != 32:
+                continue
+            seen += 1
+            for t in range(off, off + count):
+                j, a, b, c = (int(v) for v in sc.tasks[t])
+                _, nc, nr, ncb = sc.J(j)
+                assert nc <= 32 and ncb == 1
+                if kind in (S_FSTEP, S_BSTEP):
+                    assert (a, b, c) == (0, 0, 0)
+                elif kind == S_FSUM:
+                    assert a == 0
+                elif kind == S_FPUSH:
+                    assert a >= ncb and b == 0 and 0 < sc.row_len(j, a) <= NB
+                elif kind == S_BGATHER:
+                    assert a * BG < nc and nr > nc
+    assert seen > 0
