@@ -201,7 +201,7 @@ int sym_solve_batch(sym_handle h, int32_t nbatch, int32_t nrhs, const double *B,
  * sym_factor), every factor launch that has two kernel forms is timed in both with CUDA events
  * over reps kernel-by-kernel factorizations of the given values, and the faster form is stored
  * in the plan for every later factorization of the handle (the captured graphs are rebuilt).
- * Forms: in a batch, small-tile updates, POTRF and TRTRI run one warp per (tile, matrix), four
+ * Forms: in a batch, small-tile updates, POTRF, TRSM and TRTRI run one warp per (tile, matrix), four
  * matrices per CTA, or one CTA per tile and matrix, and FP64 updates of full tiles one CTA per
  * tile and matrix or one warp per (tile, matrix) updating the tile in global memory; for one matrix, FP64 updates of tiles with
  * many entries run on a thread-block cluster per tile or one CTA per tile, and small-tile POTRF

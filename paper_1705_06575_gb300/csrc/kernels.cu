@@ -1708,6 +1708,70 @@ __global__ void __launch_bounds__(32 * WT_WARPS) k_update_wg(const SNode *__rest
   }
 }
 
+// TRSM of a batch's narrow tiles (ts <= SMALL_TILE columns, <= NB rows): one warp per (tile,
+// matrix), four matrices per CTA, each warp's L_ss and 32-row chunk of the tile in its own shared
+// memory. Within a chunk the rows are spread over 32 / rows column groups as in k_trsm and each
+// element sees k_trsm's operations in the same order (bit-identical); warp barriers only.
+template <typename T>
+constexpr size_t trsm_w_smem() { return (size_t)WT_WARPS * sizeof(T) * (2 * SMALL_TILE * (SMALL_TILE + 1) + SMALL_TILE); }
+
+template <typename T>
+__global__ void __launch_bounds__(32 * WT_WARPS) k_trsm_w(const SNode *__restrict__ sn, const Int4 *__restrict__ tasks,
+                                                          T *__restrict__ Lx, int64_t toff, int32_t nmat,
+                                                          const Batch bt) {
+  constexpr int TW = SMALL_TILE, PW = 2 * TW * (TW + 1) + TW;  // per warp: Ls, X, dinv
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int32_t mat = blockIdx.y * WT_WARPS + w;
+  if (mat >= nmat) return;  // warp-uniform; only warp-level synchronization below
+  T(*Ls)[TW + 1] = reinterpret_cast<T(*)[TW + 1]>(reinterpret_cast<T *>(smem_raw) + w * PW);  // [col][row]
+  T(*X)[TW + 1] = Ls + TW;                                                                    // [col][row]
+  T *dinv = reinterpret_cast<T *>(X + TW);
+  Lx += (int64_t)mat * bt.lx;
+  const Int4 t = tasks[toff + blockIdx.x];
+  const SNode sj = sn[t.a];
+  const int i = t.b, s = t.c;
+  const int ts = min(TW, sj.ncols - s * NB);
+  int64_t rb = d_row_tile_base(i, sj.ncols, sj.ncb);
+  int tm = d_row_tile_rows(i, sj.ncols, sj.nrows, sj.ncb);
+  const int half = t.d >> 16;  // 0: whole tile; 1, 2: its first or second 32 rows
+  if (half) {
+    rb += (half - 1) * (NB / 2);
+    tm = max(0, min(NB / 2, tm - (half - 1) * (NB / 2)));
+  }
+  const T *D = Lx + sj.lx + (int64_t)(s * NB) * sj.nrows + s * NB;
+  for (int idx = lane; idx < ts * ts; idx += 32) {
+    const int r = idx % ts, c = idx / ts;
+    if (r >= c) Ls[c][r] = D[(int64_t)c * sj.nrows + r];
+  }
+  __syncwarp();
+  if (lane < ts) dinv[lane] = T(1) / Ls[lane][lane];
+  for (int r0 = 0; r0 < tm; r0 += 32) {
+    const int cm = min(32, tm - r0);  // rows of this chunk
+    T *B = Lx + sj.lx + (int64_t)(s * NB) * sj.nrows + rb + r0;
+    __syncwarp();
+    for (int idx = lane; idx < cm * ts; idx += 32) {
+      const int r = idx % cm, c = idx / cm;
+      X[c][r] = B[(int64_t)c * sj.nrows + r];
+    }
+    __syncwarp();
+    const int GR = 32 / cm, r = lane % cm, g = lane / cm;  // g >= GR: idle
+    for (int c = 0; c < ts; ++c) {
+      if (g < GR) {
+        const T xc = X[c][r] * dinv[c];  // X(r, c) is final once columns < c are applied
+        for (int cc = c + 1 + g; cc < ts; cc += GR) X[cc][r] = fma(-xc, Ls[c][cc], X[cc][r]);
+      }
+      __syncwarp();
+      if (g == 0) X[c][r] *= dinv[c];
+    }
+    __syncwarp();
+    for (int idx = lane; idx < cm * ts; idx += 32) {
+      const int rr = idx % cm, c = idx / cm;
+      B[(int64_t)c * sj.nrows + rr] = X[c][rr];
+    }
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(32 * WT_WARPS) k_potrf_w(const SNode *__restrict__ sn, const Int4 *__restrict__ tasks,
                                                            int64_t ntask, T *__restrict__ Lx, long long *status,
@@ -2096,6 +2160,8 @@ cudaError_t prepare_factor() {
   e = cudaFuncSetAttribute(k_trsm<T, SMALL_TB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)trsm_smem<T, SMALL_TB>());
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_trsm_w<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_w_smem<T>());
+  if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_trtri<T, SMALL_TB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)trtri_smem<SMALL_TB>());
   if (e != cudaSuccess) return e;
@@ -2175,7 +2241,7 @@ cudaError_t prepare_solve() {
 bool factor_launch_has_alternative(const Launch &L, int32_t nbatch, bool fp64) {
   const bool small = L.tb == SMALL_TB;
   if (nbatch > 1)  // one warp per (tile, matrix) against one CTA per tile and matrix
-    return (small && (L.kind == K_UPDATE || L.kind == K_POTRF || L.kind == K_TRTRI)) ||
+    return (small && (L.kind == K_UPDATE || L.kind == K_POTRF || L.kind == K_TRTRI || L.kind == K_TRSM)) ||
            (fp64 && !small && L.kind == K_UPDATE);
   // one matrix: a clustered FP64 update against one CTA per tile; small-tile POTRF and TRTRI
   // with one CTA per tile against one warp per tile
@@ -2261,8 +2327,12 @@ cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, co
         break;
       case K_TRSM:
         // (a warp-per-tile form with the column pairs mapped flat onto the lanes made the
-        // 512 x 128^2 batch's TRSM slower, 11.0 -> 16.3 ms: its tiles have enough rows)
-        if (small)
+        // 512 x 128^2 batch's TRSM slower, 11.0 -> 16.3 ms: its tiles have enough rows; the
+        // warp-per-(tile, matrix) form is the autotuner's alternative)
+        if (small && nb > 1 && alt)
+          e = launch_prio(k_trsm_w<T>, dim3(g, (nb + WT_WARPS - 1) / WT_WARPS), 32 * WT_WARPS, trsm_w_smem<T>(), s,
+                          prio, d.sn, d.tasks, Lx, L.off, (int32_t)nb, bt);
+        else if (small)
           e = launch_prio(k_trsm<T, SMALL_TB>, dim3(g, nb), TS, trsm_smem<T, SMALL_TB>(), s, prio, d.sn, d.tasks, Lx,
                           L.off, bt);
         else if constexpr (std::is_same<T, float>::value)  // the tile in registers

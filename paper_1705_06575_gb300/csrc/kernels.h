@@ -86,8 +86,8 @@ cudaError_t launch_update_tc(dim3 grid, cudaStream_t st, int prio, const DevPlan
                              const Batch &bt, long long *status);
 
 // Whether a factor launch has a second kernel form (the autotuner times both). A batch
-// (nbatch > 1): small-tile updates, POTRF and TRTRI, one warp per (tile, matrix) or one CTA per
-// tile and matrix; FP64 updates of full tiles, one CTA per tile and matrix or one warp per
+// (nbatch > 1): small-tile updates, POTRF, TRSM and TRTRI, one warp per (tile, matrix) or one
+// CTA per tile and matrix; FP64 updates of full tiles, one CTA per tile and matrix or one warp per
 // (tile, matrix) working in global memory (the default of each is DevPlan::batch_warp; the
 // alternative is the other). One matrix: clustered FP64 updates or one CTA per tile; small-tile POTRF and
 // TRTRI, one CTA or one warp per tile. fp64: the factor's precision (FP32 updates have no
