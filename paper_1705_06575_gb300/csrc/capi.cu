@@ -53,6 +53,7 @@ struct sym_handle_s {
   bool prepared = false;
   bool solve_prepared = false;
   cudaStream_t capture_stream = nullptr;
+  sym::PrecondGraph pgraph;       // the FP32 preconditioner of the refined solve, as a graph
   cudaGraphExec_t fgraph = nullptr;
   const double *fgraph_ax = nullptr;
   cudaGraphExec_t sgraph = nullptr;
@@ -166,6 +167,7 @@ void release_device(sym_handle_s *h) {
   for (cudaEvent_t e : h->events) cudaEventDestroy(e);
   if (h->fgraph) cudaGraphExecDestroy(h->fgraph);
   if (h->sgraph) cudaGraphExecDestroy(h->sgraph);
+  sym::precond_graph_reset(h->pgraph);
   if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
   void *ptrs[] = {h->d_sn, h->d_rows, h->d_rel, h->d_amap, h->d_updt, h->d_upde, h->d_tasks,
                   h->d_perm, h->d_Lx, h->d_status, h->d_y, h->d_stage, h->d_cptr, h->d_contrib, h->d_t};
@@ -243,6 +245,7 @@ void drop_graphs(sym_handle_s *h) {
   if (h->sgraph) cudaGraphExecDestroy(h->sgraph);
   h->fgraph = nullptr;
   h->sgraph = nullptr;
+  sym::precond_graph_reset(h->pgraph);
 }
 
 // Room for the factors of nbatch matrices (panels, diagonal inverses, pivot status and, for the
@@ -704,7 +707,14 @@ int solve_impl(sym_handle h, int32_t nbatch, int32_t nrhs, const double *B, int6
         rc = ensure_rwork(h, sym::refine_work_doubles(n, nc));
         if (rc) return rc;
         sym::RefineResult res;
-        if (sym::refine_solve(refine_ctx(h, b), nc, B + b * bstride + (int64_t)c0 * ldb, ldb,
+        sym::RefineCtx ctx = refine_ctx(h, b);
+        if (nbatch == 1 && h->use_graphs) {  // (a batch's matrices would each need their own graph)
+          rc = ensure_capture_stream(h);
+          if (rc) return rc;
+          ctx.pgraph = &h->pgraph;
+          ctx.capture = h->capture_stream;
+        }
+        if (sym::refine_solve(ctx, nc, B + b * bstride + (int64_t)c0 * ldb, ldb,
                               X + b * xstride + (int64_t)c0 * ldx, ldx, h->refine_tol, h->refine_max_iter, h->h_eta,
                               &res, h->stream) != 0)
           return cuda_fail(cudaGetLastError(), "refinement");

@@ -10,6 +10,16 @@
 
 namespace sym {
 
+// One application of the FP32 preconditioner (solves with the FP32 factor, ~500 short kernels)
+// captured as a CUDA graph and replayed at every CG iteration; owned by the handle, rebuilt when
+// a key changes.
+struct PrecondGraph {
+  cudaGraphExec_t exec = nullptr;
+  const void *key[4] = {nullptr, nullptr, nullptr, nullptr};  // input, output, FP32 work, factor
+  int nrhs = 0;
+};
+void precond_graph_reset(PrecondGraph &g);
+
 struct RefineCtx {
   const DevPlan *dp = nullptr;
   const std::vector<Launch> *fwd = nullptr;
@@ -25,6 +35,8 @@ struct RefineCtx {
                                   // factor graph references it, so it never moves
   double *work = nullptr;         // at least refine_work_doubles(n, nrhs) doubles
   int64_t n = 0;
+  PrecondGraph *pgraph = nullptr;  // non-null: replay the preconditioner as a graph, captured on
+  cudaStream_t capture = nullptr;  // this (non-default) stream
 };
 
 struct RefineResult {
