@@ -1,7 +1,7 @@
 """Profiling driver: factor one named workload and report where the time goes.
 
     python -m paper_1705_06575_gb300.profile_factor --workload conduct3d7_48 [--one-stream]
-        [--no-graphs] [--mixed [--no-tensor-cores]] [--levels] [--repeat N]
+        [--no-graphs] [--mixed [--no-tensor-cores]] [--levels] [--repeat N] [--batch B]
 
 Without --levels it factors the matrix once per repeat (after one warm-up factorization) and
 exits: a fixed, short command to run under a profiler. With --one-stream --no-graphs every launch
@@ -22,7 +22,7 @@ import sys
 import numpy as np
 
 from . import (SYM_FLAG_NO_GRAPHS, SYM_FLAG_NO_TENSOR_CORES, SYM_FLAG_ONE_STREAM, SYM_PROFILE_OFF,
-               SYM_PROFILE_ON, SYM_PROFILE_RESET, Solver, sym_profile, sym_profile_launches)
+               SYM_PROFILE_ON, SYM_PROFILE_RESET, Solver, sym_factor_batch, sym_profile, sym_profile_launches)
 
 KIND_NAMES = {1: "update", 2: "potrf", 3: "trsm", 4: "gemm", 5: "trtri"}
 
@@ -73,11 +73,23 @@ def main(argv=None):
     ap.add_argument("--no-tensor-cores", action="store_true", help="FP32 updates on the SIMT pipes")
     ap.add_argument("--levels", action="store_true")
     ap.add_argument("--repeat", type=int, default=1)
+    ap.add_argument("--batch", type=int, default=0,
+                    help="factor this many value sets of the workload's pattern together (sym_factor_batch)")
     args = ap.parse_args(argv)
     M = w.cfg(args.workload)
     flags = ((SYM_FLAG_ONE_STREAM if args.one_stream else 0) | (SYM_FLAG_NO_GRAPHS if args.no_graphs else 0) |
              (SYM_FLAG_NO_TENSOR_CORES if args.no_tensor_cores else 0))
     s = Solver(M.n, M.Ap, M.Ai, M.perm, flags=flags, precision="mixed" if args.mixed else None)
+    if args.batch > 1:  # value sets drawn like the workload's (same pattern, seeds 0..batch-1)
+        vals = np.stack([w.cfg(args.workload, b).Ax for b in range(args.batch)])
+        V = torch.from_numpy(vals).cuda()
+        for _ in range(args.repeat + 1):
+            sym_factor_batch(s.h, args.batch, V, M.nnz)
+        torch.cuda.synchronize()
+        print(json.dumps({"workload": args.workload, "batch": args.batch, "factorizations": args.repeat + 1,
+                          "status": "ok"}))
+        s.close()
+        return 0
     Ax = torch.from_numpy(M.Ax).cuda()
     s.factor(Ax)  # warm-up (and graph capture unless --no-graphs)
     torch.cuda.synchronize()
