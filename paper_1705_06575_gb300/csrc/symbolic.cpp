@@ -677,6 +677,30 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
           if (s < sj.ncb) P.tasks.push_back({J, s, s, s});
         });
       };
+      // Inverses of diagonal tiles (the solve uses them) on the auxiliary stream, after launch
+      // `wait` of the main stream: column tiles c0 <= c < c1 of the level's supernodes, full-size
+      // tiles then tiles of <= SMALL_TILE columns. The next level does not wait for them; the
+      // factorization ends with both streams joined.
+      auto trtri = [&](int32_t c0, int32_t c1, int32_t wait) {
+        int32_t first = -1;
+        for (int part = 0; part < 2; ++part) {
+          const int64_t o = (int64_t)P.tasks.size();
+          for (int32_t t = P.levelptr[l]; t < P.levelptr[l + 1]; ++t) {
+            const int32_t J = P.levellist[t];
+            for (int32_t c = c0; c < std::min(c1, P.snodes[J].ncb); ++c)
+              if ((std::min<int32_t>(NB, P.snodes[J].ncols - c * NB) <= SMALL_TILE) == (part == 1))
+                P.tasks.push_back({J, c, c, c});
+          }
+          if ((int64_t)P.tasks.size() > o) {
+            Launch T{K_TRTRI, l, o, (int64_t)P.tasks.size() - o};
+            T.stream = 1;
+            T.wait = first < 0 ? wait : -1;
+            T.tb = part == 1 ? SMALL_TILE : 0;
+            P.factor_launches.push_back(T);
+            first = (int32_t)P.factor_launches.size() - 1;
+          }
+        }
+      };
       auto trsm = [&](int32_t s) {
         return emit(K_TRSM, s, 0, -1, [&](int32_t J, const SNode &sj, int32_t nrb) {
           if (s < sj.ncb)
@@ -696,6 +720,9 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
             pending_join = -1;
           }
           note(idx);
+          // the last two column tiles' inverses start as soon as their POTRF is done (no
+          // trailing-update launch of this level follows them on the auxiliary stream)
+          if (maxcb <= 2) trtri(0, 1, idx);
         }
         note(trsm(0));
         int32_t rest_prev = -1;
@@ -708,35 +735,16 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
             if (s + 1 < sj.ncb)
               for (int32_t i = s + 1; i < nrb; ++i) P.tasks.push_back({J, i, s + 1, s});
           }));
-          note(potrf(s + 1));
+          const int32_t pidx = potrf(s + 1);
+          note(pidx);
+          if (s + 3 >= maxcb) trtri(s + 1, s + 2, pidx);
           note(trsm(s + 1));
           if (rest_idx >= 0) rest_prev = rest_idx;
         }
         // join: the next launch on the main stream waits for the last auxiliary launch
         pending_join = rest_prev;
-      }
-    }
-  }
-  // Inverses of all diagonal tiles, in one launch after the factorization (the solve uses them).
-  // It joins the auxiliary stream's last launch.
-  {
-    int32_t final_join = -1;
-    for (const Launch &L : P.factor_launches)
-      if (L.stream == 1) final_join = (int32_t)(&L - P.factor_launches.data());
-    const int64_t off = (int64_t)P.tasks.size();
-    (void)off;
-    for (int part = 0; part < 2; ++part) {  // full-size tiles, then tiles of <= SMALL_TILE columns
-      const int64_t o = (int64_t)P.tasks.size();
-      for (int32_t J = 0; J < ns; ++J)
-        for (int32_t t = 0; t < P.snodes[J].ncb; ++t)
-          if ((std::min<int32_t>(NB, P.snodes[J].ncols - t * NB) <= SMALL_TILE) == (part == 1))
-            P.tasks.push_back({J, t, t, t});
-      if ((int64_t)P.tasks.size() > o) {
-        Launch T{K_TRTRI, nlev, o, (int64_t)P.tasks.size() - o};
-        T.wait = final_join;
-        final_join = -1;
-        T.tb = part == 1 ? SMALL_TILE : 0;
-        P.factor_launches.push_back(T);
+        // the other column tiles' inverses once the level's panels are final
+        if (maxcb > 2) trtri(0, maxcb - 2, last_main);
       }
     }
   }
