@@ -453,7 +453,11 @@ def main_sn(argv=None):
     """Per-supernode rules: collect per-supernode times on training patterns of the suite, train
     one network per arm, evaluate on held-out patterns (disjoint seeds) by measured time.
 
-    python -m paper_1705_06575_gb300.costmodel sn --train N --holdout H [--arms fp64,fp32] --out DIR"""
+    python -m paper_1705_06575_gb300.costmodel sn --train N --holdout H [--arms fp64,fp32] --out DIR
+    python -m paper_1705_06575_gb300.costmodel sn --eval-only --holdout H --out DIR
+
+    --eval-only evaluates the packaged networks (pretrained_sn) on the held-out patterns instead
+    of training new ones (the training suite is not built)."""
     import argparse
     import sys
 
@@ -473,11 +477,12 @@ def main_sn(argv=None):
     ap.add_argument("--max-rows", type=int, default=200000)
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--out", default="costmodel_out")
+    ap.add_argument("--eval-only", action="store_true")
     args = ap.parse_args(argv)
     os.makedirs(args.out, exist_ok=True)
     log = lambda m: print(m, flush=True)
     t0 = time.time()
-    train, tr_est, tr_exact = suite5(args.train, args.seed, args.budget, log)
+    train, tr_est, tr_exact = suite5(0 if args.eval_only else args.train, args.seed, args.budget, log)
     hold, ho_est, ho_exact = suite5(args.holdout, args.seed + 1_000_000, args.budget, log)
     result = {"suite": "2D 5/9-point and 3D 7/27-point grids of sides 32..128, Erdos-Renyi n 50k..200k, degree 4..16",
               "flop_budget": args.budget,
@@ -486,14 +491,18 @@ def main_sn(argv=None):
               "holdout_skipped_analysis": ho_exact, "arms": {}}
     for arm in args.arms.split(","):
         prec = SYM_PREC_FP64 if arm == "fp64" else SYM_PREC_MIXED
-        X, Y, _ = collect_sn(train, torch, prec, flop_budget=args.budget, max_rows=args.max_rows,
-                             log=lambda m: None)
-        model, l0, l1 = CostModel.fit(X, Y, torch, steps=args.steps)
-        path = os.path.join(args.out, f"costmodel_sn_{arm}.json")
-        model.save(path)
+        if args.eval_only:
+            model = pretrained_sn(arm)
+            extra = {"weights": os.path.basename(WEIGHTS_SN[arm])}
+        else:
+            X, Y, _ = collect_sn(train, torch, prec, flop_budget=args.budget, max_rows=args.max_rows,
+                                 log=lambda m: None)
+            model, l0, l1 = CostModel.fit(X, Y, torch, steps=args.steps)
+            model.save(os.path.join(args.out, f"costmodel_sn_{arm}.json"))
+            extra = {"rows": int(X.shape[0]), "loss_initial": l0, "loss_final": l1}
         nh = len(hold) if arm == "fp64" or args.holdout_fp32 is None else min(len(hold), args.holdout_fp32)
         ev, rows = evaluate_sn(model, hold[:nh], torch, prec, flop_budget=args.budget, log=log)
-        ev.update({"rows": int(X.shape[0]), "loss_initial": l0, "loss_final": l1})
+        ev.update(extra)
         result["arms"][arm] = ev
         with open(os.path.join(args.out, f"eval_sn_{arm}_rows.json"), "w") as f:
             json.dump(rows, f)
