@@ -767,18 +767,29 @@ __global__ void __launch_bounds__(PR_THREADS) k_potrf_r(const SNode *__restrict_
   }
 }
 
-// (c'') FP32 panel TRSM with the tile in registers: thread (r, g) owns row r of the tile and the
-// columns g, g + 4, ... (the oldest unfinished one in x[0]). Step c, one barrier: every thread
-// applies the solved column c - 1 to its columns right of it, and the owners of column c publish
-// X(:, c) = B(:, c) / L_cc. Same operations in the same order as k_trsm (bit-identical), without
-// a shared-memory round trip per update.
+// (c'') Panel TRSM of full tiles with the tile in registers: thread (r, g) owns row r of the tile
+// and the columns g, g + 4, ... (the oldest unfinished one in x[0]). Step c, one barrier: every
+// thread applies the solved column c - 1 to its columns right of it, and the owners of column c
+// publish X(:, c) = B(:, c) / L_cc. Same operations in the same order as k_trsm (bit-identical),
+// without a shared-memory round trip per update. The number of columns a thread still updates
+// selects a fully unrolled form, so no multiply-add is issued for a finished column (a predicated
+// FP64 instruction would still take its pipe slot), and warps whose rows are all past the tile
+// skip the arithmetic.
+template <int N, typename T>
+__device__ __forceinline__ void trsm_axpy(T (&x)[NB / 4], T xp, const T *lrow, int cn) {
+#pragma unroll
+  for (int u = 0; u < N; ++u) x[u] = fma(-xp, lrow[cn + 4 * u], x[u]);
+}
+
+template <typename T>
 __global__ void __launch_bounds__(THREADS) k_trsm_r(const SNode *__restrict__ sn, const Int4 *__restrict__ tasks,
-                                                    float *__restrict__ Lx, int64_t toff, const Batch bt) {
+                                                    T *__restrict__ Lx, int64_t toff, const Batch bt) {
   static_assert(THREADS == 4 * NB, "four column groups of NB rows");
   Lx += blockIdx.y * bt.lx;
-  __shared__ float Ls[NB][NB + 1];  // [col][row], lower triangle of L_ss
-  __shared__ float xs[NB][NB + 1];  // [col][row]: solved columns
-  __shared__ float dinv[NB];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T(*Ls)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smem_raw);  // [col][row], lower triangle of L_ss
+  T(*xs)[NB + 1] = Ls + NB;                                    // [col][row]: solved columns
+  T *dinv = reinterpret_cast<T *>(xs + NB);
   const Int4 t = tasks[toff + blockIdx.x];
   const SNode sj = sn[t.a];
   const int i = t.b, s = t.c;
@@ -791,37 +802,45 @@ __global__ void __launch_bounds__(THREADS) k_trsm_r(const SNode *__restrict__ sn
     tm = max(0, min(NB / 2, tm - (half - 1) * (NB / 2)));
   }
   const int64_t ld = sj.nrows;
-  const float *D = Lx + sj.lx + (int64_t)(s * NB) * ld + s * NB;
-  float *B = Lx + sj.lx + (int64_t)(s * NB) * ld + rb;
+  const T *D = Lx + sj.lx + (int64_t)(s * NB) * ld + s * NB;
+  T *B = Lx + sj.lx + (int64_t)(s * NB) * ld + rb;
   const int tid = threadIdx.x, r = tid & (NB - 1), g = tid >> 6;
+  const bool live = (r & ~31) < tm;  // warp-uniform: some row of this warp is in the tile
   for (int idx = tid; idx < ts * ts; idx += THREADS) {
     const int rr = idx % ts, c = idx / ts;
     if (rr >= c) Ls[c][rr] = D[(int64_t)c * ld + rr];
   }
-  float x[NB / 4];
+  T x[NB / 4];
   int cn = g;  // the column in x[0]
 #pragma unroll
   for (int u = 0; u < NB / 4; ++u) {
     const int cc = g + 4 * u;
-    x[u] = (r < tm && cc < ts) ? B[(int64_t)cc * ld + r] : 0.f;
+    x[u] = (r < tm && cc < ts) ? B[(int64_t)cc * ld + r] : T(0);
   }
   __syncthreads();
-  if (tid < ts) dinv[tid] = 1.f / Ls[tid][tid];
+  if (tid < ts) dinv[tid] = T(1) / Ls[tid][tid];
   __syncthreads();
   for (int c = 0; c < ts; ++c) {
-    if (c > 0) {
-      const float xp = xs[c - 1][r];
-#pragma unroll
-      for (int u = 0; u < NB / 4; ++u) {
-        const int cc = cn + 4 * u;
-        if (cc < ts) x[u] = fma(-xp, Ls[c - 1][cc], x[u]);
+    if (c > 0 && live && cn < ts) {
+      const T xp = xs[c - 1][r];
+      const T *lrow = Ls[c - 1];
+#define SYM_CASE(N)                      \
+  case N:                                \
+    trsm_axpy<N>(x, xp, lrow, cn);       \
+    break;
+      switch ((ts - cn + 3) >> 2) {  // columns cn, cn + 4, ... below ts (1..16)
+        SYM_CASE(1) SYM_CASE(2) SYM_CASE(3) SYM_CASE(4) SYM_CASE(5) SYM_CASE(6) SYM_CASE(7) SYM_CASE(8)
+        SYM_CASE(9) SYM_CASE(10) SYM_CASE(11) SYM_CASE(12) SYM_CASE(13) SYM_CASE(14) SYM_CASE(15) SYM_CASE(16)
+        default:
+          break;
       }
+#undef SYM_CASE
     }
     if (cn == c) {  // uniform within a warp (its lanes share g)
       xs[c][r] = x[0] * dinv[c];
 #pragma unroll
       for (int u = 0; u < NB / 4 - 1; ++u) x[u] = x[u + 1];
-      x[NB / 4 - 1] = 0.f;
+      x[NB / 4 - 1] = T(0);
       cn += 4;
     }
     __syncthreads();
@@ -2154,7 +2173,7 @@ inline void trace_mark(LaunchTrace *tr, int32_t kind, cudaStream_t st) {
 
 template <typename T>
 cudaError_t prepare_factor() {
-  cudaError_t e = cudaFuncSetAttribute(k_trsm<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_trsm_r<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)trsm_smem<T, NB>());
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_trsm<T, SMALL_TB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -2335,10 +2354,8 @@ cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, co
         else if (small)
           e = launch_prio(k_trsm<T, SMALL_TB>, dim3(g, nb), TS, trsm_smem<T, SMALL_TB>(), s, prio, d.sn, d.tasks, Lx,
                           L.off, bt);
-        else if constexpr (std::is_same<T, float>::value)  // the tile in registers
-          e = launch_prio(k_trsm_r, dim3(g, nb), THREADS, 0, s, prio, d.sn, d.tasks, Lx, L.off, bt);
-        else
-          e = launch_prio(k_trsm<T, NB>, dim3(g, nb), THREADS, trsm_smem<T, NB>(), s, prio, d.sn, d.tasks, Lx, L.off,
+        else  // the tile in registers
+          e = launch_prio(k_trsm_r<T>, dim3(g, nb), THREADS, trsm_smem<T, NB>(), s, prio, d.sn, d.tasks, Lx, L.off,
                           bt);
         break;
       case K_GEMM:
