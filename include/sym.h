@@ -203,9 +203,10 @@ int sym_solve_batch(sym_handle h, int32_t nbatch, int32_t nrhs, const double *B,
  * in the plan for every later factorization of the handle (the captured graphs are rebuilt).
  * Forms: in a batch, small-tile updates, POTRF, TRSM and TRTRI run one warp per (tile, matrix), four
  * matrices per CTA, or one CTA per tile and matrix, and FP64 updates of full tiles one CTA per
- * tile and matrix or one warp per (tile, matrix) updating the tile in global memory; for one matrix, FP64 updates of tiles with
- * many entries run on a thread-block cluster per tile or one CTA per tile, and small-tile POTRF
- * and TRTRI one CTA or one warp per tile. The
+ * tile and matrix or one warp per (tile, matrix) updating the tile in global memory; for one
+ * matrix, FP64 updates of tiles with many entries run on a thread-block cluster per tile or one
+ * CTA per tile, FP32 updates of full tiles on the tensor cores or the SIMT pipes, and small-tile
+ * POTRF and TRTRI one CTA or one warp per tile. The
  * per-kernel profile totals are left as they were. *tuned: launches with two forms; *changed:
  * launches now on their second form (either pointer may be NULL). Errors as sym_factor_batch,
  * and SYM_ERR_INVALID for reps outside 1..100; the factor afterwards is that of the last run. */

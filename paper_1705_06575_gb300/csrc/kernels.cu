@@ -2262,9 +2262,11 @@ bool factor_launch_has_alternative(const Launch &L, int32_t nbatch, bool fp64) {
   if (nbatch > 1)  // one warp per (tile, matrix) against one CTA per tile and matrix
     return (small && (L.kind == K_UPDATE || L.kind == K_POTRF || L.kind == K_TRTRI || L.kind == K_TRSM)) ||
            (fp64 && !small && L.kind == K_UPDATE);
-  // one matrix: a clustered FP64 update against one CTA per tile; small-tile POTRF and TRTRI
-  // with one CTA per tile against one warp per tile
-  return (fp64 && !small && L.kind == K_UPDATE && L.cluster > 1) || (small && (L.kind == K_POTRF || L.kind == K_TRTRI));
+  // one matrix: a clustered FP64 update against one CTA per tile; FP32 full-tile updates on the
+  // tensor cores against the SIMT pipes; small-tile POTRF and TRTRI with one CTA per tile against
+  // one warp per tile
+  return (fp64 && !small && L.kind == K_UPDATE && L.cluster > 1) || (!fp64 && !small && L.kind == K_UPDATE) ||
+         (small && (L.kind == K_POTRF || L.kind == K_TRTRI));
 }
 
 template <typename T>
@@ -2302,9 +2304,9 @@ cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, co
         // FP64: flat element map (the FP64 pipe is the bound and every issued DFMA should be
         // useful); FP32: 4 x 8 register tiles (operand reuse matters at the FP32 rate)
         if constexpr (!std::is_same<T, double>::value) {
-          if (d.tensor_cores && !small)
+          if (d.tensor_cores && !small && !alt)  // (alt: the SIMT form, the autotuner's choice)
             e = launch_update_tc(dim3(g, nb), s, prio, d, Lx, L.off, bt, status);
-          else if (alt)  // a batch's small tiles: one warp per (tile, matrix)
+          else if (alt && small)  // a batch's small tiles: one warp per (tile, matrix)
             e = launch_prio(k_update_wb<T>, dim3(g, (nb + WT_WARPS - 1) / WT_WARPS), 32 * WT_WARPS, 0, s, prio,
                             d.sn, d.upd_tasks, d.upd_entries, d.rel, Lx, L.off, (int32_t)nb, bt);
           else

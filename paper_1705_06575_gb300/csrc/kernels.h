@@ -89,9 +89,9 @@ cudaError_t launch_update_tc(dim3 grid, cudaStream_t st, int prio, const DevPlan
 // (nbatch > 1): small-tile updates, POTRF, TRSM and TRTRI, one warp per (tile, matrix) or one
 // CTA per tile and matrix; FP64 updates of full tiles, one CTA per tile and matrix or one warp per
 // (tile, matrix) working in global memory (the default of each is DevPlan::batch_warp; the
-// alternative is the other). One matrix: clustered FP64 updates or one CTA per tile; small-tile POTRF and
-// TRTRI, one CTA or one warp per tile. fp64: the factor's precision (FP32 updates have no
-// cluster form).
+// alternative is the other). One matrix: clustered FP64 updates or one CTA per tile; FP32
+// full-tile updates on the tensor cores or the SIMT pipes; small-tile POTRF and TRTRI, one CTA or
+// one warp per tile. fp64: the factor's precision.
 bool factor_launch_has_alternative(const Launch &L, int32_t nbatch, bool fp64);
 
 // Numeric factorization: scatter A into the zeroed panels, then run the launch schedule.
