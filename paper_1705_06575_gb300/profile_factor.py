@@ -1,7 +1,7 @@
 """Profiling driver: factor one named workload and report where the time goes.
 
     python -m paper_1705_06575_gb300.profile_factor --workload conduct3d7_48 [--one-stream]
-        [--no-graphs] [--mixed [--no-tensor-cores]] [--levels] [--repeat N] [--batch B]
+        [--no-graphs] [--mixed [--no-tensor-cores]] [--levels] [--repeat N] [--batch B] [--solve NRHS]
 
 Without --levels it factors the matrix once per repeat (after one warm-up factorization) and
 exits: a fixed, short command to run under a profiler. With --one-stream --no-graphs every launch
@@ -22,7 +22,8 @@ import sys
 import numpy as np
 
 from . import (SYM_FLAG_NO_GRAPHS, SYM_FLAG_NO_TENSOR_CORES, SYM_FLAG_ONE_STREAM, SYM_PROFILE_OFF,
-               SYM_PROFILE_ON, SYM_PROFILE_RESET, Solver, sym_factor_batch, sym_profile, sym_profile_launches)
+               SYM_PROFILE_ON, SYM_PROFILE_RESET, Solver, sym_factor_batch, sym_profile, sym_profile_launches,
+               sym_solve_multi)
 
 KIND_NAMES = {1: "update", 2: "potrf", 3: "trsm", 4: "gemm", 5: "trtri"}
 
@@ -75,6 +76,8 @@ def main(argv=None):
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--batch", type=int, default=0,
                     help="factor this many value sets of the workload's pattern together (sym_factor_batch)")
+    ap.add_argument("--solve", type=int, default=0,
+                    help="after the factorizations, solve with this many right-hand sides (repeat + 1 times)")
     args = ap.parse_args(argv)
     M = w.cfg(args.workload)
     flags = ((SYM_FLAG_ONE_STREAM if args.one_stream else 0) | (SYM_FLAG_NO_GRAPHS if args.no_graphs else 0) |
@@ -105,8 +108,15 @@ def main(argv=None):
     else:
         for _ in range(args.repeat):
             s.factor(Ax)
+        out = {"workload": args.workload, "factorizations": args.repeat + 1, "status": "ok"}
+        if args.solve > 0:
+            B = torch.from_numpy(np.ascontiguousarray(w.rhs(M.n, args.solve, np.random.default_rng(7)).T)).cuda()
+            X = torch.empty_like(B)
+            for _ in range(args.repeat + 1):
+                sym_solve_multi(s.h, args.solve, B, M.n, X, M.n)
+            out["solves"] = args.repeat + 1
         torch.cuda.synchronize()
-        print(json.dumps({"workload": args.workload, "factorizations": args.repeat + 1, "status": "ok"}))
+        print(json.dumps(out))
     s.close()
     return 0
 
