@@ -244,3 +244,28 @@ def test_pivot_ratio_per_matrix_of_a_batch(torch_cuda):
     assert bd1 and c1 == 23 and not bd2 and c2 == 23
     assert abs(r1 - sh / (vv + sh)) <= 1e-8 * r1
     assert abs(r2 - 0.8) <= 1e-6
+
+
+def test_autotune_mixed_precision(torch_cuda):
+    """The autotuner on an FP32 factor (tensor-core or SIMT updates of full tiles, one-CTA or
+    one-warp small-tile POTRF/TRTRI, per launch): whatever forms it keeps, the FP32 factor stays
+    within the FP32 forward-error bound of the oracle's, and the refined solve reaches 1e-12."""
+    torch = torch_cuda
+    import paper_1705_06575_gb300 as S
+    M = w.cfg("conduct3d7_48")
+    s = S.Solver(M.n, M.Ap, M.Ai, M.perm, precision="mixed")
+    s.set_refinement(1e-12, 100)
+    Ax = torch.from_numpy(M.Ax).cuda()
+    tuned, changed = S.sym_autotune(s.h, 1, Ax, M.nnz, 2)
+    assert tuned > 0 and 0 <= changed <= tuned
+    s.factor(Ax)
+    o = oracle.Oracle(M.n, M.Ap, M.Ai, M.perm)
+    kmax = 20000
+    assert o.factor(M.Ax, kmax) == 0
+    vals, outside = panels_on_pattern(exports(s), s.factor_panels(), o.Lp, o.Li)
+    cols = np.repeat(np.arange(M.n), np.diff(o.Lp))
+    sel = (cols < kmax) & (o.Li < kmax)
+    assert outside == 0.0
+    assert np.abs(vals[sel] - o.Lx[sel]).max() <= 5e-4 * np.abs(o.Lx[sel]).max()
+    B, X = solve_refined(torch, s, M, 2)
+    assert oracle.backward_error(M.n, M.Ap, M.Ai, M.Ax, B, X) <= REFINED_BERR
