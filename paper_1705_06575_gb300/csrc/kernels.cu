@@ -1353,7 +1353,8 @@ __global__ void __launch_bounds__(TileCfg<TB>::threads) k_fstep(const SNode *__r
 
 // Backward step of column tile s inside J (tasks {J, i, s}, s descending): CTAs i < s form
 // zs = L_ss^{-T} z_s and apply z_i -= L_si^T zs; the CTA i = s writes the solved z_{s+1} and,
-// for tile 0, the solved z_0 (the mirror image of the forward step).
+// for tile 0, the solved z_0 (the mirror image of the forward step). Launched for supernodes of
+// at most SMALL_TILE columns; wider ones take the cluster form (k_step_c).
 template <typename T, typename V, int TB>
 __global__ void __launch_bounds__(TileCfg<TB>::threads) k_bstep(const SNode *__restrict__ sn,
                                                                 const Int4 *__restrict__ tasks,
@@ -2252,8 +2253,6 @@ cudaError_t prepare_solve() {
   cudaError_t e = cudaFuncSetAttribute(k_fstep<T, V, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)step_smem<V, NB>());
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_bstep<T, V, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)step_smem<V, NB>());
-  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_fgather<T, V>, cudaFuncAttributeNonPortableClusterSizeAllowed, 0);
 }
 
@@ -2491,11 +2490,9 @@ cudaError_t run_sweeps(const DevPlan &d, const std::vector<Launch> &fwd, const s
                                                    Linv, y, n, r0, L.off, bt)));
             break;
           }
-          e = L.tb == SMALL_TB
-                  ? launch_pdl(k_bstep<T, V, SMALL_TB>, dim3(g, nb), TileCfg<SMALL_TB>::threads,
-                               step_smem<V, SMALL_TB>(), st, d.sn, d.tasks, Lx, Linv, y, n, r0, nr, L.off, bt)
-                  : launch_pdl(k_bstep<T, V, NB>, dim3(g, nb), THREADS, step_smem<V, NB>(), st, d.sn, d.tasks, Lx,
-                               Linv, y, n, r0, nr, L.off, bt);
+          if (L.tb != SMALL_TB) return cudaErrorInvalidValue;  // (wider supernodes: the cluster form)
+          e = launch_pdl(k_bstep<T, V, SMALL_TB>, dim3(g, nb), TileCfg<SMALL_TB>::threads, step_smem<V, SMALL_TB>(),
+                         st, d.sn, d.tasks, Lx, Linv, y, n, r0, nr, L.off, bt);
           break;
         default:
           return cudaErrorInvalidValue;

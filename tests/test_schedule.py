@@ -547,3 +547,20 @@ def test_small_solve_launches_fit_the_warp_forms(maker):
                 elif kind == S_BGATHER:
                     assert a * BG < nc and nr > nc
     assert seen > 0
+
+
+@pytest.mark.parametrize("maker", [
+    lambda: w.conduct3d(16, np.random.default_rng(6), "star"),
+    lambda: w.random_spd_pattern(300, 0.02, np.random.default_rng(7)),
+    lambda: w.dd2d9(128, np.random.default_rng(2000)),
+])
+def test_step_launches_have_a_kernel_form(maker):
+    """Every column-tile step of the plan's solve is either a cluster step (supernodes wider than
+    32 columns) or a one-tile step of the small form: the executor launches no other step form."""
+    M = maker()
+    s = S.Solver(M.n, M.Ap, M.Ai, M.perm, host_only=True)
+    sc = Sched(s)
+    for key in ("fwd_launches", "bwd_launches"):
+        for (kind, off, count, _, _), tb, cl in zip(sc.launches[key], sc.tb[key], sc.cluster[key]):
+            if int(kind) in (S_FSTEP, S_BSTEP):
+                assert int(cl) == 4 or int(tb) == 32
