@@ -513,6 +513,68 @@ def main_sn(argv=None):
     print(json.dumps(result), flush=True)
 
 
+WEIGHTS_PATTERN = {"fp32": os.path.join(os.path.dirname(os.path.abspath(__file__)), "costmodel_pattern_fp32.json")}
+
+
+def main_pattern(argv=None):
+    """Per-pattern preset choice for one arm, on the suite at its stated sizes: the network of
+    `features` (one row per preset) trained on measured graph times of every preset of the
+    training patterns, then judged on held-out patterns (disjoint seeds) by measured time.
+
+    python -m paper_1705_06575_gb300.costmodel pattern --arm fp32 --train N --holdout H --out DIR"""
+    import argparse
+    import sys
+
+    import torch
+
+    here = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, here)
+    from . import SYM_PREC_MIXED
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--arm", default="fp32", choices=["fp64", "fp32"])
+    ap.add_argument("--train", type=int, default=400)
+    ap.add_argument("--holdout", type=int, default=400)
+    ap.add_argument("--seed", type=int, default=50000)
+    ap.add_argument("--budget", type=float, default=4e10)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--out", default="costmodel_out")
+    args = ap.parse_args(argv)
+    os.makedirs(args.out, exist_ok=True)
+    log = lambda m: print(m, flush=True)
+    prec = SYM_PREC_FP64 if args.arm == "fp64" else SYM_PREC_MIXED
+    t0 = time.time()
+
+    def measure(mats):
+        X, Y, G = [], [], []
+        for gi, M in enumerate(mats):
+            F = plan_features(M)
+            t = [time_graph(M, torch, prec, opt=options(p)) for p in range(len(PRESETS))]
+            X.append(F)
+            Y.append(np.log(t))
+            G += [gi] * len(PRESETS)
+            log(f"{gi + 1}/{len(mats)} {M.name}: " + " ".join(f"{v:.3f}" for v in t))
+        return np.concatenate(X), np.concatenate(Y), np.asarray(G)
+
+    train, tr_est, tr_exact = suite5(args.train, args.seed, args.budget, log)
+    hold, ho_est, ho_exact = suite5(args.holdout, args.seed + 1_000_000, args.budget, log)
+    X, Y, _ = measure(train)
+    model, l0, l1 = CostModel.fit(X, Y, torch, steps=args.steps)
+    model.save(os.path.join(args.out, f"costmodel_pattern_{args.arm}.json"))
+    Xh, Yh, Gh = measure(hold)
+    ev = evaluate(model, Xh, Yh, Gh, torch)
+    gm = lambda a: float(np.exp(np.mean(np.log(a))))
+    T = np.exp(Yh).reshape(-1, len(PRESETS))
+    ev.update({"geomean_speedup_best_preset": gm(T[:, DEFAULT] / T.min(axis=1)),
+               "arm": args.arm, "train_patterns": len(train), "holdout_patterns": len(hold),
+               "train_skipped_estimate": tr_est, "train_skipped_analysis": tr_exact,
+               "holdout_skipped_estimate": ho_est, "holdout_skipped_analysis": ho_exact,
+               "flop_budget": args.budget, "loss_initial": l0, "loss_final": l1, "seconds": time.time() - t0})
+    with open(os.path.join(args.out, f"eval_pattern_{args.arm}.json"), "w") as f:
+        json.dump(ev, f, indent=1)
+    print(json.dumps(ev), flush=True)
+
+
 def main(argv=None):
     """Collect, train and evaluate: python -m paper_1705_06575_gb300.costmodel --patterns N --out DIR
     (`sn` as the first argument: the per-supernode rules, see main_sn)."""
@@ -520,6 +582,8 @@ def main(argv=None):
     argv = sys.argv[1:] if argv is None else argv
     if argv and argv[0] == "sn":
         return main_sn(argv[1:])
+    if argv and argv[0] == "pattern":
+        return main_pattern(argv[1:])
     import argparse
     import sys
 
