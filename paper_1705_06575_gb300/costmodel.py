@@ -516,6 +516,12 @@ def main_sn(argv=None):
 WEIGHTS_PATTERN = {"fp32": os.path.join(os.path.dirname(os.path.abspath(__file__)), "costmodel_pattern_fp32.json")}
 
 
+def pretrained_pattern(arm="fp32"):
+    """The per-pattern network of one arm trained by `python -m paper_1705_06575_gb300.costmodel
+    pattern --arm fp32 --train 400 --holdout 400` (its evaluation is saved beside the weights)."""
+    return CostModel.load(WEIGHTS_PATTERN[arm])
+
+
 def main_pattern(argv=None):
     """Per-pattern preset choice for one arm, on the suite at its stated sizes: the network of
     `features` (one row per preset) trained on measured graph times of every preset of the

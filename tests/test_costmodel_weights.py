@@ -96,3 +96,18 @@ def test_pretrained_per_supernode_weights_and_evaluation():
     for arm in ("fp64", "fp32"):
         a = ev["arms"][arm]
         assert a["patterns"] > 0 and a["geomean_speedup_per_supernode"] > 0
+
+
+def test_pretrained_pattern_fp32_weights_and_evaluation():
+    """The packaged per-pattern network of the FP32 arm has the network shape, gives finite
+    predictions on host features, and its stored held-out evaluation covers 400 patterns."""
+    import json
+    import os
+    m = cm.pretrained_pattern("fp32")
+    assert m.mean.shape == (cm.NFEAT,) and np.all(m.std > 0)
+    assert m.theta.size == ref.nparams(cm.NFEAT, m.hidden) and np.all(np.isfinite(m.theta))
+    X = cm.plan_features(w.laplace2d5(60, np.random.default_rng(1)))
+    y, _ = ref.forward(m.theta.astype(np.float64), (X - m.mean) / m.std, cm.NFEAT, m.hidden)
+    assert np.all(np.isfinite(y))
+    ev = json.load(open(os.path.join(os.path.dirname(cm.__file__), "costmodel_pattern_fp32_eval.json")))
+    assert ev["arm"] == "fp32" and ev["patterns"] == 400

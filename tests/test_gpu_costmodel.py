@@ -134,3 +134,23 @@ def test_pretrained_per_supernode_rules_on_fresh_patterns(torch_cuda):
     print("per-supernode rules on fresh patterns:", ev)
     assert ev["patterns"] == len(mats)
     assert ev["geomean_speedup_per_supernode"] > 1.0
+
+
+def test_pretrained_pattern_fp32_on_fresh_patterns(torch_cuda):
+    """The packaged per-pattern network of the FP32 arm (mixed-precision factor; 400 training
+    patterns of another seed): on fresh suite patterns (the 2D grids the flop budget admits) its
+    choices beat the fixed rule by measured graph time (geometric mean above 1; on 400 held-out
+    patterns it won 158 times and never lost by more than 2%)."""
+    torch = torch_cuda
+    from paper_1705_06575_gb300 import SYM_PREC_MIXED
+    from paper_1705_06575_gb300 import costmodel as cm
+    m = cm.pretrained_pattern("fp32")
+    mats, _, _ = cm.suite5(8, 3_000_000, 3e9)
+    ratios = []
+    for M in mats:
+        t = [cm.time_graph(M, torch, SYM_PREC_MIXED, opt=cm.options(p)) for p in range(len(cm.PRESETS))]
+        c = m.choose(M, torch)
+        ratios.append(t[cm.DEFAULT] / t[c])
+    gm = float(np.exp(np.mean(np.log(ratios))))
+    print("per-pattern FP32 choice on fresh patterns:", gm, ratios)
+    assert gm > 1.0
