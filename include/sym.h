@@ -72,6 +72,9 @@ extern "C" {
 #define SYM_FLAG_NO_TENSOR_CORES 8u /* SYM_PREC_MIXED: external updates in FP32 on the SIMT
                                        pipes instead of tcgen05 TF32 splits (x = hi + lo, all four
                                        partial products accumulated in FP32) */
+#define SYM_FLAG_NO_BATCH_PANEL 16u /* sym_factor_batch: run the POTRF, TRSM and TRTRI launches of
+                                       levels of narrow supernodes apart instead of as one fused
+                                       launch per level (SYM_EXPORT_BATCH_PANEL) */
 
 typedef struct sym_handle_s *sym_handle;
 
@@ -206,9 +209,13 @@ int sym_solve_batch(sym_handle h, int32_t nbatch, int32_t nrhs, const double *B,
  * tile and matrix or one warp per (tile, matrix) updating the tile in global memory; for one
  * matrix, FP64 updates of tiles with many entries run on a thread-block cluster per tile or one
  * CTA per tile, FP32 updates of full tiles on the tensor cores or the SIMT pipes, and small-tile
- * POTRF and TRTRI one CTA or one warp per tile. The
- * per-kernel profile totals are left as they were. *tuned: launches with two forms; *changed:
- * launches now on their second form (either pointer may be NULL). Errors as sym_factor_batch,
+ * POTRF and TRTRI one CTA or one warp per tile. A batch's levels of narrow supernodes
+ * (SYM_EXPORT_BATCH_PANEL) are first timed as one fused launch against their separate POTRF,
+ * TRSM and TRTRI launches (the sums of the level's launch times), the faster kept; the launches
+ * of a level kept separate then have their forms tuned like the others. The
+ * per-kernel profile totals are left as they were. *tuned: fused levels plus launches with two
+ * forms; *changed: levels returned to separate launches plus launches now on their second form
+ * (either pointer may be NULL). Errors as sym_factor_batch,
  * and SYM_ERR_INVALID for reps outside 1..100; the factor afterwards is that of the last run. */
 int sym_autotune(sym_handle h, int32_t nbatch, const double *Ax, int64_t stride, int32_t reps, int32_t *tuned,
                  int32_t *changed);
@@ -392,6 +399,14 @@ int sym_get_factor_host(sym_handle h, double *Lx_host);
 #define SYM_EXPORT_TASKS 22
 #define SYM_EXPORT_UPD_TASKS 23
 #define SYM_EXPORT_UPD_ENTRIES 24
+/* Batches: int32 words {role, pmax, ncmax, head} per factor launch. role 1: the POTRF launch of a
+ * level whose supernodes all have at most 32 columns; sym_factor_batch factors each of their
+ * panels (Cholesky of the diagonal block, triangular solve of the rows below it, inverse of the
+ * diagonal block) in this one launch, with pmax the level's largest panel (rows x columns) and
+ * ncmax its widest supernode; role 2: that level's TRSM and TRTRI launches, which batches skip;
+ * role 0: other launches. head: for roles 1 and 2 the index of the level's role-1 launch, else
+ * -1. sym_autotune may return a level to its separate launches. */
+#define SYM_EXPORT_BATCH_PANEL 27
 /* Forward solve by pushes: supernode J writes, per chunk ch of SOLVE_CW = 512 of its columns,
  * the products L_J(r, chunk) y_J(chunk) of its rows r below the diagonal block to a buffer t at
  * tx_J + ch (nrows_J - ncols_J) + (r - ncols_J), tx_J = sum over K < J of

@@ -46,6 +46,7 @@ SYM_FLAG_HOST_ONLY = 1
 SYM_FLAG_NO_GRAPHS = 2
 SYM_FLAG_ONE_STREAM = 4
 SYM_FLAG_NO_TENSOR_CORES = 8
+SYM_FLAG_NO_BATCH_PANEL = 16
 
 # name -> (code, numpy dtype)
 EXPORTS = {
@@ -57,7 +58,7 @@ EXPORTS = {
     "levelptr": (16, np.int32), "levellist": (17, np.int32), "lxptr": (18, np.int64),
     "factor_launches": (19, np.int64), "fwd_launches": (20, np.int64), "bwd_launches": (21, np.int64),
     "tasks": (22, np.int32), "upd_tasks": (23, np.int64), "upd_entries": (24, np.int64),
-    "contrib_ptr": (25, np.int64), "contrib": (26, np.int32),
+    "contrib_ptr": (25, np.int64), "contrib": (26, np.int32), "batch_panel": (27, np.int32),
 }
 
 

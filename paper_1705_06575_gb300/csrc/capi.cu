@@ -1,9 +1,11 @@
 // capi.cu — the C ABI of include/sym.h: handle life cycle, plan upload, executor calls.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <climits>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <new>
 #include <string>
 #include <vector>
@@ -590,6 +592,8 @@ static int analyze_impl(int64_t n, const int64_t *Ap, const int32_t *Ai, const i
     h->dp.piv = h->d_piv;
     for (int c = 0; c < 2; ++c) h->dp.variant[c] = h->plan.variant[c].data();
     h->dp.batch_warp = h->plan.batch_warp.data();
+    h->dp.batch_panel = (opt.flags & SYM_FLAG_NO_BATCH_PANEL) ? nullptr : h->plan.batch_panel.data();
+    h->dp.panel_apart = h->plan.panel_apart.data();
     h->dp.axc = h->d_Axc;
     h->dp.dpos = (const int64_t *)h->d_dpos;
   }
@@ -1017,6 +1021,8 @@ int64_t sym_export(sym_handle h, int32_t what, void *out) {
     EXPB(SYM_EXPORT_TASKS, tasks, 4)
     EXPB(SYM_EXPORT_UPD_TASKS, upd_tasks, 8)
     EXPB(SYM_EXPORT_UPD_ENTRIES, upd_entries, 8)
+    EXPB(SYM_EXPORT_BATCH_PANEL, batch_panel, 4)
+    static_assert(sizeof(sym::PanelForm) == 16, "panel form record layout");
 #undef EXPB
     default:
       return fail(SYM_ERR_INVALID, "unknown export item");
@@ -1062,43 +1068,74 @@ int sym_autotune(sym_handle h, int32_t nbatch, const double *Ax, int64_t stride,
   if (nbatch < 1) return fail(SYM_ERR_INVALID, "nbatch must be at least 1");
   auto &P = h->plan;
   const size_t nl = P.factor_launches.size();
-  std::vector<char> tunable(nl, 0);
   std::vector<int8_t> &var = P.variant[nbatch > 1 ? 1 : 0];  // one matrix and batches are tuned apart
-  int32_t ntun = 0;
-  for (size_t li = 0; li < nl; ++li) ntun += tunable[li] = sym::factor_launch_has_alternative(P.factor_launches[li], nbatch,
-                                                                           h->precision == SYM_PREC_FP64);
-  if (tuned) *tuned = ntun;
+  // a batch's fused narrow levels: one fused launch against the level's separate launches
+  std::vector<size_t> heads;
+  if (nbatch > 1 && h->dp.batch_panel)
+    for (size_t li = 0; li < nl; ++li)
+      if (P.batch_panel[li].role == sym::PANEL_FUSED) heads.push_back(li);
+  if (tuned) *tuned = 0;
   if (changed) *changed = 0;
-  if (ntun == 0) return SYM_OK;
-  // time every launch in both forms (kernel by kernel, CUDA events), keeping the user's profile
+  // time every launch in the forms given by set(v) (kernel by kernel, CUDA events, reps
+  // factorizations each), keeping the user's profile
   const bool prof0 = h->profiling;
   double ms0[sym::NUM_KINDS], fl0[sym::NUM_KINDS];
   int64_t nl0[sym::NUM_KINDS];
   std::memcpy(ms0, h->prof_ms, sizeof ms0);
   std::memcpy(fl0, h->prof_flops, sizeof fl0);
   std::memcpy(nl0, h->prof_launches, sizeof nl0);
-  std::vector<double> t[2] = {std::vector<double>(nl, 0.0), std::vector<double>(nl, 0.0)};
-  for (int v = 0; v < 2 && !rc; ++v) {
-    for (size_t li = 0; li < nl; ++li) var[li] = tunable[li] ? (int8_t)v : 0;
-    drop_graphs(h);
-    h->profiling = true;
-    for (int32_t r = 0; r < reps && !rc; ++r) {
-      rc = factor_impl(h, nbatch, Ax, stride);
-      if (!rc) rc = finish_status(h);
-      if (!rc && h->last_launch_ms[0].size() == nl + 1)
-        for (size_t li = 0; li < nl; ++li) t[v][li] += h->last_launch_ms[0][li + 1];
+  auto time_forms = [&](const std::function<void(int)> &set, std::vector<double> (&t)[2]) {
+    for (int v = 0; v < 2 && !rc; ++v) {
+      t[v].assign(nl, 0.0);
+      set(v);
+      drop_graphs(h);
+      h->profiling = true;
+      for (int32_t r = 0; r < reps && !rc; ++r) {
+        rc = factor_impl(h, nbatch, Ax, stride);
+        if (!rc) rc = finish_status(h);
+        if (!rc && h->last_launch_ms[0].size() == nl + 1)
+          for (size_t li = 0; li < nl; ++li) t[v][li] += h->last_launch_ms[0][li + 1];
+      }
+    }
+  };
+  int32_t ntun = 0, nchg = 0;
+  std::vector<double> t[2];
+  if (!heads.empty()) {
+    std::fill(var.begin(), var.end(), 0);
+    time_forms([&](int v) { for (size_t hd : heads) P.panel_apart[hd] = (int8_t)v; }, t);
+    for (size_t hd : heads) {  // the level's launches in either form (covered ones take ~0 fused)
+      double sum[2] = {0.0, 0.0};
+      for (size_t li = 0; li < nl; ++li)
+        if (P.batch_panel[li].role != sym::PANEL_NONE && P.batch_panel[li].head == (int32_t)hd)
+          for (int v = 0; v < 2; ++v) sum[v] += t[v][li];
+      P.panel_apart[hd] = !rc && sum[1] < sum[0] ? 1 : 0;
+      ++ntun;
+      nchg += P.panel_apart[hd];
     }
   }
-  int32_t nchg = 0;
+  std::vector<char> tunable(nl, 0);
+  int32_t nform = 0;
   for (size_t li = 0; li < nl; ++li) {
-    var[li] = tunable[li] && !rc && t[1][li] < t[0][li] ? 1 : 0;
-    nchg += var[li];
+    // launches of a level that stays fused have one form
+    const sym::PanelForm *pf = nbatch > 1 && h->dp.batch_panel ? &P.batch_panel[li] : nullptr;
+    const bool fused = pf && pf->role != sym::PANEL_NONE && !P.panel_apart[pf->head];
+    nform += tunable[li] = !fused && sym::factor_launch_has_alternative(P.factor_launches[li], nbatch,
+                                                                        h->precision == SYM_PREC_FP64);
   }
+  if (nform > 0 && !rc) {
+    time_forms([&](int v) { for (size_t li = 0; li < nl; ++li) var[li] = tunable[li] ? (int8_t)v : 0; }, t);
+    for (size_t li = 0; li < nl; ++li) {
+      var[li] = tunable[li] && !rc && t[1][li] < t[0][li] ? 1 : 0;
+      nchg += var[li];
+    }
+  }
+  ntun += nform;
   h->profiling = prof0;
   std::memcpy(h->prof_ms, ms0, sizeof ms0);
   std::memcpy(h->prof_flops, fl0, sizeof fl0);
   std::memcpy(h->prof_launches, nl0, sizeof nl0);
   drop_graphs(h);
+  if (tuned) *tuned = ntun;
   if (changed) *changed = nchg;
   return rc;
 }

@@ -1901,6 +1901,149 @@ __global__ void __launch_bounds__(32 * WT_WARPS) k_trtri_w(const SNode *__restri
     if (lane < ts) out[(int64_t)c * ts + lane] = lane >= c ? (T)x[pk(ts, c, lane)] : T(0);
 }
 
+// Narrow levels of a batch in one launch: for every supernode of the level (at most SMALL_TILE
+// columns, one column tile) the POTRF of its diagonal block, the TRSM of the rows below it and
+// the TRTRI of the diagonal block. One warp per (supernode, MW = 32 / G matrices); lane
+// q * MW + m works on matrix m of the warp and owns the panel rows r with r % G == q. On tiles of
+// a few columns the warp-per-(tile, matrix) forms leave most lanes of every FP64 instruction idle
+// (the FP64 pipe takes a warp instruction's full time whatever its active lanes); here every lane
+// carries a matrix. The warp's panels sit in shared memory, element e (column-major, ld nrows) of
+// matrix m at e * MP + m: with one lane per matrix (MP = 33, padded) the lanes of a step touch one
+// element of 32 matrices, with G lanes per matrix (MP = MW) consecutive rows of MW matrices, both
+// free of bank conflicts. Panels are staged with cp.async, every copy in flight at once. The
+// factor is right-looking over the panel's columns; each element sees the operations of
+// k_potrf_w (rows of the diagonal block) and k_trsm_w (rows below it) in their order, and the
+// inverse those of k_trtri_w.
+// Asynchronous copy of one element from global to shared memory (cp.async, 4 or 8 bytes, both
+// addresses aligned to the size); cp_async_wait_all waits for this thread's copies.
+template <int BYTES>
+__device__ __forceinline__ void cp_async_elem(void *smem_dst, const void *gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(gsrc), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+template <typename T, int G>
+__global__ void __launch_bounds__(32) k_panel_b(const SNode *__restrict__ sn, const Int4 *__restrict__ tasks,
+                                                T *__restrict__ Lx, T *__restrict__ Linv, long long *status,
+                                                double *__restrict__ piv, const double *__restrict__ axc,
+                                                const int64_t *__restrict__ dpos, int64_t toff, int32_t nmat,
+                                                int32_t ncmax, const Batch bt) {
+  constexpr int MW = 32 / G, MP = G == 1 ? 33 : MW;  // matrices per warp, element stride
+  constexpr bool F64PIV = std::is_same<T, float>::value;  // FP64 pivot chain of FP32 factors
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double *dv = reinterpret_cast<double *>(smem_raw);     // ncmax x MW: 1 / L_cc in FP64
+  double *dd = dv + (size_t)ncmax * MW;                   // FP32: ncmax x MW FP64 pivots
+  double *xd = dd + (F64PIV ? (size_t)ncmax * MW : 0);    // FP32: strict lower inverse, packed rows
+  T *S = reinterpret_cast<T *>(xd + (F64PIV ? (size_t)ncmax * (ncmax - 1) / 2 * MW : 0));
+  const int lane = threadIdx.x, m = lane & (MW - 1), q = lane / MW;
+  const int32_t mat0 = blockIdx.y * MW, mat = mat0 + m;
+  const bool act = mat < nmat;
+  const int nm = min(MW, nmat - mat0);  // matrices of this warp
+  const Int4 t = tasks[toff + blockIdx.x];
+  const SNode sj = sn[t.a];
+  const int nc = sj.ncols, nr = sj.nrows, np = nc * nr;
+  for (int mm = 0; mm < nm; ++mm) {  // every copy in flight at once
+    const T *src = Lx + (int64_t)(mat0 + mm) * bt.lx + sj.lx;
+    for (int e = lane; e < np; e += 32) cp_async_elem<sizeof(T)>(S + e * MP + mm, src + e);
+  }
+  cp_async_wait_all();
+  __syncwarp();
+  T *const Sm = S + m;     // this lane's matrix: element (r, c) at Sm[c * ld + r * MP]
+  const int ld = nr * MP;  // column stride
+  if constexpr (F64PIV) {  // the FP64 diagonal of the updated block (as k_potrf_w loads it)
+    const double *ax = axc ? axc + (int64_t)(act ? mat : mat0) * bt.nnz : nullptr;
+    for (int c = q; c < nc; c += G) dd[c * MW + m] = act ? diag64((float)Sm[c * ld + c * MP], ax, dpos, sj.first + c) : 1.0;
+    __syncwarp();
+  }
+  for (int c = 0; c < nc; ++c) {
+    // pivot: every lane of the matrix computes it; the owner of row c stores L_cc below
+    T x, lcc;
+    if constexpr (F64PIV) {
+      double d = dd[c * MW + m];
+      if (!(d > 0.0)) {
+        if (act && q == 0) atomicMin(status + mat, (long long)(sj.first + c));
+        d = 1.0;
+      }
+      if (act && q == 0 && piv) piv[(int64_t)mat * bt.piv + sj.first + c] = d;
+      const float df = (float)d;
+      x = rsqrt_newton(df);
+      lcc = df * x;
+    } else {
+      T d = Sm[c * ld + c * MP];
+      if (!(d > T(0))) {
+        if (act && q == 0) atomicMin(status + mat, (long long)(sj.first + c));
+        d = T(1);
+      }
+      x = rsqrt_of(d);
+      lcc = d * x;
+    }
+    const T dinv = T(1) / lcc;  // k_trsm_w's 1 / L_cc
+    if (q == 0) dv[c * MW + m] = F64PIV ? 1.0 / (double)lcc : (double)dinv;  // k_trtri_w's FP64 1 / L_cc
+    // column c: rows of the diagonal block times x (POTRF), rows below it times 1 / L_cc (TRSM)
+    const int r1 = q > c ? q : q + ((c + 1 - q + G - 1) / G) * G;  // first own row > c
+    T *const colc = Sm + c * ld;
+    for (int rr = r1; rr < nr; rr += G) colc[rr * MP] *= rr < nc ? x : dinv;
+    __syncwarp();
+    if (c % G == q) colc[c * MP] = lcc;
+    for (int rr = r1; rr < nr; rr += G) {
+      T *const row = Sm + rr * MP;
+      const T lrc = row[c * ld];
+      if (F64PIV && rr < nc) dd[rr * MW + m] = fma(-(double)lrc, (double)lrc, dd[rr * MW + m]);
+      const int cend = rr < nc ? (F64PIV ? rr - 1 : rr) : nc - 1;  // FP32: the FP64 chain holds the diagonal
+#pragma unroll 4
+      for (int cc = c + 1; cc <= cend; ++cc) row[cc * ld] = fma(-lrc, colc[cc * MP], row[cc * ld]);
+    }
+    __syncwarp();
+  }
+  // zeros above the diagonal (in the FP64 arm also the start of the inverse's rows there)
+  for (int rr = q; rr < nc; rr += G)
+    for (int j = 0; j < rr; ++j) {
+      Sm[rr * ld + j * MP] = T(0);
+      if constexpr (F64PIV) xd[(size_t)(rr * (rr - 1) / 2 + j) * MW + m] = 0.0;
+    }
+  __syncwarp();
+  for (int mm = 0; mm < nm; ++mm) {
+    T *dst = Lx + (int64_t)(mat0 + mm) * bt.lx + sj.lx;
+    for (int e = lane; e < np; e += 32) dst[e] = S[e * MP + mm];
+  }
+  __syncwarp();
+  // inverse of the diagonal block in FP64: x(r, j) for r > j in the FP64 arm at position (j, r)
+  // of the panel (above the diagonal, already written out), in the FP32 arm in xd
+  auto xr = [&](int rr, int j, int mm) -> double & {
+    if constexpr (F64PIV) return xd[(size_t)(rr * (rr - 1) / 2 + j) * MW + mm];
+    else return S[(rr * nr + j) * MP + mm];
+  };
+  for (int c = 0; c + 1 < nc; ++c) {
+    const int r1 = q > c ? q : q + ((c + 1 - q + G - 1) / G) * G;
+    for (int rr = r1; rr < nc; rr += G) {
+      const double a = (double)Sm[c * ld + rr * MP];  // L(rr, c)
+      const double dr = dv[rr * MW + m];
+#pragma unroll 4
+      for (int j = 0; j <= c; ++j) {
+        const double xcj = j == c ? dv[c * MW + m] : xr(c, j, m);
+        const double v = fma(-a, xcj, xr(rr, j, m));
+        xr(rr, j, m) = rr == c + 1 ? v * dr : v;
+      }
+    }
+    __syncwarp();
+  }
+  const int ts = nc;
+  const float rts = 1.0f / (float)ts;  // e / ts for e < ts^2 <= 1024: exact through FP32
+  for (int mm = 0; mm < nm; ++mm) {
+    T *out = Linv + (int64_t)(mat0 + mm) * bt.dinv + sj.dx;
+    for (int e = lane; e < ts * ts; e += 32) {
+      const int c = (int)(((float)e + 0.5f) * rts), rr = e - c * ts;
+      out[e] = rr > c ? (T)xr(rr, c, mm) : rr == c ? (T)dv[c * MW + mm] : T(0);
+    }
+  }
+}
+
+template <typename T, int G>
+size_t panel_b_smem(int32_t pmax, int32_t ncmax) {
+  return (size_t)panel_smem_bytes(pmax, ncmax, std::is_same<T, float>::value, G);
+}
+
 // (f) Warp forms of the solve kernels for batches, on launches whose supernodes all have at most
 // SMALL_TILE columns (the schedule marks them tb = SMALL_TILE): one warp per (task, matrix), the
 // same task of WT_WARPS consecutive matrices per CTA. A batch's leaf levels hold ~10^3 tasks of a
@@ -2182,6 +2325,15 @@ cudaError_t prepare_factor() {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_trsm_w<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_w_smem<T>());
   if (e != cudaSuccess) return e;
+  {
+    void (*panel[4])(const SNode *, const Int4 *, T *, T *, long long *, double *, const double *, const int64_t *,
+                     int64_t, int32_t, int32_t, const Batch) = {k_panel_b<T, 1>, k_panel_b<T, 2>, k_panel_b<T, 4>,
+                                                                 k_panel_b<T, 8>};
+    for (auto *k : panel) {
+      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, PANEL_SMEM_HARD);
+      if (e != cudaSuccess) return e;
+    }
+  }
   e = cudaFuncSetAttribute(k_trtri<T, SMALL_TB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)trtri_smem<SMALL_TB>());
   if (e != cudaSuccess) return e;
@@ -2268,6 +2420,27 @@ bool factor_launch_has_alternative(const Launch &L, int32_t nbatch, bool fp64) {
          (small && (L.kind == K_POTRF || L.kind == K_TRTRI));
 }
 
+// One fused narrow-level launch of a batch (k_panel_b with the level's lanes per matrix).
+template <typename T>
+cudaError_t launch_panel_b(const DevPlan &d, const PanelForm &pf, unsigned g, unsigned nb, cudaStream_t s, int prio,
+                           T *Lx, T *Linv, long long *status, int64_t off, const Batch &bt) {
+  const int lanes = panel_lanes(pf.pmax, pf.ncmax, std::is_same<T, float>::value);
+#define SYM_PANEL(G)                                                                                         \
+  case G:                                                                                                    \
+    return launch_prio(k_panel_b<T, G>, dim3(g, (nb + 32 / G - 1) / (32 / G)), 32,                           \
+                       panel_b_smem<T, G>(pf.pmax, pf.ncmax), s, prio, d.sn, d.tasks, Lx, Linv, status, d.piv, \
+                       d.axc, d.dpos, off, (int32_t)nb, pf.ncmax, bt);
+  switch (lanes) {
+    SYM_PANEL(1)
+    SYM_PANEL(2)
+    SYM_PANEL(4)
+    SYM_PANEL(8)
+    default:
+      return cudaErrorInvalidValue;
+  }
+#undef SYM_PANEL
+}
+
 template <typename T>
 cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, const double *Ax,
                        T *Lx, T *Linv, long long *status, cudaStream_t st, LaunchTrace *trace, const Batch &bt,
@@ -2291,6 +2464,15 @@ cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, co
     cudaStream_t s = (dual && L.stream == 1) ? two->aux : st;
     const int prio = (dual && L.stream == 1) ? two->prio_low : two ? two->prio_high : 0;
     if (dual && L.wait >= 0) cudaStreamWaitEvent(s, (*two->events)[L.wait], 0);
+    // a batch's fused narrow level: its POTRF launch factors and inverts the whole panels, its
+    // TRSM and TRTRI launches have nothing left to do
+    int32_t panel = nb > 1 && d.batch_panel ? d.batch_panel[li].role : PANEL_NONE;
+    if (panel != PANEL_NONE && d.panel_apart && d.panel_apart[d.batch_panel[li].head]) panel = PANEL_NONE;
+    if (panel == PANEL_COVERED) {
+      if (dual) cudaEventRecord((*two->events)[li], s);
+      trace_mark(trace, L.kind, st);
+      continue;
+    }
     cudaError_t e = cudaSuccess;
     const bool small = L.tb == SMALL_TB;  // every tile of the launch fits the small variant
     // the autotuner's choice for this launch: false keeps the default form of a batch
@@ -2332,7 +2514,9 @@ cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, co
         // small tiles of a batch: a warp per tile (throughput); of one matrix: a CTA per tile, whose
         // four warps shorten each column step of the tile (latency; 64^2 factor 0.96 -> 0.83 ms);
         // the autotuner's choice (alt) swaps the two
-        if (small && (nb > 1) != alt)
+        if (panel == PANEL_FUSED)
+          e = launch_panel_b<T>(d, d.batch_panel[li], g, nb, s, prio, Lx, Linv, status, L.off, bt);
+        else if (small && (nb > 1) != alt)
           e = launch_prio(k_potrf_w<T>, dim3((g + WT_WARPS - 1) / WT_WARPS, nb), 32 * WT_WARPS, 0, s, prio, d.sn,
                           d.tasks, (int64_t)g, Lx, status, d.piv, d.axc, d.dpos, L.off, bt);
         else if (small)

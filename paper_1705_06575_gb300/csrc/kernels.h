@@ -33,6 +33,10 @@ struct DevPlan {
   const int8_t *batch_warp = nullptr;  // HOST array, one per factor launch: a batch's default form
                                        // of the launch is one warp per (tile, matrix) (full-tile
                                        // FP64 updates with small entries)
+  const PanelForm *batch_panel = nullptr;  // HOST array, one per factor launch: a batch's fused
+                                           // narrow levels (Plan::batch_panel); null: none
+  const int8_t *panel_apart = nullptr;     // HOST array (Plan::panel_apart): levels the autotuner
+                                           // runs as separate launches; null: none
   const int8_t *variant[2] = {nullptr, nullptr};  // HOST arrays, one entry per factor launch,
                                      // [0] for one matrix, [1] for batches: 1 runs the launch's
                                      // alternative kernel form (see factor_launch_has_alternative),

@@ -26,6 +26,34 @@ constexpr int SMALL_TILE = 32;
 // average default to the warp-per-(tile, matrix) form (measured on a 512 x 128^2 9-point batch:
 // 1.35-4.7x faster than one CTA per tile at 34-134 elements, about equal at 175-230).
 constexpr int BATCH_WARP_ELEMS = 160;
+// Batches, narrow levels in one launch (k_panel_b): a level whose supernodes all have at most
+// SMALL_TILE columns factors each panel (POTRF of the diagonal block, TRSM of the rows below it,
+// TRTRI of the diagonal block) in one warp per (supernode, 32 / G matrices), G lanes per matrix,
+// the warp's panels in shared memory. panel_lanes gives G for a level's largest panel (pmax
+// elements) and widest supernode (ncmax columns): the smallest of 1, 2, 4, 8 whose shared memory
+// per warp is at most PANEL_SMEM_SOFT (six warps per SM), else 8 if that fits PANEL_SMEM_HARD
+// (four warps per SM, one per scheduler), else 0 (the level keeps its separate launches).
+// f32: FP32 panels (the FP64 pivot chain and the FP64 inverse need their own arrays).
+constexpr int PANEL_SMEM_SOFT = 36 * 1024;
+constexpr int PANEL_SMEM_HARD = 56 * 1024;
+inline int64_t panel_smem_bytes(int64_t pmax, int64_t ncmax, bool f32, int g) {
+  const int64_t stride = g == 1 ? 33 : 32 / g;  // panel element stride (padded with one matrix per lane)
+  return stride * pmax * (f32 ? 4 : 8) + (32 / g) * (ncmax * 8 + (f32 ? ncmax * 8 + ncmax * (ncmax - 1) / 2 * 8 : 0));
+}
+inline int panel_lanes(int64_t pmax, int64_t ncmax, bool f32) {
+  for (int g = 1; g <= 8; g *= 2)
+    if (panel_smem_bytes(pmax, ncmax, f32, g) <= PANEL_SMEM_SOFT) return g;
+  return panel_smem_bytes(pmax, ncmax, f32, 8) <= PANEL_SMEM_HARD ? 8 : 0;
+}
+// Role of a factor launch in a batch's fused narrow levels (PanelForm::role).
+constexpr int32_t PANEL_NONE = 0, PANEL_FUSED = 1, PANEL_COVERED = 2;
+struct PanelForm {
+  int32_t role;   // PANEL_FUSED: the level's POTRF launch runs k_panel_b for batches;
+                  // PANEL_COVERED: its TRSM and TRTRI launches, which batches then skip
+  int32_t pmax;   // PANEL_FUSED: the level's largest panel, nrows x ncols elements
+  int32_t ncmax;  // PANEL_FUSED: the level's widest supernode
+  int32_t head;   // PANEL_FUSED and PANEL_COVERED: index of the level's PANEL_FUSED launch
+};
 // Trailing-update GEMM CTAs resident on the whole GPU at once (3 per SM on 152 SMs): the size of
 // one wave, used to split the last wave of a long launch into finer work.
 constexpr int GEMM_SLOTS = 3 * 152;
@@ -166,6 +194,9 @@ struct Plan {
                                       // [0] for one matrix, [1] for batches
   std::vector<int8_t> batch_warp;     // per factor launch: 1 if a batch's default form of this
                                       // full-tile update is one warp per (tile, matrix)
+  std::vector<PanelForm> batch_panel;  // per factor launch: fused narrow levels of batches
+  std::vector<int8_t> panel_apart;     // per factor launch, on PANEL_FUSED ones: 1 if the
+                                       // autotuner found the level faster as separate launches
   std::vector<Launch> fwd_launches;
   std::vector<Launch> bwd_launches;
   // Forward solve by pushes: t holds tsize entries per right-hand side; the contribution list of

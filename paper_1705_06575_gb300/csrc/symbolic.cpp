@@ -881,6 +881,33 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
     }
     P.batch_warp[li] = cnt > 0.0 && elems <= BATCH_WARP_ELEMS * cnt;
   }
+  // Batches: levels of supernodes with at most SMALL_TILE columns whose panels fit k_panel_b in
+  // either precision run their POTRF, TRSM and TRTRI as one launch (see panel_lanes). Such a
+  // level has one launch of each (one column tile, all of it small-tile).
+  P.batch_panel.assign(P.factor_launches.size(), PanelForm{PANEL_NONE, 0, 0, -1});
+  P.panel_apart.assign(P.factor_launches.size(), 0);
+  for (int32_t l = 0; l < nlev; ++l) {
+    int64_t pmax = 0, ncmax = 0;
+    bool narrow = P.levelptr[l + 1] > P.levelptr[l];
+    for (int32_t t = P.levelptr[l]; t < P.levelptr[l + 1]; ++t) {
+      const SNode &sj = P.snodes[P.levellist[t]];
+      narrow = narrow && sj.ncols <= SMALL_TILE;
+      pmax = std::max<int64_t>(pmax, (int64_t)sj.nrows * sj.ncols);
+      ncmax = std::max<int64_t>(ncmax, sj.ncols);
+    }
+    if (!narrow || panel_lanes(pmax, ncmax, false) == 0 || panel_lanes(pmax, ncmax, true) == 0) continue;
+    std::vector<size_t> potrf, other;
+    for (size_t li = 0; li < P.factor_launches.size(); ++li) {
+      const Launch &L = P.factor_launches[li];
+      if (L.level != l) continue;
+      if (L.kind == K_POTRF) potrf.push_back(li);
+      if (L.kind == K_TRSM || L.kind == K_TRTRI) other.push_back(li);
+    }
+    if (potrf.size() != 1) continue;
+    const int32_t head = (int32_t)potrf[0];
+    P.batch_panel[head] = PanelForm{PANEL_FUSED, (int32_t)pmax, (int32_t)ncmax, head};
+    for (size_t li : other) P.batch_panel[li] = PanelForm{PANEL_COVERED, 0, 0, head};
+  }
   // 12. Algorithmic flops of each kernel kind (see Plan::kind_flops).
   {
     auto sq = [](double x) { return x * x; };

@@ -1,7 +1,8 @@
 """Profiling driver: factor one named workload and report where the time goes.
 
     python -m paper_1705_06575_gb300.profile_factor --workload conduct3d7_48 [--one-stream]
-        [--no-graphs] [--mixed [--no-tensor-cores]] [--levels] [--repeat N] [--batch B] [--solve NRHS]
+        [--no-graphs] [--mixed [--no-tensor-cores]] [--levels] [--repeat N] [--batch B [--autotune]]
+        [--solve NRHS]
 
 Without --levels it factors the matrix once per repeat (after one warm-up factorization) and
 exits: a fixed, short command to run under a profiler. With --one-stream --no-graphs every launch
@@ -10,7 +11,9 @@ sym_export(FACTOR_LAUNCHES) among launches of the same kernel. With --levels it 
 profiled factorization (CUDA events around every launch, one stream) and prints a JSON summary:
 per level of the supernodal tree and per kernel kind the milliseconds, launches and tasks, the
 serialised total and the time a two-stream schedule would take if both streams' launches kept
-their serialised durations (an upper bound on what the lookahead can overlap).
+their serialised durations (an upper bound on what the lookahead can overlap). With --batch B the
+same runs on B value sets of the pattern at once (sym_factor_batch, and sym_solve_batch with
+--solve), --levels adding the solve's milliseconds per kernel kind.
 """
 from __future__ import annotations
 
@@ -22,10 +25,11 @@ import sys
 import numpy as np
 
 from . import (SYM_FLAG_NO_GRAPHS, SYM_FLAG_NO_TENSOR_CORES, SYM_FLAG_ONE_STREAM, SYM_PROFILE_OFF,
-               SYM_PROFILE_ON, SYM_PROFILE_RESET, Solver, sym_factor_batch, sym_profile, sym_profile_launches,
-               sym_solve_multi)
+               SYM_PROFILE_ON, SYM_PROFILE_RESET, Solver, sym_autotune, sym_factor_batch, sym_profile,
+               sym_profile_launches, sym_profile_read, sym_solve_batch, sym_solve_multi)
 
 KIND_NAMES = {1: "update", 2: "potrf", 3: "trsm", 4: "gemm", 5: "trtri"}
+SOLVE_KIND_NAMES = {11: "fgather", 12: "fstep", 13: "fpush", 14: "bgather", 15: "bstep", 16: "fsum", 17: "perm"}
 
 
 def level_summary(s, ms):
@@ -78,19 +82,44 @@ def main(argv=None):
                     help="factor this many value sets of the workload's pattern together (sym_factor_batch)")
     ap.add_argument("--solve", type=int, default=0,
                     help="after the factorizations, solve with this many right-hand sides (repeat + 1 times)")
+    ap.add_argument("--autotune", action="store_true", help="batches: run sym_autotune first")
     args = ap.parse_args(argv)
     M = w.cfg(args.workload)
     flags = ((SYM_FLAG_ONE_STREAM if args.one_stream else 0) | (SYM_FLAG_NO_GRAPHS if args.no_graphs else 0) |
              (SYM_FLAG_NO_TENSOR_CORES if args.no_tensor_cores else 0))
     s = Solver(M.n, M.Ap, M.Ai, M.perm, flags=flags, precision="mixed" if args.mixed else None)
     if args.batch > 1:  # value sets drawn like the workload's (same pattern, seeds 0..batch-1)
-        vals = np.stack([w.cfg(args.workload, b).Ax for b in range(args.batch)])
+        nb = args.batch
+        vals = np.stack([w.cfg(args.workload, b).Ax for b in range(nb)])
         V = torch.from_numpy(vals).cuda()
+        out = {"workload": args.workload, "batch": nb}
+        if args.autotune:
+            out["autotune"] = sym_autotune(s.h, nb, V, M.nnz, 2)
+        B = X = None
+        if args.solve > 0:
+            B = torch.from_numpy(np.random.default_rng(5).standard_normal((nb, args.solve, M.n))).cuda()
+            X = torch.empty_like(B)
+
+        def step():
+            sym_factor_batch(s.h, nb, V, M.nnz)
+            if B is not None:
+                sym_solve_batch(s.h, nb, args.solve, B, M.n, args.solve * M.n, X, M.n, args.solve * M.n)
+
         for _ in range(args.repeat + 1):
-            sym_factor_batch(s.h, args.batch, V, M.nnz)
+            step()
         torch.cuda.synchronize()
-        print(json.dumps({"workload": args.workload, "batch": args.batch, "factorizations": args.repeat + 1,
-                          "status": "ok"}))
+        if args.levels:
+            sym_profile(s.h, SYM_PROFILE_RESET)
+            sym_profile(s.h, SYM_PROFILE_ON)
+            step()
+            torch.cuda.synchronize()
+            sym_profile(s.h, SYM_PROFILE_OFF)
+            out.update(level_summary(s, sym_profile_launches(s.h, 0)))
+            if B is not None:
+                out["solve_kinds_ms"] = {name: round(sym_profile_read(s.h, k)[0], 3)
+                                         for k, name in SOLVE_KIND_NAMES.items() if sym_profile_read(s.h, k)[1]}
+        out.update({"steps": args.repeat + 1 + (1 if args.levels else 0), "status": "ok"})
+        print(json.dumps(out))
         s.close()
         return 0
     Ax = torch.from_numpy(M.Ax).cuda()

@@ -146,3 +146,39 @@ def test_autotune_keeps_results(torch_cuda):
     S.sym_factor_batch(s.h, nb, V, M.nnz)
     for b in range(nb):
         assert np.array_equal(S.sym_get_batch_factor_host(s.h, b), tuned_batch[b])
+
+
+@pytest.mark.parametrize("precision", [None, "mixed"])
+def test_fused_narrow_levels_match_separate_launches(torch_cuda, precision):
+    """A batch factors each level of narrow supernodes in one launch (lanes = matrices, 1 to 8 lanes
+    per matrix on this pattern, 37 matrices: ragged lane groups). Its panels and solves equal, bit
+    for bit, those of the level's separate POTRF, TRSM and TRTRI launches, and match the oracle."""
+    torch = torch_cuda
+    import paper_1705_06575_gb300 as S
+    nb, nrhs = 37, 2
+    M, vals = w.same_pattern_batch(lambda r: w.dd2d9(48, r), nb, 60)
+    V = torch.from_numpy(vals).cuda()
+    fused = S.Solver(M.n, M.Ap, M.Ai, M.perm, precision=precision)
+    apart = S.Solver(M.n, M.Ap, M.Ai, M.perm, precision=precision, flags=S.SYM_FLAG_NO_BATCH_PANEL)
+    assert (fused.export("batch_panel").reshape(-1, 4)[:, 0] == 1).sum() >= 4
+    B = torch.from_numpy(np.stack([w.rhs(M.n, nrhs, np.random.default_rng(b)).T for b in range(nb)])).cuda()
+    out = []
+    for s in (fused, apart):
+        S.sym_factor_batch(s.h, nb, V, M.nnz)
+        X = torch.empty_like(B)
+        S.sym_solve_batch(s.h, nb, nrhs, B, M.n, nrhs * M.n, X, M.n, nrhs * M.n)
+        torch.cuda.synchronize()
+        out.append(([S.sym_get_batch_factor_host(s.h, b).copy() for b in range(nb)], X.cpu().numpy()))
+    for b in range(nb):
+        assert np.array_equal(out[0][0][b], out[1][0][b])
+    assert np.array_equal(out[0][1], out[1][1])
+    o = oracle.Oracle(M.n, M.Ap, M.Ai, M.perm)
+    sx = exports(fused)
+    Bh = B.cpu().numpy()
+    for b in (0, 31, 32, nb - 1):
+        assert oracle.backward_error(M.n, M.Ap, M.Ai, vals[b], Bh[b].T, out[0][1][b].T) <= (
+            BERR_TOL if precision is None else REFINED_BERR)
+        if precision is None:
+            o.factor(vals[b])
+            Lb, outside = panels_on_pattern(sx, out[0][0][b], o.Lp, o.Li)
+            assert outside == 0.0 and np.abs(Lb - o.Lx).max() <= ENTRY_RTOL * np.abs(o.Lx).max()

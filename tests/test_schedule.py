@@ -15,6 +15,7 @@ NB = 64
 BG = 16
 CW = 512  # columns per forward push chunk
 K_UPDATE, K_POTRF, K_TRSM, K_GEMM, K_TRTRI = 1, 2, 3, 4, 5
+PANEL_NONE, PANEL_FUSED, PANEL_COVERED = 0, 1, 2
 S_FGATHER, S_FSTEP, S_FPUSH, S_BGATHER, S_BSTEP, S_FSUM = 11, 12, 13, 14, 15, 16
 
 
@@ -30,6 +31,7 @@ class Sched:
         ue = s.export("upd_entries").reshape(-1, 5)
         self.ue = np.stack([ue[:, 0] & 0xffffffff, ue[:, 0] >> 32, ue[:, 1] & 0xffffffff, ue[:, 1] >> 32,
                             ue[:, 2], ue[:, 3], ue[:, 4]], 1)
+        self.panel = s.export("batch_panel").reshape(-1, 4)  # {role, pmax, ncmax, head} per factor launch
         self.cptr = s.export("contrib_ptr")
         self.contrib = s.export("contrib")
         # offset of each supernode's pushed products: its rows below the diagonal block, once per
@@ -118,18 +120,42 @@ class Launch:
             store[key] = v
 
 
-def emulate_factor(sc, panels, store):
-    """store maps ('L', j, r, c) and ('I', j, s, r, c) to values."""
+def emulate_factor(sc, panels, store, batch=False):
+    """store maps ('L', j, r, c) and ('I', j, s, r, c) to values. batch: the launches as a batch
+    runs them (a fused narrow level's POTRF launch factors, solves and inverts whole panels; its
+    TRSM and TRTRI launches do nothing)."""
     def get(j, r, c):
         return store[("L", j, r, c)]
 
     record = []
-    for (kind, off, count, _, _), tb in zip(sc.launches["factor_launches"], sc.tb["factor_launches"]):
+    for li, ((kind, off, count, _, _), tb) in enumerate(zip(sc.launches["factor_launches"], sc.tb["factor_launches"])):
         kind = int(kind)
         L = Launch()
         record.append(L)
+        role = int(sc.panel[li, 0]) if batch else 0
+        if role == PANEL_COVERED:
+            L.commit(store)
+            continue
         for t in range(int(off), int(off + count)):
-            if kind == K_UPDATE:
+            if role == PANEL_FUSED:
+                j = int(sc.tasks[t][0])
+                f, nc, nr, ncb = sc.J(j)
+                assert ncb == 1 and nc <= 32 and nr * nc <= sc.panel[li, 1] and nc <= sc.panel[li, 2]
+                Pn = np.array([[get(j, r, c) for c in range(nc)] for r in range(nr)])
+                for r in range(nr):
+                    for c in range(nc):
+                        L.read(t, ("L", j, r, c))
+                Lc = np.linalg.cholesky(np.tril(Pn[:nc]) + np.tril(Pn[:nc], -1).T)
+                X = np.linalg.solve(Lc, Pn[nc:].T).T
+                full = np.vstack([Lc, X])
+                for r in range(nr):
+                    for c in range(nc):
+                        L.write(t, ("L", j, r, c), full[r, c])
+                Inv = np.linalg.inv(Lc)
+                for a in range(nc):
+                    for b in range(nc):
+                        L.write(t, ("I", j, 0, a, b), Inv[a, b])
+            elif kind == K_UPDATE:
                 j, bi, bj, e0, e1 = (int(v) for v in sc.ut[t])
                 rs, cs = sc.tile(j, bi, bj)
                 rb, cb = rs.start, cs.start
@@ -346,7 +372,8 @@ def emulate_solve(sc, store, y):
     lambda: w.random_spd_pattern(220, 0.03, np.random.default_rng(4)),
     lambda: w.wide_block(520, 40, np.random.default_rng(5)),                # two push chunks
 ])
-def test_schedule_emulation_reproduces_oracle(maker):
+@pytest.mark.parametrize("batch", [False, True])
+def test_schedule_emulation_reproduces_oracle(maker, batch):
     M = maker()
     s = S.Solver(M.n, M.Ap, M.Ai, M.perm, host_only=True)
     sc = Sched(s)
@@ -364,7 +391,7 @@ def test_schedule_emulation_reproduces_oracle(maker):
         for r in range(nr):
             for c in range(nc):
                 store[("L", j, r, c)] = Cval.get((int(R[r]), f + c), 0.0) if R[r] >= f + c else 0.0
-    emulate_factor(sc, None, store)
+    emulate_factor(sc, None, store, batch)
     # compare with the oracle on its pattern
     for j in range(len(sc.sup) - 1):
         f, nc, nr, _ = sc.J(j)
@@ -564,3 +591,54 @@ def test_step_launches_have_a_kernel_form(maker):
         for (kind, off, count, _, _), tb, cl in zip(sc.launches[key], sc.tb[key], sc.cluster[key]):
             if int(kind) in (S_FSTEP, S_BSTEP):
                 assert int(cl) == 4 or int(tb) == 32
+
+
+def _panel_lanes(pmax, ncmax, f32):
+    """The rule of the fused narrow-level kernel's lanes per matrix (smallest of 1, 2, 4, 8 whose
+    shared memory per warp is at most 36 KiB, else 8 within 56 KiB, else none)."""
+    def smem(g):
+        stride = 33 if g == 1 else 32 // g  # panel element stride (one padding slot with a lane per matrix)
+        return stride * pmax * (4 if f32 else 8) + 32 // g * (ncmax * 8 + ((ncmax * 8 + ncmax * (ncmax - 1) // 2 * 8) if f32 else 0))
+    for g in (1, 2, 4, 8):
+        if smem(g) <= 36 * 1024:
+            return g
+    return 8 if smem(8) <= 56 * 1024 else 0
+
+
+@pytest.mark.parametrize("maker", [
+    lambda: w.dd2d9(128, np.random.default_rng(2000)),                       # the batched pattern
+    lambda: w.laplace2d5(30, np.random.default_rng(1)),
+    lambda: w.conduct3d(10, np.random.default_rng(3), "star"),
+])
+def test_batch_panel_marks(maker):
+    """Every level whose supernodes all have at most 32 columns and whose panels fit the fused
+    kernel in both precisions has its POTRF launch marked fused (with the level's largest panel
+    and widest supernode) and its TRSM and TRTRI launches marked covered; nothing else is marked."""
+    M = maker()
+    s = S.Solver(M.n, M.Ap, M.Ai, M.perm, host_only=True)
+    sc = Sched(s)
+    level = s.export("level")
+    nc = np.diff(sc.sup)
+    nr = np.diff(sc.rowptr)
+    raw = s.export("factor_launches").reshape(-1, 5)
+    lkind, llev = raw[:, 0] & 0xffffffff, raw[:, 0] >> 32
+    fused_levels = set()
+    for lv in range(int(level.max()) + 1):
+        sel = level == lv
+        pmax, ncmax = int((nc * nr)[sel].max()), int(nc[sel].max())
+        eligible = ncmax <= 32 and _panel_lanes(pmax, ncmax, False) > 0 and _panel_lanes(pmax, ncmax, True) > 0
+        eligible = eligible and int(((llev == lv) & (lkind == K_POTRF)).sum()) == 1
+        head = [li for li in np.nonzero(llev == lv)[0] if lkind[li] == K_POTRF]
+        for li in np.nonzero(llev == lv)[0]:
+            role, pm, nm, hd = (int(v) for v in sc.panel[li])
+            if not eligible:
+                assert role == PANEL_NONE
+            elif lkind[li] == K_POTRF:
+                assert (role, pm, nm, hd) == (PANEL_FUSED, pmax, ncmax, li)
+            elif lkind[li] in (K_TRSM, K_TRTRI):
+                assert (role, hd) == (PANEL_COVERED, head[0])
+            else:
+                assert role == PANEL_NONE
+        if eligible:
+            fused_levels.add(lv)
+    assert fused_levels  # every pattern here has narrow levels at its leaves
