@@ -72,9 +72,10 @@ extern "C" {
 #define SYM_FLAG_NO_TENSOR_CORES 8u /* SYM_PREC_MIXED: external updates in FP32 on the SIMT
                                        pipes instead of tcgen05 TF32 splits (x = hi + lo, all four
                                        partial products accumulated in FP32) */
-#define SYM_FLAG_NO_BATCH_PANEL 16u /* sym_factor_batch: run the POTRF, TRSM and TRTRI launches of
+#define SYM_FLAG_NO_BATCH_PANEL 16u /* sym_factor_batch / sym_solve_batch: run the launches of
                                        levels of narrow supernodes apart instead of as one fused
-                                       launch per level (SYM_EXPORT_BATCH_PANEL) */
+                                       launch per level (SYM_EXPORT_BATCH_PANEL, _FWD_PANEL,
+                                       _BWD_PANEL) */
 
 typedef struct sym_handle_s *sym_handle;
 
@@ -407,6 +408,12 @@ int sym_get_factor_host(sym_handle h, double *Lx_host);
  * role 0: other launches. head: for roles 1 and 2 the index of the level's role-1 launch, else
  * -1. sym_autotune may return a level to its separate launches. */
 #define SYM_EXPORT_BATCH_PANEL 27
+/* The same for the forward and backward solve lists (SYM_EXPORT_FWD_LAUNCHES, _BWD_LAUNCHES):
+ * role 1 on the step launch of a level whose supernodes all have at most 32 columns, on which
+ * sym_solve_batch of FP64 factors runs the level's sums, steps and pushes (forward) or gathers
+ * and steps (backward) in that one launch; role 2 on the level's other launches, then skipped. */
+#define SYM_EXPORT_FWD_PANEL 28
+#define SYM_EXPORT_BWD_PANEL 29
 /* Forward solve by pushes: supernode J writes, per chunk ch of SOLVE_CW = 512 of its columns,
  * the products L_J(r, chunk) y_J(chunk) of its rows r below the diagonal block to a buffer t at
  * tx_J + ch (nrows_J - ncols_J) + (r - ncols_J), tx_J = sum over K < J of

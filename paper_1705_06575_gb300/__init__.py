@@ -59,6 +59,7 @@ EXPORTS = {
     "factor_launches": (19, np.int64), "fwd_launches": (20, np.int64), "bwd_launches": (21, np.int64),
     "tasks": (22, np.int32), "upd_tasks": (23, np.int64), "upd_entries": (24, np.int64),
     "contrib_ptr": (25, np.int64), "contrib": (26, np.int32), "batch_panel": (27, np.int32),
+    "fwd_panel": (28, np.int32), "bwd_panel": (29, np.int32),
 }
 
 

@@ -594,6 +594,12 @@ static int analyze_impl(int64_t n, const int64_t *Ap, const int32_t *Ai, const i
     h->dp.batch_warp = h->plan.batch_warp.data();
     h->dp.batch_panel = (opt.flags & SYM_FLAG_NO_BATCH_PANEL) ? nullptr : h->plan.batch_panel.data();
     h->dp.panel_apart = h->plan.panel_apart.data();
+    if (!(opt.flags & SYM_FLAG_NO_BATCH_PANEL)) {
+      h->dp.fwd_panel = h->plan.fwd_panel.data();
+      h->dp.bwd_panel = h->plan.bwd_panel.data();
+      h->dp.nfwd_panel = (int64_t)h->plan.fwd_panel.size();
+      h->dp.nbwd_panel = (int64_t)h->plan.bwd_panel.size();
+    }
     h->dp.axc = h->d_Axc;
     h->dp.dpos = (const int64_t *)h->d_dpos;
   }
@@ -1022,6 +1028,8 @@ int64_t sym_export(sym_handle h, int32_t what, void *out) {
     EXPB(SYM_EXPORT_UPD_TASKS, upd_tasks, 8)
     EXPB(SYM_EXPORT_UPD_ENTRIES, upd_entries, 8)
     EXPB(SYM_EXPORT_BATCH_PANEL, batch_panel, 4)
+    EXPB(SYM_EXPORT_FWD_PANEL, fwd_panel, 4)
+    EXPB(SYM_EXPORT_BWD_PANEL, bwd_panel, 4)
     static_assert(sizeof(sym::PanelForm) == 16, "panel form record layout");
 #undef EXPB
     default:

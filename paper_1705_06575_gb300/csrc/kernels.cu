@@ -2220,6 +2220,155 @@ __global__ void __launch_bounds__(32 * WT_WARPS) k_dstep_w(const SNode *__restri
   }
 }
 
+// FP64 solve of a batch's narrow levels in one launch per level and direction (the schedule
+// marks them, Plan::fwd_panel / bwd_panel): one warp per (supernode, MW = 32 / G matrices) as in
+// k_panel_b, lane q * MW + m on matrix m, the warp's panels and diagonal-block inverses staged in
+// shared memory (element e of matrix m at e * MP + m) before the kernel waits for its predecessor.
+// Forward, per right-hand side: each column subtracts the products its contribution list names
+// (S_FSUM), the diagonal block is solved with its inverse (S_FSTEP), and the rows below it push
+// their products (S_FPUSH); lanes of a matrix split the columns, then the rows. Backward: each
+// column subtracts the products of the rows below the diagonal block with the solved values
+// there (S_BGATHER; per column in ascending row order), then the diagonal block is solved with
+// the transposed inverse (S_BSTEP). The steps and pushes keep their warp forms' order; the
+// gather's sum runs in plain row order (the warp form adds 32 interleaved partial sums).
+// Lanes l of a warp with l % MW < nm (the lanes of the warp's nm matrices).
+__device__ __forceinline__ unsigned present_lanes(int MW, int nm) {
+  unsigned mask = 0;
+  for (int l = 0; l < 32; ++l)
+    if ((l & (MW - 1)) < nm) mask |= 1u << l;
+  return mask;
+}
+
+template <typename T>
+__device__ __forceinline__ void stage_panel_inverse(T *S, T *Si, int MP, const SNode &sj, const T *Lx,
+                                                    const T *Linv, int32_t mat0, int nm, const Batch &bt) {
+  const int lane = threadIdx.x & 31, np = sj.ncols * sj.nrows, ni = sj.ncols * sj.ncols;
+  for (int mm = 0; mm < nm; ++mm) {
+    const T *src = Lx + (int64_t)(mat0 + mm) * bt.lx + sj.lx;
+    const T *isrc = Linv + (int64_t)(mat0 + mm) * bt.dinv + sj.dx;
+    for (int e = lane; e < np; e += 32) cp_async_elem<sizeof(T)>(S + e * MP + mm, src + e);
+    for (int e = lane; e < ni; e += 32) cp_async_elem<sizeof(T)>(Si + e * MP + mm, isrc + e);
+  }
+  cp_async_wait_all();
+  __syncwarp();
+}
+
+template <typename T, typename V, int G>
+__global__ void __launch_bounds__(32) k_fwd_b(const SNode *__restrict__ sn, const Int4 *__restrict__ tasks,
+                                              const int64_t *__restrict__ cptr, const int32_t *__restrict__ contrib,
+                                              const T *__restrict__ Lx, const T *__restrict__ Linv,
+                                              V *__restrict__ y, V *__restrict__ t, int64_t tsize, int64_t n, int r0,
+                                              int nrhs, int64_t toff, int32_t nmat, int32_t pmax, int32_t ncmax,
+                                              const Batch bt) {
+  constexpr int MW = 32 / G, MP = G == 1 ? 33 : MW;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V *vb = reinterpret_cast<V *>(smem_raw);  // ncmax x MW: y_J after the sums
+  V *ob = vb + (size_t)ncmax * MW;          // ncmax x MW: y_J solved
+  T *S = reinterpret_cast<T *>(ob + (size_t)ncmax * MW);
+  T *Si = S + (size_t)pmax * MP;
+  const int lane = threadIdx.x, m = lane & (MW - 1), q = lane / MW;
+  const int32_t mat0 = blockIdx.y * MW, mat = mat0 + m;
+  const bool act = mat < nmat;
+  const int nm = min(MW, nmat - mat0);
+  const Int4 tk = tasks[toff + blockIdx.x];
+  const SNode sj = sn[tk.a];
+  const int nc = sj.ncols, nr = sj.nrows;
+  stage_panel_inverse(S, Si, MP, sj, Lx, Linv, mat0, nm, bt);
+  pdl_wait_then_trigger<V>();  // y and t are the predecessors' output
+  if (!act) return;  // lanes of absent matrices leave; the warp barriers below name the others
+  const unsigned mask = present_lanes(MW, nm);
+  y += (int64_t)mat * bt.y;
+  t += (int64_t)mat * bt.t;
+  const T *Sm = S + m, *Sim = Si + m;
+  for (int rh = 0; rh < nrhs; ++rh) {
+    V *yq = y + (int64_t)(r0 + rh) * n + sj.first;
+    V *tq = t + (int64_t)rh * tsize;
+    for (int c = q; c < nc; c += G) {  // S_FSUM: y_g minus the sum of its listed products
+      const int64_t g = sj.first + c;
+      V acc = V(0);
+      for (int64_t p = cptr[g]; p < cptr[g + 1]; ++p) acc += tq[contrib[p]];
+      vb[c * MW + m] = yq[c] - acc;
+    }
+    __syncwarp(mask);
+    for (int r = q; r < nc; r += G) {  // S_FSTEP: row r of L_JJ^-1 y_J, two partial sums
+      V a0 = V(0), a1 = V(0);
+      int k = 0;
+      for (; k + 1 <= r; k += 2) {
+        a0 = fma((V)Sim[(k * nc + r) * MP], vb[k * MW + m], a0);
+        a1 = fma((V)Sim[((k + 1) * nc + r) * MP], vb[(k + 1) * MW + m], a1);
+      }
+      if (k <= r) a0 = fma((V)Sim[(k * nc + r) * MP], vb[k * MW + m], a0);
+      const V o = a0 + a1;
+      yq[r] = o;
+      ob[r * MW + m] = o;
+    }
+    __syncwarp(mask);
+    for (int rr = nc + q; rr < nr; rr += G) {  // S_FPUSH: four partial sums over the columns
+      V a0 = V(0), a1 = V(0), a2 = V(0), a3 = V(0);  // columns c with c % 4 = 0, 1, 2, 3
+      const T *lr = Sm + rr * MP;
+      int c = 0;
+      for (; c + 3 < nc; c += 4) {
+        a0 = fma((V)lr[c * nr * MP], ob[c * MW + m], a0);
+        a1 = fma((V)lr[(c + 1) * nr * MP], ob[(c + 1) * MW + m], a1);
+        a2 = fma((V)lr[(c + 2) * nr * MP], ob[(c + 2) * MW + m], a2);
+        a3 = fma((V)lr[(c + 3) * nr * MP], ob[(c + 3) * MW + m], a3);
+      }
+      if (c < nc) a0 = fma((V)lr[c * nr * MP], ob[c * MW + m], a0);
+      if (c + 1 < nc) a1 = fma((V)lr[(c + 1) * nr * MP], ob[(c + 1) * MW + m], a1);
+      if (c + 2 < nc) a2 = fma((V)lr[(c + 2) * nr * MP], ob[(c + 2) * MW + m], a2);
+      tq[sj.tx + (rr - nc)] = (a0 + a1) + (a2 + a3);
+    }
+    __syncwarp(mask);
+  }
+}
+
+template <typename T, typename V, int G>
+__global__ void __launch_bounds__(32) k_bwd_b(const SNode *__restrict__ sn, const int32_t *__restrict__ rows,
+                                              const Int4 *__restrict__ tasks, const T *__restrict__ Lx,
+                                              const T *__restrict__ Linv, V *__restrict__ y, int64_t n, int r0,
+                                              int nrhs, int64_t toff, int32_t nmat, int32_t pmax, int32_t ncmax,
+                                              const Batch bt) {
+  constexpr int MW = 32 / G, MP = G == 1 ? 33 : MW;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V *zb = reinterpret_cast<V *>(smem_raw);  // ncmax x MW: z_J after the gather
+  T *S = reinterpret_cast<T *>(zb + (size_t)2 * ncmax * MW);
+  T *Si = S + (size_t)pmax * MP;
+  const int lane = threadIdx.x, m = lane & (MW - 1), q = lane / MW;
+  const int32_t mat0 = blockIdx.y * MW, mat = mat0 + m;
+  const bool act = mat < nmat;
+  const int nm = min(MW, nmat - mat0);
+  const Int4 tk = tasks[toff + blockIdx.x];
+  const SNode sj = sn[tk.a];
+  const int nc = sj.ncols, nr = sj.nrows;
+  const int32_t *R = rows + sj.rowp;
+  stage_panel_inverse(S, Si, MP, sj, Lx, Linv, mat0, nm, bt);
+  pdl_wait_then_trigger<V>();  // z is the predecessors' output
+  if (!act) return;
+  const unsigned mask = present_lanes(MW, nm);
+  y += (int64_t)mat * bt.y;
+  const T *Sm = S + m, *Sim = Si + m;
+  for (int rh = 0; rh < nrhs; ++rh) {
+    V *yq = y + (int64_t)(r0 + rh) * n;
+    for (int c = q; c < nc; c += G) {  // S_BGATHER
+      V sa = V(0);
+      for (int rr = nc; rr < nr; ++rr) sa = fma((V)Sm[(c * nr + rr) * MP], yq[R[rr]], sa);
+      zb[c * MW + m] = yq[sj.first + c] - sa;
+    }
+    __syncwarp(mask);
+    for (int r = q; r < nc; r += G) {  // S_BSTEP: row r of L_JJ^-T z_J, two partial sums
+      V a0 = V(0), a1 = V(0);
+      int k = r;
+      for (; k + 1 < nc; k += 2) {
+        a0 = fma((V)Sim[(r * nc + k) * MP], zb[k * MW + m], a0);
+        a1 = fma((V)Sim[(r * nc + k + 1) * MP], zb[(k + 1) * MW + m], a1);
+      }
+      if (k < nc) a0 = fma((V)Sim[(r * nc + k) * MP], zb[k * MW + m], a0);
+      yq[sj.first + r] = a0 + a1;
+    }
+    __syncwarp(mask);
+  }
+}
+
 template <typename T, int TB>
 constexpr size_t trsm_smem() { return sizeof(T) * (TB * (TB + 1) + TB * (NB + 1) + TB); }
 template <int TB>
@@ -2405,6 +2554,15 @@ cudaError_t prepare_solve() {
   cudaError_t e = cudaFuncSetAttribute(k_fstep<T, V, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)step_smem<V, NB>());
   if (e != cudaSuccess) return e;
+  if constexpr (std::is_same<T, double>::value && std::is_same<V, double>::value) {
+    const void *k[8] = {(const void *)k_fwd_b<T, V, 1>, (const void *)k_fwd_b<T, V, 2>, (const void *)k_fwd_b<T, V, 4>,
+                        (const void *)k_fwd_b<T, V, 8>, (const void *)k_bwd_b<T, V, 1>, (const void *)k_bwd_b<T, V, 2>,
+                        (const void *)k_bwd_b<T, V, 4>, (const void *)k_bwd_b<T, V, 8>};
+    for (const void *f : k) {
+      e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, PANEL_SMEM_HARD);
+      if (e != cudaSuccess) return e;
+    }
+  }
   return cudaFuncSetAttribute(k_fgather<T, V>, cudaFuncAttributeNonPortableClusterSizeAllowed, 0);
 }
 
@@ -2573,6 +2731,42 @@ cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, co
   return cudaGetLastError();
 }
 
+// A batch's fused narrow solve levels (FP64): the role of launch li of a solve list (forms: the
+// plan's marks for that list, nform entries; a pruned list never matches them).
+inline const PanelForm *solve_panel(const PanelForm *forms, int64_t nform, size_t nlist, size_t li, unsigned nb,
+                                    bool fp64) {
+  if (!fp64 || nb < 2 || !forms || (int64_t)nlist != nform) return nullptr;
+  return forms[li].role == PANEL_NONE ? nullptr : &forms[li];
+}
+
+template <typename T, typename V>
+cudaError_t launch_solve_b(bool forward, const DevPlan &d, const PanelForm &pf, unsigned g, unsigned nb,
+                           cudaStream_t st, const T *Lx, const T *Linv, V *y, V *tbuf, int r0, int nr, int64_t off,
+                           const Batch &bt) {
+  if constexpr (std::is_same<T, double>::value && std::is_same<V, double>::value) {
+    const int lanes = solve_panel_lanes(pf.pmax, pf.ncmax);
+    const size_t smem = (size_t)solve_panel_bytes(pf.pmax, pf.ncmax, lanes);
+#define SYM_SOLVE_B(G)                                                                                          \
+  case G:                                                                                                       \
+    return forward ? launch_pdl(k_fwd_b<T, V, G>, dim3(g, (nb + 32 / G - 1) / (32 / G)), 32, smem, st, d.sn,    \
+                                d.tasks, d.cptr, d.contrib, Lx, Linv, y, tbuf, d.tsize, d.n, r0, nr, off,       \
+                                (int32_t)nb, pf.pmax, pf.ncmax, bt)                                             \
+                   : launch_pdl(k_bwd_b<T, V, G>, dim3(g, (nb + 32 / G - 1) / (32 / G)), 32, smem, st, d.sn,    \
+                                d.rows, d.tasks, Lx, Linv, y, d.n, r0, nr, off, (int32_t)nb, pf.pmax, pf.ncmax, \
+                                bt);
+    switch (lanes) {
+      SYM_SOLVE_B(1)
+      SYM_SOLVE_B(2)
+      SYM_SOLVE_B(4)
+      SYM_SOLVE_B(8)
+      default:
+        break;
+    }
+#undef SYM_SOLVE_B
+  }
+  return cudaErrorInvalidValue;
+}
+
 template <typename T, typename V>
 cudaError_t run_sweeps(const DevPlan &d, const std::vector<Launch> &fwd, const std::vector<Launch> &bwd,
                        const T *Lx, const T *Linv, int nrhs, V *y, cudaStream_t st, LaunchTrace *trace,
@@ -2582,9 +2776,19 @@ cudaError_t run_sweeps(const DevPlan &d, const std::vector<Launch> &fwd, const s
   V *tbuf = reinterpret_cast<V *>(d.t);
   for (int r0 = 0; r0 < nrhs; r0 += MAXRHS) {
     const int nr = nrhs - r0 < MAXRHS ? nrhs - r0 : MAXRHS;
-    for (const Launch &L : fwd) {
+    constexpr bool fp64 = std::is_same<T, double>::value && std::is_same<V, double>::value;
+    for (size_t li = 0; li < fwd.size(); ++li) {
+      const Launch &L = fwd[li];
       const unsigned g = (unsigned)L.count;
       cudaError_t e = cudaSuccess;
+      // a batch's fused narrow level: its step launch runs the sums, steps and pushes
+      if (const PanelForm *pf = solve_panel(d.fwd_panel, d.nfwd_panel, fwd.size(), li, nb, fp64)) {
+        if (pf->role == PANEL_FUSED)
+          e = launch_solve_b<T, V>(true, d, *pf, g, nb, st, Lx, Linv, y, tbuf, r0, nr, L.off, bt);
+        if (e != cudaSuccess) return e;
+        trace_mark(trace, L.kind, st);
+        continue;
+      }
       switch (L.kind) {
         case S_FGATHER: {
           cudaLaunchConfig_t cfg = {};
@@ -2648,9 +2852,17 @@ cudaError_t run_sweeps(const DevPlan &d, const std::vector<Launch> &fwd, const s
       if (e != cudaSuccess) return e;
       trace_mark(trace, L.kind, st);
     }
-    for (const Launch &L : bwd) {
+    for (size_t li = 0; li < bwd.size(); ++li) {
+      const Launch &L = bwd[li];
       const unsigned g = (unsigned)L.count;
       cudaError_t e = cudaSuccess;
+      if (const PanelForm *pf = solve_panel(d.bwd_panel, d.nbwd_panel, bwd.size(), li, nb, fp64)) {
+        if (pf->role == PANEL_FUSED)
+          e = launch_solve_b<T, V>(false, d, *pf, g, nb, st, Lx, Linv, y, tbuf, r0, nr, L.off, bt);
+        if (e != cudaSuccess) return e;
+        trace_mark(trace, L.kind, st);
+        continue;
+      }
       switch (L.kind) {
         case S_BGATHER:
           if (nb > 1 && L.tb == SMALL_TB) {

@@ -37,6 +37,9 @@ struct DevPlan {
                                            // narrow levels (Plan::batch_panel); null: none
   const int8_t *panel_apart = nullptr;     // HOST array (Plan::panel_apart): levels the autotuner
                                            // runs as separate launches; null: none
+  const PanelForm *fwd_panel = nullptr;    // HOST arrays (Plan::fwd_panel, bwd_panel): a batch's
+  const PanelForm *bwd_panel = nullptr;    // fused narrow solve levels (FP64); null: none
+  int64_t nfwd_panel = 0, nbwd_panel = 0;  // their lengths (the solve lists' launch counts)
   const int8_t *variant[2] = {nullptr, nullptr};  // HOST arrays, one entry per factor launch,
                                      // [0] for one matrix, [1] for batches: 1 runs the launch's
                                      // alternative kernel form (see factor_launch_has_alternative),

@@ -45,6 +45,18 @@ inline int panel_lanes(int64_t pmax, int64_t ncmax, bool f32) {
     if (panel_smem_bytes(pmax, ncmax, f32, g) <= PANEL_SMEM_SOFT) return g;
   return panel_smem_bytes(pmax, ncmax, f32, 8) <= PANEL_SMEM_HARD ? 8 : 0;
 }
+// The same for a batch's FP64 solve on such levels (k_fwd_b, k_bwd_b): each warp holds its
+// matrices' panels and diagonal-block inverses (pmax + ncmax^2 elements per matrix) and two
+// vectors of ncmax values per matrix.
+inline int64_t solve_panel_bytes(int64_t pmax, int64_t ncmax, int g) {
+  const int64_t stride = g == 1 ? 33 : 32 / g;
+  return stride * (pmax + ncmax * ncmax) * 8 + (32 / g) * 2 * ncmax * 8;
+}
+inline int solve_panel_lanes(int64_t pmax, int64_t ncmax) {
+  for (int g = 1; g <= 8; g *= 2)
+    if (solve_panel_bytes(pmax, ncmax, g) <= PANEL_SMEM_SOFT) return g;
+  return solve_panel_bytes(pmax, ncmax, 8) <= PANEL_SMEM_HARD ? 8 : 0;
+}
 // Role of a factor launch in a batch's fused narrow levels (PanelForm::role).
 constexpr int32_t PANEL_NONE = 0, PANEL_FUSED = 1, PANEL_COVERED = 2;
 struct PanelForm {
@@ -199,6 +211,11 @@ struct Plan {
                                        // autotuner found the level faster as separate launches
   std::vector<Launch> fwd_launches;
   std::vector<Launch> bwd_launches;
+  // Batches (FP64): per forward / backward solve launch, the fused narrow levels: the level's
+  // S_FSTEP (forward) or S_BSTEP (backward) launch is PANEL_FUSED and runs the level's sums,
+  // steps and pushes (forward) or gathers and steps (backward) in one launch; its other launches
+  // are PANEL_COVERED.
+  std::vector<PanelForm> fwd_panel, bwd_panel;
   // Forward solve by pushes: t holds tsize entries per right-hand side; the contribution list of
   // column g, contrib[contrib_ptr[g] .. contrib_ptr[g+1]), names the entries of t that column g
   // subtracts (every row g below the diagonal block of a supernode, once per column chunk), in

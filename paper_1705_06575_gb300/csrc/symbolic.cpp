@@ -862,6 +862,31 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
       }
     }
   }
+  // Batches: the solve launches of levels of narrow supernodes whose panels fit k_fwd_b and
+  // k_bwd_b become one launch per level and direction (see solve_panel_lanes).
+  {
+    auto mark = [&](const std::vector<Launch> &list, std::vector<PanelForm> &form, int32_t step_kind) {
+      form.assign(list.size(), PanelForm{PANEL_NONE, 0, 0, -1});
+      for (int32_t l = 0; l < nlev; ++l) {
+        int64_t pmax = 0, ncmax = 0;
+        for (int32_t t = P.levelptr[l]; t < P.levelptr[l + 1]; ++t) {
+          const SNode &sj = P.snodes[P.levellist[t]];
+          pmax = std::max<int64_t>(pmax, (int64_t)sj.nrows * sj.ncols);
+          ncmax = std::max<int64_t>(ncmax, sj.ncols);
+        }
+        if (P.levelptr[l + 1] == P.levelptr[l] || !small_level(l) || solve_panel_lanes(pmax, ncmax) == 0) continue;
+        std::vector<size_t> step, other;
+        for (size_t li = 0; li < list.size(); ++li)
+          if (list[li].level == l) (list[li].kind == step_kind ? step : other).push_back(li);
+        if (step.size() != 1) continue;
+        const int32_t head = (int32_t)step[0];
+        form[head] = PanelForm{PANEL_FUSED, (int32_t)pmax, (int32_t)ncmax, head};
+        for (size_t li : other) form[li] = PanelForm{PANEL_COVERED, 0, 0, head};
+      }
+    };
+    mark(P.fwd_launches, P.fwd_panel, S_FSTEP);
+    mark(P.bwd_launches, P.bwd_panel, S_BSTEP);
+  }
   for (auto &v : P.variant) v.assign(P.factor_launches.size(), 0);
   // Default form of a batch's full-tile FP64 update launches: one warp per (tile, matrix) when
   // the launch's entries are small (at most BATCH_WARP_ELEMS output elements on average: the

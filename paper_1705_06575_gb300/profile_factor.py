@@ -64,6 +64,24 @@ def level_summary(s, ms):
             "two_stream_bound_ms": float(max(tail.values())), "levels": levels}
 
 
+def solve_level_summary(s, ms):
+    """Per level and kernel kind, the milliseconds of one profiled solve of up to 8 right-hand
+    sides (ms: sym_profile_launches(h, 1): the permutation in, the forward and backward launch
+    lists, the permutation out)."""
+    rows = {}
+    lists = [s.export("fwd_launches").reshape(-1, 5), s.export("bwd_launches").reshape(-1, 5)]
+    if len(ms) != 2 + sum(len(x) for x in lists):
+        return {"error": f"{len(ms)} timed launches"}
+    i = 1
+    for raw in lists:
+        for rec in raw:
+            kind, level = int(rec[0] & 0xffffffff), int(rec[0] >> 32)
+            key = f"{level}:{SOLVE_KIND_NAMES.get(kind, kind)}"
+            rows[key] = round(rows.get(key, 0.0) + float(ms[i]), 3)
+            i += 1
+    return rows
+
+
 def main(argv=None):
     import torch
 
@@ -118,6 +136,7 @@ def main(argv=None):
             if B is not None:
                 out["solve_kinds_ms"] = {name: round(sym_profile_read(s.h, k)[0], 3)
                                          for k, name in SOLVE_KIND_NAMES.items() if sym_profile_read(s.h, k)[1]}
+                out["solve_levels"] = solve_level_summary(s, sym_profile_launches(s.h, 1))
         out.update({"steps": args.repeat + 1 + (1 if args.levels else 0), "status": "ok"})
         print(json.dumps(out))
         s.close()

@@ -32,6 +32,8 @@ class Sched:
         self.ue = np.stack([ue[:, 0] & 0xffffffff, ue[:, 0] >> 32, ue[:, 1] & 0xffffffff, ue[:, 1] >> 32,
                             ue[:, 2], ue[:, 3], ue[:, 4]], 1)
         self.panel = s.export("batch_panel").reshape(-1, 4)  # {role, pmax, ncmax, head} per factor launch
+        self.spanel = {"fwd_launches": s.export("fwd_panel").reshape(-1, 4),
+                       "bwd_launches": s.export("bwd_panel").reshape(-1, 4)}
         self.cptr = s.export("contrib_ptr")
         self.contrib = s.export("contrib")
         # offset of each supernode's pushed products: its rows below the diagonal block, once per
@@ -244,8 +246,10 @@ def emulate_factor(sc, panels, store, batch=False):
         assert not (wi & (wj | rj)) and not (ri & wj), ("concurrent launches conflict", i, j)
 
 
-def emulate_solve(sc, store, y):
-    """y: dict index -> value (permuted numbering), updated in place."""
+def emulate_solve(sc, store, y, batch=False):
+    """y: dict index -> value (permuted numbering), updated in place. batch: the launches as a
+    batch runs them (a fused narrow level's step launch does the level's sums, steps and pushes
+    or gathers and steps; its other launches do nothing)."""
     def Lv(j, r, c):
         return store[("L", j, r, c)]
 
@@ -256,13 +260,43 @@ def emulate_solve(sc, store, y):
         for li, (kind, off, count, _, _) in enumerate(sc.launches[name]):
             kind = int(kind)
             cluster_form = int(sc.cluster[name][li]) == 4
+            role = int(sc.spanel[name][li, 0]) if batch else PANEL_NONE
             L = Launch()
+            if role == PANEL_COVERED:
+                L.commit(y)
+                continue
             for t in range(int(off), int(off + count)):
                 j, ti, tc, _ = (int(v) for v in sc.tasks[t])
                 f, nc, nr, ncb = sc.J(j)
                 R = sc.rows[sc.rowptr[j]:sc.rowptr[j + 1]]
                 tsz = lambda s: min(NB, nc - s * NB)
-                if kind == S_FGATHER:
+                if role == PANEL_FUSED:
+                    assert ncb == 1 and nc <= 32 and nr * nc <= sc.spanel[name][li, 1]
+                    Inv = np.array([[Iv(j, 0, a, b) for b in range(nc)] for a in range(nc)])
+                    if kind == S_FSTEP:
+                        v = []
+                        for c in range(nc):
+                            keys = [("t", int(e)) for e in sc.contrib[sc.cptr[f + c]:sc.cptr[f + c + 1]]]
+                            for k in keys + [f + c]:
+                                L.read(t, k)
+                            v.append(y[f + c] - sum(y[k] for k in keys))
+                        z = Inv @ np.array(v)
+                        for c in range(nc):
+                            L.write(t, f + c, z[c])
+                        for r in range(nc, nr):
+                            L.write(t, ("t", int(sc.tx[j]) + (r - nc)), sum(Lv(j, r, c) * z[c] for c in range(nc)))
+                    else:
+                        assert kind == S_BSTEP
+                        v = []
+                        for c in range(nc):
+                            for r in range(nc, nr):
+                                L.read(t, int(R[r]))
+                            L.read(t, f + c)
+                            v.append(y[f + c] - sum(Lv(j, r, c) * y[int(R[r])] for r in range(nc, nr)))
+                        z = Inv.T @ np.array(v)
+                        for c in range(nc):
+                            L.write(t, f + c, z[c])
+                elif kind == S_FGATHER:
                     bj, ut = ti, tc
                     cb = bj * NB
                     acc = {f + cb + r: y[f + cb + r] for r in range(min(NB, nc - cb))}
@@ -404,7 +438,7 @@ def test_schedule_emulation_reproduces_oracle(maker, batch):
     # solve with one right-hand side in the permuted space
     b = np.random.default_rng(9).standard_normal(M.n)
     y = {k: b[o.perm[k]] for k in range(M.n)}
-    emulate_solve(sc, store, y)
+    emulate_solve(sc, store, y, batch)
     x = np.zeros(M.n)
     for k in range(M.n):
         x[o.perm[k]] = y[k]
@@ -642,3 +676,48 @@ def test_batch_panel_marks(maker):
         if eligible:
             fused_levels.add(lv)
     assert fused_levels  # every pattern here has narrow levels at its leaves
+
+
+@pytest.mark.parametrize("maker", [
+    lambda: w.dd2d9(128, np.random.default_rng(2000)),                       # the batched pattern
+    lambda: w.laplace2d5(30, np.random.default_rng(1)),
+    lambda: w.conduct3d(10, np.random.default_rng(3), "star"),
+])
+def test_solve_panel_marks(maker):
+    """In both solve lists, every level whose supernodes all have at most 32 columns and whose
+    panels and inverses fit the fused solve kernels has its step launch marked fused (with the
+    level's largest panel and widest supernode) and its other launches marked covered."""
+    M = maker()
+    s = S.Solver(M.n, M.Ap, M.Ai, M.perm, host_only=True)
+    sc = Sched(s)
+    level = s.export("level")
+    nc = np.diff(sc.sup)
+    nr = np.diff(sc.rowptr)
+
+    def lanes(pmax, ncmax):
+        def smem(g):
+            return (33 if g == 1 else 32 // g) * (pmax + ncmax * ncmax) * 8 + 32 // g * 2 * ncmax * 8
+        for g in (1, 2, 4, 8):
+            if smem(g) <= 36 * 1024:
+                return g
+        return 8 if smem(8) <= 56 * 1024 else 0
+
+    nfused = 0
+    for name, step in (("fwd_launches", S_FSTEP), ("bwd_launches", S_BSTEP)):
+        raw = s.export(name).reshape(-1, 5)
+        kind, lev = raw[:, 0] & 0xffffffff, raw[:, 0] >> 32
+        for lv in range(int(level.max()) + 1):
+            sel = level == lv
+            pmax, ncmax = int((nc * nr)[sel].max()), int(nc[sel].max())
+            steps = [li for li in np.nonzero(lev == lv)[0] if kind[li] == step]
+            eligible = ncmax <= 32 and lanes(pmax, ncmax) > 0 and len(steps) == 1
+            for li in np.nonzero(lev == lv)[0]:
+                role, pm, nm, hd = (int(v) for v in sc.spanel[name][li])
+                if not eligible:
+                    assert role == PANEL_NONE
+                elif li == steps[0]:
+                    assert (role, pm, nm, hd) == (PANEL_FUSED, pmax, ncmax, li)
+                    nfused += 1
+                else:
+                    assert (role, hd) == (PANEL_COVERED, steps[0])
+    assert nfused >= 2
