@@ -592,6 +592,7 @@ static int analyze_impl(int64_t n, const int64_t *Ap, const int32_t *Ai, const i
     h->dp.piv = h->d_piv;
     for (int c = 0; c < 2; ++c) h->dp.variant[c] = h->plan.variant[c].data();
     h->dp.batch_warp = h->plan.batch_warp.data();
+    h->dp.batch_lanes = h->plan.batch_lanes.data();
     h->dp.batch_panel = (opt.flags & SYM_FLAG_NO_BATCH_PANEL) ? nullptr : h->plan.batch_panel.data();
     h->dp.panel_apart = h->plan.panel_apart.data();
     if (!(opt.flags & SYM_FLAG_NO_BATCH_PANEL)) {

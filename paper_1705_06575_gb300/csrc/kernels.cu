@@ -1728,6 +1728,60 @@ __global__ void __launch_bounds__(32 * WT_WARPS) k_update_wg(const SNode *__rest
   }
 }
 
+// Lanes l of a warp with l % MW < nm (the lanes of the warp's nm matrices).
+__device__ __forceinline__ unsigned present_lanes(int MW, int nm) {
+  unsigned mask = 0;
+  for (int l = 0; l < 32; ++l)
+    if ((l & (MW - 1)) < nm) mask |= 1u << l;
+  return mask;
+}
+
+// The same for a batch's small tiles with lanes mapped to matrices: one warp per (tile, MW =
+// 32 / G matrices), WT_WARPS matrix groups per CTA; lane q * MW + m takes the elements q, q + G,
+// ... of every entry for matrix m (consecutive elements are consecutive rows, so the G lanes of
+// a matrix read neighbouring operands). The small-tile levels of a batch have entries of a few
+// dozen elements and tiles of a few entries; a warp per (tile, matrix) leaves most lanes idle and
+// spends its time on latency. Element by element the operations of k_update_wb, in its order
+// (bit-identical).
+template <typename T, int G>
+__global__ void __launch_bounds__(32 * WT_WARPS) k_update_mb(const SNode *__restrict__ sn,
+                                                             const UpdTask *__restrict__ tasks,
+                                                             const UpdEntry *__restrict__ ents,
+                                                             const int32_t *__restrict__ rel, T *__restrict__ Lx,
+                                                             int64_t toff, int32_t nmat, const Batch bt) {
+  constexpr int MW = 32 / G;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, m = lane & (MW - 1), q = lane / MW;
+  const int32_t mat0 = (blockIdx.y * WT_WARPS + w) * MW;
+  if (mat0 + m >= nmat) return;  // lanes of absent matrices leave; the barriers name the others
+  const unsigned mask = present_lanes(MW, nmat - mat0);
+  Lx += (int64_t)(mat0 + m) * bt.lx;
+  const UpdTask t = tasks[toff + blockIdx.x];
+  const SNode sj = sn[t.J];
+  const int64_t rb = d_row_tile_base(t.bi, sj.ncols, sj.ncb);
+  const int cb = t.bj * NB;
+  const bool diag = t.bi == t.bj;
+  T *C = Lx + sj.lx + (int64_t)cb * sj.nrows + rb;
+  for (int64_t e = t.e0; e < t.e1; ++e) {
+    const UpdEntry E = ents[e];
+    const SNode sk = sn[E.K];
+    const int64_t ld = sk.nrows;
+    const int cnt = diag ? E.m * (E.m + 1) / 2 : E.m * E.n;
+    for (int el = q; el < cnt; el += G) {
+      int a, b;
+      if (diag) tri_decode(el, a, b);
+      else a = el % E.m, b = el / E.m;
+      const int pr = rel[E.relr + a] - (int)rb, pc = rel[E.relc + b] - cb;
+      const T *pa = Lx + sk.lx + E.r_lo + a, *pb = Lx + sk.lx + E.c_lo + b;
+      T *cp = C + (int64_t)pc * sj.nrows + pr;
+      T r = *cp;
+#pragma unroll 4
+      for (int k = 0; k < sk.ncols; ++k) r = fma(-pa[k * ld], pb[k * ld], r);
+      *cp = r;
+    }
+    __syncwarp(mask);  // an entry's writes before the next entry's reads of the same elements
+  }
+}
+
 // TRSM of a batch's narrow tiles (ts <= SMALL_TILE columns, <= NB rows): one warp per (tile,
 // matrix), four matrices per CTA, each warp's L_ss and 32-row chunk of the tile in its own shared
 // memory. Within a chunk the rows are spread over 32 / rows column groups as in k_trsm and each
@@ -2231,14 +2285,6 @@ __global__ void __launch_bounds__(32 * WT_WARPS) k_dstep_w(const SNode *__restri
 // there (S_BGATHER; per column in ascending row order), then the diagonal block is solved with
 // the transposed inverse (S_BSTEP). The steps and pushes keep their warp forms' order; the
 // gather's sum runs in plain row order (the warp form adds 32 interleaved partial sums).
-// Lanes l of a warp with l % MW < nm (the lanes of the warp's nm matrices).
-__device__ __forceinline__ unsigned present_lanes(int MW, int nm) {
-  unsigned mask = 0;
-  for (int l = 0; l < 32; ++l)
-    if ((l & (MW - 1)) < nm) mask |= 1u << l;
-  return mask;
-}
-
 template <typename T>
 __device__ __forceinline__ void stage_panel_inverse(T *S, T *Si, int MP, const SNode &sj, const T *Lx,
                                                     const T *Linv, int32_t mat0, int nm, const Batch &bt) {
@@ -2578,6 +2624,26 @@ bool factor_launch_has_alternative(const Launch &L, int32_t nbatch, bool fp64) {
          (small && (L.kind == K_POTRF || L.kind == K_TRTRI));
 }
 
+// A batch's small-tile update with lanes mapped to matrices (k_update_mb, G lanes per matrix).
+template <typename T>
+cudaError_t launch_update_mb(int lanes, unsigned g, unsigned nb, cudaStream_t s, int prio, const DevPlan &d, T *Lx,
+                             int64_t off, const Batch &bt) {
+#define SYM_UPD_MB(G)                                                                                           \
+  case G:                                                                                                       \
+    return launch_prio(k_update_mb<T, G>, dim3(g, (nb + WT_WARPS * (32 / G) - 1) / (WT_WARPS * (32 / G))),      \
+                       32 * WT_WARPS, 0, s, prio, d.sn, d.upd_tasks, d.upd_entries, d.rel, Lx, off, (int32_t)nb, \
+                       bt);
+  switch (lanes) {
+    SYM_UPD_MB(1)
+    SYM_UPD_MB(2)
+    SYM_UPD_MB(4)
+    SYM_UPD_MB(8)
+    default:
+      return cudaErrorInvalidValue;
+  }
+#undef SYM_UPD_MB
+}
+
 // One fused narrow-level launch of a batch (k_panel_b with the level's lanes per matrix).
 template <typename T>
 cudaError_t launch_panel_b(const DevPlan &d, const PanelForm &pf, unsigned g, unsigned nb, cudaStream_t s, int prio,
@@ -2652,7 +2718,9 @@ cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, co
             e = launch_prio(k_update_f32, dim3(g, nb), F32_THREADS, 0, s, prio, d.sn, d.upd_tasks, d.upd_entries,
                             d.rel, Lx, L.off, bt);
         }
-        else if (small && nb > 1 && !alt)  // a batch: one warp per (tile, matrix)
+        else if (small && nb > 1 && !alt && d.batch_lanes && d.batch_lanes[li] > 0)  // lanes = matrices
+          e = launch_update_mb<T>(d.batch_lanes[li], g, nb, s, prio, d, Lx, L.off, bt);
+        else if (small && nb > 1)  // a batch: one warp per (tile, matrix)
           e = launch_prio(k_update_wb<T>, dim3(g, (nb + WT_WARPS - 1) / WT_WARPS), 32 * WT_WARPS, 0, s, prio,
                           d.sn, d.upd_tasks, d.upd_entries, d.rel, Lx, L.off, (int32_t)nb, bt);
         else if (!small && nb > 1 && (d.batch_warp && d.batch_warp[li]) != alt)  // small entries of a batch

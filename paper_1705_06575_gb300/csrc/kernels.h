@@ -33,6 +33,8 @@ struct DevPlan {
   const int8_t *batch_warp = nullptr;  // HOST array, one per factor launch: a batch's default form
                                        // of the launch is one warp per (tile, matrix) (full-tile
                                        // FP64 updates with small entries)
+  const int8_t *batch_lanes = nullptr;     // HOST array, one per factor launch: a batch's lanes
+                                           // per matrix for small-tile updates (Plan::batch_lanes)
   const PanelForm *batch_panel = nullptr;  // HOST array, one per factor launch: a batch's fused
                                            // narrow levels (Plan::batch_panel); null: none
   const int8_t *panel_apart = nullptr;     // HOST array (Plan::panel_apart): levels the autotuner

@@ -206,6 +206,9 @@ struct Plan {
                                       // [0] for one matrix, [1] for batches
   std::vector<int8_t> batch_warp;     // per factor launch: 1 if a batch's default form of this
                                       // full-tile update is one warp per (tile, matrix)
+  std::vector<int8_t> batch_lanes;     // per factor launch: for a small-tile update, a batch's
+                                      // lanes per matrix in the lanes-to-matrices form (1, 2, 4
+                                      // or 8), else 0
   std::vector<PanelForm> batch_panel;  // per factor launch: fused narrow levels of batches
   std::vector<int8_t> panel_apart;     // per factor launch, on PANEL_FUSED ones: 1 if the
                                        // autotuner found the level faster as separate launches

@@ -891,7 +891,26 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
   // Default form of a batch's full-tile FP64 update launches: one warp per (tile, matrix) when
   // the launch's entries are small (at most BATCH_WARP_ELEMS output elements on average: the
   // one-CTA form then spends its time staging and waiting at barriers), else one CTA per tile.
+  // Small-tile update launches of a batch run with lanes mapped to matrices (k_update_mb), about
+  // three elements of an average entry per lane: G = the largest power of two <= mean / 3, 1..8.
   P.batch_warp.assign(P.factor_launches.size(), 0);
+  P.batch_lanes.assign(P.factor_launches.size(), 0);
+  for (size_t li = 0; li < P.factor_launches.size(); ++li) {
+    const Launch &L = P.factor_launches[li];
+    if (L.kind != K_UPDATE || L.tb != SMALL_TILE) continue;
+    double elems = 0.0, cnt = 0.0;
+    for (int64_t t = L.off; t < L.off + L.count; ++t) {
+      const UpdTask &u = P.upd_tasks[t];
+      for (int64_t e = u.e0; e < u.e1; ++e) {
+        const UpdEntry &E = P.upd_entries[e];
+        elems += u.bi == u.bj ? 0.5 * E.m * (E.m + 1) : (double)E.m * E.n;
+        cnt += 1.0;
+      }
+    }
+    int g = 1;
+    while (g < 8 && cnt > 0.0 && 2 * g * 3.0 * cnt <= elems) g *= 2;
+    P.batch_lanes[li] = (int8_t)g;
+  }
   for (size_t li = 0; li < P.factor_launches.size(); ++li) {
     const Launch &L = P.factor_launches[li];
     if (L.kind != K_UPDATE || L.tb == SMALL_TILE) continue;
