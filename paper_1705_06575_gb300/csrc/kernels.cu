@@ -1977,6 +1977,41 @@ __device__ __forceinline__ void cp_async_elem(void *smem_dst, const void *gsrc) 
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// Copies between global memory (np contiguous elements per matrix, matrix mm's at
+// base + mm * mstride, mm < nm) and a warp's lanes-to-matrices layout (element e of matrix mm at
+// S[e * MP + mm]). One lane per matrix (G = 1, MP = 33): consecutive lanes on consecutive
+// elements of one matrix (coalesced, and the padded rows keep the shared accesses apart). G > 1
+// (MP = MW): consecutive lanes on consecutive shared addresses, the MW matrices fastest (with a
+// stride of MW elements the first mapping would put the lanes on few banks).
+template <typename T, int G>
+__device__ __forceinline__ void stage_in(T *S, const T *base, int64_t mstride, int np, int nm) {
+  constexpr int MW = 32 / G, MP = G == 1 ? 33 : MW;
+  const int lane = threadIdx.x & 31;
+  if constexpr (G == 1) {
+    for (int mm = 0; mm < nm; ++mm)
+      for (int e = lane; e < np; e += 32) cp_async_elem<sizeof(T)>(S + e * MP + mm, base + mm * mstride + e);
+  } else {
+    for (int i = lane; i < np * MW; i += 32) {
+      const int mm = i & (MW - 1);
+      if (mm < nm) cp_async_elem<sizeof(T)>(S + i, base + mm * mstride + i / MW);
+    }
+  }
+}
+template <typename T, int G>
+__device__ __forceinline__ void stage_out(T *base, int64_t mstride, const T *S, int np, int nm) {
+  constexpr int MW = 32 / G, MP = G == 1 ? 33 : MW;
+  const int lane = threadIdx.x & 31;
+  if constexpr (G == 1) {
+    for (int mm = 0; mm < nm; ++mm)
+      for (int e = lane; e < np; e += 32) base[mm * mstride + e] = S[e * MP + mm];
+  } else {
+    for (int i = lane; i < np * MW; i += 32) {
+      const int mm = i & (MW - 1);
+      if (mm < nm) base[mm * mstride + i / MW] = S[i];
+    }
+  }
+}
+
 template <typename T, int G>
 __global__ void __launch_bounds__(32) k_panel_b(const SNode *__restrict__ sn, const Int4 *__restrict__ tasks,
                                                 T *__restrict__ Lx, T *__restrict__ Linv, long long *status,
@@ -1997,10 +2032,7 @@ __global__ void __launch_bounds__(32) k_panel_b(const SNode *__restrict__ sn, co
   const Int4 t = tasks[toff + blockIdx.x];
   const SNode sj = sn[t.a];
   const int nc = sj.ncols, nr = sj.nrows, np = nc * nr;
-  for (int mm = 0; mm < nm; ++mm) {  // every copy in flight at once
-    const T *src = Lx + (int64_t)(mat0 + mm) * bt.lx + sj.lx;
-    for (int e = lane; e < np; e += 32) cp_async_elem<sizeof(T)>(S + e * MP + mm, src + e);
-  }
+  stage_in<T, G>(S, Lx + (int64_t)mat0 * bt.lx + sj.lx, bt.lx, np, nm);  // every copy in flight at once
   cp_async_wait_all();
   __syncwarp();
   T *const Sm = S + m;     // this lane's matrix: element (r, c) at Sm[c * ld + r * MP]
@@ -2057,10 +2089,7 @@ __global__ void __launch_bounds__(32) k_panel_b(const SNode *__restrict__ sn, co
       if constexpr (F64PIV) xd[(size_t)(rr * (rr - 1) / 2 + j) * MW + m] = 0.0;
     }
   __syncwarp();
-  for (int mm = 0; mm < nm; ++mm) {
-    T *dst = Lx + (int64_t)(mat0 + mm) * bt.lx + sj.lx;
-    for (int e = lane; e < np; e += 32) dst[e] = S[e * MP + mm];
-  }
+  stage_out<T, G>(Lx + (int64_t)mat0 * bt.lx + sj.lx, bt.lx, S, np, nm);
   __syncwarp();
   // inverse of the diagonal block in FP64: x(r, j) for r > j in the FP64 arm at position (j, r)
   // of the panel (above the diagonal, already written out), in the FP32 arm in xd
@@ -2084,12 +2113,11 @@ __global__ void __launch_bounds__(32) k_panel_b(const SNode *__restrict__ sn, co
   }
   const int ts = nc;
   const float rts = 1.0f / (float)ts;  // e / ts for e < ts^2 <= 1024: exact through FP32
-  for (int mm = 0; mm < nm; ++mm) {
-    T *out = Linv + (int64_t)(mat0 + mm) * bt.dinv + sj.dx;
-    for (int e = lane; e < ts * ts; e += 32) {
-      const int c = (int)(((float)e + 0.5f) * rts), rr = e - c * ts;
-      out[e] = rr > c ? (T)xr(rr, c, mm) : rr == c ? (T)dv[c * MW + mm] : T(0);
-    }
+  T *out = Linv + (int64_t)mat0 * bt.dinv + sj.dx;
+  for (int i = lane; i < ts * ts * MW; i += 32) {  // matrices fastest (as stage_out with G > 1)
+    const int mm = i & (MW - 1), e = i / MW;
+    const int c = (int)(((float)e + 0.5f) * rts), rr = e - c * ts;
+    if (mm < nm) out[mm * bt.dinv + e] = rr > c ? (T)xr(rr, c, mm) : rr == c ? (T)dv[c * MW + mm] : T(0);
   }
 }
 
@@ -2285,16 +2313,11 @@ __global__ void __launch_bounds__(32 * WT_WARPS) k_dstep_w(const SNode *__restri
 // there (S_BGATHER; per column in ascending row order), then the diagonal block is solved with
 // the transposed inverse (S_BSTEP). The steps and pushes keep their warp forms' order; the
 // gather's sum runs in plain row order (the warp form adds 32 interleaved partial sums).
-template <typename T>
-__device__ __forceinline__ void stage_panel_inverse(T *S, T *Si, int MP, const SNode &sj, const T *Lx,
-                                                    const T *Linv, int32_t mat0, int nm, const Batch &bt) {
-  const int lane = threadIdx.x & 31, np = sj.ncols * sj.nrows, ni = sj.ncols * sj.ncols;
-  for (int mm = 0; mm < nm; ++mm) {
-    const T *src = Lx + (int64_t)(mat0 + mm) * bt.lx + sj.lx;
-    const T *isrc = Linv + (int64_t)(mat0 + mm) * bt.dinv + sj.dx;
-    for (int e = lane; e < np; e += 32) cp_async_elem<sizeof(T)>(S + e * MP + mm, src + e);
-    for (int e = lane; e < ni; e += 32) cp_async_elem<sizeof(T)>(Si + e * MP + mm, isrc + e);
-  }
+template <typename T, int G>
+__device__ __forceinline__ void stage_panel_inverse(T *S, T *Si, const SNode &sj, const T *Lx, const T *Linv,
+                                                    int32_t mat0, int nm, const Batch &bt) {
+  stage_in<T, G>(S, Lx + (int64_t)mat0 * bt.lx + sj.lx, bt.lx, sj.ncols * sj.nrows, nm);
+  stage_in<T, G>(Si, Linv + (int64_t)mat0 * bt.dinv + sj.dx, bt.dinv, sj.ncols * sj.ncols, nm);
   cp_async_wait_all();
   __syncwarp();
 }
@@ -2319,7 +2342,7 @@ __global__ void __launch_bounds__(32) k_fwd_b(const SNode *__restrict__ sn, cons
   const Int4 tk = tasks[toff + blockIdx.x];
   const SNode sj = sn[tk.a];
   const int nc = sj.ncols, nr = sj.nrows;
-  stage_panel_inverse(S, Si, MP, sj, Lx, Linv, mat0, nm, bt);
+  stage_panel_inverse<T, G>(S, Si, sj, Lx, Linv, mat0, nm, bt);
   pdl_wait_then_trigger<V>();  // y and t are the predecessors' output
   if (!act) return;  // lanes of absent matrices leave; the warp barriers below name the others
   const unsigned mask = present_lanes(MW, nm);
@@ -2387,7 +2410,7 @@ __global__ void __launch_bounds__(32) k_bwd_b(const SNode *__restrict__ sn, cons
   const SNode sj = sn[tk.a];
   const int nc = sj.ncols, nr = sj.nrows;
   const int32_t *R = rows + sj.rowp;
-  stage_panel_inverse(S, Si, MP, sj, Lx, Linv, mat0, nm, bt);
+  stage_panel_inverse<T, G>(S, Si, sj, Lx, Linv, mat0, nm, bt);
   pdl_wait_then_trigger<V>();  // z is the predecessors' output
   if (!act) return;
   const unsigned mask = present_lanes(MW, nm);

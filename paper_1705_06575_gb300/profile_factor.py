@@ -152,6 +152,17 @@ def main(argv=None):
         sym_profile(s.h, SYM_PROFILE_OFF)
         out = level_summary(s, sym_profile_launches(s.h, 0))
         out["workload"] = args.workload
+        if args.solve > 0:  # one profiled solve: milliseconds per level and kernel kind
+            B = torch.from_numpy(np.ascontiguousarray(w.rhs(M.n, args.solve, np.random.default_rng(7)).T)).cuda()
+            X = torch.empty_like(B)
+            sym_solve_multi(s.h, args.solve, B, M.n, X, M.n)
+            torch.cuda.synchronize()
+            sym_profile(s.h, SYM_PROFILE_RESET)
+            sym_profile(s.h, SYM_PROFILE_ON)
+            sym_solve_multi(s.h, args.solve, B, M.n, X, M.n)
+            torch.cuda.synchronize()
+            sym_profile(s.h, SYM_PROFILE_OFF)
+            out["solve_levels"] = solve_level_summary(s, sym_profile_launches(s.h, 1))
         print(json.dumps(out))
     else:
         for _ in range(args.repeat):
