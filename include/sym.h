@@ -205,9 +205,10 @@ int sym_solve_batch(sym_handle h, int32_t nbatch, int32_t nrhs, const double *B,
  * sym_factor), every factor launch that has two kernel forms is timed in both with CUDA events
  * over reps kernel-by-kernel factorizations of the given values, and the faster form is stored
  * in the plan for every later factorization of the handle (the captured graphs are rebuilt).
- * Forms: in a batch, small-tile updates, POTRF, TRSM and TRTRI run one warp per (tile, matrix), four
- * matrices per CTA, or one CTA per tile and matrix, and FP64 updates of full tiles one CTA per
- * tile and matrix or one warp per (tile, matrix) updating the tile in global memory; for one
+ * Forms: in a batch, FP64 updates run with the lanes of a warp on several matrices or one warp
+ * per (tile, matrix) (small tiles, and full tiles with small entries) or one CTA per tile and
+ * matrix (full tiles with large entries); small-tile POTRF, TRSM and TRTRI one warp per (tile,
+ * matrix), four matrices per CTA, or one CTA per tile and matrix; for one
  * matrix, FP64 updates of tiles with many entries run on a thread-block cluster per tile or one
  * CTA per tile, FP32 updates of full tiles on the tensor cores or the SIMT pipes, and small-tile
  * POTRF and TRTRI one CTA or one warp per tile. A batch's levels of narrow supernodes

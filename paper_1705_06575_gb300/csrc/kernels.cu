@@ -2741,12 +2741,16 @@ cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, co
             e = launch_prio(k_update_f32, dim3(g, nb), F32_THREADS, 0, s, prio, d.sn, d.upd_tasks, d.upd_entries,
                             d.rel, Lx, L.off, bt);
         }
-        else if (small && nb > 1 && !alt && d.batch_lanes && d.batch_lanes[li] > 0)  // lanes = matrices
+        // a batch, lanes = matrices: the default of small tiles and of full tiles with small entries
+        // (alternatives: a warp per (tile, matrix) on the tile in shared or global memory), the
+        // alternative of full tiles with large entries (default: one CTA per tile and matrix)
+        else if (nb > 1 && d.batch_lanes && d.batch_lanes[li] > 0 &&
+                 (small || (d.batch_warp && d.batch_warp[li])) != alt)
           e = launch_update_mb<T>(d.batch_lanes[li], g, nb, s, prio, d, Lx, L.off, bt);
         else if (small && nb > 1)  // a batch: one warp per (tile, matrix)
           e = launch_prio(k_update_wb<T>, dim3(g, (nb + WT_WARPS - 1) / WT_WARPS), 32 * WT_WARPS, 0, s, prio,
                           d.sn, d.upd_tasks, d.upd_entries, d.rel, Lx, L.off, (int32_t)nb, bt);
-        else if (!small && nb > 1 && (d.batch_warp && d.batch_warp[li]) != alt)  // small entries of a batch
+        else if (!small && nb > 1 && d.batch_warp && d.batch_warp[li])  // small entries of a batch
           e = launch_prio(k_update_wg<T>, dim3(g, (nb + WT_WARPS - 1) / WT_WARPS), 32 * WT_WARPS, 0, s, prio,
                           d.sn, d.upd_tasks, d.upd_entries, d.rel, Lx, L.off, (int32_t)nb, bt);
         else if (small)

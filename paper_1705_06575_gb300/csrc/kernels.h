@@ -95,10 +95,11 @@ cudaError_t launch_update_tc(dim3 grid, cudaStream_t st, int prio, const DevPlan
                              const Batch &bt, long long *status);
 
 // Whether a factor launch has a second kernel form (the autotuner times both). A batch
-// (nbatch > 1): small-tile updates, POTRF, TRSM and TRTRI, one warp per (tile, matrix) or one
-// CTA per tile and matrix; FP64 updates of full tiles, one CTA per tile and matrix or one warp per
-// (tile, matrix) working in global memory (the default of each is DevPlan::batch_warp; the
-// alternative is the other). One matrix: clustered FP64 updates or one CTA per tile; FP32
+// (nbatch > 1): FP64 updates with lanes mapped to matrices (default for small tiles and for full
+// tiles with small entries, DevPlan::batch_warp) against one warp per (tile, matrix) (small tiles;
+// full tiles with small entries, in global memory) or one CTA per tile and matrix (the default of
+// full tiles with large entries); small-tile POTRF, TRSM and TRTRI, one warp per (tile, matrix)
+// or one CTA per tile and matrix. One matrix: clustered FP64 updates or one CTA per tile; FP32
 // full-tile updates on the tensor cores or the SIMT pipes; small-tile POTRF and TRTRI, one CTA or
 // one warp per tile. fp64: the factor's precision.
 bool factor_launch_has_alternative(const Launch &L, int32_t nbatch, bool fp64);

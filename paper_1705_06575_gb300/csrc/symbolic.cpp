@@ -897,7 +897,7 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
   P.batch_lanes.assign(P.factor_launches.size(), 0);
   for (size_t li = 0; li < P.factor_launches.size(); ++li) {
     const Launch &L = P.factor_launches[li];
-    if (L.kind != K_UPDATE || L.tb != SMALL_TILE) continue;
+    if (L.kind != K_UPDATE) continue;
     double elems = 0.0, cnt = 0.0;
     for (int64_t t = L.off; t < L.off + L.count; ++t) {
       const UpdTask &u = P.upd_tasks[t];
