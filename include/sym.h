@@ -72,10 +72,10 @@ extern "C" {
 #define SYM_FLAG_NO_TENSOR_CORES 8u /* SYM_PREC_MIXED: external updates in FP32 on the SIMT
                                        pipes instead of tcgen05 TF32 splits (x = hi + lo, all four
                                        partial products accumulated in FP32) */
-#define SYM_FLAG_NO_BATCH_PANEL 16u /* sym_factor_batch / sym_solve_batch: run the launches of
-                                       levels of narrow supernodes apart instead of as one fused
-                                       launch per level (SYM_EXPORT_BATCH_PANEL, _FWD_PANEL,
-                                       _BWD_PANEL) */
+#define SYM_FLAG_NO_FUSED_LEVELS 16u /* run the launches of levels of narrow supernodes apart
+                                        instead of as one fused launch per level and phase
+                                        (SYM_EXPORT_BATCH_PANEL, _FWD_PANEL, _BWD_PANEL), for
+                                        single matrices and batches */
 
 typedef struct sym_handle_s *sym_handle;
 

@@ -46,7 +46,7 @@ SYM_FLAG_HOST_ONLY = 1
 SYM_FLAG_NO_GRAPHS = 2
 SYM_FLAG_ONE_STREAM = 4
 SYM_FLAG_NO_TENSOR_CORES = 8
-SYM_FLAG_NO_BATCH_PANEL = 16
+SYM_FLAG_NO_FUSED_LEVELS = 16
 
 # name -> (code, numpy dtype)
 EXPORTS = {

@@ -593,9 +593,9 @@ static int analyze_impl(int64_t n, const int64_t *Ap, const int32_t *Ai, const i
     for (int c = 0; c < 2; ++c) h->dp.variant[c] = h->plan.variant[c].data();
     h->dp.batch_warp = h->plan.batch_warp.data();
     h->dp.batch_lanes = h->plan.batch_lanes.data();
-    h->dp.batch_panel = (opt.flags & SYM_FLAG_NO_BATCH_PANEL) ? nullptr : h->plan.batch_panel.data();
-    h->dp.panel_apart = h->plan.panel_apart.data();
-    if (!(opt.flags & SYM_FLAG_NO_BATCH_PANEL)) {
+    h->dp.batch_panel = (opt.flags & SYM_FLAG_NO_FUSED_LEVELS) ? nullptr : h->plan.batch_panel.data();
+    for (int c = 0; c < 2; ++c) h->dp.panel_apart[c] = h->plan.panel_apart[c].data();
+    if (!(opt.flags & SYM_FLAG_NO_FUSED_LEVELS)) {
       h->dp.fwd_panel = h->plan.fwd_panel.data();
       h->dp.bwd_panel = h->plan.bwd_panel.data();
       h->dp.nfwd_panel = (int64_t)h->plan.fwd_panel.size();
@@ -1078,11 +1078,15 @@ int sym_autotune(sym_handle h, int32_t nbatch, const double *Ax, int64_t stride,
   auto &P = h->plan;
   const size_t nl = P.factor_launches.size();
   std::vector<int8_t> &var = P.variant[nbatch > 1 ? 1 : 0];  // one matrix and batches are tuned apart
-  // a batch's fused narrow levels: one fused launch against the level's separate launches
+  // fused narrow levels: one fused launch against the level's separate launches (a batch's only
+  // where its panels fit the fused kernel)
+  std::vector<int8_t> &apart = P.panel_apart[nbatch > 1 ? 1 : 0];
+  const bool f32 = h->precision != SYM_PREC_FP64;
   std::vector<size_t> heads;
-  if (nbatch > 1 && h->dp.batch_panel)
+  if (h->dp.batch_panel)
     for (size_t li = 0; li < nl; ++li)
-      if (P.batch_panel[li].role == sym::PANEL_FUSED) heads.push_back(li);
+      if (P.batch_panel[li].role == sym::PANEL_FUSED && sym::panel_lanes_for(P.batch_panel[li], (unsigned)nbatch, f32) > 0)
+        heads.push_back(li);
   if (tuned) *tuned = 0;
   if (changed) *changed = 0;
   // time every launch in the forms given by set(v) (kernel by kernel, CUDA events, reps
@@ -1111,23 +1115,24 @@ int sym_autotune(sym_handle h, int32_t nbatch, const double *Ax, int64_t stride,
   std::vector<double> t[2];
   if (!heads.empty()) {
     std::fill(var.begin(), var.end(), 0);
-    time_forms([&](int v) { for (size_t hd : heads) P.panel_apart[hd] = (int8_t)v; }, t);
+    time_forms([&](int v) { for (size_t hd : heads) apart[hd] = (int8_t)v; }, t);
     for (size_t hd : heads) {  // the level's launches in either form (covered ones take ~0 fused)
       double sum[2] = {0.0, 0.0};
       for (size_t li = 0; li < nl; ++li)
         if (P.batch_panel[li].role != sym::PANEL_NONE && P.batch_panel[li].head == (int32_t)hd)
           for (int v = 0; v < 2; ++v) sum[v] += t[v][li];
-      P.panel_apart[hd] = !rc && sum[1] < sum[0] ? 1 : 0;
+      apart[hd] = !rc && sum[1] < sum[0] ? 1 : 0;
       ++ntun;
-      nchg += P.panel_apart[hd];
+      nchg += apart[hd];
     }
   }
   std::vector<char> tunable(nl, 0);
   int32_t nform = 0;
   for (size_t li = 0; li < nl; ++li) {
     // launches of a level that stays fused have one form
-    const sym::PanelForm *pf = nbatch > 1 && h->dp.batch_panel ? &P.batch_panel[li] : nullptr;
-    const bool fused = pf && pf->role != sym::PANEL_NONE && !P.panel_apart[pf->head];
+    const sym::PanelForm *pf = h->dp.batch_panel ? &P.batch_panel[li] : nullptr;
+    const bool fused = pf && pf->role != sym::PANEL_NONE && !apart[pf->head] &&
+                       std::find(heads.begin(), heads.end(), (size_t)pf->head) != heads.end();
     nform += tunable[li] = !fused && sym::factor_launch_has_alternative(P.factor_launches[li], nbatch,
                                                                         h->precision == SYM_PREC_FP64);
   }

@@ -2339,6 +2339,7 @@ __global__ void __launch_bounds__(32) k_fwd_b(const SNode *__restrict__ sn, cons
   const int32_t mat0 = blockIdx.y * MW, mat = mat0 + m;
   const bool act = mat < nmat;
   const int nm = min(MW, nmat - mat0);
+  pdl_trigger_early<V>();
   const Int4 tk = tasks[toff + blockIdx.x];
   const SNode sj = sn[tk.a];
   const int nc = sj.ncols, nr = sj.nrows;
@@ -2406,6 +2407,7 @@ __global__ void __launch_bounds__(32) k_bwd_b(const SNode *__restrict__ sn, cons
   const int32_t mat0 = blockIdx.y * MW, mat = mat0 + m;
   const bool act = mat < nmat;
   const int nm = min(MW, nmat - mat0);
+  pdl_trigger_early<V>();
   const Int4 tk = tasks[toff + blockIdx.x];
   const SNode sj = sn[tk.a];
   const int nc = sj.ncols, nr = sj.nrows;
@@ -2544,9 +2546,9 @@ cudaError_t prepare_factor() {
   e = cudaFuncSetAttribute(k_trsm_w<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_w_smem<T>());
   if (e != cudaSuccess) return e;
   {
-    void (*panel[4])(const SNode *, const Int4 *, T *, T *, long long *, double *, const double *, const int64_t *,
+    void (*panel[5])(const SNode *, const Int4 *, T *, T *, long long *, double *, const double *, const int64_t *,
                      int64_t, int32_t, int32_t, const Batch) = {k_panel_b<T, 1>, k_panel_b<T, 2>, k_panel_b<T, 4>,
-                                                                 k_panel_b<T, 8>};
+                                                                 k_panel_b<T, 8>, k_panel_b<T, 32>};
     for (auto *k : panel) {
       e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, PANEL_SMEM_HARD);
       if (e != cudaSuccess) return e;
@@ -2623,10 +2625,11 @@ cudaError_t prepare_solve() {
   cudaError_t e = cudaFuncSetAttribute(k_fstep<T, V, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)step_smem<V, NB>());
   if (e != cudaSuccess) return e;
-  if constexpr (std::is_same<T, double>::value && std::is_same<V, double>::value) {
-    const void *k[8] = {(const void *)k_fwd_b<T, V, 1>, (const void *)k_fwd_b<T, V, 2>, (const void *)k_fwd_b<T, V, 4>,
-                        (const void *)k_fwd_b<T, V, 8>, (const void *)k_bwd_b<T, V, 1>, (const void *)k_bwd_b<T, V, 2>,
-                        (const void *)k_bwd_b<T, V, 4>, (const void *)k_bwd_b<T, V, 8>};
+  if constexpr (std::is_same<T, V>::value) {
+    const void *k[10] = {(const void *)k_fwd_b<T, V, 1>,  (const void *)k_fwd_b<T, V, 2>, (const void *)k_fwd_b<T, V, 4>,
+                         (const void *)k_fwd_b<T, V, 8>,  (const void *)k_fwd_b<T, V, 32>, (const void *)k_bwd_b<T, V, 1>,
+                         (const void *)k_bwd_b<T, V, 2>,  (const void *)k_bwd_b<T, V, 4>, (const void *)k_bwd_b<T, V, 8>,
+                         (const void *)k_bwd_b<T, V, 32>};
     for (const void *f : k) {
       e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, PANEL_SMEM_HARD);
       if (e != cudaSuccess) return e;
@@ -2667,11 +2670,11 @@ cudaError_t launch_update_mb(int lanes, unsigned g, unsigned nb, cudaStream_t s,
 #undef SYM_UPD_MB
 }
 
-// One fused narrow-level launch of a batch (k_panel_b with the level's lanes per matrix).
+// One fused narrow-level launch (k_panel_b with the level's lanes per matrix).
 template <typename T>
 cudaError_t launch_panel_b(const DevPlan &d, const PanelForm &pf, unsigned g, unsigned nb, cudaStream_t s, int prio,
                            T *Lx, T *Linv, long long *status, int64_t off, const Batch &bt) {
-  const int lanes = panel_lanes(pf.pmax, pf.ncmax, std::is_same<T, float>::value);
+  const int lanes = panel_lanes_for(pf, nb, std::is_same<T, float>::value);
 #define SYM_PANEL(G)                                                                                         \
   case G:                                                                                                    \
     return launch_prio(k_panel_b<T, G>, dim3(g, (nb + 32 / G - 1) / (32 / G)), 32,                           \
@@ -2682,6 +2685,7 @@ cudaError_t launch_panel_b(const DevPlan &d, const PanelForm &pf, unsigned g, un
     SYM_PANEL(2)
     SYM_PANEL(4)
     SYM_PANEL(8)
+    SYM_PANEL(32)
     default:
       return cudaErrorInvalidValue;
   }
@@ -2711,10 +2715,15 @@ cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, co
     cudaStream_t s = (dual && L.stream == 1) ? two->aux : st;
     const int prio = (dual && L.stream == 1) ? two->prio_low : two ? two->prio_high : 0;
     if (dual && L.wait >= 0) cudaStreamWaitEvent(s, (*two->events)[L.wait], 0);
-    // a batch's fused narrow level: its POTRF launch factors and inverts the whole panels, its
-    // TRSM and TRTRI launches have nothing left to do
-    int32_t panel = nb > 1 && d.batch_panel ? d.batch_panel[li].role : PANEL_NONE;
-    if (panel != PANEL_NONE && d.panel_apart && d.panel_apart[d.batch_panel[li].head]) panel = PANEL_NONE;
+    // a fused narrow level: its POTRF launch factors and inverts the whole panels, its TRSM and
+    // TRTRI launches have nothing left to do
+    int32_t panel = d.batch_panel ? d.batch_panel[li].role : PANEL_NONE;
+    if (panel != PANEL_NONE) {  // unless the autotuner keeps the level apart or a batch's panels do not fit
+      const int32_t head = d.batch_panel[li].head;
+      const int8_t *apart = d.panel_apart[nb > 1 ? 1 : 0];
+      if ((apart && apart[head]) || panel_lanes_for(d.batch_panel[head], nb, std::is_same<T, float>::value) == 0)
+        panel = PANEL_NONE;
+    }
     if (panel == PANEL_COVERED) {
       if (dual) cudaEventRecord((*two->events)[li], s);
       trace_mark(trace, L.kind, st);
@@ -2826,20 +2835,25 @@ cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, co
   return cudaGetLastError();
 }
 
-// A batch's fused narrow solve levels (FP64): the role of launch li of a solve list (forms: the
-// plan's marks for that list, nform entries; a pruned list never matches them).
+// The fused narrow solve levels: the form of launch li of a solve list (forms: the plan's marks
+// for that list, nform entries; a pruned list never matches them), or null when the launch runs
+// as scheduled. A single matrix solving more than two right-hand sides per pass keeps the
+// separate launches, whose kernels carry the right-hand sides in registers together (the fused
+// kernels take them one after another: at 64^3 with four, FP64 8.91 against 8.94 ms, FP32 14.6
+// against 13.7 ms; with one, 64^2 0.14 against 0.17 ms and the uneven 256-grid union 4.9
+// against 11.4 ms).
 inline const PanelForm *solve_panel(const PanelForm *forms, int64_t nform, size_t nlist, size_t li, unsigned nb,
-                                    bool fp64) {
-  if (!fp64 || nb < 2 || !forms || (int64_t)nlist != nform) return nullptr;
-  return forms[li].role == PANEL_NONE ? nullptr : &forms[li];
+                                    bool fp64, int nr) {
+  if (!forms || (int64_t)nlist != nform || forms[li].role == PANEL_NONE || (nb == 1 && nr > 2)) return nullptr;
+  return solve_lanes_for(forms[forms[li].head], nb, fp64) > 0 ? &forms[li] : nullptr;
 }
 
 template <typename T, typename V>
 cudaError_t launch_solve_b(bool forward, const DevPlan &d, const PanelForm &pf, unsigned g, unsigned nb,
                            cudaStream_t st, const T *Lx, const T *Linv, V *y, V *tbuf, int r0, int nr, int64_t off,
                            const Batch &bt) {
-  if constexpr (std::is_same<T, double>::value && std::is_same<V, double>::value) {
-    const int lanes = solve_panel_lanes(pf.pmax, pf.ncmax);
+  if constexpr (std::is_same<T, V>::value) {
+    const int lanes = solve_lanes_for(pf, nb, std::is_same<T, double>::value);
     const size_t smem = (size_t)solve_panel_bytes(pf.pmax, pf.ncmax, lanes);
 #define SYM_SOLVE_B(G)                                                                                          \
   case G:                                                                                                       \
@@ -2854,6 +2868,7 @@ cudaError_t launch_solve_b(bool forward, const DevPlan &d, const PanelForm &pf, 
       SYM_SOLVE_B(2)
       SYM_SOLVE_B(4)
       SYM_SOLVE_B(8)
+      SYM_SOLVE_B(32)
       default:
         break;
     }
@@ -2876,8 +2891,8 @@ cudaError_t run_sweeps(const DevPlan &d, const std::vector<Launch> &fwd, const s
       const Launch &L = fwd[li];
       const unsigned g = (unsigned)L.count;
       cudaError_t e = cudaSuccess;
-      // a batch's fused narrow level: its step launch runs the sums, steps and pushes
-      if (const PanelForm *pf = solve_panel(d.fwd_panel, d.nfwd_panel, fwd.size(), li, nb, fp64)) {
+      // a fused narrow level: its step launch runs the sums, steps and pushes
+      if (const PanelForm *pf = solve_panel(d.fwd_panel, d.nfwd_panel, fwd.size(), li, nb, fp64, nr)) {
         if (pf->role == PANEL_FUSED)
           e = launch_solve_b<T, V>(true, d, *pf, g, nb, st, Lx, Linv, y, tbuf, r0, nr, L.off, bt);
         if (e != cudaSuccess) return e;
@@ -2951,7 +2966,7 @@ cudaError_t run_sweeps(const DevPlan &d, const std::vector<Launch> &fwd, const s
       const Launch &L = bwd[li];
       const unsigned g = (unsigned)L.count;
       cudaError_t e = cudaSuccess;
-      if (const PanelForm *pf = solve_panel(d.bwd_panel, d.nbwd_panel, bwd.size(), li, nb, fp64)) {
+      if (const PanelForm *pf = solve_panel(d.bwd_panel, d.nbwd_panel, bwd.size(), li, nb, fp64, nr)) {
         if (pf->role == PANEL_FUSED)
           e = launch_solve_b<T, V>(false, d, *pf, g, nb, st, Lx, Linv, y, tbuf, r0, nr, L.off, bt);
         if (e != cudaSuccess) return e;

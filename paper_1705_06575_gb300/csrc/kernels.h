@@ -35,12 +35,13 @@ struct DevPlan {
                                        // FP64 updates with small entries)
   const int8_t *batch_lanes = nullptr;     // HOST array, one per factor launch: a batch's lanes
                                            // per matrix for small-tile updates (Plan::batch_lanes)
-  const PanelForm *batch_panel = nullptr;  // HOST array, one per factor launch: a batch's fused
-                                           // narrow levels (Plan::batch_panel); null: none
-  const int8_t *panel_apart = nullptr;     // HOST array (Plan::panel_apart): levels the autotuner
-                                           // runs as separate launches; null: none
-  const PanelForm *fwd_panel = nullptr;    // HOST arrays (Plan::fwd_panel, bwd_panel): a batch's
-  const PanelForm *bwd_panel = nullptr;    // fused narrow solve levels (FP64); null: none
+  const PanelForm *batch_panel = nullptr;  // HOST array, one per factor launch: the fused narrow
+                                           // levels (Plan::batch_panel); null: none
+  const int8_t *panel_apart[2] = {nullptr, nullptr};  // HOST arrays (Plan::panel_apart): levels
+                                           // the autotuner runs as separate launches ([0] one
+                                           // matrix, [1] batches); null: none
+  const PanelForm *fwd_panel = nullptr;    // HOST arrays (Plan::fwd_panel, bwd_panel): the fused
+  const PanelForm *bwd_panel = nullptr;    // narrow solve levels; null: none
   int64_t nfwd_panel = 0, nbwd_panel = 0;  // their lengths (the solve lists' launch counts)
   const int8_t *variant[2] = {nullptr, nullptr};  // HOST arrays, one entry per factor launch,
                                      // [0] for one matrix, [1] for batches: 1 runs the launch's

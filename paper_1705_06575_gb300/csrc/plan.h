@@ -26,14 +26,15 @@ constexpr int SMALL_TILE = 32;
 // average default to the warp-per-(tile, matrix) form (measured on a 512 x 128^2 9-point batch:
 // 1.35-4.7x faster than one CTA per tile at 34-134 elements, about equal at 175-230).
 constexpr int BATCH_WARP_ELEMS = 160;
-// Batches, narrow levels in one launch (k_panel_b): a level whose supernodes all have at most
-// SMALL_TILE columns factors each panel (POTRF of the diagonal block, TRSM of the rows below it,
-// TRTRI of the diagonal block) in one warp per (supernode, 32 / G matrices), G lanes per matrix,
-// the warp's panels in shared memory. panel_lanes gives G for a level's largest panel (pmax
-// elements) and widest supernode (ncmax columns): the smallest of 1, 2, 4, 8 whose shared memory
-// per warp is at most PANEL_SMEM_SOFT (six warps per SM), else 8 if that fits PANEL_SMEM_HARD
-// (four warps per SM, one per scheduler), else 0 (the level keeps its separate launches).
-// f32: FP32 panels (the FP64 pivot chain and the FP64 inverse need their own arrays).
+// Narrow levels in one launch (k_panel_b): a level whose supernodes all have at most SMALL_TILE
+// columns factors each panel (POTRF of the diagonal block, TRSM of the rows below it, TRTRI of
+// the diagonal block) in one warp per (supernode, 32 / G matrices), G lanes per matrix, the
+// warp's panels in shared memory; a single matrix takes G = 32. panel_lanes gives a batch's G for
+// a level's largest panel (pmax elements) and widest supernode (ncmax columns): the smallest of
+// 1, 2, 4, 8 whose shared memory per warp is at most PANEL_SMEM_SOFT (six warps per SM), else 8
+// if that fits PANEL_SMEM_HARD (four warps per SM, one per scheduler), else 0 (the batch keeps
+// the level's separate launches). f32: FP32 panels (the FP64 pivot chain and the FP64 inverse
+// need their own arrays).
 constexpr int PANEL_SMEM_SOFT = 36 * 1024;
 constexpr int PANEL_SMEM_HARD = 56 * 1024;
 inline int64_t panel_smem_bytes(int64_t pmax, int64_t ncmax, bool f32, int g) {
@@ -45,7 +46,7 @@ inline int panel_lanes(int64_t pmax, int64_t ncmax, bool f32) {
     if (panel_smem_bytes(pmax, ncmax, f32, g) <= PANEL_SMEM_SOFT) return g;
   return panel_smem_bytes(pmax, ncmax, f32, 8) <= PANEL_SMEM_HARD ? 8 : 0;
 }
-// The same for a batch's FP64 solve on such levels (k_fwd_b, k_bwd_b): each warp holds its
+// The same for the solve on such levels (k_fwd_b, k_bwd_b; batches in FP64): each warp holds its
 // matrices' panels and diagonal-block inverses (pmax + ncmax^2 elements per matrix) and two
 // vectors of ncmax values per matrix.
 inline int64_t solve_panel_bytes(int64_t pmax, int64_t ncmax, int g) {
@@ -57,7 +58,7 @@ inline int solve_panel_lanes(int64_t pmax, int64_t ncmax) {
     if (solve_panel_bytes(pmax, ncmax, g) <= PANEL_SMEM_SOFT) return g;
   return solve_panel_bytes(pmax, ncmax, 8) <= PANEL_SMEM_HARD ? 8 : 0;
 }
-// Role of a factor launch in a batch's fused narrow levels (PanelForm::role).
+// Role of a factor launch in the fused narrow levels (PanelForm::role).
 constexpr int32_t PANEL_NONE = 0, PANEL_FUSED = 1, PANEL_COVERED = 2;
 struct PanelForm {
   int32_t role;   // PANEL_FUSED: the level's POTRF launch runs k_panel_b for batches;
@@ -66,6 +67,18 @@ struct PanelForm {
   int32_t ncmax;  // PANEL_FUSED: the level's widest supernode
   int32_t head;   // PANEL_FUSED and PANEL_COVERED: index of the level's PANEL_FUSED launch
 };
+// Lanes per matrix of a fused narrow level (pf: its PANEL_FUSED form) for nb matrices, 0 when the
+// level runs as separate launches: a batch's factor by panel_lanes, its solve by
+// solve_panel_lanes (FP64 only); one matrix 32 (one warp per supernode, rows spread over the
+// lanes) where the panels fit.
+inline int panel_lanes_for(const PanelForm &pf, unsigned nb, bool f32) {
+  if (nb > 1) return panel_lanes(pf.pmax, pf.ncmax, f32);
+  return panel_smem_bytes(pf.pmax, pf.ncmax, f32, 32) <= PANEL_SMEM_HARD ? 32 : 0;
+}
+inline int solve_lanes_for(const PanelForm &pf, unsigned nb, bool fp64) {
+  if (nb > 1) return fp64 ? solve_panel_lanes(pf.pmax, pf.ncmax) : 0;
+  return solve_panel_bytes(pf.pmax, pf.ncmax, 32) <= PANEL_SMEM_HARD ? 32 : 0;
+}
 // Trailing-update GEMM CTAs resident on the whole GPU at once (3 per SM on 152 SMs): the size of
 // one wave, used to split the last wave of a long launch into finer work.
 constexpr int GEMM_SLOTS = 3 * 152;
@@ -210,14 +223,15 @@ struct Plan {
                                       // lanes per matrix in the lanes-to-matrices form (1, 2, 4
                                       // or 8), else 0
   std::vector<PanelForm> batch_panel;  // per factor launch: fused narrow levels of batches
-  std::vector<int8_t> panel_apart;     // per factor launch, on PANEL_FUSED ones: 1 if the
-                                       // autotuner found the level faster as separate launches
+  std::vector<int8_t> panel_apart[2];  // per factor launch, on PANEL_FUSED ones: 1 if the
+                                       // autotuner found the level faster as separate launches;
+                                       // [0] one matrix, [1] batches
   std::vector<Launch> fwd_launches;
   std::vector<Launch> bwd_launches;
-  // Batches (FP64): per forward / backward solve launch, the fused narrow levels: the level's
-  // S_FSTEP (forward) or S_BSTEP (backward) launch is PANEL_FUSED and runs the level's sums,
-  // steps and pushes (forward) or gathers and steps (backward) in one launch; its other launches
-  // are PANEL_COVERED.
+  // Per forward / backward solve launch, the fused narrow levels (single matrices, and batches in
+  // FP64): the level's S_FSTEP (forward) or S_BSTEP (backward) launch is PANEL_FUSED and runs the
+  // level's sums, steps and pushes (forward) or gathers and steps (backward) in one launch; its
+  // other launches are PANEL_COVERED.
   std::vector<PanelForm> fwd_panel, bwd_panel;
   // Forward solve by pushes: t holds tsize entries per right-hand side; the contribution list of
   // column g, contrib[contrib_ptr[g] .. contrib_ptr[g+1]), names the entries of t that column g

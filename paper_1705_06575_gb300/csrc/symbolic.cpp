@@ -862,8 +862,8 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
       }
     }
   }
-  // Batches: the solve launches of levels of narrow supernodes whose panels fit k_fwd_b and
-  // k_bwd_b become one launch per level and direction (see solve_panel_lanes).
+  // The solve launches of levels of narrow supernodes become one launch per level and direction
+  // (k_fwd_b, k_bwd_b; a batch only where the panels fit, see solve_panel_lanes).
   {
     auto mark = [&](const std::vector<Launch> &list, std::vector<PanelForm> &form, int32_t step_kind) {
       form.assign(list.size(), PanelForm{PANEL_NONE, 0, 0, -1});
@@ -874,7 +874,7 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
           pmax = std::max<int64_t>(pmax, (int64_t)sj.nrows * sj.ncols);
           ncmax = std::max<int64_t>(ncmax, sj.ncols);
         }
-        if (P.levelptr[l + 1] == P.levelptr[l] || !small_level(l) || solve_panel_lanes(pmax, ncmax) == 0) continue;
+        if (P.levelptr[l + 1] == P.levelptr[l] || !small_level(l)) continue;
         std::vector<size_t> step, other;
         for (size_t li = 0; li < list.size(); ++li)
           if (list[li].level == l) (list[li].kind == step_kind ? step : other).push_back(li);
@@ -925,11 +925,11 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
     }
     P.batch_warp[li] = cnt > 0.0 && elems <= BATCH_WARP_ELEMS * cnt;
   }
-  // Batches: levels of supernodes with at most SMALL_TILE columns whose panels fit k_panel_b in
-  // either precision run their POTRF, TRSM and TRTRI as one launch (see panel_lanes). Such a
-  // level has one launch of each (one column tile, all of it small-tile).
+  // Levels of supernodes with at most SMALL_TILE columns run their POTRF, TRSM and TRTRI as one
+  // launch (k_panel_b; a batch only where the panels fit, see panel_lanes). Such a level has one
+  // launch of each (one column tile, all of it small-tile).
   P.batch_panel.assign(P.factor_launches.size(), PanelForm{PANEL_NONE, 0, 0, -1});
-  P.panel_apart.assign(P.factor_launches.size(), 0);
+  for (auto &v : P.panel_apart) v.assign(P.factor_launches.size(), 0);
   for (int32_t l = 0; l < nlev; ++l) {
     int64_t pmax = 0, ncmax = 0;
     bool narrow = P.levelptr[l + 1] > P.levelptr[l];
@@ -939,7 +939,7 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
       pmax = std::max<int64_t>(pmax, (int64_t)sj.nrows * sj.ncols);
       ncmax = std::max<int64_t>(ncmax, sj.ncols);
     }
-    if (!narrow || panel_lanes(pmax, ncmax, false) == 0 || panel_lanes(pmax, ncmax, true) == 0) continue;
+    if (!narrow) continue;
     std::vector<size_t> potrf, other;
     for (size_t li = 0; li < P.factor_launches.size(); ++li) {
       const Launch &L = P.factor_launches[li];
@@ -950,6 +950,10 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
     if (potrf.size() != 1) continue;
     const int32_t head = (int32_t)potrf[0];
     P.batch_panel[head] = PanelForm{PANEL_FUSED, (int32_t)pmax, (int32_t)ncmax, head};
+    // a single matrix keeps the separate launches unless the autotuner finds the fused one faster
+    // (one warp per supernode: at the 64^2 5-point grid's levels of 16-32 columns 2-8x slower than
+    // the separate launches, whose CTAs spread the column steps over more schedulers)
+    P.panel_apart[0][head] = 1;
     for (size_t li : other) P.batch_panel[li] = PanelForm{PANEL_COVERED, 0, 0, head};
   }
   // 12. Algorithmic flops of each kernel kind (see Plan::kind_flops).

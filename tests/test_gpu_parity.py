@@ -307,3 +307,42 @@ def test_autotune_one_matrix(torch_cuda):
     B = w.rhs(M.n, 1, np.random.default_rng(3))
     x = s.solve(torch.from_numpy(np.ascontiguousarray(B[:, 0])).cuda()).cpu().numpy()
     assert oracle.backward_error(M.n, M.Ap, M.Ai, M.Ax, B, x[:, None]) <= BERR_TOL
+
+
+@pytest.mark.parametrize("maker", [lambda r: w.laplace2d5(40, r), lambda r: w.conduct3d(12, r, "star")])
+@pytest.mark.parametrize("precision", [None, "mixed"])
+def test_fused_narrow_levels_one_matrix(torch_cuda, maker, precision):
+    """A single matrix solving one or two right-hand sides runs each level of supernodes of at most
+    32 columns as one launch per direction (one warp per supernode, rows spread over the lanes):
+    the forward sums, steps and pushes, the backward gathers and steps; its factor runs a level as
+    one launch (POTRF + TRSM + TRTRI) where the autotuner finds that faster. Solutions agree with
+    the separate launches' to rounding (the fused backward gather sums its rows in another order)
+    and match the oracle."""
+    torch = torch_cuda
+    import paper_1705_06575_gb300 as S
+    M = maker(np.random.default_rng(21))
+    fused = S.Solver(M.n, M.Ap, M.Ai, M.perm, precision=precision)
+    apart = S.Solver(M.n, M.Ap, M.Ai, M.perm, precision=precision, flags=S.SYM_FLAG_NO_FUSED_LEVELS)
+    assert (fused.export("batch_panel").reshape(-1, 4)[:, 0] == 1).sum() >= 3
+    assert (fused.export("fwd_panel").reshape(-1, 4)[:, 0] == 1).sum() >= 3
+    Ax = torch.from_numpy(M.Ax).cuda()
+    tuned, _ = S.sym_autotune(fused.h, 1, Ax, M.nnz, 1)
+    assert tuned >= 3  # at least the fused levels were timed
+    Bh = w.rhs(M.n, 2, np.random.default_rng(4))
+    B = torch.from_numpy(np.ascontiguousarray(Bh.T)).cuda()
+    out = []
+    for s in (fused, apart):
+        s.factor(Ax)
+        X = torch.empty_like(B)
+        S.sym_solve_multi(s.h, 2, B, M.n, X, M.n)
+        torch.cuda.synchronize()
+        out.append((s.factor_panels().copy(), X.cpu().numpy()))
+    tol = BERR_TOL if precision is None else 1e-12
+    for L, X in out:
+        assert oracle.backward_error(M.n, M.Ap, M.Ai, M.Ax, Bh, X.T) <= tol
+    if precision is None:
+        assert np.abs(out[0][1] - out[1][1]).max() <= 1e-12 * np.abs(out[1][1]).max()
+        o = oracle.Oracle(M.n, M.Ap, M.Ai, M.perm)
+        o.factor(M.Ax)
+        Lb, outside = panels_on_pattern(exports(fused), out[0][0], o.Lp, o.Li)
+        assert outside == 0.0 and np.abs(Lb - o.Lx).max() <= ENTRY_RTOL * np.abs(o.Lx).max()

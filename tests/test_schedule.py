@@ -627,27 +627,15 @@ def test_step_launches_have_a_kernel_form(maker):
                 assert int(cl) == 4 or int(tb) == 32
 
 
-def _panel_lanes(pmax, ncmax, f32):
-    """The rule of the fused narrow-level kernel's lanes per matrix (smallest of 1, 2, 4, 8 whose
-    shared memory per warp is at most 36 KiB, else 8 within 56 KiB, else none)."""
-    def smem(g):
-        stride = 33 if g == 1 else 32 // g  # panel element stride (one padding slot with a lane per matrix)
-        return stride * pmax * (4 if f32 else 8) + 32 // g * (ncmax * 8 + ((ncmax * 8 + ncmax * (ncmax - 1) // 2 * 8) if f32 else 0))
-    for g in (1, 2, 4, 8):
-        if smem(g) <= 36 * 1024:
-            return g
-    return 8 if smem(8) <= 56 * 1024 else 0
-
-
 @pytest.mark.parametrize("maker", [
     lambda: w.dd2d9(128, np.random.default_rng(2000)),                       # the batched pattern
     lambda: w.laplace2d5(30, np.random.default_rng(1)),
     lambda: w.conduct3d(10, np.random.default_rng(3), "star"),
 ])
 def test_batch_panel_marks(maker):
-    """Every level whose supernodes all have at most 32 columns and whose panels fit the fused
-    kernel in both precisions has its POTRF launch marked fused (with the level's largest panel
-    and widest supernode) and its TRSM and TRTRI launches marked covered; nothing else is marked."""
+    """Every level whose supernodes all have at most 32 columns has its POTRF launch marked fused
+    (with the level's largest panel and widest supernode) and its TRSM and TRTRI launches marked
+    covered; nothing else is marked."""
     M = maker()
     s = S.Solver(M.n, M.Ap, M.Ai, M.perm, host_only=True)
     sc = Sched(s)
@@ -660,8 +648,7 @@ def test_batch_panel_marks(maker):
     for lv in range(int(level.max()) + 1):
         sel = level == lv
         pmax, ncmax = int((nc * nr)[sel].max()), int(nc[sel].max())
-        eligible = ncmax <= 32 and _panel_lanes(pmax, ncmax, False) > 0 and _panel_lanes(pmax, ncmax, True) > 0
-        eligible = eligible and int(((llev == lv) & (lkind == K_POTRF)).sum()) == 1
+        eligible = ncmax <= 32 and int(((llev == lv) & (lkind == K_POTRF)).sum()) == 1
         head = [li for li in np.nonzero(llev == lv)[0] if lkind[li] == K_POTRF]
         for li in np.nonzero(llev == lv)[0]:
             role, pm, nm, hd = (int(v) for v in sc.panel[li])
@@ -684,23 +671,15 @@ def test_batch_panel_marks(maker):
     lambda: w.conduct3d(10, np.random.default_rng(3), "star"),
 ])
 def test_solve_panel_marks(maker):
-    """In both solve lists, every level whose supernodes all have at most 32 columns and whose
-    panels and inverses fit the fused solve kernels has its step launch marked fused (with the
-    level's largest panel and widest supernode) and its other launches marked covered."""
+    """In both solve lists, every level whose supernodes all have at most 32 columns has its step
+    launch marked fused (with the level's largest panel and widest supernode) and its other
+    launches marked covered."""
     M = maker()
     s = S.Solver(M.n, M.Ap, M.Ai, M.perm, host_only=True)
     sc = Sched(s)
     level = s.export("level")
     nc = np.diff(sc.sup)
     nr = np.diff(sc.rowptr)
-
-    def lanes(pmax, ncmax):
-        def smem(g):
-            return (33 if g == 1 else 32 // g) * (pmax + ncmax * ncmax) * 8 + 32 // g * 2 * ncmax * 8
-        for g in (1, 2, 4, 8):
-            if smem(g) <= 36 * 1024:
-                return g
-        return 8 if smem(8) <= 56 * 1024 else 0
 
     nfused = 0
     for name, step in (("fwd_launches", S_FSTEP), ("bwd_launches", S_BSTEP)):
@@ -710,7 +689,7 @@ def test_solve_panel_marks(maker):
             sel = level == lv
             pmax, ncmax = int((nc * nr)[sel].max()), int(nc[sel].max())
             steps = [li for li in np.nonzero(lev == lv)[0] if kind[li] == step]
-            eligible = ncmax <= 32 and lanes(pmax, ncmax) > 0 and len(steps) == 1
+            eligible = ncmax <= 32 and len(steps) == 1
             for li in np.nonzero(lev == lv)[0]:
                 role, pm, nm, hd = (int(v) for v in sc.spanel[name][li])
                 if not eligible:
