@@ -36,6 +36,7 @@ constexpr int BATCH_WARP_ELEMS = 160;
 // the level's separate launches). f32: FP32 panels (the FP64 pivot chain and the FP64 inverse
 // need their own arrays).
 constexpr int PANEL_SMEM_SOFT = 36 * 1024;
+constexpr int PANEL_ONE_MIN = 8 * 152;  // see symbolic.cpp (fused factor levels of one matrix)
 constexpr int PANEL_SMEM_HARD = 56 * 1024;
 inline int64_t panel_smem_bytes(int64_t pmax, int64_t ncmax, bool f32, int g) {
   const int64_t stride = g == 1 ? 33 : 32 / g;  // panel element stride (padded with one matrix per lane)

@@ -950,10 +950,12 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
     if (potrf.size() != 1) continue;
     const int32_t head = (int32_t)potrf[0];
     P.batch_panel[head] = PanelForm{PANEL_FUSED, (int32_t)pmax, (int32_t)ncmax, head};
-    // a single matrix keeps the separate launches unless the autotuner finds the fused one faster
-    // (one warp per supernode: at the 64^2 5-point grid's levels of 16-32 columns 2-8x slower than
-    // the separate launches, whose CTAs spread the column steps over more schedulers)
-    P.panel_apart[0][head] = 1;
+    // A single matrix runs the fused launch (one warp per supernode) by default only on levels of
+    // at least PANEL_ONE_MIN supernodes, where many warps per SM hide each one's column chain; on
+    // the 64^2 5-point grid's levels of 16-256 supernodes it was up to 2-8x slower than the
+    // separate launches, whose CTAs spread the column steps over more schedulers. The autotuner
+    // decides either way.
+    P.panel_apart[0][head] = P.levelptr[l + 1] - P.levelptr[l] < PANEL_ONE_MIN;
     for (size_t li : other) P.batch_panel[li] = PanelForm{PANEL_COVERED, 0, 0, head};
   }
   // 12. Algorithmic flops of each kernel kind (see Plan::kind_flops).
