@@ -109,8 +109,8 @@ typedef struct {
   int32_t nlevels;          /* levels of the supernodal tree */
   int32_t max_ncols;        /* widest supernode */
   int64_t npairs;           /* (descendant, ancestor) update pairs */
-  int64_t nlaunch_factor;   /* kernel launches per sym_factor */
-  int64_t nlaunch_solve;    /* kernel launches per sym_solve */
+  int64_t nlaunch_factor;   /* kernel launches per sym_factor (one matrix, current forms) */
+  int64_t nlaunch_solve;    /* kernel launches per sym_solve (one right-hand side) */
   double analyze_seconds;   /* host time of the inspector */
   int64_t device_bytes;     /* device memory held by the handle */
   int64_t upd_tasks;        /* tiles receiving descendant updates */

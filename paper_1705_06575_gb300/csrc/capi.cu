@@ -85,6 +85,7 @@ struct sym_handle_s {
   std::vector<cudaEvent_t> la_events;
   cudaEvent_t la_fork = nullptr, la_join = nullptr;
   sym::TwoStreams two;
+  bool fused_levels = true;  // narrow levels as one launch per phase (SYM_FLAG_NO_FUSED_LEVELS)
   bool lookahead = true;  // run the factor schedule's auxiliary-stream launches concurrently
   // per-kernel profiling
   bool profiling = false;
@@ -478,6 +479,7 @@ static int analyze_impl(int64_t n, const int64_t *Ap, const int32_t *Ai, const i
   h->host_only = (opt.flags & SYM_FLAG_HOST_ONLY) != 0;
   h->use_graphs = (opt.flags & SYM_FLAG_NO_GRAPHS) == 0;
   h->lookahead = (opt.flags & SYM_FLAG_ONE_STREAM) == 0;
+  h->fused_levels = (opt.flags & SYM_FLAG_NO_FUSED_LEVELS) == 0;
   if (!h->host_only) {
     int rc = SYM_OK;
     auto &P = h->plan;
@@ -925,8 +927,21 @@ int sym_info(sym_handle h, sym_stats *s) {
   s->nlevels = (int32_t)P.levelptr.size() - 1;
   s->max_ncols = P.max_ncols;
   s->npairs = (int64_t)P.desc.size();
+  // kernels one matrix launches: the schedule's launches (+ zeroing and scatter, + the two
+  // permutations) minus those of fused narrow levels that a factor, or a solve with one
+  // right-hand side, skips by default
   s->nlaunch_factor = (int64_t)P.factor_launches.size() + 2;
   s->nlaunch_solve = (int64_t)P.fwd_launches.size() + (int64_t)P.bwd_launches.size() + 2;
+  if (h->fused_levels) {
+    const bool f32 = h->precision != SYM_PREC_FP64;
+    for (const sym::PanelForm &pf : P.batch_panel)
+      if (pf.role == sym::PANEL_COVERED && !P.panel_apart[0][pf.head] &&
+          sym::panel_lanes_for(P.batch_panel[pf.head], 1, f32) > 0)
+        --s->nlaunch_factor;
+    for (const auto *forms : {&P.fwd_panel, &P.bwd_panel})
+      for (const sym::PanelForm &pf : *forms)
+        if (pf.role == sym::PANEL_COVERED && sym::solve_lanes_for((*forms)[pf.head], 1, !f32) > 0) --s->nlaunch_solve;
+  }
   s->analyze_seconds = P.analyze_seconds;
   s->device_bytes = h->device_bytes;
   s->upd_tasks = (int64_t)P.upd_tasks.size();

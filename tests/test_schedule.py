@@ -700,3 +700,21 @@ def test_solve_panel_marks(maker):
                 else:
                     assert (role, hd) == (PANEL_COVERED, steps[0])
     assert nfused >= 2
+
+
+def test_launch_counts_skip_fused_levels():
+    """sym_info's kernel counts leave out the launches that a fused narrow level covers: every
+    covered solve launch for one right-hand side (the panels of this grid fit the one-warp form),
+    and none of the factor's on levels of fewer than 1216 supernodes; with the fused levels off,
+    the whole schedule (+ zeroing and scatter, + the two permutations)."""
+    M = w.laplace2d5(30, np.random.default_rng(1))
+    s = S.Solver(M.n, M.Ap, M.Ai, M.perm, host_only=True)
+    off = S.Solver(M.n, M.Ap, M.Ai, M.perm, flags=S.SYM_FLAG_HOST_ONLY | S.SYM_FLAG_NO_FUSED_LEVELS)
+    nf = len(s.export("factor_launches")) // 5
+    nfwd, nbwd = len(s.export("fwd_launches")) // 5, len(s.export("bwd_launches")) // 5
+    covered = int((s.export("fwd_panel").reshape(-1, 4)[:, 0] == 2).sum() +
+                  (s.export("bwd_panel").reshape(-1, 4)[:, 0] == 2).sum())
+    assert covered > 0
+    assert (off.info().nlaunch_factor, off.info().nlaunch_solve) == (nf + 2, nfwd + nbwd + 2)
+    assert s.info().nlaunch_factor == nf + 2  # (no level of this grid has 1216 supernodes)
+    assert s.info().nlaunch_solve == nfwd + nbwd + 2 - covered
