@@ -401,13 +401,14 @@ int sym_get_factor_host(sym_handle h, double *Lx_host);
 #define SYM_EXPORT_TASKS 22
 #define SYM_EXPORT_UPD_TASKS 23
 #define SYM_EXPORT_UPD_ENTRIES 24
-/* Batches: int32 words {role, pmax, ncmax, head} per factor launch. role 1: the POTRF launch of a
- * level whose supernodes all have at most 32 columns; sym_factor_batch factors each of their
+/* Fused narrow levels: int32 words {role, pmax, ncmax, head} per factor launch. role 1: the POTRF
+ * launch of a level whose supernodes all have at most 32 columns, which can factor each of their
  * panels (Cholesky of the diagonal block, triangular solve of the rows below it, inverse of the
  * diagonal block) in this one launch, with pmax the level's largest panel (rows x columns) and
- * ncmax its widest supernode; role 2: that level's TRSM and TRTRI launches, which batches skip;
- * role 0: other launches. head: for roles 1 and 2 the index of the level's role-1 launch, else
- * -1. sym_autotune may return a level to its separate launches. */
+ * ncmax its widest supernode; role 2: that level's TRSM and TRTRI launches, then skipped; role
+ * 0: other launches. head: for roles 1 and 2 the index of the level's role-1 launch, else -1.
+ * Batches run such a level fused where its panels fit the kernel's shared memory; a single
+ * matrix where the level has at least 1216 supernodes; sym_autotune times both ways. */
 #define SYM_EXPORT_BATCH_PANEL 27
 /* The same for the forward and backward solve lists (SYM_EXPORT_FWD_LAUNCHES, _BWD_LAUNCHES):
  * role 1 on the step launch of a level whose supernodes all have at most 32 columns, on which

@@ -223,7 +223,8 @@ struct Plan {
   std::vector<int8_t> batch_lanes;     // per factor launch: for a small-tile update, a batch's
                                       // lanes per matrix in the lanes-to-matrices form (1, 2, 4
                                       // or 8), else 0
-  std::vector<PanelForm> batch_panel;  // per factor launch: fused narrow levels of batches
+  std::vector<PanelForm> batch_panel;  // per factor launch: fused narrow levels (batches and,
+                                       // where panel_apart[0] allows, single matrices)
   std::vector<int8_t> panel_apart[2];  // per factor launch, on PANEL_FUSED ones: 1 if the
                                        // autotuner found the level faster as separate launches;
                                        // [0] one matrix, [1] batches
