@@ -2322,7 +2322,7 @@ __device__ __forceinline__ void stage_panel_inverse(T *S, T *Si, const SNode &sj
   __syncwarp();
 }
 
-template <typename T, typename V, int G>
+template <typename T, typename V, int G, int NR>
 __global__ void __launch_bounds__(32) k_fwd_b(const SNode *__restrict__ sn, const Int4 *__restrict__ tasks,
                                               const int64_t *__restrict__ cptr, const int32_t *__restrict__ contrib,
                                               const T *__restrict__ Lx, const T *__restrict__ Linv,
@@ -2331,9 +2331,9 @@ __global__ void __launch_bounds__(32) k_fwd_b(const SNode *__restrict__ sn, cons
                                               const Batch bt) {
   constexpr int MW = 32 / G, MP = G == 1 ? 33 : MW;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  V *vb = reinterpret_cast<V *>(smem_raw);  // ncmax x MW: y_J after the sums
-  V *ob = vb + (size_t)ncmax * MW;          // ncmax x MW: y_J solved
-  T *S = reinterpret_cast<T *>(ob + (size_t)ncmax * MW);
+  V *vb = reinterpret_cast<V *>(smem_raw);  // NR x ncmax x MW: y_J after the sums
+  V *ob = vb + (size_t)NR * ncmax * MW;     // NR x ncmax x MW: y_J solved
+  T *S = reinterpret_cast<T *>(ob + (size_t)NR * ncmax * MW);
   T *Si = S + (size_t)pmax * MP;
   const int lane = threadIdx.x, m = lane & (MW - 1), q = lane / MW;
   const int32_t mat0 = blockIdx.y * MW, mat = mat0 + m;
@@ -2350,49 +2350,86 @@ __global__ void __launch_bounds__(32) k_fwd_b(const SNode *__restrict__ sn, cons
   y += (int64_t)mat * bt.y;
   t += (int64_t)mat * bt.t;
   const T *Sm = S + m, *Sim = Si + m;
-  for (int rh = 0; rh < nrhs; ++rh) {
-    V *yq = y + (int64_t)(r0 + rh) * n + sj.first;
-    V *tq = t + (int64_t)rh * tsize;
+  auto vs = [&](V *b, int u, int c) -> V & { return b[((size_t)u * ncmax + c) * MW + m]; };
+  for (int rh0 = 0; rh0 < nrhs; rh0 += NR) {  // NR right-hand sides at a time, in registers
+    const int cnt = min(NR, nrhs - rh0);
+    V *yq = y + (int64_t)(r0 + rh0) * n + sj.first;  // right-hand side u at yq + u * n
+    V *tq = t + (int64_t)rh0 * tsize;                 // and tq + u * tsize
     for (int c = q; c < nc; c += G) {  // S_FSUM: y_g minus the sum of its listed products
       const int64_t g = sj.first + c;
-      V acc = V(0);
-      for (int64_t p = cptr[g]; p < cptr[g + 1]; ++p) acc += tq[contrib[p]];
-      vb[c * MW + m] = yq[c] - acc;
+      V acc[NR];
+#pragma unroll
+      for (int u = 0; u < NR; ++u) acc[u] = V(0);
+      for (int64_t p = cptr[g]; p < cptr[g + 1]; ++p) {
+        const int64_t e = contrib[p];
+#pragma unroll
+        for (int u = 0; u < NR; ++u)
+          if (u < cnt) acc[u] += tq[u * tsize + e];
+      }
+#pragma unroll
+      for (int u = 0; u < NR; ++u)
+        if (u < cnt) vs(vb, u, c) = yq[u * n + c] - acc[u];
     }
     __syncwarp(mask);
     for (int r = q; r < nc; r += G) {  // S_FSTEP: row r of L_JJ^-1 y_J, two partial sums
-      V a0 = V(0), a1 = V(0);
+      V a0[NR], a1[NR];
+#pragma unroll
+      for (int u = 0; u < NR; ++u) a0[u] = a1[u] = V(0);
       int k = 0;
       for (; k + 1 <= r; k += 2) {
-        a0 = fma((V)Sim[(k * nc + r) * MP], vb[k * MW + m], a0);
-        a1 = fma((V)Sim[((k + 1) * nc + r) * MP], vb[(k + 1) * MW + m], a1);
+        const V l0 = (V)Sim[(k * nc + r) * MP], l1 = (V)Sim[((k + 1) * nc + r) * MP];
+#pragma unroll
+        for (int u = 0; u < NR; ++u) {
+          a0[u] = fma(l0, vs(vb, u, k), a0[u]);
+          a1[u] = fma(l1, vs(vb, u, k + 1), a1[u]);
+        }
       }
-      if (k <= r) a0 = fma((V)Sim[(k * nc + r) * MP], vb[k * MW + m], a0);
-      const V o = a0 + a1;
-      yq[r] = o;
-      ob[r * MW + m] = o;
+      if (k <= r) {
+        const V l0 = (V)Sim[(k * nc + r) * MP];
+#pragma unroll
+        for (int u = 0; u < NR; ++u) a0[u] = fma(l0, vs(vb, u, k), a0[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < NR; ++u)
+        if (u < cnt) {
+          const V o = a0[u] + a1[u];
+          yq[u * n + r] = o;
+          vs(ob, u, r) = o;
+        }
     }
     __syncwarp(mask);
     for (int rr = nc + q; rr < nr; rr += G) {  // S_FPUSH: four partial sums over the columns
-      V a0 = V(0), a1 = V(0), a2 = V(0), a3 = V(0);  // columns c with c % 4 = 0, 1, 2, 3
+      V a[4][NR];  // columns c with c % 4 = 0, 1, 2, 3
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int u = 0; u < NR; ++u) a[j][u] = V(0);
       const T *lr = Sm + rr * MP;
       int c = 0;
       for (; c + 3 < nc; c += 4) {
-        a0 = fma((V)lr[c * nr * MP], ob[c * MW + m], a0);
-        a1 = fma((V)lr[(c + 1) * nr * MP], ob[(c + 1) * MW + m], a1);
-        a2 = fma((V)lr[(c + 2) * nr * MP], ob[(c + 2) * MW + m], a2);
-        a3 = fma((V)lr[(c + 3) * nr * MP], ob[(c + 3) * MW + m], a3);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const V l = (V)lr[(c + j) * nr * MP];
+#pragma unroll
+          for (int u = 0; u < NR; ++u) a[j][u] = fma(l, vs(ob, u, c + j), a[j][u]);
+        }
       }
-      if (c < nc) a0 = fma((V)lr[c * nr * MP], ob[c * MW + m], a0);
-      if (c + 1 < nc) a1 = fma((V)lr[(c + 1) * nr * MP], ob[(c + 1) * MW + m], a1);
-      if (c + 2 < nc) a2 = fma((V)lr[(c + 2) * nr * MP], ob[(c + 2) * MW + m], a2);
-      tq[sj.tx + (rr - nc)] = (a0 + a1) + (a2 + a3);
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        if (c + j < nc) {
+          const V l = (V)lr[(c + j) * nr * MP];
+#pragma unroll
+          for (int u = 0; u < NR; ++u) a[j][u] = fma(l, vs(ob, u, c + j), a[j][u]);
+        }
+#pragma unroll
+      for (int u = 0; u < NR; ++u)
+        if (u < cnt) tq[u * tsize + sj.tx + (rr - nc)] = (a[0][u] + a[1][u]) + (a[2][u] + a[3][u]);
     }
     __syncwarp(mask);
   }
 }
 
-template <typename T, typename V, int G>
+template <typename T, typename V, int G, int NR>
 __global__ void __launch_bounds__(32) k_bwd_b(const SNode *__restrict__ sn, const int32_t *__restrict__ rows,
                                               const Int4 *__restrict__ tasks, const T *__restrict__ Lx,
                                               const T *__restrict__ Linv, V *__restrict__ y, int64_t n, int r0,
@@ -2400,8 +2437,8 @@ __global__ void __launch_bounds__(32) k_bwd_b(const SNode *__restrict__ sn, cons
                                               const Batch bt) {
   constexpr int MW = 32 / G, MP = G == 1 ? 33 : MW;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  V *zb = reinterpret_cast<V *>(smem_raw);  // ncmax x MW: z_J after the gather
-  T *S = reinterpret_cast<T *>(zb + (size_t)2 * ncmax * MW);
+  V *zb = reinterpret_cast<V *>(smem_raw);  // NR x ncmax x MW: z_J after the gather
+  T *S = reinterpret_cast<T *>(zb + (size_t)2 * NR * ncmax * MW);
   T *Si = S + (size_t)pmax * MP;
   const int lane = threadIdx.x, m = lane & (MW - 1), q = lane / MW;
   const int32_t mat0 = blockIdx.y * MW, mat = mat0 + m;
@@ -2418,23 +2455,47 @@ __global__ void __launch_bounds__(32) k_bwd_b(const SNode *__restrict__ sn, cons
   const unsigned mask = present_lanes(MW, nm);
   y += (int64_t)mat * bt.y;
   const T *Sm = S + m, *Sim = Si + m;
-  for (int rh = 0; rh < nrhs; ++rh) {
-    V *yq = y + (int64_t)(r0 + rh) * n;
+  auto zs = [&](int u, int c) -> V & { return zb[((size_t)u * ncmax + c) * MW + m]; };
+  for (int rh0 = 0; rh0 < nrhs; rh0 += NR) {
+    const int cnt = min(NR, nrhs - rh0);
+    V *yq = y + (int64_t)(r0 + rh0) * n;  // right-hand side u at yq + u * n
     for (int c = q; c < nc; c += G) {  // S_BGATHER
-      V sa = V(0);
-      for (int rr = nc; rr < nr; ++rr) sa = fma((V)Sm[(c * nr + rr) * MP], yq[R[rr]], sa);
-      zb[c * MW + m] = yq[sj.first + c] - sa;
+      V sa[NR];
+#pragma unroll
+      for (int u = 0; u < NR; ++u) sa[u] = V(0);
+      for (int rr = nc; rr < nr; ++rr) {
+        const V l = (V)Sm[(c * nr + rr) * MP];
+        const int64_t g = R[rr];
+#pragma unroll
+        for (int u = 0; u < NR; ++u)
+          if (u < cnt) sa[u] = fma(l, yq[u * n + g], sa[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < NR; ++u)
+        if (u < cnt) zs(u, c) = yq[u * n + sj.first + c] - sa[u];
     }
     __syncwarp(mask);
     for (int r = q; r < nc; r += G) {  // S_BSTEP: row r of L_JJ^-T z_J, two partial sums
-      V a0 = V(0), a1 = V(0);
+      V a0[NR], a1[NR];
+#pragma unroll
+      for (int u = 0; u < NR; ++u) a0[u] = a1[u] = V(0);
       int k = r;
       for (; k + 1 < nc; k += 2) {
-        a0 = fma((V)Sim[(r * nc + k) * MP], zb[k * MW + m], a0);
-        a1 = fma((V)Sim[(r * nc + k + 1) * MP], zb[(k + 1) * MW + m], a1);
+        const V l0 = (V)Sim[(r * nc + k) * MP], l1 = (V)Sim[(r * nc + k + 1) * MP];
+#pragma unroll
+        for (int u = 0; u < NR; ++u) {
+          a0[u] = fma(l0, zs(u, k), a0[u]);
+          a1[u] = fma(l1, zs(u, k + 1), a1[u]);
+        }
       }
-      if (k < nc) a0 = fma((V)Sim[(r * nc + k) * MP], zb[k * MW + m], a0);
-      yq[sj.first + r] = a0 + a1;
+      if (k < nc) {
+        const V l0 = (V)Sim[(r * nc + k) * MP];
+#pragma unroll
+        for (int u = 0; u < NR; ++u) a0[u] = fma(l0, zs(u, k), a0[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < NR; ++u)
+        if (u < cnt) yq[u * n + sj.first + r] = a0[u] + a1[u];
     }
     __syncwarp(mask);
   }
@@ -2626,10 +2687,13 @@ cudaError_t prepare_solve() {
                                        (int)step_smem<V, NB>());
   if (e != cudaSuccess) return e;
   if constexpr (std::is_same<T, V>::value) {
-    const void *k[10] = {(const void *)k_fwd_b<T, V, 1>,  (const void *)k_fwd_b<T, V, 2>, (const void *)k_fwd_b<T, V, 4>,
-                         (const void *)k_fwd_b<T, V, 8>,  (const void *)k_fwd_b<T, V, 32>, (const void *)k_bwd_b<T, V, 1>,
-                         (const void *)k_bwd_b<T, V, 2>,  (const void *)k_bwd_b<T, V, 4>, (const void *)k_bwd_b<T, V, 8>,
-                         (const void *)k_bwd_b<T, V, 32>};
+    const void *k[14] = {(const void *)k_fwd_b<T, V, 1, 1>,  (const void *)k_fwd_b<T, V, 2, 1>,
+                         (const void *)k_fwd_b<T, V, 4, 1>,  (const void *)k_fwd_b<T, V, 8, 1>,
+                         (const void *)k_fwd_b<T, V, 32, 1>, (const void *)k_fwd_b<T, V, 32, 4>,
+                         (const void *)k_fwd_b<T, V, 32, 8>, (const void *)k_bwd_b<T, V, 1, 1>,
+                         (const void *)k_bwd_b<T, V, 2, 1>,  (const void *)k_bwd_b<T, V, 4, 1>,
+                         (const void *)k_bwd_b<T, V, 8, 1>,  (const void *)k_bwd_b<T, V, 32, 1>,
+                         (const void *)k_bwd_b<T, V, 32, 4>, (const void *)k_bwd_b<T, V, 32, 8>};
     for (const void *f : k) {
       e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, PANEL_SMEM_HARD);
       if (e != cudaSuccess) return e;
@@ -2837,14 +2901,14 @@ cudaError_t run_factor(const DevPlan &d, const std::vector<Launch> &launches, co
 
 // The fused narrow solve levels: the form of launch li of a solve list (forms: the plan's marks
 // for that list, nform entries; a pruned list never matches them), or null when the launch runs
-// as scheduled. A single matrix solving more than two right-hand sides per pass keeps the
-// separate launches, whose kernels carry the right-hand sides in registers together (the fused
-// kernels take them one after another: at 64^3 with four, FP64 8.91 against 8.94 ms, FP32 14.6
-// against 13.7 ms; with one, 64^2 0.14 against 0.17 ms and the uneven 256-grid union 4.9
-// against 11.4 ms).
+// as scheduled. A single FP32 matrix solving more than two right-hand sides per pass keeps the
+// separate launches (the 64^3 refined solve with four: 13.9 ms fused against 13.7 ms; FP64 with
+// four 8.74 against 8.96 ms; with one, FP64 and FP32 alike, 64^2 0.14 against 0.17 ms and the
+// uneven 256-grid union 4.9 against 11.4 ms).
 inline const PanelForm *solve_panel(const PanelForm *forms, int64_t nform, size_t nlist, size_t li, unsigned nb,
                                     bool fp64, int nr) {
-  if (!forms || (int64_t)nlist != nform || forms[li].role == PANEL_NONE || (nb == 1 && nr > 2)) return nullptr;
+  if (!forms || (int64_t)nlist != nform || forms[li].role == PANEL_NONE) return nullptr;
+  if (nb == 1 && !fp64 && nr > 2) return nullptr;
   return solve_lanes_for(forms[forms[li].head], nb, fp64) > 0 ? &forms[li] : nullptr;
 }
 
@@ -2854,24 +2918,24 @@ cudaError_t launch_solve_b(bool forward, const DevPlan &d, const PanelForm &pf, 
                            const Batch &bt) {
   if constexpr (std::is_same<T, V>::value) {
     const int lanes = solve_lanes_for(pf, nb, std::is_same<T, double>::value);
-    const size_t smem = (size_t)solve_panel_bytes(pf.pmax, pf.ncmax, lanes);
-#define SYM_SOLVE_B(G)                                                                                          \
-  case G:                                                                                                       \
-    return forward ? launch_pdl(k_fwd_b<T, V, G>, dim3(g, (nb + 32 / G - 1) / (32 / G)), 32, smem, st, d.sn,    \
-                                d.tasks, d.cptr, d.contrib, Lx, Linv, y, tbuf, d.tsize, d.n, r0, nr, off,       \
-                                (int32_t)nb, pf.pmax, pf.ncmax, bt)                                             \
-                   : launch_pdl(k_bwd_b<T, V, G>, dim3(g, (nb + 32 / G - 1) / (32 / G)), 32, smem, st, d.sn,    \
-                                d.rows, d.tasks, Lx, Linv, y, d.n, r0, nr, off, (int32_t)nb, pf.pmax, pf.ncmax, \
-                                bt);
-    switch (lanes) {
-      SYM_SOLVE_B(1)
-      SYM_SOLVE_B(2)
-      SYM_SOLVE_B(4)
-      SYM_SOLVE_B(8)
-      SYM_SOLVE_B(32)
-      default:
-        break;
-    }
+    // right-hand sides per pass of the kernel: batches one at a time, a single matrix 1, 4 or 8
+    const int nrb = nb > 1 || nr <= 2 ? 1 : nr <= 4 ? 4 : 8;
+    const size_t smem = (size_t)solve_panel_bytes(pf.pmax, pf.ncmax, lanes, nrb);
+#define SYM_SOLVE_B(G, NRB)                                                                                      \
+  if (lanes == G && nrb == NRB)                                                                                  \
+    return forward ? launch_pdl(k_fwd_b<T, V, G, NRB>, dim3(g, (nb + 32 / G - 1) / (32 / G)), 32, smem, st,     \
+                                d.sn, d.tasks, d.cptr, d.contrib, Lx, Linv, y, tbuf, d.tsize, d.n, r0, nr, off,  \
+                                (int32_t)nb, pf.pmax, pf.ncmax, bt)                                              \
+                   : launch_pdl(k_bwd_b<T, V, G, NRB>, dim3(g, (nb + 32 / G - 1) / (32 / G)), 32, smem, st,     \
+                                d.sn, d.rows, d.tasks, Lx, Linv, y, d.n, r0, nr, off, (int32_t)nb, pf.pmax,       \
+                                pf.ncmax, bt);
+    SYM_SOLVE_B(1, 1)
+    SYM_SOLVE_B(2, 1)
+    SYM_SOLVE_B(4, 1)
+    SYM_SOLVE_B(8, 1)
+    SYM_SOLVE_B(32, 1)
+    SYM_SOLVE_B(32, 4)
+    SYM_SOLVE_B(32, 8)
 #undef SYM_SOLVE_B
   }
   return cudaErrorInvalidValue;

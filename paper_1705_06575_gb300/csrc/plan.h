@@ -49,10 +49,10 @@ inline int panel_lanes(int64_t pmax, int64_t ncmax, bool f32) {
 }
 // The same for the solve on such levels (k_fwd_b, k_bwd_b; batches in FP64): each warp holds its
 // matrices' panels and diagonal-block inverses (pmax + ncmax^2 elements per matrix) and two
-// vectors of ncmax values per matrix.
-inline int64_t solve_panel_bytes(int64_t pmax, int64_t ncmax, int g) {
-  const int64_t stride = g == 1 ? 33 : 32 / g;
-  return stride * (pmax + ncmax * ncmax) * 8 + (32 / g) * 2 * ncmax * 8;
+// vectors of ncmax values per matrix and right-hand side of a pass.
+inline int64_t solve_panel_bytes(int64_t pmax, int64_t ncmax, int g, int nrb = 1) {
+  const int64_t stride = g == 1 ? 33 : 32 / g;  // nrb: right-hand sides per pass of the kernel
+  return stride * (pmax + ncmax * ncmax) * 8 + (32 / g) * 2 * nrb * ncmax * 8;
 }
 inline int solve_panel_lanes(int64_t pmax, int64_t ncmax) {
   for (int g = 1; g <= 8; g *= 2)
@@ -78,7 +78,7 @@ inline int panel_lanes_for(const PanelForm &pf, unsigned nb, bool f32) {
 }
 inline int solve_lanes_for(const PanelForm &pf, unsigned nb, bool fp64) {
   if (nb > 1) return fp64 ? solve_panel_lanes(pf.pmax, pf.ncmax) : 0;
-  return solve_panel_bytes(pf.pmax, pf.ncmax, 32) <= PANEL_SMEM_HARD ? 32 : 0;
+  return solve_panel_bytes(pf.pmax, pf.ncmax, 32, 8) <= PANEL_SMEM_HARD ? 32 : 0;
 }
 // Trailing-update GEMM CTAs resident on the whole GPU at once (3 per SM on 152 SMs): the size of
 // one wave, used to split the last wave of a long launch into finer work.
