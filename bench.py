@@ -535,10 +535,9 @@ def run_ours(args):
     s = S.Solver(M.n, M.Ap, M.Ai, M.perm)
     analyze_s = time.perf_counter() - t0
     info = s.info()
-    # kernels per step: the factor's (sym_info) and a solve of NRHS > 2 right-hand sides, which
-    # runs every launch of the solve schedule (+ the two permutations)
-    launches_step = int(info.nlaunch_factor) + len(s.export("fwd_launches")) // 5 + \
-        len(s.export("bwd_launches")) // 5 + 2
+    # kernels per step: the factor's and the FP64 solve's (sym_info; the fused narrow levels of an
+    # FP64 solve skip the same launches for any number of right-hand sides)
+    launches_step = int(info.nlaunch_factor + info.nlaunch_solve)
     stream = torch.cuda.current_stream()
     s.set_stream(stream)
     Ax = torch.from_numpy(M.Ax).cuda()

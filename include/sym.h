@@ -110,7 +110,8 @@ typedef struct {
   int32_t max_ncols;        /* widest supernode */
   int64_t npairs;           /* (descendant, ancestor) update pairs */
   int64_t nlaunch_factor;   /* kernel launches per sym_factor (one matrix, current forms) */
-  int64_t nlaunch_solve;    /* kernel launches per sym_solve (one right-hand side) */
+  int64_t nlaunch_solve;    /* kernel launches per sym_solve (FP64 factors: also per pass of up to
+                               8 right-hand sides of sym_solve_multi; FP32: passes of one or two) */
   double analyze_seconds;   /* host time of the inspector */
   int64_t device_bytes;     /* device memory held by the handle */
   int64_t upd_tasks;        /* tiles receiving descendant updates */
