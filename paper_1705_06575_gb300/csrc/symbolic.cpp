@@ -952,9 +952,9 @@ int analyze(int64_t n, const int64_t *Ap, const int32_t *Ai, const int32_t *perm
     P.batch_panel[head] = PanelForm{PANEL_FUSED, (int32_t)pmax, (int32_t)ncmax, head};
     // A single matrix runs the fused launch (one warp per supernode) by default only on levels of
     // at least PANEL_ONE_MIN supernodes, where many warps per SM hide each one's column chain; on
-    // the 64^2 5-point grid's levels of 16-256 supernodes it was up to 2-8x slower than the
-    // separate launches, whose CTAs spread the column steps over more schedulers. The autotuner
-    // decides either way.
+    // the 64^2 5-point grid's levels of 1-64 supernodes of 16-32 columns it was 1.7-4.3x slower
+    // than the separate launches, whose CTAs spread the column steps over more schedulers. The
+    // autotuner decides either way.
     P.panel_apart[0][head] = P.levelptr[l + 1] - P.levelptr[l] < PANEL_ONE_MIN;
     for (size_t li : other) P.batch_panel[li] = PanelForm{PANEL_COVERED, 0, 0, head};
   }
