@@ -1736,13 +1736,13 @@ __device__ __forceinline__ unsigned present_lanes(int MW, int nm) {
   return mask;
 }
 
-// The same for a batch's small tiles with lanes mapped to matrices: one warp per (tile, MW =
-// 32 / G matrices), WT_WARPS matrix groups per CTA; lane q * MW + m takes the elements q, q + G,
-// ... of every entry for matrix m (consecutive elements are consecutive rows, so the G lanes of
-// a matrix read neighbouring operands). The small-tile levels of a batch have entries of a few
-// dozen elements and tiles of a few entries; a warp per (tile, matrix) leaves most lanes idle and
-// spends its time on latency. Element by element the operations of k_update_wb, in its order
-// (bit-identical).
+// The same for a batch with lanes mapped to matrices (tiles of any size, updated in global
+// memory): one warp per (tile, MW = 32 / G matrices), WT_WARPS matrix groups per CTA; lane
+// q * MW + m takes the elements q, q + G, ... of every entry for matrix m (consecutive elements
+// are consecutive rows, so the G lanes of a matrix read neighbouring operands). The small-tile
+// levels of a batch have entries of a few dozen elements and tiles of a few entries; a warp per
+// (tile, matrix) leaves most lanes idle and spends its time on latency. Element by element the
+// operations of k_update_wb and k_update_wg, in their order (bit-identical).
 template <typename T, int G>
 __global__ void __launch_bounds__(32 * WT_WARPS) k_update_mb(const SNode *__restrict__ sn,
                                                              const UpdTask *__restrict__ tasks,
